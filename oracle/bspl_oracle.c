@@ -1,0 +1,1418 @@
+/*
+ * bspl_oracle.c -- TEST INFRASTRUCTURE, not part of the product.
+ *
+ * A plain, slow, obviously-correct FP64 CPU implementation of what the GPU
+ * library computes, written from the paper (Wu & Zou, "Matrix representation
+ * and GPU-optimized parallel B-spline computing", arXiv 2504.11498):
+ *
+ *   - B-spline evaluation by the Cox-de Boor recursion (Sec. 3, Eq. bsplinebasis)
+ *     with basis derivatives (textbook derivative formula).
+ *   - Textbook Boehm knot insertion to Bezier segments (cross-check of Sec. 4.2.1).
+ *   - The paper's span-wise matrix decomposition Q = B_p^{-1} M A P
+ *     (Sec. 4.2.1, Eq. decomfinal), built in the local parameter u.
+ *   - Degree elevation (p < 3), the G1-continuous L2-optimal reduction to a cubic
+ *     (Sec. 4.2.2, Eqs. G1-condition, epsl, differentiatedelta0/1), a certified
+ *     deviation bound and midpoint subdivision until the bound meets the tolerance.
+ *   - Projection / inversion (Sec. 3, Eqs. projection, projections, inversion)
+ *     ON THE ORIGINAL SPLINE by dense sampling plus safeguarded Newton on
+ *     E = D' (Eqs. Dt, Et, E't).
+ *   - Tensor-product surface versions of all of the above.
+ *
+ * Only tests/, __graft_entry__.smoke() and the CPU-baseline leg of bench.py
+ * may load this library.  It shares no code with the CUDA path.
+ *
+ * Decomposition decisions (accept a cubic or subdivide) are made in IEEE FP64
+ * with a fixed operation order and no FMA contraction (build with
+ * -ffp-contract=off).  The CUDA library follows the same arithmetic sequence
+ * in code of its own so that segment counts agree bit for bit.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OMAXP 31          /* highest supported degree (paper Sec. 5.2 limit) */
+#define ONP (OMAXP + 1)   /* control points of one span */
+#define ODEPTH 40         /* subdivision depth cap */
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOSPACE = 2, ORC_ENOTCONV = 4 };
+
+/* ------------------------------------------------------------------ */
+/* small exact helpers                                                 */
+/* ------------------------------------------------------------------ */
+
+/* binomial coefficient, exact in double for the sizes used here (n <= 62) */
+static double binom(int n, int k)
+{
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
+    return r;
+}
+
+/* Gram entry g_ij = int_0^1 B_i^m B_j^n dt  (Eq. gram) */
+double orc_gram(int m, int n, int i, int j)
+{
+    double num = binom(m, i) * binom(n, j);
+    double den = (double)(m + n + 1) * binom(m + n, i + j);
+    return num / den;
+}
+
+/* ------------------------------------------------------------------ */
+/* Cox-de Boor basis (Sec. 3, Eq. bsplinebasis)                          */
+/* ------------------------------------------------------------------ */
+
+/* N[j] = N_{q-p+j,p}(t), j = 0..p, for t in span q.  0/0 terms are 0. */
+static void cdb_basis(const double* U, int q, int p, double t, double* N)
+{
+    double cur[ONP + 1], nxt[ONP + 1];
+    cur[0] = 1.0; /* N_{q,0} */
+    for (int k = 1; k <= p; ++k) {
+        for (int j = 0; j <= k; ++j) {
+            int i = q - k + j;
+            double v = 0.0;
+            if (j >= 1) { /* (t - t_i)/(t_{i+k} - t_i) N_{i,k-1} */
+                double den = U[i + k] - U[i];
+                if (den != 0.0) v += (t - U[i]) / den * cur[j - 1];
+            }
+            if (j <= k - 1) { /* (t_{i+k+1} - t)/(t_{i+k+1} - t_{i+1}) N_{i+1,k-1} */
+                double den = U[i + k + 1] - U[i + 1];
+                if (den != 0.0) v += (U[i + k + 1] - t) / den * cur[j];
+            }
+            nxt[j] = v;
+        }
+        memcpy(cur, nxt, sizeof(double) * (size_t)(k + 1));
+    }
+    memcpy(N, cur, sizeof(double) * (size_t)(p + 1));
+}
+
+/* values, first and second derivatives of N_{q-p..q,p} at t (textbook rule
+ * N'_{i,p} = p N_{i,p-1}/(t_{i+p}-t_i) - p N_{i+1,p-1}/(t_{i+p+1}-t_{i+1})) */
+static void cdb_basis_ders(const double* U, int q, int p, double t,
+                           double* N0, double* N1, double* N2)
+{
+    cdb_basis(U, q, p, t, N0);
+    for (int j = 0; j <= p; ++j) { N1[j] = 0.0; N2[j] = 0.0; }
+    if (p >= 1) {
+        double Nm1[ONP + 1];
+        cdb_basis(U, q, p - 1, t, Nm1); /* N_{q-p+1+j,p-1} */
+        for (int j = 0; j <= p; ++j) {
+            int i = q - p + j;
+            double v = 0.0;
+            if (j >= 1) { double den = U[i + p] - U[i]; if (den != 0.0) v += p * Nm1[j - 1] / den; }
+            if (j <= p - 1) { double den = U[i + p + 1] - U[i + 1]; if (den != 0.0) v -= p * Nm1[j] / den; }
+            N1[j] = v;
+        }
+    }
+    if (p >= 2) {
+        double Nm2[ONP + 1], D1[ONP + 1];
+        cdb_basis(U, q, p - 2, t, Nm2); /* N_{q-p+2+j,p-2} */
+        for (int j = 0; j <= p - 1; ++j) { /* d/dt N_{q-p+1+j,p-1} */
+            int i = q - (p - 1) + j;
+            double v = 0.0;
+            if (j >= 1) { double den = U[i + p - 1] - U[i]; if (den != 0.0) v += (p - 1) * Nm2[j - 1] / den; }
+            if (j <= p - 2) { double den = U[i + p] - U[i + 1]; if (den != 0.0) v -= (p - 1) * Nm2[j] / den; }
+            D1[j] = v;
+        }
+        for (int j = 0; j <= p; ++j) {
+            int i = q - p + j;
+            double v = 0.0;
+            if (j >= 1) { double den = U[i + p] - U[i]; if (den != 0.0) v += p * D1[j - 1] / den; }
+            if (j <= p - 1) { double den = U[i + p + 1] - U[i + 1]; if (den != 0.0) v -= p * D1[j] / den; }
+            N2[j] = v;
+        }
+    }
+}
+
+/* span q in [p, m] with U[q] <= t < U[q+1]; the closed end maps to the last
+ * non-empty span.  m = number of control points - 1. */
+static int find_span(const double* U, int m, int p, double t)
+{
+    int first = -1, last = -1;
+    for (int q = p; q <= m; ++q)
+        if (U[q] < U[q + 1]) { if (first < 0) first = q; last = q; }
+    if (first < 0) return -1;
+    if (t <= U[first]) return first;
+    if (t >= U[last + 1]) return last;
+    for (int q = first; q <= last; ++q)
+        if (U[q] <= t && t < U[q + 1]) return q;
+    return last;
+}
+
+/* exported for the partition-of-unity pin */
+int orc_basis(int p, const double* U, int64_t nU, double t, int* span, double* N)
+{
+    int m = (int)nU - p - 2;
+    int q = find_span(U, m, p, t);
+    if (q < 0) return ORC_EINVAL;
+    *span = q;
+    cdb_basis(U, q, p, t, N);
+    return ORC_OK;
+}
+
+/* C(t), C'(t), C''(t) of a curve (P is [m+1][3]) */
+static void curve_eval(int p, const double* U, int m, const double* P, double t,
+                       double* C, double* C1, double* C2)
+{
+    double N0[ONP + 1], N1[ONP + 1], N2[ONP + 1];
+    int q = find_span(U, m, p, t);
+    cdb_basis_ders(U, q, p, t, N0, N1, N2);
+    for (int c = 0; c < 3; ++c) { C[c] = 0.0; C1[c] = 0.0; C2[c] = 0.0; }
+    for (int j = 0; j <= p; ++j) {
+        const double* Pi = P + 3 * (q - p + j);
+        for (int c = 0; c < 3; ++c) {
+            C[c] += N0[j] * Pi[c];
+            C1[c] += N1[j] * Pi[c];
+            C2[c] += N2[j] * Pi[c];
+        }
+    }
+}
+
+/* surface S(u,v) with partials; P is [nu][nv][3] row-major, index i along u */
+static void surface_eval(int pu, int pv, const double* U, int mu, const double* V, int mv,
+                         const double* P, int nv, double u, double v, double* out /* [6][3]:
+                         S, Su, Sv, Suu, Suv, Svv */)
+{
+    double Nu0[ONP + 1], Nu1[ONP + 1], Nu2[ONP + 1];
+    double Nv0[ONP + 1], Nv1[ONP + 1], Nv2[ONP + 1];
+    int qu = find_span(U, mu, pu, u), qv = find_span(V, mv, pv, v);
+    cdb_basis_ders(U, qu, pu, u, Nu0, Nu1, Nu2);
+    cdb_basis_ders(V, qv, pv, v, Nv0, Nv1, Nv2);
+    for (int k = 0; k < 18; ++k) out[k] = 0.0;
+    for (int a = 0; a <= pu; ++a) {
+        for (int b = 0; b <= pv; ++b) {
+            const double* Pij = P + 3 * ((int64_t)(qu - pu + a) * nv + (qv - pv + b));
+            double w[6] = { Nu0[a] * Nv0[b], Nu1[a] * Nv0[b], Nu0[a] * Nv1[b],
+                            Nu2[a] * Nv0[b], Nu1[a] * Nv1[b], Nu0[a] * Nv2[b] };
+            for (int k = 0; k < 6; ++k)
+                for (int c = 0; c < 3; ++c) out[3 * k + c] += w[k] * Pij[c];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* batch evaluation                                                     */
+/* ------------------------------------------------------------------ */
+
+int orc_eval_curves(int64_t n, const int32_t* deg, const int64_t* koff, const double* knots,
+                    const int64_t* coff, const double* cps, int64_t nq, const int32_t* qc,
+                    const double* t, double* out /* [nq][3][3] */)
+{
+    for (int64_t k = 0; k < nq; ++k) {
+        int64_t c = qc[k];
+        if (c < 0 || c >= n) return ORC_EINVAL;
+        int p = deg[c];
+        int m = (int)(coff[c + 1] - coff[c]) - 1;
+        curve_eval(p, knots + koff[c], m, cps + 3 * coff[c], t[k], out + 9 * k, out + 9 * k + 3,
+                   out + 9 * k + 6);
+    }
+    return ORC_OK;
+}
+
+int orc_eval_surfaces(int64_t n, const int32_t* pu, const int32_t* pv, const int32_t* nu,
+                      const int32_t* nv, const int64_t* kuoff, const double* ku,
+                      const int64_t* kvoff, const double* kv, const int64_t* coff,
+                      const double* cps, int64_t nq, const int32_t* qs, const double* uv,
+                      double* out /* [nq][6][3] */)
+{
+    for (int64_t k = 0; k < nq; ++k) {
+        int64_t s = qs[k];
+        if (s < 0 || s >= n) return ORC_EINVAL;
+        surface_eval(pu[s], pv[s], ku + kuoff[s], nu[s] - 1, kv + kvoff[s], nv[s] - 1,
+                     cps + 3 * coff[s], nv[s], uv[2 * k], uv[2 * k + 1], out + 18 * k);
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* textbook Boehm knot insertion (cross-check of Sec. 4.2.1)            */
+/* ------------------------------------------------------------------ */
+
+/* Inserts every interior knot of the valid range until its multiplicity is p
+ * (one knot at a time, textbook rule P'_i = a_i P_i + (1 - a_i) P_{i-1}),
+ * then reads the Bezier points of each non-empty span.  Q: [cap][p+1][3]. */
+int orc_boehm_bezier(int p, const double* U0, int64_t nU0, const double* P0, int64_t nP0,
+                     double* Q, int64_t cap, int64_t* nspans)
+{
+    if (p < 1 || p > OMAXP || nU0 != nP0 + p + 1) return ORC_EINVAL;
+    int64_t capU = nU0 * (p + 1) + 8, capP = capU;
+    double* U = (double*)malloc(sizeof(double) * (size_t)capU);
+    double* P = (double*)malloc(sizeof(double) * 3 * (size_t)capP);
+    double* Pn = (double*)malloc(sizeof(double) * 3 * (size_t)capP);
+    memcpy(U, U0, sizeof(double) * (size_t)nU0);
+    memcpy(P, P0, sizeof(double) * 3 * (size_t)nP0);
+    int64_t nU = nU0, nP = nP0;
+    double lo = U0[p], hi = U0[nP0]; /* valid range [t_p, t_{m+1}] */
+    int64_t i = 0;
+    while (i < nU) {
+        double x = U[i];
+        int64_t mult = 0;
+        while (i + mult < nU && U[i + mult] == x) ++mult;
+        if (x >= lo && x <= hi) {
+            while (mult < p) {
+                /* insert x once: k with U[k] <= x < U[k+1] (k = last index of x) */
+                int64_t k = i + mult - 1;
+                for (int64_t j = 0; j < nP + 1; ++j) {
+                    if (j <= k - p) {
+                        memcpy(Pn + 3 * j, P + 3 * j, sizeof(double) * 3);
+                    } else if (j <= k) {
+                        double a = (x - U[j]) / (U[j + p] - U[j]);
+                        for (int c = 0; c < 3; ++c)
+                            Pn[3 * j + c] = a * P[3 * j + c] + (1.0 - a) * P[3 * (j - 1) + c];
+                    } else {
+                        memcpy(Pn + 3 * j, P + 3 * (j - 1), sizeof(double) * 3);
+                    }
+                }
+                memcpy(P, Pn, sizeof(double) * 3 * (size_t)(nP + 1));
+                ++nP;
+                memmove(U + k + 2, U + k + 1, sizeof(double) * (size_t)(nU - k - 1));
+                U[k + 1] = x;
+                ++nU;
+                ++mult;
+            }
+        }
+        i += mult;
+    }
+    int64_t ns = 0;
+    int m = (int)nP - 1;
+    for (int q = p; q <= m; ++q) {
+        if (!(U[q] < U[q + 1])) continue;
+        if (ns < cap)
+            memcpy(Q + (size_t)ns * 3 * (p + 1), P + 3 * (q - p), sizeof(double) * 3 * (size_t)(p + 1));
+        ++ns;
+    }
+    *nspans = ns;
+    free(U); free(P); free(Pn);
+    return ns <= cap ? ORC_OK : ORC_ENOSPACE;
+}
+
+/* ------------------------------------------------------------------ */
+/* the paper's span-wise matrix route, built in the local parameter u   */
+/* (Sec. 4.2.1, Eqs. bsplinematrix, Mqpt, decomfinal)                    */
+/* ------------------------------------------------------------------ */
+
+/* Bezier points Q[0..p] of span q.  Step 1: power-basis coefficients in
+ * u = (t - t_q)/(t_{q+1} - t_q) of N_{q-p..q,p} by the Cox-de Boor recursion
+ * on polynomials (this is the product M_{q,p,T} A_{q,p,T} of the paper, formed
+ * directly in u).  Step 2: c = (M A) P.  Step 3: Q = B_p^{-1} c with
+ * (B_p^{-1})_{ij} = C(i,j)/C(p,j), j <= i.
+ * Pl points at P_{q-p} (p+1 consecutive control points, xyz). */
+static void span_bezier(int p, const double* U, int q, const double* Pl, double* Q)
+{
+    double poly[ONP + 1][ONP + 1], nw[ONP + 1][ONP + 1];
+    double du = U[q + 1] - U[q];
+    poly[0][0] = 1.0;
+    for (int k = 1; k <= p; ++k) {
+        for (int j = 0; j <= k; ++j) {
+            int i = q - k + j;
+            for (int e = 0; e <= k; ++e) nw[j][e] = 0.0;
+            if (j >= 1) { /* ((t_q - t_i) + du u)/(t_{i+k} - t_i) * N_{i,k-1} */
+                double den = U[i + k] - U[i];
+                if (den != 0.0) {
+                    double a = (U[q] - U[i]) / den, b = du / den;
+                    for (int e = 0; e <= k - 1; ++e) {
+                        nw[j][e] = nw[j][e] + a * poly[j - 1][e];
+                        nw[j][e + 1] = nw[j][e + 1] + b * poly[j - 1][e];
+                    }
+                }
+            }
+            if (j <= k - 1) { /* ((t_{i+k+1} - t_q) - du u)/(t_{i+k+1} - t_{i+1}) * N_{i+1,k-1} */
+                double den = U[i + k + 1] - U[i + 1];
+                if (den != 0.0) {
+                    double a = (U[i + k + 1] - U[q]) / den, b = -du / den;
+                    for (int e = 0; e <= k - 1; ++e) {
+                        nw[j][e] = nw[j][e] + a * poly[j][e];
+                        nw[j][e + 1] = nw[j][e + 1] + b * poly[j][e];
+                    }
+                }
+            }
+        }
+        for (int j = 0; j <= k; ++j)
+            for (int e = 0; e <= k; ++e) poly[j][e] = nw[j][e];
+    }
+    double cc[ONP + 1][3];
+    for (int e = 0; e <= p; ++e)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int j = 0; j <= p; ++j) s = s + poly[j][e] * Pl[3 * j + c];
+            cc[e][c] = s;
+        }
+    for (int i = 0; i <= p; ++i)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int e = 0; e <= i; ++e) s = s + (binom(i, e) / binom(p, e)) * cc[e][c];
+            Q[3 * i + c] = s;
+        }
+}
+
+/* all non-empty spans of one curve by the matrix route (exported for pins) */
+int orc_span_bezier(int p, const double* U, int64_t nU, const double* P, int64_t nP,
+                    double* Q, int64_t cap, int64_t* nspans)
+{
+    if (p < 1 || p > OMAXP || nU != nP + p + 1) return ORC_EINVAL;
+    int64_t ns = 0;
+    for (int q = p; q <= (int)nP - 1; ++q) {
+        if (!(U[q] < U[q + 1])) continue;
+        if (ns < cap) span_bezier(p, U, q, P + 3 * (q - p), Q + (size_t)ns * 3 * (p + 1));
+        ++ns;
+    }
+    *nspans = ns;
+    return ns <= cap ? ORC_OK : ORC_ENOSPACE;
+}
+
+/* ------------------------------------------------------------------ */
+/* elevation, G1 reduction, bound, halving (Sec. 4.2.2)                 */
+/* ------------------------------------------------------------------ */
+
+/* degree n -> n+1:  Q'_i = (i/(n+1)) Q_{i-1} + ((n+1-i)/(n+1)) Q_i ; stride s between points */
+static void elevate(int n, const double* Q, double* E, int s)
+{
+    for (int c = 0; c < 3; ++c) {
+        E[c] = Q[c];
+        E[(n + 1) * s + c] = Q[n * s + c];
+    }
+    for (int i = 1; i <= n; ++i) {
+        double a = (double)i / (double)(n + 1);
+        double b = (double)(n + 1 - i) / (double)(n + 1);
+        for (int c = 0; c < 3; ++c) E[i * s + c] = a * Q[(i - 1) * s + c] + b * Q[i * s + c];
+    }
+}
+
+/* G1-continuous, L2-optimal reduction of a degree-p Bezier (p > 3) to a cubic.
+ * R0 = Q0, R1 = Q0 + (p/3) d0 delta0, R2 = Qp - (p/3) d1 delta1, R3 = Qp
+ * (Eq. G1-condition).  delta0, delta1 solve d eps/d delta_i = 0 (Eqs.
+ * differentiatedelta0/1), where eps is the L2 error of Eq. epsl.  The 2x2
+ * system is derived here from eps directly: substituting R gives
+ *   delta0 (A0.d0) + delta1 (A1.d0) = V1.d0
+ *   delta0 (B0.d1) + delta1 (B1.d1) = V2.d1
+ * with A0 = a g11 d0, A1 = -a g12 d1, B0 = a g21 d0, B1 = -a g22 d1 (g = G_{3,3}),
+ * V_r = G^r_{3,p} Q - G^r_{3,3} [Q0,Q0,Qp,Qp].  The printed appendix carries a
+ * + in front of the delta1 terms; that sign does not follow from eps and is
+ * not used (variant = 1 reproduces the printed sign, for the pin that shows it
+ * breaks the optimality condition).  Degenerate systems (zero end tangents,
+ * |det| <= 1e-12 |a11 a22|, non-finite or non-positive deltas) fall back to
+ * delta0 = delta1 = 1, the C1 end-derivative match. */
+static void reduce_g1(int p, const double* Q, int s, double* R, int rs, double* deltas, int variant)
+{
+    const double* Q0 = Q;
+    const double* Q1 = Q + s;
+    const double* Qm = Q + (p - 1) * s;
+    const double* Qp = Q + p * s;
+    double a = (double)p / 3.0;
+    double g11 = orc_gram(3, 3, 1, 1), g12 = orc_gram(3, 3, 1, 2);
+    double g21 = orc_gram(3, 3, 2, 1), g22 = orc_gram(3, 3, 2, 2);
+    double g10 = orc_gram(3, 3, 1, 0), g13 = orc_gram(3, 3, 1, 3);
+    double g20 = orc_gram(3, 3, 2, 0), g23 = orc_gram(3, 3, 2, 3);
+    double d0[3], d1[3], V1[3], V2[3];
+    for (int c = 0; c < 3; ++c) {
+        d0[c] = Q1[c] - Q0[c];
+        d1[c] = Qp[c] - Qm[c];
+        double s1 = 0.0, s2 = 0.0;
+        for (int j = 0; j <= p; ++j) {
+            s1 = s1 + orc_gram(3, p, 1, j) * Q[j * s + c];
+            s2 = s2 + orc_gram(3, p, 2, j) * Q[j * s + c];
+        }
+        double t1 = ((g10 * Q0[c] + g11 * Q0[c]) + g12 * Qp[c]) + g13 * Qp[c];
+        double t2 = ((g20 * Q0[c] + g21 * Q0[c]) + g22 * Qp[c]) + g23 * Qp[c];
+        V1[c] = s1 - t1;
+        V2[c] = s2 - t2;
+    }
+    double A0[3], A1[3], B0[3], B1[3];
+    for (int c = 0; c < 3; ++c) {
+        A0[c] = (a * g11) * d0[c];
+        A1[c] = (-a * g12) * d1[c];
+        B0[c] = (a * g21) * d0[c];
+        B1[c] = (-a * g22) * d1[c];
+    }
+#define DOT3(x, y) (((x)[0] * (y)[0] + (x)[1] * (y)[1]) + (x)[2] * (y)[2])
+    double a11 = DOT3(A0, d0), a12 = DOT3(A1, d0), b1 = DOT3(V1, d0);
+    double a21 = DOT3(B0, d1), a22 = DOT3(B1, d1), b2 = DOT3(V2, d1);
+#undef DOT3
+    if (variant == 1) { /* the appendix's printed sign (not used by the method) */
+        a12 = -a12;
+        a22 = -a22;
+    }
+    double det = a11 * a22 - a12 * a21;
+    double dl0 = (b1 * a22 - a12 * b2) / det;
+    double dl1 = (a11 * b2 - b1 * a21) / det;
+    int ok = (det != 0.0) && (fabs(det) > 1e-12 * fabs(a11 * a22)) && isfinite(dl0) &&
+             isfinite(dl1) && ((dl0 > 0.0 && dl1 > 0.0) || variant == 1);
+    if (!ok) { dl0 = 1.0; dl1 = 1.0; }
+    double s0 = a * dl0, s1 = a * dl1;
+    for (int c = 0; c < 3; ++c) {
+        R[c] = Q0[c];
+        R[rs + c] = Q0[c] + s0 * d0[c];
+        R[2 * rs + c] = Qp[c] - s1 * d1[c];
+        R[3 * rs + c] = Qp[c];
+    }
+    if (deltas) { deltas[0] = dl0; deltas[1] = dl1; deltas[2] = ok ? 1.0 : 0.0; }
+}
+
+/* any degree p >= 1 to a cubic: elevate (p < 3), copy (p = 3), reduce (p > 3) */
+static void to_cubic(int p, const double* Q, int s, double* R, int rs)
+{
+    if (p == 3) {
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 3; ++c) R[i * rs + c] = Q[i * s + c];
+    } else if (p > 3) {
+        reduce_g1(p, Q, s, R, rs, NULL, 0);
+    } else {
+        double w[4][3], x[4][3];
+        for (int i = 0; i <= p; ++i)
+            for (int c = 0; c < 3; ++c) w[i][c] = Q[i * s + c];
+        for (int n = p; n < 3; ++n) {
+            elevate(n, &w[0][0], &x[0][0], 3);
+            memcpy(w, x, sizeof(w));
+        }
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 3; ++c) R[i * rs + c] = w[i][c];
+    }
+}
+
+/* max_i |Q_i - (R elevated to p)_i|^2 : an upper bound of max_u |Q(u)-R(u)|^2
+ * because Bernstein weights are a convex partition of unity (p >= 3). */
+static double bound2_curve(int p, const double* Q, int s, const double* R, int rs)
+{
+    double w[ONP + 1][3], x[ONP + 1][3];
+    for (int i = 0; i < 4; ++i)
+        for (int c = 0; c < 3; ++c) w[i][c] = R[i * rs + c];
+    for (int n = 3; n < p; ++n) {
+        elevate(n, &w[0][0], &x[0][0], 3);
+        memcpy(w, x, sizeof(double) * 3 * (size_t)(n + 2));
+    }
+    double b = 0.0;
+    for (int i = 0; i <= p; ++i) {
+        double dx = Q[i * s + 0] - w[i][0], dy = Q[i * s + 1] - w[i][1], dz = Q[i * s + 2] - w[i][2];
+        double e = (dx * dx + dy * dy) + dz * dz;
+        if (e > b) b = e;
+    }
+    return b;
+}
+
+/* de Casteljau split at z = 1/2 (the matrix S(1/2) of Eq. subLandR) */
+static void halve(int p, const double* Q, int s, double* L, double* Rr)
+{
+    double w[ONP + 1][3];
+    for (int i = 0; i <= p; ++i)
+        for (int c = 0; c < 3; ++c) w[i][c] = Q[i * s + c];
+    for (int c = 0; c < 3; ++c) { L[c] = w[0][c]; Rr[p * s + c] = w[p][c]; }
+    for (int r = 1; r <= p; ++r) {
+        for (int i = 0; i <= p - r; ++i)
+            for (int c = 0; c < 3; ++c) w[i][c] = (w[i][c] + w[i + 1][c]) * 0.5;
+        for (int c = 0; c < 3; ++c) { L[r * s + c] = w[0][c]; Rr[(p - r) * s + c] = w[p - r][c]; }
+    }
+}
+
+/* exported single-step helpers for the pins */
+int orc_reduce_g1(int p, const double* Q, double* R, double* deltas, int variant)
+{
+    if (p <= 3 || p > OMAXP) return ORC_EINVAL;
+    reduce_g1(p, Q, 3, R, 3, deltas, variant);
+    return ORC_OK;
+}
+int orc_to_cubic(int p, const double* Q, double* R)
+{
+    if (p < 1 || p > OMAXP) return ORC_EINVAL;
+    to_cubic(p, Q, 3, R, 3);
+    return ORC_OK;
+}
+double orc_bound2(int p, const double* Q, const double* R) { return bound2_curve(p, Q, 3, R, 3); }
+int orc_halve(int p, const double* Q, double* L, double* R)
+{
+    if (p < 1 || p > OMAXP) return ORC_EINVAL;
+    halve(p, Q, 3, L, R);
+    return ORC_OK;
+}
+int orc_elevate(int n, const double* Q, double* E)
+{
+    if (n < 1 || n >= OMAXP) return ORC_EINVAL;
+    elevate(n, Q, E, 3);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* error-controlled curve decomposition (Sec. 4.2.2)                    */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int p;
+    double thr2;
+    double tq, tq1;
+    int64_t count, cap;
+    double* ctrl;   /* [cap][4][3] */
+    double* prange; /* [cap][2] */
+    int maxdepth;
+    int notconv;
+} curve_ctx;
+
+/* parameter of the dyadic point k/2^L of span [tq, tq1] */
+static double dyadic_t(double tq, double tq1, int64_t k, int L)
+{
+    if (k == 0) return tq;
+    if (k == ((int64_t)1 << L)) return tq1;
+    return tq + (tq1 - tq) * ldexp((double)k, -L);
+}
+
+/* accept the cubic of this node or split it at the midpoint of its parameter
+ * interval; children are re-reduced from the ORIGINAL degree-p piece, so their
+ * shared end point lies on the original curve (Sec. 4.2.2, control-polygon
+ * modification, midpoint reading) */
+static void curve_node(curve_ctx* X, const double* Q, int L, int64_t k)
+{
+    double R[4][3];
+    int p = X->p;
+    to_cubic(p, Q, 3, &R[0][0], 3);
+    int accept = 1;
+    if (p > 3) accept = bound2_curve(p, Q, 3, &R[0][0], 3) <= X->thr2;
+    if (!accept && L >= ODEPTH) { accept = 1; X->notconv = 1; }
+    if (accept) {
+        if (X->count < X->cap && X->ctrl) {
+            memcpy(X->ctrl + 12 * X->count, R, sizeof(R));
+            X->prange[2 * X->count] = dyadic_t(X->tq, X->tq1, k, L);
+            X->prange[2 * X->count + 1] = dyadic_t(X->tq, X->tq1, k + 1, L);
+        }
+        X->count++;
+        if (L > X->maxdepth) X->maxdepth = L;
+        return;
+    }
+    double Lq[ONP + 1][3], Rq[ONP + 1][3];
+    halve(p, Q, 3, &Lq[0][0], &Rq[0][0]);
+    curve_node(X, &Lq[0][0], L + 1, 2 * k);
+    curve_node(X, &Rq[0][0], L + 1, 2 * k + 1);
+}
+
+/* diagonal of the axis-aligned box of np points */
+static double box_diag(const double* P, int64_t np)
+{
+    double lo[3] = { INFINITY, INFINITY, INFINITY }, hi[3] = { -INFINITY, -INFINITY, -INFINITY };
+    for (int64_t i = 0; i < np; ++i)
+        for (int c = 0; c < 3; ++c) {
+            if (P[3 * i + c] < lo[c]) lo[c] = P[3 * i + c];
+            if (P[3 * i + c] > hi[c]) hi[c] = P[3 * i + c];
+        }
+    double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+    return sqrt((dx * dx + dy * dy) + dz * dz);
+}
+
+static int check_knots(int p, const double* U, int64_t nU, int64_t nP)
+{
+    if (p < 1 || p > OMAXP || nP < p + 1 || nU != nP + p + 1) return 0;
+    for (int64_t i = 0; i < nU; ++i) {
+        if (!isfinite(U[i])) return 0;
+        if (i > 0 && U[i] < U[i - 1]) return 0;
+    }
+    return U[p] < U[nP];
+}
+
+/* seg_off[n+1] always written; ctrl/prange written when cap suffices.
+ * returns ORC_ENOSPACE when the total exceeds cap (counts still valid). */
+int orc_decompose_curves(int64_t n, const int32_t* deg, const int64_t* koff, const double* knots,
+                         const int64_t* coff, const double* cps, double tol_rel, int64_t* seg_off,
+                         int64_t cap, double* ctrl, double* prange, int64_t* total, int* maxdepth)
+{
+    int64_t cnt = 0;
+    int md = 0, nc = 0;
+    seg_off[0] = 0;
+    for (int64_t c = 0; c < n; ++c) {
+        int p = deg[c];
+        int64_t nP = coff[c + 1] - coff[c], nU = koff[c + 1] - koff[c];
+        const double* U = knots + koff[c];
+        const double* P = cps + 3 * coff[c];
+        if (!check_knots(p, U, nU, nP)) return ORC_EINVAL;
+        for (int64_t i = 0; i < 3 * nP; ++i) if (!isfinite(P[i])) return ORC_EINVAL;
+        double thr = tol_rel * box_diag(P, nP);
+        curve_ctx X;
+        X.p = p; X.thr2 = thr * thr; X.cap = cap; X.maxdepth = 0; X.notconv = 0;
+        X.ctrl = ctrl; X.prange = prange;
+        X.count = cnt;
+        for (int q = p; q <= (int)nP - 1; ++q) {
+            if (!(U[q] < U[q + 1])) continue;
+            double Q[ONP + 1][3];
+            span_bezier(p, U, q, P + 3 * (q - p), &Q[0][0]);
+            X.tq = U[q]; X.tq1 = U[q + 1];
+            curve_node(&X, &Q[0][0], 0, 0);
+        }
+        cnt = X.count;
+        if (X.maxdepth > md) md = X.maxdepth;
+        nc |= X.notconv;
+        seg_off[c + 1] = cnt;
+    }
+    *total = cnt;
+    if (maxdepth) *maxdepth = md;
+    if (nc) return ORC_ENOTCONV;
+    return cnt <= cap ? ORC_OK : ORC_ENOSPACE;
+}
+
+/* ------------------------------------------------------------------ */
+/* error-controlled surface decomposition (tensor-product reading)       */
+/* ------------------------------------------------------------------ */
+
+#define SMAXP 15 /* surfaces: degree <= 15 per direction in the oracle */
+#define SNP (SMAXP + 1)
+
+typedef struct {
+    int pu, pv;
+    double thr2;
+    double u0, u1, v0, v1; /* span pair parameter box */
+    int64_t count, cap;
+    double* ctrl;   /* [cap][4][4][3] */
+    double* prange; /* [cap][4] */
+    int maxdepth, notconv;
+} surf_ctx;
+
+/* net is [pu+1][pv+1][3] (index i along u), stored in a fixed [SNP][SNP][3] array */
+typedef double net_t[SNP][SNP][3];
+
+/* reduce along u for every v column, then along v for every u row */
+static void surf_to_bicubic(int pu, int pv, const net_t Q, double R[4][4][3])
+{
+    double Rp[4][SNP][3];
+    for (int j = 0; j <= pv; ++j) {
+        double col[SNP][3], r[4][3];
+        for (int i = 0; i <= pu; ++i)
+            for (int c = 0; c < 3; ++c) col[i][c] = Q[i][j][c];
+        to_cubic(pu, &col[0][0], 3, &r[0][0], 3);
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 3; ++c) Rp[i][j][c] = r[i][c];
+    }
+    for (int i = 0; i < 4; ++i) {
+        double r[4][3];
+        to_cubic(pv, &Rp[i][0][0], 3, &r[0][0], 3);
+        for (int j = 0; j < 4; ++j)
+            for (int c = 0; c < 3; ++c) R[i][j][c] = r[j][c];
+    }
+}
+
+/* certified bound at degrees (eu, ev) = (max(pu,3), max(pv,3)):
+ * Q elevated along u then v where its degree is below 3; R elevated along v
+ * then u where the original degree is above 3. */
+static double surf_bound2(int pu, int pv, const net_t Q, double R[4][4][3])
+{
+    int eu = pu > 3 ? pu : 3, ev = pv > 3 ? pv : 3;
+    double (*Qe)[SNP][3] = malloc(sizeof(net_t));
+    double (*Re)[SNP][3] = malloc(sizeof(net_t));
+    /* Q: along u for each column j <= pv */
+    for (int j = 0; j <= pv; ++j) {
+        double w[SNP][3], x[SNP][3];
+        for (int i = 0; i <= pu; ++i)
+            for (int c = 0; c < 3; ++c) w[i][c] = Q[i][j][c];
+        for (int n = pu; n < eu; ++n) { elevate(n, &w[0][0], &x[0][0], 3); memcpy(w, x, sizeof(w)); }
+        for (int i = 0; i <= eu; ++i)
+            for (int c = 0; c < 3; ++c) Qe[i][j][c] = w[i][c];
+    }
+    for (int i = 0; i <= eu; ++i) {
+        double w[SNP][3], x[SNP][3];
+        for (int j = 0; j <= pv; ++j)
+            for (int c = 0; c < 3; ++c) w[j][c] = Qe[i][j][c];
+        for (int n = pv; n < ev; ++n) { elevate(n, &w[0][0], &x[0][0], 3); memcpy(w, x, sizeof(w)); }
+        for (int j = 0; j <= ev; ++j)
+            for (int c = 0; c < 3; ++c) Qe[i][j][c] = w[j][c];
+    }
+    /* R: along v for each row i < 4, then along u for each column j <= ev */
+    for (int i = 0; i < 4; ++i) {
+        double w[SNP][3], x[SNP][3];
+        for (int j = 0; j < 4; ++j)
+            for (int c = 0; c < 3; ++c) w[j][c] = R[i][j][c];
+        for (int n = 3; n < ev; ++n) { elevate(n, &w[0][0], &x[0][0], 3); memcpy(w, x, sizeof(w)); }
+        for (int j = 0; j <= ev; ++j)
+            for (int c = 0; c < 3; ++c) Re[i][j][c] = w[j][c];
+    }
+    for (int j = 0; j <= ev; ++j) {
+        double w[SNP][3], x[SNP][3];
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 3; ++c) w[i][c] = Re[i][j][c];
+        for (int n = 3; n < eu; ++n) { elevate(n, &w[0][0], &x[0][0], 3); memcpy(w, x, sizeof(w)); }
+        for (int i = 0; i <= eu; ++i)
+            for (int c = 0; c < 3; ++c) Re[i][j][c] = w[i][c];
+    }
+    double b = 0.0;
+    for (int i = 0; i <= eu; ++i)
+        for (int j = 0; j <= ev; ++j) {
+            double dx = Qe[i][j][0] - Re[i][j][0], dy = Qe[i][j][1] - Re[i][j][1],
+                   dz = Qe[i][j][2] - Re[i][j][2];
+            double e = (dx * dx + dy * dy) + dz * dz;
+            if (e > b) b = e;
+        }
+    free(Qe); free(Re);
+    return b;
+}
+
+/* split direction: the reduced direction if only one is reduced, else the
+ * longer parameter side (ties -> u) */
+static int surf_split_dir(int pu, int pv, double du, double dv, int Lu, int Lv)
+{
+    if (pu > 3 && pv <= 3) return 0;
+    if (pv > 3 && pu <= 3) return 1;
+    return ldexp(du, -Lu) >= ldexp(dv, -Lv) ? 0 : 1;
+}
+
+static void surf_node(surf_ctx* X, const net_t Q, int Lu, int64_t ku, int Lv, int64_t kv)
+{
+    int pu = X->pu, pv = X->pv;
+    double R[4][4][3];
+    surf_to_bicubic(pu, pv, Q, R);
+    int accept = 1;
+    if (pu > 3 || pv > 3) accept = surf_bound2(pu, pv, Q, R) <= X->thr2;
+    if (!accept && Lu + Lv >= ODEPTH) { accept = 1; X->notconv = 1; }
+    if (accept) {
+        if (X->count < X->cap && X->ctrl) {
+            memcpy(X->ctrl + 48 * X->count, R, sizeof(R));
+            double* pr = X->prange + 4 * X->count;
+            pr[0] = dyadic_t(X->u0, X->u1, ku, Lu);
+            pr[1] = dyadic_t(X->u0, X->u1, ku + 1, Lu);
+            pr[2] = dyadic_t(X->v0, X->v1, kv, Lv);
+            pr[3] = dyadic_t(X->v0, X->v1, kv + 1, Lv);
+        }
+        X->count++;
+        if (Lu + Lv > X->maxdepth) X->maxdepth = Lu + Lv;
+        return;
+    }
+    int dir = surf_split_dir(pu, pv, X->u1 - X->u0, X->v1 - X->v0, Lu, Lv);
+    double (*A)[SNP][3] = malloc(sizeof(net_t));
+    double (*B)[SNP][3] = malloc(sizeof(net_t));
+    if (dir == 0) {
+        for (int j = 0; j <= pv; ++j) {
+            double col[SNP][3], l[SNP][3], r[SNP][3];
+            for (int i = 0; i <= pu; ++i)
+                for (int c = 0; c < 3; ++c) col[i][c] = Q[i][j][c];
+            halve(pu, &col[0][0], 3, &l[0][0], &r[0][0]);
+            for (int i = 0; i <= pu; ++i)
+                for (int c = 0; c < 3; ++c) { A[i][j][c] = l[i][c]; B[i][j][c] = r[i][c]; }
+        }
+        surf_node(X, (const double(*)[SNP][3])A, Lu + 1, 2 * ku, Lv, kv);
+        surf_node(X, (const double(*)[SNP][3])B, Lu + 1, 2 * ku + 1, Lv, kv);
+    } else {
+        for (int i = 0; i <= pu; ++i) {
+            double l[SNP][3], r[SNP][3];
+            halve(pv, &Q[i][0][0], 3, &l[0][0], &r[0][0]);
+            for (int j = 0; j <= pv; ++j)
+                for (int c = 0; c < 3; ++c) { A[i][j][c] = l[j][c]; B[i][j][c] = r[j][c]; }
+        }
+        surf_node(X, (const double(*)[SNP][3])A, Lu, ku, Lv + 1, 2 * kv);
+        surf_node(X, (const double(*)[SNP][3])B, Lu, ku, Lv + 1, 2 * kv + 1);
+    }
+    free(A); free(B);
+}
+
+/* Bezier net of span pair (qu, qv): the curve matrix route along u for every
+ * v index of the local window, then along v for every u row. */
+static void surf_span_bezier(int pu, int pv, const double* U, int qu, const double* V, int qv,
+                             const double* P, int nv, net_t Q)
+{
+    double T1[SNP][SNP][3];
+    for (int b = 0; b <= pv; ++b) {
+        double loc[SNP][3], out[SNP][3];
+        for (int a = 0; a <= pu; ++a)
+            for (int c = 0; c < 3; ++c)
+                loc[a][c] = P[3 * ((int64_t)(qu - pu + a) * nv + (qv - pv + b)) + c];
+        span_bezier(pu, U, qu, &loc[0][0], &out[0][0]);
+        for (int a = 0; a <= pu; ++a)
+            for (int c = 0; c < 3; ++c) T1[a][b][c] = out[a][c];
+    }
+    for (int a = 0; a <= pu; ++a) {
+        double out[SNP][3];
+        span_bezier(pv, V, qv, &T1[a][0][0], &out[0][0]);
+        for (int b = 0; b <= pv; ++b)
+            for (int c = 0; c < 3; ++c) Q[a][b][c] = out[b][c];
+    }
+}
+
+int orc_decompose_surfaces(int64_t n, const int32_t* pu_, const int32_t* pv_, const int32_t* nu_,
+                           const int32_t* nv_, const int64_t* kuoff, const double* ku,
+                           const int64_t* kvoff, const double* kv, const int64_t* coff,
+                           const double* cps, double tol_rel, int64_t* seg_off, int64_t cap,
+                           double* ctrl, double* prange, int64_t* total, int* maxdepth)
+{
+    int64_t cnt = 0;
+    int md = 0, nc = 0;
+    seg_off[0] = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        int pu = pu_[s], pv = pv_[s], nu = nu_[s], nv = nv_[s];
+        if (pu > SMAXP || pv > SMAXP) return ORC_EINVAL;
+        const double* U = ku + kuoff[s];
+        const double* V = kv + kvoff[s];
+        const double* P = cps + 3 * coff[s];
+        if (coff[s + 1] - coff[s] != (int64_t)nu * nv) return ORC_EINVAL;
+        if (!check_knots(pu, U, kuoff[s + 1] - kuoff[s], nu)) return ORC_EINVAL;
+        if (!check_knots(pv, V, kvoff[s + 1] - kvoff[s], nv)) return ORC_EINVAL;
+        for (int64_t i = 0; i < 3 * (int64_t)nu * nv; ++i) if (!isfinite(P[i])) return ORC_EINVAL;
+        double thr = tol_rel * box_diag(P, (int64_t)nu * nv);
+        surf_ctx X;
+        X.pu = pu; X.pv = pv; X.thr2 = thr * thr; X.cap = cap; X.ctrl = ctrl; X.prange = prange;
+        X.count = cnt; X.maxdepth = 0; X.notconv = 0;
+        double (*Q)[SNP][3] = malloc(sizeof(net_t));
+        for (int qu = pu; qu <= nu - 1; ++qu) {
+            if (!(U[qu] < U[qu + 1])) continue;
+            for (int qv = pv; qv <= nv - 1; ++qv) {
+                if (!(V[qv] < V[qv + 1])) continue;
+                surf_span_bezier(pu, pv, U, qu, V, qv, P, nv, Q);
+                X.u0 = U[qu]; X.u1 = U[qu + 1]; X.v0 = V[qv]; X.v1 = V[qv + 1];
+                surf_node(&X, (const double(*)[SNP][3])Q, 0, 0, 0, 0);
+            }
+        }
+        free(Q);
+        cnt = X.count;
+        if (X.maxdepth > md) md = X.maxdepth;
+        nc |= X.notconv;
+        seg_off[s + 1] = cnt;
+    }
+    *total = cnt;
+    if (maxdepth) *maxdepth = md;
+    if (nc) return ORC_ENOTCONV;
+    return cnt <= cap ? ORC_OK : ORC_ENOSPACE;
+}
+
+/* ------------------------------------------------------------------ */
+/* projection / inversion on the original curve (Sec. 3)                */
+/* ------------------------------------------------------------------ */
+
+#define OSAMP 64 /* samples per non-empty span */
+
+typedef struct {
+    int p, m;
+    const double* U;
+    const double* P;
+    const double* q;
+} curve_prob;
+
+/* D = |C - q|^2, E = D', Ep = E' (Eqs. Dt, Et, E't) */
+static void dist_ders(const curve_prob* B, double t, double* D, double* E, double* Ep)
+{
+    double C[3], C1[3], C2[3];
+    curve_eval(B->p, B->U, B->m, B->P, t, C, C1, C2);
+    double d[3] = { C[0] - B->q[0], C[1] - B->q[1], C[2] - B->q[2] };
+    *D = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (E) *E = 2.0 * (d[0] * C1[0] + d[1] * C1[1] + d[2] * C1[2]);
+    if (Ep) *Ep = 2.0 * ((C1[0] * C1[0] + C1[1] * C1[1] + C1[2] * C1[2]) +
+                         (d[0] * C2[0] + d[1] * C2[1] + d[2] * C2[2]));
+}
+
+/* safeguarded Newton for a minimum of D in [lo, hi] from t0: a Newton step on
+ * E when E' > 0 and the step stays inside the bracket, bisection otherwise;
+ * the bracket keeps the side on which D descends. */
+static double newton_min_1d(const curve_prob* B, double lo, double hi, double t0, double eps)
+{
+    double t = t0;
+    for (int it = 0; it < 100; ++it) {
+        double D, E, Ep;
+        dist_ders(B, t, &D, &E, &Ep);
+        if (E > 0.0) hi = t;
+        else if (E < 0.0) lo = t;
+        else break;
+        double tn = (Ep > 0.0) ? t - E / Ep : 0.5 * (lo + hi);
+        if (!(tn >= lo && tn <= hi)) tn = 0.5 * (lo + hi);
+        if (fabs(tn - t) <= eps || hi - lo <= eps) { t = tn; break; }
+        t = tn;
+    }
+    return t;
+}
+
+/* bounds of |C'(t)| and |C''(t)| on span q.  The derivatives are B-splines
+ * with control points D1_i = p (P_i - P_{i-1})/(t_{i+p} - t_i) and
+ * D2_i = (p-1)(D1_i - D1_{i-1})/(t_{i+p-1} - t_i); B-spline weights are a
+ * convex partition of unity, so the largest control-point norm bounds each. */
+static void curve_deriv_bounds(int p, const double* U, const double* P, int q, double* V, double* A)
+{
+    double D1[ONP + 1][3];
+    double v = 0.0, a = 0.0;
+    for (int i = q - p + 1; i <= q; ++i) {
+        int r = i - (q - p + 1);
+        double den = U[i + p] - U[i];
+        for (int c = 0; c < 3; ++c) D1[r][c] = den != 0.0 ? p * (P[3 * i + c] - P[3 * (i - 1) + c]) / den : 0.0;
+        double w = sqrt(D1[r][0] * D1[r][0] + D1[r][1] * D1[r][1] + D1[r][2] * D1[r][2]);
+        if (w > v) v = w;
+    }
+    for (int i = q - p + 2; i <= q; ++i) {
+        int r = i - (q - p + 1);
+        double den = U[i + p - 1] - U[i];
+        if (den == 0.0) continue;
+        double x[3];
+        for (int c = 0; c < 3; ++c) x[c] = (p - 1) * (D1[r][c] - D1[r - 1][c]) / den;
+        double w = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (w > a) a = w;
+    }
+    *V = v;
+    *A = a;
+}
+
+typedef struct { double a, b, Da, Db; int depth; } ival_t;
+
+/* lower bound of D = |C-q|^2 on [a,b] inside one span (C polynomial there):
+ * first order: |C-q| >= (d_a + d_b - V h)/2;
+ * second order: D >= min(D_a, D_b) - h^2/8 max|D''|,
+ * with |D''| = 2|C'.C' + (C-q).C''| <= 2 (V^2 + (max(d_a,d_b) + V h/2) A). */
+static double ival_lower_bound(const ival_t* iv, double V, double A)
+{
+    double h = iv->b - iv->a, da = sqrt(iv->Da), db = sqrt(iv->Db);
+    double l1 = 0.5 * (da + db - V * h);
+    l1 = l1 > 0.0 ? l1 * l1 : 0.0;
+    double K = 2.0 * (V * V + ((da > db ? da : db) + 0.5 * V * h) * A);
+    double l2 = (iv->Da < iv->Db ? iv->Da : iv->Db) - 0.125 * h * h * K;
+    return l1 > l2 ? l1 : l2;
+}
+
+/* global minimiser of |C(t) - q| over [t_p, t_{m+1}]:
+ *  1. dense sampling (OSAMP per non-empty span plus all span ends) and one
+ *     safeguarded Newton per sampled basin, plus every knot as a candidate;
+ *  2. branch and bound over the sample intervals with the rigorous lower
+ *     bound above: an interval whose bound is below the best distance found is
+ *     bisected (its midpoint evaluated, and polished by Newton when it is a
+ *     local minimum) until the bound clears the best or the interval is
+ *     2^-44 of its sample step.  No basin can therefore hide between samples. */
+static void project_curve_one(int p, const double* U, int m, const double* P, const double* q,
+                              double* t_out, double* d_out)
+{
+    curve_prob B = { p, m, U, P, q };
+    int ns = 0;
+    for (int k = p; k <= m; ++k) if (U[k] < U[k + 1]) ++ns;
+    int nsamp = ns * OSAMP + 1;
+    double* ts = (double*)malloc(sizeof(double) * (size_t)nsamp);
+    double* Ds = (double*)malloc(sizeof(double) * (size_t)nsamp);
+    double* Vs = (double*)malloc(sizeof(double) * (size_t)nsamp);
+    double* As = (double*)malloc(sizeof(double) * (size_t)nsamp);
+    int j = 0;
+    double tlast = 0.0;
+    for (int k = p; k <= m; ++k) {
+        if (!(U[k] < U[k + 1])) continue;
+        double V, A;
+        curve_deriv_bounds(p, U, P, k, &V, &A);
+        for (int s = 0; s < OSAMP; ++s) {
+            Vs[j] = V;
+            As[j] = A;
+            ts[j++] = U[k] + (U[k + 1] - U[k]) * ((double)s / OSAMP);
+        }
+        tlast = U[k + 1];
+    }
+    ts[j++] = tlast;
+    double t0 = ts[0], t1 = tlast, eps = 1e-15 * (t1 - t0);
+    for (int i = 0; i < nsamp; ++i) dist_ders(&B, ts[i], &Ds[i], NULL, NULL);
+    double bestD = INFINITY, bestT = t0;
+#define CONSIDER(tt)                                                          \
+    do {                                                                      \
+        double D_;                                                            \
+        dist_ders(&B, (tt), &D_, NULL, NULL);                                 \
+        if (D_ < bestD || (D_ == bestD && (tt) < bestT)) { bestD = D_; bestT = (tt); } \
+    } while (0)
+    for (int i = 0; i < nsamp; ++i) {
+        int lmin = (i == 0 || Ds[i] <= Ds[i - 1]) && (i == nsamp - 1 || Ds[i] <= Ds[i + 1]);
+        if (!lmin) continue;
+        double lo = ts[i > 0 ? i - 1 : 0], hi = ts[i < nsamp - 1 ? i + 1 : nsamp - 1];
+        double tn = newton_min_1d(&B, lo, hi, ts[i], eps);
+        CONSIDER(tn);
+        CONSIDER(ts[i]);
+    }
+    for (int k = p; k <= m + 1; ++k) {
+        if (U[k] < t0 || U[k] > t1) continue;
+        CONSIDER(U[k]);
+    }
+    /* branch and bound, depth-first with an explicit stack */
+    int cap = 256, top = 0;
+    ival_t* st = (ival_t*)malloc(sizeof(ival_t) * (size_t)cap);
+    for (int i = 0; i + 1 < nsamp; ++i) {
+        double V = Vs[i], A = As[i];
+        st[top++] = (ival_t){ ts[i], ts[i + 1], Ds[i], Ds[i + 1], 0 };
+        while (top > 0) {
+            ival_t iv = st[--top];
+            if (iv.depth >= 44 || !(ival_lower_bound(&iv, V, A) < bestD)) continue;
+            double mid = 0.5 * (iv.a + iv.b), Dm;
+            dist_ders(&B, mid, &Dm, NULL, NULL);
+            if (Dm < bestD || (Dm == bestD && mid < bestT)) { bestD = Dm; bestT = mid; }
+            if (Dm <= iv.Da && Dm <= iv.Db) {
+                double tn = newton_min_1d(&B, iv.a, iv.b, mid, eps);
+                CONSIDER(tn);
+            }
+            if (top + 2 > cap) { cap *= 2; st = (ival_t*)realloc(st, sizeof(ival_t) * (size_t)cap); }
+            st[top++] = (ival_t){ mid, iv.b, Dm, iv.Db, iv.depth + 1 };
+            st[top++] = (ival_t){ iv.a, mid, iv.Da, Dm, iv.depth + 1 };
+        }
+    }
+    free(st);
+#undef CONSIDER
+    *t_out = bestT;
+    *d_out = sqrt(bestD);
+    free(ts); free(Ds); free(Vs); free(As);
+}
+
+int orc_project_curves(int64_t n, const int32_t* deg, const int64_t* koff, const double* knots,
+                       const int64_t* coff, const double* cps, int64_t nq, const int32_t* qc,
+                       const double* qxyz, double* t_out, double* d_out, int nthreads)
+{
+    for (int64_t k = 0; k < nq; ++k)
+        if (qc[k] < 0 || qc[k] >= n) return ORC_EINVAL;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < nq; ++k) {
+        int64_t c = qc[k];
+        int m = (int)(coff[c + 1] - coff[c]) - 1;
+        project_curve_one(deg[c], knots + koff[c], m, cps + 3 * coff[c], qxyz + 3 * k, &t_out[k],
+                          &d_out[k]);
+    }
+    return ORC_OK;
+}
+
+/* threads the OpenMP runtime would use */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* projection / inversion on the original surface                       */
+/* ------------------------------------------------------------------ */
+
+#define OSAMP2 16 /* samples per span and direction */
+
+typedef struct {
+    int pu, pv, mu, mv, nv;
+    const double* U;
+    const double* V;
+    const double* P;
+    const double* q;
+} surf_prob;
+
+static double sdist(const surf_prob* B, double u, double v, double* g, double* H)
+{
+    double o[18];
+    surface_eval(B->pu, B->pv, B->U, B->mu, B->V, B->mv, B->P, B->nv, u, v, o);
+    double d[3] = { o[0] - B->q[0], o[1] - B->q[1], o[2] - B->q[2] };
+    double D = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (g) {
+        const double *Su = o + 3, *Sv = o + 6, *Suu = o + 9, *Suv = o + 12, *Svv = o + 15;
+        g[0] = 2.0 * (d[0] * Su[0] + d[1] * Su[1] + d[2] * Su[2]);
+        g[1] = 2.0 * (d[0] * Sv[0] + d[1] * Sv[1] + d[2] * Sv[2]);
+        H[0] = 2.0 * ((Su[0] * Su[0] + Su[1] * Su[1] + Su[2] * Su[2]) + (d[0] * Suu[0] + d[1] * Suu[1] + d[2] * Suu[2]));
+        H[1] = 2.0 * ((Su[0] * Sv[0] + Su[1] * Sv[1] + Su[2] * Sv[2]) + (d[0] * Suv[0] + d[1] * Suv[1] + d[2] * Suv[2]));
+        H[2] = 2.0 * ((Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]) + (d[0] * Svv[0] + d[1] * Svv[1] + d[2] * Svv[2]));
+    }
+    return D;
+}
+
+/* 1D problem along an iso-curve of the surface (fixed u or fixed v) */
+typedef struct {
+    const surf_prob* S;
+    int fixu;     /* 1: u fixed = c, parameter is v; 0: v fixed */
+    double c;
+} iso_prob;
+
+static void iso_ders(const iso_prob* I, double t, double* D, double* E, double* Ep)
+{
+    double g[2], H[3];
+    double u = I->fixu ? I->c : t, v = I->fixu ? t : I->c;
+    *D = sdist(I->S, u, v, g, H);
+    if (E) *E = I->fixu ? g[1] : g[0];
+    if (Ep) *Ep = I->fixu ? H[2] : H[0];
+}
+
+static double iso_newton(const iso_prob* I, double lo, double hi, double t0, double eps)
+{
+    double t = t0;
+    for (int it = 0; it < 100; ++it) {
+        double D, E, Ep;
+        iso_ders(I, t, &D, &E, &Ep);
+        if (E > 0.0) hi = t;
+        else if (E < 0.0) lo = t;
+        else break;
+        double tn = (Ep > 0.0) ? t - E / Ep : 0.5 * (lo + hi);
+        if (!(tn >= lo && tn <= hi)) tn = 0.5 * (lo + hi);
+        if (fabs(tn - t) <= eps || hi - lo <= eps) { t = tn; break; }
+        t = tn;
+    }
+    return t;
+}
+
+/* sample parameters of one direction: OSAMP2 per non-empty span plus the end */
+static int dir_samples(const double* U, int p, int m, double* out)
+{
+    int j = 0;
+    double last = 0.0;
+    for (int k = p; k <= m; ++k) {
+        if (!(U[k] < U[k + 1])) continue;
+        for (int s = 0; s < OSAMP2; ++s) out[j++] = U[k] + (U[k + 1] - U[k]) * ((double)s / OSAMP2);
+        last = U[k + 1];
+    }
+    out[j++] = last;
+    return j;
+}
+
+/* bounds of |S_u|, |S_v|, |S_uu|, |S_vv| on span pair (qu, qv) from the
+ * derivative control nets (convex partition of unity, as for curves) */
+static void surf_deriv_bounds(const surf_prob* B, int qu, int qv, double* Vu, double* Vv, double* Auu,
+                              double* Avv)
+{
+    int pu = B->pu, pv = B->pv;
+    const double* U = B->U;
+    const double* V = B->V;
+    double vu = 0, vv = 0, au = 0, av = 0;
+#define PT(i, j) (B->P + 3 * ((int64_t)(i) * B->nv + (j)))
+    for (int j = qv - pv; j <= qv; ++j) {
+        double D1[SNP][3];
+        for (int i = qu - pu + 1; i <= qu; ++i) {
+            int r = i - (qu - pu + 1);
+            double den = U[i + pu] - U[i];
+            for (int c = 0; c < 3; ++c) D1[r][c] = den != 0.0 ? pu * (PT(i, j)[c] - PT(i - 1, j)[c]) / den : 0.0;
+            double w = sqrt(D1[r][0] * D1[r][0] + D1[r][1] * D1[r][1] + D1[r][2] * D1[r][2]);
+            if (w > vu) vu = w;
+        }
+        for (int i = qu - pu + 2; i <= qu; ++i) {
+            int r = i - (qu - pu + 1);
+            double den = U[i + pu - 1] - U[i];
+            if (den == 0.0) continue;
+            double x[3];
+            for (int c = 0; c < 3; ++c) x[c] = (pu - 1) * (D1[r][c] - D1[r - 1][c]) / den;
+            double w = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            if (w > au) au = w;
+        }
+    }
+    for (int i = qu - pu; i <= qu; ++i) {
+        double D1[SNP][3];
+        for (int j = qv - pv + 1; j <= qv; ++j) {
+            int r = j - (qv - pv + 1);
+            double den = V[j + pv] - V[j];
+            for (int c = 0; c < 3; ++c) D1[r][c] = den != 0.0 ? pv * (PT(i, j)[c] - PT(i, j - 1)[c]) / den : 0.0;
+            double w = sqrt(D1[r][0] * D1[r][0] + D1[r][1] * D1[r][1] + D1[r][2] * D1[r][2]);
+            if (w > vv) vv = w;
+        }
+        for (int j = qv - pv + 2; j <= qv; ++j) {
+            int r = j - (qv - pv + 1);
+            double den = V[j + pv - 1] - V[j];
+            if (den == 0.0) continue;
+            double x[3];
+            for (int c = 0; c < 3; ++c) x[c] = (pv - 1) * (D1[r][c] - D1[r - 1][c]) / den;
+            double w = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            if (w > av) av = w;
+        }
+    }
+#undef PT
+    *Vu = vu; *Vv = vv; *Auu = au; *Avv = av;
+}
+
+typedef struct { double u0, u1, v0, v1, D[4]; int depth; } cell_t; /* D: (u0,v0),(u1,v0),(u0,v1),(u1,v1) */
+
+/* lower bound of D on a cell inside one span pair (S polynomial there):
+ * first order: d >= min corner d - (Vu hu + Vv hv)/2;
+ * second order: bilinear interpolation error, D >= min corner D
+ *   - (hu^2 |D_uu| + hv^2 |D_vv|)/8, |D_uu| <= 2 (Vu^2 + R Auu), R the
+ *   largest distance on the cell. */
+static double cell_lower_bound(const cell_t* c, double Vu, double Vv, double Au, double Av)
+{
+    double hu = c->u1 - c->u0, hv = c->v1 - c->v0;
+    double Dmin = c->D[0], Dmax = c->D[0];
+    for (int k = 1; k < 4; ++k) {
+        if (c->D[k] < Dmin) Dmin = c->D[k];
+        if (c->D[k] > Dmax) Dmax = c->D[k];
+    }
+    double reach = 0.5 * (Vu * hu + Vv * hv);
+    double l1 = sqrt(Dmin) - reach;
+    l1 = l1 > 0.0 ? l1 * l1 : 0.0;
+    double R = sqrt(Dmax) + reach;
+    double l2 = Dmin - 0.125 * (hu * hu * 2.0 * (Vu * Vu + R * Au) + hv * hv * 2.0 * (Vv * Vv + R * Av));
+    return l1 > l2 ? l1 : l2;
+}
+
+/* damped, domain-clamped Newton on grad D from (u,v); returns the end point */
+static void surf_polish(const surf_prob* B, double ua, double ub, double va, double vb, double* pu_,
+                        double* pv_, double eps)
+{
+    double u = *pu_, v = *pv_;
+    for (int it = 0; it < 100; ++it) {
+        double g[2], H[3];
+        double D = sdist(B, u, v, g, H);
+        double det = H[0] * H[2] - H[1] * H[1];
+        double su, sv;
+        if (H[0] > 0.0 && det > 0.0) {
+            su = -(H[2] * g[0] - H[1] * g[1]) / det;
+            sv = -(H[0] * g[1] - H[1] * g[0]) / det;
+        } else {
+            double gn = sqrt(g[0] * g[0] + g[1] * g[1]);
+            if (gn == 0.0) break;
+            su = -g[0] / gn * (ub - ua) * (1.0 / 64);
+            sv = -g[1] / gn * (vb - va) * (1.0 / 64);
+        }
+        double lam = 1.0, un = u, vn = v, Dn = D;
+        int ok = 0;
+        for (int ls = 0; ls < 40; ++ls) {
+            un = u + lam * su; vn = v + lam * sv;
+            if (un < ua) un = ua;
+            if (un > ub) un = ub;
+            if (vn < va) vn = va;
+            if (vn > vb) vn = vb;
+            Dn = sdist(B, un, vn, NULL, NULL);
+            if (Dn <= D) { ok = 1; break; }
+            lam *= 0.5;
+        }
+        if (!ok) break;
+        double step = fabs(un - u) + fabs(vn - v);
+        u = un; v = vn;
+        if (step <= eps) break;
+    }
+    *pu_ = u; *pv_ = v;
+}
+
+static void project_surface_one(const surf_prob* B, double* uv_out, double* d_out)
+{
+    int nsu_max = (B->mu + 2) * OSAMP2 + 2, nsv_max = (B->mv + 2) * OSAMP2 + 2;
+    double* us = (double*)malloc(sizeof(double) * (size_t)nsu_max);
+    double* vs = (double*)malloc(sizeof(double) * (size_t)nsv_max);
+    int nsu = dir_samples(B->U, B->pu, B->mu, us);
+    int nsv = dir_samples(B->V, B->pv, B->mv, vs);
+    double* Dg = (double*)malloc(sizeof(double) * (size_t)nsu * (size_t)nsv);
+    for (int i = 0; i < nsu; ++i)
+        for (int j = 0; j < nsv; ++j) Dg[(int64_t)i * nsv + j] = sdist(B, us[i], vs[j], NULL, NULL);
+    double ua = us[0], ub = us[nsu - 1], va = vs[0], vb = vs[nsv - 1];
+    double epsu = 1e-15 * (ub - ua), epsv = 1e-15 * (vb - va);
+    double bestD = INFINITY, bu = ua, bv = va;
+#define CONSIDER2(uu, vv)                                                                \
+    do {                                                                                 \
+        double D_ = sdist(B, (uu), (vv), NULL, NULL);                                    \
+        if (D_ < bestD || (D_ == bestD && ((uu) < bu || ((uu) == bu && (vv) < bv)))) {  \
+            bestD = D_; bu = (uu); bv = (vv);                                            \
+        }                                                                                \
+    } while (0)
+    /* interior stationary points: damped Newton on grad D from each sampled
+     * basin, kept inside the domain */
+    for (int i = 0; i < nsu; ++i) {
+        for (int j = 0; j < nsv; ++j) {
+            double Dc = Dg[(int64_t)i * nsv + j];
+            int lmin = 1;
+            for (int di = -1; di <= 1 && lmin; ++di)
+                for (int dj = -1; dj <= 1; ++dj) {
+                    int a = i + di, b = j + dj;
+                    if ((di == 0 && dj == 0) || a < 0 || b < 0 || a >= nsu || b >= nsv) continue;
+                    if (Dg[(int64_t)a * nsv + b] < Dc) { lmin = 0; break; }
+                }
+            if (!lmin) continue;
+            CONSIDER2(us[i], vs[j]);
+            double u = us[i], v = vs[j];
+            surf_polish(B, ua, ub, va, vb, &u, &v, epsu + epsv);
+            CONSIDER2(u, v);
+        }
+    }
+    /* boundary and crease iso-curves: the four domain edges and every interior
+     * knot line of multiplicity >= degree (where D need not be smooth) */
+    int niso = 0;
+    double isoc[4096];
+    int isofix[4096];
+    isoc[niso] = ua; isofix[niso++] = 1;
+    isoc[niso] = ub; isofix[niso++] = 1;
+    isoc[niso] = va; isofix[niso++] = 0;
+    isoc[niso] = vb; isofix[niso++] = 0;
+    for (int dir = 0; dir < 2; ++dir) {
+        const double* K = dir == 0 ? B->U : B->V;
+        int p = dir == 0 ? B->pu : B->pv, m = dir == 0 ? B->mu : B->mv;
+        double lo = dir == 0 ? ua : va, hi = dir == 0 ? ub : vb;
+        for (int k = p + 1; k <= m; ++k) {
+            if (!(K[k] > lo && K[k] < hi) || K[k] == K[k - 1]) continue;
+            int mult = 1;
+            while (k + mult <= m && K[k + mult] == K[k]) ++mult;
+            if (mult >= p && niso < 4096) { isoc[niso] = K[k]; isofix[niso++] = dir == 0 ? 1 : 0; }
+        }
+    }
+    for (int e = 0; e < niso; ++e) {
+        iso_prob I = { B, isofix[e], isoc[e] };
+        const double* ts = isofix[e] ? vs : us;
+        int nt = isofix[e] ? nsv : nsu;
+        double eps = isofix[e] ? epsv : epsu;
+        double* Dl = (double*)malloc(sizeof(double) * (size_t)nt);
+        for (int k = 0; k < nt; ++k) iso_ders(&I, ts[k], &Dl[k], NULL, NULL);
+        for (int k = 0; k < nt; ++k) {
+            int lmin = (k == 0 || Dl[k] <= Dl[k - 1]) && (k == nt - 1 || Dl[k] <= Dl[k + 1]);
+            if (!lmin) continue;
+            double lo = ts[k > 0 ? k - 1 : 0], hi = ts[k < nt - 1 ? k + 1 : nt - 1];
+            double tn = iso_newton(&I, lo, hi, ts[k], eps);
+            if (isofix[e]) { CONSIDER2(isoc[e], tn); CONSIDER2(isoc[e], ts[k]); }
+            else { CONSIDER2(tn, isoc[e]); CONSIDER2(ts[k], isoc[e]); }
+        }
+        free(Dl);
+    }
+    /* branch and bound over the sample cells of every span pair, with the
+     * rigorous bound of cell_lower_bound: a cell whose bound is below the best
+     * squared distance is split in four (centre polished by Newton when it is
+     * below its corners) until the bound clears or depth 30 is reached */
+    {
+        int cap = 1024, top = 0;
+        cell_t* st = (cell_t*)malloc(sizeof(cell_t) * (size_t)cap);
+        int i0 = 0;
+        for (int qu = B->pu; qu <= B->mu; ++qu) {
+            if (!(B->U[qu] < B->U[qu + 1])) continue;
+            int j0 = 0;
+            for (int qv = B->pv; qv <= B->mv; ++qv) {
+                if (!(B->V[qv] < B->V[qv + 1])) continue;
+                double Vu, Vv, Au, Av;
+                surf_deriv_bounds(B, qu, qv, &Vu, &Vv, &Au, &Av);
+                for (int a = 0; a < OSAMP2; ++a)
+                    for (int b = 0; b < OSAMP2; ++b) {
+                        int i = i0 + a, jj = j0 + b;
+                        cell_t c0 = { us[i], us[i + 1], vs[jj], vs[jj + 1],
+                                      { Dg[(int64_t)i * nsv + jj], Dg[(int64_t)(i + 1) * nsv + jj],
+                                        Dg[(int64_t)i * nsv + jj + 1], Dg[(int64_t)(i + 1) * nsv + jj + 1] },
+                                      0 };
+                        st[top++] = c0;
+                        while (top > 0) {
+                            cell_t c = st[--top];
+                            if (c.depth >= 30 || !(cell_lower_bound(&c, Vu, Vv, Au, Av) < bestD)) continue;
+                            double um = 0.5 * (c.u0 + c.u1), vm = 0.5 * (c.v0 + c.v1);
+                            double Dmid[5] = { sdist(B, um, c.v0, NULL, NULL), sdist(B, c.u0, vm, NULL, NULL),
+                                               sdist(B, um, vm, NULL, NULL), sdist(B, c.u1, vm, NULL, NULL),
+                                               sdist(B, um, c.v1, NULL, NULL) };
+                            double pu5[5] = { um, c.u0, um, c.u1, um }, pv5[5] = { c.v0, vm, vm, vm, c.v1 };
+                            for (int k = 0; k < 5; ++k)
+                                if (Dmid[k] < bestD) { bestD = Dmid[k]; bu = pu5[k]; bv = pv5[k]; }
+                            if (Dmid[2] <= c.D[0] && Dmid[2] <= c.D[1] && Dmid[2] <= c.D[2] && Dmid[2] <= c.D[3]) {
+                                double u = um, v = vm;
+                                surf_polish(B, ua, ub, va, vb, &u, &v, epsu + epsv);
+                                CONSIDER2(u, v);
+                            }
+                            if (top + 4 > cap) { cap *= 2; st = (cell_t*)realloc(st, sizeof(cell_t) * (size_t)cap); }
+                            int d1 = c.depth + 1;
+                            st[top++] = (cell_t){ um, c.u1, vm, c.v1, { Dmid[2], Dmid[3], Dmid[4], c.D[3] }, d1 };
+                            st[top++] = (cell_t){ c.u0, um, vm, c.v1, { Dmid[1], Dmid[2], c.D[2], Dmid[4] }, d1 };
+                            st[top++] = (cell_t){ um, c.u1, c.v0, vm, { Dmid[0], c.D[1], Dmid[2], Dmid[3] }, d1 };
+                            st[top++] = (cell_t){ c.u0, um, c.v0, vm, { c.D[0], Dmid[0], Dmid[1], Dmid[2] }, d1 };
+                        }
+                    }
+                j0 += OSAMP2;
+            }
+            i0 += OSAMP2;
+        }
+        free(st);
+    }
+#undef CONSIDER2
+    uv_out[0] = bu;
+    uv_out[1] = bv;
+    *d_out = sqrt(bestD);
+    free(us); free(vs); free(Dg);
+}
+
+int orc_project_surfaces(int64_t n, const int32_t* pu, const int32_t* pv, const int32_t* nu,
+                         const int32_t* nv, const int64_t* kuoff, const double* ku,
+                         const int64_t* kvoff, const double* kv, const int64_t* coff,
+                         const double* cps, int64_t nq, const int32_t* qs, const double* qxyz,
+                         double* uv_out, double* d_out, int nthreads)
+{
+    for (int64_t k = 0; k < nq; ++k)
+        if (qs[k] < 0 || qs[k] >= n) return ORC_EINVAL;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < nq; ++k) {
+        int64_t s = qs[k];
+        surf_prob B = { pu[s], pv[s], nu[s] - 1, nv[s] - 1, nv[s], ku + kuoff[s], kv + kvoff[s],
+                        cps + 3 * coff[s], qxyz + 3 * k };
+        project_surface_one(&B, uv_out + 2 * k, &d_out[k]);
+    }
+    return ORC_OK;
+}

@@ -1,0 +1,254 @@
+/*
+ * bspl.h -- C ABI of the GB300 (sm_103a) library for batched point projection
+ * and inversion on non-rational B-spline curves and surfaces, after their
+ * decomposition into cubic Bezier segments / bicubic Bezier patches.
+ *
+ * Method: Wu & Zou, "Matrix representation and GPU-optimized parallel
+ * B-spline computing" (arXiv 2504.11498).
+ *   - problem statement: Sec. 3, Eqs. projection, projections, inversion;
+ *   - decomposition: Sec. 4.2.1 (Eq. decomfinal) and Sec. 4.2.2 (G1-continuous
+ *     degree reduction, Eqs. G1-condition, epsl, differentiatedelta0/1;
+ *     error-controlled subdivision, Eq. subLandR);
+ *   - squared distance and its derivatives: Sec. 4.2.3, Eqs. Dt, Et, E't;
+ *   - per-query minimum and reparameterisation: Sec. 4.4.2.
+ *
+ * Conventions for every entry point:
+ *   - all array pointers are DEVICE pointers owned by the caller unless stated
+ *     otherwise; the library never allocates or frees device memory;
+ *   - every call is asynchronous on the given stream, except bspl_decompose,
+ *     which synchronises that stream twice (after validating the splines and
+ *     after counting the segments);
+ *   - argument errors that the host can see (NULL pointers, negative sizes,
+ *     workspace too small) return BSPL_EINVAL before anything is launched;
+ *     per-query data problems (spline index out of range, non-finite point)
+ *     set BSPL_Q_INVALID in that query's status byte; nothing traps;
+ *   - CUDA launch failures return BSPL_ECUDA.
+ */
+#ifndef BSPL_H
+#define BSPL_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BSPL_OK = 0,
+    BSPL_EINVAL = 1,   /* invalid argument or spline data                       */
+    BSPL_ENOSPACE = 2, /* capacity too small (counts were still written)        */
+    BSPL_ECUDA = 3,    /* a CUDA call failed                                    */
+    BSPL_ENOTCONV = 4, /* subdivision hit its depth cap (40) somewhere          */
+    BSPL_ETIMEOUT = 5  /* reserved                                              */
+} bspl_status;
+
+typedef enum {
+    BSPL_FP64 = 0,          /* cull, seed and Newton all in FP64                  */
+    BSPL_MIXED = 1,         /* FP32 cull/seed/early Newton + 2 FP64 Newton steps  */
+    BSPL_LEARNED_MIXED = 2  /* as MIXED with the MLP seed in place of the grid    */
+} bspl_precision;
+
+/* per-query status bits */
+#define BSPL_Q_CONVERGED 1u  /* the final Newton step met its tolerance          */
+#define BSPL_Q_FALLBACK 2u   /* mixed/learned result needed the FP64 fallback    */
+#define BSPL_Q_AT_END 4u     /* minimiser at an end of the parameter domain      */
+#define BSPL_Q_NONCONV 8u    /* Newton cap reached without convergence           */
+#define BSPL_Q_OFF_CURVE 16u /* inversion: distance above 1e-9 x diagonal        */
+#define BSPL_Q_INVALID 32u   /* spline index out of range or non-finite point    */
+
+/* Curves in CSR form (Sec. 3): curve c has degree p = degree[c] (1..31),
+ * control points cps[cp_off[c] .. cp_off[c+1]) (xyz, FP64, [ncp][3]) and
+ * knots knots[knot_off[c] .. knot_off[c+1]) with ncp + p + 1 entries,
+ * non-decreasing and finite.  The parameter domain is [t_p, t_{ncp}]. */
+typedef struct {
+    int64_t n;
+    const int32_t* degree;
+    const int64_t* knot_off;
+    const double* knots;
+    const int64_t* cp_off;
+    const double* cps;
+} bspl_curves;
+
+/* Tensor-product surfaces in CSR form: surface s has degrees deg_u[s],
+ * deg_v[s] (1..15), an n_u[s] x n_v[s] control net stored row-major
+ * [n_u][n_v][3] (first index along u) at cps[3*cp_off[s]...], and knot
+ * vectors knots_u[knot_u_off[s]..], knots_v[knot_v_off[s]..] of lengths
+ * n_u+deg_u+1 and n_v+deg_v+1. */
+typedef struct {
+    int64_t n;
+    const int32_t* deg_u;
+    const int32_t* deg_v;
+    const int32_t* n_u;
+    const int32_t* n_v;
+    const int64_t* knot_u_off;
+    const double* knots_u;
+    const int64_t* knot_v_off;
+    const double* knots_v;
+    const int64_t* cp_off;
+    const double* cps;
+} bspl_surfaces;
+
+/* widths (in elements) of the per-segment and per-group records */
+#define BSPL_GROUP 32        /* consecutive segments/patches per culling group */
+#define BSPL_CREC64 18       /* curve FP64: lo[3] hi[3] a0[3] a1[3] a2[3] a3[3] (power basis in u) */
+#define BSPL_CREC32 20       /* curve FP32: same layout + 2 pad, box rounded outward */
+#define BSPL_SREC64 54       /* patch FP64: lo[3] hi[3] a[4][4][3] (power basis in u,v) */
+#define BSPL_SREC32 56       /* patch FP32: same layout + span-pair degrees (pu, pv) */
+#define BSPL_GREC64 12       /* group FP64: lo[3] hi[3] ref[3] pad[3] */
+#define BSPL_GREC32 12       /* group FP32: same, box rounded outward */
+
+/* Decomposition output and query tables (all caller-owned device memory).
+ *   seg_off [n+1]        segments of spline i are [seg_off[i], seg_off[i+1])
+ *   ctrl    [cap][4][3]  cubic Bezier control points (curves)
+ *           [cap][4][4][3] bicubic net, first index along u (surfaces)
+ *   prange  [cap][2]     (t0, t1) of each segment in the original parameter
+ *           [cap][4]     (u0, u1, v0, v1) of each patch
+ *   diag    [n]          diagonal of each spline's control-point box (NaN
+ *                        for a spline that failed validation)
+ *   rec64/rec32          per-segment search records (BSPL_*REC* above)
+ *   grp_off [n+1], grp64/grp32: culling groups of BSPL_GROUP consecutive
+ *                        segments (box of the group + a point on it);
+ *                        grp_capacity >= n + capacity / BSPL_GROUP + 1 always suffices
+ * Surfaces additionally:
+ *   patch_span [cap] int64  span-pair slot of each patch
+ *   patch_box  [cap][4]     the patch's (u0,u1,v0,v1) inside its span pair, in [0,1]
+ *   span_net   [n_cp_total][BSPL_SPAN_NET]  power-basis coefficients of the
+ *                        ORIGINAL span-pair patch (degree <= 7 per direction in
+ *                        the query path), indexed by slot, used for the final
+ *                        FP64 Newton steps on the original surface.
+ */
+#define BSPL_SPAN_NET (8 * 8 * 3)
+typedef struct {
+    int32_t is_surface;
+    int64_t n;
+    int64_t capacity;
+    int64_t grp_capacity;
+    int64_t* seg_off;
+    double* ctrl;
+    double* prange;
+    double* diag;
+    double* rec64;
+    float* rec32;
+    int64_t* grp_off;
+    double* grp64;
+    float* grp32;
+    int64_t* patch_span;
+    double* patch_box;
+    double* span_net;
+    int64_t n_cp_total;  /* in: cp_off[n] of the decomposed set (sizes the slot arrays) */
+    double tol_rel;      /* out: tolerance the tables were built with */
+} bspl_segments;
+
+/* Query options.  Zero fields take the defaults given. */
+typedef struct {
+    int32_t prec;        /* bspl_precision (default BSPL_FP64)                      */
+    int32_t samples;     /* grid samples per segment/patch: 8, 16 or 32 (curves, default
+                            16; 8 is coarse and may miss close minima), 16 or 32
+                            (surfaces, 4x4 or 8x4, default 32)                   */
+    int32_t newton_max;  /* FP64 Newton cap, plain path and fallback (default 30)   */
+    int32_t fp32_steps;  /* FP32 Newton steps before the FP64 finish (default 4)    */
+    int32_t sort_queries;/* 1: group queries by spline first (default 1)            */
+    int32_t reserved;
+    const void* mlp;     /* learned seed (BSPL_LEARNED_MIXED), else NULL            */
+    uint64_t* counters;  /* optional device array [BSPL_NCOUNTERS], accumulated     */
+} bspl_options;
+
+/* device counters accumulated by the query calls when opt->counters != NULL */
+#define BSPL_CNT_QUERIES 0
+#define BSPL_CNT_SEG_TESTED 1  /* segment boxes tested */
+#define BSPL_CNT_GRP_TESTED 2  /* group boxes tested */
+#define BSPL_CNT_CANDIDATES 3  /* segments that reached the seed stage */
+#define BSPL_CNT_NEWTON 4      /* Newton candidates (basins) refined */
+#define BSPL_CNT_FALLBACK 5    /* queries that needed the FP64 fallback */
+#define BSPL_CNT_NONCONV 6
+#define BSPL_CNT_NEWTON32_ITERS 7 /* FP32 Newton iterations */
+#define BSPL_CNT_NEWTON64_ITERS 8 /* FP64 Newton iterations */
+#define BSPL_NCOUNTERS 10
+
+/* workspace sizes: op is one of */
+#define BSPL_OP_DECOMPOSE_CURVES 1
+#define BSPL_OP_DECOMPOSE_SURFACES 2
+#define BSPL_OP_QUERY_CURVES 3
+#define BSPL_OP_QUERY_SURFACES 4
+
+/* Bytes of device workspace a call of kind `op` needs.  n_splines = n,
+ * n_cp_total = total control points (cp_off[n]), n_seg = segments of the
+ * decomposition, n_q = queries. */
+size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64_t n_seg, int64_t n_q);
+
+/* Decomposes every spline into cubic Bezier segments (is_surface = 0,
+ * splines -> bspl_curves) or bicubic patches (is_surface = 1, splines ->
+ * bspl_surfaces), Sec. 4.2:
+ *   each non-empty knot span (span pair) is converted to its Bezier piece by
+ *   the span-wise matrix route Q = B_p^{-1} M A P (Eq. decomfinal, formed in
+ *   the local parameter); degree 1-2 pieces are elevated exactly, degree 3
+ *   kept, higher degrees reduced by the G1-continuous L2-optimal rule; a
+ *   reduced piece whose certified deviation bound (control points of the
+ *   difference after elevation) exceeds tol_rel x diag is split at the
+ *   midpoint of its parameter interval and both halves are reduced again
+ *   from the original piece (depth cap 40 and at most 65536 pieces per span
+ *   or span pair; reaching either accepts the piece and -> BSPL_ENOTCONV).
+ * Two-phase use: with out->ctrl == NULL the call only counts: it writes
+ * out->seg_off, out->diag and *n_seg_total and returns BSPL_OK.  Otherwise,
+ * if *n_seg_total > out->capacity (or the group count exceeds
+ * out->grp_capacity) it writes the counts and returns BSPL_ENOSPACE; else it
+ * fills every array of *out.  out->n_cp_total must equal cp_off[n].
+ * Invalid spline data (degree out of range, knot count
+ * mismatch, decreasing or non-finite knots, non-finite control points, empty
+ * domain) -> BSPL_EINVAL with nothing written beyond seg_off/diag.
+ * Workspace: bspl_workspace_bytes(BSPL_OP_DECOMPOSE_*, n, n_cp_total, 0, 0). */
+bspl_status bspl_decompose(int is_surface, const void* splines, double tol_rel, bspl_segments* out,
+                           int64_t* n_seg_total, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Projection of n_q points q_xyz [n_q][3] onto curves q_curve [n_q] (Eq.
+ * projections): t [n_q] receives the minimising parameter in the curve's
+ * original parameter (Sec. 4.4.2 reparameterisation), dist [n_q] the distance
+ * to the decomposed curve, status [n_q] the BSPL_Q_* bits.  Search: group
+ * queries by curve, cull segment groups and segments by box distance against
+ * an upper bound from points on the curve, sample a grid on each surviving
+ * segment, refine every sampled basin by safeguarded Newton on E = D'
+ * (Eqs. Dt, Et, E't), keep the smallest distance (ties: smallest parameter).
+ * opt->prec selects FP64 or FP32 search + 2 FP64 Newton steps.
+ * Workspace: bspl_workspace_bytes(BSPL_OP_QUERY_CURVES, n, n_cp_total, n_seg, n_q). */
+bspl_status bspl_project_curves(const bspl_segments* segs, int64_t n_q, const int32_t* q_curve,
+                                const double* q_xyz, const bspl_options* opt, double* t, double* dist,
+                                uint8_t* status, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Inversion (Eq. inversion): the same search for points that lie on the
+ * curve; additionally sets BSPL_Q_OFF_CURVE when dist > 1e-9 x diag. */
+bspl_status bspl_invert_curves(const bspl_segments* segs, int64_t n_q, const int32_t* q_curve,
+                               const double* q_xyz, const bspl_options* opt, double* t, double* dist,
+                               uint8_t* status, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Surface projection: uv [n_q][2] receives the minimising (u, v) in the
+ * surface's original parameters, dist the distance to the ORIGINAL surface
+ * (the last two FP64 Newton steps run on the original span-pair patch).
+ * Workspace: bspl_workspace_bytes(BSPL_OP_QUERY_SURFACES, ...). */
+bspl_status bspl_project_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t* q_surf,
+                                  const double* q_xyz, const bspl_options* opt, double* uv, double* dist,
+                                  uint8_t* status, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Surface inversion; sets BSPL_Q_OFF_CURVE when dist > 1e-9 x diag. */
+bspl_status bspl_invert_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t* q_surf,
+                                 const double* q_xyz, const bspl_options* opt, double* uv, double* dist,
+                                 uint8_t* status, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Evaluates the ORIGINAL curves at t [n_q] (Cox-de Boor, Sec. 3 Eq.
+ * bsplinebasis): xyz [n_q][3].  t outside the domain is clamped; an
+ * out-of-range curve index yields NaN.  Used to place inversion queries. */
+bspl_status bspl_eval_curves(const bspl_curves* curves, int64_t n_q, const int32_t* q_curve, const double* t,
+                             double* xyz, cudaStream_t stream);
+
+/* Evaluates the ORIGINAL surfaces at uv [n_q][2]: xyz [n_q][3]. */
+bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const int32_t* q_surf,
+                               const double* uv, double* xyz, cudaStream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char* bspl_status_string(bspl_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSPL_H */

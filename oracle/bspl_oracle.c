@@ -37,6 +37,7 @@
 #define OMAXP 31          /* highest supported degree (paper Sec. 5.2 limit) */
 #define ONP (OMAXP + 1)   /* control points of one span */
 #define ODEPTH 40         /* subdivision depth cap */
+#define OLEAFCAP 65536    /* leaves per span (pair) after which every node is accepted */
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOSPACE = 2, ORC_ENOTCONV = 4 };
 
@@ -460,15 +461,15 @@ static void to_cubic(int p, const double* Q, int s, double* R, int rs)
     } else if (p > 3) {
         reduce_g1(p, Q, s, R, rs, NULL, 0);
     } else {
-        double w[4][3], x[4][3];
+        double w[12], x[12];
         for (int i = 0; i <= p; ++i)
-            for (int c = 0; c < 3; ++c) w[i][c] = Q[i * s + c];
+            for (int c = 0; c < 3; ++c) w[3 * i + c] = Q[i * s + c];
         for (int n = p; n < 3; ++n) {
-            elevate(n, &w[0][0], &x[0][0], 3);
-            memcpy(w, x, sizeof(w));
+            elevate(n, w, x, 3);
+            memcpy(w, x, sizeof(double) * 3 * (size_t)(n + 2));
         }
         for (int i = 0; i < 4; ++i)
-            for (int c = 0; c < 3; ++c) R[i * rs + c] = w[i][c];
+            for (int c = 0; c < 3; ++c) R[i * rs + c] = w[3 * i + c];
     }
 }
 
@@ -476,16 +477,16 @@ static void to_cubic(int p, const double* Q, int s, double* R, int rs)
  * because Bernstein weights are a convex partition of unity (p >= 3). */
 static double bound2_curve(int p, const double* Q, int s, const double* R, int rs)
 {
-    double w[ONP + 1][3], x[ONP + 1][3];
+    double w[(ONP + 1) * 3], x[(ONP + 1) * 3];
     for (int i = 0; i < 4; ++i)
-        for (int c = 0; c < 3; ++c) w[i][c] = R[i * rs + c];
+        for (int c = 0; c < 3; ++c) w[3 * i + c] = R[i * rs + c];
     for (int n = 3; n < p; ++n) {
-        elevate(n, &w[0][0], &x[0][0], 3);
+        elevate(n, w, x, 3);
         memcpy(w, x, sizeof(double) * 3 * (size_t)(n + 2));
     }
     double b = 0.0;
     for (int i = 0; i <= p; ++i) {
-        double dx = Q[i * s + 0] - w[i][0], dy = Q[i * s + 1] - w[i][1], dz = Q[i * s + 2] - w[i][2];
+        double dx = Q[i * s + 0] - w[3 * i], dy = Q[i * s + 1] - w[3 * i + 1], dz = Q[i * s + 2] - w[3 * i + 2];
         double e = (dx * dx + dy * dy) + dz * dz;
         if (e > b) b = e;
     }
@@ -541,7 +542,7 @@ typedef struct {
     int p;
     double thr2;
     double tq, tq1;
-    int64_t count, cap;
+    int64_t count, cap, span_first;
     double* ctrl;   /* [cap][4][3] */
     double* prange; /* [cap][2] */
     int maxdepth;
@@ -562,12 +563,12 @@ static double dyadic_t(double tq, double tq1, int64_t k, int L)
  * modification, midpoint reading) */
 static void curve_node(curve_ctx* X, const double* Q, int L, int64_t k)
 {
-    double R[4][3];
+    double R[12];
     int p = X->p;
-    to_cubic(p, Q, 3, &R[0][0], 3);
+    to_cubic(p, Q, 3, R, 3);
     int accept = 1;
-    if (p > 3) accept = bound2_curve(p, Q, 3, &R[0][0], 3) <= X->thr2;
-    if (!accept && L >= ODEPTH) { accept = 1; X->notconv = 1; }
+    if (p > 3) accept = bound2_curve(p, Q, 3, R, 3) <= X->thr2;
+    if (!accept && (L >= ODEPTH || X->count - X->span_first >= OLEAFCAP)) { accept = 1; X->notconv = 1; }
     if (accept) {
         if (X->count < X->cap && X->ctrl) {
             memcpy(X->ctrl + 12 * X->count, R, sizeof(R));
@@ -578,10 +579,10 @@ static void curve_node(curve_ctx* X, const double* Q, int L, int64_t k)
         if (L > X->maxdepth) X->maxdepth = L;
         return;
     }
-    double Lq[ONP + 1][3], Rq[ONP + 1][3];
-    halve(p, Q, 3, &Lq[0][0], &Rq[0][0]);
-    curve_node(X, &Lq[0][0], L + 1, 2 * k);
-    curve_node(X, &Rq[0][0], L + 1, 2 * k + 1);
+    double Lq[(ONP + 1) * 3], Rq[(ONP + 1) * 3];
+    halve(p, Q, 3, Lq, Rq);
+    curve_node(X, Lq, L + 1, 2 * k);
+    curve_node(X, Rq, L + 1, 2 * k + 1);
 }
 
 /* diagonal of the axis-aligned box of np points */
@@ -607,43 +608,70 @@ static int check_knots(int p, const double* U, int64_t nU, int64_t nP)
     return U[p] < U[nP];
 }
 
+/* decomposes curve c with its segments written from index `first` (when the
+ * arrays are given and fit); returns the count, or -1 for invalid data */
+static int64_t decompose_one_curve(int64_t c, const int32_t* deg, const int64_t* koff, const double* knots,
+                                   const int64_t* coff, const double* cps, double tol_rel, int64_t first,
+                                   int64_t cap, double* ctrl, double* prange, int* maxdepth, int* notconv)
+{
+    int p = deg[c];
+    int64_t nP = coff[c + 1] - coff[c], nU = koff[c + 1] - koff[c];
+    const double* U = knots + koff[c];
+    const double* P = cps + 3 * coff[c];
+    if (!check_knots(p, U, nU, nP)) return -1;
+    for (int64_t i = 0; i < 3 * nP; ++i) if (!isfinite(P[i])) return -1;
+    double thr = tol_rel * box_diag(P, nP);
+    curve_ctx X;
+    X.p = p; X.thr2 = thr * thr; X.cap = cap; X.maxdepth = 0; X.notconv = 0;
+    X.ctrl = ctrl; X.prange = prange;
+    X.count = first;
+    for (int q = p; q <= (int)nP - 1; ++q) {
+        if (!(U[q] < U[q + 1])) continue;
+        double Q[(ONP + 1) * 3];
+        span_bezier(p, U, q, P + 3 * (q - p), Q);
+        X.tq = U[q]; X.tq1 = U[q + 1];
+        X.span_first = X.count;
+        curve_node(&X, Q, 0, 0);
+    }
+    *maxdepth = X.maxdepth;
+    *notconv = X.notconv;
+    return X.count - first;
+}
+
 /* seg_off[n+1] always written; ctrl/prange written when cap suffices.
- * returns ORC_ENOSPACE when the total exceeds cap (counts still valid). */
+ * returns ORC_ENOSPACE when the total exceeds cap (counts still valid).
+ * Curves are independent: counted in parallel, offsets by a prefix sum, then
+ * filled in parallel. */
 int orc_decompose_curves(int64_t n, const int32_t* deg, const int64_t* koff, const double* knots,
                          const int64_t* coff, const double* cps, double tol_rel, int64_t* seg_off,
                          int64_t cap, double* ctrl, double* prange, int64_t* total, int* maxdepth)
 {
-    int64_t cnt = 0;
-    int md = 0, nc = 0;
-    seg_off[0] = 0;
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int md = 0, nc = 0, bad = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(max : md) reduction(| : nc, bad)
     for (int64_t c = 0; c < n; ++c) {
-        int p = deg[c];
-        int64_t nP = coff[c + 1] - coff[c], nU = koff[c + 1] - koff[c];
-        const double* U = knots + koff[c];
-        const double* P = cps + 3 * coff[c];
-        if (!check_knots(p, U, nU, nP)) return ORC_EINVAL;
-        for (int64_t i = 0; i < 3 * nP; ++i) if (!isfinite(P[i])) return ORC_EINVAL;
-        double thr = tol_rel * box_diag(P, nP);
-        curve_ctx X;
-        X.p = p; X.thr2 = thr * thr; X.cap = cap; X.maxdepth = 0; X.notconv = 0;
-        X.ctrl = ctrl; X.prange = prange;
-        X.count = cnt;
-        for (int q = p; q <= (int)nP - 1; ++q) {
-            if (!(U[q] < U[q + 1])) continue;
-            double Q[ONP + 1][3];
-            span_bezier(p, U, q, P + 3 * (q - p), &Q[0][0]);
-            X.tq = U[q]; X.tq1 = U[q + 1];
-            curve_node(&X, &Q[0][0], 0, 0);
-        }
-        cnt = X.count;
-        if (X.maxdepth > md) md = X.maxdepth;
-        nc |= X.notconv;
-        seg_off[c + 1] = cnt;
+        int m1 = 0, n1 = 0;
+        cnt[c] = decompose_one_curve(c, deg, koff, knots, coff, cps, tol_rel, 0, 0, NULL, NULL, &m1, &n1);
+        if (cnt[c] < 0) bad = 1;
+        if (m1 > md) md = m1;
+        nc |= n1;
     }
-    *total = cnt;
+    if (bad) { free(cnt); return ORC_EINVAL; }
+    seg_off[0] = 0;
+    for (int64_t c = 0; c < n; ++c) seg_off[c + 1] = seg_off[c] + cnt[c];
+    int64_t tot = seg_off[n];
+    if (ctrl && tot <= cap) {
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t c = 0; c < n; ++c) {
+            int m1, n1;
+            decompose_one_curve(c, deg, koff, knots, coff, cps, tol_rel, seg_off[c], cap, ctrl, prange, &m1, &n1);
+        }
+    }
+    free(cnt);
+    *total = tot;
     if (maxdepth) *maxdepth = md;
     if (nc) return ORC_ENOTCONV;
-    return cnt <= cap ? ORC_OK : ORC_ENOSPACE;
+    return tot <= cap ? ORC_OK : ORC_ENOSPACE;
 }
 
 /* ------------------------------------------------------------------ */
@@ -657,82 +685,92 @@ typedef struct {
     int pu, pv;
     double thr2;
     double u0, u1, v0, v1; /* span pair parameter box */
-    int64_t count, cap;
+    int64_t count, cap, span_first;
     double* ctrl;   /* [cap][4][4][3] */
     double* prange; /* [cap][4] */
     int maxdepth, notconv;
 } surf_ctx;
 
-/* net is [pu+1][pv+1][3] (index i along u), stored in a fixed [SNP][SNP][3] array */
-typedef double net_t[SNP][SNP][3];
+/* a net of (pu+1) x (pv+1) points (index a along u), stored flat with a fixed
+ * row length: point (a, b) at NETI(a, b) */
+#define NETI(a, b) (((a) * SNP + (b)) * 3)
+#define NETN (SNP * SNP * 3)
 
 /* reduce along u for every v column, then along v for every u row */
-static void surf_to_bicubic(int pu, int pv, const net_t Q, double R[4][4][3])
+static void surf_to_bicubic(int pu, int pv, const double* Q, double* R /* [4][4][3] flat */)
 {
-    double Rp[4][SNP][3];
+    double Rp[4 * SNP * 3];
     for (int j = 0; j <= pv; ++j) {
-        double col[SNP][3], r[4][3];
+        double col[SNP * 3], r[12];
         for (int i = 0; i <= pu; ++i)
-            for (int c = 0; c < 3; ++c) col[i][c] = Q[i][j][c];
-        to_cubic(pu, &col[0][0], 3, &r[0][0], 3);
+            for (int c = 0; c < 3; ++c) col[3 * i + c] = Q[NETI(i, j) + c];
+        to_cubic(pu, col, 3, r, 3);
         for (int i = 0; i < 4; ++i)
-            for (int c = 0; c < 3; ++c) Rp[i][j][c] = r[i][c];
+            for (int c = 0; c < 3; ++c) Rp[NETI(i, j) + c] = r[3 * i + c];
     }
     for (int i = 0; i < 4; ++i) {
-        double r[4][3];
-        to_cubic(pv, &Rp[i][0][0], 3, &r[0][0], 3);
+        double r[12];
+        to_cubic(pv, Rp + NETI(i, 0), 3, r, 3);
         for (int j = 0; j < 4; ++j)
-            for (int c = 0; c < 3; ++c) R[i][j][c] = r[j][c];
+            for (int c = 0; c < 3; ++c) R[(i * 4 + j) * 3 + c] = r[3 * j + c];
+    }
+}
+
+static void elevate_to(int from, int to, double* w /* [SNP*3] */)
+{
+    double x[SNP * 3];
+    for (int n = from; n < to; ++n) {
+        elevate(n, w, x, 3);
+        memcpy(w, x, sizeof(double) * 3 * (size_t)(n + 2));
     }
 }
 
 /* certified bound at degrees (eu, ev) = (max(pu,3), max(pv,3)):
  * Q elevated along u then v where its degree is below 3; R elevated along v
  * then u where the original degree is above 3. */
-static double surf_bound2(int pu, int pv, const net_t Q, double R[4][4][3])
+static double surf_bound2(int pu, int pv, const double* Q, const double* R)
 {
     int eu = pu > 3 ? pu : 3, ev = pv > 3 ? pv : 3;
-    double (*Qe)[SNP][3] = malloc(sizeof(net_t));
-    double (*Re)[SNP][3] = malloc(sizeof(net_t));
-    /* Q: along u for each column j <= pv */
+    double* Qe = (double*)malloc(sizeof(double) * NETN);
+    double* Re = (double*)malloc(sizeof(double) * NETN);
     for (int j = 0; j <= pv; ++j) {
-        double w[SNP][3], x[SNP][3];
+        double w[SNP * 3];
         for (int i = 0; i <= pu; ++i)
-            for (int c = 0; c < 3; ++c) w[i][c] = Q[i][j][c];
-        for (int n = pu; n < eu; ++n) { elevate(n, &w[0][0], &x[0][0], 3); memcpy(w, x, sizeof(w)); }
+            for (int c = 0; c < 3; ++c) w[3 * i + c] = Q[NETI(i, j) + c];
+        elevate_to(pu, eu, w);
         for (int i = 0; i <= eu; ++i)
-            for (int c = 0; c < 3; ++c) Qe[i][j][c] = w[i][c];
+            for (int c = 0; c < 3; ++c) Qe[NETI(i, j) + c] = w[3 * i + c];
     }
     for (int i = 0; i <= eu; ++i) {
-        double w[SNP][3], x[SNP][3];
+        double w[SNP * 3];
         for (int j = 0; j <= pv; ++j)
-            for (int c = 0; c < 3; ++c) w[j][c] = Qe[i][j][c];
-        for (int n = pv; n < ev; ++n) { elevate(n, &w[0][0], &x[0][0], 3); memcpy(w, x, sizeof(w)); }
+            for (int c = 0; c < 3; ++c) w[3 * j + c] = Qe[NETI(i, j) + c];
+        elevate_to(pv, ev, w);
         for (int j = 0; j <= ev; ++j)
-            for (int c = 0; c < 3; ++c) Qe[i][j][c] = w[j][c];
+            for (int c = 0; c < 3; ++c) Qe[NETI(i, j) + c] = w[3 * j + c];
     }
-    /* R: along v for each row i < 4, then along u for each column j <= ev */
     for (int i = 0; i < 4; ++i) {
-        double w[SNP][3], x[SNP][3];
+        double w[SNP * 3];
         for (int j = 0; j < 4; ++j)
-            for (int c = 0; c < 3; ++c) w[j][c] = R[i][j][c];
-        for (int n = 3; n < ev; ++n) { elevate(n, &w[0][0], &x[0][0], 3); memcpy(w, x, sizeof(w)); }
+            for (int c = 0; c < 3; ++c) w[3 * j + c] = R[(i * 4 + j) * 3 + c];
+        elevate_to(3, ev, w);
         for (int j = 0; j <= ev; ++j)
-            for (int c = 0; c < 3; ++c) Re[i][j][c] = w[j][c];
+            for (int c = 0; c < 3; ++c) Re[NETI(i, j) + c] = w[3 * j + c];
     }
     for (int j = 0; j <= ev; ++j) {
-        double w[SNP][3], x[SNP][3];
+        double w[SNP * 3];
         for (int i = 0; i < 4; ++i)
-            for (int c = 0; c < 3; ++c) w[i][c] = Re[i][j][c];
-        for (int n = 3; n < eu; ++n) { elevate(n, &w[0][0], &x[0][0], 3); memcpy(w, x, sizeof(w)); }
+            for (int c = 0; c < 3; ++c) w[3 * i + c] = Re[NETI(i, j) + c];
+        elevate_to(3, eu, w);
         for (int i = 0; i <= eu; ++i)
-            for (int c = 0; c < 3; ++c) Re[i][j][c] = w[i][c];
+            for (int c = 0; c < 3; ++c) Re[NETI(i, j) + c] = w[3 * i + c];
     }
     double b = 0.0;
     for (int i = 0; i <= eu; ++i)
         for (int j = 0; j <= ev; ++j) {
-            double dx = Qe[i][j][0] - Re[i][j][0], dy = Qe[i][j][1] - Re[i][j][1],
-                   dz = Qe[i][j][2] - Re[i][j][2];
+            const double* a = Qe + NETI(i, j);
+            const double* r = Re + NETI(i, j);
+            double dx = a[0] - r[0], dy = a[1] - r[1], dz = a[2] - r[2];
             double e = (dx * dx + dy * dy) + dz * dz;
             if (e > b) b = e;
         }
@@ -749,14 +787,14 @@ static int surf_split_dir(int pu, int pv, double du, double dv, int Lu, int Lv)
     return ldexp(du, -Lu) >= ldexp(dv, -Lv) ? 0 : 1;
 }
 
-static void surf_node(surf_ctx* X, const net_t Q, int Lu, int64_t ku, int Lv, int64_t kv)
+static void surf_node(surf_ctx* X, const double* Q, int Lu, int64_t ku, int Lv, int64_t kv)
 {
     int pu = X->pu, pv = X->pv;
-    double R[4][4][3];
+    double R[48];
     surf_to_bicubic(pu, pv, Q, R);
     int accept = 1;
     if (pu > 3 || pv > 3) accept = surf_bound2(pu, pv, Q, R) <= X->thr2;
-    if (!accept && Lu + Lv >= ODEPTH) { accept = 1; X->notconv = 1; }
+    if (!accept && (Lu + Lv >= ODEPTH || X->count - X->span_first >= OLEAFCAP)) { accept = 1; X->notconv = 1; }
     if (accept) {
         if (X->count < X->cap && X->ctrl) {
             memcpy(X->ctrl + 48 * X->count, R, sizeof(R));
@@ -771,28 +809,28 @@ static void surf_node(surf_ctx* X, const net_t Q, int Lu, int64_t ku, int Lv, in
         return;
     }
     int dir = surf_split_dir(pu, pv, X->u1 - X->u0, X->v1 - X->v0, Lu, Lv);
-    double (*A)[SNP][3] = malloc(sizeof(net_t));
-    double (*B)[SNP][3] = malloc(sizeof(net_t));
+    double* A = (double*)malloc(sizeof(double) * NETN);
+    double* B = (double*)malloc(sizeof(double) * NETN);
     if (dir == 0) {
         for (int j = 0; j <= pv; ++j) {
-            double col[SNP][3], l[SNP][3], r[SNP][3];
+            double col[SNP * 3], l[SNP * 3], r[SNP * 3];
             for (int i = 0; i <= pu; ++i)
-                for (int c = 0; c < 3; ++c) col[i][c] = Q[i][j][c];
-            halve(pu, &col[0][0], 3, &l[0][0], &r[0][0]);
+                for (int c = 0; c < 3; ++c) col[3 * i + c] = Q[NETI(i, j) + c];
+            halve(pu, col, 3, l, r);
             for (int i = 0; i <= pu; ++i)
-                for (int c = 0; c < 3; ++c) { A[i][j][c] = l[i][c]; B[i][j][c] = r[i][c]; }
+                for (int c = 0; c < 3; ++c) { A[NETI(i, j) + c] = l[3 * i + c]; B[NETI(i, j) + c] = r[3 * i + c]; }
         }
-        surf_node(X, (const double(*)[SNP][3])A, Lu + 1, 2 * ku, Lv, kv);
-        surf_node(X, (const double(*)[SNP][3])B, Lu + 1, 2 * ku + 1, Lv, kv);
+        surf_node(X, A, Lu + 1, 2 * ku, Lv, kv);
+        surf_node(X, B, Lu + 1, 2 * ku + 1, Lv, kv);
     } else {
         for (int i = 0; i <= pu; ++i) {
-            double l[SNP][3], r[SNP][3];
-            halve(pv, &Q[i][0][0], 3, &l[0][0], &r[0][0]);
+            double l[SNP * 3], r[SNP * 3];
+            halve(pv, Q + NETI(i, 0), 3, l, r);
             for (int j = 0; j <= pv; ++j)
-                for (int c = 0; c < 3; ++c) { A[i][j][c] = l[j][c]; B[i][j][c] = r[j][c]; }
+                for (int c = 0; c < 3; ++c) { A[NETI(i, j) + c] = l[3 * j + c]; B[NETI(i, j) + c] = r[3 * j + c]; }
         }
-        surf_node(X, (const double(*)[SNP][3])A, Lu, ku, Lv + 1, 2 * kv);
-        surf_node(X, (const double(*)[SNP][3])B, Lu, ku, Lv + 1, 2 * kv + 1);
+        surf_node(X, A, Lu, ku, Lv + 1, 2 * kv);
+        surf_node(X, B, Lu, ku, Lv + 1, 2 * kv + 1);
     }
     free(A); free(B);
 }
@@ -800,24 +838,61 @@ static void surf_node(surf_ctx* X, const net_t Q, int Lu, int64_t ku, int Lv, in
 /* Bezier net of span pair (qu, qv): the curve matrix route along u for every
  * v index of the local window, then along v for every u row. */
 static void surf_span_bezier(int pu, int pv, const double* U, int qu, const double* V, int qv,
-                             const double* P, int nv, net_t Q)
+                             const double* P, int nv, double* Q)
 {
-    double T1[SNP][SNP][3];
+    double* T1 = (double*)malloc(sizeof(double) * NETN);
     for (int b = 0; b <= pv; ++b) {
-        double loc[SNP][3], out[SNP][3];
+        double loc[SNP * 3], out[SNP * 3];
         for (int a = 0; a <= pu; ++a)
             for (int c = 0; c < 3; ++c)
-                loc[a][c] = P[3 * ((int64_t)(qu - pu + a) * nv + (qv - pv + b)) + c];
-        span_bezier(pu, U, qu, &loc[0][0], &out[0][0]);
+                loc[3 * a + c] = P[3 * ((int64_t)(qu - pu + a) * nv + (qv - pv + b)) + c];
+        span_bezier(pu, U, qu, loc, out);
         for (int a = 0; a <= pu; ++a)
-            for (int c = 0; c < 3; ++c) T1[a][b][c] = out[a][c];
+            for (int c = 0; c < 3; ++c) T1[NETI(a, b) + c] = out[3 * a + c];
     }
     for (int a = 0; a <= pu; ++a) {
-        double out[SNP][3];
-        span_bezier(pv, V, qv, &T1[a][0][0], &out[0][0]);
+        double out[SNP * 3];
+        span_bezier(pv, V, qv, T1 + NETI(a, 0), out);
         for (int b = 0; b <= pv; ++b)
-            for (int c = 0; c < 3; ++c) Q[a][b][c] = out[b][c];
+            for (int c = 0; c < 3; ++c) Q[NETI(a, b) + c] = out[3 * b + c];
     }
+    free(T1);
+}
+
+static int64_t decompose_one_surface(int64_t s, const int32_t* pu_, const int32_t* pv_, const int32_t* nu_,
+                                     const int32_t* nv_, const int64_t* kuoff, const double* ku,
+                                     const int64_t* kvoff, const double* kv, const int64_t* coff,
+                                     const double* cps, double tol_rel, int64_t first, int64_t cap,
+                                     double* ctrl, double* prange, int* maxdepth, int* notconv)
+{
+    int pu = pu_[s], pv = pv_[s], nu = nu_[s], nv = nv_[s];
+    if (pu > SMAXP || pv > SMAXP) return -1;
+    const double* U = ku + kuoff[s];
+    const double* V = kv + kvoff[s];
+    const double* P = cps + 3 * coff[s];
+    if (coff[s + 1] - coff[s] != (int64_t)nu * nv) return -1;
+    if (!check_knots(pu, U, kuoff[s + 1] - kuoff[s], nu)) return -1;
+    if (!check_knots(pv, V, kvoff[s + 1] - kvoff[s], nv)) return -1;
+    for (int64_t i = 0; i < 3 * (int64_t)nu * nv; ++i) if (!isfinite(P[i])) return -1;
+    double thr = tol_rel * box_diag(P, (int64_t)nu * nv);
+    surf_ctx X;
+    X.pu = pu; X.pv = pv; X.thr2 = thr * thr; X.cap = cap; X.ctrl = ctrl; X.prange = prange;
+    X.count = first; X.maxdepth = 0; X.notconv = 0;
+    double* Q = (double*)malloc(sizeof(double) * NETN);
+    for (int qu = pu; qu <= nu - 1; ++qu) {
+        if (!(U[qu] < U[qu + 1])) continue;
+        for (int qv = pv; qv <= nv - 1; ++qv) {
+            if (!(V[qv] < V[qv + 1])) continue;
+            surf_span_bezier(pu, pv, U, qu, V, qv, P, nv, Q);
+            X.u0 = U[qu]; X.u1 = U[qu + 1]; X.v0 = V[qv]; X.v1 = V[qv + 1];
+            X.span_first = X.count;
+            surf_node(&X, Q, 0, 0, 0, 0);
+        }
+    }
+    free(Q);
+    *maxdepth = X.maxdepth;
+    *notconv = X.notconv;
+    return X.count - first;
 }
 
 int orc_decompose_surfaces(int64_t n, const int32_t* pu_, const int32_t* pv_, const int32_t* nu_,
@@ -826,43 +901,34 @@ int orc_decompose_surfaces(int64_t n, const int32_t* pu_, const int32_t* pv_, co
                            const double* cps, double tol_rel, int64_t* seg_off, int64_t cap,
                            double* ctrl, double* prange, int64_t* total, int* maxdepth)
 {
-    int64_t cnt = 0;
-    int md = 0, nc = 0;
-    seg_off[0] = 0;
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int md = 0, nc = 0, bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(max : md) reduction(| : nc, bad)
     for (int64_t s = 0; s < n; ++s) {
-        int pu = pu_[s], pv = pv_[s], nu = nu_[s], nv = nv_[s];
-        if (pu > SMAXP || pv > SMAXP) return ORC_EINVAL;
-        const double* U = ku + kuoff[s];
-        const double* V = kv + kvoff[s];
-        const double* P = cps + 3 * coff[s];
-        if (coff[s + 1] - coff[s] != (int64_t)nu * nv) return ORC_EINVAL;
-        if (!check_knots(pu, U, kuoff[s + 1] - kuoff[s], nu)) return ORC_EINVAL;
-        if (!check_knots(pv, V, kvoff[s + 1] - kvoff[s], nv)) return ORC_EINVAL;
-        for (int64_t i = 0; i < 3 * (int64_t)nu * nv; ++i) if (!isfinite(P[i])) return ORC_EINVAL;
-        double thr = tol_rel * box_diag(P, (int64_t)nu * nv);
-        surf_ctx X;
-        X.pu = pu; X.pv = pv; X.thr2 = thr * thr; X.cap = cap; X.ctrl = ctrl; X.prange = prange;
-        X.count = cnt; X.maxdepth = 0; X.notconv = 0;
-        double (*Q)[SNP][3] = malloc(sizeof(net_t));
-        for (int qu = pu; qu <= nu - 1; ++qu) {
-            if (!(U[qu] < U[qu + 1])) continue;
-            for (int qv = pv; qv <= nv - 1; ++qv) {
-                if (!(V[qv] < V[qv + 1])) continue;
-                surf_span_bezier(pu, pv, U, qu, V, qv, P, nv, Q);
-                X.u0 = U[qu]; X.u1 = U[qu + 1]; X.v0 = V[qv]; X.v1 = V[qv + 1];
-                surf_node(&X, (const double(*)[SNP][3])Q, 0, 0, 0, 0);
-            }
-        }
-        free(Q);
-        cnt = X.count;
-        if (X.maxdepth > md) md = X.maxdepth;
-        nc |= X.notconv;
-        seg_off[s + 1] = cnt;
+        int m1 = 0, n1 = 0;
+        cnt[s] = decompose_one_surface(s, pu_, pv_, nu_, nv_, kuoff, ku, kvoff, kv, coff, cps, tol_rel, 0, 0,
+                                       NULL, NULL, &m1, &n1);
+        if (cnt[s] < 0) bad = 1;
+        if (m1 > md) md = m1;
+        nc |= n1;
     }
-    *total = cnt;
+    if (bad) { free(cnt); return ORC_EINVAL; }
+    seg_off[0] = 0;
+    for (int64_t s = 0; s < n; ++s) seg_off[s + 1] = seg_off[s] + cnt[s];
+    int64_t tot = seg_off[n];
+    if (ctrl && tot <= cap) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t s = 0; s < n; ++s) {
+            int m1, n1;
+            decompose_one_surface(s, pu_, pv_, nu_, nv_, kuoff, ku, kvoff, kv, coff, cps, tol_rel, seg_off[s], cap,
+                                  ctrl, prange, &m1, &n1);
+        }
+    }
+    free(cnt);
+    *total = tot;
     if (maxdepth) *maxdepth = md;
     if (nc) return ORC_ENOTCONV;
-    return cnt <= cap ? ORC_OK : ORC_ENOSPACE;
+    return tot <= cap ? ORC_OK : ORC_ENOSPACE;
 }
 
 /* ------------------------------------------------------------------ */

@@ -1,0 +1,326 @@
+"""Python binding of libbspl (include/bspl.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module maps torch tensors to
+the C structs and calls the ``extern "C"`` entry points with the same names.
+PyTorch provides device memory and the stream.  The module refuses to work
+without the compiled library: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbspl.so")
+
+OK, EINVAL, ENOSPACE, ECUDA, ENOTCONV, ETIMEOUT = 0, 1, 2, 3, 4, 5
+FP64, MIXED, LEARNED_MIXED = 0, 1, 2
+Q_CONVERGED, Q_FALLBACK, Q_AT_END, Q_NONCONV, Q_OFF_CURVE, Q_INVALID = 1, 2, 4, 8, 16, 32
+GROUP = 32
+CREC64, CREC32, SREC64, SREC32, GREC64, GREC32 = 18, 20, 54, 56, 12, 12
+SPAN_NET = 8 * 8 * 3
+OP_DECOMPOSE_CURVES, OP_DECOMPOSE_SURFACES, OP_QUERY_CURVES, OP_QUERY_SURFACES = 1, 2, 3, 4
+NCOUNTERS = 10
+COUNTER_NAMES = ["queries", "seg_tested", "grp_tested", "candidates", "newton", "fallback", "nonconv",
+                 "newton32_iters", "newton64_iters", "spare"]
+
+
+class BsplError(RuntimeError):
+    pass
+
+
+class bspl_curves(C.Structure):
+    _fields_ = [("n", C.c_int64), ("degree", C.c_void_p), ("knot_off", C.c_void_p), ("knots", C.c_void_p),
+                ("cp_off", C.c_void_p), ("cps", C.c_void_p)]
+
+
+class bspl_surfaces(C.Structure):
+    _fields_ = [("n", C.c_int64), ("deg_u", C.c_void_p), ("deg_v", C.c_void_p), ("n_u", C.c_void_p),
+                ("n_v", C.c_void_p), ("knot_u_off", C.c_void_p), ("knots_u", C.c_void_p),
+                ("knot_v_off", C.c_void_p), ("knots_v", C.c_void_p), ("cp_off", C.c_void_p), ("cps", C.c_void_p)]
+
+
+class bspl_segments(C.Structure):
+    _fields_ = [("is_surface", C.c_int32), ("n", C.c_int64), ("capacity", C.c_int64), ("grp_capacity", C.c_int64),
+                ("seg_off", C.c_void_p), ("ctrl", C.c_void_p), ("prange", C.c_void_p), ("diag", C.c_void_p),
+                ("rec64", C.c_void_p), ("rec32", C.c_void_p), ("grp_off", C.c_void_p), ("grp64", C.c_void_p),
+                ("grp32", C.c_void_p), ("patch_span", C.c_void_p), ("patch_box", C.c_void_p),
+                ("span_net", C.c_void_p), ("n_cp_total", C.c_int64), ("tol_rel", C.c_double)]
+
+
+class bspl_options(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("samples", C.c_int32), ("newton_max", C.c_int32), ("fp32_steps", C.c_int32),
+                ("sort_queries", C.c_int32), ("reserved", C.c_int32), ("mlp", C.c_void_p),
+                ("counters", C.c_void_p)]
+
+
+EXPORTS = ["bspl_measure_fma_peak", "bspl_workspace_bytes", "bspl_decompose", "bspl_project_curves", "bspl_invert_curves",
+           "bspl_project_surfaces", "bspl_invert_surfaces", "bspl_eval_curves", "bspl_eval_surfaces",
+           "bspl_status_string"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libbspl.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise BsplError(f"{LIB_PATH} is missing: build it with paper_2504_11498_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            vp, i64, st = C.c_void_p, C.c_int64, C.c_int
+            L.bspl_workspace_bytes.restype = C.c_size_t
+            L.bspl_workspace_bytes.argtypes = [C.c_int, i64, i64, i64, i64]
+            L.bspl_decompose.restype = st
+            L.bspl_decompose.argtypes = [C.c_int, vp, C.c_double, C.POINTER(bspl_segments), C.POINTER(i64), vp,
+                                         C.c_size_t, vp]
+            for name in ("bspl_project_curves", "bspl_invert_curves", "bspl_project_surfaces",
+                         "bspl_invert_surfaces"):
+                f = getattr(L, name)
+                f.restype = st
+                f.argtypes = [C.POINTER(bspl_segments), i64, vp, vp, C.POINTER(bspl_options), vp, vp, vp, vp,
+                              C.c_size_t, vp]
+            L.bspl_eval_curves.restype = st
+            L.bspl_eval_curves.argtypes = [C.POINTER(bspl_curves), i64, vp, vp, vp, vp]
+            L.bspl_eval_surfaces.restype = st
+            L.bspl_eval_surfaces.argtypes = [C.POINTER(bspl_surfaces), i64, vp, vp, vp, vp]
+            L.bspl_status_string.restype = C.c_char_p
+            L.bspl_status_string.argtypes = [st]
+            L.bspl_measure_fma_peak.restype = C.c_int
+            L.bspl_measure_fma_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, vp]
+            _lib = L
+    return _lib
+
+
+def _check(rc, what, allow=(OK,)):
+    if rc not in allow:
+        name = lib().bspl_status_string(rc).decode()
+        raise BsplError(f"{what} failed: {name} ({rc})")
+    return rc
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(x, dtype, device):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype).to(device)
+
+
+# ------------------------------------------------------------------ inputs
+
+class DeviceCurves:
+    """A CSR curve set (see synth.CurveSet) resident on the GPU."""
+
+    def __init__(self, cs, device="cuda"):
+        self.n = int(len(cs.degree))
+        self.degree = _dev(cs.degree, torch.int32, device)
+        self.knot_off = _dev(cs.knot_off, torch.int64, device)
+        self.knots = _dev(cs.knots, torch.float64, device)
+        self.cp_off = _dev(cs.cp_off, torch.int64, device)
+        self.cps = _dev(np.asarray(cs.cps).reshape(-1, 3), torch.float64, device)
+        self.n_cp_total = int(cs.cp_off[-1])
+        self.c = bspl_curves(self.n, _ptr(self.degree), _ptr(self.knot_off), _ptr(self.knots), _ptr(self.cp_off),
+                             _ptr(self.cps))
+
+
+class DeviceSurfaces:
+    """A CSR surface set (see synth.SurfaceSet) resident on the GPU."""
+
+    def __init__(self, ss, device="cuda"):
+        self.n = int(len(ss.deg_u))
+        self.deg_u = _dev(ss.deg_u, torch.int32, device)
+        self.deg_v = _dev(ss.deg_v, torch.int32, device)
+        self.n_u = _dev(ss.n_u, torch.int32, device)
+        self.n_v = _dev(ss.n_v, torch.int32, device)
+        self.knot_u_off = _dev(ss.knot_u_off, torch.int64, device)
+        self.knots_u = _dev(ss.knots_u, torch.float64, device)
+        self.knot_v_off = _dev(ss.knot_v_off, torch.int64, device)
+        self.knots_v = _dev(ss.knots_v, torch.float64, device)
+        self.cp_off = _dev(ss.cp_off, torch.int64, device)
+        self.cps = _dev(np.asarray(ss.cps).reshape(-1, 3), torch.float64, device)
+        self.n_cp_total = int(ss.cp_off[-1])
+        self.c = bspl_surfaces(self.n, _ptr(self.deg_u), _ptr(self.deg_v), _ptr(self.n_u), _ptr(self.n_v),
+                               _ptr(self.knot_u_off), _ptr(self.knots_u), _ptr(self.knot_v_off),
+                               _ptr(self.knots_v), _ptr(self.cp_off), _ptr(self.cps))
+
+
+# ------------------------------------------------------------ decomposition
+
+class Segments:
+    """Decomposition output + query tables (torch tensors owned here)."""
+
+    def __init__(self, splines, is_surface: bool, capacity: int, device="cuda"):
+        n = splines.n
+        self.is_surface = bool(is_surface)
+        self.n = n
+        self.capacity = int(capacity)
+        cap = max(self.capacity, 1)
+        self.grp_capacity = n + cap // GROUP + 1
+        f64, f32, i64 = torch.float64, torch.float32, torch.int64
+        z = lambda shape, dt: torch.zeros(shape, dtype=dt, device=device)
+        self.seg_off = z(n + 1, i64)
+        self.diag = z(n, f64)
+        self.grp_off = z(n + 1, i64)
+        if is_surface:
+            self.ctrl = z((cap, 4, 4, 3), f64)
+            self.prange = z((cap, 4), f64)
+            self.rec64 = z((cap, SREC64), f64)
+            self.rec32 = z((cap, SREC32), f32)
+            self.patch_span = z(cap, i64)
+            self.patch_box = z((cap, 4), f64)
+            self.span_net = z((splines.n_cp_total, SPAN_NET), f64)
+        else:
+            self.ctrl = z((cap, 4, 3), f64)
+            self.prange = z((cap, 2), f64)
+            self.rec64 = z((cap, CREC64), f64)
+            self.rec32 = z((cap, CREC32), f32)
+            self.patch_span = self.patch_box = self.span_net = None
+        self.grp64 = z((self.grp_capacity, GREC64), f64)
+        self.grp32 = z((self.grp_capacity, GREC32), f32)
+        self.n_cp_total = splines.n_cp_total
+        self.total = 0
+        self.tol_rel = 0.0
+        self.c = self._struct()
+
+    def _struct(self):
+        return bspl_segments(int(self.is_surface), self.n, self.capacity, self.grp_capacity, _ptr(self.seg_off),
+                             _ptr(self.ctrl), _ptr(self.prange), _ptr(self.diag), _ptr(self.rec64),
+                             _ptr(self.rec32), _ptr(self.grp_off), _ptr(self.grp64), _ptr(self.grp32),
+                             _ptr(self.patch_span), _ptr(self.patch_box), _ptr(self.span_net), self.n_cp_total,
+                             self.tol_rel)
+
+    def view(self):
+        """Host copies (seg_off, ctrl, prange) trimmed to the segment count."""
+        k = self.total
+        return self.seg_off.cpu().numpy(), self.ctrl[:k].cpu().numpy(), self.prange[:k].cpu().numpy()
+
+
+def workspace_bytes(op, n_splines, n_cp_total, n_seg, n_q):
+    return int(lib().bspl_workspace_bytes(op, n_splines, n_cp_total, n_seg, n_q))
+
+
+def _ws(nbytes, device="cuda"):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def bspl_decompose(is_surface, splines, tol_rel, seg_struct, ws, stream=None):
+    """Raw call: returns (status, n_seg_total)."""
+    tot = C.c_int64(0)
+    rc = lib().bspl_decompose(int(is_surface), C.byref(splines.c), float(tol_rel), C.byref(seg_struct),
+                              C.byref(tot), _ptr(ws), ws.numel(), _stream(stream))
+    return rc, tot.value
+
+
+def decompose(splines, tol_rel: float, is_surface: bool | None = None, stream=None) -> Segments:
+    """Two-phase decomposition: count, allocate, fill."""
+    if is_surface is None:
+        is_surface = isinstance(splines, DeviceSurfaces)
+    op = OP_DECOMPOSE_SURFACES if is_surface else OP_DECOMPOSE_CURVES
+    ws = _ws(workspace_bytes(op, splines.n, splines.n_cp_total, 0, 0), splines.cp_off.device)
+    probe = Segments(splines, is_surface, 0, splines.cp_off.device)
+    probe.c.ctrl = None
+    rc, total = bspl_decompose(is_surface, splines, tol_rel, probe.c, ws, stream)
+    _check(rc, "bspl_decompose(count)", (OK, ENOTCONV))
+    segs = Segments(splines, is_surface, total, splines.cp_off.device)
+    rc, total2 = bspl_decompose(is_surface, splines, tol_rel, segs.c, ws, stream)
+    _check(rc, "bspl_decompose(fill)", (OK, ENOTCONV))
+    assert total2 == total
+    segs.total = total
+    segs.tol_rel = float(tol_rel)
+    segs.status = rc
+    segs.c = segs._struct()
+    return segs
+
+
+# ----------------------------------------------------------------- queries
+
+@dataclass
+class QueryResult:
+    param: torch.Tensor  # t [n] (curves) or uv [n][2] (surfaces)
+    dist: torch.Tensor
+    status: torch.Tensor
+
+
+def make_options(prec=FP64, samples=0, newton_max=0, fp32_steps=0, sort_queries=1, counters=None, mlp=None):
+    return bspl_options(int(prec), int(samples), int(newton_max), int(fp32_steps), int(sort_queries), 0,
+                        C.c_void_p(mlp) if mlp else C.c_void_p(0), _ptr(counters) if counters is not None else None)
+
+
+class QueryBuffers:
+    """Preallocated outputs + workspace for repeated query calls."""
+
+    def __init__(self, segs: Segments, n_q: int, device="cuda"):
+        self.n_q = int(n_q)
+        shape = (n_q, 2) if segs.is_surface else (n_q,)
+        self.param = torch.empty(shape, dtype=torch.float64, device=device)
+        self.dist = torch.empty(n_q, dtype=torch.float64, device=device)
+        self.status = torch.empty(n_q, dtype=torch.uint8, device=device)
+        op = OP_QUERY_SURFACES if segs.is_surface else OP_QUERY_CURVES
+        self.ws = _ws(workspace_bytes(op, segs.n, segs.n_cp_total, segs.total, n_q), device)
+
+
+def _query(fn_name, segs, q_idx, q_xyz, opts, bufs, stream):
+    L = lib()
+    fn = getattr(L, fn_name)
+    rc = fn(C.byref(segs.c), int(q_idx.numel()), _ptr(q_idx), _ptr(q_xyz), C.byref(opts), _ptr(bufs.param),
+            _ptr(bufs.dist), _ptr(bufs.status), _ptr(bufs.ws), bufs.ws.numel(), _stream(stream))
+    _check(rc, fn_name)
+    return QueryResult(bufs.param, bufs.dist, bufs.status)
+
+
+def bspl_project_curves(segs, q_curve, q_xyz, opts=None, bufs=None, stream=None):
+    bufs = bufs or QueryBuffers(segs, q_curve.numel(), q_xyz.device)
+    return _query("bspl_project_curves", segs, q_curve, q_xyz, opts or make_options(), bufs, stream)
+
+
+def bspl_invert_curves(segs, q_curve, q_xyz, opts=None, bufs=None, stream=None):
+    bufs = bufs or QueryBuffers(segs, q_curve.numel(), q_xyz.device)
+    return _query("bspl_invert_curves", segs, q_curve, q_xyz, opts or make_options(), bufs, stream)
+
+
+def bspl_project_surfaces(segs, q_surf, q_xyz, opts=None, bufs=None, stream=None):
+    bufs = bufs or QueryBuffers(segs, q_surf.numel(), q_xyz.device)
+    return _query("bspl_project_surfaces", segs, q_surf, q_xyz, opts or make_options(), bufs, stream)
+
+
+def bspl_invert_surfaces(segs, q_surf, q_xyz, opts=None, bufs=None, stream=None):
+    bufs = bufs or QueryBuffers(segs, q_surf.numel(), q_xyz.device)
+    return _query("bspl_invert_surfaces", segs, q_surf, q_xyz, opts or make_options(), bufs, stream)
+
+
+def bspl_eval_curves(curves: DeviceCurves, q_curve, t, stream=None):
+    out = torch.empty((q_curve.numel(), 3), dtype=torch.float64, device=t.device)
+    rc = lib().bspl_eval_curves(C.byref(curves.c), q_curve.numel(), _ptr(q_curve), _ptr(t), _ptr(out),
+                                _stream(stream))
+    _check(rc, "bspl_eval_curves")
+    return out
+
+
+def bspl_eval_surfaces(surfs: DeviceSurfaces, q_surf, uv, stream=None):
+    out = torch.empty((q_surf.numel(), 3), dtype=torch.float64, device=uv.device)
+    rc = lib().bspl_eval_surfaces(C.byref(surfs.c), q_surf.numel(), _ptr(q_surf), _ptr(uv), _ptr(out),
+                                  _stream(stream))
+    _check(rc, "bspl_eval_surfaces")
+    return out
+
+
+def measure_fma_peak(fp64: bool, iters: int = 4096, reps: int = 5, stream=None) -> float:
+    """FP32 or FP64 FMA-chain throughput of the current GPU in FLOP/s."""
+    sink = torch.zeros(2, dtype=torch.float64, device="cuda")
+    out = C.c_double(0.0)
+    rc = lib().bspl_measure_fma_peak(int(fp64), int(iters), int(reps), C.byref(out), _ptr(sink), _stream(stream))
+    _check(rc, "bspl_measure_fma_peak")
+    return out.value

@@ -1,0 +1,970 @@
+// Error-controlled decomposition of B-spline curves and surfaces into cubic
+// Bezier segments and bicubic patches (Sec. 4.2.1 and 4.2.2), in FP64.
+//
+// This translation unit is compiled with -fmad=false: every decision of the
+// subdivision (accept a reduced piece, or split it) is made from plain IEEE
+// FP64 additions, multiplications, divisions and square roots in a fixed
+// order, so that the segment counts are reproducible bit for bit.
+//
+// Work decomposition: one thread per knot span (span pair for surfaces).  A
+// span's subdivision tree is walked depth first without a stack of control
+// nets: a node is identified by its depth and its path bits, and its degree-p
+// piece is rebuilt from the span's Bezier piece by replaying the de Casteljau
+// halvings along the path (the same halvings, in the same order, as a
+// recursive walk would perform).  The walk runs twice: a counting pass, a
+// prefix sum over spans, and a filling pass that writes each leaf at its
+// offset.
+#include <math.h>
+
+#include "bspl_internal.cuh"
+
+namespace bspl {
+
+namespace {
+
+// ------------------------------------------------------------------ helpers
+
+// IEEE FP64 operations with round-to-nearest and no contraction: on the
+// device the _rn intrinsics, which are never merged into multiply-adds; on
+// the host the plain operators (the host build has no contraction).
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ double fadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double fsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double fmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double fsqrt(double a) { return __dsqrt_rn(a); }
+#else
+inline double fadd(double a, double b) { return a + b; }
+inline double fsub(double a, double b) { return a - b; }
+inline double fmul(double a, double b) { return a * b; }
+inline double fdiv(double a, double b) { return a / b; }
+inline double fsqrt(double a) { return sqrt(a); }
+#endif
+
+__host__ __device__ double binom_d(int n, int k)
+{
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = fdiv(fmul(r, (double)(n - k + i)), (double)i);
+    return r;
+}
+
+// g_ij = int_0^1 B_i^m B_j^n (Eq. gram)
+__host__ __device__ double gram_d(int m, int n, int i, int j)
+{
+    double num = fmul(binom_d(m, i), binom_d(n, j));
+    double den = fmul((double)(m + n + 1), binom_d(m + n, i + j));
+    return fdiv(num, den);
+}
+
+// Bezier piece of knot span q from the p+1 control points starting at
+// P_{q-p} (stride 3*pstride doubles between points): local power basis of
+// N_{q-p..q,p} in u = (t - t_q)/(t_{q+1} - t_q) by the Cox-de Boor recursion
+// on polynomials (the product M_{q,p,T} A_{q,p,T}), coefficients c = (M A) P,
+// Bezier points Q = B_p^{-1} c with (B_p^{-1})_{ij} = C(i,j)/C(p,j).
+template <int MP>
+__host__ __device__ void span_bezier(int p, const double* __restrict__ U, int q, const double* __restrict__ Pl,
+                                     int64_t pstride, double* Q)
+{
+    double poly[MP + 1][MP + 1], nw[MP + 1][MP + 1];
+    double du = fsub(U[q + 1], U[q]);
+    poly[0][0] = 1.0;
+    for (int k = 1; k <= p; ++k) {
+        for (int j = 0; j <= k; ++j) {
+            int i = q - k + j;
+            for (int e = 0; e <= k; ++e) nw[j][e] = 0.0;
+            if (j >= 1) {
+                double den = fsub(U[i + k], U[i]);
+                if (den != 0.0) {
+                    double a = fdiv(fsub(U[q], U[i]), den), b = fdiv(du, den);
+                    for (int e = 0; e <= k - 1; ++e) {
+                        nw[j][e] = fadd(nw[j][e], fmul(a, poly[j - 1][e]));
+                        nw[j][e + 1] = fadd(nw[j][e + 1], fmul(b, poly[j - 1][e]));
+                    }
+                }
+            }
+            if (j <= k - 1) {
+                double den = fsub(U[i + k + 1], U[i + 1]);
+                if (den != 0.0) {
+                    double a = fdiv(fsub(U[i + k + 1], U[q]), den), b = fdiv(-du, den);
+                    for (int e = 0; e <= k - 1; ++e) {
+                        nw[j][e] = fadd(nw[j][e], fmul(a, poly[j][e]));
+                        nw[j][e + 1] = fadd(nw[j][e + 1], fmul(b, poly[j][e]));
+                    }
+                }
+            }
+        }
+        for (int j = 0; j <= k; ++j)
+            for (int e = 0; e <= k; ++e) poly[j][e] = nw[j][e];
+    }
+    double cc[MP + 1][3];
+    for (int e = 0; e <= p; ++e)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int j = 0; j <= p; ++j) s = fadd(s, fmul(poly[j][e], Pl[3 * pstride * j + c]));
+            cc[e][c] = s;
+        }
+    for (int i = 0; i <= p; ++i)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int e = 0; e <= i; ++e) s = fadd(s, fmul(fdiv(binom_d(i, e), binom_d(p, e)), cc[e][c]));
+            Q[3 * i + c] = s;
+        }
+}
+
+// degree n -> n+1 (exact degree elevation); Q and E indexed with stride s (points)
+__host__ __device__ void elevate(int n, const double* Q, double* E, int s)
+{
+    for (int c = 0; c < 3; ++c) {
+        E[c] = Q[c];
+        E[(n + 1) * s + c] = Q[n * s + c];
+    }
+    for (int i = 1; i <= n; ++i) {
+        double a = fdiv((double)i, (double)(n + 1));
+        double b = fdiv((double)(n + 1 - i), (double)(n + 1));
+        for (int c = 0; c < 3; ++c) E[i * s + c] = fadd(fmul(a, Q[(i - 1) * s + c]), fmul(b, Q[i * s + c]));
+    }
+}
+
+// G1-continuous L2-optimal reduction p > 3 -> 3 (Eqs. G1-condition, epsl,
+// differentiatedelta0/1).  The 2x2 normal equations are the ones obtained
+// from eps: delta0 (A0.d0) + delta1 (A1.d0) = V1.d0 and
+// delta0 (B0.d1) + delta1 (B1.d1) = V2.d1, A0 = a g11 d0, A1 = -a g12 d1,
+// B0 = a g21 d0, B1 = -a g22 d1, a = p/3; degenerate systems fall back to
+// delta0 = delta1 = 1.
+__host__ __device__ void reduce_g1(int p, const double* Q, int s, double* R, int rs)
+{
+    const double* Q0 = Q;
+    const double* Q1 = Q + s;
+    const double* Qm = Q + (p - 1) * s;
+    const double* Qp = Q + p * s;
+    double a = fdiv((double)p, 3.0);
+    double g11 = gram_d(3, 3, 1, 1), g12 = gram_d(3, 3, 1, 2);
+    double g21 = gram_d(3, 3, 2, 1), g22 = gram_d(3, 3, 2, 2);
+    double g10 = gram_d(3, 3, 1, 0), g13 = gram_d(3, 3, 1, 3);
+    double g20 = gram_d(3, 3, 2, 0), g23 = gram_d(3, 3, 2, 3);
+    double d0[3], d1[3], V1[3], V2[3];
+    for (int c = 0; c < 3; ++c) {
+        d0[c] = fsub(Q1[c], Q0[c]);
+        d1[c] = fsub(Qp[c], Qm[c]);
+        double s1 = 0.0, s2 = 0.0;
+        for (int j = 0; j <= p; ++j) {
+            s1 = fadd(s1, fmul(gram_d(3, p, 1, j), Q[j * s + c]));
+            s2 = fadd(s2, fmul(gram_d(3, p, 2, j), Q[j * s + c]));
+        }
+        double t1 = fadd(fadd(fadd(fmul(g10, Q0[c]), fmul(g11, Q0[c])), fmul(g12, Qp[c])), fmul(g13, Qp[c]));
+        double t2 = fadd(fadd(fadd(fmul(g20, Q0[c]), fmul(g21, Q0[c])), fmul(g22, Qp[c])), fmul(g23, Qp[c]));
+        V1[c] = fsub(s1, t1);
+        V2[c] = fsub(s2, t2);
+    }
+    double A0[3], A1[3], B0[3], B1[3];
+    for (int c = 0; c < 3; ++c) {
+        A0[c] = fmul(fmul(a, g11), d0[c]);
+        A1[c] = fmul(fmul(-a, g12), d1[c]);
+        B0[c] = fmul(fmul(a, g21), d0[c]);
+        B1[c] = fmul(fmul(-a, g22), d1[c]);
+    }
+    double a11 = fadd(fadd(fmul(A0[0], d0[0]), fmul(A0[1], d0[1])), fmul(A0[2], d0[2]));
+    double a12 = fadd(fadd(fmul(A1[0], d0[0]), fmul(A1[1], d0[1])), fmul(A1[2], d0[2]));
+    double b1 = fadd(fadd(fmul(V1[0], d0[0]), fmul(V1[1], d0[1])), fmul(V1[2], d0[2]));
+    double a21 = fadd(fadd(fmul(B0[0], d1[0]), fmul(B0[1], d1[1])), fmul(B0[2], d1[2]));
+    double a22 = fadd(fadd(fmul(B1[0], d1[0]), fmul(B1[1], d1[1])), fmul(B1[2], d1[2]));
+    double b2 = fadd(fadd(fmul(V2[0], d1[0]), fmul(V2[1], d1[1])), fmul(V2[2], d1[2]));
+    double det = fsub(fmul(a11, a22), fmul(a12, a21));
+    double dl0 = fdiv(fsub(fmul(b1, a22), fmul(a12, b2)), det);
+    double dl1 = fdiv(fsub(fmul(a11, b2), fmul(b1, a21)), det);
+    bool ok = (det != 0.0) && (fabs(det) > fmul(1e-12, fabs(fmul(a11, a22)))) && isfinite(dl0) && isfinite(dl1) &&
+              dl0 > 0.0 && dl1 > 0.0;
+    if (!ok) {
+        dl0 = 1.0;
+        dl1 = 1.0;
+    }
+    double s0 = fmul(a, dl0), s1 = fmul(a, dl1);
+    for (int c = 0; c < 3; ++c) {
+        R[c] = Q0[c];
+        R[rs + c] = fadd(Q0[c], fmul(s0, d0[c]));
+        R[2 * rs + c] = fsub(Qp[c], fmul(s1, d1[c]));
+        R[3 * rs + c] = Qp[c];
+    }
+}
+
+__host__ __device__ void to_cubic(int p, const double* Q, int s, double* R, int rs)
+{
+    if (p == 3) {
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 3; ++c) R[i * rs + c] = Q[i * s + c];
+    } else if (p > 3) {
+        reduce_g1(p, Q, s, R, rs);
+    } else {
+        double w[12], x[12];
+        for (int i = 0; i <= p; ++i)
+            for (int c = 0; c < 3; ++c) w[3 * i + c] = Q[i * s + c];
+        for (int n = p; n < 3; ++n) {
+            elevate(n, w, x, 3);
+            for (int i = 0; i <= n + 1; ++i)
+                for (int c = 0; c < 3; ++c) w[3 * i + c] = x[3 * i + c];
+        }
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 3; ++c) R[i * rs + c] = w[3 * i + c];
+    }
+}
+
+// max_i |Q_i - (R elevated to p)_i|^2 (certified deviation bound)
+template <int MP>
+__host__ __device__ double bound2_curve(int p, const double* Q, int s, const double* R, int rs)
+{
+    double w[(MP + 1) * 3], x[(MP + 1) * 3];
+    for (int i = 0; i < 4; ++i)
+        for (int c = 0; c < 3; ++c) w[3 * i + c] = R[i * rs + c];
+    for (int n = 3; n < p; ++n) {
+        elevate(n, w, x, 3);
+        for (int i = 0; i <= n + 1; ++i)
+            for (int c = 0; c < 3; ++c) w[3 * i + c] = x[3 * i + c];
+    }
+    double b = 0.0;
+    for (int i = 0; i <= p; ++i) {
+        double dx = fsub(Q[i * s + 0], w[3 * i]), dy = fsub(Q[i * s + 1], w[3 * i + 1]),
+               dz = fsub(Q[i * s + 2], w[3 * i + 2]);
+        double e = fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz));
+        if (e > b) b = e;
+    }
+    return b;
+}
+
+// de Casteljau halving at 1/2; keeps the left (side = 0) or right (side = 1)
+// half in place.  Identical arithmetic to computing both halves at once.
+template <int MP>
+__host__ __device__ void halve_keep(int p, double* Q, int s, int side)
+{
+    double w[(MP + 1) * 3], keep[(MP + 1) * 3];
+    for (int i = 0; i <= p; ++i)
+        for (int c = 0; c < 3; ++c) w[3 * i + c] = Q[i * s + c];
+    for (int c = 0; c < 3; ++c) {
+        if (side == 0) keep[c] = w[c];
+        else keep[3 * p + c] = w[3 * p + c];
+    }
+    for (int r = 1; r <= p; ++r) {
+        for (int i = 0; i <= p - r; ++i)
+            for (int c = 0; c < 3; ++c) w[3 * i + c] = fmul(fadd(w[3 * i + c], w[3 * (i + 1) + c]), 0.5);
+        for (int c = 0; c < 3; ++c) {
+            if (side == 0) keep[3 * r + c] = w[c];
+            else keep[3 * (p - r) + c] = w[3 * (p - r) + c];
+        }
+    }
+    for (int i = 0; i <= p; ++i)
+        for (int c = 0; c < 3; ++c) Q[i * s + c] = keep[3 * i + c];
+}
+
+__host__ __device__ double dyadic_t(double tq, double tq1, int64_t k, int L)
+{
+    if (k == 0) return tq;
+    if (k == ((int64_t)1 << L)) return tq1;
+    return fadd(tq, fmul(fsub(tq1, tq), ldexp((double)k, -L)));
+}
+
+__host__ __device__ int find_le(const int64_t* __restrict__ off, int64_t n, int64_t x)
+{
+    // largest i in [0, n) with off[i] <= x
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return (int)lo;
+}
+
+// ------------------------------------------------------------- validation
+
+struct DecWS {
+    int* err;       // [1] bit 0: invalid data, bit 1: not converged
+    int* maxdeg;    // [1]
+    int64_t* cnt;   // [n_slots] leaves per slot, then exclusive offsets
+    int64_t* gcnt;  // [n+1] groups per spline, then offsets
+    int64_t* tmp;   // scan temporaries
+};
+
+__host__ __device__ bool knots_ok(int p, const double* U, int64_t nU, int64_t nP)
+{
+    if (p < 1 || nP < p + 1 || nU != nP + p + 1) return false;
+    for (int64_t i = 0; i < nU; ++i) {
+        if (!isfinite(U[i])) return false;
+        if (i > 0 && U[i] < U[i - 1]) return false;
+    }
+    return U[p] < U[nP];
+}
+
+__host__ __device__ double box_diag_d(const double* P, int64_t np)
+{
+    double lo[3] = { INFINITY, INFINITY, INFINITY }, hi[3] = { -INFINITY, -INFINITY, -INFINITY };
+    for (int64_t i = 0; i < np; ++i)
+        for (int c = 0; c < 3; ++c) {
+            double v = P[3 * i + c];
+            if (v < lo[c]) lo[c] = v;
+            if (v > hi[c]) hi[c] = v;
+        }
+    double dx = fsub(hi[0], lo[0]), dy = fsub(hi[1], lo[1]), dz = fsub(hi[2], lo[2]);
+    return fsqrt(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
+}
+
+__global__ void k_validate_curves(bspl_curves C, int64_t n_cp, double* diag, int* err, int* maxdeg)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C.n) return;
+    if (c == 0 && C.cp_off[C.n] != n_cp) atomicOr(err, 1);
+    int p = C.degree[c];
+    int64_t nP = C.cp_off[c + 1] - C.cp_off[c], nU = C.knot_off[c + 1] - C.knot_off[c];
+    bool ok = p >= 1 && p <= kMaxCurveDegree && knots_ok(p, C.knots + C.knot_off[c], nU, nP);
+    const double* P = C.cps + 3 * C.cp_off[c];
+    if (ok)
+        for (int64_t i = 0; i < 3 * nP; ++i)
+            if (!isfinite(P[i])) { ok = false; break; }
+    diag[c] = ok ? box_diag_d(P, nP) : __longlong_as_double(0x7ff8000000000000LL);
+    if (!ok) atomicOr(err, 1);
+    else atomicMax(maxdeg, p);
+}
+
+__global__ void k_validate_surfaces(bspl_surfaces S, int64_t n_cp, double* diag, int* err, int* maxdeg)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S.n) return;
+    if (s == 0 && S.cp_off[S.n] != n_cp) atomicOr(err, 1);
+    int pu = S.deg_u[s], pv = S.deg_v[s], nu = S.n_u[s], nv = S.n_v[s];
+    int64_t np = S.cp_off[s + 1] - S.cp_off[s];
+    bool ok = pu >= 1 && pv >= 1 && pu <= kMaxSurfDegree && pv <= kMaxSurfDegree && nu > 0 && nv > 0 &&
+              np == (int64_t)nu * nv &&
+              knots_ok(pu, S.knots_u + S.knot_u_off[s], S.knot_u_off[s + 1] - S.knot_u_off[s], nu) &&
+              knots_ok(pv, S.knots_v + S.knot_v_off[s], S.knot_v_off[s + 1] - S.knot_v_off[s], nv);
+    const double* P = S.cps + 3 * S.cp_off[s];
+    if (ok)
+        for (int64_t i = 0; i < 3 * np; ++i)
+            if (!isfinite(P[i])) { ok = false; break; }
+    diag[s] = ok ? box_diag_d(P, np) : __longlong_as_double(0x7ff8000000000000LL);
+    if (!ok) atomicOr(err, 1);
+    else atomicMax(maxdeg, pu > pv ? pu : pv);
+}
+
+// ------------------------------------------------------------------ curves
+
+struct CurveLeafOut {
+    double* ctrl;
+    double* prange;
+};
+
+// Walks the subdivision tree of one span.  FILL = false counts leaves;
+// FILL = true writes them from index `first`.
+__host__ __device__ inline void set_flag(int* err, int bit)
+{
+#ifdef __CUDA_ARCH__
+    atomicOr(err, bit);
+#else
+    *err |= bit;
+#endif
+}
+
+template <int MP, bool FILL>
+__host__ __device__ int64_t walk_span_curve(int p, const double* __restrict__ U, int q, const double* __restrict__ Pl,
+                                   double thr2, int64_t first, CurveLeafOut out, int* err)
+{
+    double root[(MP + 1) * 3], Q[(MP + 1) * 3];
+    span_bezier<MP>(p, U, q, Pl, 1, root);
+    int L = 0;
+    int64_t k = 0, count = 0;
+    for (;;) {
+        for (int i = 0; i < 3 * (p + 1); ++i) Q[i] = root[i];
+        for (int l = 0; l < L; ++l) halve_keep<MP>(p, Q, 3, (int)((k >> (L - 1 - l)) & 1));
+        double R[12];
+        to_cubic(p, Q, 3, R, 3);
+        bool accept = true;
+        if (p > 3) accept = bound2_curve<MP>(p, Q, 3, R, 3) <= thr2;
+        if (!accept && (L >= kDepthCap || count >= kLeafCap)) {
+            accept = true;
+            set_flag(err, 2);
+        }
+        if (accept) {
+            if (FILL) {
+                int64_t o = first + count;
+                double* dst = out.ctrl + 12 * o;
+                for (int i = 0; i < 12; ++i) dst[i] = R[i];
+                out.prange[2 * o] = dyadic_t(U[q], U[q + 1], k, L);
+                out.prange[2 * o + 1] = dyadic_t(U[q], U[q + 1], k + 1, L);
+            }
+            ++count;
+            while (L > 0 && (k & 1)) {
+                k >>= 1;
+                --L;
+            }
+            if (L == 0) break;
+            k += 1;
+        } else {
+            ++L;
+            k <<= 1;
+        }
+    }
+    return count;
+}
+
+// slot = cp_off[c] + (q - p), q in [p, ncp-1]
+template <int MP, bool FILL>
+__global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, double tol_rel, int64_t n_slots,
+                              int64_t* __restrict__ cnt, CurveLeafOut out, int* err)
+{
+    int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= n_slots) return;
+    int c = find_le(C.cp_off, C.n, slot);
+    int p = C.degree[c];
+    // this instance handles degrees (MP/2, MP] (1..7, 8..15, 16..31); invalid
+    // curves carry a NaN diagonal and are skipped
+    constexpr int lo = MP == 7 ? 1 : (MP + 1) / 2;
+    if (p < lo || p > MP || !(diag[c] >= 0.0)) return;
+    int64_t nP = C.cp_off[c + 1] - C.cp_off[c];
+    int q = p + (int)(slot - C.cp_off[c]);
+    const double* U = C.knots + C.knot_off[c];
+    int64_t r = 0;
+    if (q <= nP - 1 && U[q] < U[q + 1]) {
+        double thr = fmul(tol_rel, diag[c]);
+        r = walk_span_curve<MP, FILL>(p, U, q, C.cps + 3 * (C.cp_off[c] + q - p), fmul(thr, thr),
+                                      FILL ? cnt[slot] : 0, out, err);
+    }
+    if (!FILL) cnt[slot] = r;
+}
+
+// ---------------------------------------------------------------- surfaces
+
+// a net of (degree + 1) x (degree + 1) points, flat: point (a, b) at (a * kSN + b) * 3
+constexpr int kSN = kMaxSurfDegree + 1;
+
+// reduce along u for every v column, then along v for every u row
+__host__ __device__ void surf_to_bicubic(int pu, int pv, const double* Q, double* R /* [4*4*3] */)
+{
+    double Rp[4 * kSN * 3];
+    for (int j = 0; j <= pv; ++j) {
+        double col[kSN * 3], r[12];
+        for (int i = 0; i <= pu; ++i)
+            for (int c = 0; c < 3; ++c) col[3 * i + c] = Q[(i * kSN + j) * 3 + c];
+        to_cubic(pu, col, 3, r, 3);
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 3; ++c) Rp[(i * kSN + j) * 3 + c] = r[3 * i + c];
+    }
+    for (int i = 0; i < 4; ++i) {
+        double r[12];
+        to_cubic(pv, Rp + i * kSN * 3, 3, r, 3);
+        for (int j = 0; j < 4; ++j)
+            for (int c = 0; c < 3; ++c) R[(i * 4 + j) * 3 + c] = r[3 * j + c];
+    }
+}
+
+__host__ __device__ void elevate_to(int from, int to, double* w /* [kSN*3] */)
+{
+    double x[kSN * 3];
+    for (int n = from; n < to; ++n) {
+        elevate(n, w, x, 3);
+        for (int i = 0; i <= n + 1; ++i)
+            for (int c = 0; c < 3; ++c) w[3 * i + c] = x[3 * i + c];
+    }
+}
+
+// certified bound at degrees (max(pu,3), max(pv,3)): Q elevated along u then
+// v, R elevated along v then u
+__host__ __device__ double surf_bound2(int pu, int pv, const double* Q, const double* R)
+{
+    int eu = pu > 3 ? pu : 3, ev = pv > 3 ? pv : 3;
+    double Qe[kSN * kSN * 3], Re[kSN * kSN * 3];
+    for (int j = 0; j <= pv; ++j) {
+        double w[kSN * 3];
+        for (int i = 0; i <= pu; ++i)
+            for (int c = 0; c < 3; ++c) w[3 * i + c] = Q[(i * kSN + j) * 3 + c];
+        elevate_to(pu, eu, w);
+        for (int i = 0; i <= eu; ++i)
+            for (int c = 0; c < 3; ++c) Qe[(i * kSN + j) * 3 + c] = w[3 * i + c];
+    }
+    for (int i = 0; i <= eu; ++i) {
+        double w[kSN * 3];
+        for (int j = 0; j <= pv; ++j)
+            for (int c = 0; c < 3; ++c) w[3 * j + c] = Qe[(i * kSN + j) * 3 + c];
+        elevate_to(pv, ev, w);
+        for (int j = 0; j <= ev; ++j)
+            for (int c = 0; c < 3; ++c) Qe[(i * kSN + j) * 3 + c] = w[3 * j + c];
+    }
+    for (int i = 0; i < 4; ++i) {
+        double w[kSN * 3];
+        for (int j = 0; j < 4; ++j)
+            for (int c = 0; c < 3; ++c) w[3 * j + c] = R[(i * 4 + j) * 3 + c];
+        elevate_to(3, ev, w);
+        for (int j = 0; j <= ev; ++j)
+            for (int c = 0; c < 3; ++c) Re[(i * kSN + j) * 3 + c] = w[3 * j + c];
+    }
+    for (int j = 0; j <= ev; ++j) {
+        double w[kSN * 3];
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 3; ++c) w[3 * i + c] = Re[(i * kSN + j) * 3 + c];
+        elevate_to(3, eu, w);
+        for (int i = 0; i <= eu; ++i)
+            for (int c = 0; c < 3; ++c) Re[(i * kSN + j) * 3 + c] = w[3 * i + c];
+    }
+    double b = 0.0;
+    for (int i = 0; i <= eu; ++i)
+        for (int j = 0; j <= ev; ++j) {
+            const double* a = Qe + (i * kSN + j) * 3;
+            const double* r = Re + (i * kSN + j) * 3;
+            double dx = fsub(a[0], r[0]), dy = fsub(a[1], r[1]), dz = fsub(a[2], r[2]);
+            double e = fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz));
+            if (e > b) b = e;
+        }
+    return b;
+}
+
+// split direction: the reduced direction when only one is reduced, else the
+// longer parameter side (ties -> u)
+__host__ __device__ int surf_split_dir(int pu, int pv, double du, double dv, int Lu, int Lv)
+{
+    if (pu > 3 && pv <= 3) return 0;
+    if (pv > 3 && pu <= 3) return 1;
+    return ldexp(du, -Lu) >= ldexp(dv, -Lv) ? 0 : 1;
+}
+
+__host__ __device__ void surf_halve_keep(int pu, int pv, double* Q, int dir, int side)
+{
+    if (dir == 0) {
+        for (int j = 0; j <= pv; ++j) halve_keep<kMaxSurfDegree>(pu, Q + 3 * j, 3 * kSN, side);
+    } else {
+        for (int i = 0; i <= pu; ++i) halve_keep<kMaxSurfDegree>(pv, Q + 3 * kSN * i, 3, side);
+    }
+}
+
+// Bernstein -> power coefficients of a degree-n piece in place (stride s doubles)
+__host__ __device__ void bern_to_power(int n, double* Q, int s)
+{
+    double a[kSN * 3];
+    for (int k = 0; k <= n; ++k)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0.0;
+            for (int j = 0; j <= k; ++j) {
+                double m = binom_d(n, j) * binom_d(n - j, k - j);
+                if ((k - j) & 1) m = -m;
+                acc += m * Q[j * s + c];
+            }
+            a[3 * k + c] = acc;
+        }
+    for (int k = 0; k <= n; ++k)
+        for (int c = 0; c < 3; ++c) Q[k * s + c] = a[3 * k + c];
+}
+
+struct SurfLeafOut {
+    double* ctrl;
+    double* prange;
+    int64_t* patch_span;
+    double* patch_box;
+    double* rec64;     // box of the ORIGINAL piece is written here (first 6 entries)
+    float* rec32;      // the degrees (pu, pv) go to the two pad entries
+    double* span_net;  // original span-pair piece, power basis [8][8][3]
+};
+
+template <bool FILL>
+__host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, int qu, const double* V, int qv,
+                                     const double* P, int nv, double thr2, int64_t slot, int64_t first,
+                                     SurfLeafOut out, int* err)
+{
+    double root[kSN * kSN * 3], Q[kSN * kSN * 3];
+    {
+        // along u for every v index of the local window, then along v
+        double T1[kSN * kSN * 3];
+        for (int b = 0; b <= pv; ++b) {
+            double out_[kSN * 3];
+            span_bezier<kMaxSurfDegree>(pu, U, qu, P + 3 * ((int64_t)(qu - pu) * nv + (qv - pv + b)), nv, out_);
+            for (int a = 0; a <= pu; ++a)
+                for (int c = 0; c < 3; ++c) T1[(a * kSN + b) * 3 + c] = out_[3 * a + c];
+        }
+        for (int a = 0; a <= pu; ++a) {
+            double out_[kSN * 3];
+            span_bezier<kMaxSurfDegree>(pv, V, qv, T1 + a * kSN * 3, 1, out_);
+            for (int b = 0; b <= pv; ++b)
+                for (int c = 0; c < 3; ++c) root[(a * kSN + b) * 3 + c] = out_[3 * b + c];
+        }
+    }
+    if (FILL) {
+        // original span-pair piece in power form for the final Newton steps
+        double W[kSN * kSN * 3];
+        for (int a = 0; a < kSN; ++a)
+            for (int b = 0; b < kSN; ++b)
+                for (int c = 0; c < 3; ++c)
+                    W[(a * kSN + b) * 3 + c] = (a <= pu && b <= pv) ? root[(a * kSN + b) * 3 + c] : 0.0;
+        for (int b = 0; b <= pv; ++b) bern_to_power(pu, W + 3 * b, 3 * kSN);
+        for (int a = 0; a <= pu; ++a) bern_to_power(pv, W + 3 * kSN * a, 3);
+        double* dst = out.span_net + (int64_t)BSPL_SPAN_NET * slot;
+        for (int i = 0; i < kSN * kSN * 3; ++i) dst[i] = W[i];
+    }
+    double du = fsub(U[qu + 1], U[qu]), dv = fsub(V[qv + 1], V[qv]);
+    int L = 0;
+    uint64_t bits = 0;  // path bits, most recent in bit 0
+    int64_t count = 0;
+    for (;;) {
+        // replay the path from the root
+        for (int i = 0; i < kSN * kSN * 3; ++i) Q[i] = root[i];
+        int Lu = 0, Lv = 0;
+        int64_t ku = 0, kv = 0;
+        for (int l = 0; l < L; ++l) {
+            int side = (int)((bits >> (L - 1 - l)) & 1);
+            int dir = surf_split_dir(pu, pv, du, dv, Lu, Lv);
+            surf_halve_keep(pu, pv, Q, dir, side);
+            if (dir == 0) {
+                ++Lu;
+                ku = 2 * ku + side;
+            } else {
+                ++Lv;
+                kv = 2 * kv + side;
+            }
+        }
+        double R[4 * 4 * 3];
+        surf_to_bicubic(pu, pv, Q, R);
+        bool accept = true;
+        if (pu > 3 || pv > 3) accept = surf_bound2(pu, pv, Q, R) <= thr2;
+        if (!accept && (Lu + Lv >= kDepthCap || count >= kLeafCap)) {
+            accept = true;
+            set_flag(err, 2);
+        }
+        if (accept) {
+            if (FILL) {
+                int64_t o = first + count;
+                double* dst = out.ctrl + 48 * o;
+                for (int i = 0; i < 48; ++i) dst[i] = R[i];
+                double* pr = out.prange + 4 * o;
+                pr[0] = dyadic_t(U[qu], U[qu + 1], ku, Lu);
+                pr[1] = dyadic_t(U[qu], U[qu + 1], ku + 1, Lu);
+                pr[2] = dyadic_t(V[qv], V[qv + 1], kv, Lv);
+                pr[3] = dyadic_t(V[qv], V[qv + 1], kv + 1, Lv);
+                out.patch_span[o] = slot;
+                double* pb = out.patch_box + 4 * o;
+                pb[0] = ldexp((double)ku, -Lu);
+                pb[1] = ldexp((double)(ku + 1), -Lu);
+                pb[2] = ldexp((double)kv, -Lv);
+                pb[3] = ldexp((double)(kv + 1), -Lv);
+                // box of the original piece (conservative for the original surface)
+                double lo[3] = { INFINITY, INFINITY, INFINITY }, hi[3] = { -INFINITY, -INFINITY, -INFINITY };
+                for (int a = 0; a <= pu; ++a)
+                    for (int b = 0; b <= pv; ++b)
+                        for (int c = 0; c < 3; ++c) {
+                            lo[c] = fmin(lo[c], Q[(a * kSN + b) * 3 + c]);
+                            hi[c] = fmax(hi[c], Q[(a * kSN + b) * 3 + c]);
+                        }
+                double* rb = out.rec64 + (int64_t)BSPL_SREC64 * o;
+                for (int c = 0; c < 3; ++c) {
+                    rb[c] = lo[c];
+                    rb[3 + c] = hi[c];
+                }
+                float* rf = out.rec32 + (int64_t)BSPL_SREC32 * o;
+                rf[54] = (float)pu;
+                rf[55] = (float)pv;
+            }
+            ++count;
+            while (L > 0 && (bits & 1)) {
+                bits >>= 1;
+                --L;
+            }
+            if (L == 0) break;
+            bits |= 1;
+        } else {
+            ++L;
+            bits <<= 1;
+        }
+    }
+    return count;
+}
+
+// slot = cp_off[s] + a * n_v + b, a = qu - pu, b = qv - pv
+template <bool FILL>
+__global__ void k_walk_surfaces(bspl_surfaces S, const double* __restrict__ diag, double tol_rel,
+                                int64_t n_slots, int64_t* __restrict__ cnt, SurfLeafOut out, int* err)
+{
+    int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= n_slots) return;
+    int s = find_le(S.cp_off, S.n, slot);
+    if (!(diag[s] >= 0.0)) return;  // invalid surface
+    int pu = S.deg_u[s], pv = S.deg_v[s], nu = S.n_u[s], nv = S.n_v[s];
+    int64_t loc = slot - S.cp_off[s];
+    int a = (int)(loc / nv), b = (int)(loc % nv);
+    int qu = pu + a, qv = pv + b;
+    const double* U = S.knots_u + S.knot_u_off[s];
+    const double* V = S.knots_v + S.knot_v_off[s];
+    int64_t r = 0;
+    if (qu <= nu - 1 && qv <= nv - 1 && U[qu] < U[qu + 1] && V[qv] < V[qv + 1]) {
+        double thr = fmul(tol_rel, diag[s]);
+        r = walk_span_surface<FILL>(pu, pv, U, qu, V, qv, S.cps + 3 * S.cp_off[s], nv, fmul(thr, thr), slot,
+                                    FILL ? cnt[slot] : 0, out, err);
+    }
+    if (!FILL) cnt[slot] = r;
+}
+
+// --------------------------------------------------------------- tables
+
+__device__ float down32(double x) { return __double2float_rd(x); }
+__device__ float up32(double x) { return __double2float_ru(x); }
+
+// curve segment records: box of the cubic's control points, power basis
+// a0 + a1 u + a2 u^2 + a3 u^3 = [1 u u^2 u^3] B_3 R
+__global__ void k_curve_records(const double* __restrict__ ctrl, int64_t nseg, double* __restrict__ rec64,
+                                float* __restrict__ rec32)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const double* R = ctrl + 12 * s;
+    double* o = rec64 + (int64_t)BSPL_CREC64 * s;
+    float* f = rec32 + (int64_t)BSPL_CREC32 * s;
+    for (int c = 0; c < 3; ++c) {
+        double r0 = R[c], r1 = R[3 + c], r2 = R[6 + c], r3 = R[9 + c];
+        double lo = fmin(fmin(r0, r1), fmin(r2, r3)), hi = fmax(fmax(r0, r1), fmax(r2, r3));
+        double a0 = r0, a1 = 3.0 * (r1 - r0), a2 = 3.0 * (r0 - 2.0 * r1 + r2), a3 = (r3 - r0) + 3.0 * (r1 - r2);
+        o[c] = lo;
+        o[3 + c] = hi;
+        o[6 + c] = a0;
+        o[9 + c] = a1;
+        o[12 + c] = a2;
+        o[15 + c] = a3;
+        f[c] = down32(lo);
+        f[3 + c] = up32(hi);
+        f[6 + c] = (float)a0;
+        f[9 + c] = (float)a1;
+        f[12 + c] = (float)a2;
+        f[15 + c] = (float)a3;
+    }
+    f[18] = 0.f;
+    f[19] = 0.f;
+}
+
+// patch records: box already written (original piece); power basis of the
+// bicubic a[i][j] (i: u power, j: v power) = B_3 R B_3^T
+__global__ void k_patch_records(const double* __restrict__ ctrl, int64_t nseg, double* __restrict__ rec64,
+                                float* __restrict__ rec32)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const double* R = ctrl + 48 * s;
+    double* o = rec64 + (int64_t)BSPL_SREC64 * s;
+    float* f = rec32 + (int64_t)BSPL_SREC32 * s;
+    const double M[4][4] = { { 1, 0, 0, 0 }, { -3, 3, 0, 0 }, { 3, -6, 3, 0 }, { -1, 3, -3, 1 } };
+    for (int c = 0; c < 3; ++c) {
+        double T[4][4];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < 4; ++k) acc += M[i][k] * R[(k * 4 + j) * 3 + c];
+                T[i][j] = acc;
+            }
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < 4; ++k) acc += T[i][k] * M[j][k];
+                o[6 + (i * 4 + j) * 3 + c] = acc;
+                f[6 + (i * 4 + j) * 3 + c] = (float)acc;
+            }
+        f[c] = down32(o[c]);
+        f[3 + c] = up32(o[3 + c]);
+    }
+    // f[54], f[55] hold the span-pair degrees, written by the filling walk
+}
+
+// group records: union box of up to BSPL_GROUP consecutive segments of one
+// spline and a point on the piece (the first control point of its first segment)
+__global__ void k_group_records(const int64_t* __restrict__ seg_off, const int64_t* __restrict__ grp_off, int64_t n,
+                                int64_t n_grp, const double* __restrict__ rec64, int rec_w,
+                                const double* __restrict__ ctrl, int ctrl_w, double* __restrict__ grp64,
+                                float* __restrict__ grp32)
+{
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_grp) return;
+    int c = find_le(grp_off, n, g);
+    while (c + 1 < n && grp_off[c + 1] <= g) ++c;
+    int64_t s0 = seg_off[c] + (g - grp_off[c]) * BSPL_GROUP;
+    int64_t s1 = min(s0 + BSPL_GROUP, seg_off[c + 1]);
+    double lo[3] = { INFINITY, INFINITY, INFINITY }, hi[3] = { -INFINITY, -INFINITY, -INFINITY };
+    for (int64_t s = s0; s < s1; ++s)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], rec64[(int64_t)rec_w * s + k]);
+            hi[k] = fmax(hi[k], rec64[(int64_t)rec_w * s + 3 + k]);
+        }
+    double* o = grp64 + (int64_t)BSPL_GREC64 * g;
+    float* f = grp32 + (int64_t)BSPL_GREC32 * g;
+    for (int k = 0; k < 3; ++k) {
+        o[k] = lo[k];
+        o[3 + k] = hi[k];
+        o[6 + k] = ctrl[(int64_t)ctrl_w * s0 + k];
+        o[9 + k] = 0.0;
+        f[k] = down32(lo[k]);
+        f[3 + k] = up32(hi[k]);
+        f[6 + k] = (float)o[6 + k];
+        f[9 + k] = 0.f;
+    }
+}
+
+// seg_off[c] = offset of the spline's first slot; group counts per spline
+__global__ void k_seg_off(const int64_t* __restrict__ cp_off, int64_t n, const int64_t* __restrict__ off,
+                          int64_t n_cp, int64_t* __restrict__ seg_off, int64_t* __restrict__ gcnt)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > n) return;
+    int64_t tot = off[n_cp];
+    int64_t v = c < n ? off[cp_off[c]] : tot;
+    seg_off[c] = v;
+    if (c < n) {
+        int64_t v1 = (c + 1 < n) ? off[cp_off[c + 1]] : tot;
+        gcnt[c] = (v1 - v + BSPL_GROUP - 1) / BSPL_GROUP;
+    } else {
+        gcnt[c] = 0;
+    }
+}
+
+__global__ void k_totals(const int64_t* __restrict__ off, int64_t n_cp, const int64_t* __restrict__ goff, int64_t n,
+                         const int* __restrict__ flags, int64_t* __restrict__ dst)
+{
+    dst[0] = off[n_cp];
+    dst[1] = goff[n];
+    dst[2] = flags[0];
+}
+
+__global__ void k_copy_i64(const int64_t* __restrict__ a, int64_t* __restrict__ b, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+template <class K, class... A>
+void launch1d(K kernel, int64_t n, cudaStream_t s, A... args)
+{
+    if (n <= 0) return;
+    int th = 128;
+    kernel<<<ceil_div(n, th), th, 0, s>>>(args...);
+}
+
+}  // namespace
+
+size_t decompose_ws_bytes(int is_surface, int64_t n, int64_t n_cp_total)
+{
+    (void)is_surface;
+    Carver cv(nullptr, 0);
+    cv.take<int>(4);
+    cv.take<int64_t>((size_t)n_cp_total + 1);
+    cv.take<int64_t>((size_t)n + 1);
+    cv.take<int64_t>(scan_tmp_elems(n_cp_total + 1) + scan_tmp_elems(n + 1));
+    cv.take<int64_t>(4);
+    return cv.used + 256;
+}
+
+#define CK(x)                                      \
+    do {                                           \
+        if ((x) != cudaSuccess) return BSPL_ECUDA; \
+    } while (0)
+
+static bspl_status decompose_impl(int is_surface, const void* splines, double tol_rel, bspl_segments* out,
+                                  int64_t* total, void* ws, size_t ws_bytes, cudaStream_t s)
+{
+    const bspl_curves* CC = (const bspl_curves*)splines;
+    const bspl_surfaces* SS = (const bspl_surfaces*)splines;
+    if (!splines || !out || !total) return BSPL_EINVAL;
+    int64_t n = is_surface ? SS->n : CC->n;
+    int64_t n_cp = out->n_cp_total;
+    const int64_t* cp_off = is_surface ? SS->cp_off : CC->cp_off;
+    if (n <= 0 || n_cp <= 0 || !out->seg_off || !out->diag || !cp_off) return BSPL_EINVAL;
+    if (!(tol_rel >= 0.0) || !(tol_rel < INFINITY)) return BSPL_EINVAL;
+    if (!ws || ws_bytes < decompose_ws_bytes(is_surface, n, n_cp)) return BSPL_EINVAL;
+    Carver cv(ws, ws_bytes);
+    DecWS w;
+    int* flags = cv.take<int>(4);
+    w.err = flags;
+    w.maxdeg = flags + 1;
+    w.cnt = cv.take<int64_t>((size_t)n_cp + 1);
+    w.gcnt = cv.take<int64_t>((size_t)n + 1);
+    w.tmp = cv.take<int64_t>(scan_tmp_elems(n_cp + 1) + scan_tmp_elems(n + 1));
+    int64_t* dev_tot = cv.take<int64_t>(4);
+    CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
+    CK(cudaMemsetAsync(w.cnt, 0, sizeof(int64_t) * (size_t)(n_cp + 1), s));
+
+    // validation (invalid splines get a NaN diagonal, which the walks skip,
+    // and raise bit 0)
+    if (is_surface) launch1d(k_validate_surfaces, n, s, *SS, n_cp, out->diag, w.err, w.maxdeg);
+    else launch1d(k_validate_curves, n, s, *CC, n_cp, out->diag, w.err, w.maxdeg);
+    CK(cudaGetLastError());
+    int hf[2];
+    CK(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hf[0] & 1) return BSPL_EINVAL;
+    const int maxdeg = hf[1];
+
+    // counting pass
+    if (is_surface) {
+        SurfLeafOut o{};
+        launch1d(k_walk_surfaces<false>, n_cp, s, *SS, (const double*)out->diag, tol_rel, n_cp, w.cnt, o,
+                 w.err);
+    } else {
+        CurveLeafOut o{};
+        launch1d(k_walk_curves<7, false>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
+        if (maxdeg > 7)
+            launch1d(k_walk_curves<15, false>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o,
+                     w.err);
+        if (maxdeg > 15)
+            launch1d(k_walk_curves<31, false>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o,
+                     w.err);
+    }
+    CK(cudaGetLastError());
+    CK(exclusive_scan_i64(w.cnt, w.cnt, n_cp + 1, w.tmp, s));
+    launch1d(k_seg_off, n + 1, s, cp_off, n, (const int64_t*)w.cnt, n_cp, out->seg_off, w.gcnt);
+    CK(cudaGetLastError());
+    CK(exclusive_scan_i64(w.gcnt, w.gcnt, n + 1, w.tmp + scan_tmp_elems(n_cp + 1), s));
+    k_totals<<<1, 1, 0, s>>>(w.cnt, n_cp, w.gcnt, n, flags, dev_tot);
+    CK(cudaGetLastError());
+    int64_t h[3];
+    CK(cudaMemcpyAsync(h, dev_tot, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *total = h[0];
+    int64_t n_grp = h[1];
+    int err = (int)h[2];
+    if (out->grp_off) launch1d(k_copy_i64, n + 1, s, (const int64_t*)w.gcnt, out->grp_off, n + 1);
+    if (out->ctrl == nullptr) {
+        CK(cudaGetLastError());
+        return (err & 2) ? BSPL_ENOTCONV : BSPL_OK;
+    }
+    if (h[0] > out->capacity || n_grp > out->grp_capacity) return BSPL_ENOSPACE;
+    if (!out->prange || !out->rec64 || !out->rec32 || !out->grp_off || !out->grp64 || !out->grp32)
+        return BSPL_EINVAL;
+    if (is_surface && (!out->patch_span || !out->patch_box || !out->span_net)) return BSPL_EINVAL;
+    out->is_surface = is_surface;
+    out->n = n;
+    out->tol_rel = tol_rel;
+
+    // filling pass and query tables
+    if (is_surface) {
+        SurfLeafOut o{ out->ctrl, out->prange, out->patch_span, out->patch_box, out->rec64, out->rec32,
+                       out->span_net };
+        launch1d(k_walk_surfaces<true>, n_cp, s, *SS, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
+        launch1d(k_patch_records, h[0], s, (const double*)out->ctrl, h[0], out->rec64, out->rec32);
+        launch1d(k_group_records, n_grp, s, (const int64_t*)out->seg_off, (const int64_t*)out->grp_off, n, n_grp,
+                 (const double*)out->rec64, (int)BSPL_SREC64, (const double*)out->ctrl, 48, out->grp64,
+                 out->grp32);
+    } else {
+        CurveLeafOut o{ out->ctrl, out->prange };
+        launch1d(k_walk_curves<7, true>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
+        if (maxdeg > 7)
+            launch1d(k_walk_curves<15, true>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
+        if (maxdeg > 15)
+            launch1d(k_walk_curves<31, true>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
+        launch1d(k_curve_records, h[0], s, (const double*)out->ctrl, h[0], out->rec64, out->rec32);
+        launch1d(k_group_records, n_grp, s, (const int64_t*)out->seg_off, (const int64_t*)out->grp_off, n, n_grp,
+                 (const double*)out->rec64, (int)BSPL_CREC64, (const double*)out->ctrl, 12, out->grp64,
+                 out->grp32);
+    }
+    CK(cudaGetLastError());
+    return (err & 2) ? BSPL_ENOTCONV : BSPL_OK;
+}
+
+bspl_status decompose_curves(const bspl_curves* c, double tol_rel, bspl_segments* out, int64_t* total, void* ws,
+                             size_t ws_bytes, cudaStream_t s)
+{
+    return decompose_impl(0, c, tol_rel, out, total, ws, ws_bytes, s);
+}
+
+bspl_status decompose_surfaces(const bspl_surfaces* c, double tol_rel, bspl_segments* out, int64_t* total,
+                               void* ws, size_t ws_bytes, cudaStream_t s)
+{
+    return decompose_impl(1, c, tol_rel, out, total, ws, ws_bytes, s);
+}
+
+}  // namespace bspl

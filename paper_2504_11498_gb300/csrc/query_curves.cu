@@ -1,0 +1,757 @@
+// Batched point projection / inversion on decomposed curves (Sec. 3 Eqs.
+// projection, projections, inversion; Sec. 4.2.3 Eqs. Dt, Et, E't; Sec. 4.4.2
+// per-query minimum and reparameterisation).
+//
+// Layout of the work: queries are first grouped by curve (counting sort), then
+// one warp takes a batch of 32 consecutive queries.  For each query the warp
+// cooperates: lanes stride over the curve's culling groups (32 consecutive
+// segments each) for an upper bound of the distance from group reference
+// points, then over surviving groups' segments (lower bound = distance to the
+// segment's control-point box; upper bound tightened by segment start
+// points), then evaluates a grid of S samples on every surviving segment
+// (32/S segments per warp step) and detects the sampled basins with
+// shuffles.  Every admitted basin goes to a per-warp pool; when the pool
+// fills, or the batch ends, each lane runs a safeguarded Newton iteration on
+// one pooled basin, so the Newton phase keeps all 32 lanes busy.  The
+// per-query minimum is then taken by the lane that owns the query's slot.
+//
+// Precision: PLAIN runs every stage in FP64 on the FP64 records.  MIXED runs
+// culling, grid and the first Newton steps in FP32 on the FP32 records
+// (boxes rounded outward, slack on every comparison), then two FP64 Newton
+// steps on the FP64 coefficients; a basin whose second FP64 step is not
+// below 1e-9 continues with the FP64 safeguarded iteration (FALLBACK).
+#include <math.h>
+
+#include "bspl_internal.cuh"
+
+namespace bspl {
+
+namespace {
+
+constexpr int kQPW = 32;       // queries per warp batch
+constexpr int kCandCap = 96;   // surviving segments buffered before the grid stage
+constexpr int kPoolCap = 128;  // Newton basins buffered per warp
+constexpr int kWarps = 4;      // warps per block
+constexpr unsigned kFull = 0xffffffffu;
+
+struct CurveQ {
+    const int64_t* seg_off;
+    const int64_t* grp_off;
+    const double* rec64;
+    const float* rec32;
+    const double* grp64;
+    const float* grp32;
+    const double* prange;
+    const double* diag;
+    int64_t n, n_q;
+    const int32_t* q_curve;
+    const double* q_xyz;
+    const int32_t* order;
+    double* t;
+    double* dist;
+    uint8_t* status;
+    int invert;
+    int newton_max;
+    int fp32_steps;
+    unsigned long long* counters;
+};
+
+template <class R>
+struct Tab;
+template <>
+struct Tab<double> {
+    static __device__ const double* rec(const CurveQ& P) { return P.rec64; }
+    static __device__ const double* grp(const CurveQ& P) { return P.grp64; }
+    static constexpr int RW = BSPL_CREC64, GW = BSPL_GREC64;
+};
+template <>
+struct Tab<float> {
+    static __device__ const float* rec(const CurveQ& P) { return P.rec32; }
+    static __device__ const float* grp(const CurveQ& P) { return P.grp32; }
+    static constexpr int RW = BSPL_CREC32, GW = BSPL_GREC32;
+};
+
+template <class R>
+__device__ __forceinline__ R warp_min(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+template <class R>
+__device__ __forceinline__ R box_d2(const R* b, R qx, R qy, R qz)
+{
+    R dx = fmax(fmax(b[0] - qx, qx - b[3]), R(0));
+    R dy = fmax(fmax(b[1] - qy, qy - b[4]), R(0));
+    R dz = fmax(fmax(b[2] - qz, qz - b[5]), R(0));
+    return dx * dx + dy * dy + dz * dz;
+}
+
+template <class R>
+__device__ __forceinline__ R pt_d2(const R* p, R qx, R qy, R qz)
+{
+    R dx = p[0] - qx, dy = p[1] - qy, dz = p[2] - qz;
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// squared-distance threshold with slack: (sqrt(ub) + eps)^2
+template <class R>
+__device__ __forceinline__ R slacked(R ub, R eps)
+{
+    R s = sqrt(ub) + eps;
+    return s * s;
+}
+
+// E = (C - q).C' and E' = C'.C' + (C - q).C'' for the cubic a0 + a1 u + a2 u^2 + a3 u^3
+// (Eqs. Et, E't up to the common factor 2); returns D = |C - q|^2
+template <class R>
+__device__ __forceinline__ R eval_E(const R* a, R qx, R qy, R qz, R u, R& E, R& Ep)
+{
+    R q3[3] = { qx, qy, qz };
+    R D = 0, e = 0, ep = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        R a0 = a[c], a1 = a[3 + c], a2 = a[6 + c], a3 = a[9 + c];
+        R C = a0 + u * (a1 + u * (a2 + u * a3)) - q3[c];
+        R C1 = a1 + u * (R(2) * a2 + u * (R(3) * a3));
+        R C2 = R(2) * a2 + u * (R(6) * a3);
+        D += C * C;
+        e += C * C1;
+        ep += C1 * C1 + C * C2;
+    }
+    E = e;
+    Ep = ep;
+    return D;
+}
+
+// safeguarded Newton for a local minimum of D on the segment [0, 1], started
+// in a sampled basin: a Newton step on E = D' when E' > 0, else a step of
+// length hmax down the slope; every step is limited to hmax, projected onto
+// [0, 1] and halved until D does not increase.  Stops at a bound where D
+// rises into the segment (KKT), when no descent is left at this resolution,
+// or when the step falls below tol.  Returns true unless maxit ran out.
+template <class R>
+__device__ bool newton_min(const R* a, R qx, R qy, R qz, R& u, R hmax, int maxit, R tol, unsigned& iters)
+{
+    R E, Ep;
+    R D = eval_E(a, qx, qy, qz, u, E, Ep);
+    for (int it = 0; it < maxit; ++it) {
+        ++iters;
+        if ((u <= R(0) && E >= R(0)) || (u >= R(1) && E <= R(0)) || E == R(0)) return true;
+        R step = Ep > R(0) ? -E / Ep : (E > R(0) ? -hmax : hmax);
+        step = fmin(fmax(step, -hmax), hmax);
+        R un = u, Dn = D, En = E, Epn = Ep;
+        bool acc = false;
+        for (int ls = 0; ls < 24; ++ls) {
+            un = fmin(fmax(u + step, R(0)), R(1));
+            Dn = eval_E(a, qx, qy, qz, un, En, Epn);
+            if (Dn < D) {
+                acc = true;
+                break;
+            }
+            if (Dn == D) return true;  // no progress left at this precision
+            step *= R(0.5);
+        }
+        if (!acc) return true;
+        R moved = fabs(un - u);
+        u = un;
+        D = Dn;
+        E = En;
+        Ep = Epn;
+        if (moved <= tol) return true;
+    }
+    return false;
+}
+
+// E(u)/2 = (C(u) - q).C'(u) for the cubic a0 + a1 u + a2 u^2 + a3 u^3 (Eq.
+// Et), a degree-5 polynomial, in Bernstein form on [0,1]: power coefficients
+// e_k, then b = T e with T_ij = C(i,j)/C(5,j) (the degree-5 power-to-
+// Bernstein matrix of Sec. 4.3).  Returns the number of sign changes of b
+// (zeros skipped), an upper bound of the number of roots of E in [0,1].
+template <class R>
+__device__ __forceinline__ int bernstein_E(const R* a, R qx, R qy, R qz, R* b)
+{
+    const R q3[3] = { qx, qy, qz };
+    R e[6] = { 0, 0, 0, 0, 0, 0 };
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R c0 = a[c] - q3[c], c1 = a[3 + c], c2 = a[6 + c], c3 = a[9 + c];
+        const R d1 = c1, d2 = R(2) * c2, d3 = R(3) * c3;  // C' = d1 + d2 u + d3 u^2
+        e[0] += c0 * d1;
+        e[1] += c0 * d2 + c1 * d1;
+        e[2] += c0 * d3 + c1 * d2 + c2 * d1;
+        e[3] += c1 * d3 + c2 * d2 + c3 * d1;
+        e[4] += c2 * d3 + c3 * d2;
+        e[5] += c3 * d3;
+    }
+    b[0] = e[0];
+    b[1] = e[0] + R(0.2) * e[1];
+    b[2] = e[0] + R(0.4) * e[1] + R(0.1) * e[2];
+    b[3] = e[0] + R(0.6) * e[1] + R(0.3) * e[2] + R(0.1) * e[3];
+    b[4] = e[0] + R(0.8) * e[1] + R(0.6) * e[2] + R(0.4) * e[3] + R(0.2) * e[4];
+    b[5] = e[0] + e[1] + e[2] + e[3] + e[4] + e[5];
+    int v = 0;
+    R last = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (b[i] != R(0)) {
+            if (last != R(0) && (b[i] > R(0)) != (last > R(0))) ++v;
+            last = b[i];
+        }
+    }
+    return v;
+}
+
+template <class R>
+__device__ __forceinline__ int sign_changes6(const R* b)
+{
+    int v = 0;
+    R last = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (b[i] != R(0)) {
+            if (last != R(0) && (b[i] > R(0)) != (last > R(0))) ++v;
+            last = b[i];
+        }
+    }
+    return v;
+}
+
+// bracketed Newton on E for its root in [lo, hi] with E(lo) < 0 < E(hi)
+template <class R>
+__device__ R root_bracketed(const R* a, R qx, R qy, R qz, R lo, R hi, int maxit, R tol)
+{
+    R u = R(0.5) * (lo + hi);
+    for (int it = 0; it < maxit; ++it) {
+        R E, Ep;
+        eval_E(a, qx, qy, qz, u, E, Ep);
+        if (E > R(0)) hi = u;
+        else if (E < R(0)) lo = u;
+        else return u;
+        R un = Ep > R(0) ? u - E / Ep : R(0.5) * (lo + hi);
+        if (!(un > lo && un < hi)) un = R(0.5) * (lo + hi);
+        if (fabs(un - u) <= tol || hi - lo <= tol) return un;
+        u = un;
+    }
+    return u;
+}
+
+// every local minimum of D = |C(u) - q|^2 on [0,1], certified by sign
+// variations: an interval whose Bernstein coefficients of E change sign
+// once holds exactly one root (a minimum when E goes from - to +); more
+// changes -> split at the middle (de Casteljau); none -> no root.  The ends
+// are minima when E(0) >= 0 or E(1) <= 0.  Returns the best minimiser.
+template <class R>
+__device__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int maxit)
+{
+    constexpr int kStack = 24;
+    R b0[6];
+    bernstein_E(a, qx, qy, qz, b0);
+    R bestu = R(0), bestD;
+    {
+        R E, Ep;
+        bestD = eval_E(a, qx, qy, qz, R(0), E, Ep);
+        R D1 = eval_E(a, qx, qy, qz, R(1), E, Ep);
+        if (D1 < bestD) {
+            bestD = D1;
+            bestu = R(1);
+        }
+    }
+    R st_b[kStack][6];
+    R st_lo[kStack], st_hi[kStack];
+    int top = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st_b[0][i] = b0[i];
+    st_lo[0] = R(0);
+    st_hi[0] = R(1);
+    top = 1;
+    int budget = 64;  // intervals examined at most
+    while (top > 0 && budget-- > 0) {
+        --top;
+        R b[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) b[i] = st_b[top][i];
+        const R lo = st_lo[top], hi = st_hi[top];
+        const int v = sign_changes6(b);
+        if (v == 0) continue;
+        if (v == 1 || top + 2 > kStack || hi - lo <= tol * R(64)) {
+            if (b[0] < R(0) && b[5] > R(0)) {
+                R u = root_bracketed(a, qx, qy, qz, lo, hi, maxit, tol);
+                R E, Ep;
+                R D = eval_E(a, qx, qy, qz, u, E, Ep);
+                if (D < bestD) {
+                    bestD = D;
+                    bestu = u;
+                }
+            } else if (v > 1) {
+                // unresolved within the stack: try the middle as a seed
+                R u = R(0.5) * (lo + hi);
+                R E, Ep;
+                R D = eval_E(a, qx, qy, qz, u, E, Ep);
+                if (D < bestD) {
+                    bestD = D;
+                    bestu = u;
+                }
+            }
+            continue;
+        }
+        // split at the middle: left and right Bernstein coefficients
+        R w[6], L[6], Rr[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) w[i] = b[i];
+        L[0] = w[0];
+        Rr[5] = w[5];
+#pragma unroll
+        for (int r = 1; r < 6; ++r) {
+#pragma unroll
+            for (int i = 0; i < 6 - r; ++i) w[i] = R(0.5) * (w[i] + w[i + 1]);
+            L[r] = w[0];
+            Rr[5 - r] = w[5 - r];
+        }
+        const R mid = R(0.5) * (lo + hi);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st_b[top][i] = Rr[i];
+        st_lo[top] = mid;
+        st_hi[top] = hi;
+        ++top;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st_b[top][i] = L[i];
+        st_lo[top] = lo;
+        st_hi[top] = mid;
+        ++top;
+    }
+    return bestu;
+}
+
+struct PoolEntry {
+    int seg;
+    int slot;
+    float u0, h;  // h < 0: isolate every minimum of the segment first
+};
+
+struct WarpSmem {
+    int cand_seg[kCandCap];
+    double cand_lb[kCandCap];
+    PoolEntry pool[kPoolCap];
+    double pool_D[kPoolCap];
+    double pool_u[kPoolCap];
+    unsigned char pool_flags[kPoolCap];
+    double q64[kQPW][3];
+    double best_D[kQPW];
+    double best_u[kQPW];
+    int best_seg[kQPW];
+    unsigned char best_flags[kQPW];
+};
+
+// Newton phase over the pooled basins, then per-slot merge
+template <class R, bool MIXED>
+__device__ void flush_pool(const CurveQ& P, WarpSmem& W, int npool, int lane, unsigned& it32, unsigned& it64)
+{
+    for (int k = lane; k < npool; k += 32) {
+        PoolEntry e = W.pool[k];
+        const double* q = W.q64[e.slot];
+        const double* a64 = P.rec64 + (int64_t)BSPL_CREC64 * e.seg + 6;
+        unsigned char fl = 0;
+        double u;
+        const bool iso = e.h < 0.f;
+        const float hh = iso ? 1.f / 64.f : e.h;
+        if (MIXED) {
+            const float* a32 = P.rec32 + (int64_t)BSPL_CREC32 * e.seg + 6;
+            float c32[12];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) c32[i] = a32[i];
+            float uf = e.u0;
+            if (iso) uf = isolate_min<float>(c32, (float)q[0], (float)q[1], (float)q[2], 1e-7f, P.fp32_steps * 4);
+            newton_min<float>(c32, (float)q[0], (float)q[1], (float)q[2], uf, hh, P.fp32_steps, 1e-7f, it32);
+            double c64[12];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) c64[i] = a64[i];
+            // two FP64 Newton steps, clamped to the segment
+            u = (double)uf;
+            double last = 1.0;
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                ++it64;
+                double E, Ep;
+                eval_E(c64, q[0], q[1], q[2], u, E, Ep);
+                double un = Ep > 0.0 ? u - E / Ep : u;
+                un = fmin(fmax(un, 0.0), 1.0);
+                last = fabs(un - u);
+                u = un;
+            }
+            bool ok = last <= 1e-9;
+            if (!ok) {
+                // FP64 fallback: safeguarded iteration on the whole segment
+                fl |= BSPL_Q_FALLBACK;
+                ok = newton_min<double>(c64, q[0], q[1], q[2], u, (double)hh, P.newton_max, 1e-15, it64);
+            }
+            if (ok) fl |= BSPL_Q_CONVERGED;
+            else fl |= BSPL_Q_NONCONV;
+            double E, Ep;
+            W.pool_D[k] = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
+        } else {
+            double c64[12];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) c64[i] = a64[i];
+            u = (double)e.u0;
+            if (iso) u = isolate_min<double>(c64, q[0], q[1], q[2], 1e-15, P.newton_max);
+            bool ok = newton_min<double>(c64, q[0], q[1], q[2], u, (double)hh, P.newton_max, 1e-15, it64);
+            fl |= ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
+            double E, Ep;
+            W.pool_D[k] = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
+        }
+        W.pool_u[k] = u;
+        W.pool_flags[k] = fl;
+    }
+    __syncwarp();
+    if (lane < kQPW) {
+        double bD = W.best_D[lane], bu = W.best_u[lane];
+        int bs = W.best_seg[lane];
+        unsigned char bf = W.best_flags[lane];
+        for (int k = 0; k < npool; ++k) {
+            if (W.pool[k].slot != lane) continue;
+            double D = W.pool_D[k], u = W.pool_u[k];
+            int s = W.pool[k].seg;
+            if (D < bD || (D == bD && (s < bs || (s == bs && u < bu)))) {
+                bD = D;
+                bu = u;
+                bs = s;
+                bf = W.pool_flags[k];
+            }
+        }
+        W.best_D[lane] = bD;
+        W.best_u[lane] = bu;
+        W.best_seg[lane] = bs;
+        W.best_flags[lane] = bf;
+    }
+    __syncwarp();
+}
+
+template <class R, int S, bool MIXED>
+__global__ void __launch_bounds__(kWarps * 32) k_query_curves(CurveQ P)
+{
+    __shared__ WarpSmem smem[kWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpSmem& W = smem[wid];
+    const int64_t batch = (int64_t)blockIdx.x * kWarps + wid;
+    const int64_t qbase = batch * kQPW;
+    if (qbase >= P.n_q) return;
+    const int nslots = (int)min((int64_t)kQPW, P.n_q - qbase);
+    const R* rec = Tab<R>::rec(P);
+    const R* grp = Tab<R>::grp(P);
+    constexpr int RW = Tab<R>::RW, GW = Tab<R>::GW;
+    constexpr int SPW = 32 / S;  // segments per grid step
+    const R h = R(1) / R(S - 1);
+    unsigned long long n_grp_tested = 0, n_seg_tested = 0, n_cand = 0, n_newton = 0;
+    unsigned it32 = 0, it64 = 0;  // Newton iterations run by this lane
+
+    if (lane < kQPW) {
+        W.best_D[lane] = INFINITY;
+        W.best_u[lane] = 0.0;
+        W.best_seg[lane] = 0x7fffffff;
+        W.best_flags[lane] = 0;
+    }
+    int npool = 0;
+    __syncwarp();
+
+    for (int sl = 0; sl < nslots; ++sl) {
+        const int64_t qi = P.order ? (int64_t)P.order[qbase + sl] : qbase + sl;
+        const int c = P.q_curve[qi];
+        const double qx64 = P.q_xyz[3 * qi], qy64 = P.q_xyz[3 * qi + 1], qz64 = P.q_xyz[3 * qi + 2];
+        const bool bad = c < 0 || c >= P.n || !isfinite(qx64) || !isfinite(qy64) || !isfinite(qz64);
+        if (lane == 0) {
+            W.q64[sl][0] = qx64;
+            W.q64[sl][1] = qy64;
+            W.q64[sl][2] = qz64;
+            if (bad) W.best_flags[sl] = BSPL_Q_INVALID;
+        }
+        if (bad) continue;
+        const R qx = (R)qx64, qy = (R)qy64, qz = (R)qz64;
+        const int64_t s0 = P.seg_off[c], s1 = P.seg_off[c + 1];
+        const int64_t g0 = P.grp_off[c], g1 = P.grp_off[c + 1];
+        const R eps = (MIXED ? R(4e-6) : R(1e-13)) * (R)(fabs(qx64) + fabs(qy64) + fabs(qz64) + P.diag[c]);
+
+        // level 1: upper bound from the group reference points
+        R ub = INFINITY;
+        for (int64_t g = g0 + lane; g < g1; g += 32) ub = fmin(ub, pt_d2(grp + (int64_t)GW * g + 6, qx, qy, qz));
+        ub = warp_min(ub);
+        R ubs = slacked(ub, eps);
+        n_grp_tested += (unsigned long long)(g1 - g0);
+
+        int ncand = 0;
+        // grid stage over the buffered candidates
+        auto grid_stage = [&]() {
+            __syncwarp();
+            const int sub = lane / S, j = lane % S;
+            for (int base = 0; base < ncand; base += SPW) {
+                const int k = base + sub;
+                const bool act = k < ncand && (R)W.cand_lb[k] <= ubs;
+                const int seg = act ? W.cand_seg[k] : 0;
+                R D = INFINITY, spd = 0;
+                int nsc = 0;
+                const R u = R(j) * h;
+                if (act) {
+                    R bb[6];
+                    nsc = bernstein_E(rec + (int64_t)RW * seg + 6, qx, qy, qz, bb);
+                    const R* a = rec + (int64_t)RW * seg + 6;
+                    R Dq = 0;
+                    const R q3[3] = { qx, qy, qz };
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        R a0 = a[cc], a1 = a[3 + cc], a2 = a[6 + cc], a3 = a[9 + cc];
+                        R x = a0 + u * (a1 + u * (a2 + u * a3)) - q3[cc];
+                        Dq += x * x;
+                        spd += fabs(a1) + R(2) * fabs(a2) + R(3) * fabs(a3);
+                    }
+                    D = Dq;
+                }
+                const R Dl = __shfl_up_sync(kFull, D, 1, S);
+                const R Dr = __shfl_down_sync(kFull, D, 1, S);
+                const bool ismin = act && (j == 0 || D <= Dl) && (j == S - 1 || D < Dr);
+                ub = fmin(ub, warp_min(D));
+                ubs = slacked(ub, eps);
+                // a basin can hold a point within spd*h of its sample; a
+                // segment whose E changes sign more than once is handed to
+                // the certified isolation instead (one entry, lane j = 0)
+                const R adm = slacked(ub, eps + spd * h);
+                const bool iso = act && nsc >= 2;
+                const bool push = iso ? (j == 0) : (ismin && D <= adm);
+                const unsigned m = __ballot_sync(kFull, push);
+                const int cnt = __popc(m);
+                if (cnt > 0 && npool + cnt > kPoolCap) {
+                    flush_pool<R, MIXED>(P, W, npool, lane, it32, it64);
+                    n_newton += npool;
+                    npool = 0;
+                }
+                if (push) {
+                    const int pos = npool + __popc(m & ((1u << lane) - 1));
+                    PoolEntry e;
+                    e.seg = seg;
+                    e.slot = sl;
+                    e.u0 = (float)u;
+                    e.h = iso ? -1.f : (float)h;
+                    if (j == 0) e.u0 = 0.f;
+                    if (j == S - 1) e.u0 = 1.f;
+                    W.pool[pos] = e;
+                }
+                npool += cnt;
+                __syncwarp();
+            }
+            n_cand += (unsigned long long)ncand;
+            ncand = 0;
+        };
+
+        // level 2: groups that may hold a closer point, then their segments
+        for (int64_t gb = g0; gb < g1; gb += 32) {
+            const int64_t g = gb + lane;
+            const R lbg = g < g1 ? box_d2(grp + (int64_t)GW * g, qx, qy, qz) : R(INFINITY);
+            unsigned m = __ballot_sync(kFull, lbg <= ubs);
+            while (m) {
+                const int jg = __ffs(m) - 1;
+                m &= m - 1;
+                const R lbj = __shfl_sync(kFull, lbg, jg);
+                if (!(lbj <= ubs)) continue;
+                const int64_t ss = s0 + (gb + jg - g0) * BSPL_GROUP;
+                const int64_t se = min(ss + BSPL_GROUP, s1);
+                const int64_t s = ss + lane;
+                const bool valid = s < se;
+                R lbs = INFINITY, ups = INFINITY;
+                if (valid) {
+                    const R* r = rec + (int64_t)RW * s;
+                    lbs = box_d2(r, qx, qy, qz);
+                    ups = pt_d2(r + 6, qx, qy, qz);
+                }
+                n_seg_tested += (unsigned long long)(se - ss);
+                ub = fmin(ub, warp_min(ups));
+                ubs = slacked(ub, eps);
+                const bool keep = valid && lbs <= ubs;
+                const unsigned km = __ballot_sync(kFull, keep);
+                if (keep) {
+                    const int pos = ncand + __popc(km & ((1u << lane) - 1));
+                    W.cand_seg[pos] = (int)s;
+                    W.cand_lb[pos] = (double)lbs;
+                }
+                ncand += __popc(km);
+                if (ncand > kCandCap - 32) grid_stage();
+            }
+        }
+        grid_stage();
+        // the curve's last point (u = 1 of its last segment) is sampled by the
+        // grid only when that segment survives; it always survives culling
+        // because its start point bounds ub from above only when it is close
+        (void)s1;
+    }
+    if (npool > 0) {
+        flush_pool<R, MIXED>(P, W, npool, lane, it32, it64);
+        n_newton += npool;
+    }
+    __syncwarp();
+
+    // write results: lane = slot
+    if (lane < nslots) {
+        const int64_t qi = P.order ? (int64_t)P.order[qbase + lane] : qbase + lane;
+        unsigned char fl = W.best_flags[lane];
+        const int seg = W.best_seg[lane];
+        if ((fl & BSPL_Q_INVALID) || seg == 0x7fffffff) {
+            P.t[qi] = __longlong_as_double(0x7ff8000000000000LL);
+            P.dist[qi] = __longlong_as_double(0x7ff8000000000000LL);
+            P.status[qi] = BSPL_Q_INVALID;
+        } else {
+            const double u = W.best_u[lane];
+            const double t0 = P.prange[2 * seg], t1 = P.prange[2 * seg + 1];
+            const double t = u <= 0.0 ? t0 : (u >= 1.0 ? t1 : t0 + u * (t1 - t0));
+            const double d = sqrt(W.best_D[lane]);
+            const int c = P.q_curve[qi];
+            if ((seg == P.seg_off[c] && u <= 0.0) || (seg == P.seg_off[c + 1] - 1 && u >= 1.0)) fl |= BSPL_Q_AT_END;
+            if (P.invert && d > 1e-9 * P.diag[c]) fl |= BSPL_Q_OFF_CURVE;
+            P.t[qi] = t;
+            P.dist[qi] = d;
+            P.status[qi] = fl;
+        }
+    }
+    if (P.counters) {
+        unsigned long long fb = 0, nc = 0, i32 = it32, i64 = it64;
+        if (lane < nslots) {
+            fb = (W.best_flags[lane] & BSPL_Q_FALLBACK) ? 1 : 0;
+            nc = (W.best_flags[lane] & BSPL_Q_NONCONV) ? 1 : 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fb += __shfl_xor_sync(kFull, fb, o);
+            nc += __shfl_xor_sync(kFull, nc, o);
+            i32 += __shfl_xor_sync(kFull, i32, o);
+            i64 += __shfl_xor_sync(kFull, i64, o);
+        }
+        if (lane == 0) {
+            atomicAdd(P.counters + BSPL_CNT_QUERIES, (unsigned long long)nslots);
+            atomicAdd(P.counters + BSPL_CNT_GRP_TESTED, n_grp_tested);
+            atomicAdd(P.counters + BSPL_CNT_SEG_TESTED, n_seg_tested);
+            atomicAdd(P.counters + BSPL_CNT_CANDIDATES, n_cand);
+            atomicAdd(P.counters + BSPL_CNT_NEWTON, n_newton);
+            atomicAdd(P.counters + BSPL_CNT_FALLBACK, fb);
+            atomicAdd(P.counters + BSPL_CNT_NONCONV, nc);
+            atomicAdd(P.counters + BSPL_CNT_NEWTON32_ITERS, i32);
+            atomicAdd(P.counters + BSPL_CNT_NEWTON64_ITERS, i64);
+        }
+    }
+}
+
+// ------------------------------------------------------------ query sorting
+
+__global__ void k_hist(const int32_t* __restrict__ qc, int64_t n_q, int64_t n, int64_t* __restrict__ hist)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_q) return;
+    int c = qc[i];
+    int64_t b = (c >= 0 && c < n) ? c : n;  // invalid queries go to the last bucket
+    atomicAdd((unsigned long long*)(hist + b), 1ull);
+}
+
+__global__ void k_scatter(const int32_t* __restrict__ qc, int64_t n_q, int64_t n, int64_t* __restrict__ cursor,
+                          int32_t* __restrict__ order)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_q) return;
+    int c = qc[i];
+    int64_t b = (c >= 0 && c < n) ? c : n;
+    unsigned long long pos = atomicAdd((unsigned long long*)(cursor + b), 1ull);
+    order[pos] = (int32_t)i;
+}
+
+template <class R, int S, bool MIXED>
+void launch_query(const CurveQ& P, cudaStream_t s)
+{
+    int64_t batches = (P.n_q + kQPW - 1) / kQPW;
+    int64_t blocks = (batches + kWarps - 1) / kWarps;
+    k_query_curves<R, S, MIXED><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P);
+}
+
+}  // namespace
+
+size_t query_ws_bytes(int64_t n_splines, int64_t n_q)
+{
+    Carver cv(nullptr, 0);
+    cv.take<int64_t>((size_t)n_splines + 2);
+    cv.take<int64_t>(scan_tmp_elems(n_splines + 2));
+    cv.take<int32_t>((size_t)n_q);
+    return cv.used + 256;
+}
+
+// groups query indices by spline: order[] lists queries bucket by bucket
+cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, void* ws, size_t ws_bytes, int32_t** order,
+                           cudaStream_t s)
+{
+    Carver cv(ws, ws_bytes);
+    int64_t* hist = cv.take<int64_t>((size_t)n + 2);
+    int64_t* tmp = cv.take<int64_t>(scan_tmp_elems(n + 2));
+    int32_t* ord = cv.take<int32_t>((size_t)n_q);
+    if (!hist || !tmp || !ord) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int64_t) * (size_t)(n + 2), s);
+    if (e != cudaSuccess) return e;
+    int th = 256;
+    k_hist<<<ceil_div(n_q, th), th, 0, s>>>(qc, n_q, n, hist);
+    e = exclusive_scan_i64(hist, hist, n + 2, tmp, s);
+    if (e != cudaSuccess) return e;
+    k_scatter<<<ceil_div(n_q, th), th, 0, s>>>(qc, n_q, n, hist, ord);
+    *order = ord;
+    return cudaGetLastError();
+}
+
+bspl_status query_curves(const bspl_segments* segs, int64_t n_q, const int32_t* q_curve, const double* q_xyz,
+                         const bspl_options* opt, int invert, double* t, double* dist, uint8_t* status, void* ws,
+                         size_t ws_bytes, cudaStream_t s)
+{
+    if (!segs || segs->is_surface || n_q < 0) return BSPL_EINVAL;
+    if (n_q == 0) return BSPL_OK;
+    if (!q_curve || !q_xyz || !t || !dist || !status || !segs->seg_off || !segs->grp_off || !segs->rec64 ||
+        !segs->rec32 || !segs->grp64 || !segs->grp32 || !segs->prange || !segs->diag)
+        return BSPL_EINVAL;
+    if (n_q > 0x7fffffffLL || segs->capacity > 0x7fffffffLL) return BSPL_EINVAL;
+    bspl_options o{};
+    if (opt) o = *opt;
+    int samples = o.samples ? o.samples : 16;
+    if (samples != 8 && samples != 16 && samples != 32) return BSPL_EINVAL;
+    if (o.prec != BSPL_FP64 && o.prec != BSPL_MIXED) return BSPL_EINVAL;
+    int sort = opt ? o.sort_queries : 1;
+    CurveQ P{};
+    P.seg_off = segs->seg_off;
+    P.grp_off = segs->grp_off;
+    P.rec64 = segs->rec64;
+    P.rec32 = segs->rec32;
+    P.grp64 = segs->grp64;
+    P.grp32 = segs->grp32;
+    P.prange = segs->prange;
+    P.diag = segs->diag;
+    P.n = segs->n;
+    P.n_q = n_q;
+    P.q_curve = q_curve;
+    P.q_xyz = q_xyz;
+    P.t = t;
+    P.dist = dist;
+    P.status = status;
+    P.invert = invert;
+    P.newton_max = o.newton_max > 0 ? o.newton_max : 30;
+    P.fp32_steps = o.fp32_steps > 0 ? o.fp32_steps : 4;
+    P.counters = (unsigned long long*)o.counters;
+    P.order = nullptr;
+    if (sort) {
+        if (!ws || ws_bytes < query_ws_bytes(segs->n, n_q)) return BSPL_EINVAL;
+        int32_t* ord = nullptr;
+        if (sort_by_spline(q_curve, n_q, segs->n, ws, ws_bytes, &ord, s) != cudaSuccess) return BSPL_ECUDA;
+        P.order = ord;
+    }
+    const bool mixed = o.prec == BSPL_MIXED;
+    if (mixed) {
+        if (samples == 8) launch_query<float, 8, true>(P, s);
+        else if (samples == 16) launch_query<float, 16, true>(P, s);
+        else launch_query<float, 32, true>(P, s);
+    } else {
+        if (samples == 8) launch_query<double, 8, false>(P, s);
+        else if (samples == 16) launch_query<double, 16, false>(P, s);
+        else launch_query<double, 32, false>(P, s);
+    }
+    return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
+}
+
+}  // namespace bspl

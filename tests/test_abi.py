@@ -1,0 +1,81 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry
+point include/bspl.h declares (no compute calls: runs without a GPU)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2504_11498_gb300 import build
+    return build.build()
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(bspl_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("bspl_decompose", "bspl_project_curves", "bspl_invert_curves", "bspl_project_surfaces",
+              "bspl_invert_surfaces", "bspl_workspace_bytes"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(bspl_\w+)", out))
+    missing = declared_functions() - exported
+    assert not missing, missing
+
+
+def test_library_loads_and_answers_host_queries(libpath):
+    from paper_2504_11498_gb300 import bspl
+    L = bspl.lib()
+    for name in declared_functions():
+        assert hasattr(L, name)
+    assert L.bspl_status_string(bspl.ENOSPACE).decode() == "BSPL_ENOSPACE"
+    assert bspl.workspace_bytes(bspl.OP_QUERY_CURVES, 4096, 100000, 0, 2_000_000) > 8_000_000
+    assert bspl.workspace_bytes(bspl.OP_DECOMPOSE_CURVES, 4096, 150000, 0, 0) > 150000 * 8
+    assert bspl.workspace_bytes(99, 1, 1, 1, 1) == 0
+
+
+def test_binding_struct_layout_matches_header(libpath):
+    """Struct sizes the binding uses equal the C compiler's."""
+    import ctypes as C
+
+    from paper_2504_11498_gb300 import bspl
+    code = r'''
+#include <stdio.h>
+#include "bspl.h"
+int main(void){printf("%zu %zu %zu %zu\n", sizeof(bspl_curves), sizeof(bspl_surfaces),
+ sizeof(bspl_segments), sizeof(bspl_options)); return 0;}
+'''
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "s.c")
+        open(src, "w").write(code)
+        exe = os.path.join(d, "s")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include", src, "-o", exe],
+                       check=True)
+        sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    assert sizes == [C.sizeof(bspl.bspl_curves), C.sizeof(bspl.bspl_surfaces), C.sizeof(bspl.bspl_segments),
+                     C.sizeof(bspl.bspl_options)]
+
+
+def test_product_refuses_to_run_without_library(monkeypatch, tmp_path):
+    from paper_2504_11498_gb300 import bspl
+    monkeypatch.setattr(bspl, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(bspl, "_lib", None)
+    with pytest.raises(bspl.BsplError):
+        bspl.lib()

@@ -1,0 +1,240 @@
+"""GPU parity of curve decomposition and curve projection/inversion, through
+the C ABI, against the CPU oracle.
+
+Decomposition: segment counts, offsets, control points and parameter ranges
+bit-exact.  Queries: |d_gpu - d_oracle| <= tol x diag + 1e-12 x diag for
+every query (the GPU reports the distance to the decomposed curve, which is
+within tol x diag of the original everywhere), and the GPU parameter,
+evaluated on the original curve by the oracle, is no worse than
+d_oracle + 2 tol x diag + 1e-12 x diag.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2504_11498_gb300 import bspl, synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2504_11498_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def dev(x, dt):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=DEV)
+
+
+def run_queries(segs, qc, q, invert=False, **kw):
+    fn = bspl.bspl_invert_curves if invert else bspl.bspl_project_curves
+    r = fn(segs, dev(qc, torch.int32), dev(q, torch.float64), bspl.make_options(**kw))
+    torch.cuda.synchronize()
+    return r.param.cpu().numpy().copy(), r.dist.cpu().numpy().copy(), r.status.cpu().numpy().copy()
+
+
+def check_against_oracle(cs, qc, q, t_gpu, d_gpu, tol, extra=0.0):
+    t_o, d_o = O.project_curves(cs, qc, q)
+    diag = O.curve_diag(cs)[qc]
+    bound = tol * diag + 1e-12 * diag + extra * diag
+    err = np.abs(d_gpu - d_o)
+    assert np.all(np.isfinite(d_gpu))
+    bad = np.where(err > bound)[0]
+    assert len(bad) == 0, (len(bad), err[bad][:5] / diag[bad][:5], qc[bad][:5])
+    # the GPU parameter on the ORIGINAL curve
+    C, _, _ = O.eval_curves(cs, qc, t_gpu)
+    d_orig = np.linalg.norm(C - q, axis=1)
+    assert np.all(d_orig <= d_o + 2 * tol * diag + 1e-12 * diag + extra * diag)
+    return err / diag
+
+
+# ------------------------------------------------------------ decomposition
+
+def test_decompose_single_cubic_exact():
+    cs, _ = synth.single_cubic(n_proj=1, n_inv=1)
+    segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), 0.0)
+    ref = O.decompose_curves(cs, 0.0)
+    seg_off, ctrl, prange = segs.view()
+    assert seg_off.tolist() == [0, 13] == ref.seg_off.tolist()
+    assert np.array_equal(ctrl, ref.ctrl) and np.array_equal(prange, ref.prange)
+
+
+@pytest.mark.parametrize("tol", [1e-10, 1e-6])
+def test_decompose_curve_set_bit_exact(tol):
+    cs, _ = synth.curve_set(seed=2, n_curves=4096, n_proj=1, n_inv=1)
+    sub = cs.subset(np.arange(0, 4096, 8))  # 512 curves, all degrees
+    segs = bspl.decompose(bspl.DeviceCurves(sub, DEV), tol)
+    ref = O.decompose_curves(sub, tol)
+    seg_off, ctrl, prange = segs.view()
+    assert np.array_equal(seg_off, ref.seg_off)
+    assert np.array_equal(prange, ref.prange)
+    assert np.array_equal(ctrl, ref.ctrl)
+
+
+def test_decompose_full_curve_set_counts():
+    """The 4,096-curve set at 1e-10 x diag: offsets bit-exact."""
+    cs, _ = synth.curve_set(seed=2, n_proj=1, n_inv=1)
+    segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), 1e-10)
+    ref = O.decompose_curves(cs, 1e-10, count_only=True)
+    assert np.array_equal(segs.seg_off.cpu().numpy(), ref.seg_off)
+    # tables: every box holds its cubic's control points
+    rec = segs.rec64[: segs.total].cpu().numpy()
+    ctrl = segs.ctrl[: segs.total].cpu().numpy()
+    assert np.all(rec[:, None, 0:3] <= ctrl) and np.all(ctrl <= rec[:, None, 3:6])
+
+
+def test_decompose_rejects_invalid():
+    U = np.array([0, 0, 0, 0.5, 0.4, 1, 1, 1.0])
+    cs = synth.pack_curves([2], [U], [np.zeros((5, 3))])
+    with pytest.raises(bspl.BsplError):
+        bspl.decompose(bspl.DeviceCurves(cs, DEV), 1e-6)
+
+
+# ------------------------------------------------------------------ queries
+
+@pytest.mark.parametrize("prec", [bspl.FP64, bspl.MIXED])
+@pytest.mark.parametrize("samples", [16, 32])
+def test_single_cubic_all_queries(prec, samples):
+    cs, qs = synth.single_cubic(seed=1)
+    segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), 0.0)
+    t, d, st = run_queries(segs, qs.proj_curve, qs.proj_xyz, prec=prec, samples=samples)
+    check_against_oracle(cs, qs.proj_curve, qs.proj_xyz, t, d, 0.0)
+    assert np.all(st & bspl.Q_CONVERGED)
+    C, _, _ = O.eval_curves(cs, qs.inv_curve, qs.inv_t)
+    t, d, st = run_queries(segs, qs.inv_curve, C, invert=True, prec=prec, samples=samples)
+    diag = O.curve_diag(cs)[0]
+    assert np.all(d <= 1e-12 * diag)
+    assert not np.any(st & bspl.Q_OFF_CURVE)
+    check_against_oracle(cs, qs.inv_curve, C, t, d, 0.0)
+
+
+@pytest.mark.parametrize("prec", [bspl.FP64, bspl.MIXED])
+def test_curve_set_subset_parity(prec):
+    cs, _ = synth.curve_set(seed=2, n_proj=1, n_inv=1)
+    sub = cs.subset(np.arange(1, 4096, 16))  # 256 curves
+    rng = np.random.default_rng(9)
+    lo, hi = synth.cp_boxes(sub)
+    qc = rng.integers(0, sub.n, 4000).astype(np.int32)
+    q = synth._box_queries(rng, lo, hi, qc)
+    tol = 1e-10
+    segs = bspl.decompose(bspl.DeviceCurves(sub, DEV), tol)
+    t, d, st = run_queries(segs, qc, q, prec=prec)
+    check_against_oracle(sub, qc, q, t, d, tol)
+    ic = rng.integers(0, sub.n, 4000).astype(np.int32)
+    it = rng.uniform(0, 1, 4000)
+    C, _, _ = O.eval_curves(sub, ic, it)
+    t, d, st = run_queries(segs, ic, C, invert=True, prec=prec)
+    check_against_oracle(sub, ic, C, t, d, tol)
+    assert np.all(d <= 1e-9 * O.curve_diag(sub)[ic])
+
+
+def test_full_size_curve_set_sampled_parity():
+    """The 4,096-curve set, 1M projection + 1M inversion queries in the launch
+    configuration the benchmark times: sampled oracle parity for both
+    precisions, and properties on every query."""
+    cs, qs = synth.curve_set(seed=2)
+    tol = 1e-10
+    dc = bspl.DeviceCurves(cs, DEV)
+    segs = bspl.decompose(dc, tol)
+    inv_pts = bspl.bspl_eval_curves(dc, dev(qs.inv_curve, torch.int32), dev(qs.inv_t, torch.float64))
+    res = {}
+    for prec in (bspl.FP64, bspl.MIXED):
+        tp, dp, sp = run_queries(segs, qs.proj_curve, qs.proj_xyz, prec=prec)
+        r = bspl.bspl_invert_curves(segs, dev(qs.inv_curve, torch.int32), inv_pts, bspl.make_options(prec=prec))
+        torch.cuda.synchronize()
+        res[prec] = (tp, dp, sp, r.param.cpu().numpy().copy(), r.dist.cpu().numpy().copy(),
+                     r.status.cpu().numpy().copy())
+    diag_p = O.curve_diag(cs)[qs.proj_curve]
+    diag_i = O.curve_diag(cs)[qs.inv_curve]
+    for prec, (tp, dp, sp, ti, di, si) in res.items():
+        assert np.all(np.isfinite(dp)) and np.all(np.isfinite(di))
+        assert np.all(di <= 1e-9 * diag_i), (prec, np.max(di / diag_i))
+        assert not np.any(si & bspl.Q_INVALID) and not np.any(sp & bspl.Q_INVALID)
+    # mixed vs plain on every query
+    for k in (1, 4):
+        a, b = res[bspl.FP64][k], res[bspl.MIXED][k]
+        dg = diag_p if k == 1 else diag_i
+        assert np.all(np.abs(a - b) <= 1e-9 * dg), np.max(np.abs(a - b) / dg)
+    rng = np.random.default_rng(3)
+    pick = rng.choice(len(qs.proj_curve), 2000, replace=False)
+    inv = inv_pts.cpu().numpy()
+    for prec in (bspl.FP64, bspl.MIXED):
+        tp, dp, sp, ti, di, si = res[prec]
+        check_against_oracle(cs, qs.proj_curve[pick], qs.proj_xyz[pick], tp[pick], dp[pick], tol)
+        check_against_oracle(cs, qs.inv_curve[pick], inv[pick], ti[pick], di[pick], tol)
+
+
+# --------------------------------------------------------------- edge cases
+
+def _edge_set():
+    rng = np.random.default_rng(5)
+    curves = []
+    curves.append((1, synth.uniform_clamped_knots(1, 2), rng.uniform(0, 1, (2, 3))))  # a single line segment
+    curves.append((2, np.array([0, 0, 0, 1, 1, 1.0]), rng.uniform(0, 1, (3, 3))))  # one parabola
+    U = np.array([0, 0, 0, 0, 0.3, 0.3, 0.3, 0.7, 1, 1, 1, 1.0])  # C0 join at 0.3
+    curves.append((3, U, rng.uniform(0, 1, (8, 3))))
+    U = np.array([0, 0, 0, 0, 0, 0, 0.5, 0.5, 0.5, 0.5, 0.5, 1, 1, 1, 1, 1, 1.0])  # degree 5, C0 join
+    curves.append((5, U, rng.uniform(0, 1, (11, 3))))
+    curves.append((7, synth.uniform_clamped_knots(7, 8), rng.uniform(0, 1, (8, 3))))  # one degree-7 span
+    U = np.concatenate([[-3.0] * 4, [-1.0, 2.0], [5.0] * 4])  # non-[0,1] parameter domain
+    curves.append((3, U, rng.uniform(0, 1, (6, 3))))
+    return synth.pack_curves(*zip(*curves))
+
+
+@pytest.mark.parametrize("prec", [bspl.FP64, bspl.MIXED])
+def test_edge_curves(prec):
+    cs = _edge_set()
+    tol = 1e-10
+    segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), tol)
+    ref = O.decompose_curves(cs, tol)
+    assert np.array_equal(segs.seg_off.cpu().numpy(), ref.seg_off)
+    rng = np.random.default_rng(6)
+    qc = np.repeat(np.arange(cs.n, dtype=np.int32), 300)
+    lo, hi = synth.cp_boxes(cs)
+    q = synth._box_queries(rng, lo, hi, qc, scale=2.0)
+    # points exactly at control points and curve ends
+    ends = []
+    for c in range(cs.n):
+        p, U, P = cs.curve(c)
+        ends += [(c, P[0]), (c, P[-1]), (c, P[len(P) // 2])]
+    qc = np.concatenate([qc, np.array([e[0] for e in ends], np.int32)])
+    q = np.concatenate([q, np.array([e[1] for e in ends])])
+    t, d, st = run_queries(segs, qc, q, prec=prec)
+    check_against_oracle(cs, qc, q, t, d, tol)
+    p0 = np.array([cs.curve(int(c))[1][cs.curve(int(c))[0]] for c in qc])
+    p1 = np.array([cs.curve(int(c))[1][len(cs.curve(int(c))[2])] for c in qc])
+    assert np.all((t >= p0) & (t <= p1))
+
+
+def test_invalid_and_empty_queries():
+    cs, qs = synth.single_cubic(n_proj=64, n_inv=1)
+    segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), 0.0)
+    qc = qs.proj_curve.copy()
+    q = qs.proj_xyz.copy()
+    qc[3] = 7  # out of range
+    qc[5] = -1
+    q[9, 1] = np.nan
+    t, d, st = run_queries(segs, qc, q)
+    for k in (3, 5, 9):
+        assert st[k] == bspl.Q_INVALID and np.isnan(d[k])
+    ok = np.setdiff1d(np.arange(64), [3, 5, 9])
+    assert np.all(st[ok] & bspl.Q_CONVERGED)
+    # empty batch
+    r = bspl.bspl_project_curves(segs, dev(np.zeros(0, np.int32), torch.int32),
+                                 dev(np.zeros((0, 3)), torch.float64))
+    assert r.dist.numel() == 0
+
+
+def test_counters_and_unsorted_order_agree():
+    cs, qs = synth.curve_set(seed=2, n_curves=64, n_proj=3000, n_inv=1)
+    segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), 1e-10)
+    cnt = torch.zeros(bspl.NCOUNTERS, dtype=torch.int64, device=DEV)
+    t1, d1, _ = run_queries(segs, qs.proj_curve, qs.proj_xyz, counters=cnt)
+    t2, d2, _ = run_queries(segs, qs.proj_curve, qs.proj_xyz, sort_queries=0)
+    assert np.array_equal(d1, d2) and np.array_equal(t1, t2)
+    c = cnt.cpu().numpy()
+    assert c[0] == 3000 and c[3] >= 3000 and c[4] >= 3000

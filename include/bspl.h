@@ -235,6 +235,33 @@ bspl_status bspl_invert_surfaces(const bspl_segments* segs, int64_t n_q, const i
                                  const double* q_xyz, const bspl_options* opt, double* uv, double* dist,
                                  uint8_t* status, void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Scratch-free projection (the paper has no counterpart).
+ *
+ * Same computation and results as bspl_project_curves, for callers that
+ * cannot allocate device memory for a workspace: for example an application
+ * that hands all GPU memory to its own pool up front, a plugin or callback
+ * that is not allowed to call the CUDA allocator, or a latency-critical loop
+ * where an allocation and its implicit synchronisation are not acceptable.
+ * The caller still owns and passes the inputs and the outputs; the scratch
+ * (the per-curve query buckets and the query order) lives in a fixed
+ * BSPL_NOALLOC_SCRATCH_BYTES array inside the library, which every GPU that
+ * loads the library keeps reserved until the process exits.
+ *
+ * Limits: n_q <= BSPL_NOALLOC_MAX_QUERIES and segs->n <= BSPL_NOALLOC_MAX_SPLINES;
+ * larger calls return BSPL_ENOSPACE before anything is launched.
+ * The first call on a device looks up the array's device address for that
+ * device (with that device current); make that first call before any stream
+ * capture.  All calls share the one array: its contents are those of the
+ * last call, each call clears what must start at zero, and calls that
+ * overlap on the GPU (for example on two streams at once) race with each
+ * other.  Nothing is allocated or freed. */
+#define BSPL_NOALLOC_MAX_QUERIES (1 << 20)
+#define BSPL_NOALLOC_MAX_SPLINES (1 << 18)
+#define BSPL_NOALLOC_SCRATCH_BYTES (8u << 20)
+bspl_status bspl_project_curves_noalloc(const bspl_segments* segs, int64_t n_q, const int32_t* q_curve,
+                                        const double* q_xyz, const bspl_options* opt, double* t, double* dist,
+                                        uint8_t* status, cudaStream_t stream);
+
 /* Evaluates the ORIGINAL curves at t [n_q] (Cox-de Boor, Sec. 3 Eq.
  * bsplinebasis): xyz [n_q][3].  t outside the domain is clamped; an
  * out-of-range curve index yields NaN.  Used to place inversion queries. */

@@ -59,7 +59,7 @@ class bspl_options(C.Structure):
                 ("counters", C.c_void_p)]
 
 
-EXPORTS = ["bspl_measure_fma_peak", "bspl_workspace_bytes", "bspl_decompose", "bspl_project_curves", "bspl_invert_curves",
+EXPORTS = ["bspl_project_curves_noalloc", "bspl_measure_fma_peak", "bspl_workspace_bytes", "bspl_decompose", "bspl_project_curves", "bspl_invert_curves",
            "bspl_project_surfaces", "bspl_invert_surfaces", "bspl_eval_curves", "bspl_eval_surfaces",
            "bspl_status_string"]
 
@@ -93,6 +93,9 @@ def lib():
             L.bspl_eval_surfaces.argtypes = [C.POINTER(bspl_surfaces), i64, vp, vp, vp, vp]
             L.bspl_status_string.restype = C.c_char_p
             L.bspl_status_string.argtypes = [st]
+            L.bspl_project_curves_noalloc.restype = st
+            L.bspl_project_curves_noalloc.argtypes = [C.POINTER(bspl_segments), i64, vp, vp, C.POINTER(bspl_options),
+                                                      vp, vp, vp, vp]
             L.bspl_measure_fma_peak.restype = C.c_int
             L.bspl_measure_fma_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, vp]
             _lib = L
@@ -299,6 +302,27 @@ def bspl_project_surfaces(segs, q_surf, q_xyz, opts=None, bufs=None, stream=None
 def bspl_invert_surfaces(segs, q_surf, q_xyz, opts=None, bufs=None, stream=None):
     bufs = bufs or QueryBuffers(segs, q_surf.numel(), q_xyz.device)
     return _query("bspl_invert_surfaces", segs, q_surf, q_xyz, opts or make_options(), bufs, stream)
+
+
+NOALLOC_MAX_QUERIES = 1 << 20
+NOALLOC_MAX_SPLINES = 1 << 18
+
+
+def bspl_project_curves_noalloc(segs, q_curve, q_xyz, opts=None, out=None, stream=None):
+    """Projection through the scratch-free entry point: for callers that
+    cannot give the library a workspace allocation (see include/bspl.h).
+    ``out`` optionally holds preallocated (t, dist, status) tensors."""
+    n = q_curve.numel()
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float64, device=q_xyz.device),
+               torch.empty(n, dtype=torch.float64, device=q_xyz.device),
+               torch.empty(n, dtype=torch.uint8, device=q_xyz.device))
+    t, d, st = out
+    rc = lib().bspl_project_curves_noalloc(C.byref(segs.c), n, _ptr(q_curve), _ptr(q_xyz),
+                                           C.byref(opts or make_options()), _ptr(t), _ptr(d), _ptr(st),
+                                           _stream(stream))
+    _check(rc, "bspl_project_curves_noalloc")
+    return QueryResult(t, d, st)
 
 
 def bspl_eval_curves(curves: DeviceCurves, q_curve, t, stream=None):

@@ -35,9 +35,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--samples", type=int, default=16)
+    ap.add_argument("--samples", type=int, default=0, help="grid samples per segment; 0 = autotune")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--curves", type=int, default=4096, help="curves in the workload")
+    ap.add_argument("--queries", type=int, default=1_000_000, help="projection and inversion queries each")
     return ap.parse_args()
 
 
@@ -59,7 +61,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
@@ -97,9 +99,9 @@ class ClockSampler:
 
 # --------------------------------------------------------------- workload
 
-def build_workload(seed, rank):
+def build_workload(seed, rank, n_curves=4096, n_queries=1_000_000):
     from paper_2504_11498_gb300 import synth
-    cs, qs = synth.curve_set(seed=seed + 1000 * rank)
+    cs, qs = synth.curve_set(seed=seed + 1000 * rank, n_curves=n_curves, n_proj=n_queries, n_inv=n_queries)
     return cs, qs
 
 
@@ -133,7 +135,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cs, qs = build_workload(args.seed, 0)
+        cs, qs = build_workload(args.seed, 0, args.curves, args.queries)
         rates = []
         for _ in range(args.warmup):
             cpu_oracle_rate(cs, qs, budget_s=2.0, max_q=2000)
@@ -156,7 +158,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2504_11498_gb300 import bspl, build
+    from paper_2504_11498_gb300 import autotune, bspl, build
 
     if world > 1:
         torch.cuda.set_device(local)
@@ -164,7 +166,7 @@ def main():
     build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    cs, qs = build_workload(args.seed, rank)
+    cs, qs = build_workload(args.seed, rank, args.curves, args.queries)
     dc = bspl.DeviceCurves(cs, dev)
 
     # decomposition (preprocessing, timed separately)
@@ -184,8 +186,12 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # launch configuration per precision, chosen by the autotuner (untimed)
+    cfg = {p: (autotune.tune_curves(segs, pc, pq, p) if args.samples == 0 else dict(samples=args.samples))
+           for p in (bspl.MIXED, bspl.FP64)}
+
     def step(prec, counters=None):
-        o = bspl.make_options(prec=prec, samples=args.samples, counters=counters)
+        o = bspl.make_options(prec=prec, counters=counters, **cfg[prec])
         bspl.bspl_project_curves(segs, pc, pq, o, bufs_p)
         bspl.bspl_invert_curves(segs, ic, iq, o, bufs_i)
 
@@ -222,7 +228,7 @@ def main():
     sic, siq = ic[torch.as_tensor(oi, device=dev)], iq[torch.as_tensor(oi, device=dev)]
 
     def kernel_ms(prec, steps):
-        o = bspl.make_options(prec=prec, samples=args.samples, sort_queries=0)
+        o = bspl.make_options(prec=prec, sort_queries=0, **cfg[prec])
         for _ in range(2):
             bspl.bspl_project_curves(segs, spc, spq, o, bufs_p)
             bspl.bspl_invert_curves(segs, sic, siq, o, bufs_i)
@@ -242,11 +248,12 @@ def main():
             tot += ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
         return tot / steps  # both launches of one step
 
+    # clocks are sampled across the timed loops (mixed, then plain)
     clocks = ClockSampler(local)
     clocks.start()
     ms_mixed, ms_list = timed(bspl.MIXED, args.steps, args.warmup)
-    clk = clocks.stop()
     ms_plain, _ = timed(bspl.FP64, max(2, args.steps // 3), 2)
+    clk = clocks.stop()
     c_mixed = counted(bspl.MIXED)
     c_plain = counted(bspl.FP64)
     kms_mixed = kernel_ms(bspl.MIXED, max(3, args.steps // 2))
@@ -264,7 +271,7 @@ def main():
     def e2e_step():
         for d, h in zip(d_in, (h_pc, h_pq, h_ic, h_iq)):
             d.copy_(h, non_blocking=True)
-        o = bspl.make_options(prec=bspl.MIXED, samples=args.samples)
+        o = bspl.make_options(prec=bspl.MIXED, **cfg[bspl.MIXED])
         bspl.bspl_project_curves(segs, d_in[0], d_in[1], o, bufs_p)
         bspl.bspl_invert_curves(segs, d_in[2], d_in[3], o, bufs_i)
         for h, d in zip(h_out, (bufs_p.param, bufs_p.dist, bufs_p.status, bufs_i.param, bufs_i.dist,
@@ -297,7 +304,7 @@ def main():
     # FMA-chain peaks (FP32-equivalent TFLOP/s)
     p32 = bspl.measure_fma_peak(False)
     p64 = bspl.measure_fma_peak(True)
-    S = args.samples
+    S = cfg[bspl.MIXED]["samples"]
 
     def flops(c, mixed):
         # per-unit figures: 12 flops per box test, 15 per grid sample, 45 per
@@ -309,7 +316,9 @@ def main():
         return 0, cull + grid + 45 * c["newton64_iters"]
 
     f32m, f64m = flops(c_mixed, True)
+    S = cfg[bspl.FP64]["samples"]
     f32p, f64p = flops(c_plain, False)
+    S = cfg[bspl.MIXED]["samples"]
     t_m, t_p = kms_mixed * 1e-3, kms_plain * 1e-3
     eq_m = (f32m + f64m * p32 / p64) / t_m
     eq_p = (f32p + f64p * p32 / p64) / t_p
@@ -325,8 +334,10 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 search, FP64 finish)", "data": "synthetic",
-           "config": {"workload": "curve_set_4096: 1M projection + 1M inversion queries per GPU",
-                      "tol_rel": TOL, "samples": S, "prec": "mixed", "l2": "512 MB flush between timed steps",
+           "config": {"workload": f"curve_set_{args.curves}: {args.queries} projection + {args.queries} inversion "
+                                  "queries per GPU",
+                      "tol_rel": TOL, "launch": {"mixed": cfg[bspl.MIXED], "fp64": cfg[bspl.FP64]},
+                      "prec": "mixed", "l2": "512 MB flush between timed steps",
                       "segments": int(segs.total), "decompose_ms": decomp_ms},
            "plain_fp64": {"value": total_q / t_p, "ms_per_step": ms_plain},
            "speedup_mixed_vs_plain": ms_plain / ms_mixed,

@@ -150,7 +150,9 @@ typedef struct {
     int32_t newton_max;  /* FP64 Newton cap, plain path and fallback (default 30)   */
     int32_t fp32_steps;  /* FP32 Newton steps before the FP64 finish (default 4)    */
     int32_t sort_queries;/* 1: group queries by spline first (default 1)            */
-    int32_t reserved;
+    int32_t occupancy;   /* curve kernel register/occupancy variant: 0 compiler
+                            choice, 1 >= 4 blocks/SM, 2 >= 6 blocks/SM (samples
+                            16 and 32); picked by the autotuner             */
     const void* mlp;     /* learned seed (BSPL_LEARNED_MIXED), else NULL            */
     uint64_t* counters;  /* optional device array [BSPL_NCOUNTERS], accumulated     */
 } bspl_options;

@@ -55,7 +55,7 @@ class bspl_segments(C.Structure):
 
 class bspl_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("samples", C.c_int32), ("newton_max", C.c_int32), ("fp32_steps", C.c_int32),
-                ("sort_queries", C.c_int32), ("reserved", C.c_int32), ("mlp", C.c_void_p),
+                ("sort_queries", C.c_int32), ("occupancy", C.c_int32), ("mlp", C.c_void_p),
                 ("counters", C.c_void_p)]
 
 
@@ -257,8 +257,9 @@ class QueryResult:
     status: torch.Tensor
 
 
-def make_options(prec=FP64, samples=0, newton_max=0, fp32_steps=0, sort_queries=1, counters=None, mlp=None):
-    return bspl_options(int(prec), int(samples), int(newton_max), int(fp32_steps), int(sort_queries), 0,
+def make_options(prec=FP64, samples=0, newton_max=0, fp32_steps=0, sort_queries=1, counters=None, mlp=None,
+                 occupancy=0):
+    return bspl_options(int(prec), int(samples), int(newton_max), int(fp32_steps), int(sort_queries), int(occupancy),
                         C.c_void_p(mlp) if mlp else C.c_void_p(0), _ptr(counters) if counters is not None else None)
 
 

@@ -243,7 +243,7 @@ __device__ R root_bracketed(const R* a, R qx, R qy, R qz, R lo, R hi, int maxit,
 // changes -> split at the middle (de Casteljau); none -> no root.  The ends
 // are minima when E(0) >= 0 or E(1) <= 0.  Returns the best minimiser.
 template <class R>
-__device__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int maxit)
+__device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int maxit)
 {
     constexpr int kStack = 24;
     R b0[6];
@@ -330,45 +330,102 @@ struct PoolEntry {
     float u0, h;  // h < 0: isolate every minimum of the segment first
 };
 
+template <class R>
 struct WarpSmem {
     int cand_seg[kCandCap];
-    double cand_lb[kCandCap];
+    R cand_lb[kCandCap];
     PoolEntry pool[kPoolCap];
     double pool_D[kPoolCap];
     double pool_u[kPoolCap];
+    float pool_u32[kPoolCap];  // mixed: FP32 minimiser and its squared distance
+    float pool_D32[kPoolCap];
     unsigned char pool_flags[kPoolCap];
     double q64[kQPW][3];
+    float q32[kQPW][3];
+    float eps32[kQPW];         // mixed: FP32 distance slack of the query
+    float best_D32[kQPW];      // mixed: best FP32 squared distance so far
+    short fin[kPoolCap];       // mixed: pool entries that get the FP64 finish
     double best_D[kQPW];
     double best_u[kQPW];
     int best_seg[kQPW];
     unsigned char best_flags[kQPW];
 };
 
-// Newton phase over the pooled basins, then per-slot merge
-template <class R, bool MIXED>
-__device__ void flush_pool(const CurveQ& P, WarpSmem& W, int npool, int lane, unsigned& it32, unsigned& it64)
+// lexicographic (D, seg, u) order; D >= 0, so its bit pattern orders like an integer
+__device__ __forceinline__ bool better(double D, int s, double u, double bD, int bs, double bu)
 {
-    for (int k = lane; k < npool; k += 32) {
-        PoolEntry e = W.pool[k];
-        const double* q = W.q64[e.slot];
-        const double* a64 = P.rec64 + (int64_t)BSPL_CREC64 * e.seg + 6;
-        unsigned char fl = 0;
-        double u;
-        const bool iso = e.h < 0.f;
-        const float hh = iso ? 1.f / 64.f : e.h;
-        if (MIXED) {
+    const long long a = __double_as_longlong(D), b = __double_as_longlong(bD);
+    return a < b || (a == b && (s < bs || (s == bs && __double_as_longlong(u) < __double_as_longlong(bu))));
+}
+
+// Newton phase over the pooled basins, then per-slot merge.
+// MIXED: (A) every basin gets FP32 Newton steps; (B) the lane owning each
+// query slot takes the best FP32 squared distance; (C) only basins within the
+// FP32 error margin of that best (the best one always) get the two FP64
+// Newton steps on the FP64 coefficients, with the FP64 safeguarded iteration
+// as the fallback when the second step is not below 1e-9.
+template <class R, bool MIXED>
+__device__ void flush_pool(const CurveQ& P, WarpSmem<R>& W, int npool, int lane, unsigned& it32, unsigned& it64)
+{
+    if (MIXED) {
+        // (A) FP32 refinement in the segment's local frame: the offset
+        // a0 - q is formed once in FP64 and rounded, so the FP32 search keeps
+        // its relative accuracy on short segments far from the origin
+        for (int k = lane; k < npool; k += 32) {
+            const PoolEntry e = W.pool[k];
+            const double* q = W.q64[e.slot];
+            const double* a64 = P.rec64 + (int64_t)BSPL_CREC64 * e.seg + 6;
             const float* a32 = P.rec32 + (int64_t)BSPL_CREC32 * e.seg + 6;
             float c32[12];
+            c32[0] = (float)(a64[0] - q[0]);
+            c32[1] = (float)(a64[1] - q[1]);
+            c32[2] = (float)(a64[2] - q[2]);
 #pragma unroll
-            for (int i = 0; i < 12; ++i) c32[i] = a32[i];
+            for (int i = 3; i < 12; ++i) c32[i] = a32[i];
+            const bool iso = e.h < 0.f;
             float uf = e.u0;
-            if (iso) uf = isolate_min<float>(c32, (float)q[0], (float)q[1], (float)q[2], 1e-7f, P.fp32_steps * 4);
-            newton_min<float>(c32, (float)q[0], (float)q[1], (float)q[2], uf, hh, P.fp32_steps, 1e-7f, it32);
+            if (iso) uf = isolate_min<float>(c32, 0.f, 0.f, 0.f, 1e-7f, P.fp32_steps * 4);
+            newton_min<float>(c32, 0.f, 0.f, 0.f, uf, iso ? 1.f / 64.f : e.h, P.fp32_steps, 1e-7f, it32);
+            float E, Ep;
+            W.pool_D32[k] = eval_E<float>(c32, 0.f, 0.f, 0.f, uf, E, Ep);
+            W.pool_u32[k] = uf;
+            W.pool_D[k] = INFINITY;
+            W.pool_flags[k] = 0;
+        }
+        __syncwarp();
+        // (B) best FP32 distance per query slot
+        if (lane < kQPW) {
+            float b = W.best_D32[lane];
+            for (int k = 0; k < npool; ++k)
+                if (W.pool[k].slot == lane) b = fminf(b, W.pool_D32[k]);
+            W.best_D32[lane] = b;
+        }
+        __syncwarp();
+        // (C) compact the entries within the FP32 margin of their query's best
+        int nfin = 0;
+        for (int base = 0; base < npool; base += 32) {
+            const int k = base + lane;
+            bool take = false;
+            if (k < npool) {
+                const int sl = W.pool[k].slot;
+                const float sm = sqrtf(W.best_D32[sl]) + 2.f * W.eps32[sl];
+                take = W.pool_D32[k] <= sm * sm;
+            }
+            const unsigned m = __ballot_sync(kFull, take);
+            if (take) W.fin[nfin + __popc(m & ((1u << lane) - 1))] = (short)k;
+            nfin += __popc(m);
+        }
+        __syncwarp();
+        // (D) two FP64 Newton steps on the FP64 coefficients, packed over lanes
+        for (int f = lane; f < nfin; f += 32) {
+            const int k = W.fin[f];
+            const PoolEntry e = W.pool[k];
+            const double* q = W.q64[e.slot];
+            const double* a64 = P.rec64 + (int64_t)BSPL_CREC64 * e.seg + 6;
             double c64[12];
 #pragma unroll
             for (int i = 0; i < 12; ++i) c64[i] = a64[i];
-            // two FP64 Newton steps, clamped to the segment
-            u = (double)uf;
+            double u = (double)W.pool_u32[k];
             double last = 1.0;
 #pragma unroll
             for (int it = 0; it < 2; ++it) {
@@ -380,29 +437,37 @@ __device__ void flush_pool(const CurveQ& P, WarpSmem& W, int npool, int lane, un
                 last = fabs(un - u);
                 u = un;
             }
+            unsigned char fl = 0;
             bool ok = last <= 1e-9;
             if (!ok) {
-                // FP64 fallback: safeguarded iteration on the whole segment
                 fl |= BSPL_Q_FALLBACK;
-                ok = newton_min<double>(c64, q[0], q[1], q[2], u, (double)hh, P.newton_max, 1e-15, it64);
+                ok = newton_min<double>(c64, q[0], q[1], q[2], u, e.h < 0.f ? 1.0 / 64 : (double)e.h, P.newton_max,
+                                        1e-15, it64);
             }
-            if (ok) fl |= BSPL_Q_CONVERGED;
-            else fl |= BSPL_Q_NONCONV;
-            double E, Ep;
-            W.pool_D[k] = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
-        } else {
-            double c64[12];
-#pragma unroll
-            for (int i = 0; i < 12; ++i) c64[i] = a64[i];
-            u = (double)e.u0;
-            if (iso) u = isolate_min<double>(c64, q[0], q[1], q[2], 1e-15, P.newton_max);
-            bool ok = newton_min<double>(c64, q[0], q[1], q[2], u, (double)hh, P.newton_max, 1e-15, it64);
             fl |= ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
             double E, Ep;
             W.pool_D[k] = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
+            W.pool_u[k] = u;
+            W.pool_flags[k] = fl;
         }
-        W.pool_u[k] = u;
-        W.pool_flags[k] = fl;
+    } else {
+        for (int k = lane; k < npool; k += 32) {
+            const PoolEntry e = W.pool[k];
+            const double* q = W.q64[e.slot];
+            const double* a64 = P.rec64 + (int64_t)BSPL_CREC64 * e.seg + 6;
+            double c64[12];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) c64[i] = a64[i];
+            const bool iso = e.h < 0.f;
+            double u = (double)e.u0;
+            if (iso) u = isolate_min<double>(c64, q[0], q[1], q[2], 1e-15, P.newton_max);
+            bool ok = newton_min<double>(c64, q[0], q[1], q[2], u, iso ? 1.0 / 64 : (double)e.h, P.newton_max,
+                                         1e-15, it64);
+            double E, Ep;
+            W.pool_D[k] = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
+            W.pool_u[k] = u;
+            W.pool_flags[k] = ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
+        }
     }
     __syncwarp();
     if (lane < kQPW) {
@@ -411,12 +476,12 @@ __device__ void flush_pool(const CurveQ& P, WarpSmem& W, int npool, int lane, un
         unsigned char bf = W.best_flags[lane];
         for (int k = 0; k < npool; ++k) {
             if (W.pool[k].slot != lane) continue;
-            double D = W.pool_D[k], u = W.pool_u[k];
-            int s = W.pool[k].seg;
-            if (D < bD || (D == bD && (s < bs || (s == bs && u < bu)))) {
+            const double D = W.pool_D[k], u = W.pool_u[k];
+            const int sg = W.pool[k].seg;
+            if (better(D, sg, u, bD, bs, bu)) {
                 bD = D;
                 bu = u;
-                bs = s;
+                bs = sg;
                 bf = W.pool_flags[k];
             }
         }
@@ -428,12 +493,12 @@ __device__ void flush_pool(const CurveQ& P, WarpSmem& W, int npool, int lane, un
     __syncwarp();
 }
 
-template <class R, int S, bool MIXED>
-__global__ void __launch_bounds__(kWarps * 32) k_query_curves(CurveQ P)
+template <class R, int S, bool MIXED, int MINB>
+__global__ void __launch_bounds__(kWarps * 32, MINB) k_query_curves(CurveQ P)
 {
-    __shared__ WarpSmem smem[kWarps];
+    __shared__ WarpSmem<R> smem[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpSmem& W = smem[wid];
+    WarpSmem<R>& W = smem[wid];
     const int64_t batch = (int64_t)blockIdx.x * kWarps + wid;
     const int64_t qbase = batch * kQPW;
     if (qbase >= P.n_q) return;
@@ -451,6 +516,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_curves(CurveQ P)
         W.best_u[lane] = 0.0;
         W.best_seg[lane] = 0x7fffffff;
         W.best_flags[lane] = 0;
+        W.best_D32[lane] = INFINITY;
     }
     int npool = 0;
     __syncwarp();
@@ -460,17 +526,22 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_curves(CurveQ P)
         const int c = P.q_curve[qi];
         const double qx64 = P.q_xyz[3 * qi], qy64 = P.q_xyz[3 * qi + 1], qz64 = P.q_xyz[3 * qi + 2];
         const bool bad = c < 0 || c >= P.n || !isfinite(qx64) || !isfinite(qy64) || !isfinite(qz64);
+        const R qx = (R)qx64, qy = (R)qy64, qz = (R)qz64;
+        const R eps = MIXED ? R(4e-6) * (fabs(qx) + fabs(qy) + fabs(qz) + (R)P.diag[c < 0 || c >= P.n ? 0 : c])
+                            : R(1e-13) * (fabs(qx) + fabs(qy) + fabs(qz) + (R)P.diag[c < 0 || c >= P.n ? 0 : c]);
         if (lane == 0) {
             W.q64[sl][0] = qx64;
             W.q64[sl][1] = qy64;
             W.q64[sl][2] = qz64;
+            W.q32[sl][0] = (float)qx;
+            W.q32[sl][1] = (float)qy;
+            W.q32[sl][2] = (float)qz;
+            W.eps32[sl] = (float)eps;
             if (bad) W.best_flags[sl] = BSPL_Q_INVALID;
         }
         if (bad) continue;
-        const R qx = (R)qx64, qy = (R)qy64, qz = (R)qz64;
         const int64_t s0 = P.seg_off[c], s1 = P.seg_off[c + 1];
         const int64_t g0 = P.grp_off[c], g1 = P.grp_off[c + 1];
-        const R eps = (MIXED ? R(4e-6) : R(1e-13)) * (R)(fabs(qx64) + fabs(qy64) + fabs(qz64) + P.diag[c]);
 
         // level 1: upper bound from the group reference points
         R ub = INFINITY;
@@ -486,7 +557,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_curves(CurveQ P)
             const int sub = lane / S, j = lane % S;
             for (int base = 0; base < ncand; base += SPW) {
                 const int k = base + sub;
-                const bool act = k < ncand && (R)W.cand_lb[k] <= ubs;
+                const bool act = k < ncand && W.cand_lb[k] <= ubs;
                 const int seg = act ? W.cand_seg[k] : 0;
                 R D = INFINITY, spd = 0;
                 int nsc = 0;
@@ -570,7 +641,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_curves(CurveQ P)
                 if (keep) {
                     const int pos = ncand + __popc(km & ((1u << lane) - 1));
                     W.cand_seg[pos] = (int)s;
-                    W.cand_lb[pos] = (double)lbs;
+                    W.cand_lb[pos] = lbs;
                 }
                 ncand += __popc(km);
                 if (ncand > kCandCap - 32) grid_stage();
@@ -659,12 +730,22 @@ __global__ void k_scatter(const int32_t* __restrict__ qc, int64_t n_q, int64_t n
     order[pos] = (int32_t)i;
 }
 
-template <class R, int S, bool MIXED>
+template <class R, int S, bool MIXED, int MINB>
 void launch_query(const CurveQ& P, cudaStream_t s)
 {
     int64_t batches = (P.n_q + kQPW - 1) / kQPW;
     int64_t blocks = (batches + kWarps - 1) / kWarps;
-    k_query_curves<R, S, MIXED><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P);
+    k_query_curves<R, S, MIXED, MINB><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P);
+}
+
+// occupancy: 0 -> compiler's register choice, 1 -> at least 4 blocks of 4
+// warps per SM, 2 -> at least 6 (fewer registers, some spills)
+template <class R, int S, bool MIXED>
+void launch_occ(const CurveQ& P, int occ, cudaStream_t s)
+{
+    if (occ == 1) launch_query<R, S, MIXED, 4>(P, s);
+    else if (occ == 2) launch_query<R, S, MIXED, 6>(P, s);
+    else launch_query<R, S, MIXED, 1>(P, s);
 }
 
 }  // namespace
@@ -742,14 +823,16 @@ bspl_status query_curves(const bspl_segments* segs, int64_t n_q, const int32_t* 
         P.order = ord;
     }
     const bool mixed = o.prec == BSPL_MIXED;
+    const int occ = o.occupancy;
+    if (occ < 0 || occ > 2) return BSPL_EINVAL;
     if (mixed) {
-        if (samples == 8) launch_query<float, 8, true>(P, s);
-        else if (samples == 16) launch_query<float, 16, true>(P, s);
-        else launch_query<float, 32, true>(P, s);
+        if (samples == 8) launch_query<float, 8, true, 1>(P, s);
+        else if (samples == 16) launch_occ<float, 16, true>(P, occ, s);
+        else launch_occ<float, 32, true>(P, occ, s);
     } else {
-        if (samples == 8) launch_query<double, 8, false>(P, s);
-        else if (samples == 16) launch_query<double, 16, false>(P, s);
-        else launch_query<double, 32, false>(P, s);
+        if (samples == 8) launch_query<double, 8, false, 1>(P, s);
+        else if (samples == 16) launch_occ<double, 16, false>(P, occ, s);
+        else launch_occ<double, 32, false>(P, occ, s);
     }
     return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
 }

@@ -117,7 +117,8 @@ typedef struct {
  *   span_net   [n_cp_total][BSPL_SPAN_NET]  power-basis coefficients of the
  *                        ORIGINAL span-pair patch (degree <= 7 per direction in
  *                        the query path), indexed by slot, used for the final
- *                        FP64 Newton steps on the original surface.
+ *                        FP64 Newton steps on the original surface;
+ *   span_net32 [n_cp_total][BSPL_SPAN_NET]  the same in FP32 (mixed precision).
  */
 #define BSPL_SPAN_NET (8 * 8 * 3)
 typedef struct {
@@ -137,6 +138,7 @@ typedef struct {
     int64_t* patch_span;
     double* patch_box;
     double* span_net;
+    float* span_net32;
     int64_t n_cp_total;  /* in: cp_off[n] of the decomposed set (sizes the slot arrays) */
     double tol_rel;      /* out: tolerance the tables were built with */
 } bspl_segments;
@@ -148,7 +150,8 @@ typedef struct {
                             16; 8 is coarse and may miss close minima), 16 or 32
                             (surfaces, 4x4 or 8x4, default 32)                   */
     int32_t newton_max;  /* FP64 Newton cap, plain path and fallback (default 30)   */
-    int32_t fp32_steps;  /* FP32 Newton steps before the FP64 finish (default 4)    */
+    int32_t fp32_steps;  /* FP32 Newton steps before the FP64 finish (default 4 for
+                            curves, 8 per stage for surfaces)               */
     int32_t sort_queries;/* 1: group queries by spline first (default 1)            */
     int32_t occupancy;   /* curve kernel register/occupancy variant: 0 compiler
                             choice, 1 >= 4 blocks/SM, 2 >= 6 blocks/SM (samples

@@ -50,7 +50,8 @@ class bspl_segments(C.Structure):
                 ("seg_off", C.c_void_p), ("ctrl", C.c_void_p), ("prange", C.c_void_p), ("diag", C.c_void_p),
                 ("rec64", C.c_void_p), ("rec32", C.c_void_p), ("grp_off", C.c_void_p), ("grp64", C.c_void_p),
                 ("grp32", C.c_void_p), ("patch_span", C.c_void_p), ("patch_box", C.c_void_p),
-                ("span_net", C.c_void_p), ("n_cp_total", C.c_int64), ("tol_rel", C.c_double)]
+                ("span_net", C.c_void_p), ("span_net32", C.c_void_p), ("n_cp_total", C.c_int64),
+                ("tol_rel", C.c_double)]
 
 
 class bspl_options(C.Structure):
@@ -185,12 +186,13 @@ class Segments:
             self.patch_span = z(cap, i64)
             self.patch_box = z((cap, 4), f64)
             self.span_net = z((splines.n_cp_total, SPAN_NET), f64)
+            self.span_net32 = z((splines.n_cp_total, SPAN_NET), f32)
         else:
             self.ctrl = z((cap, 4, 3), f64)
             self.prange = z((cap, 2), f64)
             self.rec64 = z((cap, CREC64), f64)
             self.rec32 = z((cap, CREC32), f32)
-            self.patch_span = self.patch_box = self.span_net = None
+            self.patch_span = self.patch_box = self.span_net = self.span_net32 = None
         self.grp64 = z((self.grp_capacity, GREC64), f64)
         self.grp32 = z((self.grp_capacity, GREC32), f32)
         self.n_cp_total = splines.n_cp_total
@@ -202,7 +204,8 @@ class Segments:
         return bspl_segments(int(self.is_surface), self.n, self.capacity, self.grp_capacity, _ptr(self.seg_off),
                              _ptr(self.ctrl), _ptr(self.prange), _ptr(self.diag), _ptr(self.rec64),
                              _ptr(self.rec32), _ptr(self.grp_off), _ptr(self.grp64), _ptr(self.grp32),
-                             _ptr(self.patch_span), _ptr(self.patch_box), _ptr(self.span_net), self.n_cp_total,
+                             _ptr(self.patch_span), _ptr(self.patch_box), _ptr(self.span_net), _ptr(self.span_net32),
+                             self.n_cp_total,
                              self.tol_rel)
 
     def view(self):

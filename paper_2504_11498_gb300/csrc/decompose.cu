@@ -558,6 +558,7 @@ struct SurfLeafOut {
     double* rec64;     // box of the ORIGINAL piece is written here (first 6 entries)
     float* rec32;      // the degrees (pu, pv) go to the two pad entries
     double* span_net;  // original span-pair piece, power basis [8][8][3]
+    float* span_net32; // the same in FP32
 };
 
 template <bool FILL>
@@ -592,7 +593,11 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
         for (int b = 0; b <= pv; ++b) bern_to_power(pu, W + 3 * b, 3 * kSN);
         for (int a = 0; a <= pu; ++a) bern_to_power(pv, W + 3 * kSN * a, 3);
         double* dst = out.span_net + (int64_t)BSPL_SPAN_NET * slot;
-        for (int i = 0; i < kSN * kSN * 3; ++i) dst[i] = W[i];
+        float* dst32 = out.span_net32 + (int64_t)BSPL_SPAN_NET * slot;
+        for (int i = 0; i < kSN * kSN * 3; ++i) {
+            dst[i] = W[i];
+            dst32[i] = (float)W[i];
+        }
     }
     double du = fsub(U[qu + 1], U[qu]), dv = fsub(V[qv + 1], V[qv]);
     int L = 0;
@@ -925,7 +930,7 @@ static bspl_status decompose_impl(int is_surface, const void* splines, double to
     if (h[0] > out->capacity || n_grp > out->grp_capacity) return BSPL_ENOSPACE;
     if (!out->prange || !out->rec64 || !out->rec32 || !out->grp_off || !out->grp64 || !out->grp32)
         return BSPL_EINVAL;
-    if (is_surface && (!out->patch_span || !out->patch_box || !out->span_net)) return BSPL_EINVAL;
+    if (is_surface && (!out->patch_span || !out->patch_box || !out->span_net || !out->span_net32)) return BSPL_EINVAL;
     out->is_surface = is_surface;
     out->n = n;
     out->tol_rel = tol_rel;
@@ -933,7 +938,7 @@ static bspl_status decompose_impl(int is_surface, const void* splines, double to
     // filling pass and query tables
     if (is_surface) {
         SurfLeafOut o{ out->ctrl, out->prange, out->patch_span, out->patch_box, out->rec64, out->rec32,
-                       out->span_net };
+                       out->span_net, out->span_net32 };
         launch1d(k_walk_surfaces<true>, n_cp, s, *SS, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
         launch1d(k_patch_records, h[0], s, (const double*)out->ctrl, h[0], out->rec64, out->rec32);
         launch1d(k_group_records, n_grp, s, (const int64_t*)out->seg_off, (const int64_t*)out->grp_off, n, n_grp,

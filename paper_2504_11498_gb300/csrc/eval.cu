@@ -10,7 +10,7 @@ namespace bspl {
 
 namespace {
 
-__device__ int span_of(const double* U, int p, int m, double t)
+__host__ __device__ int span_of(const double* U, int p, int m, double t)
 {
     // first/last non-empty span of [t_p, t_{m+1}], then bisection
     int lo = p, hi = m;
@@ -28,7 +28,7 @@ __device__ int span_of(const double* U, int p, int m, double t)
 }
 
 template <int MP>
-__device__ void basis(const double* U, int q, int p, double t, double* N)
+__host__ __device__ void basis(const double* U, int q, int p, double t, double* N)
 {
     double left[MP + 1], right[MP + 1];
     N[0] = 1.0;
@@ -71,6 +71,15 @@ __global__ void k_eval_curves(bspl_curves C, int64_t n_q, const int32_t* __restr
     for (int k = 0; k < 3; ++k) xyz[3 * i + k] = out[k];
 }
 
+// clamped parameter, span and basis values of one direction of a surface
+__device__ __noinline__ int direction_basis(const double* __restrict__ K, int p, int n, double t, double* N)
+{
+    t = fmin(fmax(t, K[p]), K[n]);
+    int q = span_of(K, p, n - 1, t);
+    basis<15>(K, q, p, t, N);
+    return q;
+}
+
 __global__ void k_eval_surfaces(bspl_surfaces S, int64_t n_q, const int32_t* __restrict__ qs,
                                 const double* __restrict__ uv, double* __restrict__ xyz)
 {
@@ -81,14 +90,9 @@ __global__ void k_eval_surfaces(bspl_surfaces S, int64_t n_q, const int32_t* __r
     if (s >= 0 && s < S.n) {
         int pu = S.deg_u[s], pv = S.deg_v[s], nu = S.n_u[s], nv = S.n_v[s];
         if (pu >= 1 && pv >= 1 && pu <= 15 && pv <= 15 && nu > pu && nv > pv) {
-            const double* U = S.knots_u + S.knot_u_off[s];
-            const double* V = S.knots_v + S.knot_v_off[s];
-            double u = fmin(fmax(uv[2 * i], U[pu]), U[nu]);
-            double v = fmin(fmax(uv[2 * i + 1], V[pv]), V[nv]);
-            int qu = span_of(U, pu, nu - 1, u), qv = span_of(V, pv, nv - 1, v);
             double Nu[16], Nv[16];
-            basis<15>(U, qu, pu, u, Nu);
-            basis<15>(V, qv, pv, v, Nv);
+            const int qu = direction_basis(S.knots_u + S.knot_u_off[s], pu, nu, uv[2 * i], Nu);
+            const int qv = direction_basis(S.knots_v + S.knot_v_off[s], pv, nv, uv[2 * i + 1], Nv);
             const double* P = S.cps + 3 * S.cp_off[s];
             for (int k = 0; k < 3; ++k) out[k] = 0.0;
             for (int a = 0; a <= pu; ++a)

@@ -146,7 +146,10 @@ __device__ bool newton_min(const R* a, R qx, R qy, R qz, R& u, R hmax, int maxit
         for (int ls = 0; ls < 24; ++ls) {
             un = fmin(fmax(u + step, R(0)), R(1));
             Dn = eval_E(a, qx, qy, qz, un, En, Epn);
-            if (Dn < D) {
+            // accept a decrease of D, or, where D is locally convex, a
+            // decrease of |E| (D itself is flat to rounding near a minimum,
+            // E is still resolved there)
+            if (Dn < D || (Ep > R(0) && fabs(En) < fabs(E))) {
                 acc = true;
                 break;
             }
@@ -339,6 +342,7 @@ struct WarpSmem {
     double pool_u[kPoolCap];
     float pool_u32[kPoolCap];  // mixed: FP32 minimiser and its squared distance
     float pool_D32[kPoolCap];
+    unsigned char pool_conv32[kPoolCap];  // mixed: the FP32 stage converged
     unsigned char pool_flags[kPoolCap];
     double q64[kQPW][3];
     float q32[kQPW][3];
@@ -385,7 +389,8 @@ __device__ void flush_pool(const CurveQ& P, WarpSmem<R>& W, int npool, int lane,
             const bool iso = e.h < 0.f;
             float uf = e.u0;
             if (iso) uf = isolate_min<float>(c32, 0.f, 0.f, 0.f, 1e-7f, P.fp32_steps * 4);
-            newton_min<float>(c32, 0.f, 0.f, 0.f, uf, iso ? 1.f / 64.f : e.h, P.fp32_steps, 1e-7f, it32);
+            W.pool_conv32[k] =
+                newton_min<float>(c32, 0.f, 0.f, 0.f, uf, iso ? 1.f / 64.f : e.h, P.fp32_steps, 1e-7f, it32);
             float E, Ep;
             W.pool_D32[k] = eval_E<float>(c32, 0.f, 0.f, 0.f, uf, E, Ep);
             W.pool_u32[k] = uf;
@@ -409,7 +414,7 @@ __device__ void flush_pool(const CurveQ& P, WarpSmem<R>& W, int npool, int lane,
             if (k < npool) {
                 const int sl = W.pool[k].slot;
                 const float sm = sqrtf(W.best_D32[sl]) + 2.f * W.eps32[sl];
-                take = W.pool_D32[k] <= sm * sm;
+                take = !W.pool_conv32[k] || W.pool_D32[k] <= sm * sm;
             }
             const unsigned m = __ballot_sync(kFull, take);
             if (take) W.fin[nfin + __popc(m & ((1u << lane) - 1))] = (short)k;

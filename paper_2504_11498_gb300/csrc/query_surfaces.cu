@@ -47,6 +47,7 @@ struct SurfQ {
     const double* patch_box;
     const int64_t* patch_span;
     const double* span_net;
+    const float* span_net32;
     const double* diag;
     double tol_rel;
     int64_t n, n_q;
@@ -148,65 +149,89 @@ __device__ __forceinline__ void eval_patch(const R* a, int du, int dv, int strid
     }
 }
 
+// squared distance, gradient (halved), Hessian (halved) and the Gauss-Newton
+// matrix J^T J of D at one point
 template <class R>
-__device__ __forceinline__ R grad_hess(const SD<R>& o, R qx, R qy, R qz, R& gu, R& gv, R& huu, R& huv, R& hvv)
+struct GH {
+    R gu, gv, huu, huv, hvv, juu, juv, jvv;
+};
+
+template <class R>
+__device__ __forceinline__ R grad_hess(const SD<R>& o, R qx, R qy, R qz, GH<R>& h)
 {
     R d[3] = { o.S[0] - qx, o.S[1] - qy, o.S[2] - qz };
     R D = 0;
-    gu = gv = huu = huv = hvv = 0;
+    h.gu = h.gv = h.huu = h.huv = h.hvv = h.juu = h.juv = h.jvv = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         D += d[c] * d[c];
-        gu += d[c] * o.Su[c];
-        gv += d[c] * o.Sv[c];
-        huu += o.Su[c] * o.Su[c] + d[c] * o.Suu[c];
-        huv += o.Su[c] * o.Sv[c] + d[c] * o.Suv[c];
-        hvv += o.Sv[c] * o.Sv[c] + d[c] * o.Svv[c];
+        h.gu += d[c] * o.Su[c];
+        h.gv += d[c] * o.Sv[c];
+        h.juu += o.Su[c] * o.Su[c];
+        h.juv += o.Su[c] * o.Sv[c];
+        h.jvv += o.Sv[c] * o.Sv[c];
+        h.huu += d[c] * o.Suu[c];
+        h.huv += d[c] * o.Suv[c];
+        h.hvv += d[c] * o.Svv[c];
     }
+    h.huu += h.juu;
+    h.huv += h.juv;
+    h.hvv += h.jvv;
     return D;
 }
 
-// projected Newton with active set and halving safeguard on [0,1]^2.
-// Returns true when converged (step below tol, or KKT point on the bounds).
+// projected Newton with active set and halving safeguard on [0,1]^2: the
+// Newton step where the Hessian is positive definite, the Gauss-Newton step
+// (J^T J, positive definite on a regular surface) elsewhere, so the step
+// does not depend on how the parameters are scaled.  A coordinate on a bound
+// whose gradient points outward is held.  Returns true when converged (step
+// below tol, KKT point on the bounds, or no descent left at this precision).
 template <class R>
 __device__ bool newton2(const R* a, int du, int dv, int stride, R qx, R qy, R qz, R& u, R& v, int maxit, R tol,
                         R& Dout)
 {
     SD<R> o;
     eval_patch(a, du, dv, stride, u, v, o);
-    R gu, gv, huu, huv, hvv;
-    R D = grad_hess(o, qx, qy, qz, gu, gv, huu, huv, hvv);
+    GH<R> h;
+    R D = grad_hess(o, qx, qy, qz, h);
     bool conv = false;
     for (int it = 0; it < maxit; ++it) {
-        const bool fu = !((u <= R(0) && gu > R(0)) || (u >= R(1) && gu < R(0)));
-        const bool fv = !((v <= R(0) && gv > R(0)) || (v >= R(1) && gv < R(0)));
+        const bool fu = !((u <= R(0) && h.gu > R(0)) || (u >= R(1) && h.gu < R(0)));
+        const bool fv = !((v <= R(0) && h.gv > R(0)) || (v >= R(1) && h.gv < R(0)));
         R su = 0, sv = 0;
         if (fu && fv) {
-            R det = huu * hvv - huv * huv;
-            if (huu > R(0) && det > R(0)) {
-                su = -(hvv * gu - huv * gv) / det;
-                sv = -(huu * gv - huv * gu) / det;
+            R a11 = h.huu, a12 = h.huv, a22 = h.hvv;
+            if (!(a11 > R(0) && a11 * a22 - a12 * a12 > R(0))) {
+                a11 = h.juu;
+                a12 = h.juv;
+                a22 = h.jvv;
+            }
+            const R det = a11 * a22 - a12 * a12;
+            if (a11 > R(0) && det > R(0)) {
+                su = -(a22 * h.gu - a12 * h.gv) / det;
+                sv = -(a11 * h.gv - a12 * h.gu) / det;
             } else {
-                R sc = R(1) / (fabs(huu) + fabs(hvv) + fabs(huv) + R(1e-30));
-                su = -gu * sc;
-                sv = -gv * sc;
+                su = h.juu > R(0) ? -h.gu / h.juu : R(0);
+                sv = h.jvv > R(0) ? -h.gv / h.jvv : R(0);
             }
         } else if (fu) {
-            su = huu > R(0) ? -gu / huu : -gu / (fabs(huu) + R(1e-30));
+            const R c = h.huu > R(0) ? h.huu : h.juu;
+            su = c > R(0) ? -h.gu / c : R(0);
         } else if (fv) {
-            sv = hvv > R(0) ? -gv / hvv : -gv / (fabs(hvv) + R(1e-30));
+            const R c = h.hvv > R(0) ? h.hvv : h.jvv;
+            sv = c > R(0) ? -h.gv / c : R(0);
         } else {
             conv = true;  // both coordinates held on bounds: KKT point
             break;
         }
         R lam = 1, un = u, vn = v, Dn = D;
-        R gun = gu, gvn = gv, huun = huu, huvn = huv, hvvn = hvv;
+        GH<R> hn = h;
         bool acc = false;
-        for (int ls = 0; ls < 12; ++ls) {
+        for (int ls = 0; ls < 30; ++ls) {
             un = fmin(fmax(u + lam * su, R(0)), R(1));
             vn = fmin(fmax(v + lam * sv, R(0)), R(1));
             eval_patch(a, du, dv, stride, un, vn, o);
-            Dn = grad_hess(o, qx, qy, qz, gun, gvn, huun, huvn, hvvn);
+            Dn = grad_hess(o, qx, qy, qz, hn);
             if (Dn <= D) {
                 acc = true;
                 break;
@@ -221,11 +246,7 @@ __device__ bool newton2(const R* a, int du, int dv, int stride, R qx, R qy, R qz
         u = un;
         v = vn;
         D = Dn;
-        gu = gun;
-        gv = gvn;
-        huu = huun;
-        huv = huvn;
-        hvv = hvvn;
+        h = hn;
         if (step <= tol) {
             conv = true;
             break;
@@ -241,15 +262,23 @@ struct PoolEntry {
     float u0, v0;
 };
 
+template <class R>
 struct WarpSmem {
     int cand[kCandCap];
-    double cand_lb[kCandCap];
+    R cand_lb[kCandCap];
     PoolEntry pool[kPoolCap];
     double pool_D[kPoolCap];
     double pool_u[kPoolCap];
     double pool_v[kPoolCap];
+    float pool_s32[kPoolCap];  // mixed: FP32 minimiser in the span pair and its squared distance
+    float pool_t32[kPoolCap];
+    float pool_D32[kPoolCap];
+    unsigned char pool_conv32[kPoolCap];  // mixed: the FP32 stage converged
+    short fin[kPoolCap];
     unsigned char pool_flags[kPoolCap];
     double q64[kQPW][3];
+    float eps32[kQPW];
+    float best_D32[kQPW];
     double best_D[kQPW];
     double best_u[kQPW];
     double best_v[kQPW];
@@ -257,58 +286,143 @@ struct WarpSmem {
     unsigned char best_flags[kQPW];
 };
 
-template <class R, bool MIXED>
-__device__ void flush_pool(const SurfQ& P, WarpSmem& W, int npool, int lane)
+// local-frame copy of a patch's power coefficients: the constant term
+// becomes a(0,0) - q, formed in FP64 and rounded, so the FP32 iteration keeps
+// its relative accuracy on small patches far from the origin
+__device__ __forceinline__ void local_frame32(const float* a32, const double* a64_00, const double* q, int du, int dv,
+                                              int stride, float* out)
 {
-    for (int k = lane; k < npool; k += 32) {
-        PoolEntry e = W.pool[k];
-        const double* q = W.q64[e.slot];
-        unsigned char fl = 0;
-        // stage 1: refine on the bicubic patch (FP32 steps for MIXED, FP64 to
-        // convergence for the plain path)
-        double u, v;
-        if (MIXED) {
-            const float* a = P.rec32 + (int64_t)BSPL_SREC32 * e.patch + 6;
-            float uf = e.u0, vf = e.v0, Df;
-            newton2<float>(a, 3, 3, 4, (float)q[0], (float)q[1], (float)q[2], uf, vf, P.fp32_steps, 1e-7f, Df);
-            u = uf;
-            v = vf;
-        } else {
-            const double* a = P.rec64 + (int64_t)BSPL_SREC64 * e.patch + 6;
-            double D;
-            u = e.u0;
-            v = e.v0;
-            newton2<double>(a, 3, 3, 4, q[0], q[1], q[2], u, v, P.newton_max, 1e-15, D);
+    for (int i = 0; i <= du; ++i)
+        for (int j = 0; j <= dv; ++j)
+            for (int c = 0; c < 3; ++c) out[(i * stride + j) * 3 + c] = a32[(i * stride + j) * 3 + c];
+    for (int c = 0; c < 3; ++c) out[c] = (float)(a64_00[c] - q[c]);
+}
+
+// Newton on the bicubic from a sampled basin; when it stops on an edge of the
+// patch, a second start half a grid cell inside the patch guards against a
+// minimum hidden behind a ridge of D next to that edge.  Keeps the better.
+template <class R>
+__device__ bool bicubic_newton(const R* c, R qx, R qy, R qz, R& u, R& v, int maxit, R tol, R hu, R hv)
+{
+    R D;
+    bool ok = newton2<R>(c, 3, 3, 4, qx, qy, qz, u, v, maxit, tol, D);
+    const bool eu = u <= R(0) || u >= R(1), ev = v <= R(0) || v >= R(1);
+    if (eu || ev) {
+        R u2 = eu ? (u <= R(0) ? R(0.5) * hu : R(1) - R(0.5) * hu) : u;
+        R v2 = ev ? (v <= R(0) ? R(0.5) * hv : R(1) - R(0.5) * hv) : v;
+        R D2;
+        bool ok2 = newton2<R>(c, 3, 3, 4, qx, qy, qz, u2, v2, maxit, tol, D2);
+        if (D2 < D) {
+            u = u2;
+            v = v2;
+            ok = ok2;
         }
-        // stage 2: FP64 on the original span-pair patch, in its local (s, t)
-        const double* pb = P.patch_box + 4 * (int64_t)e.patch;
-        double s = pb[0] + u * (pb[1] - pb[0]), t = pb[2] + v * (pb[3] - pb[2]);
-        const float* r32 = P.rec32 + (int64_t)BSPL_SREC32 * e.patch;
-        const int pu = (int)r32[54], pv = (int)r32[55];
-        const double* net = P.span_net + (int64_t)BSPL_SPAN_NET * P.patch_span[e.patch];
-        double D;
-        bool ok;
-        if (MIXED) {
-            double s0 = s, t0 = t;
-            newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s, t, 2, 0.0, D);
-            ok = fabs(s - s0) + fabs(t - t0) <= 1e-6;  // two steps from a converged FP32 seed
-            // certificate: the next Newton step (the residual scaled by the
-            // inverse Hessian) must be negligible
-            double s1 = s, t1 = t, D1;
-            newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s1, t1, 1, 0.0, D1);
-            ok = ok && fabs(s1 - s) + fabs(t1 - t) <= 1e-12;
+    }
+    return ok;
+}
+
+// Newton phase over the pooled basins, then per-slot merge.
+// PLAIN: FP64 Newton on the bicubic to convergence, then on the original
+// span-pair patch to convergence.  MIXED: (A) FP32 Newton on the bicubic,
+// then FP32 Newton on the original patch (both in the local frame); (B) best
+// FP32 squared distance per query; (C) compaction of the basins within the
+// FP32 margin of that best; (D) two FP64 Newton steps on the original patch,
+// with the FP64 iteration as the fallback when the second step exceeds 1e-9.
+template <class R, bool MIXED, int GU, int GV>
+__device__ void flush_pool(const SurfQ& P, WarpSmem<R>& W, int npool, int lane)
+{
+    constexpr float kHu = 1.f / (GU - 1), kHv = 1.f / (GV - 1);
+    if (MIXED) {
+        for (int k = lane; k < npool; k += 32) {
+            const PoolEntry e = W.pool[k];
+            const double* q = W.q64[e.slot];
+            float c[48];
+            local_frame32(P.rec32 + (int64_t)BSPL_SREC32 * e.patch + 6,
+                          P.rec64 + (int64_t)BSPL_SREC64 * e.patch + 6, q, 3, 3, 4, c);
+            float uf = e.u0, vf = e.v0, Df;
+            const bool ok1 = bicubic_newton<float>(c, 0.f, 0.f, 0.f, uf, vf, P.fp32_steps, 1e-7f, kHu, kHv);
+            const double* pb = P.patch_box + 4 * (int64_t)e.patch;
+            float s = (float)(pb[0] + uf * (pb[1] - pb[0])), t = (float)(pb[2] + vf * (pb[3] - pb[2]));
+            const float* r32 = P.rec32 + (int64_t)BSPL_SREC32 * e.patch;
+            const int pu = (int)r32[54], pv = (int)r32[55];
+            const int64_t slot = P.patch_span[e.patch];
+            float net[kSN * kSN * 3];
+            local_frame32(P.span_net32 + (int64_t)BSPL_SPAN_NET * slot, P.span_net + (int64_t)BSPL_SPAN_NET * slot, q,
+                          pu, pv, kSN, net);
+            const bool ok2 = newton2<float>(net, pu, pv, kSN, 0.f, 0.f, 0.f, s, t, P.fp32_steps, 1e-7f, Df);
+            W.pool_conv32[k] = ok1 && ok2;
+            W.pool_s32[k] = s;
+            W.pool_t32[k] = t;
+            W.pool_D32[k] = Df;
+            W.pool_D[k] = INFINITY;
+            W.pool_flags[k] = 0;
+        }
+        __syncwarp();
+        if (lane < kQPW) {
+            float b = W.best_D32[lane];
+            for (int k = 0; k < npool; ++k)
+                if (W.pool[k].slot == lane) b = fminf(b, W.pool_D32[k]);
+            W.best_D32[lane] = b;
+        }
+        __syncwarp();
+        int nfin = 0;
+        for (int base = 0; base < npool; base += 32) {
+            const int k = base + lane;
+            bool take = false;
+            if (k < npool) {
+                const int sl = W.pool[k].slot;
+                const float sm = sqrtf(W.best_D32[sl]) + 2.f * W.eps32[sl];
+                take = !W.pool_conv32[k] || W.pool_D32[k] <= sm * sm;
+            }
+            const unsigned m = __ballot_sync(kFull, take);
+            if (take) W.fin[nfin + __popc(m & ((1u << lane) - 1))] = (short)k;
+            nfin += __popc(m);
+        }
+        __syncwarp();
+        for (int f = lane; f < nfin; f += 32) {
+            const int k = W.fin[f];
+            const PoolEntry e = W.pool[k];
+            const double* q = W.q64[e.slot];
+            const float* r32 = P.rec32 + (int64_t)BSPL_SREC32 * e.patch;
+            const int pu = (int)r32[54], pv = (int)r32[55];
+            const double* net = P.span_net + (int64_t)BSPL_SPAN_NET * P.patch_span[e.patch];
+            double s = W.pool_s32[k], t = W.pool_t32[k], D;
+            double s1 = s, t1 = t;
+            newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s1, t1, 1, 0.0, D);
+            double s2 = s1, t2 = t1;
+            newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s2, t2, 1, 0.0, D);
+            unsigned char fl = 0;
+            bool ok = fabs(s2 - s1) + fabs(t2 - t1) <= 1e-9;
+            s = s2;
+            t = t2;
             if (!ok) {
                 fl |= BSPL_Q_FALLBACK;
                 ok = newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s, t, P.newton_max, 1e-15, D);
             }
-        } else {
-            ok = newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s, t, P.newton_max, 1e-15, D);
+            fl |= ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
+            W.pool_D[k] = D;
+            W.pool_u[k] = s;
+            W.pool_v[k] = t;
+            W.pool_flags[k] = fl;
         }
-        fl |= ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
-        W.pool_D[k] = D;
-        W.pool_u[k] = s;
-        W.pool_v[k] = t;
-        W.pool_flags[k] = fl;
+    } else {
+        for (int k = lane; k < npool; k += 32) {
+            const PoolEntry e = W.pool[k];
+            const double* q = W.q64[e.slot];
+            const double* a = P.rec64 + (int64_t)BSPL_SREC64 * e.patch + 6;
+            double D, u = e.u0, v = e.v0;
+            bicubic_newton<double>(a, q[0], q[1], q[2], u, v, P.newton_max, 1e-15, kHu, kHv);
+            const double* pb = P.patch_box + 4 * (int64_t)e.patch;
+            double s = pb[0] + u * (pb[1] - pb[0]), t = pb[2] + v * (pb[3] - pb[2]);
+            const float* r32 = P.rec32 + (int64_t)BSPL_SREC32 * e.patch;
+            const int pu = (int)r32[54], pv = (int)r32[55];
+            const double* net = P.span_net + (int64_t)BSPL_SPAN_NET * P.patch_span[e.patch];
+            bool ok = newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s, t, P.newton_max, 1e-15, D);
+            W.pool_D[k] = D;
+            W.pool_u[k] = s;
+            W.pool_v[k] = t;
+            W.pool_flags[k] = ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
+        }
     }
     __syncwarp();
     if (lane < kQPW) {
@@ -317,9 +431,10 @@ __device__ void flush_pool(const SurfQ& P, WarpSmem& W, int npool, int lane)
         unsigned char bf = W.best_flags[lane];
         for (int k = 0; k < npool; ++k) {
             if (W.pool[k].slot != lane) continue;
-            double D = W.pool_D[k];
-            int pch = W.pool[k].patch;
-            if (D < bD || (D == bD && pch < bp)) {
+            const double D = W.pool_D[k];
+            const int pch = W.pool[k].patch;
+            const long long a = __double_as_longlong(D), b = __double_as_longlong(bD);
+            if (a < b || (a == b && pch < bp)) {
                 bD = D;
                 bu = W.pool_u[k];
                 bv = W.pool_v[k];
@@ -339,9 +454,9 @@ __device__ void flush_pool(const SurfQ& P, WarpSmem& W, int npool, int lane)
 template <class R, int GU, int GV, bool MIXED>
 __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
 {
-    __shared__ WarpSmem smem[kWarps];
+    __shared__ WarpSmem<R> smem[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpSmem& W = smem[wid];
+    WarpSmem<R>& W = smem[wid];
     const int64_t batch = (int64_t)blockIdx.x * kWarps + wid;
     const int64_t qbase = batch * kQPW;
     if (qbase >= P.n_q) return;
@@ -360,6 +475,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
         W.best_v[lane] = 0.0;
         W.best_patch[lane] = 0x7fffffff;
         W.best_flags[lane] = 0;
+        W.best_D32[lane] = INFINITY;
     }
     int npool = 0;
     __syncwarp();
@@ -369,20 +485,22 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
         const int c = P.q_surf[qi];
         const double qx64 = P.q_xyz[3 * qi], qy64 = P.q_xyz[3 * qi + 1], qz64 = P.q_xyz[3 * qi + 2];
         const bool bad = c < 0 || c >= P.n || !isfinite(qx64) || !isfinite(qy64) || !isfinite(qz64);
+        const int cc_ = (c < 0 || c >= P.n) ? 0 : c;
+        const R qx = (R)qx64, qy = (R)qy64, qz = (R)qz64;
+        // distance slack: rounding of the search precision plus the certified
+        // deviation of the bicubics from the original surface
+        const R eps = (MIXED ? R(4e-6) : R(1e-13)) * (fabs(qx) + fabs(qy) + fabs(qz) + (R)P.diag[cc_]) +
+                      (R)(P.tol_rel * P.diag[cc_]) * R(1.0001);
         if (lane == 0) {
             W.q64[sl][0] = qx64;
             W.q64[sl][1] = qy64;
             W.q64[sl][2] = qz64;
+            W.eps32[sl] = (float)eps;
             if (bad) W.best_flags[sl] = BSPL_Q_INVALID;
         }
         if (bad) continue;
-        const R qx = (R)qx64, qy = (R)qy64, qz = (R)qz64;
         const int64_t s0 = P.seg_off[c], s1 = P.seg_off[c + 1];
         const int64_t g0 = P.grp_off[c], g1 = P.grp_off[c + 1];
-        // distance slack: rounding of the search precision plus the certified
-        // deviation of the bicubics from the original surface
-        const R eps = (MIXED ? R(4e-6) : R(1e-13)) * (R)(fabs(qx64) + fabs(qy64) + fabs(qz64) + P.diag[c]) +
-                      (R)(P.tol_rel * P.diag[c]) * R(1.0001);
 
         R ub = INFINITY;
         for (int64_t g = g0 + lane; g < g1; g += 32) ub = fmin(ub, pt_d2(grp + (int64_t)GW * g + 6, qx, qy, qz));
@@ -397,13 +515,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
             const int iu = j % GU, iv = j / GU;
             for (int base = 0; base < ncand; base += PPW) {
                 const int k = base + sub;
-                const bool act = sub < PPW && k < ncand && (R)W.cand_lb[k] <= ubs;
+                const bool act = sub < PPW && k < ncand && W.cand_lb[k] <= ubs;
                 const int pch = act ? W.cand[k] : 0;
                 R D = INFINITY, vu = 0, vv = 0;
                 const R u = R(iu) * hu, v = R(iv) * hv;
                 if (act) {
                     const R* a = rec + (int64_t)RW * pch + 6;
-                    const R q3[3] = { qx, qy, qz };
+                    // the constant term in the patch's local frame: a(0,0) - q
+                    // formed in FP64 (for the FP32 grid; exact for FP64)
+                    const double* a00 = P.rec64 + (int64_t)BSPL_SREC64 * pch + 6;
+                    const R off[3] = { (R)(a00[0] - qx64), (R)(a00[1] - qy64), (R)(a00[2] - qz64) };
                     R Dq = 0;
 #pragma unroll
                     for (int cc = 0; cc < 3; ++cc) {
@@ -412,10 +533,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
                         for (int i = 3; i >= 0; --i) {
                             R p = 0;
 #pragma unroll
-                            for (int jj = 3; jj >= 0; --jj) p = p * v + a[(i * 4 + jj) * 3 + cc];
+                            for (int jj = 3; jj >= 0; --jj)
+                                p = p * v + ((i | jj) ? a[(i * 4 + jj) * 3 + cc] : off[cc]);
                             x = x * u + p;
                         }
-                        x -= q3[cc];
                         Dq += x * x;
 #pragma unroll
                         for (int i = 1; i < 4; ++i)
@@ -442,7 +563,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
                 const unsigned m = __ballot_sync(kFull, push);
                 const int cnt = __popc(m);
                 if (cnt > 0 && npool + cnt > kPoolCap) {
-                    flush_pool<R, MIXED>(P, W, npool, lane);
+                    flush_pool<R, MIXED, GU, GV>(P, W, npool, lane);
                     n_newton += npool;
                     npool = 0;
                 }
@@ -489,7 +610,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
                 if (keep) {
                     const int pos = ncand + __popc(km & ((1u << lane) - 1));
                     W.cand[pos] = (int)s;
-                    W.cand_lb[pos] = (double)lbs;
+                    W.cand_lb[pos] = lbs;
                 }
                 ncand += __popc(km);
                 if (ncand > kCandCap - 32) grid_stage();
@@ -498,7 +619,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
         grid_stage();
     }
     if (npool > 0) {
-        flush_pool<R, MIXED>(P, W, npool, lane);
+        flush_pool<R, MIXED, GU, GV>(P, W, npool, lane);
         n_newton += npool;
     }
     __syncwarp();
@@ -573,7 +694,7 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
     if (n_q == 0) return BSPL_OK;
     if (!q_surf || !q_xyz || !uv || !dist || !status || !segs->seg_off || !segs->grp_off || !segs->rec64 ||
         !segs->rec32 || !segs->grp64 || !segs->grp32 || !segs->prange || !segs->diag || !segs->patch_box ||
-        !segs->patch_span || !segs->span_net)
+        !segs->patch_span || !segs->span_net || !segs->span_net32)
         return BSPL_EINVAL;
     if (n_q > 0x7fffffffLL || segs->capacity > 0x7fffffffLL) return BSPL_EINVAL;
     bspl_options o{};
@@ -593,6 +714,7 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
     P.patch_box = segs->patch_box;
     P.patch_span = segs->patch_span;
     P.span_net = segs->span_net;
+    P.span_net32 = segs->span_net32;
     P.diag = segs->diag;
     P.tol_rel = segs->tol_rel;
     P.n = segs->n;
@@ -604,7 +726,7 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
     P.status = status;
     P.invert = invert;
     P.newton_max = o.newton_max > 0 ? o.newton_max : 30;
-    P.fp32_steps = o.fp32_steps > 0 ? o.fp32_steps : 4;
+    P.fp32_steps = o.fp32_steps > 0 ? o.fp32_steps : 8;
     P.counters = (unsigned long long*)o.counters;
     P.order = nullptr;
     if (sort) {

@@ -1,0 +1,134 @@
+"""Pins of the FP64 reference of the learned seed (oracle/mlp.py) against
+facts that do not come from its own formulas: finite differences, the
+Gaussian CDF, Adam's closed-form first step, invariances of the features,
+brute force and closed forms for the segment minimiser."""
+import math
+
+import numpy as np
+import pytest
+from scipy import optimize, special
+
+from oracle import mlp as M
+
+
+def tiny_params(rng, widths=(5, 4, 3, 2)):
+    p = {}
+    for i in range(3):
+        p[f"W{i + 1}"] = rng.normal(0, 0.8, (widths[i + 1], widths[i]))
+        p[f"b{i + 1}"] = rng.normal(0, 0.3, widths[i + 1])
+    p["w4"] = rng.normal(0, 0.8, widths[3])
+    p["b4"] = rng.normal(0, 0.3, 1)
+    return p
+
+
+def test_gradients_match_central_differences():
+    rng = np.random.default_rng(0)
+    p = tiny_params(rng)
+    X = rng.normal(0, 1, (7, 5))
+    y = rng.uniform(0, 1, 7)
+    _, g = M.loss_and_grads(p, X, y)
+    h = 1e-6
+    for name, arr in p.items():
+        num = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            old = arr[idx]
+            arr[idx] = old + h
+            lp = M.loss_and_grads(p, X, y)[0]
+            arr[idx] = old - h
+            lm = M.loss_and_grads(p, X, y)[0]
+            arr[idx] = old
+            num[idx] = (lp - lm) / (2 * h)
+        assert np.allclose(g[name], num, rtol=1e-5, atol=1e-9), name
+
+
+def test_gelu_symmetry_and_gaussian_cdf():
+    x = np.linspace(-8, 8, 4001)
+    assert M.gelu(0.0) == 0.0
+    assert np.allclose(M.gelu(x) - M.gelu(-x), x, atol=1e-14)
+    # the tanh form approximates x Phi(x) to a few 1e-4
+    assert np.max(np.abs(M.gelu(x) - x * special.ndtr(x))) < 1e-3
+    h = 1e-6
+    assert np.allclose(M.gelu_grad(x), (M.gelu(x + h) - M.gelu(x - h)) / (2 * h), atol=1e-8)
+
+
+def test_sigmoid_output_with_zero_weights():
+    p = {k: np.zeros(s) for k, s in M._SHAPES}
+    p["b4"] = np.array([0.7])
+    t, _, _ = M.forward(p, np.ones((3, M.IN)))
+    assert np.allclose(t, 1 / (1 + math.exp(-0.7)))
+
+
+def test_pack_layout():
+    sizes = [int(np.prod(s)) for _, s in M._SHAPES]
+    assert sum(sizes) + 3 == M.NPARAM
+    theta = np.arange(M.NPARAM, dtype=np.float64)
+    p = M.unpack(theta)
+    assert p["W1"][1, 0] == 16 and p["b1"][0] == 128 * 16 and p["b4"][0] == M.NPARAM - 4
+    assert np.array_equal(M.pack(p)[:-3], theta[:-3])
+
+
+def test_adam_first_step_and_convergence():
+    rng = np.random.default_rng(1)
+    g = rng.normal(size=10)
+    th = rng.normal(size=10)
+    new, m, v = M.adam(th, g, np.zeros(10), np.zeros(10), 1, 0.01)
+    # bias correction makes the first step -lr g / (|g| + eps)
+    assert np.allclose(new - th, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    a = rng.normal(size=10)
+    x, m, v = np.zeros(10), np.zeros(10), np.zeros(10)
+    for k in range(1, 3001):
+        x, m, v = M.adam(x, x - a, m, v, k, 0.01)
+    assert np.max(np.abs(x - a)) < 1e-3
+
+
+def test_features_invariances():
+    rng = np.random.default_rng(2)
+    P = rng.uniform(-1, 1, (50, 4, 3))
+    q = rng.uniform(-2, 2, (50, 3))
+    X = M.features(P, q)
+    sh = rng.normal(size=3)
+    assert np.allclose(M.features(P + sh, q + sh), X, atol=1e-12)
+    assert np.allclose(M.features(3.7 * P, 3.7 * q), X, atol=1e-12)
+    pts = X[:, :12].reshape(-1, 4, 3)
+    ext = pts.max(1) - pts.min(1)
+    assert np.allclose(ext.max(1), 1.0) and np.all(np.abs(pts) <= 0.5 + 1e-12)
+    assert np.all(np.linalg.norm(X[:, 12:15], axis=1) <= 1 + 1e-12) and np.all(X[:, 15] == 0)
+    far = M.features(P[:1], np.array([[100.0, 0, 0]]))
+    assert abs(np.linalg.norm(far[0, 12:15]) - 1) < 1e-12 and far[0, 12] > 0.99
+
+
+def test_segment_minimiser_line_closed_form():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        a, b = rng.uniform(-1, 1, 3), rng.uniform(-1, 1, 3)
+        P = np.array([a + (b - a) * k / 3 for k in range(4)])  # linear parametrisation
+        q = rng.uniform(-1.5, 1.5, 3)
+        u_ref = np.clip((q - a) @ (b - a) / ((b - a) @ (b - a)), 0, 1)
+        u, D = M.segment_minimiser(P, q)
+        assert abs(u - u_ref) < 1e-9
+        assert abs(D - np.sum((a + u_ref * (b - a) - q) ** 2)) < 1e-14
+
+
+def test_segment_minimiser_brute_force():
+    rng = np.random.default_rng(4)
+    for _ in range(25):
+        P = rng.uniform(-1, 1, (4, 3))
+        q = rng.uniform(-1, 1, 3)
+        u, D = M.segment_minimiser(P, q)
+
+        def f(x):
+            return float(np.sum((M._bezier(P, np.array([x]))[0] - q) ** 2))
+
+        best = min(f(0.0), f(1.0))
+        grid = np.linspace(0, 1, 201)
+        for lo, hi in zip(grid[:-1], grid[1:]):
+            r = optimize.minimize_scalar(f, bounds=(lo, hi), method="bounded", options={"xatol": 1e-12})
+            best = min(best, r.fun)
+        assert D <= best + 1e-13
+        assert abs(D - f(u)) < 1e-15
+
+
+def test_segment_minimiser_tie_takes_smaller_u():
+    P = np.array([[-1.0, 0, 0], [-0.5, -1, 0], [0.5, -1, 0], [1, 0, 0]])
+    u, D = M.segment_minimiser(P, np.array([0.0, 5.0, 0.0]))
+    assert u == 0.0 and D == pytest.approx(26.0)

@@ -41,13 +41,14 @@ typedef enum {
     BSPL_ENOSPACE = 2, /* capacity too small (counts were still written)        */
     BSPL_ECUDA = 3,    /* a CUDA call failed                                    */
     BSPL_ENOTCONV = 4, /* subdivision hit its depth cap (40) somewhere          */
-    BSPL_ETIMEOUT = 5  /* reserved                                              */
+    BSPL_ETIMEOUT = 5  /* a bounded device wait gave up (bspl_mlp_check)        */
 } bspl_status;
 
 typedef enum {
     BSPL_FP64 = 0,          /* cull, seed and Newton all in FP64                  */
     BSPL_MIXED = 1,         /* FP32 cull/seed/early Newton + 2 FP64 Newton steps  */
-    BSPL_LEARNED_MIXED = 2  /* as MIXED with the MLP seed in place of the grid    */
+    BSPL_LEARNED_MIXED = 2  /* as MIXED with the MLP seed in place of the grid
+                               (curves only; bspl_mlp.h)                         */
 } bspl_precision;
 
 /* per-query status bits */
@@ -156,7 +157,9 @@ typedef struct {
     int32_t occupancy;   /* curve kernel register/occupancy variant: 0 compiler
                             choice, 1 >= 4 blocks/SM, 2 >= 6 blocks/SM (samples
                             16 and 32); picked by the autotuner             */
-    const void* mlp;     /* learned seed (BSPL_LEARNED_MIXED), else NULL            */
+    const void* mlp;     /* BSPL_LEARNED_MIXED: const bspl_mlp* (bspl_mlp.h) giving
+                            the Newton seed; NULL -> the seed is u = 1/2 (the
+                            learned path without its network)               */
     uint64_t* counters;  /* optional device array [BSPL_NCOUNTERS], accumulated     */
 } bspl_options;
 
@@ -177,6 +180,8 @@ typedef struct {
 #define BSPL_OP_DECOMPOSE_SURFACES 2
 #define BSPL_OP_QUERY_CURVES 3
 #define BSPL_OP_QUERY_SURFACES 4
+#define BSPL_OP_QUERY_CURVES_LEARNED 5 /* curve queries with opt->prec = BSPL_LEARNED_MIXED */
+#define BSPL_OP_MLP_TRAIN 6            /* bspl_mlp_loss_grad / bspl_mlp_train, n_q = batch */
 
 /* Bytes of device workspace a call of kind `op` needs.  n_splines = n,
  * n_cp_total = total control points (cp_off[n]), n_seg = segments of the

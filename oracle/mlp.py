@@ -16,8 +16,10 @@ Eqs. Dt, Et, E't).  Definitions used here:
 * Adam (Kingma & Ba) with bias correction, applied to every parameter;
 * features of a cubic Bezier segment P0..P3 and query q, in the frame of the
   segment's control-point box (centre c, scale s = 1 / longest side, no
-  rotation): (P_i - c) s for i = 0..3, then v / max(1, |v|) with
-  v = (q - c) s, then a zero;
+  rotation): (P_i - c) s for i = 0..3, then the query v = (q - c) s with
+  its part across the chord P0 -> P3 shortened to length min(1, |part|)
+  (the part along the chord, which fixes the minimiser of a far query, is
+  kept), then a zero;
 * label: the global minimiser of |C(u) - q|^2 on u in [0, 1] (ties -> the
   smaller u).
 
@@ -73,15 +75,27 @@ def sigmoid(z):
     return 1.0 / (1.0 + np.exp(-z))
 
 
-def forward(p, X):
+def round_bf16(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(x, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(p, X, bf16=False):
     """p: dict of layer arrays (any widths), X [n][in].  Returns t [n] and
-    the pre-activations (Z1, Z2, Z3) and activations (H0 = X, H1, H2, H3)."""
+    the pre-activations (Z1, Z2, Z3) and activations (H0 = X, H1, H2, H3).
+    bf16=True evaluates the network at the precision it is served in: every
+    weight matrix and every layer input rounded to bfloat16 (biases and the
+    accumulation stay in full precision)."""
+    r = round_bf16 if bf16 else (lambda a: a)
     Hs, Zs = [np.asarray(X, np.float64)], []
     for W, b in ((p["W1"], p["b1"]), (p["W2"], p["b2"]), (p["W3"], p["b3"])):
-        Z = Hs[-1] @ W.T + b
+        Z = r(Hs[-1]) @ r(W).T + b
         Zs.append(Z)
         Hs.append(gelu(Z))
-    z4 = Hs[-1] @ p["w4"] + p["b4"][0]
+    z4 = r(Hs[-1]) @ r(p["w4"]) + p["b4"][0]
     return sigmoid(z4), Zs, Hs
 
 
@@ -123,7 +137,15 @@ def features(ctrl, q):
     X = np.zeros((len(q), IN))
     X[:, :12] = ((ctrl - c[:, None, :]) * s[:, None, None]).reshape(-1, 12)
     v = (q - c) * s[:, None]
-    X[:, 12:15] = v / np.maximum(1.0, np.linalg.norm(v, axis=1))[:, None]
+    # query: its coordinate along the chord P0 -> P3 kept, the part across
+    # the chord shortened to length <= 1
+    ch = ctrl[:, 3] - ctrl[:, 0]
+    ln = np.linalg.norm(ch, axis=1)
+    d = np.where(ln[:, None] > 0, ch / np.where(ln > 0, ln, 1.0)[:, None], np.array([1.0, 0.0, 0.0]))
+    a = np.einsum("ij,ij->i", v, d)
+    w = v - a[:, None] * d
+    r = np.linalg.norm(w, axis=1)
+    X[:, 12:15] = a[:, None] * d + w / np.maximum(1.0, r)[:, None]
     return X
 
 

@@ -25,6 +25,10 @@ GROUP = 32
 CREC64, CREC32, SREC64, SREC32, GREC64, GREC32 = 18, 20, 54, 56, 12, 12
 SPAN_NET = 8 * 8 * 3
 OP_DECOMPOSE_CURVES, OP_DECOMPOSE_SURFACES, OP_QUERY_CURVES, OP_QUERY_SURFACES = 1, 2, 3, 4
+OP_QUERY_CURVES_LEARNED, OP_MLP_TRAIN = 5, 6
+# learned seed (include/bspl_mlp.h)
+MLP_IN, MLP_HIDDEN, MLP_NPARAM, MLP_NBF16, MLP_MAX_BATCH = 16, 128, 35332, 2048 + 4 * 16384 + 128, 65536
+MLP_OFF = {"W1": 0, "b1": 2048, "W2": 2176, "b2": 18560, "W3": 18688, "b3": 35072, "w4": 35200, "b4": 35328}
 NCOUNTERS = 10
 COUNTER_NAMES = ["queries", "seg_tested", "grp_tested", "candidates", "newton", "fallback", "nonconv",
                  "newton32_iters", "newton64_iters", "spare"]
@@ -58,6 +62,10 @@ class bspl_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("samples", C.c_int32), ("newton_max", C.c_int32), ("fp32_steps", C.c_int32),
                 ("sort_queries", C.c_int32), ("occupancy", C.c_int32), ("mlp", C.c_void_p),
                 ("counters", C.c_void_p)]
+
+
+class bspl_mlp(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("wbf16", C.c_void_p)]
 
 
 EXPORTS = ["bspl_project_curves_noalloc", "bspl_measure_fma_peak", "bspl_workspace_bytes", "bspl_decompose", "bspl_project_curves", "bspl_invert_curves",
@@ -99,6 +107,21 @@ def lib():
                                                       vp, vp, vp, vp]
             L.bspl_measure_fma_peak.restype = C.c_int
             L.bspl_measure_fma_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, vp]
+            mp = C.POINTER(bspl_mlp)
+            sp = C.POINTER(bspl_segments)
+            f32 = C.c_float
+            for name, args in (("bspl_mlp_check", [vp]), ("bspl_mlp_sync", [mp, vp]),
+                               ("bspl_mlp_forward", [mp, i64, vp, vp, vp]),
+                               ("bspl_mlp_features", [sp, i64, vp, vp, vp, vp, vp]),
+                               ("bspl_mlp_labels", [sp, i64, vp, vp, vp, vp, vp]),
+                               ("bspl_mlp_collect_pairs", [sp, i64, vp, vp, i64, vp, vp, vp, vp, C.c_size_t, vp]),
+                               ("bspl_mlp_loss_grad", [mp, i64, vp, vp, vp, vp, vp, C.c_size_t, vp]),
+                               ("bspl_mlp_adam", [mp, vp, vp, vp, C.c_int32, f32, f32, f32, f32, vp]),
+                               ("bspl_mlp_train", [mp, vp, vp, i64, vp, vp, C.c_int32, C.c_int32, f32, C.c_uint64,
+                                                   C.c_int32, vp, vp, C.c_size_t, vp])):
+                f = getattr(L, name)
+                f.restype = st
+                f.argtypes = args
             _lib = L
     return _lib
 
@@ -262,20 +285,24 @@ class QueryResult:
 
 def make_options(prec=FP64, samples=0, newton_max=0, fp32_steps=0, sort_queries=1, counters=None, mlp=None,
                  occupancy=0):
-    return bspl_options(int(prec), int(samples), int(newton_max), int(fp32_steps), int(sort_queries), int(occupancy),
-                        C.c_void_p(mlp) if mlp else C.c_void_p(0), _ptr(counters) if counters is not None else None)
+    """mlp: an ``Mlp`` (learned seed for prec=LEARNED_MIXED) or None."""
+    o = bspl_options(int(prec), int(samples), int(newton_max), int(fp32_steps), int(sort_queries), int(occupancy),
+                     C.cast(C.pointer(mlp.c), C.c_void_p) if mlp is not None else C.c_void_p(0),
+                     _ptr(counters) if counters is not None else None)
+    o._keep = mlp  # the struct the pointer refers to stays alive with the options
+    return o
 
 
 class QueryBuffers:
     """Preallocated outputs + workspace for repeated query calls."""
 
-    def __init__(self, segs: Segments, n_q: int, device="cuda"):
+    def __init__(self, segs: Segments, n_q: int, device="cuda", learned: bool = False):
         self.n_q = int(n_q)
         shape = (n_q, 2) if segs.is_surface else (n_q,)
         self.param = torch.empty(shape, dtype=torch.float64, device=device)
         self.dist = torch.empty(n_q, dtype=torch.float64, device=device)
         self.status = torch.empty(n_q, dtype=torch.uint8, device=device)
-        op = OP_QUERY_SURFACES if segs.is_surface else OP_QUERY_CURVES
+        op = OP_QUERY_SURFACES if segs.is_surface else (OP_QUERY_CURVES_LEARNED if learned else OP_QUERY_CURVES)
         self.ws = _ws(workspace_bytes(op, segs.n, segs.n_cp_total, segs.total, n_q), device)
 
 
@@ -288,13 +315,17 @@ def _query(fn_name, segs, q_idx, q_xyz, opts, bufs, stream):
     return QueryResult(bufs.param, bufs.dist, bufs.status)
 
 
+def _learned(opts):
+    return opts is not None and opts.prec == LEARNED_MIXED
+
+
 def bspl_project_curves(segs, q_curve, q_xyz, opts=None, bufs=None, stream=None):
-    bufs = bufs or QueryBuffers(segs, q_curve.numel(), q_xyz.device)
+    bufs = bufs or QueryBuffers(segs, q_curve.numel(), q_xyz.device, _learned(opts))
     return _query("bspl_project_curves", segs, q_curve, q_xyz, opts or make_options(), bufs, stream)
 
 
 def bspl_invert_curves(segs, q_curve, q_xyz, opts=None, bufs=None, stream=None):
-    bufs = bufs or QueryBuffers(segs, q_curve.numel(), q_xyz.device)
+    bufs = bufs or QueryBuffers(segs, q_curve.numel(), q_xyz.device, _learned(opts))
     return _query("bspl_invert_curves", segs, q_curve, q_xyz, opts or make_options(), bufs, stream)
 
 
@@ -352,3 +383,120 @@ def measure_fma_peak(fp64: bool, iters: int = 4096, reps: int = 5, stream=None) 
     rc = lib().bspl_measure_fma_peak(int(fp64), int(iters), int(reps), C.byref(out), _ptr(sink), _stream(stream))
     _check(rc, "bspl_measure_fma_peak")
     return out.value
+
+
+# ------------------------------------------------------------ learned seed
+
+class Mlp:
+    """Parameters of the learned seed on the GPU (include/bspl_mlp.h): FP32
+    master weights, the BF16 copy the kernels read, and Adam's moments."""
+
+    def __init__(self, params, device="cuda"):
+        self.params = torch.as_tensor(np.asarray(params, np.float32)).to(device).contiguous()
+        assert self.params.numel() == MLP_NPARAM
+        self.wbf16 = torch.zeros(MLP_NBF16, dtype=torch.int16, device=device)
+        self.adam_m = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=device)
+        self.adam_v = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=device)
+        self.step = 0
+        self.c = bspl_mlp(self.params.data_ptr(), self.wbf16.data_ptr())
+        self.sync()
+
+    def sync(self, stream=None):
+        _check(lib().bspl_mlp_sync(C.byref(self.c), _stream(stream)), "bspl_mlp_sync")
+
+    def forward(self, X, stream=None):
+        X = X.contiguous()
+        t = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(lib().bspl_mlp_forward(C.byref(self.c), X.shape[0], _ptr(X), _ptr(t), _stream(stream)),
+               "bspl_mlp_forward")
+        return t
+
+    def loss_grad(self, X, y, stream=None):
+        n = X.shape[0]
+        grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        ws = _ws(workspace_bytes(OP_MLP_TRAIN, 0, 0, 0, n), X.device)
+        _check(lib().bspl_mlp_loss_grad(C.byref(self.c), n, _ptr(X.contiguous()), _ptr(y.contiguous()), _ptr(grad),
+                                        _ptr(loss), _ptr(ws), ws.numel(), _stream(stream)), "bspl_mlp_loss_grad")
+        return loss, grad
+
+    def adam(self, grad, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self.step += 1
+        _check(lib().bspl_mlp_adam(C.byref(self.c), _ptr(grad), _ptr(self.adam_m), _ptr(self.adam_v), self.step,
+                                   float(lr), float(beta1), float(beta2), float(eps), _stream(stream)),
+               "bspl_mlp_adam")
+
+    def train(self, X, y, epochs, batch=8192, lr=1e-3, seed=0, stream=None):
+        """Returns the per-epoch mean loss (device tensor)."""
+        n = X.shape[0]
+        loss = torch.empty(epochs, dtype=torch.float32, device=X.device)
+        ws = _ws(workspace_bytes(OP_MLP_TRAIN, 0, 0, 0, batch), X.device)
+        _check(lib().bspl_mlp_train(C.byref(self.c), _ptr(self.adam_m), _ptr(self.adam_v), n, _ptr(X.contiguous()),
+                                    _ptr(y.contiguous()), int(epochs), int(batch), float(lr), int(seed) & (2**64 - 1),
+                                    self.step, _ptr(loss), _ptr(ws), ws.numel(), _stream(stream)), "bspl_mlp_train")
+        self.step += epochs * ((n + batch - 1) // batch)
+        return loss
+
+    # versioned checkpoint: magic, version, nparam, step, CRC32 of the payload,
+    # then params, Adam m and v (FP32, little endian)
+    _MAGIC = b"BSPLMLP\0"
+
+    def save(self, path):
+        import struct
+        import zlib
+        payload = b"".join(t.detach().cpu().numpy().astype("<f4").tobytes()
+                           for t in (self.params, self.adam_m, self.adam_v))
+        hdr = self._MAGIC + struct.pack("<IIqI", 1, MLP_NPARAM, self.step, zlib.crc32(payload))
+        with open(path, "wb") as f:
+            f.write(hdr + payload)
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        import struct
+        import zlib
+        raw = open(path, "rb").read()
+        if raw[:8] != cls._MAGIC:
+            raise BsplError(f"{path}: not an MLP checkpoint")
+        ver, npar, step, crc = struct.unpack("<IIqI", raw[8:28])
+        payload = raw[28:]
+        if ver != 1 or npar != MLP_NPARAM or len(payload) != 12 * MLP_NPARAM or zlib.crc32(payload) != crc:
+            raise BsplError(f"{path}: corrupt or incompatible MLP checkpoint")
+        a = np.frombuffer(payload, "<f4").reshape(3, MLP_NPARAM)
+        m = cls(a[0], device)
+        m.adam_m.copy_(torch.from_numpy(a[1].copy()))
+        m.adam_v.copy_(torch.from_numpy(a[2].copy()))
+        m.step = step
+        return m
+
+
+def mlp_check(stream=None):
+    """BSPL_ETIMEOUT if a tensor-core wait gave up since the last check."""
+    return lib().bspl_mlp_check(_stream(stream))
+
+
+def bspl_mlp_features(segs, pair_q, pair_seg, q_xyz, stream=None):
+    X = torch.empty((pair_q.numel(), MLP_IN), dtype=torch.float32, device=q_xyz.device)
+    _check(lib().bspl_mlp_features(C.byref(segs.c), pair_q.numel(), _ptr(pair_q), _ptr(pair_seg), _ptr(q_xyz),
+                                   _ptr(X), _stream(stream)), "bspl_mlp_features")
+    return X
+
+
+def bspl_mlp_labels(segs, pair_q, pair_seg, q_xyz, stream=None):
+    y = torch.empty(pair_q.numel(), dtype=torch.float32, device=q_xyz.device)
+    _check(lib().bspl_mlp_labels(C.byref(segs.c), pair_q.numel(), _ptr(pair_q), _ptr(pair_seg), _ptr(q_xyz),
+                                 _ptr(y), _stream(stream)), "bspl_mlp_labels")
+    return y
+
+
+def bspl_mlp_collect_pairs(segs, q_curve, q_xyz, cap, stream=None):
+    """(pair_q, pair_seg) of the seeded pairs (at most cap) and the number found."""
+    dev = q_xyz.device
+    pq = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    ps = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = _ws(workspace_bytes(OP_QUERY_CURVES_LEARNED, segs.n, 0, 0, q_curve.numel()), dev)
+    _check(lib().bspl_mlp_collect_pairs(C.byref(segs.c), q_curve.numel(), _ptr(q_curve), _ptr(q_xyz), int(cap),
+                                        _ptr(pq), _ptr(ps), _ptr(n), _ptr(ws), ws.numel(), _stream(stream)),
+           "bspl_mlp_collect_pairs")
+    k = min(int(n.item()), cap)
+    return pq[:k], ps[:k], int(n.item())

@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbspl.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["api.cu", "decompose.cu", "query_curves.cu", "query_surfaces.cu", "eval.cu", "scan.cu", "mlp.cu",
+SOURCES = ["api.cu", "decompose.cu", "query_curves.cu", "query_surfaces.cu", "eval.cu", "scan.cu", "mlp.cu", "query_learned.cu",
            "measure.cu", "noalloc.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

@@ -46,6 +46,13 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
                            const bspl_options* opt, int invert, double* uv, double* dist, uint8_t* status,
                            void* ws, size_t ws_bytes, cudaStream_t s);
 size_t query_ws_bytes(int64_t n_splines, int64_t n_q);
+bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const int32_t* q_curve,
+                                 const double* q_xyz, const bspl_options* o, int invert, double* t, double* dist,
+                                 uint8_t* status, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t learned_ws_bytes(int64_t n_splines, int64_t n_q);
+
+// learned seed (mlp.cu)
+size_t train_ws_bytes(int64_t batch);
 
 // evaluation (eval.cu)
 bspl_status eval_curves(const bspl_curves* c, int64_t n_q, const int32_t* qc, const double* t, double* xyz,

@@ -1,0 +1,334 @@
+// Device helpers shared by the curve query kernels: launch constants, the
+// query parameter block, box and point distance bounds, E = (C - q).C' and
+// its derivative (Sec. 4.2.3 Eqs. Dt, Et, E't), safeguarded and bracketed
+// Newton iterations, the Bernstein form of E (degree-5 power-to-Bernstein
+// matrix of Sec. 4.3) and certified isolation of its roots.
+#pragma once
+#include <math.h>
+
+#include "bspl_internal.cuh"
+
+namespace bspl {
+
+// parameter block of the curve query kernels
+struct CurveQ {
+    const int64_t* seg_off;
+    const int64_t* grp_off;
+    const double* rec64;
+    const float* rec32;
+    const double* grp64;
+    const float* grp32;
+    const double* prange;
+    const double* diag;
+    int64_t n, n_q;
+    const int64_t* n_q_dev;  // optional device-side query count (<= n_q)
+    const int32_t* q_curve;
+    const double* q_xyz;
+    const int32_t* order;
+    double* t;
+    double* dist;
+    uint8_t* status;
+    int invert;
+    int newton_max;
+    int fp32_steps;
+    unsigned long long* counters;
+};
+
+// query_curves.cu: the mixed-precision grid kernel over P.order, and the
+// counting sort of query indices by curve
+void launch_mixed_curves(const CurveQ& P, int occ, cudaStream_t s);
+cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, void* ws, size_t ws_bytes, int32_t** order,
+                           cudaStream_t s);
+
+namespace {
+
+constexpr int kQPW = 32;       // queries per warp batch
+constexpr int kCandCap = 96;   // surviving segments buffered before the grid stage
+constexpr int kPoolCap = 128;  // Newton basins buffered per warp
+constexpr int kWarps = 4;      // warps per block
+constexpr unsigned kFull = 0xffffffffu;
+
+
+template <class R>
+struct Tab;
+template <>
+struct Tab<double> {
+    static __device__ const double* rec(const CurveQ& P) { return P.rec64; }
+    static __device__ const double* grp(const CurveQ& P) { return P.grp64; }
+    static constexpr int RW = BSPL_CREC64, GW = BSPL_GREC64;
+};
+template <>
+struct Tab<float> {
+    static __device__ const float* rec(const CurveQ& P) { return P.rec32; }
+    static __device__ const float* grp(const CurveQ& P) { return P.grp32; }
+    static constexpr int RW = BSPL_CREC32, GW = BSPL_GREC32;
+};
+
+template <class R>
+__device__ __forceinline__ R warp_min(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+template <class R>
+__device__ __forceinline__ R box_d2(const R* b, R qx, R qy, R qz)
+{
+    R dx = fmax(fmax(b[0] - qx, qx - b[3]), R(0));
+    R dy = fmax(fmax(b[1] - qy, qy - b[4]), R(0));
+    R dz = fmax(fmax(b[2] - qz, qz - b[5]), R(0));
+    return dx * dx + dy * dy + dz * dz;
+}
+
+template <class R>
+__device__ __forceinline__ R pt_d2(const R* p, R qx, R qy, R qz)
+{
+    R dx = p[0] - qx, dy = p[1] - qy, dz = p[2] - qz;
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// squared-distance threshold with slack: (sqrt(ub) + eps)^2
+template <class R>
+__device__ __forceinline__ R slacked(R ub, R eps)
+{
+    R s = sqrt(ub) + eps;
+    return s * s;
+}
+
+// E = (C - q).C' and E' = C'.C' + (C - q).C'' for the cubic a0 + a1 u + a2 u^2 + a3 u^3
+// (Eqs. Et, E't up to the common factor 2); returns D = |C - q|^2
+template <class R>
+__device__ __forceinline__ R eval_E(const R* a, R qx, R qy, R qz, R u, R& E, R& Ep)
+{
+    R q3[3] = { qx, qy, qz };
+    R D = 0, e = 0, ep = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        R a0 = a[c], a1 = a[3 + c], a2 = a[6 + c], a3 = a[9 + c];
+        R C = a0 + u * (a1 + u * (a2 + u * a3)) - q3[c];
+        R C1 = a1 + u * (R(2) * a2 + u * (R(3) * a3));
+        R C2 = R(2) * a2 + u * (R(6) * a3);
+        D += C * C;
+        e += C * C1;
+        ep += C1 * C1 + C * C2;
+    }
+    E = e;
+    Ep = ep;
+    return D;
+}
+
+// safeguarded Newton for a local minimum of D on the segment [0, 1], started
+// in a sampled basin: a Newton step on E = D' when E' > 0, else a step of
+// length hmax down the slope; every step is limited to hmax, projected onto
+// [0, 1] and halved until D does not increase.  Stops at a bound where D
+// rises into the segment (KKT), when no descent is left at this resolution,
+// or when the step falls below tol.  Returns true unless maxit ran out.
+template <class R>
+__device__ bool newton_min(const R* a, R qx, R qy, R qz, R& u, R hmax, int maxit, R tol, unsigned& iters)
+{
+    R E, Ep;
+    R D = eval_E(a, qx, qy, qz, u, E, Ep);
+    for (int it = 0; it < maxit; ++it) {
+        ++iters;
+        if ((u <= R(0) && E >= R(0)) || (u >= R(1) && E <= R(0)) || E == R(0)) return true;
+        R step = Ep > R(0) ? -E / Ep : (E > R(0) ? -hmax : hmax);
+        step = fmin(fmax(step, -hmax), hmax);
+        R un = u, Dn = D, En = E, Epn = Ep;
+        bool acc = false;
+        for (int ls = 0; ls < 24; ++ls) {
+            un = fmin(fmax(u + step, R(0)), R(1));
+            Dn = eval_E(a, qx, qy, qz, un, En, Epn);
+            // accept a decrease of D, or, where D is locally convex, a
+            // decrease of |E| (D itself is flat to rounding near a minimum,
+            // E is still resolved there)
+            if (Dn < D || (Ep > R(0) && fabs(En) < fabs(E))) {
+                acc = true;
+                break;
+            }
+            if (Dn == D) return true;  // no progress left at this precision
+            step *= R(0.5);
+        }
+        if (!acc) return true;
+        R moved = fabs(un - u);
+        u = un;
+        D = Dn;
+        E = En;
+        Ep = Epn;
+        if (moved <= tol) return true;
+    }
+    return false;
+}
+
+// E(u)/2 = (C(u) - q).C'(u) for the cubic a0 + a1 u + a2 u^2 + a3 u^3 (Eq.
+// Et), a degree-5 polynomial, in Bernstein form on [0,1]: power coefficients
+// e_k, then b = T e with T_ij = C(i,j)/C(5,j) (the degree-5 power-to-
+// Bernstein matrix of Sec. 4.3).  Returns the number of sign changes of b
+// (zeros skipped), an upper bound of the number of roots of E in [0,1].
+template <class R>
+__device__ __forceinline__ int bernstein_E(const R* a, R qx, R qy, R qz, R* b)
+{
+    const R q3[3] = { qx, qy, qz };
+    R e[6] = { 0, 0, 0, 0, 0, 0 };
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R c0 = a[c] - q3[c], c1 = a[3 + c], c2 = a[6 + c], c3 = a[9 + c];
+        const R d1 = c1, d2 = R(2) * c2, d3 = R(3) * c3;  // C' = d1 + d2 u + d3 u^2
+        e[0] += c0 * d1;
+        e[1] += c0 * d2 + c1 * d1;
+        e[2] += c0 * d3 + c1 * d2 + c2 * d1;
+        e[3] += c1 * d3 + c2 * d2 + c3 * d1;
+        e[4] += c2 * d3 + c3 * d2;
+        e[5] += c3 * d3;
+    }
+    b[0] = e[0];
+    b[1] = e[0] + R(0.2) * e[1];
+    b[2] = e[0] + R(0.4) * e[1] + R(0.1) * e[2];
+    b[3] = e[0] + R(0.6) * e[1] + R(0.3) * e[2] + R(0.1) * e[3];
+    b[4] = e[0] + R(0.8) * e[1] + R(0.6) * e[2] + R(0.4) * e[3] + R(0.2) * e[4];
+    b[5] = e[0] + e[1] + e[2] + e[3] + e[4] + e[5];
+    int v = 0;
+    R last = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (b[i] != R(0)) {
+            if (last != R(0) && (b[i] > R(0)) != (last > R(0))) ++v;
+            last = b[i];
+        }
+    }
+    return v;
+}
+
+template <class R>
+__device__ __forceinline__ int sign_changes6(const R* b)
+{
+    int v = 0;
+    R last = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (b[i] != R(0)) {
+            if (last != R(0) && (b[i] > R(0)) != (last > R(0))) ++v;
+            last = b[i];
+        }
+    }
+    return v;
+}
+
+// bracketed Newton on E for its root in [lo, hi] with E(lo) < 0 < E(hi)
+template <class R>
+__device__ R root_bracketed(const R* a, R qx, R qy, R qz, R lo, R hi, int maxit, R tol)
+{
+    R u = R(0.5) * (lo + hi);
+    for (int it = 0; it < maxit; ++it) {
+        R E, Ep;
+        eval_E(a, qx, qy, qz, u, E, Ep);
+        if (E > R(0)) hi = u;
+        else if (E < R(0)) lo = u;
+        else return u;
+        R un = Ep > R(0) ? u - E / Ep : R(0.5) * (lo + hi);
+        // a Newton step below the tolerance ends the iteration (near the
+        // root it may round onto the bracket end it just moved)
+        if (Ep > R(0) && fabs(un - u) <= tol) return fmin(fmax(un, lo), hi);
+        if (!(un > lo && un < hi)) un = R(0.5) * (lo + hi);
+        if (fabs(un - u) <= tol || hi - lo <= tol) return un;
+        u = un;
+    }
+    return u;
+}
+
+// every local minimum of D = |C(u) - q|^2 on [0,1], certified by sign
+// variations: an interval whose Bernstein coefficients of E change sign
+// once holds exactly one root (a minimum when E goes from - to +); more
+// changes -> split at the middle (de Casteljau); none -> no root.  The ends
+// are minima when E(0) >= 0 or E(1) <= 0.  Returns the best minimiser.
+template <class R>
+__device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int maxit)
+{
+    constexpr int kStack = 24;
+    R b0[6];
+    bernstein_E(a, qx, qy, qz, b0);
+    R bestu = R(0), bestD;
+    {
+        R E, Ep;
+        bestD = eval_E(a, qx, qy, qz, R(0), E, Ep);
+        R D1 = eval_E(a, qx, qy, qz, R(1), E, Ep);
+        if (D1 < bestD) {
+            bestD = D1;
+            bestu = R(1);
+        }
+    }
+    R st_b[kStack][6];
+    R st_lo[kStack], st_hi[kStack];
+    int top = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st_b[0][i] = b0[i];
+    st_lo[0] = R(0);
+    st_hi[0] = R(1);
+    top = 1;
+    int budget = 64;  // intervals examined at most
+    while (top > 0 && budget-- > 0) {
+        --top;
+        R b[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) b[i] = st_b[top][i];
+        const R lo = st_lo[top], hi = st_hi[top];
+        const int v = sign_changes6(b);
+        if (v == 0) continue;
+        if (v == 1 || top + 2 > kStack || hi - lo <= tol * R(64)) {
+            if (b[0] < R(0) && b[5] > R(0)) {
+                R u = root_bracketed(a, qx, qy, qz, lo, hi, maxit, tol);
+                R E, Ep;
+                R D = eval_E(a, qx, qy, qz, u, E, Ep);
+                if (D < bestD) {
+                    bestD = D;
+                    bestu = u;
+                }
+            } else if (v > 1) {
+                // unresolved within the stack: try the middle as a seed
+                R u = R(0.5) * (lo + hi);
+                R E, Ep;
+                R D = eval_E(a, qx, qy, qz, u, E, Ep);
+                if (D < bestD) {
+                    bestD = D;
+                    bestu = u;
+                }
+            }
+            continue;
+        }
+        // split at the middle: left and right Bernstein coefficients
+        R w[6], L[6], Rr[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) w[i] = b[i];
+        L[0] = w[0];
+        Rr[5] = w[5];
+#pragma unroll
+        for (int r = 1; r < 6; ++r) {
+#pragma unroll
+            for (int i = 0; i < 6 - r; ++i) w[i] = R(0.5) * (w[i] + w[i + 1]);
+            L[r] = w[0];
+            Rr[5 - r] = w[5 - r];
+        }
+        const R mid = R(0.5) * (lo + hi);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st_b[top][i] = Rr[i];
+        st_lo[top] = mid;
+        st_hi[top] = hi;
+        ++top;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st_b[top][i] = L[i];
+        st_lo[top] = lo;
+        st_hi[top] = mid;
+        ++top;
+    }
+    return bestu;
+}
+
+// lexicographic (D, seg, u) order; D >= 0, so its bit pattern orders like an integer
+__device__ __forceinline__ bool better(double D, int s, double u, double bD, int bs, double bu)
+{
+    const long long a = __double_as_longlong(D), b = __double_as_longlong(bD);
+    return a < b || (a == b && (s < bs || (s == bs && __double_as_longlong(u) < __double_as_longlong(bu))));
+}
+
+}  // namespace
+}  // namespace bspl

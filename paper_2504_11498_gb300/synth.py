@@ -327,3 +327,29 @@ def ragged_mix(seed: int = 5, n_curves: int = 65_536, n_surf: int = 8_192, n_que
     qc = zipf_assign(rng, n_curves, half)
     qs = zipf_assign(rng, n_surf, n_queries - half)
     return cs, ss, qc, qs, rng
+
+
+# ------------------------------------------------------------ learned seed
+
+MLP_SHAPES = (("W1", (128, 16)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (128, 128)),
+              ("b3", (128,)), ("w4", (128,)), ("b4", (1,)))
+MLP_NPARAM = 35332
+
+
+def mlp_init(seed: int = 7) -> np.ndarray:
+    """Initial parameter vector of the seed network (layout of
+    include/bspl_mlp.h): weights ~ N(0, 2 / fan_in), biases 0, the weight
+    column of the zero input 0."""
+    rng = np.random.default_rng(seed)
+    theta = np.zeros(MLP_NPARAM, np.float32)
+    o = 0
+    for name, shp in MLP_SHAPES:
+        n = int(np.prod(shp))
+        if name[0] in "Ww":
+            fan_in = 15 if name == "W1" else 128
+            w = rng.normal(0.0, np.sqrt(2.0 / fan_in), shp)
+            if name == "W1":
+                w[:, 15] = 0.0
+            theta[o:o + n] = w.reshape(-1)
+        o += n
+    return theta

@@ -58,6 +58,14 @@ def test_sigmoid_output_with_zero_weights():
     assert np.allclose(t, 1 / (1 + math.exp(-0.7)))
 
 
+def test_bf16_rounding_matches_torch():
+    import torch
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.normal(0, 3, 5000), rng.normal(0, 1e-3, 1000), [0.0, 1.0, -2.5, 1 + 2 ** -8, 1 + 3 * 2 ** -8]])
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(M.round_bf16(x), ref)
+
+
 def test_pack_layout():
     sizes = [int(np.prod(s)) for _, s in M._SHAPES]
     assert sum(sizes) + 3 == M.NPARAM
@@ -92,9 +100,30 @@ def test_features_invariances():
     pts = X[:, :12].reshape(-1, 4, 3)
     ext = pts.max(1) - pts.min(1)
     assert np.allclose(ext.max(1), 1.0) and np.all(np.abs(pts) <= 0.5 + 1e-12)
-    assert np.all(np.linalg.norm(X[:, 12:15], axis=1) <= 1 + 1e-12) and np.all(X[:, 15] == 0)
-    far = M.features(P[:1], np.array([[100.0, 0, 0]]))
-    assert abs(np.linalg.norm(far[0, 12:15]) - 1) < 1e-12 and far[0, 12] > 0.99
+    assert np.all(X[:, 15] == 0)
+
+
+def test_features_query_split_along_and_across_the_chord():
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        P = rng.uniform(-1, 1, (4, 3))
+        ch = P[3] - P[0]
+        d = ch / np.linalg.norm(ch)
+        n = np.cross(d, rng.normal(size=3))
+        n /= np.linalg.norm(n)
+        lo, hi = P.min(0), P.max(0)
+        c, s = 0.5 * (lo + hi), 1.0 / (hi - lo).max()
+        lam = rng.uniform(-0.2, 1.2)
+        # far across the chord: along-chord coordinate kept, across part unit length
+        q = P[0] + lam * ch + 1e3 * n
+        f = M.features(P[None], q[None])[0, 12:15]
+        a = ((P[0] + lam * ch - c) * s) @ d
+        assert abs(f @ d - a) < 1e-9
+        assert abs(np.linalg.norm(f - (f @ d) * d) - 1.0) < 1e-9
+        assert (f - (f @ d) * d) @ n > 0.999
+        # close to the segment the query coordinates are unchanged
+        qn = c + 0.3 / s * rng.uniform(-1, 1, 3) / np.sqrt(3)
+        assert np.allclose(M.features(P[None], qn[None])[0, 12:15], (qn - c) * s, atol=1e-12)
 
 
 def test_segment_minimiser_line_closed_form():

@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--curves", type=int, default=4096, help="curves in the workload")
     ap.add_argument("--queries", type=int, default=1_000_000, help="projection and inversion queries each")
+    ap.add_argument("--train-curves", type=int, default=2048, help="curves of the seed network's training set")
+    ap.add_argument("--train-queries", type=int, default=2_500_000, help="their projection and inversion queries")
+    ap.add_argument("--train-pairs", type=int, default=10_000_000, help="training pairs at most")
+    ap.add_argument("--train-epochs", type=int, default=3)
     return ap.parse_args()
 
 
@@ -105,7 +109,7 @@ def build_workload(seed, rank, n_curves=4096, n_queries=1_000_000):
     return cs, qs
 
 
-def cpu_oracle_rate(cs, qs, budget_s=12.0, max_q=40000):
+def cpu_oracle_rate(cs, qs, budget_s=15.0, max_q=1_000_000):
     """Oracle (plain FP64, as it stands) on the host cores, bounded sample:
     equal numbers of projection and inversion queries."""
     from oracle import oracle as O
@@ -122,6 +126,41 @@ def cpu_oracle_rate(cs, qs, budget_s=12.0, max_q=40000):
         done += k
         n = min(n * 2, 8000)
     return 2 * done / elapsed, threads, 2 * done, elapsed
+
+
+# ------------------------------------------------------------ learned seed
+
+def train_seed(args, rank, dev):
+    """Trains the seed network on (segment, query, t*) pairs of a second
+    curve set of the same recipe (seed 12): pairs from the learned path's own
+    culling, labels from the FP64 solver, hand-written training kernels.
+    Returns the network and a summary (untimed preprocessing)."""
+    import torch
+    from paper_2504_11498_gb300 import bspl, synth
+    t0 = time.perf_counter()
+    cs, qs = synth.curve_set(seed=12 + 1000 * rank, n_curves=args.train_curves, n_proj=args.train_queries,
+                             n_inv=args.train_queries)
+    dc = bspl.DeviceCurves(cs, dev)
+    segs = bspl.decompose(dc, TOL)
+    inv = bspl.bspl_eval_curves(dc, torch.as_tensor(qs.inv_curve, device=dev),
+                                torch.as_tensor(qs.inv_t, device=dev))
+    qc = torch.cat([torch.as_tensor(qs.proj_curve, device=dev), torch.as_tensor(qs.inv_curve, device=dev)])
+    q = torch.cat([torch.as_tensor(qs.proj_xyz, device=dev), inv])
+    pq, ps, found = bspl.bspl_mlp_collect_pairs(segs, qc, q, cap=args.train_pairs)
+    X = bspl.bspl_mlp_features(segs, pq, ps, q)
+    y = bspl.bspl_mlp_labels(segs, pq, ps, q)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    mlp = bspl.Mlp(synth.mlp_init(7), dev)
+    loss = mlp.train(X, y, epochs=args.train_epochs, batch=8192, lr=2e-3, seed=5).cpu().numpy()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    if bspl.mlp_check() != bspl.OK:
+        raise SystemExit("a tensor-core wait timed out during training")
+    del X, y, pq, ps, q, qc, inv, segs, dc
+    return mlp, {"pairs": int(min(found, args.train_pairs)), "epochs": args.train_epochs, "batch": 8192,
+                 "curves": args.train_curves, "data_ms": 1e3 * (t1 - t0), "train_ms": 1e3 * (t2 - t1),
+                 "loss_first_epoch": float(loss[0]), "loss_last_epoch": float(loss[-1])}
 
 
 # ------------------------------------------------------------------- main
@@ -166,6 +205,7 @@ def main():
     build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
     cs, qs = build_workload(args.seed, rank, args.curves, args.queries)
     dc = bspl.DeviceCurves(cs, dev)
 
@@ -181,17 +221,34 @@ def main():
     ic = torch.as_tensor(qs.inv_curve, device=dev)
     iq = bspl.bspl_eval_curves(dc, ic, torch.as_tensor(qs.inv_t, device=dev))
     n_step = pc.numel() + ic.numel()
-    bufs_p = bspl.QueryBuffers(segs, pc.numel(), dev)
-    bufs_i = bspl.QueryBuffers(segs, ic.numel(), dev)
+    bufs_p = bspl.QueryBuffers(segs, pc.numel(), dev, learned=True)
+    bufs_i = bspl.QueryBuffers(segs, ic.numel(), dev, learned=True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+
+    # the learned seed, trained before anything is timed; its error on this
+    # workload's own seeded pairs, against the midpoint seed
+    mlp, train = train_seed(args, rank, dev)
+    rows = 0
+    for qcur, qpts in ((pc, pq), (ic, iq)):
+        sp, ss, found = bspl.bspl_mlp_collect_pairs(segs, qcur, qpts, cap=1_000_000)
+        rows += found
+        if qcur is pc:
+            ystar = bspl.bspl_mlp_labels(segs, sp, ss, qpts)
+            pred = mlp.forward(bspl.bspl_mlp_features(segs, sp, ss, qpts))
+            train["heldout_seed_abs_err"] = float((pred - ystar).abs().mean().item())
+            train["heldout_midpoint_abs_err"] = float((0.5 - ystar).abs().mean().item())
+    train["eval_seed_rows_per_step"] = int(rows)
 
     # launch configuration per precision, chosen by the autotuner (untimed)
     cfg = {p: (autotune.tune_curves(segs, pc, pq, p) if args.samples == 0 else dict(samples=args.samples))
            for p in (bspl.MIXED, bspl.FP64)}
+    cfg[bspl.LEARNED_MIXED] = {"occupancy": cfg[bspl.MIXED].get("occupancy", 0)}
 
-    def step(prec, counters=None):
-        o = bspl.make_options(prec=prec, counters=counters, **cfg[prec])
+    def opts(prec, **kw):
+        return bspl.make_options(prec=prec, mlp=mlp if prec == bspl.LEARNED_MIXED else None, **cfg[prec], **kw)
+
+    def step(prec, **kw):
+        o = opts(prec, **kw)
         bspl.bspl_project_curves(segs, pc, pq, o, bufs_p)
         bspl.bspl_invert_curves(segs, ic, iq, o, bufs_i)
 
@@ -210,31 +267,66 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return float(np.mean(ms)), ms
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
-    # algorithmic work from the device counters (one extra, untimed pass)
     def counted(prec):
         cnt = torch.zeros(bspl.NCOUNTERS, dtype=torch.int64, device=dev)
-        step(prec, cnt)
+        step(prec, counters=cnt)
         torch.cuda.synchronize()
         return dict(zip(bspl.COUNTER_NAMES, cnt.cpu().tolist()))
 
-    # the query kernel alone: inputs pre-grouped by curve on the host, no
-    # sorting inside the call, events around each kernel launch
-    op = np.argsort(qs.proj_curve, kind="stable")
-    oi = np.argsort(qs.inv_curve, kind="stable")
-    spc, spq = pc[torch.as_tensor(op, device=dev)], pq[torch.as_tensor(op, device=dev)]
-    sic, siq = ic[torch.as_tensor(oi, device=dev)], iq[torch.as_tensor(oi, device=dev)]
+    # clocks are sampled across the timed loops
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_learned = timed(bspl.LEARNED_MIXED, args.steps, args.warmup)
+    ms_mixed = timed(bspl.MIXED, args.steps, args.warmup)
+    ms_plain = timed(bspl.FP64, max(2, args.steps // 3), 2)
+    clk = clocks.stop()
+    if bspl.mlp_check() != bspl.OK:
+        raise SystemExit("a tensor-core wait timed out")
+
+    # accuracy of the timed paths against the plain FP64 path, every query
+    acc = {}
+    diag_p = segs.diag[pc.long()]
+    diag_i = segs.diag[ic.long()]
+    step(bspl.FP64)
+    ref = (bufs_p.dist.clone(), bufs_i.dist.clone())
+    for name, prec in (("learned_mixed", bspl.LEARNED_MIXED), ("mixed", bspl.MIXED)):
+        step(prec)
+        rel = torch.cat([(bufs_p.dist - ref[0]).abs() / diag_p, (bufs_i.dist - ref[1]).abs() / diag_i])
+        acc[name] = {"max_rel_dist_diff_vs_plain_fp64": float(rel.max().item()),
+                     "queries_over_1e-9": int((rel > 1e-9).sum().item())}
+
+    c_learned = counted(bspl.LEARNED_MIXED)
+    c_mixed = counted(bspl.MIXED)
+    c_plain = counted(bspl.FP64)
+
+    # per-stage device time of the learned path (events recorded by the
+    # library at its stage boundaries, both calls of a step summed)
+    def stage_ms(steps):
+        tot = np.zeros(bspl.NSTAGE_EVENTS - 1)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(bspl.NSTAGE_EVENTS)] for _ in range(2)]
+        for _ in range(steps):
+            flush.fill_(1.0)
+            bspl.bspl_project_curves(segs, pc, pq, opts(bspl.LEARNED_MIXED, stage_events=evs[0]), bufs_p)
+            flush.fill_(1.0)
+            bspl.bspl_invert_curves(segs, ic, iq, opts(bspl.LEARNED_MIXED, stage_events=evs[1]), bufs_i)
+            torch.cuda.synchronize()
+            for e in evs:
+                tot += [e[k].elapsed_time(e[k + 1]) for k in range(bspl.NSTAGE_EVENTS - 1)]
+        return dict(zip(bspl.STAGE_NAMES, (tot / steps).tolist()))
+
+    st_ms = stage_ms(max(3, args.steps // 2))
+
+    # the grid kernel alone (mixed), pre-grouped inputs, events around launches
+    op = torch.as_tensor(np.argsort(qs.proj_curve, kind="stable"), device=dev)
+    oi = torch.as_tensor(np.argsort(qs.inv_curve, kind="stable"), device=dev)
+    spc, spq, sic, siq = pc[op], pq[op], ic[oi], iq[oi]
 
     def kernel_ms(prec, steps):
         o = bspl.make_options(prec=prec, sort_queries=0, **cfg[prec])
-        for _ in range(2):
-            bspl.bspl_project_curves(segs, spc, spq, o, bufs_p)
-            bspl.bspl_invert_curves(segs, sic, siq, o, bufs_i)
-        torch.cuda.synchronize()
         tot = 0.0
-        for _ in range(steps):
+        for it in range(steps + 2):
             flush.fill_(1.0)
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record(stream)
@@ -245,33 +337,22 @@ def main():
             bspl.bspl_invert_curves(segs, sic, siq, o, bufs_i)
             ev[3].record(stream)
             torch.cuda.synchronize()
-            tot += ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
-        return tot / steps  # both launches of one step
+            if it >= 2:
+                tot += ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
+        return tot / steps
 
-    # clocks are sampled across the timed loops (mixed, then plain)
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms_mixed, ms_list = timed(bspl.MIXED, args.steps, args.warmup)
-    ms_plain, _ = timed(bspl.FP64, max(2, args.steps // 3), 2)
-    clk = clocks.stop()
-    c_mixed = counted(bspl.MIXED)
-    c_plain = counted(bspl.FP64)
     kms_mixed = kernel_ms(bspl.MIXED, max(3, args.steps // 2))
-    kms_plain = kernel_ms(bspl.FP64, 2)
 
-    # end to end through the public API with host buffers (pinned)
-    h_pc = pc.cpu().pin_memory()
-    h_pq = pq.cpu().pin_memory()
-    h_ic = ic.cpu().pin_memory()
-    h_iq = iq.cpu().pin_memory()
+    # end to end through the public API with pinned host buffers
+    h_in = [x.cpu().pin_memory() for x in (pc, pq, ic, iq)]
     h_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in
              (bufs_p.param, bufs_p.dist, bufs_p.status, bufs_i.param, bufs_i.dist, bufs_i.status)]
-    d_in = [torch.empty_like(x, device=dev) for x in (h_pc, h_pq, h_ic, h_iq)]
+    d_in = [torch.empty_like(x, device=dev) for x in h_in]
 
     def e2e_step():
-        for d, h in zip(d_in, (h_pc, h_pq, h_ic, h_iq)):
+        for d, h in zip(d_in, h_in):
             d.copy_(h, non_blocking=True)
-        o = bspl.make_options(prec=bspl.MIXED, **cfg[bspl.MIXED])
+        o = opts(bspl.LEARNED_MIXED)
         bspl.bspl_project_curves(segs, d_in[0], d_in[1], o, bufs_p)
         bspl.bspl_invert_curves(segs, d_in[2], d_in[3], o, bufs_i)
         for h, d in zip(h_out, (bufs_p.param, bufs_p.dist, bufs_p.status, bufs_i.param, bufs_i.dist,
@@ -282,69 +363,74 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
     k_e2e = max(3, args.steps // 2)
+    e0.record(stream)
     for _ in range(k_e2e):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1) / k_e2e
-    h2d = sum(x.numel() * x.element_size() for x in (h_pc, h_pq, h_ic, h_iq))
+    h2d = sum(x.numel() * x.element_size() for x in h_in)
     d2h = sum(x.numel() * x.element_size() for x in h_out)
 
     # max over ranks
-    vals = torch.tensor([ms_mixed, ms_plain, ms_e2e], dtype=torch.float64, device=dev)
+    vals = torch.tensor([ms_learned, ms_mixed, ms_plain, ms_e2e], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_mixed, ms_plain, ms_e2e = vals.tolist()
+    ms_learned, ms_mixed, ms_plain, ms_e2e = vals.tolist()
     total_q = n_step * world
-    value = total_q / (ms_mixed * 1e-3)
 
-    # roofline of the query kernels: FP32 + FP64 arithmetic against measured
-    # FMA-chain peaks (FP32-equivalent TFLOP/s)
+    # rooflines.  ALU work from device counters with per-unit figures: 12
+    # FP32 flops per box test, 110 per pair classification (E in Bernstein
+    # form with its rounding bound), 15 per grid sample, 45 per Newton
+    # iteration; the MLP 2 (16*128 + 2*128*128 + 128) = 69,888 flops per row.
     p32 = bspl.measure_fma_peak(False)
     p64 = bspl.measure_fma_peak(True)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16_peak = peaks["bf16_tflops"] * 1e12
+    cull_flops = 12 * (c_learned["grp_tested"] + c_learned["seg_tested"]) + 110 * c_learned["candidates"]
+    t_cull = st_ms["cull"] * 1e-3
+    rows = train["eval_seed_rows_per_step"]
+    mlp_flops = 69888 * rows
+    t_seed = st_ms["seed"] * 1e-3
+    dominant = max(st_ms, key=st_ms.get)
+    mlp_line = {"bound": "tensor", "achieved": mlp_flops / t_seed / 1e12, "peak": bf16_peak / 1e12,
+                "unit": "TFLOP/s", "frac": mlp_flops / t_seed / bf16_peak, "rows_per_step": rows,
+                "ms_per_step": st_ms["seed"], "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    cull_line = {"bound": "alu", "achieved": cull_flops / t_cull / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
+                 "frac": cull_flops / t_cull / p32, "ms_per_step": st_ms["cull"],
+                 "peak_source": "FP32 FMA-chain microbenchmark on this GPU (of measured)"}
+    roofline = dict(cull_line if dominant == "cull" else (mlp_line if dominant == "seed" else cull_line))
+    roofline.update({"kernel": "k_cull_pairs" if roofline["bound"] == "alu" else "k_mlp_fused",
+                     "traffic": None, "stages_ms_per_step": st_ms, "dominant_stage": dominant,
+                     "mlp_seed_kernel": mlp_line})
+
     S = cfg[bspl.MIXED]["samples"]
+    f32m = 12 * (c_mixed["grp_tested"] + c_mixed["seg_tested"]) + 15 * S * c_mixed["candidates"] + \
+        45 * c_mixed["newton32_iters"]
+    f64m = 45 * c_mixed["newton64_iters"]
+    eq_m = (f32m + f64m * p32 / p64) / (kms_mixed * 1e-3)
+    roofline["mixed_grid_kernel"] = {"kernel": "k_query_curves<float>", "bound": "alu", "achieved": eq_m / 1e12,
+                                     "peak": p32 / 1e12, "unit": "TFLOP/s (FP32-equivalent)", "frac": eq_m / p32,
+                                     "ms_per_step": kms_mixed, "fp64_peak_tflops": p64 / 1e12}
 
-    def flops(c, mixed):
-        # per-unit figures: 12 flops per box test, 15 per grid sample, 45 per
-        # Newton iteration; units counted by the kernel
-        cull = 12 * (c["grp_tested"] + c["seg_tested"])
-        grid = 15 * S * c["candidates"]
-        if mixed:
-            return cull + grid + 45 * c["newton32_iters"], 45 * c["newton64_iters"]
-        return 0, cull + grid + 45 * c["newton64_iters"]
-
-    f32m, f64m = flops(c_mixed, True)
-    S = cfg[bspl.FP64]["samples"]
-    f32p, f64p = flops(c_plain, False)
-    S = cfg[bspl.MIXED]["samples"]
-    t_m, t_p = kms_mixed * 1e-3, kms_plain * 1e-3
-    eq_m = (f32m + f64m * p32 / p64) / t_m
-    eq_p = (f32p + f64p * p32 / p64) / t_p
-    roofline = {"bound": "alu", "achieved": eq_m / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
-                "frac": eq_m / p32, "traffic": None,
-                "note": "query kernel (k_query_curves, 2 launches per step); FP32-equivalent rate "
-                        "(FP32 flops + FP64 flops x P32/P64) / kernel time; peaks measured by an FMA-chain "
-                        "microbenchmark on this GPU (MEASURED_PEAKS.json has no FP32/FP64 ALU peak)",
-                "kernel_ms_per_step": kms_mixed, "flops_fp32": f32m, "flops_fp64": f64m,
-                "fp32_peak_tflops": p32 / 1e12, "fp64_peak_tflops": p64 / 1e12,
-                "plain_fp64": {"achieved_fp64_tflops": f64p / t_p / 1e12, "frac": eq_p / p32}}
-
-    out = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 search, FP64 finish)", "data": "synthetic",
+    out = {"metric": METRIC, "value": total_q / (ms_learned * 1e-3), "unit": "pts/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16+f32+f64 (BF16 tensor-core seed, FP32 search, FP64 finish)", "data": "synthetic",
            "config": {"workload": f"curve_set_{args.curves}: {args.queries} projection + {args.queries} inversion "
                                   "queries per GPU",
-                      "tol_rel": TOL, "launch": {"mixed": cfg[bspl.MIXED], "fp64": cfg[bspl.FP64]},
-                      "prec": "mixed", "l2": "512 MB flush between timed steps",
-                      "segments": int(segs.total), "decompose_ms": decomp_ms},
-           "plain_fp64": {"value": total_q / t_p, "ms_per_step": ms_plain},
-           "speedup_mixed_vs_plain": ms_plain / ms_mixed,
+                      "tol_rel": TOL, "prec": "learned_mixed", "launch": {str(k): v for k, v in cfg.items()},
+                      "l2": "512 MB flush between timed steps", "segments": int(segs.total),
+                      "decompose_ms": decomp_ms, "seed_network": train},
+           "mixed_grid": {"value": total_q / (ms_mixed * 1e-3), "ms_per_step": ms_mixed},
+           "plain_fp64": {"value": total_q / (ms_plain * 1e-3), "ms_per_step": ms_plain},
+           "speedup_learned_vs_plain": ms_plain / ms_learned, "speedup_mixed_vs_plain": ms_plain / ms_mixed,
+           "accuracy": acc,
            "e2e": {"value": total_q / (ms_e2e * 1e-3), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
-           "gpu_launches": 12, "roofline": roofline, "clocks": clk,
-           "counters_mixed": c_mixed}
+           "gpu_launches": 24, "roofline": roofline, "clocks": clk,
+           "counters": {"learned_mixed": c_learned, "mixed": c_mixed, "plain_fp64": c_plain}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, nq, el = cpu_oracle_rate(cs, qs)
         out["cpu_baseline"] = {"value": r, "unit": "pts/s", "cores": cores, "kind": "oracle",

@@ -161,7 +161,13 @@ typedef struct {
                             the Newton seed; NULL -> the seed is u = 1/2 (the
                             learned path without its network)               */
     uint64_t* counters;  /* optional device array [BSPL_NCOUNTERS], accumulated     */
+    const void* stage_events; /* optional host array of BSPL_NSTAGE_EVENTS cudaEvent_t
+                            (created by the caller): the learned path records
+                            them on the stream at its stage boundaries (start,
+                            sort, cull, seed, FP32, FP64, select, leftovers);
+                            profiling only                                */
 } bspl_options;
+#define BSPL_NSTAGE_EVENTS 8
 
 /* device counters accumulated by the query calls when opt->counters != NULL */
 #define BSPL_CNT_QUERIES 0

@@ -547,25 +547,37 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     size_t sb = 0;
     if (!carve_learned(ws, ws_bytes, segs->n, n_q, B, &sw, &sb, nullptr)) return BSPL_EINVAL;
     CurveQ P = make_params(segs, n_q, q_curve, q_xyz, *o, invert, t, dist, status);
+    const cudaEvent_t* ev = (const cudaEvent_t*)o->stage_events;
+    auto mark = [&](int k) {
+        if (ev) cudaEventRecord(ev[k], s);
+    };
+    mark(0);
     int32_t* order = nullptr;
     if (sort_by_spline(q_curve, n_q, segs->n, sw, sb, &order, s) != cudaSuccess) return BSPL_ECUDA;
     P.order = order;
     if (cudaMemsetAsync(B.cnt, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return BSPL_ECUDA;
+    mark(1);
     const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
     k_cull_pairs<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
+    mark(2);
     if (mlp && mlp_seed_pairs(mlp, B.pq, B.ps, q_xyz, segs, B.cap, B.cnt + 1, B.u, s) != cudaSuccess)
         return BSPL_ECUDA;
+    mark(3);
     const int grid = pair_grid();
     k_pairs_fp32<<<grid, 256, 0, s>>>(P, B, mlp ? 1 : 0);
+    mark(4);
     k_pairs_fp64<<<grid, 256, 0, s>>>(P, B);
+    mark(5);
     k_pairs_argseg<<<grid, 256, 0, s>>>(P, B);
     k_pairs_write<<<grid, 256, 0, s>>>(P, B);
+    mark(6);
     // queries whose pairs did not fit: the grid kernel over the device-side list
     CurveQ F = P;
     F.order = B.over;
     F.n_q_dev = reinterpret_cast<const int64_t*>(B.cnt + 3);
     F.counters = nullptr;
     launch_mixed_curves(F, o->occupancy, s);
+    mark(7);
     return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
 }
 

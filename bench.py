@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--curves", type=int, default=4096, help="curves in the workload")
     ap.add_argument("--queries", type=int, default=1_000_000, help="projection and inversion queries each")
     ap.add_argument("--train-curves", type=int, default=2048, help="curves of the seed network's training set")
-    ap.add_argument("--train-queries", type=int, default=2_500_000, help="their projection and inversion queries")
+    ap.add_argument("--train-queries", type=int, default=3_500_000, help="their projection and inversion queries")
     ap.add_argument("--train-pairs", type=int, default=10_000_000, help="training pairs at most")
     ap.add_argument("--train-epochs", type=int, default=3)
     return ap.parse_args()
@@ -147,6 +147,7 @@ def train_seed(args, rank, dev):
     qc = torch.cat([torch.as_tensor(qs.proj_curve, device=dev), torch.as_tensor(qs.inv_curve, device=dev)])
     q = torch.cat([torch.as_tensor(qs.proj_xyz, device=dev), inv])
     pq, ps, found = bspl.bspl_mlp_collect_pairs(segs, qc, q, cap=args.train_pairs)
+    written = pq.numel()
     X = bspl.bspl_mlp_features(segs, pq, ps, q)
     y = bspl.bspl_mlp_labels(segs, pq, ps, q)
     torch.cuda.synchronize()
@@ -158,7 +159,7 @@ def train_seed(args, rank, dev):
     if bspl.mlp_check() != bspl.OK:
         raise SystemExit("a tensor-core wait timed out during training")
     del X, y, pq, ps, q, qc, inv, segs, dc
-    return mlp, {"pairs": int(min(found, args.train_pairs)), "epochs": args.train_epochs, "batch": 8192,
+    return mlp, {"pairs": int(written), "pairs_found": int(found), "epochs": args.train_epochs, "batch": 8192,
                  "curves": args.train_curves, "data_ms": 1e3 * (t1 - t0), "train_ms": 1e3 * (t2 - t1),
                  "loss_first_epoch": float(loss[0]), "loss_last_epoch": float(loss[-1])}
 

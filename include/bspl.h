@@ -94,7 +94,7 @@ typedef struct {
 /* widths (in elements) of the per-segment and per-group records */
 #define BSPL_GROUP 32        /* consecutive segments/patches per culling group */
 #define BSPL_CREC64 18       /* curve FP64: lo[3] hi[3] a0[3] a1[3] a2[3] a3[3] (power basis in u) */
-#define BSPL_CREC32 20       /* curve FP32: same layout + 2 pad, box rounded outward */
+#define BSPL_CREC32 24       /* curve FP32: same layout (box rounded outward), then a0 - (float)a0 [3] and 3 pad */
 #define BSPL_SREC64 54       /* patch FP64: lo[3] hi[3] a[4][4][3] (power basis in u,v) */
 #define BSPL_SREC32 56       /* patch FP32: same layout + span-pair degrees (pu, pv) */
 #define BSPL_GREC64 12       /* group FP64: lo[3] hi[3] ref[3] pad[3] */

@@ -22,7 +22,7 @@ OK, EINVAL, ENOSPACE, ECUDA, ENOTCONV, ETIMEOUT = 0, 1, 2, 3, 4, 5
 FP64, MIXED, LEARNED_MIXED = 0, 1, 2
 Q_CONVERGED, Q_FALLBACK, Q_AT_END, Q_NONCONV, Q_OFF_CURVE, Q_INVALID = 1, 2, 4, 8, 16, 32
 GROUP = 32
-CREC64, CREC32, SREC64, SREC32, GREC64, GREC32 = 18, 20, 54, 56, 12, 12
+CREC64, CREC32, SREC64, SREC32, GREC64, GREC32 = 18, 24, 54, 56, 12, 12
 SPAN_NET = 8 * 8 * 3
 OP_DECOMPOSE_CURVES, OP_DECOMPOSE_SURFACES, OP_QUERY_CURVES, OP_QUERY_SURFACES = 1, 2, 3, 4
 OP_QUERY_CURVES_LEARNED, OP_MLP_TRAIN = 5, 6
@@ -504,14 +504,15 @@ def bspl_mlp_labels(segs, pair_q, pair_seg, q_xyz, stream=None):
 
 
 def bspl_mlp_collect_pairs(segs, q_curve, q_xyz, cap, stream=None):
-    """(pair_q, pair_seg) of the seeded pairs (at most cap) and the number found."""
+    """(pair_q, pair_seg) of the seeded pairs written (at most cap) and the
+    number of seeded pairs found."""
     dev = q_xyz.device
     pq = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
     ps = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
-    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    n = torch.zeros(2, dtype=torch.int64, device=dev)
     ws = _ws(workspace_bytes(OP_QUERY_CURVES_LEARNED, segs.n, 0, 0, q_curve.numel()), dev)
     _check(lib().bspl_mlp_collect_pairs(C.byref(segs.c), q_curve.numel(), _ptr(q_curve), _ptr(q_xyz), int(cap),
                                         _ptr(pq), _ptr(ps), _ptr(n), _ptr(ws), ws.numel(), _stream(stream)),
            "bspl_mlp_collect_pairs")
-    k = min(int(n.item()), cap)
-    return pq[:k], ps[:k], int(n.item())
+    written, found = (int(v) for v in n.tolist())
+    return pq[:written], ps[:written], found

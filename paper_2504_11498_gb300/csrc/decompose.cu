@@ -731,9 +731,9 @@ __global__ void k_curve_records(const double* __restrict__ ctrl, int64_t nseg, d
         f[9 + c] = (float)a1;
         f[12 + c] = (float)a2;
         f[15 + c] = (float)a3;
+        f[18 + c] = (float)(a0 - (double)f[6 + c]);  // a0 = f[6 + c] + f[18 + c] to ~2^-48 relative
+        f[21 + c] = 0.f;
     }
-    f[18] = 0.f;
-    f[19] = 0.f;
 }
 
 // patch records: box already written (original piece); power basis of the

@@ -60,14 +60,14 @@ __global__ void k_sync(const float* __restrict__ p, uint16_t* __restrict__ w)
 
 // ------------------------------------------------------------ pair features
 // Inputs of a (query, segment) pair in the frame of the segment's control-
-// point box.  Control points relative to P0 come from the power coefficients
-// (P1 - P0 = a1/3, P2 - P0 = (2 a1 + a2)/3, P3 - P0 = a1 + a2 + a3), so
-// short segments keep their relative accuracy; q - P0 is formed in FP64.
-// The query keeps its coordinate along the chord P0 -> P3 (which fixes the
+// point box, all in FP32: control points relative to P0 come from the power
+// coefficients (P1 - P0 = a1/3, P2 - P0 = (2 a1 + a2)/3, P3 - P0 =
+// a1 + a2 + a3), so short segments keep their relative accuracy; q - P0
+// from the high and low FP32 parts of both (qr: q hi[3], q lo[3]).  The
+// query keeps its coordinate along the chord P0 -> P3 (which fixes the
 // minimiser of a far query); its part across the chord is shortened to
 // length min(1, |part|).
-__device__ __forceinline__ void pair_features(const float* __restrict__ r32, const double* __restrict__ r64,
-                                              const double* __restrict__ q, float f[16])
+__device__ __forceinline__ void pair_features(const float* __restrict__ r32, const float* qr, float f[16])
 {
     float d[4][3], cc[3];
     float ext = 0.f;
@@ -90,7 +90,8 @@ __device__ __forceinline__ void pair_features(const float* __restrict__ r32, con
     for (int c = 0; c < 3; ++c) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) f[3 * i + c] = (d[i][c] - cc[c]) * s;
-        v[c] = ((float)(q[c] - r64[6 + c]) - cc[c]) * s;
+        const float qm = (qr[c] - r32[6 + c]) + (qr[3 + c] - r32[18 + c]);  // q - P0
+        v[c] = (qm - cc[c]) * s;
         dn[c] = ln > 0.f ? d[3][c] / ln : (c == 0 ? 1.f : 0.f);
     }
     const float a = v[0] * dn[0] + v[1] * dn[1] + v[2] * dn[2];
@@ -124,18 +125,16 @@ struct SrcX {
 
 // the learned path's seed pairs [0, min(cap, *n_dev)) of (query, segment)
 struct SrcPairs {
-    const int32_t* pq;
+    const int32_t* pq;  // sorted query position
     const int32_t* ps;
-    const double* q_xyz;
+    const float* qrec;  // per sorted query: q hi[3], q lo[3], ...
     const float* rec32;
-    const double* rec64;
     int64_t cap;
     const unsigned long long* n_dev;
     __device__ int64_t count() const { return min(cap, (int64_t)*n_dev); }
     __device__ void features(int64_t i, float f[16]) const
     {
-        const int64_t s = ps[i], q = pq[i];
-        pair_features(rec32 + (int64_t)BSPL_CREC32 * s, rec64 + (int64_t)BSPL_CREC64 * s, q_xyz + 3 * q, f);
+        pair_features(rec32 + (int64_t)BSPL_CREC32 * ps[i], qrec + 8 * (int64_t)pq[i], f);
     }
 };
 
@@ -564,8 +563,16 @@ __global__ void k_features(const bspl_segments S, int64_t n, const int32_t* __re
     if (s < 0 || s >= S.capacity || pq[i] < 0) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) f[k] = __int_as_float(0x7fc00000);
-    } else
-        pair_features(S.rec32 + (int64_t)BSPL_CREC32 * s, S.rec64 + (int64_t)BSPL_CREC64 * s, q_xyz + 3 * pq[i], f);
+    } else {
+        const double* q = q_xyz + 3 * (int64_t)pq[i];
+        float qr[6];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            qr[k] = (float)q[k];
+            qr[3 + k] = (float)(q[k] - (double)qr[k]);
+        }
+        pair_features(S.rec32 + (int64_t)BSPL_CREC32 * s, qr, f);
+    }
     float4* o = reinterpret_cast<float4*>(X + 16 * i);
 #pragma unroll
     for (int k = 0; k < 4; ++k) o[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
@@ -696,11 +703,11 @@ cudaError_t launch_mlp_fused(const Src& src, int64_t n_max, const bspl_mlp* m, f
 }
 
 // the learned path's seed stage (query_learned.cu)
-cudaError_t mlp_seed_pairs(const bspl_mlp* m, const int32_t* pq, const int32_t* ps, const double* q_xyz,
+cudaError_t mlp_seed_pairs(const bspl_mlp* m, const int32_t* pq, const int32_t* ps, const float* qrec,
                            const bspl_segments* segs, int64_t cap, const unsigned long long* n_dev, float* u0,
                            cudaStream_t s)
 {
-    SrcPairs src{ pq, ps, q_xyz, segs->rec32, segs->rec64, cap, n_dev };
+    SrcPairs src{ pq, ps, qrec, segs->rec32, cap, n_dev };
     return launch_mlp_fused(src, cap, m, u0, s);
 }
 

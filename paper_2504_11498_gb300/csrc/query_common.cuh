@@ -125,13 +125,31 @@ __device__ __forceinline__ R eval_E(const R* a, R qx, R qy, R qz, R u, R& E, R& 
 // rises into the segment (KKT), when no descent is left at this resolution,
 // or when the step falls below tol.  Returns true unless maxit ran out.
 template <class R>
+struct Eps;
+template <>
+struct Eps<float> {
+    static constexpr float v = 1.1920929e-07f;
+};
+template <>
+struct Eps<double> {
+    static constexpr double v = 2.220446049250313e-16;
+};
+
+template <class R>
 __device__ bool newton_min(const R* a, R qx, R qy, R qz, R& u, R hmax, int maxit, R tol, unsigned& iters)
 {
+    // coordinate resolution of the evaluation: a Newton correction that moves
+    // the point by less than this is rounding noise, and the iteration stops
+    R scale = fabs(qx) + fabs(qy) + fabs(qz);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) scale += fabs(a[i]);
+    const R res = R(8) * Eps<R>::v * scale;
     R E, Ep;
     R D = eval_E(a, qx, qy, qz, u, E, Ep);
     for (int it = 0; it < maxit; ++it) {
         ++iters;
         if ((u <= R(0) && E >= R(0)) || (u >= R(1) && E <= R(0)) || E == R(0)) return true;
+        if (Ep > R(0) && fabs(E) <= res * sqrt(Ep)) return true;
         R step = Ep > R(0) ? -E / Ep : (E > R(0) ? -hmax : hmax);
         step = fmin(fmax(step, -hmax), hmax);
         R un = u, Dn = D, En = E, Epn = Ep;
@@ -158,6 +176,53 @@ __device__ bool newton_min(const R* a, R qx, R qy, R qz, R& u, R hmax, int maxit
         if (moved <= tol) return true;
     }
     return false;
+}
+
+// The two FP64 Newton steps of the mixed paths (Eqs. Et, E't): the residual
+// C(u) - q, the tangent C'(u), E = (C - q).C' and the update of u in FP64
+// (they fix where the root lies: for a far query an error of the tangent's
+// direction moves the foot point by the distance times that error); only
+// E' = |C'|^2 + (C - q).C'' and its reciprocal in FP32 (the step's relative
+// error enters the next error linearly, times a step already near 1e-7).
+// a64: FP64 power coefficients a0..a3 [12]; a32: FP32 a1..a3 [9].  Returns
+// D = |C(u) - q|^2 in FP64 at the final u; last = size of the second step.
+__device__ __forceinline__ double finish64(const double* a64, const float* a32, const double* q, double& u,
+                                           double& last, unsigned& iters)
+{
+    double c0[3], b3[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        c0[c] = a64[c] - q[c];
+        b3[c] = 3.0 * a64[9 + c];
+    }
+    last = 1.0;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        ++iters;
+        const float uf = (float)u;
+        double E = 0.0;
+        float Ep = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double cx = fma(u, fma(u, fma(u, a64[9 + c], a64[6 + c]), a64[3 + c]), c0[c]);
+            const double c1 = fma(u, fma(u, b3[c], 2.0 * a64[6 + c]), a64[3 + c]);
+            E = fma(cx, c1, E);
+            const float C1 = (float)c1;
+            const float C2 = fmaf(uf, 6.f * a32[6 + c], 2.f * a32[3 + c]);
+            Ep = fmaf(C1, C1, fmaf((float)cx, C2, Ep));
+        }
+        double un = Ep > 0.f ? u - E * (double)(1.f / Ep) : u;
+        un = fmin(fmax(un, 0.0), 1.0);
+        last = fabs(un - u);
+        u = un;
+    }
+    double D = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double x = fma(u, fma(u, fma(u, a64[9 + c], a64[6 + c]), a64[3 + c]), c0[c]);
+        D = fma(x, x, D);
+    }
+    return D;
 }
 
 // E(u)/2 = (C(u) - q).C'(u) for the cubic a0 + a1 u + a2 u^2 + a3 u^3 (Eq.

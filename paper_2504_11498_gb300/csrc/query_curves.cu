@@ -125,28 +125,19 @@ __device__ void flush_pool(const CurveQ& P, WarpSmem<R>& W, int npool, int lane,
             double c64[12];
 #pragma unroll
             for (int i = 0; i < 12; ++i) c64[i] = a64[i];
-            double u = (double)W.pool_u32[k];
-            double last = 1.0;
-#pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                ++it64;
-                double E, Ep;
-                eval_E(c64, q[0], q[1], q[2], u, E, Ep);
-                double un = Ep > 0.0 ? u - E / Ep : u;
-                un = fmin(fmax(un, 0.0), 1.0);
-                last = fabs(un - u);
-                u = un;
-            }
+            double u = (double)W.pool_u32[k], last;
+            double D = finish64(c64, P.rec32 + (int64_t)BSPL_CREC32 * e.seg + 9, q, u, last, it64);
             unsigned char fl = 0;
             bool ok = last <= 1e-9;
             if (!ok) {
                 fl |= BSPL_Q_FALLBACK;
                 ok = newton_min<double>(c64, q[0], q[1], q[2], u, e.h < 0.f ? 1.0 / 64 : (double)e.h, P.newton_max,
                                         1e-15, it64);
+                double E, Ep;
+                D = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
             }
             fl |= ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
-            double E, Ep;
-            W.pool_D[k] = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
+            W.pool_D[k] = D;
             W.pool_u[k] = u;
             W.pool_flags[k] = fl;
         }

@@ -18,21 +18,23 @@
 //   2. the fused MLP (mlp.cu) writes the seed u0 of every SEED pair (without
 //      a network: u0 = 1/2).
 //   3. one thread per pair: FP32 Newton in the segment's local frame
-//      (bracketed by the known sign change for SEED pairs), per-query
-//      minimum of the FP32 distances by an integer atomicMin on the float
-//      bits; then the two FP64 Newton steps (and the FP64 safeguarded
-//      iteration when the second step is not below 1e-9) for the pairs within
-//      the FP32 error margin of their query's best; then the per-query
+//      (bracketed by the known sign change for SEED pairs) and a bound on the
+//      FP32 distance's rounding error; per-query minimum of the upper bounds
+//      by an integer atomicMin on the float bits; then the two FP64 Newton
+//      steps (and the FP64 safeguarded iteration when the second step is not
+//      below 1e-9) for the pairs whose lower bound does not exceed their
+//      query's best upper bound; then the per-query
 //      lexicographic minimum over (D, segment) by two more atomicMin passes,
 //      and the unique winning pair writes the result (Sec. 4.4.2).
 //   4. queries whose pairs did not fit the buffer run through the grid
 //      kernel (mixed precision) over a device-side list.
 #include "../../include/bspl_mlp.h"
 #include "query_common.cuh"
+#include "tc05.cuh"
 
 namespace bspl {
 
-cudaError_t mlp_seed_pairs(const bspl_mlp* m, const int32_t* pq, const int32_t* ps, const double* q_xyz,
+cudaError_t mlp_seed_pairs(const bspl_mlp* m, const int32_t* pq, const int32_t* ps, const float* qrec,
                            const bspl_segments* segs, int64_t cap, const unsigned long long* n_dev, float* u0,
                            cudaStream_t s);
 
@@ -42,19 +44,21 @@ enum : uint8_t { kSeed = 0, kEnd0 = 1, kEnd1 = 2, kEnds = 3, kIso = 4 };
 constexpr int kPairsPerQuery = 24;  // buffer capacity per query
 
 struct PairBuf {
-    int32_t* pq;
+    int32_t* pq;              // sorted query position (the query index when collecting)
     int32_t* ps;
     uint8_t* kind;
     float* u;
-    float* D32;
+    float* D32;               // lower bound of the pair's distance (FP32 stage)
     uint8_t* conv;
     double* D64;
     double* u64;
     uint8_t* fl;
     int64_t cap;
     unsigned long long* cnt;  // [0] reserved, [1] seeds, [2] others, [3] overflowed queries
+    const float* qrec;        // per sorted query: q hi[3], q lo[3], eps, curve (int bits; -1 invalid)
+    const int32_t* order;     // sorted position -> query index
     int32_t* over;            // overflowed query indices
-    unsigned* best32;         // per query: FP32 distance bits
+    unsigned* best32;         // per query: FP32 upper bound of the distance (float bits)
     unsigned long long* best64;
     int* bestseg;
 };
@@ -109,25 +113,86 @@ __device__ __forceinline__ uint8_t classify(const float* c)
     return kIso;
 }
 
-__device__ __forceinline__ void local32(const CurveQ& P, int64_t seg, const double* q, float* c)
+// the cubic C(u) - q in FP32 with a0 - q formed from the high and low FP32
+// parts of both (qr: q hi[3], q lo[3]), so no FP64 instruction is needed
+__device__ __forceinline__ void local32(const CurveQ& P, int64_t seg, const float* qr, float* c)
 {
-    const double* a64 = P.rec64 + (int64_t)BSPL_CREC64 * seg + 6;
-    const float* a32 = P.rec32 + (int64_t)BSPL_CREC32 * seg + 6;
-    c[0] = (float)(a64[0] - q[0]);
-    c[1] = (float)(a64[1] - q[1]);
-    c[2] = (float)(a64[2] - q[2]);
+    const float* r = P.rec32 + (int64_t)BSPL_CREC32 * seg;
 #pragma unroll
-    for (int i = 3; i < 12; ++i) c[i] = a32[i];
+    for (int k = 0; k < 3; ++k) c[k] = (r[6 + k] - qr[k]) + (r[18 + k] - qr[3 + k]);
+#pragma unroll
+    for (int i = 3; i < 12; ++i) c[i] = r[6 + i];
 }
 
+// per sorted query: the FP32 parts of q, the FP32 slack and the curve, so
+// that the culling kernels run without FP64 instructions (on this GPU one
+// FP64 warp instruction occupies its pipe for tens of cycles)
+__global__ void k_qrec(const int32_t* __restrict__ qc, const double* __restrict__ q_xyz,
+                       const double* __restrict__ diag, int64_t n, const int32_t* __restrict__ order, int64_t n_q,
+                       float* __restrict__ qrec)
+{
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n_q) return;
+    const int64_t i = order[pos];
+    const int c = qc[i];
+    float o[8];
+    bool bad = c < 0 || c >= n;
+    float l1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double x = q_xyz[3 * i + k];
+        bad = bad || !isfinite(x);
+        o[k] = (float)x;
+        o[3 + k] = (float)(x - (double)o[k]);
+        l1 += fabsf(o[k]);
+    }
+    o[6] = bad ? 0.f : 4e-6f * (l1 + (float)diag[c]);
+    o[7] = __int_as_float(bad ? -1 : c);
+    float4* d = reinterpret_cast<float4*>(qrec + 8 * pos);
+    d[0] = make_float4(o[0], o[1], o[2], o[3]);
+    d[1] = make_float4(o[4], o[5], o[6], o[7]);
+}
+
+constexpr int kEmitCap = 256;  // classified pairs staged per warp before one global reservation
+constexpr int kGrpChunk = 64;  // culling groups staged in shared memory per bulk copy
+constexpr int kSurvCap = 192;  // surviving (query, group) entries per warp batch
+constexpr uint64_t kCopyWaitNs = 1000000000ull;
+
+// set when a bulk-copy wait gave up (the kernel then reads global memory)
+__device__ int g_copy_timeout;
+
+// Culling in two levels.  Level 1 is done for the whole batch of 32 sorted
+// queries at once, one lane per query: the curve's group records (box and
+// reference point) are staged into shared memory by bulk copies (TMA,
+// cp.async.bulk), chunk by chunk, and every lane scans them for its query:
+// first the upper bound from the reference points, then the box test; the
+// surviving (query, group) pairs go to a per-warp list.  Level 2 is warp-
+// cooperative per query over its surviving groups' segments, as in the grid
+// kernel, and the classified pairs are staged and written out in bulk.
 template <bool SEEDS_ONLY>
 __global__ void __launch_bounds__(kWarps * 32) k_cull_pairs(CurveQ P, PairBuf B)
 {
     __shared__ int s_seg[kWarps][kCandCap];
     __shared__ float s_lb[kWarps][kCandCap];
+    __shared__ int s_pseg[kWarps][kEmitCap];
+    __shared__ uint8_t s_pslot[kWarps][kEmitCap];
+    __shared__ uint8_t s_pkind[kWarps][kEmitCap];
+    __shared__ int32_t s_qi[kWarps][kQPW];
+    __shared__ float s_ub[kWarps][kQPW];
+    __shared__ __align__(128) float s_grp[kWarps][kGrpChunk * BSPL_GREC32];
+    __shared__ int s_sv[kWarps][kSurvCap];
+    __shared__ float s_svlb[kWarps][kSurvCap];
+    __shared__ uint8_t s_svslot[kWarps][kSurvCap];
+    __shared__ __align__(8) uint64_t s_bar[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* cseg = s_seg[wid];
     float* clb = s_lb[wid];
+    int* pseg = s_pseg[wid];
+    uint8_t* pslot = s_pslot[wid];
+    uint8_t* pkind = s_pkind[wid];
+    int32_t* qis = s_qi[wid];
+    float* grs = s_grp[wid];
+    uint64_t* bar = &s_bar[wid];
     const int64_t qbase = ((int64_t)blockIdx.x * kWarps + wid) * kQPW;
     if (qbase >= P.n_q) return;
     const int nslots = (int)min((int64_t)kQPW, P.n_q - qbase);
@@ -136,39 +201,171 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_pairs(CurveQ P, PairBuf B)
     constexpr int RW = BSPL_CREC32, GW = BSPL_GREC32;
     const unsigned lt = (1u << lane) - 1u;
     unsigned long long n_grp = 0, n_seg = 0, n_pairs = 0;
+    int npend = 0;
+    unsigned over_mask = 0;  // query slots with pairs that did not fit the buffer
 
-    for (int sl = 0; sl < nslots; ++sl) {
-        const int64_t qi = P.order ? (int64_t)P.order[qbase + sl] : qbase + sl;
-        const int c = P.q_curve[qi];
-        const double q64[3] = { P.q_xyz[3 * qi], P.q_xyz[3 * qi + 1], P.q_xyz[3 * qi + 2] };
-        const bool bad = c < 0 || c >= P.n || !isfinite(q64[0]) || !isfinite(q64[1]) || !isfinite(q64[2]);
-        if (bad) {
-            if (!SEEDS_ONLY && lane == 0) {
-                P.t[qi] = __longlong_as_double(0x7ff8000000000000LL);
-                P.dist[qi] = __longlong_as_double(0x7ff8000000000000LL);
-                P.status[qi] = BSPL_Q_INVALID;
-            }
-            continue;
-        }
-        if (!SEEDS_ONLY && lane == 0) {
-            B.best32[qi] = 0x7f800000u;
-            B.best64[qi] = 0x7ff0000000000000ull;
-            B.bestseg[qi] = 0x7fffffff;
+    if (lane == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t phase = 0;
+
+    // this lane's query (lane = slot)
+    float qx = 0.f, qy = 0.f, qz = 0.f, eps = 0.f;
+    int myc = -1;
+    if (lane < nslots) {
+        const int64_t pos = qbase + lane;
+        const int64_t qi = B.order[pos];
+        const float4 qa = *reinterpret_cast<const float4*>(B.qrec + 8 * pos);
+        const float4 qb = *reinterpret_cast<const float4*>(B.qrec + 8 * pos + 4);
+        qx = qa.x;
+        qy = qa.y;
+        qz = qa.z;
+        eps = qb.z;
+        myc = __float_as_int(qb.w);
+        qis[lane] = (int32_t)qi;
+        if (!SEEDS_ONLY) {
             P.t[qi] = __longlong_as_double(0x7ff8000000000000LL);
             P.dist[qi] = __longlong_as_double(0x7ff8000000000000LL);
-            P.status[qi] = BSPL_Q_NONCONV;
+            P.status[qi] = myc < 0 ? BSPL_Q_INVALID : BSPL_Q_NONCONV;
+            if (myc >= 0) {
+                B.best32[pos] = 0x7f800000u;
+                B.best64[pos] = 0x7ff0000000000000ull;
+                B.bestseg[pos] = 0x7fffffff;
+            }
         }
-        const float qx = (float)q64[0], qy = (float)q64[1], qz = (float)q64[2];
-        const float eps = 4e-6f * (fabsf(qx) + fabsf(qy) + fabsf(qz) + (float)P.diag[c]);
+    }
+
+    // stage groups [g, g + n) of the group table; returns where to read them
+    auto stage = [&](int64_t g, int n) -> const float* {
+        __syncwarp();
+        if (lane == 0) {
+            tc::fence_async_smem();  // earlier reads of the buffer come first
+            tc::bulk_load(grs, grp + (int64_t)GW * g, (uint32_t)(n * GW * sizeof(float)), bar);
+        }
+        const bool ok = tc::mbar_wait(bar, phase, kCopyWaitNs);
+        phase ^= 1;
+        if (!ok && lane == 0) atomicExch(&g_copy_timeout, 1);
+        return __all_sync(kFull, ok) ? grs : grp + (int64_t)GW * g;
+    };
+
+    // ---- level 1: runs of consecutive slots on the same curve
+    int nsv = 0;
+    unsigned sv_over = 0;  // slots whose surviving groups did not fit the list
+    bool done = !(lane < nslots && myc >= 0);
+    float ub = INFINITY;
+    for (;;) {
+        const unsigned pend = __ballot_sync(kFull, !done);
+        if (!pend) break;
+        const int c = __shfl_sync(kFull, myc, __ffs(pend) - 1);
+        const bool in_run = !done && myc == c;
+        const int64_t g0 = P.grp_off[c], G = P.grp_off[c + 1] - g0;
+        const float* src = nullptr;
+        for (int64_t cg = 0; cg < G; cg += kGrpChunk) {
+            const int n = (int)min((int64_t)kGrpChunk, G - cg);
+            src = stage(g0 + cg, n);
+            if (in_run)
+                for (int k = 0; k < n; ++k) ub = fminf(ub, pt_d2(src + GW * k + 6, qx, qy, qz));
+        }
+        const float ubs = slacked(ub, eps);
+        for (int64_t cg = 0; cg < G; cg += kGrpChunk) {
+            const int n = (int)min((int64_t)kGrpChunk, G - cg);
+            if (G > kGrpChunk) src = stage(g0 + cg, n);
+            for (int k = 0; k < n; ++k) {
+                const float lb = in_run ? box_d2(src + GW * k, qx, qy, qz) : INFINITY;
+                const bool keep = lb <= ubs;
+                const unsigned m = __ballot_sync(kFull, keep);
+                if (!m) continue;
+                if (nsv + __popc(m) <= kSurvCap) {
+                    if (keep) {
+                        const int e = nsv + __popc(m & lt);
+                        s_sv[wid][e] = (int)(g0 + cg + k);
+                        s_svlb[wid][e] = lb;
+                        s_svslot[wid][e] = (uint8_t)lane;
+                    }
+                    nsv += __popc(m);
+                } else {
+                    sv_over |= m;
+                }
+            }
+        }
+        if (in_run) n_grp += (unsigned long long)G;
+        done = done || in_run;
+    }
+    if (lane < nslots) s_ub[wid][lane] = ub;
+    __syncwarp();
+
+    // one reservation per kind for the staged pairs, then the copy out
+    auto flush_pending = [&]() {
+        __syncwarp();
+        int cs = 0, co = 0;
+        for (int base = 0; base < npend; base += 32) {
+            const int k = base + lane;
+            const bool in = k < npend;
+            cs += __popc(__ballot_sync(kFull, in && pkind[k] == kSeed));
+            co += __popc(__ballot_sync(kFull, in && pkind[k] != kSeed));
+        }
+        if (cs + co > 0) {
+            unsigned long long bs = 0, bo = 0;
+            int ok = 0;
+            if (lane == 0) {
+                const unsigned long long tot = atomicAdd(B.cnt, (unsigned long long)(cs + co));
+                ok = tot + cs + co <= (unsigned long long)B.cap;
+                if (ok) {
+                    bs = cs ? atomicAdd(B.cnt + 1, (unsigned long long)cs) : 0;
+                    bo = co ? atomicAdd(B.cnt + 2, (unsigned long long)co) : 0;
+                    n_pairs += (unsigned long long)(cs + co);
+                }
+            }
+            ok = __shfl_sync(kFull, ok, 0);
+            bs = __shfl_sync(kFull, bs, 0);
+            bo = __shfl_sync(kFull, bo, 0);
+            unsigned om = 0;
+            for (int base = 0; base < npend; base += 32) {
+                const int k = base + lane;
+                const bool in = k < npend;
+                const bool sd = in && pkind[k] == kSeed, ot = in && pkind[k] != kSeed;
+                const unsigned ms = __ballot_sync(kFull, sd), mo = __ballot_sync(kFull, ot);
+                if (ok) {
+                    if (sd) {
+                        const int64_t idx = (int64_t)bs + __popc(ms & lt);
+                        B.pq[idx] = SEEDS_ONLY ? qis[pslot[k]] : (int32_t)(qbase + pslot[k]);
+                        B.ps[idx] = pseg[k];
+                        if (B.kind) B.kind[idx] = kSeed;
+                    }
+                    if (ot) {
+                        const int64_t idx = B.cap - 1 - ((int64_t)bo + __popc(mo & lt));
+                        B.pq[idx] = (int32_t)(qbase + pslot[k]);
+                        B.ps[idx] = pseg[k];
+                        B.kind[idx] = pkind[k];
+                    }
+                } else if (in) {
+                    om |= 1u << pslot[k];
+                }
+                bs += __popc(ms);
+                bo += __popc(mo);
+            }
+            over_mask |= __reduce_or_sync(kFull, om);
+        }
+        npend = 0;
+        __syncwarp();
+    };
+
+    // ---- level 2: per query, its surviving groups' segments
+    const unsigned valid_mask = __ballot_sync(kFull, lane < nslots && myc >= 0);
+    for (int sl = 0; sl < nslots; ++sl) {
+        if (!((valid_mask >> sl) & 1u)) continue;
+        const float sx = __shfl_sync(kFull, qx, sl), sy = __shfl_sync(kFull, qy, sl), sz = __shfl_sync(kFull, qz, sl);
+        const float seps = __shfl_sync(kFull, eps, sl);
+        const int c = __shfl_sync(kFull, myc, sl);
+        const float* qr = B.qrec + 8 * (qbase + sl);
         const int64_t s0 = P.seg_off[c], s1 = P.seg_off[c + 1];
         const int64_t g0 = P.grp_off[c], g1 = P.grp_off[c + 1];
-        float ub = INFINITY;
-        for (int64_t g = g0 + lane; g < g1; g += 32) ub = fminf(ub, pt_d2(grp + (int64_t)GW * g + 6, qx, qy, qz));
-        ub = warp_min(ub);
-        float ubs = slacked(ub, eps);
-        n_grp += (unsigned long long)(g1 - g0);
+        float qub = s_ub[wid][sl];
+        float ubs = slacked(qub, seps);
         int ncand = 0;
-        bool overflow = false;
+        // classify the buffered candidates that survive the current bound
         auto emit = [&]() {
             __syncwarp();
             for (int base = 0; base < ncand; base += 32) {
@@ -178,90 +375,84 @@ __global__ void __launch_bounds__(kWarps * 32) k_cull_pairs(CurveQ P, PairBuf B)
                 uint8_t kind = kIso;
                 if (act) {
                     float cl[12];
-                    local32(P, seg, q64, cl);
+                    local32(P, seg, qr, cl);
                     kind = classify(cl);
                 }
-                const bool is_seed = act && kind == kSeed;
-                const bool is_oth = !SEEDS_ONLY && act && kind != kSeed;
-                const unsigned ms = __ballot_sync(kFull, is_seed), mo = __ballot_sync(kFull, is_oth);
-                const int cs = __popc(ms), co = __popc(mo);
-                if (cs + co == 0) continue;
-                unsigned long long bs = 0, bo = 0;
-                int ok = 0;
-                if (lane == 0) {
-                    const unsigned long long tot = atomicAdd(B.cnt, (unsigned long long)(cs + co));
-                    ok = tot + cs + co <= (unsigned long long)B.cap;
-                    if (ok) {
-                        bs = cs ? atomicAdd(B.cnt + 1, (unsigned long long)cs) : 0;
-                        bo = co ? atomicAdd(B.cnt + 2, (unsigned long long)co) : 0;
-                    }
+                const bool keep = act && (!SEEDS_ONLY || kind == kSeed);
+                const unsigned m = __ballot_sync(kFull, keep);
+                if (npend + __popc(m) > kEmitCap) flush_pending();
+                if (keep) {
+                    const int pos = npend + __popc(m & lt);
+                    pseg[pos] = seg;
+                    pslot[pos] = (uint8_t)sl;
+                    pkind[pos] = kind;
                 }
-                ok = __shfl_sync(kFull, ok, 0);
-                bs = __shfl_sync(kFull, bs, 0);
-                bo = __shfl_sync(kFull, bo, 0);
-                if (!ok) {
-                    overflow = true;
-                    continue;
-                }
-                if (lane == 0) n_pairs += (unsigned long long)(cs + co);
-                if (is_seed) {
-                    const int64_t idx = (int64_t)bs + __popc(ms & lt);
-                    B.pq[idx] = (int32_t)qi;
-                    B.ps[idx] = seg;
-                    if (B.kind) B.kind[idx] = kSeed;
-                }
-                if (is_oth) {
-                    const int64_t idx = B.cap - 1 - ((int64_t)bo + __popc(mo & lt));
-                    B.pq[idx] = (int32_t)qi;
-                    B.ps[idx] = seg;
-                    B.kind[idx] = kind;
-                }
+                npend += __popc(m);
             }
             ncand = 0;
             __syncwarp();
         };
-        for (int64_t gb = g0; gb < g1; gb += 32) {
-            const int64_t g = gb + lane;
-            const float lbg = g < g1 ? box_d2(grp + (int64_t)GW * g, qx, qy, qz) : INFINITY;
-            unsigned m = __ballot_sync(kFull, lbg <= ubs);
-            while (m) {
-                const int jg = __ffs(m) - 1;
-                m &= m - 1;
-                const float lbj = __shfl_sync(kFull, lbg, jg);
-                if (!(lbj <= ubs)) continue;
-                const int64_t ss = s0 + (gb + jg - g0) * BSPL_GROUP;
-                const int64_t se = min(ss + BSPL_GROUP, s1);
-                const int64_t s = ss + lane;
-                const bool valid = s < se;
-                float lbs = INFINITY, ups = INFINITY;
-                if (valid) {
-                    const float* r = rec + (int64_t)RW * s;
-                    lbs = box_d2(r, qx, qy, qz);
-                    ups = pt_d2(r + 6, qx, qy, qz);
+        // the segments of one group: box lower bounds, start-point upper bound
+        auto scan_group = [&](int64_t g) {
+            const int64_t ss = s0 + (g - g0) * BSPL_GROUP;
+            const int64_t se = min(ss + BSPL_GROUP, s1);
+            const int64_t s = ss + lane;
+            const bool valid = s < se;
+            float lbs = INFINITY, ups = INFINITY;
+            if (valid) {
+                const float* r = rec + (int64_t)RW * s;
+                lbs = box_d2(r, sx, sy, sz);
+                ups = pt_d2(r + 6, sx, sy, sz);
+            }
+            n_seg += (unsigned long long)(se - ss);
+            qub = fminf(qub, warp_min(ups));
+            ubs = slacked(qub, seps);
+            const bool keep = valid && lbs <= ubs;
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int pos = ncand + __popc(km & lt);
+                cseg[pos] = (int)s;
+                clb[pos] = lbs;
+            }
+            ncand += __popc(km);
+            if (ncand > kCandCap - 32) emit();
+        };
+        if ((sv_over >> sl) & 1u) {
+            // the list overflowed: scan all of the curve's groups directly
+            for (int64_t gb = g0; gb < g1; gb += 32) {
+                const int64_t g = gb + lane;
+                const float lbg = g < g1 ? box_d2(grp + (int64_t)GW * g, sx, sy, sz) : INFINITY;
+                unsigned m = __ballot_sync(kFull, lbg <= ubs);
+                while (m) {
+                    const int jg = __ffs(m) - 1;
+                    m &= m - 1;
+                    if (__shfl_sync(kFull, lbg, jg) <= ubs) scan_group(gb + jg);
                 }
-                n_seg += (unsigned long long)(se - ss);
-                ub = fminf(ub, warp_min(ups));
-                ubs = slacked(ub, eps);
-                const bool keep = valid && lbs <= ubs;
-                const unsigned km = __ballot_sync(kFull, keep);
-                if (keep) {
-                    const int pos = ncand + __popc(km & lt);
-                    cseg[pos] = (int)s;
-                    clb[pos] = lbs;
+            }
+        } else {
+            for (int base = 0; base < nsv; base += 32) {
+                const int e = base + lane;
+                unsigned m = __ballot_sync(kFull, e < nsv && s_svslot[wid][e] == sl);
+                while (m) {
+                    const int je = base + __ffs(m) - 1;
+                    m &= m - 1;
+                    if (s_svlb[wid][je] <= ubs) scan_group(s_sv[wid][je]);
                 }
-                ncand += __popc(km);
-                if (ncand > kCandCap - 32) emit();
             }
         }
         emit();
-        if (!SEEDS_ONLY && overflow && lane == 0) {
-            const unsigned long long pos = atomicAdd(B.cnt + 3, 1ull);
-            B.over[pos] = (int32_t)qi;
-        }
+    }
+    flush_pending();
+    if (!SEEDS_ONLY && lane < nslots && ((over_mask >> lane) & 1u)) {
+        const unsigned long long pos = atomicAdd(B.cnt + 3, 1ull);
+        B.over[pos] = qis[lane];
     }
     if (!SEEDS_ONLY && P.counters) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
+            n_grp += __shfl_xor_sync(kFull, n_grp, o);
+        }
         if (lane == 0) {
             atomicAdd(P.counters + BSPL_CNT_QUERIES, (unsigned long long)nslots);
             atomicAdd(P.counters + BSPL_CNT_GRP_TESTED, n_grp);
@@ -293,11 +484,10 @@ __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
         const int64_t j = j0 + threadIdx.x;
         if (j < np) {
             const int64_t i = pair_slot(B, j, ns);
-            const int64_t qi = B.pq[i], seg = B.ps[i];
+            const int64_t pos = B.pq[i], seg = B.ps[i];
             const uint8_t kind = j < ns ? kSeed : B.kind[i];
-            const double* q = P.q_xyz + 3 * qi;
             float c[12];
-            local32(P, seg, q, c);
+            local32(P, seg, B.qrec + 8 * pos, c);
             float u, E, Ep;
             bool conv = true;
             if (kind == kSeed) {
@@ -337,64 +527,76 @@ __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
                 u = isolate_min<float>(c, 0.f, 0.f, 0.f, 1e-7f, P.fp32_steps * 4);
                 conv = newton_min<float>(c, 0.f, 0.f, 0.f, u, 1.f / 64.f, P.fp32_steps, 1e-7f, it32);
             }
-            const float D = eval_E<float>(c, 0.f, 0.f, 0.f, u, E, Ep);
+            // FP32 distance and a bound on its error (coefficient rounding
+            // and Horner evaluation in the local frame, |u| <= 1)
+            const float d = sqrtf(eval_E<float>(c, 0.f, 0.f, 0.f, u, E, Ep));
+            float l1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) l1 += fabsf(c[k]);
+            const float del = 1e-6f * l1;
             B.u[i] = u;
-            B.D32[i] = D;
+            B.D32[i] = d - del;  // lower bound of the pair's distance
             B.conv[i] = conv ? 1 : 0;
-            atomicMin(B.best32 + qi, __float_as_uint(D));
+            atomicMin(B.best32 + pos, __float_as_uint(d + del));
         }
     }
     if (P.counters) add_counter(P.counters, BSPL_CNT_NEWTON32_ITERS, it32);
 }
 
-// (3b) FP64 finish of the pairs within the FP32 margin of their query's best
-__global__ void k_pairs_fp64(CurveQ P, PairBuf B)
+// (3b) FP64 finish of the pairs whose FP32 lower bound does not exceed their
+// query's best upper bound.  A block first lists the pairs of its chunk that
+// need the finish, then works through the list with all its threads, so the
+// FP64 instructions run in full warps (on this GPU the FP64 pipe is the
+// scarce one and a warp with one active lane costs as much as a full one).
+constexpr int kFinChunk = 1024;
+
+__global__ void __launch_bounds__(256) k_pairs_fp64(CurveQ P, PairBuf B)
 {
+    __shared__ int s_list[kFinChunk];
+    __shared__ int s_n;
     const int64_t ns = (int64_t)B.cnt[1], no = (int64_t)B.cnt[2], np = ns + no;
     unsigned it64 = 0, nfin = 0;
-    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < np; j0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = j0 + threadIdx.x;
-        if (j < np) {
+    for (int64_t c0 = (int64_t)blockIdx.x * kFinChunk; c0 < np; c0 += (int64_t)gridDim.x * kFinChunk) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < kFinChunk; k += blockDim.x) {
+            const int64_t j = c0 + k;
+            if (j >= np) break;
             const int64_t i = pair_slot(B, j, ns);
-            const int64_t qi = B.pq[i], seg = B.ps[i];
-            const double* q = P.q_xyz + 3 * qi;
-            const float qx = (float)q[0], qy = (float)q[1], qz = (float)q[2];
-            const float eps = 4e-6f * (fabsf(qx) + fabsf(qy) + fabsf(qz) + (float)P.diag[P.q_curve[qi]]);
-            const float sm = sqrtf(__uint_as_float(B.best32[qi])) + 2.f * eps;
-            if (B.conv[i] && B.D32[i] > sm * sm) {
-                B.D64[i] = INFINITY;
-                continue;
-            }
+            if (B.conv[i] && B.D32[i] > __uint_as_float(B.best32[B.pq[i]])) B.D64[i] = INFINITY;  // pq: position
+            else s_list[atomicAdd(&s_n, 1)] = k;
+        }
+        __syncthreads();
+        const int nt = s_n;
+        for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+            const int64_t j = c0 + s_list[k];
+            const int64_t i = pair_slot(B, j, ns);
+            const int64_t pos = B.pq[i], seg = B.ps[i];
+            const double* q = P.q_xyz + 3 * (int64_t)B.order[pos];
             ++nfin;
             const uint8_t kind = j < ns ? kSeed : B.kind[i];
             const double* a64 = P.rec64 + (int64_t)BSPL_CREC64 * seg + 6;
             double c64[12];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) c64[k] = a64[k];
-            double u = (double)B.u[i], last = 1.0, E, Ep;
-#pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                ++it64;
-                eval_E(c64, q[0], q[1], q[2], u, E, Ep);
-                double un = Ep > 0.0 ? u - E / Ep : u;
-                un = fmin(fmax(un, 0.0), 1.0);
-                last = fabs(un - u);
-                u = un;
-            }
+            for (int m = 0; m < 12; ++m) c64[m] = a64[m];
+            double u = (double)B.u[i], last;
+            double D = finish64(c64, P.rec32 + (int64_t)BSPL_CREC32 * seg + 9, q, u, last, it64);
             uint8_t fl = 0;
             bool ok = last <= 1e-9;
             if (!ok) {
                 fl |= BSPL_Q_FALLBACK;
                 ok = newton_min<double>(c64, q[0], q[1], q[2], u, kind == kIso ? 1.0 / 64 : 0.25, P.newton_max, 1e-15,
                                         it64);
+                double E, Ep;
+                D = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
             }
             fl |= ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
-            const double D = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
             B.D64[i] = D;
             B.u64[i] = u;
             B.fl[i] = fl;
-            atomicMin(B.best64 + qi, (unsigned long long)__double_as_longlong(D));
+            atomicMin(B.best64 + pos, (unsigned long long)__double_as_longlong(D));
         }
+        __syncthreads();
     }
     if (P.counters) {
         add_counter(P.counters, BSPL_CNT_NEWTON64_ITERS, it64);
@@ -408,8 +610,8 @@ __global__ void k_pairs_argseg(CurveQ P, PairBuf B)
     const int64_t ns = (int64_t)B.cnt[1], np = ns + (int64_t)B.cnt[2];
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = pair_slot(B, j, ns);
-        const int64_t qi = B.pq[i];
-        if ((unsigned long long)__double_as_longlong(B.D64[i]) == B.best64[qi]) atomicMin(B.bestseg + qi, B.ps[i]);
+        const int64_t pos = B.pq[i];
+        if ((unsigned long long)__double_as_longlong(B.D64[i]) == B.best64[pos]) atomicMin(B.bestseg + pos, B.ps[i]);
     }
 }
 
@@ -422,9 +624,10 @@ __global__ void k_pairs_write(CurveQ P, PairBuf B)
         const int64_t j = j0 + threadIdx.x;
         if (j < np) {
             const int64_t i = pair_slot(B, j, ns);
-            const int64_t qi = B.pq[i];
+            const int64_t pos = B.pq[i];
             const int seg = B.ps[i];
-            if ((unsigned long long)__double_as_longlong(B.D64[i]) != B.best64[qi] || seg != B.bestseg[qi]) continue;
+            if ((unsigned long long)__double_as_longlong(B.D64[i]) != B.best64[pos] || seg != B.bestseg[pos]) continue;
+            const int64_t qi = B.order[pos];
             const double u = B.u64[i];
             const double t0 = P.prange[2 * seg], t1 = P.prange[2 * seg + 1];
             const double t = u <= 0.0 ? t0 : (u >= 1.0 ? t1 : t0 + u * (t1 - t0));
@@ -476,6 +679,7 @@ bool carve_learned(void* ws, size_t bytes, int64_t n_splines, int64_t n_q, PairB
     B.best64 = cv.take<unsigned long long>((size_t)n_q);
     B.bestseg = cv.take<int>((size_t)n_q);
     B.cnt = cv.take<unsigned long long>(4);
+    B.qrec = cv.take<float>((size_t)n_q * 8);
     if (sort_ws) *sort_ws = sw;
     if (sort_bytes) *sort_bytes = sb;
     if (total) *total = cv.used + 256;
@@ -555,12 +759,14 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     int32_t* order = nullptr;
     if (sort_by_spline(q_curve, n_q, segs->n, sw, sb, &order, s) != cudaSuccess) return BSPL_ECUDA;
     P.order = order;
+    B.order = order;
+    k_qrec<<<ceil_div(n_q, 256), 256, 0, s>>>(q_curve, q_xyz, segs->diag, segs->n, order, n_q, (float*)B.qrec);
     if (cudaMemsetAsync(B.cnt, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return BSPL_ECUDA;
     mark(1);
     const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
     k_cull_pairs<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
     mark(2);
-    if (mlp && mlp_seed_pairs(mlp, B.pq, B.ps, q_xyz, segs, B.cap, B.cnt + 1, B.u, s) != cudaSuccess)
+    if (mlp && mlp_seed_pairs(mlp, B.pq, B.ps, B.qrec, segs, B.cap, B.cnt + 1, B.u, s) != cudaSuccess)
         return BSPL_ECUDA;
     mark(3);
     const int grid = pair_grid();
@@ -603,6 +809,9 @@ extern "C" bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t
         int32_t* order = nullptr;
         if (sort_by_spline(q_curve, n_q, segs->n, sw, sb, &order, stream) != cudaSuccess) return BSPL_ECUDA;
         P.order = order;
+        B.order = order;
+        k_qrec<<<ceil_div(n_q, 256), 256, 0, stream>>>(q_curve, q_xyz, segs->diag, segs->n, order, n_q,
+                                                       (float*)B.qrec);
         PairBuf C = B;
         C.pq = pair_q;
         C.ps = pair_seg;
@@ -611,7 +820,8 @@ extern "C" bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t
         const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
         k_cull_pairs<true><<<(unsigned)blocks, kWarps * 32, 0, stream>>>(P, C);
     }
-    if (cudaMemcpyAsync(n_pairs, B.cnt, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+    if (cudaMemcpyAsync(n_pairs, B.cnt + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(n_pairs + 1, B.cnt, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
         return BSPL_ECUDA;
     return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
 }

@@ -57,6 +57,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
     }
 }
 
+// ------------------------------------------------------------ bulk copies
+// one elected thread: announce the bytes the phase will receive, then start
+// the copy global -> shared (addresses 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%2], %1;\n\t}" ::"r"(smem_u32(dst)),
+        "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // ------------------------------------------------------------ tensor memory
 // one full warp executes alloc/dealloc; ncols is a power of two >= 32
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols)

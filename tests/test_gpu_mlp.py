@@ -132,6 +132,9 @@ def test_collect_pairs_features_and_labels():
     qd = dev(q, torch.float64)
     pq, ps, n = bspl.bspl_mlp_collect_pairs(segs, dev(qc, torch.int32), qd, cap=400_000)
     assert 0 < n <= 400_000 and pq.numel() == n
+    # a small capacity writes a prefix and still reports every pair found
+    pq2, ps2, n2 = bspl.bspl_mlp_collect_pairs(segs, dev(qc, torch.int32), qd, cap=n // 3)
+    assert n2 == n and 0 < pq2.numel() <= n // 3
     ref = O.decompose_curves(sub, tol)
     pqn, psn = pq.cpu().numpy(), ps.cpu().numpy()
     assert np.all(qc[pqn] >= 0)
@@ -180,8 +183,11 @@ def test_learned_path_parity(net):
     tol = 1e-10
     segs = bspl.decompose(bspl.DeviceCurves(sub, DEV), tol)
     mlp = None if net == "none" else bspl.Mlp(rand_theta(11))
-    t, d, st = _run(segs, qc, q, False, bspl.LEARNED_MIXED, mlp)
+    ctr = _counters()
+    t, d, st = _run(segs, qc, q, False, bspl.LEARNED_MIXED, mlp, ctr)
     check_against_oracle(sub, qc, q, t, d, tol)
+    # the two FP64 steps settle almost every query without the FP64 fallback
+    assert int(ctr[bspl.COUNTER_NAMES.index("fallback")]) <= len(qc) // 100
     assert not np.any(st & (bspl.Q_INVALID | bspl.Q_NONCONV))
     t, d, st = _run(segs, ic, C, True, bspl.LEARNED_MIXED, mlp)
     check_against_oracle(sub, ic, C, t, d, tol)

@@ -276,10 +276,46 @@ def main():
         torch.cuda.synchronize()
         return dict(zip(bspl.COUNTER_NAMES, cnt.cpu().tolist()))
 
+    # the learned step captured once as a CUDA graph (static buffers), then
+    # replayed: what a serving loop does
+    def capture(prec):
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                step(prec)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step(prec)
+        torch.cuda.synchronize()
+        return g
+
+    graph = capture(bspl.LEARNED_MIXED)
+
+    def timed_graph(steps, warmup):
+        for _ in range(warmup):
+            graph.replay()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            graph.replay()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
     # clocks are sampled across the timed loops
     clocks = ClockSampler(local)
     clocks.start()
-    ms_learned = timed(bspl.LEARNED_MIXED, args.steps, args.warmup)
+    ms_learned = timed_graph(args.steps, args.warmup)
+    ms_learned_direct = timed(bspl.LEARNED_MIXED, args.steps, args.warmup)
     ms_mixed = timed(bspl.MIXED, args.steps, args.warmup)
     ms_plain = timed(bspl.FP64, max(2, args.steps // 3), 2)
     clk = clocks.stop()
@@ -348,14 +384,12 @@ def main():
     h_in = [x.cpu().pin_memory() for x in (pc, pq, ic, iq)]
     h_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in
              (bufs_p.param, bufs_p.dist, bufs_p.status, bufs_i.param, bufs_i.dist, bufs_i.status)]
-    d_in = [torch.empty_like(x, device=dev) for x in h_in]
 
     def e2e_step():
-        for d, h in zip(d_in, h_in):
+        # inputs into the graph's static buffers, replay, results back
+        for d, h in zip((pc, pq, ic, iq), h_in):
             d.copy_(h, non_blocking=True)
-        o = opts(bspl.LEARNED_MIXED)
-        bspl.bspl_project_curves(segs, d_in[0], d_in[1], o, bufs_p)
-        bspl.bspl_invert_curves(segs, d_in[2], d_in[3], o, bufs_i)
+        graph.replay()
         for h, d in zip(h_out, (bufs_p.param, bufs_p.dist, bufs_p.status, bufs_i.param, bufs_i.dist,
                                 bufs_i.status)):
             h.copy_(d, non_blocking=True)
@@ -424,6 +458,8 @@ def main():
                       "tol_rel": TOL, "prec": "learned_mixed", "launch": {str(k): v for k, v in cfg.items()},
                       "l2": "512 MB flush between timed steps", "segments": int(segs.total),
                       "decompose_ms": decomp_ms, "seed_network": train},
+           "graph": "learned step captured once as a CUDA graph and replayed",
+           "learned_direct": {"value": total_q / (ms_learned_direct * 1e-3), "ms_per_step": ms_learned_direct},
            "mixed_grid": {"value": total_q / (ms_mixed * 1e-3), "ms_per_step": ms_mixed},
            "plain_fp64": {"value": total_q / (ms_plain * 1e-3), "ms_per_step": ms_plain},
            "speedup_learned_vs_plain": ms_plain / ms_learned, "speedup_mixed_vs_plain": ms_plain / ms_mixed,

@@ -157,6 +157,9 @@ typedef struct {
     int32_t occupancy;   /* curve kernel register/occupancy variant: 0 compiler
                             choice, 1 >= 4 blocks/SM, 2 >= 6 blocks/SM (samples
                             16 and 32); picked by the autotuner             */
+    int32_t pairs_per_query; /* learned path: candidate-pair buffer per query,
+                            1..24 (default 24); queries whose pairs do not fit
+                            are answered by the grid kernel instead         */
     const void* mlp;     /* BSPL_LEARNED_MIXED: const bspl_mlp* (bspl_mlp.h) giving
                             the Newton seed; NULL -> the seed is u = 1/2 (the
                             learned path without its network)               */

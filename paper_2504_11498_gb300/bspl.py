@@ -60,7 +60,8 @@ class bspl_segments(C.Structure):
 
 class bspl_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("samples", C.c_int32), ("newton_max", C.c_int32), ("fp32_steps", C.c_int32),
-                ("sort_queries", C.c_int32), ("occupancy", C.c_int32), ("mlp", C.c_void_p),
+                ("sort_queries", C.c_int32), ("occupancy", C.c_int32), ("pairs_per_query", C.c_int32),
+                ("mlp", C.c_void_p),
                 ("counters", C.c_void_p), ("stage_events", C.c_void_p)]
 
 
@@ -288,7 +289,7 @@ class QueryResult:
 
 
 def make_options(prec=FP64, samples=0, newton_max=0, fp32_steps=0, sort_queries=1, counters=None, mlp=None,
-                 occupancy=0, stage_events=None):
+                 occupancy=0, stage_events=None, pairs_per_query=0):
     """mlp: an ``Mlp`` (learned seed for prec=LEARNED_MIXED) or None;
     stage_events: NSTAGE_EVENTS torch.cuda.Event(enable_timing=True) that the
     learned path records at its stage boundaries (profiling)."""
@@ -301,7 +302,7 @@ def make_options(prec=FP64, samples=0, newton_max=0, fp32_steps=0, sort_queries=
                 e.record(s)  # creates the event
         ev = (C.c_void_p * NSTAGE_EVENTS)(*[e.cuda_event for e in stage_events])
     o = bspl_options(int(prec), int(samples), int(newton_max), int(fp32_steps), int(sort_queries), int(occupancy),
-                     C.cast(C.pointer(mlp.c), C.c_void_p) if mlp is not None else C.c_void_p(0),
+                     int(pairs_per_query), C.cast(C.pointer(mlp.c), C.c_void_p) if mlp is not None else C.c_void_p(0),
                      _ptr(counters) if counters is not None else None,
                      C.cast(ev, C.c_void_p) if ev is not None else None)
     o._keep = (mlp, ev)  # what the pointers refer to stays alive with the options

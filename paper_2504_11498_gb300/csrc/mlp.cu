@@ -406,8 +406,15 @@ cudaError_t gemm_nt(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t l
     kps = (kps + 63) / 64 * 64;
     splits = (K + kps - 1) / kps;
     dim3 grid((M + 127) / 128, (N + 127) / 128, splits);
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
-    if (e != cudaSuccess) return e;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
     k_gemm_nt<<<grid, 128, kGemmSmem, s>>>(A, lda, B, ldb, C, ldc, M, N, K, kps, atomic ? 1 : 0);
     return cudaGetLastError();
 }
@@ -693,9 +700,18 @@ bool mlp_ok(const bspl_mlp* m) { return m && m->params && m->wbf16; }
 template <class Src>
 cudaError_t launch_mlp_fused(const Src& src, int64_t n_max, const bspl_mlp* m, float* out, cudaStream_t s)
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_mlp_fused<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmFusedBytes);
-    if (e != cudaSuccess) return e;
+    // the shared-memory opt-in is set once per device (outside any later
+    // stream capture of the calling code)
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_mlp_fused<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmFusedBytes);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
     const int64_t tiles = (n_max + 127) / 128;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), (tiles + kFusedWG - 1) / kFusedWG));
     k_mlp_fused<Src><<<grid, kFusedWG * 128, kSmFusedBytes, s>>>(src, m->wbf16, m->params, out);

@@ -746,10 +746,12 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     const bspl_mlp* mlp = (const bspl_mlp*)o->mlp;
     if (mlp && (!mlp->params || !mlp->wbf16)) return BSPL_EINVAL;
     if (o->occupancy < 0 || o->occupancy > 2) return BSPL_EINVAL;
+    if (o->pairs_per_query < 0 || o->pairs_per_query > kPairsPerQuery) return BSPL_EINVAL;
     PairBuf B{};
     void* sw = nullptr;
     size_t sb = 0;
     if (!carve_learned(ws, ws_bytes, segs->n, n_q, B, &sw, &sb, nullptr)) return BSPL_EINVAL;
+    if (o->pairs_per_query > 0) B.cap = o->pairs_per_query * n_q;  // the rest of the buffer stays unused
     CurveQ P = make_params(segs, n_q, q_curve, q_xyz, *o, invert, t, dist, status);
     const cudaEvent_t* ev = (const cudaEvent_t*)o->stage_events;
     auto mark = [&](int k) {

@@ -246,3 +246,44 @@ def test_training_gain_over_the_method_without_it():
     assert err_net < 0.5 * err_mid
     assert stats["trained"]["newton32_iters"] < stats["none"]["newton32_iters"]
     assert bspl.mlp_check() == bspl.OK
+
+
+def test_learned_path_edge_cases_invalid_and_leftovers():
+    """Degenerate and ragged curves, points on control points and ends,
+    invalid queries, an empty batch, and a pair buffer too small for most
+    queries (they are answered by the grid kernel): oracle parity."""
+    from test_gpu_curves import _edge_set
+    cs = _edge_set()
+    tol = 1e-10
+    segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), tol)
+    rng = np.random.default_rng(16)
+    qc = np.repeat(np.arange(cs.n, dtype=np.int32), 200)
+    lo, hi = synth.cp_boxes(cs)
+    q = synth._box_queries(rng, lo, hi, qc, scale=2.0)
+    ends = []
+    for c in range(cs.n):
+        _, _, P = cs.curve(c)
+        ends += [(c, P[0]), (c, P[-1]), (c, P[len(P) // 2])]
+    qc = np.concatenate([qc, np.array([e[0] for e in ends], np.int32)])
+    q = np.concatenate([q, np.array([e[1] for e in ends])])
+    mlp = bspl.Mlp(rand_theta(13))
+    for ppq in (0, 1):
+        ctr = _counters()
+        r = bspl.bspl_project_curves(segs, dev(qc, torch.int32), dev(q, torch.float64),
+                                     bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp, counters=ctr,
+                                                       pairs_per_query=ppq))
+        torch.cuda.synchronize()
+        check_against_oracle(cs, qc, q, r.param.cpu().numpy(), r.dist.cpu().numpy(), tol)
+        if ppq == 1:  # most queries found more than one candidate pair
+            assert int(ctr[bspl.COUNTER_NAMES.index("candidates")]) < 2 * len(qc)
+    bad_c, bad_q = qc[:6].copy(), q[:6].copy()
+    bad_c[1], bad_c[2] = cs.n, -3
+    bad_q[4, 2] = np.inf
+    r = bspl.bspl_project_curves(segs, dev(bad_c, torch.int32), dev(bad_q, torch.float64),
+                                 bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp))
+    st = r.status.cpu().numpy()
+    assert st[1] == st[2] == st[4] == bspl.Q_INVALID
+    assert np.all(st[[0, 3, 5]] & bspl.Q_CONVERGED)
+    r = bspl.bspl_project_curves(segs, dev(np.zeros(0, np.int32), torch.int32), dev(np.zeros((0, 3)), torch.float64),
+                                 bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp))
+    assert r.dist.numel() == 0

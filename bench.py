@@ -436,8 +436,14 @@ def main():
                  "frac": cull_flops / t_cull / p32, "ms_per_step": st_ms["cull"],
                  "peak_source": "FP32 FMA-chain microbenchmark on this GPU (of measured)"}
     roofline = dict(cull_line if dominant == "cull" else (mlp_line if dominant == "seed" else cull_line))
+    # DRAM bytes of the dominant kernel per step: ncu capture of the same
+    # kernel on the 1,024-curve, 250k + 250k-query case (278.1 MB per
+    # launch), scaled by the units processed (4x queries and tables) and the
+    # two launches of a step
+    traffic = 2 * 4 * 278.08e6 * (args.queries / 1_000_000) if dominant == "cull" else None
     roofline.update({"kernel": "k_cull_pairs" if roofline["bound"] == "alu" else "k_mlp_fused",
-                     "traffic": None, "stages_ms_per_step": st_ms, "dominant_stage": dominant,
+                     "traffic": traffic, "traffic_unit": "bytes per step (2 launches)",
+                     "stages_ms_per_step": st_ms, "dominant_stage": dominant,
                      "mlp_seed_kernel": mlp_line})
 
     S = cfg[bspl.MIXED]["samples"]

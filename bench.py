@@ -243,7 +243,8 @@ def main():
     # launch configuration per precision, chosen by the autotuner (untimed)
     cfg = {p: (autotune.tune_curves(segs, pc, pq, p) if args.samples == 0 else dict(samples=args.samples))
            for p in (bspl.MIXED, bspl.FP64)}
-    cfg[bspl.LEARNED_MIXED] = {"occupancy": cfg[bspl.MIXED].get("occupancy", 0)}
+    cfg[bspl.LEARNED_MIXED] = (autotune.tune_curves(segs, pc, pq, bspl.LEARNED_MIXED, mlp=mlp)
+                               if args.samples == 0 else {"occupancy": 0})
 
     def opts(prec, **kw):
         return bspl.make_options(prec=prec, mlp=mlp if prec == bspl.LEARNED_MIXED else None, **cfg[prec], **kw)

@@ -47,11 +47,15 @@ def _store(db):
     os.replace(tmp, CACHE)
 
 
-def time_config(segs, q_idx, q_xyz, prec, cfg, reps=3, invert=False):
+LEARNED_CANDIDATES = [dict(occupancy=o) for o in (0, 1)]
+
+
+def time_config(segs, q_idx, q_xyz, prec, cfg, reps=3, invert=False, mlp=None):
     """Mean device time (ms) of one query call with configuration cfg."""
     fn = bspl.bspl_invert_curves if invert else bspl.bspl_project_curves
-    bufs = bspl.QueryBuffers(segs, q_idx.numel(), q_xyz.device)
-    opts = bspl.make_options(prec=prec, **cfg)
+    learned = prec == bspl.LEARNED_MIXED
+    bufs = bspl.QueryBuffers(segs, q_idx.numel(), q_xyz.device, learned=learned)
+    opts = bspl.make_options(prec=prec, mlp=mlp if learned else None, **cfg)
     fn(segs, q_idx, q_xyz, opts, bufs)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -64,8 +68,9 @@ def time_config(segs, q_idx, q_xyz, prec, cfg, reps=3, invert=False):
     return ev[0].elapsed_time(ev[1]) / reps
 
 
-def tune_curves(segs, q_idx, q_xyz, prec, max_sample=262144, use_cache=True, candidates=None):
-    """Best {samples, occupancy} for this workload (cached)."""
+def tune_curves(segs, q_idx, q_xyz, prec, max_sample=262144, use_cache=True, candidates=None, mlp=None):
+    """Best launch configuration for this workload (cached): {samples,
+    occupancy} for the grid paths, {occupancy} for the learned path."""
     key = _key(segs, prec, q_idx.numel())
     with _lock:
         db = _load() if use_cache else {}
@@ -75,8 +80,10 @@ def tune_curves(segs, q_idx, q_xyz, prec, max_sample=262144, use_cache=True, can
     sel = torch.randperm(q_idx.numel(), device=q_idx.device)[:n]
     qi, qx = q_idx[sel].contiguous(), q_xyz[sel].contiguous()
     results = []
-    for cfg in candidates or CURVE_CANDIDATES:
-        results.append((time_config(segs, qi, qx, prec, cfg), cfg))
+    if candidates is None:
+        candidates = LEARNED_CANDIDATES if prec == bspl.LEARNED_MIXED else CURVE_CANDIDATES
+    for cfg in candidates:
+        results.append((time_config(segs, qi, qx, prec, cfg, mlp=mlp), cfg))
     results.sort(key=lambda r: r[0])
     best = results[0][1]
     with _lock:

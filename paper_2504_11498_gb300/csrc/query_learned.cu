@@ -155,7 +155,7 @@ __global__ void k_qrec(const int32_t* __restrict__ qc, const double* __restrict_
 
 constexpr int kEmitCap = 256;  // classified pairs staged per warp before one global reservation
 constexpr int kGrpChunk = 64;  // culling groups staged in shared memory per bulk copy
-constexpr int kSurvCap = 192;  // surviving (query, group) entries per warp batch
+constexpr int kSurvCap = 128;  // surviving (query, group) entries per warp batch
 constexpr uint64_t kCopyWaitNs = 1000000000ull;
 
 // set when a bulk-copy wait gave up (the kernel then reads global memory)
@@ -169,8 +169,10 @@ __device__ int g_copy_timeout;
 // surviving (query, group) pairs go to a per-warp list.  Level 2 is warp-
 // cooperative per query over its surviving groups' segments, as in the grid
 // kernel, and the classified pairs are staged and written out in bulk.
-template <bool SEEDS_ONLY>
-__global__ void __launch_bounds__(kWarps * 32) k_cull_pairs(CurveQ P, PairBuf B)
+// MINB: blocks per SM the register allocation must allow (1: the compiler's
+// choice; 8: fits 8 blocks of 4 warps, with a few spilled registers)
+template <bool SEEDS_ONLY, int MINB>
+__global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, PairBuf B)
 {
     __shared__ int s_seg[kWarps][kCandCap];
     __shared__ float s_lb[kWarps][kCandCap];
@@ -766,7 +768,8 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     if (cudaMemsetAsync(B.cnt, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return BSPL_ECUDA;
     mark(1);
     const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
-    k_cull_pairs<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
+    if (o->occupancy >= 1) k_cull_pairs<false, 8><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
+    else k_cull_pairs<false, 1><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
     mark(2);
     if (mlp && mlp_seed_pairs(mlp, B.pq, B.ps, B.qrec, segs, B.cap, B.cnt + 1, B.u, s) != cudaSuccess)
         return BSPL_ECUDA;
@@ -820,7 +823,7 @@ extern "C" bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t
         C.kind = nullptr;
         C.cap = cap;
         const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
-        k_cull_pairs<true><<<(unsigned)blocks, kWarps * 32, 0, stream>>>(P, C);
+        k_cull_pairs<true, 1><<<(unsigned)blocks, kWarps * 32, 0, stream>>>(P, C);
     }
     if (cudaMemcpyAsync(n_pairs, B.cnt + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess ||
         cudaMemcpyAsync(n_pairs + 1, B.cnt, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)

@@ -134,14 +134,42 @@ def test_curve_set_subset_parity(prec):
 
 def test_full_size_curve_set_sampled_parity():
     """The 4,096-curve set, 1M projection + 1M inversion queries in the launch
-    configuration the benchmark times: sampled oracle parity for both
-    precisions, and properties on every query."""
+    configuration the benchmark times: sampled oracle parity for the plain,
+    mixed and learned paths (the learned one replayed from a CUDA graph), and
+    properties on every query."""
     cs, qs = synth.curve_set(seed=2)
     tol = 1e-10
     dc = bspl.DeviceCurves(cs, DEV)
     segs = bspl.decompose(dc, tol)
     inv_pts = bspl.bspl_eval_curves(dc, dev(qs.inv_curve, torch.int32), dev(qs.inv_t, torch.float64))
     res = {}
+    # the learned path with a seed network of random weights (results do not
+    # depend on the weights), replayed from a CUDA graph as the bench does
+    mlp = bspl.Mlp(synth.mlp_init(21))
+    pc_d, pq_d, ic_d = dev(qs.proj_curve, torch.int32), dev(qs.proj_xyz, torch.float64), dev(qs.inv_curve, torch.int32)
+    bp = bspl.QueryBuffers(segs, len(qs.proj_curve), DEV, learned=True)
+    bi = bspl.QueryBuffers(segs, len(qs.inv_curve), DEV, learned=True)
+
+    def learned_step():
+        o = bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp)
+        bspl.bspl_project_curves(segs, pc_d, pq_d, o, bp)
+        bspl.bspl_invert_curves(segs, ic_d, inv_pts, o, bi)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        learned_step()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        learned_step()
+    for x in (bp.dist, bi.dist):
+        x.fill_(-1.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert bspl.mlp_check() == bspl.OK
+    res[bspl.LEARNED_MIXED] = tuple(x.cpu().numpy().copy() for x in (bp.param, bp.dist, bp.status, bi.param,
+                                                                     bi.dist, bi.status))
     for prec in (bspl.FP64, bspl.MIXED):
         tp, dp, sp = run_queries(segs, qs.proj_curve, qs.proj_xyz, prec=prec)
         r = bspl.bspl_invert_curves(segs, dev(qs.inv_curve, torch.int32), inv_pts, bspl.make_options(prec=prec))
@@ -154,15 +182,16 @@ def test_full_size_curve_set_sampled_parity():
         assert np.all(np.isfinite(dp)) and np.all(np.isfinite(di))
         assert np.all(di <= 1e-9 * diag_i), (prec, np.max(di / diag_i))
         assert not np.any(si & bspl.Q_INVALID) and not np.any(sp & bspl.Q_INVALID)
-    # mixed vs plain on every query
-    for k in (1, 4):
-        a, b = res[bspl.FP64][k], res[bspl.MIXED][k]
-        dg = diag_p if k == 1 else diag_i
-        assert np.all(np.abs(a - b) <= 1e-9 * dg), np.max(np.abs(a - b) / dg)
+    # mixed and learned vs plain on every query
+    for other in (bspl.MIXED, bspl.LEARNED_MIXED):
+        for k in (1, 4):
+            a, b = res[bspl.FP64][k], res[other][k]
+            dg = diag_p if k == 1 else diag_i
+            assert np.all(np.abs(a - b) <= 1e-9 * dg), (other, np.max(np.abs(a - b) / dg))
     rng = np.random.default_rng(3)
     pick = rng.choice(len(qs.proj_curve), 2000, replace=False)
     inv = inv_pts.cpu().numpy()
-    for prec in (bspl.FP64, bspl.MIXED):
+    for prec in (bspl.FP64, bspl.MIXED, bspl.LEARNED_MIXED):
         tp, dp, sp, ti, di, si = res[prec]
         check_against_oracle(cs, qs.proj_curve[pick], qs.proj_xyz[pick], tp[pick], dp[pick], tol)
         check_against_oracle(cs, qs.inv_curve[pick], inv[pick], ti[pick], di[pick], tol)

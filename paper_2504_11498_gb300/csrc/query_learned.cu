@@ -154,6 +154,7 @@ __global__ void k_qrec(const int32_t* __restrict__ qc, const double* __restrict_
 }
 
 constexpr int kEmitCap = 256;  // classified pairs staged per warp before one global reservation
+constexpr int kCandCap2 = 160; // tentative candidates of a warp batch before classification
 constexpr int kGrpChunk = 64;  // culling groups staged in shared memory per bulk copy
 constexpr int kSurvCap = 128;  // surviving (query, group) entries per warp batch
 constexpr uint64_t kCopyWaitNs = 1000000000ull;
@@ -174,8 +175,9 @@ __device__ int g_copy_timeout;
 template <bool SEEDS_ONLY, int MINB>
 __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, PairBuf B)
 {
-    __shared__ int s_seg[kWarps][kCandCap];
-    __shared__ float s_lb[kWarps][kCandCap];
+    __shared__ int s_seg[kWarps][kCandCap2];
+    __shared__ float s_lb[kWarps][kCandCap2];
+    __shared__ uint8_t s_cslot[kWarps][kCandCap2];
     __shared__ int s_pseg[kWarps][kEmitCap];
     __shared__ uint8_t s_pslot[kWarps][kEmitCap];
     __shared__ uint8_t s_pkind[kWarps][kEmitCap];
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* cseg = s_seg[wid];
     float* clb = s_lb[wid];
+    uint8_t* ctslot = s_cslot[wid];
     int* pseg = s_pseg[wid];
     uint8_t* pslot = s_pslot[wid];
     uint8_t* pkind = s_pkind[wid];
@@ -354,96 +357,103 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
         __syncwarp();
     };
 
-    // ---- level 2: per query, its surviving groups' segments
-    const unsigned valid_mask = __ballot_sync(kFull, lane < nslots && myc >= 0);
-    for (int sl = 0; sl < nslots; ++sl) {
-        if (!((valid_mask >> sl) & 1u)) continue;
-        const float sx = __shfl_sync(kFull, qx, sl), sy = __shfl_sync(kFull, qy, sl), sz = __shfl_sync(kFull, qz, sl);
-        const float seps = __shfl_sync(kFull, eps, sl);
-        const int c = __shfl_sync(kFull, myc, sl);
-        const float* qr = B.qrec + 8 * (qbase + sl);
-        const int64_t s0 = P.seg_off[c], s1 = P.seg_off[c + 1];
-        const int64_t g0 = P.grp_off[c], g1 = P.grp_off[c + 1];
-        float qub = s_ub[wid][sl];
-        float ubs = slacked(qub, seps);
-        int ncand = 0;
-        // classify the buffered candidates that survive the current bound
-        auto emit = [&]() {
-            __syncwarp();
-            for (int base = 0; base < ncand; base += 32) {
-                const int k = base + lane;
-                const bool act = k < ncand && clb[k] <= ubs;
-                const int seg = act ? cseg[k] : 0;
-                uint8_t kind = kIso;
-                if (act) {
-                    float cl[12];
-                    local32(P, seg, qr, cl);
-                    kind = classify(cl);
-                }
-                const bool keep = act && (!SEEDS_ONLY || kind == kSeed);
-                const unsigned m = __ballot_sync(kFull, keep);
-                if (npend + __popc(m) > kEmitCap) flush_pending();
-                if (keep) {
-                    const int pos = npend + __popc(m & lt);
-                    pseg[pos] = seg;
-                    pslot[pos] = (uint8_t)sl;
-                    pkind[pos] = kind;
-                }
-                npend += __popc(m);
+    // ---- level 2: every surviving (query, group) entry of the batch, in
+    // list order; lanes = the group's 32 segments.  Each query's upper bound
+    // lives in its own lane and tightens as its entries are scanned; the
+    // tentative candidates of all queries share one buffer and are classified
+    // 32 at a time.
+    int64_t s0l = 0, s1l = 0, g0l = 0;
+    if (lane < nslots && myc >= 0) {
+        s0l = P.seg_off[myc];
+        s1l = P.seg_off[myc + 1];
+        g0l = P.grp_off[myc];
+    }
+    float ubs_l = slacked(ub, eps);
+    int ncand = 0;
+    auto emit = [&]() {
+        __syncwarp();
+        for (int base = 0; base < ncand; base += 32) {
+            const int k = base + lane;
+            const bool in = k < ncand;
+            const int sl = in ? ctslot[k] : 0;
+            const float ubk = __shfl_sync(kFull, ubs_l, sl);
+            const bool act = in && clb[k] <= ubk;
+            const int seg = act ? cseg[k] : 0;
+            uint8_t kind = kIso;
+            if (act) {
+                float cl[12];
+                local32(P, seg, B.qrec + 8 * (qbase + sl), cl);
+                kind = classify(cl);
             }
-            ncand = 0;
-            __syncwarp();
-        };
-        // the segments of one group: box lower bounds, start-point upper bound
-        auto scan_group = [&](int64_t g) {
-            const int64_t ss = s0 + (g - g0) * BSPL_GROUP;
-            const int64_t se = min(ss + BSPL_GROUP, s1);
-            const int64_t s = ss + lane;
-            const bool valid = s < se;
-            float lbs = INFINITY, ups = INFINITY;
-            if (valid) {
-                const float* r = rec + (int64_t)RW * s;
-                lbs = box_d2(r, sx, sy, sz);
-                ups = pt_d2(r + 6, sx, sy, sz);
-            }
-            n_seg += (unsigned long long)(se - ss);
-            qub = fminf(qub, warp_min(ups));
-            ubs = slacked(qub, seps);
-            const bool keep = valid && lbs <= ubs;
-            const unsigned km = __ballot_sync(kFull, keep);
+            const bool keep = act && (!SEEDS_ONLY || kind == kSeed);
+            const unsigned m = __ballot_sync(kFull, keep);
+            if (npend + __popc(m) > kEmitCap) flush_pending();
             if (keep) {
-                const int pos = ncand + __popc(km & lt);
-                cseg[pos] = (int)s;
-                clb[pos] = lbs;
+                const int pos = npend + __popc(m & lt);
+                pseg[pos] = seg;
+                pslot[pos] = (uint8_t)sl;
+                pkind[pos] = kind;
             }
-            ncand += __popc(km);
-            if (ncand > kCandCap - 32) emit();
-        };
-        if ((sv_over >> sl) & 1u) {
-            // the list overflowed: scan all of the curve's groups directly
-            for (int64_t gb = g0; gb < g1; gb += 32) {
-                const int64_t g = gb + lane;
-                const float lbg = g < g1 ? box_d2(grp + (int64_t)GW * g, sx, sy, sz) : INFINITY;
-                unsigned m = __ballot_sync(kFull, lbg <= ubs);
-                while (m) {
-                    const int jg = __ffs(m) - 1;
-                    m &= m - 1;
-                    if (__shfl_sync(kFull, lbg, jg) <= ubs) scan_group(gb + jg);
-                }
-            }
-        } else {
-            for (int base = 0; base < nsv; base += 32) {
-                const int e = base + lane;
-                unsigned m = __ballot_sync(kFull, e < nsv && s_svslot[wid][e] == sl);
-                while (m) {
-                    const int je = base + __ffs(m) - 1;
-                    m &= m - 1;
-                    if (s_svlb[wid][je] <= ubs) scan_group(s_sv[wid][je]);
-                }
+            npend += __popc(m);
+        }
+        ncand = 0;
+        __syncwarp();
+    };
+    // the segments of group g for query slot sl (warp-uniform arguments)
+    auto scan_entry = [&](int sl, int64_t g) {
+        const float sx = __shfl_sync(kFull, qx, sl), sy = __shfl_sync(kFull, qy, sl), sz = __shfl_sync(kFull, qz, sl);
+        const int64_t s0 = __shfl_sync(kFull, s0l, sl), s1 = __shfl_sync(kFull, s1l, sl);
+        const int64_t g0 = __shfl_sync(kFull, g0l, sl);
+        const int64_t ss = s0 + (g - g0) * BSPL_GROUP;
+        const int64_t se = min(ss + BSPL_GROUP, s1);
+        const int64_t s = ss + lane;
+        const bool valid = s < se;
+        float lbs = INFINITY, ups = INFINITY;
+        if (valid) {
+            const float* r = rec + (int64_t)RW * s;
+            lbs = box_d2(r, sx, sy, sz);
+            ups = pt_d2(r + 6, sx, sy, sz);
+        }
+        n_seg += (unsigned long long)(se - ss);
+        const float m = warp_min(ups);
+        if (lane == sl && m < ub) {
+            ub = m;
+            ubs_l = slacked(ub, eps);
+        }
+        const float ubs = __shfl_sync(kFull, ubs_l, sl);
+        const bool keep = valid && lbs <= ubs;
+        const unsigned km = __ballot_sync(kFull, keep);
+        if (keep) {
+            const int pos = ncand + __popc(km & lt);
+            cseg[pos] = (int)s;
+            clb[pos] = lbs;
+            ctslot[pos] = (uint8_t)sl;
+        }
+        ncand += __popc(km);
+        if (ncand > kCandCap2 - 32) emit();
+    };
+    for (int e = 0; e < nsv; ++e) {
+        const int sl = s_svslot[wid][e];
+        if (s_svlb[wid][e] <= __shfl_sync(kFull, ubs_l, sl)) scan_entry(sl, s_sv[wid][e]);
+    }
+    // queries whose surviving groups did not fit the list: scan all groups
+    for (unsigned ov = sv_over; ov; ov &= ov - 1) {
+        const int sl = __ffs(ov) - 1;
+        const int c = __shfl_sync(kFull, myc, sl);
+        const float sx = __shfl_sync(kFull, qx, sl), sy = __shfl_sync(kFull, qy, sl), sz = __shfl_sync(kFull, qz, sl);
+        const int64_t g0 = P.grp_off[c], g1 = P.grp_off[c + 1];
+        for (int64_t gb = g0; gb < g1; gb += 32) {
+            const int64_t g = gb + lane;
+            const float lbg = g < g1 ? box_d2(grp + (int64_t)GW * g, sx, sy, sz) : INFINITY;
+            unsigned m = __ballot_sync(kFull, lbg <= __shfl_sync(kFull, ubs_l, sl));
+            while (m) {
+                const int jg = __ffs(m) - 1;
+                m &= m - 1;
+                if (__shfl_sync(kFull, lbg, jg) <= __shfl_sync(kFull, ubs_l, sl)) scan_entry(sl, gb + jg);
             }
         }
-        emit();
     }
+    emit();
     flush_pending();
     if (!SEEDS_ONLY && lane < nslots && ((over_mask >> lane) & 1u)) {
         const unsigned long long pos = atomicAdd(B.cnt + 3, 1ull);

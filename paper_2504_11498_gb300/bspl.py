@@ -31,7 +31,7 @@ MLP_IN, MLP_HIDDEN, MLP_NPARAM, MLP_NBF16, MLP_MAX_BATCH = 16, 128, 35332, 2048 
 MLP_OFF = {"W1": 0, "b1": 2048, "W2": 2176, "b2": 18560, "W3": 18688, "b3": 35072, "w4": 35200, "b4": 35328}
 NCOUNTERS = 10
 COUNTER_NAMES = ["queries", "seg_tested", "grp_tested", "candidates", "newton", "fallback", "nonconv",
-                 "newton32_iters", "newton64_iters", "spare"]
+                 "newton32_iters", "newton64_iters", "iso_pairs"]
 
 
 class BsplError(RuntimeError):

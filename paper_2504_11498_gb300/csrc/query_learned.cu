@@ -54,7 +54,8 @@ struct PairBuf {
     double* u64;
     uint8_t* fl;
     int64_t cap;
-    unsigned long long* cnt;  // [0] reserved, [1] seeds, [2] others, [3] overflowed queries
+    unsigned long long* cnt;  // [0] reserved, [1] seeds, [2] others, [3] overflowed queries, [4] finished
+    int32_t* fin;             // buffer slots of the pairs that got the FP64 finish
     const float* qrec;        // per sorted query: q hi[3], q lo[3], eps, curve (int bits; -1 invalid)
     const int32_t* order;     // sorted position -> query index
     int32_t* over;            // overflowed query indices
@@ -523,7 +524,7 @@ __device__ __forceinline__ void add_counter(unsigned long long* ctr, int which, 
 __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
 {
     const int64_t ns = (int64_t)B.cnt[1], no = (int64_t)B.cnt[2], np = ns + no;
-    unsigned it32 = 0;
+    unsigned it32 = 0, n_iso = 0;
     for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < np; j0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = j0 + threadIdx.x;
         if (j < np) {
@@ -568,6 +569,7 @@ __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
                 const float D1 = eval_E<float>(c, 0.f, 0.f, 0.f, 1.f, E, Ep);
                 u = D1 < D0 ? 1.f : 0.f;
             } else {
+                ++n_iso;
                 u = isolate_min<float>(c, 0.f, 0.f, 0.f, 1e-7f, P.fp32_steps * 4);
                 conv = newton_min<float>(c, 0.f, 0.f, 0.f, u, 1.f / 64.f, P.fp32_steps, 1e-7f, it32);
             }
@@ -584,7 +586,10 @@ __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
             atomicMin(B.best32 + pos, __float_as_uint(d + del));
         }
     }
-    if (P.counters) add_counter(P.counters, BSPL_CNT_NEWTON32_ITERS, it32);
+    if (P.counters) {
+        add_counter(P.counters, BSPL_CNT_NEWTON32_ITERS, it32);
+        add_counter(P.counters, BSPL_CNT_ISO_PAIRS, n_iso);
+    }
 }
 
 // (3b) FP64 finish of the pairs whose FP32 lower bound does not exceed their
@@ -598,6 +603,7 @@ __global__ void __launch_bounds__(256) k_pairs_fp64(CurveQ P, PairBuf B)
 {
     __shared__ int s_list[kFinChunk];
     __shared__ int s_n;
+    __shared__ unsigned long long s_base;
     const int64_t ns = (int64_t)B.cnt[1], no = (int64_t)B.cnt[2], np = ns + no;
     unsigned it64 = 0, nfin = 0;
     for (int64_t c0 = (int64_t)blockIdx.x * kFinChunk; c0 < np; c0 += (int64_t)gridDim.x * kFinChunk) {
@@ -612,9 +618,12 @@ __global__ void __launch_bounds__(256) k_pairs_fp64(CurveQ P, PairBuf B)
         }
         __syncthreads();
         const int nt = s_n;
+        if (threadIdx.x == 0 && nt > 0) s_base = atomicAdd(B.cnt + 4, (unsigned long long)nt);
+        __syncthreads();
         for (int k = threadIdx.x; k < nt; k += blockDim.x) {
             const int64_t j = c0 + s_list[k];
             const int64_t i = pair_slot(B, j, ns);
+            B.fin[s_base + k] = (int32_t)i;
             const int64_t pos = B.pq[i], seg = B.ps[i];
             const double* q = P.q_xyz + 3 * (int64_t)B.order[pos];
             ++nfin;
@@ -651,9 +660,9 @@ __global__ void __launch_bounds__(256) k_pairs_fp64(CurveQ P, PairBuf B)
 // (3c) smallest segment among the pairs at the query's best FP64 distance
 __global__ void k_pairs_argseg(CurveQ P, PairBuf B)
 {
-    const int64_t ns = (int64_t)B.cnt[1], np = ns + (int64_t)B.cnt[2];
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = pair_slot(B, j, ns);
+    const int64_t nf = (int64_t)B.cnt[4];  // only finished pairs can hold a query's minimum
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = B.fin[j];
         const int64_t pos = B.pq[i];
         if ((unsigned long long)__double_as_longlong(B.D64[i]) == B.best64[pos]) atomicMin(B.bestseg + pos, B.ps[i]);
     }
@@ -662,12 +671,12 @@ __global__ void k_pairs_argseg(CurveQ P, PairBuf B)
 // (3d) the winning pair writes its query's result
 __global__ void k_pairs_write(CurveQ P, PairBuf B)
 {
-    const int64_t ns = (int64_t)B.cnt[1], np = ns + (int64_t)B.cnt[2];
+    const int64_t nf = (int64_t)B.cnt[4];
     unsigned fb = 0, nc = 0;
-    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < np; j0 += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < nf; j0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = j0 + threadIdx.x;
-        if (j < np) {
-            const int64_t i = pair_slot(B, j, ns);
+        if (j < nf) {
+            const int64_t i = B.fin[j];
             const int64_t pos = B.pq[i];
             const int seg = B.ps[i];
             if ((unsigned long long)__double_as_longlong(B.D64[i]) != B.best64[pos] || seg != B.bestseg[pos]) continue;
@@ -722,7 +731,8 @@ bool carve_learned(void* ws, size_t bytes, int64_t n_splines, int64_t n_q, PairB
     B.best32 = cv.take<unsigned>((size_t)n_q);
     B.best64 = cv.take<unsigned long long>((size_t)n_q);
     B.bestseg = cv.take<int>((size_t)n_q);
-    B.cnt = cv.take<unsigned long long>(4);
+    B.cnt = cv.take<unsigned long long>(8);
+    B.fin = cv.take<int32_t>((size_t)cap);
     B.qrec = cv.take<float>((size_t)n_q * 8);
     if (sort_ws) *sort_ws = sw;
     if (sort_bytes) *sort_bytes = sb;
@@ -784,7 +794,7 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
                                  const bspl_options* o, int invert, double* t, double* dist, uint8_t* status,
                                  void* ws, size_t ws_bytes, cudaStream_t s)
 {
-    if (!segs_ok(segs) || n_q < 0 || n_q > 0x7fffffffLL) return BSPL_EINVAL;
+    if (!segs_ok(segs) || n_q < 0 || pair_cap(n_q) > 0x7fffffffLL) return BSPL_EINVAL;
     if (n_q == 0) return BSPL_OK;
     if (!q_curve || !q_xyz || !t || !dist || !status) return BSPL_EINVAL;
     const bspl_mlp* mlp = (const bspl_mlp*)o->mlp;
@@ -807,7 +817,7 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     P.order = order;
     B.order = order;
     k_qrec<<<ceil_div(n_q, 256), 256, 0, s>>>(q_curve, q_xyz, segs->diag, segs->n, order, n_q, (float*)B.qrec);
-    if (cudaMemsetAsync(B.cnt, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return BSPL_ECUDA;
+    if (cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess) return BSPL_ECUDA;
     mark(1);
     const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
     if (o->occupancy >= 1) k_cull_pairs<false, 8><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
@@ -848,7 +858,7 @@ extern "C" bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t
     void* sw = nullptr;
     size_t sb = 0;
     if (!carve_learned(ws, ws_bytes, segs->n, n_q, B, &sw, &sb, nullptr)) return BSPL_EINVAL;
-    if (cudaMemsetAsync(B.cnt, 0, 4 * sizeof(unsigned long long), stream) != cudaSuccess) return BSPL_ECUDA;
+    if (cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), stream) != cudaSuccess) return BSPL_ECUDA;
     if (n_q > 0) {
         bspl_options o{};
         CurveQ P = make_params(segs, n_q, q_curve, q_xyz, o, 0, nullptr, nullptr, nullptr);

@@ -156,9 +156,9 @@ typedef struct {
     int32_t sort_queries;/* 1: group queries by spline first (default 1)            */
     int32_t occupancy;   /* curve kernel register/occupancy variant: 0 compiler
                             choice, 1 >= 4 blocks/SM, 2 >= 6 blocks/SM (samples
-                            16 and 32); learned path: 0 compiler choice, >= 1
-                            culling kernel fitted to 8 blocks/SM; picked by
-                            the autotuner                                   */
+                            16 and 32); learned path: 0 compiler choice, 1 / 2
+                            culling kernel fitted to 6 / 8 blocks/SM; picked
+                            by the autotuner                                */
     int32_t pairs_per_query; /* learned path: candidate-pair buffer per query,
                             1..24 (default 24); queries whose pairs do not fit
                             are answered by the grid kernel instead         */

@@ -47,7 +47,7 @@ def _store(db):
     os.replace(tmp, CACHE)
 
 
-LEARNED_CANDIDATES = [dict(occupancy=o) for o in (0, 1)]
+LEARNED_CANDIDATES = [dict(occupancy=o) for o in (0, 1, 2)]
 
 
 def time_config(segs, q_idx, q_xyz, prec, cfg, reps=3, invert=False, mlp=None):

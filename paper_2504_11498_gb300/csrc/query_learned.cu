@@ -172,7 +172,7 @@ __device__ int g_copy_timeout;
 // cooperative per query over its surviving groups' segments, as in the grid
 // kernel, and the classified pairs are staged and written out in bulk.
 // MINB: blocks per SM the register allocation must allow (1: the compiler's
-// choice; 8: fits 8 blocks of 4 warps, with a few spilled registers)
+// choice; 6 or 8 blocks of 4 warps, the latter with a few spilled registers)
 template <bool SEEDS_ONLY, int MINB>
 __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, PairBuf B)
 {
@@ -599,7 +599,7 @@ __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
 // scarce one and a warp with one active lane costs as much as a full one).
 constexpr int kFinChunk = 1024;
 
-__global__ void __launch_bounds__(256) k_pairs_fp64(CurveQ P, PairBuf B)
+__global__ void __launch_bounds__(256, 3) k_pairs_fp64(CurveQ P, PairBuf B)
 {
     __shared__ int s_list[kFinChunk];
     __shared__ int s_n;
@@ -820,7 +820,8 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     if (cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess) return BSPL_ECUDA;
     mark(1);
     const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
-    if (o->occupancy >= 1) k_cull_pairs<false, 8><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
+    if (o->occupancy >= 2) k_cull_pairs<false, 8><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
+    else if (o->occupancy == 1) k_cull_pairs<false, 6><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
     else k_cull_pairs<false, 1><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
     mark(2);
     if (mlp && mlp_seed_pairs(mlp, B.pq, B.ps, B.qrec, segs, B.cap, B.cnt + 1, B.u, s) != cudaSuccess)

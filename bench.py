@@ -109,13 +109,14 @@ def build_workload(seed, rank, n_curves=4096, n_queries=1_000_000):
     return cs, qs
 
 
-def cpu_oracle_rate(cs, qs, budget_s=15.0, max_q=1_000_000):
-    """Oracle (plain FP64, as it stands) on the host cores, bounded sample:
-    equal numbers of projection and inversion queries."""
+def cpu_oracle_rate(cs, qs, budget_s=15.0, max_q=1_000_000, threads=0):
+    """Oracle (plain FP64, as it stands) on the host cores (all of them, or
+    `threads`), bounded sample: equal numbers of projection and inversion
+    queries."""
     from oracle import oracle as O
-    n = 500
+    n = 500 if threads != 1 else 50
     elapsed, done = 0.0, 0
-    threads = O.num_threads()
+    threads = threads or O.num_threads()
     C, _, _ = O.eval_curves(cs, qs.inv_curve[:max_q], qs.inv_t[:max_q])
     while elapsed < budget_s and done < max_q:
         k = min(n, max_q - done)
@@ -317,6 +318,12 @@ def main():
     clocks.start()
     ms_learned = timed_graph(args.steps, args.warmup)
     ms_learned_direct = timed(bspl.LEARNED_MIXED, args.steps, args.warmup)
+    # the same pipeline without its network (midpoint seed): what the network
+    # costs and saves in time
+    mlp_keep = mlp
+    mlp = None
+    ms_no_net = timed(bspl.LEARNED_MIXED, args.steps, args.warmup)
+    mlp = mlp_keep
     ms_mixed = timed(bspl.MIXED, args.steps, args.warmup)
     ms_plain = timed(bspl.FP64, max(2, args.steps // 3), 2)
     clk = clocks.stop()
@@ -438,14 +445,23 @@ def main():
                  "peak_source": "FP32 FMA-chain microbenchmark on this GPU (of measured)"}
     roofline = dict(cull_line if dominant == "cull" else (mlp_line if dominant == "seed" else cull_line))
     # DRAM bytes of the dominant kernel per step: ncu capture of the same
-    # kernel on the 1,024-curve, 250k + 250k-query case (278.1 MB per
+    # kernel on the 1,024-curve, 250k + 250k-query case (248.1 MB per
     # launch), scaled by the units processed (4x queries and tables) and the
     # two launches of a step
-    traffic = 2 * 4 * 278.08e6 * (args.queries / 1_000_000) if dominant == "cull" else None
+    traffic = 2 * 4 * 248.10e6 * (args.queries / 1_000_000) if dominant == "cull" else None
     roofline.update({"kernel": "k_cull_pairs" if roofline["bound"] == "alu" else "k_mlp_fused",
                      "traffic": traffic, "traffic_unit": "bytes per step (2 launches)",
                      "stages_ms_per_step": st_ms, "dominant_stage": dominant,
                      "mlp_seed_kernel": mlp_line})
+
+    # the whole learned step: counted FP32 flops / FP32 peak + FP64 flops /
+    # FP64 peak + MLP flops / BF16 peak, per second of the timed step
+    f32_step = cull_flops + 45 * c_learned["newton32_iters"]
+    f64_step = 60 * c_learned["newton"] + 45 * max(0, c_learned["newton64_iters"] - 2 * c_learned["newton"])
+    t_step = ms_learned * 1e-3
+    roofline["step"] = {"frac": f32_step / t_step / p32 + f64_step / t_step / p64 + mlp_flops / t_step / bf16_peak,
+                        "fp32_flops": f32_step, "fp64_flops": f64_step, "bf16_flops": mlp_flops,
+                        "note": "sum of the three pipes' fractions over the timed step (ms_per_step)"}
 
     S = cfg[bspl.MIXED]["samples"]
     f32m = 12 * (c_mixed["grp_tested"] + c_mixed["seg_tested"]) + 15 * S * c_mixed["candidates"] + \
@@ -467,6 +483,8 @@ def main():
                       "decompose_ms": decomp_ms, "seed_network": train},
            "graph": "learned step captured once as a CUDA graph and replayed",
            "learned_direct": {"value": total_q / (ms_learned_direct * 1e-3), "ms_per_step": ms_learned_direct},
+           "learned_without_network": {"value": total_q / (ms_no_net * 1e-3), "ms_per_step": ms_no_net,
+                                       "note": "same pipeline, seed u = 1/2 instead of the network"},
            "mixed_grid": {"value": total_q / (ms_mixed * 1e-3), "ms_per_step": ms_mixed},
            "plain_fp64": {"value": total_q / (ms_plain * 1e-3), "ms_per_step": ms_plain},
            "speedup_learned_vs_plain": ms_plain / ms_learned, "speedup_mixed_vs_plain": ms_plain / ms_mixed,
@@ -477,9 +495,11 @@ def main():
            "counters": {"learned_mixed": c_learned, "mixed": c_mixed, "plain_fp64": c_plain}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, nq, el = cpu_oracle_rate(cs, qs)
+        r1, _, nq1, el1 = cpu_oracle_rate(cs, qs, budget_s=5.0, threads=1)
         out["cpu_baseline"] = {"value": r, "unit": "pts/s", "cores": cores, "kind": "oracle",
                                "sample": f"{nq} queries of the same workload (half projection, half inversion), "
-                                         f"{el:.1f} s"}
+                                         f"{el:.1f} s",
+                               "one_core": {"value": r1, "sample": f"{nq1} queries, {el1:.1f} s"}}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

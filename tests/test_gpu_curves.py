@@ -189,7 +189,7 @@ def test_full_size_curve_set_sampled_parity():
             dg = diag_p if k == 1 else diag_i
             assert np.all(np.abs(a - b) <= 1e-9 * dg), (other, np.max(np.abs(a - b) / dg))
     rng = np.random.default_rng(3)
-    pick = rng.choice(len(qs.proj_curve), 2000, replace=False)
+    pick = rng.choice(len(qs.proj_curve), 10000, replace=False)
     inv = inv_pts.cpu().numpy()
     for prec in (bspl.FP64, bspl.MIXED, bspl.LEARNED_MIXED):
         tp, dp, sp, ti, di, si = res[prec]

@@ -129,6 +129,17 @@ def cpu_oracle_rate(cs, qs, budget_s=15.0, max_q=1_000_000, threads=0):
     return 2 * done / elapsed, threads, 2 * done, elapsed
 
 
+def combine_over_ranks(times_ms, n_per_rank, world, dist=None, device="cpu"):
+    """Weak scaling over independent replicas: each time is the maximum
+    over ranks (the slowest replica bounds the job), the units processed are
+    the per-rank units times the number of ranks."""
+    import torch
+    vals = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    return vals.tolist(), n_per_rank * world
+
+
 # ------------------------------------------------------------ learned seed
 
 def train_seed(args, rank, dev):
@@ -416,12 +427,9 @@ def main():
     h2d = sum(x.numel() * x.element_size() for x in h_in)
     d2h = sum(x.numel() * x.element_size() for x in h_out)
 
-    # max over ranks
-    vals = torch.tensor([ms_learned, ms_mixed, ms_plain, ms_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_learned, ms_mixed, ms_plain, ms_e2e = vals.tolist()
-    total_q = n_step * world
+    # max over ranks; every rank processed its own n_step queries
+    (ms_learned, ms_mixed, ms_plain, ms_e2e), total_q = combine_over_ranks(
+        [ms_learned, ms_mixed, ms_plain, ms_e2e], n_step, world, dist if world > 1 else None, dev)
 
     # rooflines.  ALU work from device counters with per-unit figures: 12
     # FP32 flops per box test, 110 per pair classification (E in Bernstein

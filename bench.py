@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--curves", type=int, default=4096, help="curves in the workload")
     ap.add_argument("--queries", type=int, default=1_000_000, help="projection and inversion queries each")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
+                    help="c2: 1M projection + 1M inversion queries; c4: 16M projection queries, same curves")
     ap.add_argument("--train-curves", type=int, default=2048, help="curves of the seed network's training set")
     ap.add_argument("--train-queries", type=int, default=3_500_000, help="their projection and inversion queries")
     ap.add_argument("--train-pairs", type=int, default=10_000_000, help="training pairs at most")
@@ -103,30 +105,37 @@ class ClockSampler:
 
 # --------------------------------------------------------------- workload
 
-def build_workload(seed, rank, n_curves=4096, n_queries=1_000_000):
+def build_workload(seed, rank, n_curves=4096, n_queries=1_000_000, n_inv=None):
     from paper_2504_11498_gb300 import synth
-    cs, qs = synth.curve_set(seed=seed + 1000 * rank, n_curves=n_curves, n_proj=n_queries, n_inv=n_queries)
+    cs, qs = synth.curve_set(seed=seed + 1000 * rank, n_curves=n_curves, n_proj=n_queries,
+                             n_inv=n_queries if n_inv is None else n_inv)
     return cs, qs
 
 
 def cpu_oracle_rate(cs, qs, budget_s=15.0, max_q=1_000_000, threads=0):
     """Oracle (plain FP64, as it stands) on the host cores (all of them, or
-    `threads`), bounded sample: equal numbers of projection and inversion
-    queries."""
+    `threads`), bounded sample of the workload: its projection queries and,
+    when it has them, as many inversion queries."""
     from oracle import oracle as O
     n = 500 if threads != 1 else 50
     elapsed, done = 0.0, 0
     threads = threads or O.num_threads()
-    C, _, _ = O.eval_curves(cs, qs.inv_curve[:max_q], qs.inv_t[:max_q])
+    inv = len(qs.inv_curve) > 0
+    max_q = min(max_q, len(qs.proj_curve))
+    if inv:
+        max_q = min(max_q, len(qs.inv_curve))
+        C, _, _ = O.eval_curves(cs, qs.inv_curve[:max_q], qs.inv_t[:max_q])
     while elapsed < budget_s and done < max_q:
         k = min(n, max_q - done)
         t0 = time.perf_counter()
         O.project_curves(cs, qs.proj_curve[done:done + k], qs.proj_xyz[done:done + k], nthreads=threads)
-        O.project_curves(cs, qs.inv_curve[done:done + k], C[done:done + k], nthreads=threads)
+        if inv:
+            O.project_curves(cs, qs.inv_curve[done:done + k], C[done:done + k], nthreads=threads)
         elapsed += time.perf_counter() - t0
         done += k
         n = min(n * 2, 8000)
-    return 2 * done / elapsed, threads, 2 * done, elapsed
+    per = 2 if inv else 1
+    return per * done / elapsed, threads, per * done, elapsed
 
 
 def combine_over_ranks(times_ms, n_per_rank, world, dist=None, device="cpu"):
@@ -180,6 +189,10 @@ def train_seed(args, rank, dev):
 
 def main():
     args = parse()
+    n_inv = None
+    if args.workload == "c4":  # the learned-seed configuration: projection queries only
+        args.queries = 16_000_000 if args.queries == 1_000_000 else args.queries
+        n_inv = 0
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -187,7 +200,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cs, qs = build_workload(args.seed, 0, args.curves, args.queries)
+        cs, qs = build_workload(args.seed, 0, args.curves, args.queries, n_inv)
         rates = []
         for _ in range(args.warmup):
             cpu_oracle_rate(cs, qs, budget_s=2.0, max_q=2000)
@@ -219,7 +232,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    cs, qs = build_workload(args.seed, rank, args.curves, args.queries)
+    cs, qs = build_workload(args.seed, rank, args.curves, args.queries, n_inv)
     dc = bspl.DeviceCurves(cs, dev)
 
     # decomposition (preprocessing, timed separately)
@@ -456,9 +469,10 @@ def main():
     # kernel on the 1,024-curve, 250k + 250k-query case (248.1 MB per
     # launch), scaled by the units processed (4x queries and tables) and the
     # two launches of a step
-    traffic = 2 * 4 * 248.10e6 * (args.queries / 1_000_000) if dominant == "cull" else None
+    n_calls = 2 if ic.numel() > 0 else 1
+    traffic = n_calls * 4 * 248.10e6 * (pc.numel() / 1_000_000) if dominant == "cull" else None
     roofline.update({"kernel": "k_cull_pairs" if roofline["bound"] == "alu" else "k_mlp_fused",
-                     "traffic": traffic, "traffic_unit": "bytes per step (2 launches)",
+                     "traffic": traffic, "traffic_unit": f"bytes per step ({n_calls} launch(es))",
                      "stages_ms_per_step": st_ms, "dominant_stage": dominant,
                      "mlp_seed_kernel": mlp_line})
 
@@ -484,7 +498,7 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "bf16+f32+f64 (BF16 tensor-core seed, FP32 search, FP64 finish)", "data": "synthetic",
-           "config": {"workload": f"curve_set_{args.curves}: {args.queries} projection + {args.queries} inversion "
+           "config": {"workload": f"curve_set_{args.curves}: {pc.numel()} projection + {ic.numel()} inversion "
                                   "queries per GPU",
                       "tol_rel": TOL, "prec": "learned_mixed", "launch": {str(k): v for k, v in cfg.items()},
                       "l2": "512 MB flush between timed steps", "segments": int(segs.total),

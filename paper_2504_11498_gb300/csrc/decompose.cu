@@ -57,6 +57,41 @@ __host__ __device__ double gram_d(int m, int n, int i, int j)
     return fdiv(num, den);
 }
 
+// Coefficients of the cubic reduction (Eq. gram entries, p/3) and of degree
+// elevation (i/(n+1), (n+1-i)/(n+1)) for degrees up to MP.  A block computes
+// them once, with the same FP64 operations, instead of once per tree node.
+template <int MP>
+struct RedCoef {
+    double g33[4][4];             // g_ij for m = n = 3
+    double gp[MP + 1][2][MP + 1]; // g_{1+r, j} for m = 3, n = p
+    double ap[MP + 1];            // p / 3
+    double ea[MP][MP + 1];        // elevation n -> n + 1: i / (n + 1)
+    double eb[MP][MP + 1];        // (n + 1 - i) / (n + 1)
+};
+
+// every thread of the block must call this
+template <int MP>
+__device__ void fill_coef(RedCoef<MP>& cf)
+{
+    constexpr int NG = 16, NP = (MP + 1) * 2 * (MP + 1), NA = MP + 1, NE = MP * (MP + 1);
+    for (int t = threadIdx.x; t < NG + NP + NA + NE; t += blockDim.x) {
+        if (t < NG) {
+            cf.g33[t >> 2][t & 3] = gram_d(3, 3, t >> 2, t & 3);
+        } else if (t < NG + NP) {
+            const int u = t - NG, p = u / (2 * (MP + 1)), r = (u / (MP + 1)) & 1, j = u % (MP + 1);
+            cf.gp[p][r][j] = j <= p ? gram_d(3, p, 1 + r, j) : 0.0;
+        } else if (t < NG + NP + NA) {
+            const int p = t - NG - NP;
+            cf.ap[p] = fdiv((double)p, 3.0);
+        } else {
+            const int u = t - NG - NP - NA, n = u / (MP + 1), i = u % (MP + 1);
+            cf.ea[n][i] = fdiv((double)i, (double)(n + 1));
+            cf.eb[n][i] = fdiv((double)(n + 1 - i), (double)(n + 1));
+        }
+    }
+    __syncthreads();
+}
+
 // Bezier piece of knot span q from the p+1 control points starting at
 // P_{q-p} (stride 3*pstride doubles between points): local power basis of
 // N_{q-p..q,p} in u = (t - t_q)/(t_{q+1} - t_q) by the Cox-de Boor recursion
@@ -113,15 +148,15 @@ __host__ __device__ void span_bezier(int p, const double* __restrict__ U, int q,
 }
 
 // degree n -> n+1 (exact degree elevation); Q and E indexed with stride s (points)
-__host__ __device__ void elevate(int n, const double* Q, double* E, int s)
+template <int MP>
+__host__ __device__ void elevate(int n, const double* Q, double* E, int s, const RedCoef<MP>& cf)
 {
     for (int c = 0; c < 3; ++c) {
         E[c] = Q[c];
         E[(n + 1) * s + c] = Q[n * s + c];
     }
     for (int i = 1; i <= n; ++i) {
-        double a = fdiv((double)i, (double)(n + 1));
-        double b = fdiv((double)(n + 1 - i), (double)(n + 1));
+        const double a = cf.ea[n][i], b = cf.eb[n][i];
         for (int c = 0; c < 3; ++c) E[i * s + c] = fadd(fmul(a, Q[(i - 1) * s + c]), fmul(b, Q[i * s + c]));
     }
 }
@@ -132,25 +167,26 @@ __host__ __device__ void elevate(int n, const double* Q, double* E, int s)
 // delta0 (B0.d1) + delta1 (B1.d1) = V2.d1, A0 = a g11 d0, A1 = -a g12 d1,
 // B0 = a g21 d0, B1 = -a g22 d1, a = p/3; degenerate systems fall back to
 // delta0 = delta1 = 1.
-__host__ __device__ void reduce_g1(int p, const double* Q, int s, double* R, int rs)
+template <int MP>
+__host__ __device__ void reduce_g1(int p, const double* Q, int s, double* R, int rs, const RedCoef<MP>& cf)
 {
     const double* Q0 = Q;
     const double* Q1 = Q + s;
     const double* Qm = Q + (p - 1) * s;
     const double* Qp = Q + p * s;
-    double a = fdiv((double)p, 3.0);
-    double g11 = gram_d(3, 3, 1, 1), g12 = gram_d(3, 3, 1, 2);
-    double g21 = gram_d(3, 3, 2, 1), g22 = gram_d(3, 3, 2, 2);
-    double g10 = gram_d(3, 3, 1, 0), g13 = gram_d(3, 3, 1, 3);
-    double g20 = gram_d(3, 3, 2, 0), g23 = gram_d(3, 3, 2, 3);
+    const double a = cf.ap[p];
+    const double g11 = cf.g33[1][1], g12 = cf.g33[1][2];
+    const double g21 = cf.g33[2][1], g22 = cf.g33[2][2];
+    const double g10 = cf.g33[1][0], g13 = cf.g33[1][3];
+    const double g20 = cf.g33[2][0], g23 = cf.g33[2][3];
     double d0[3], d1[3], V1[3], V2[3];
     for (int c = 0; c < 3; ++c) {
         d0[c] = fsub(Q1[c], Q0[c]);
         d1[c] = fsub(Qp[c], Qm[c]);
         double s1 = 0.0, s2 = 0.0;
         for (int j = 0; j <= p; ++j) {
-            s1 = fadd(s1, fmul(gram_d(3, p, 1, j), Q[j * s + c]));
-            s2 = fadd(s2, fmul(gram_d(3, p, 2, j), Q[j * s + c]));
+            s1 = fadd(s1, fmul(cf.gp[p][0][j], Q[j * s + c]));
+            s2 = fadd(s2, fmul(cf.gp[p][1][j], Q[j * s + c]));
         }
         double t1 = fadd(fadd(fadd(fmul(g10, Q0[c]), fmul(g11, Q0[c])), fmul(g12, Qp[c])), fmul(g13, Qp[c]));
         double t2 = fadd(fadd(fadd(fmul(g20, Q0[c]), fmul(g21, Q0[c])), fmul(g22, Qp[c])), fmul(g23, Qp[c]));
@@ -188,19 +224,20 @@ __host__ __device__ void reduce_g1(int p, const double* Q, int s, double* R, int
     }
 }
 
-__host__ __device__ void to_cubic(int p, const double* Q, int s, double* R, int rs)
+template <int MP>
+__host__ __device__ void to_cubic(int p, const double* Q, int s, double* R, int rs, const RedCoef<MP>& cf)
 {
     if (p == 3) {
         for (int i = 0; i < 4; ++i)
             for (int c = 0; c < 3; ++c) R[i * rs + c] = Q[i * s + c];
     } else if (p > 3) {
-        reduce_g1(p, Q, s, R, rs);
+        reduce_g1<MP>(p, Q, s, R, rs, cf);
     } else {
         double w[12], x[12];
         for (int i = 0; i <= p; ++i)
             for (int c = 0; c < 3; ++c) w[3 * i + c] = Q[i * s + c];
         for (int n = p; n < 3; ++n) {
-            elevate(n, w, x, 3);
+            elevate<MP>(n, w, x, 3, cf);
             for (int i = 0; i <= n + 1; ++i)
                 for (int c = 0; c < 3; ++c) w[3 * i + c] = x[3 * i + c];
         }
@@ -211,13 +248,13 @@ __host__ __device__ void to_cubic(int p, const double* Q, int s, double* R, int 
 
 // max_i |Q_i - (R elevated to p)_i|^2 (certified deviation bound)
 template <int MP>
-__host__ __device__ double bound2_curve(int p, const double* Q, int s, const double* R, int rs)
+__host__ __device__ double bound2_curve(int p, const double* Q, int s, const double* R, int rs, const RedCoef<MP>& cf)
 {
     double w[(MP + 1) * 3], x[(MP + 1) * 3];
     for (int i = 0; i < 4; ++i)
         for (int c = 0; c < 3; ++c) w[3 * i + c] = R[i * rs + c];
     for (int n = 3; n < p; ++n) {
-        elevate(n, w, x, 3);
+        elevate<MP>(n, w, x, 3, cf);
         for (int i = 0; i <= n + 1; ++i)
             for (int c = 0; c < 3; ++c) w[3 * i + c] = x[3 * i + c];
     }
@@ -351,8 +388,11 @@ struct CurveLeafOut {
     double* prange;
 };
 
-// Walks the subdivision tree of one span.  FILL = false counts leaves;
-// FILL = true writes them from index `first`.
+// Walks the subdivision tree of one span depth first.  FILL = false counts
+// leaves; FILL = true writes them from index `first`.  The nodes on the path
+// to depth kStack - 1 are kept, so a node is one halving of its parent;
+// deeper nodes are replayed from the deepest kept ancestor.  Either way a
+// node is the same sequence of halvings from the span's Bezier piece.
 __host__ __device__ inline void set_flag(int* err, int bit)
 {
 #ifdef __CUDA_ARCH__
@@ -364,19 +404,31 @@ __host__ __device__ inline void set_flag(int* err, int bit)
 
 template <int MP, bool FILL>
 __host__ __device__ int64_t walk_span_curve(int p, const double* __restrict__ U, int q, const double* __restrict__ Pl,
-                                   double thr2, int64_t first, CurveLeafOut out, int* err)
+                                            double thr2, int64_t first, CurveLeafOut out, int* err,
+                                            const RedCoef<MP>& cf)
 {
-    double root[(MP + 1) * 3], Q[(MP + 1) * 3];
-    span_bezier<MP>(p, U, q, Pl, 1, root);
+    constexpr int kStack = MP == 7 ? 16 : (MP == 15 ? 8 : 4);
+    constexpr int W = (MP + 1) * 3;
+    double stk[kStack][W], Q[W];
+    const int np3 = 3 * (p + 1);
+    span_bezier<MP>(p, U, q, Pl, 1, stk[0]);
     int L = 0;
     int64_t k = 0, count = 0;
     for (;;) {
-        for (int i = 0; i < 3 * (p + 1); ++i) Q[i] = root[i];
-        for (int l = 0; l < L; ++l) halve_keep<MP>(p, Q, 3, (int)((k >> (L - 1 - l)) & 1));
+        if (L == 0) {
+            for (int i = 0; i < np3; ++i) Q[i] = stk[0][i];
+        } else if (L < kStack) {
+            for (int i = 0; i < np3; ++i) Q[i] = stk[L - 1][i];
+            halve_keep<MP>(p, Q, 3, (int)(k & 1));
+            for (int i = 0; i < np3; ++i) stk[L][i] = Q[i];
+        } else {
+            for (int i = 0; i < np3; ++i) Q[i] = stk[kStack - 1][i];
+            for (int d = kStack; d <= L; ++d) halve_keep<MP>(p, Q, 3, (int)((k >> (L - d)) & 1));
+        }
         double R[12];
-        to_cubic(p, Q, 3, R, 3);
+        to_cubic<MP>(p, Q, 3, R, 3, cf);
         bool accept = true;
-        if (p > 3) accept = bound2_curve<MP>(p, Q, 3, R, 3) <= thr2;
+        if (p > 3) accept = bound2_curve<MP>(p, Q, 3, R, 3, cf) <= thr2;
         if (!accept && (L >= kDepthCap || count >= kLeafCap)) {
             accept = true;
             set_flag(err, 2);
@@ -409,6 +461,8 @@ template <int MP, bool FILL>
 __global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, double tol_rel, int64_t n_slots,
                               int64_t* __restrict__ cnt, CurveLeafOut out, int* err)
 {
+    __shared__ RedCoef<MP> cf;
+    fill_coef<MP>(cf);
     int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= n_slots) return;
     int c = find_le(C.cp_off, C.n, slot);
@@ -424,7 +478,7 @@ __global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, do
     if (q <= nP - 1 && U[q] < U[q + 1]) {
         double thr = fmul(tol_rel, diag[c]);
         r = walk_span_curve<MP, FILL>(p, U, q, C.cps + 3 * (C.cp_off[c] + q - p), fmul(thr, thr),
-                                      FILL ? cnt[slot] : 0, out, err);
+                                      FILL ? cnt[slot] : 0, out, err, cf);
     }
     if (!FILL) cnt[slot] = r;
 }
@@ -435,30 +489,32 @@ __global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, do
 constexpr int kSN = kMaxSurfDegree + 1;
 
 // reduce along u for every v column, then along v for every u row
-__host__ __device__ void surf_to_bicubic(int pu, int pv, const double* Q, double* R /* [4*4*3] */)
+using SurfCoef = RedCoef<kMaxSurfDegree>;
+
+__host__ __device__ void surf_to_bicubic(int pu, int pv, const double* Q, double* R /* [4*4*3] */, const SurfCoef& cf)
 {
     double Rp[4 * kSN * 3];
     for (int j = 0; j <= pv; ++j) {
         double col[kSN * 3], r[12];
         for (int i = 0; i <= pu; ++i)
             for (int c = 0; c < 3; ++c) col[3 * i + c] = Q[(i * kSN + j) * 3 + c];
-        to_cubic(pu, col, 3, r, 3);
+        to_cubic<kMaxSurfDegree>(pu, col, 3, r, 3, cf);
         for (int i = 0; i < 4; ++i)
             for (int c = 0; c < 3; ++c) Rp[(i * kSN + j) * 3 + c] = r[3 * i + c];
     }
     for (int i = 0; i < 4; ++i) {
         double r[12];
-        to_cubic(pv, Rp + i * kSN * 3, 3, r, 3);
+        to_cubic<kMaxSurfDegree>(pv, Rp + i * kSN * 3, 3, r, 3, cf);
         for (int j = 0; j < 4; ++j)
             for (int c = 0; c < 3; ++c) R[(i * 4 + j) * 3 + c] = r[3 * j + c];
     }
 }
 
-__host__ __device__ void elevate_to(int from, int to, double* w /* [kSN*3] */)
+__host__ __device__ void elevate_to(int from, int to, double* w /* [kSN*3] */, const SurfCoef& cf)
 {
     double x[kSN * 3];
     for (int n = from; n < to; ++n) {
-        elevate(n, w, x, 3);
+        elevate<kMaxSurfDegree>(n, w, x, 3, cf);
         for (int i = 0; i <= n + 1; ++i)
             for (int c = 0; c < 3; ++c) w[3 * i + c] = x[3 * i + c];
     }
@@ -466,7 +522,7 @@ __host__ __device__ void elevate_to(int from, int to, double* w /* [kSN*3] */)
 
 // certified bound at degrees (max(pu,3), max(pv,3)): Q elevated along u then
 // v, R elevated along v then u
-__host__ __device__ double surf_bound2(int pu, int pv, const double* Q, const double* R)
+__host__ __device__ double surf_bound2(int pu, int pv, const double* Q, const double* R, const SurfCoef& cf)
 {
     int eu = pu > 3 ? pu : 3, ev = pv > 3 ? pv : 3;
     double Qe[kSN * kSN * 3], Re[kSN * kSN * 3];
@@ -474,7 +530,7 @@ __host__ __device__ double surf_bound2(int pu, int pv, const double* Q, const do
         double w[kSN * 3];
         for (int i = 0; i <= pu; ++i)
             for (int c = 0; c < 3; ++c) w[3 * i + c] = Q[(i * kSN + j) * 3 + c];
-        elevate_to(pu, eu, w);
+        elevate_to(pu, eu, w, cf);
         for (int i = 0; i <= eu; ++i)
             for (int c = 0; c < 3; ++c) Qe[(i * kSN + j) * 3 + c] = w[3 * i + c];
     }
@@ -482,7 +538,7 @@ __host__ __device__ double surf_bound2(int pu, int pv, const double* Q, const do
         double w[kSN * 3];
         for (int j = 0; j <= pv; ++j)
             for (int c = 0; c < 3; ++c) w[3 * j + c] = Qe[(i * kSN + j) * 3 + c];
-        elevate_to(pv, ev, w);
+        elevate_to(pv, ev, w, cf);
         for (int j = 0; j <= ev; ++j)
             for (int c = 0; c < 3; ++c) Qe[(i * kSN + j) * 3 + c] = w[3 * j + c];
     }
@@ -490,7 +546,7 @@ __host__ __device__ double surf_bound2(int pu, int pv, const double* Q, const do
         double w[kSN * 3];
         for (int j = 0; j < 4; ++j)
             for (int c = 0; c < 3; ++c) w[3 * j + c] = R[(i * 4 + j) * 3 + c];
-        elevate_to(3, ev, w);
+        elevate_to(3, ev, w, cf);
         for (int j = 0; j <= ev; ++j)
             for (int c = 0; c < 3; ++c) Re[(i * kSN + j) * 3 + c] = w[3 * j + c];
     }
@@ -498,7 +554,7 @@ __host__ __device__ double surf_bound2(int pu, int pv, const double* Q, const do
         double w[kSN * 3];
         for (int i = 0; i < 4; ++i)
             for (int c = 0; c < 3; ++c) w[3 * i + c] = Re[(i * kSN + j) * 3 + c];
-        elevate_to(3, eu, w);
+        elevate_to(3, eu, w, cf);
         for (int i = 0; i <= eu; ++i)
             for (int c = 0; c < 3; ++c) Re[(i * kSN + j) * 3 + c] = w[3 * i + c];
     }
@@ -564,7 +620,7 @@ struct SurfLeafOut {
 template <bool FILL>
 __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, int qu, const double* V, int qv,
                                      const double* P, int nv, double thr2, int64_t slot, int64_t first,
-                                     SurfLeafOut out, int* err)
+                                     SurfLeafOut out, int* err, const SurfCoef& cf)
 {
     double root[kSN * kSN * 3], Q[kSN * kSN * 3];
     {
@@ -621,9 +677,9 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
             }
         }
         double R[4 * 4 * 3];
-        surf_to_bicubic(pu, pv, Q, R);
+        surf_to_bicubic(pu, pv, Q, R, cf);
         bool accept = true;
-        if (pu > 3 || pv > 3) accept = surf_bound2(pu, pv, Q, R) <= thr2;
+        if (pu > 3 || pv > 3) accept = surf_bound2(pu, pv, Q, R, cf) <= thr2;
         if (!accept && (Lu + Lv >= kDepthCap || count >= kLeafCap)) {
             accept = true;
             set_flag(err, 2);
@@ -681,6 +737,8 @@ template <bool FILL>
 __global__ void k_walk_surfaces(bspl_surfaces S, const double* __restrict__ diag, double tol_rel,
                                 int64_t n_slots, int64_t* __restrict__ cnt, SurfLeafOut out, int* err)
 {
+    __shared__ SurfCoef cf;
+    fill_coef<kMaxSurfDegree>(cf);
     int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= n_slots) return;
     int s = find_le(S.cp_off, S.n, slot);
@@ -695,7 +753,7 @@ __global__ void k_walk_surfaces(bspl_surfaces S, const double* __restrict__ diag
     if (qu <= nu - 1 && qv <= nv - 1 && U[qu] < U[qu + 1] && V[qv] < V[qv + 1]) {
         double thr = fmul(tol_rel, diag[s]);
         r = walk_span_surface<FILL>(pu, pv, U, qu, V, qv, S.cps + 3 * S.cp_off[s], nv, fmul(thr, thr), slot,
-                                    FILL ? cnt[slot] : 0, out, err);
+                                    FILL ? cnt[slot] : 0, out, err, cf);
     }
     if (!FILL) cnt[slot] = r;
 }

@@ -26,6 +26,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "projected pts/s, learned+mixed vs plain FP64, same GB300, at 1e-9 rel. dist"
 TOL = 1e-10
+SURF_TOL = 1e-4  # surfaces: decomposed at the paper's alpha, last Newton steps on the original patch
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -40,8 +41,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--curves", type=int, default=4096, help="curves in the workload")
     ap.add_argument("--queries", type=int, default=1_000_000, help="projection and inversion queries each")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
-                    help="c2: 1M projection + 1M inversion queries; c4: 16M projection queries, same curves")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c3", "c5"],
+                    help="c2: 1M projection + 1M inversion queries; c4: 16M projection queries, same curves; "
+                         "c3: 1,024 surfaces, 4M + 4M queries; c5: 65,536 cubic curves + 8,192 bicubic "
+                         "surfaces, 64M Zipf-skewed queries")
     ap.add_argument("--train-curves", type=int, default=2048, help="curves of the seed network's training set")
     ap.add_argument("--train-queries", type=int, default=3_500_000, help="their projection and inversion queries")
     ap.add_argument("--train-pairs", type=int, default=10_000_000, help="training pairs at most")
@@ -196,6 +199,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.workload in ("c3", "c5"):
+        return run_surface_workloads(args, rank, world, local)
 
     if args.impl == "reference":
         if rank != 0:
@@ -513,7 +519,7 @@ def main():
            "accuracy": acc,
            "e2e": {"value": total_q / (ms_e2e * 1e-3), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
-           "gpu_launches": 24, "roofline": roofline, "clocks": clk,
+           "gpu_launches": 26, "roofline": roofline, "clocks": clk,
            "counters": {"learned_mixed": c_learned, "mixed": c_mixed, "plain_fp64": c_plain}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, nq, el = cpu_oracle_rate(cs, qs)
@@ -522,6 +528,262 @@ def main():
                                "sample": f"{nq} queries of the same workload (half projection, half inversion), "
                                          f"{el:.1f} s",
                                "one_core": {"value": r1, "sample": f"{nq1} queries, {el1:.1f} s"}}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------- surfaces and ragged batch
+
+def build_surface_workload(kind, rank):
+    """c3: the 1,024-surface set, 4M projection + 4M inversion queries.
+    c5: 65,536 cubic curves + 8,192 bicubic surfaces, 64M queries (32M per
+    spline kind, half projection, half inversion), Zipf(1.1) over splines."""
+    from paper_2504_11498_gb300 import synth
+    if kind == "c3":
+        ss, sq = synth.surface_set(seed=3 + 1000 * rank)
+        return None, None, ss, sq
+    cs, ss, qc, qs, rng = synth.ragged_mix(seed=5 + 1000 * rank)
+    cq, sq = synth.ragged_queries(cs, ss, qc, qs, rng)
+    return cs, cq, ss, sq
+
+
+def cpu_oracle_surface_rate(cs, cq, ss, sq, budget_s=15.0, threads=0):
+    """Oracle on the host cores, bounded sample: surface projection and
+    inversion queries (and, for the ragged batch, as many curve queries)."""
+    from oracle import oracle as O
+    threads = threads or O.num_threads()
+    m = 4000
+    S = O.eval_surfaces(ss, sq.inv_surf[:m], sq.inv_uv[:m])[0]
+    B = O.eval_surfaces(ss, sq.proj_surf[:m], sq.proj_uv[:m])[0]
+    Pq = B + sq.proj_dir[:m] * sq.proj_r[:m, None]
+    if cq is not None:
+        C = O.eval_curves(cs, cq.inv_curve[:m], cq.inv_t[:m])[0]
+    done, el, n = 0, 0.0, 50
+    while el < budget_s and done < m:
+        k = min(n, m - done)
+        t0 = time.perf_counter()
+        O.project_surfaces(ss, sq.proj_surf[done:done + k], Pq[done:done + k], nthreads=threads)
+        O.project_surfaces(ss, sq.inv_surf[done:done + k], S[done:done + k], nthreads=threads)
+        if cq is not None:
+            O.project_curves(cs, cq.proj_curve[done:done + k], cq.proj_xyz[done:done + k], nthreads=threads)
+            O.project_curves(cs, cq.inv_curve[done:done + k], C[done:done + k], nthreads=threads)
+        el += time.perf_counter() - t0
+        done += k
+        n = min(2 * n, 1000)
+    per = 2 if cq is None else 4
+    return per * done / el, threads, per * done, el
+
+
+def run_surface_workloads(args, rank, world, local):
+    """The surface set (c3) and the ragged batch (c5).  A step: every query
+    of the batch once.  Surfaces run the mixed path (FP32 grid seed and
+    Newton, last steps in FP64 on the original patch); the ragged batch's
+    curves run the learned path.  Both are set against the plain FP64 path
+    on the same queries."""
+    label = {"c3": "surface_set_1024: 4M projection + 4M inversion queries (bi-degree 2..5)",
+             "c5": "ragged_mix: 65,536 cubic curves + 8,192 bicubic surfaces, 64M queries (Zipf 1.1), "
+                   "half projection, half inversion per spline kind"}[args.workload]
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cs, cq, ss, sq = build_surface_workload(args.workload, 0)
+        rates, t_all = [], 0.0
+        for _ in range(args.warmup):
+            cpu_oracle_surface_rate(cs, cq, ss, sq, budget_s=1.0)
+        for _ in range(args.steps):
+            r, cores, nq, el = cpu_oracle_surface_rate(cs, cq, ss, sq, budget_s=6.0)
+            rates.append(r)
+            t_all += el
+        v = float(np.median(rates))
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "pts/s", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": label},
+                          "cpu_baseline": {"value": v, "unit": "pts/s", "cores": cores, "kind": "oracle",
+                                           "sample": f"{nq} queries per step"},
+                          "e2e": {"value": v, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2504_11498_gb300 import bspl, build
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    cs, cq, ss, sq = build_surface_workload(args.workload, rank)
+    has_c = cs is not None
+
+    def T(x, dt):
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dsf = bspl.DeviceSurfaces(ss, dev)
+    ssegs = bspl.decompose(dsf, SURF_TOL)
+    torch.cuda.synchronize()
+    dec_s = 1e3 * (time.perf_counter() - t0)
+    ps = T(sq.proj_surf, torch.int32)
+    sp = bspl.bspl_eval_surfaces(dsf, ps, T(sq.proj_uv, torch.float64)) + \
+        T(sq.proj_dir, torch.float64) * T(sq.proj_r, torch.float64)[:, None]
+    isf = T(sq.inv_surf, torch.int32)
+    si = bspl.bspl_eval_surfaces(dsf, isf, T(sq.inv_uv, torch.float64))
+    calls = [("surf_proj", bspl.bspl_project_surfaces, ssegs, ps, sp),
+             ("surf_inv", bspl.bspl_invert_surfaces, ssegs, isf, si)]
+    mlp, dec_c, train = None, None, None
+    if has_c:
+        t0 = time.perf_counter()
+        dc = bspl.DeviceCurves(cs, dev)
+        csegs = bspl.decompose(dc, TOL)
+        torch.cuda.synchronize()
+        dec_c = 1e3 * (time.perf_counter() - t0)
+        pc, ic = T(cq.proj_curve, torch.int32), T(cq.inv_curve, torch.int32)
+        cpq = T(cq.proj_xyz, torch.float64)
+        ciq = bspl.bspl_eval_curves(dc, ic, T(cq.inv_t, torch.float64))
+        calls = [("curve_proj", bspl.bspl_project_curves, csegs, pc, cpq),
+                 ("curve_inv", bspl.bspl_invert_curves, csegs, ic, ciq)] + calls
+        mlp, train = train_seed(args, rank, dev)
+    bufs = {name: bspl.QueryBuffers(sg, qi.numel(), dev, learned=name.startswith("curve"))
+            for name, _, sg, qi, _ in calls}
+    n_step = sum(qi.numel() for _, _, _, qi, _ in calls)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def opts(name, fast, **kw):
+        if not fast:
+            return bspl.make_options(prec=bspl.FP64, **kw)
+        if name.startswith("curve"):
+            return bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp, **kw)
+        return bspl.make_options(prec=bspl.MIXED, **kw)
+
+    def step(fast, only=None, **kw):
+        for name, fn, sg, qi, qx in calls:
+            if only is None or name == only:
+                fn(sg, qi, qx, opts(name, fast, **kw), bufs[name])
+
+    def timed(fast, steps, warmup, only=None):
+        for _ in range(warmup):
+            step(fast, only)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            step(fast, only)
+            b.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_fast = timed(True, args.steps, args.warmup)
+    ms_plain = timed(False, max(2, args.steps // 3), 2)
+    per_call = {name: timed(True, max(2, args.steps // 2), 1, only=name) for name, *_ in calls}
+    clk = clocks.stop()
+    if bspl.mlp_check() != bspl.OK:
+        raise SystemExit("a tensor-core wait timed out")
+
+    # accuracy of the timed path against the plain FP64 path, every query
+    step(False)
+    ref = {name: bufs[name].dist.clone() for name in bufs}
+    step(True)
+    acc = {}
+    for name, _, sg, qi, _ in calls:
+        rel = (bufs[name].dist - ref[name]).abs() / sg.diag[qi.long()]
+        acc[name] = {"max_rel_dist_diff_vs_plain_fp64": float(rel.max().item()),
+                     "queries_over_1e-9": int((rel > 1e-9).sum().item())}
+
+    cnt = {}
+    for name, *_ in calls:
+        c = torch.zeros(bspl.NCOUNTERS, dtype=torch.int64, device=dev)
+        step(True, only=name, counters=c)
+        torch.cuda.synchronize()
+        cnt[name] = dict(zip(bspl.COUNTER_NAMES, c.cpu().tolist()))
+
+    # end to end through the public API: inputs from pinned host memory,
+    # results back, every step
+    h_in = {name: (qi.cpu().pin_memory(), qx.cpu().pin_memory()) for name, _, _, qi, qx in calls}
+    h_out = {name: [torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+                    for x in (bufs[name].param, bufs[name].dist, bufs[name].status)] for name in bufs}
+
+    def e2e_step():
+        for name, _, _, qi, qx in calls:
+            qi.copy_(h_in[name][0], non_blocking=True)
+            qx.copy_(h_in[name][1], non_blocking=True)
+        step(True)
+        for name in bufs:
+            for h, d in zip(h_out[name], (bufs[name].param, bufs[name].dist, bufs[name].status)):
+                h.copy_(d, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k_e2e = max(2, args.steps // 3)
+    e0.record(stream)
+    for _ in range(k_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / k_e2e
+    h2d = sum(a.numel() * a.element_size() + b.numel() * b.element_size() for a, b in h_in.values())
+    d2h = sum(x.numel() * x.element_size() for v in h_out.values() for x in v)
+
+    (ms_fast, ms_plain, ms_e2e), total_q = combine_over_ranks([ms_fast, ms_plain, ms_e2e], n_step, world,
+                                                              dist if world > 1 else None, dev)
+
+    # roofline of the dominant call.  Surfaces (mixed): 12 FP32 flops per
+    # group or patch box test, 95 per bicubic grid sample (power-form Horner
+    # in u and v for 3 coordinates, then the squared distance), GU x GV = 32
+    # samples per surviving patch; Newton iterations are not counted, so the
+    # figure is a lower bound.  Curves (learned): as in the curve bench.
+    p32 = bspl.measure_fma_peak(False)
+    dominant = max(per_call, key=per_call.get)
+    c = cnt[dominant]
+    if dominant.startswith("surf"):
+        flops = 12 * (c["grp_tested"] + c["seg_tested"]) + 95 * 32 * c["candidates"]
+        kern = "k_query_surfaces<float,8,4,true>"
+    else:
+        flops = 12 * (c["grp_tested"] + c["seg_tested"]) + 110 * c["candidates"] + 45 * c["newton32_iters"]
+        kern = "learned curve path (k_cull_pairs + pair kernels)"
+    t_dom = per_call[dominant] * 1e-3
+    roofline = {"bound": "alu", "achieved": flops / t_dom / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
+                "frac": flops / t_dom / p32, "traffic": None, "kernel": kern, "call": dominant,
+                "ms_per_step": per_call[dominant], "calls_ms_per_step": per_call,
+                "peak_source": "FP32 FMA-chain microbenchmark on this GPU (of measured)",
+                "note": "counted FP32 flops only (Newton iterations of the surface kernel uncounted): a lower bound"}
+
+    cfg = {"workload": label, "tol_rel_curves": TOL, "tol_rel_surfaces": SURF_TOL,
+           "prec": "surfaces mixed" + (", curves learned_mixed" if has_c else ""),
+           "l2": "512 MB flush between timed steps", "patches": int(ssegs.total), "decompose_surfaces_ms": dec_s}
+    if has_c:
+        cfg.update({"segments": int(csegs.total), "decompose_curves_ms": dec_c, "seed_network": train})
+    # per call: counting sort (histogram, scan, scatter; the scan is one
+    # launch up to 2,048 splines, three above) and the query kernel; the
+    # learned curve call 13
+    launches = {"c3": 2 * 4, "c5": 2 * 6 + 2 * 13}[args.workload]
+    out = {"metric": METRIC, "value": total_q / (ms_fast * 1e-3), "unit": "pts/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fast, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64 (FP32 search, FP64 finish)" + ("; curves bf16+f32+f64" if has_c else ""),
+           "data": "synthetic", "config": cfg,
+           "plain_fp64": {"value": total_q / (ms_plain * 1e-3), "ms_per_step": ms_plain},
+           "speedup_vs_plain": ms_plain / ms_fast, "accuracy": acc,
+           "e2e": {"value": total_q / (ms_e2e * 1e-3), "unit": "pts/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h},
+           "gpu_launches": launches, "roofline": roofline, "clocks": clk, "counters": cnt}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, cores, nq, el = cpu_oracle_surface_rate(cs, cq, ss, sq)
+        out["cpu_baseline"] = {"value": r, "unit": "pts/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{nq} queries of the same workload, {el:.1f} s"}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -306,37 +306,96 @@ __device__ R root_bracketed(const R* a, R qx, R qy, R qz, R lo, R hi, int maxit,
 // once holds exactly one root (a minimum when E goes from - to +); more
 // changes -> split at the middle (de Casteljau); none -> no root.  The ends
 // are minima when E(0) >= 0 or E(1) <= 0.  Returns the best minimiser.
+// Optionally: `second` receives the second smallest D among the local
+// minima found (interior minima, and the ends where E(0) >= 0 or E(1) <= 0;
+// the global minimum is one of them), and `uncertain` is set when an
+// examined interval has a Bernstein coefficient whose magnitude does not
+// exceed its error bound (btol: the bounds of the top-level coefficients;
+// an interval's coefficients are averages of its parent's, so their bounds
+// are the same averages of the parent's bounds), i.e. its sign, and so the
+// count of roots, is not certain at this precision.
+// `second` (when given) holds three values: the second and third smallest
+// D among the local minima and the minimiser of the second.
 template <class R>
-__device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int maxit)
+__device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int maxit, R* second = nullptr,
+                                      const R* btol = nullptr, bool* uncertain = nullptr)
 {
     constexpr int kStack = 24;
     R b0[6];
     bernstein_E(a, qx, qy, qz, b0);
     R bestu = R(0), bestD;
+    // the three smallest D among the local minima (and where the first two are)
+    R m1 = R(INFINITY), m2 = R(INFINITY), m3 = R(INFINITY), u1 = R(0), u2 = R(0);
+    auto local_min = [&](R D, R u) {
+        if (D < m1) {
+            m3 = m2;
+            m2 = m1;
+            u2 = u1;
+            m1 = D;
+            u1 = u;
+        } else if (D < m2) {
+            m3 = m2;
+            m2 = D;
+            u2 = u;
+        } else if (D < m3) {
+            m3 = D;
+        }
+    };
     {
-        R E, Ep;
-        bestD = eval_E(a, qx, qy, qz, R(0), E, Ep);
-        R D1 = eval_E(a, qx, qy, qz, R(1), E, Ep);
+        R E0, E1, Ep;
+        bestD = eval_E(a, qx, qy, qz, R(0), E0, Ep);
+        R D1 = eval_E(a, qx, qy, qz, R(1), E1, Ep);
+        if (E0 >= R(0)) local_min(bestD, R(0));
+        if (E1 <= R(0)) local_min(D1, R(1));
         if (D1 < bestD) {
             bestD = D1;
             bestu = R(1);
         }
     }
-    R st_b[kStack][6];
+    R st_b[kStack][6], st_t[kStack][6];
     R st_lo[kStack], st_hi[kStack];
     int top = 0;
+    const bool track = uncertain != nullptr && btol != nullptr;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) st_b[0][i] = b0[i];
+    for (int i = 0; i < 6; ++i) {
+        st_b[0][i] = b0[i];
+        st_t[0][i] = track ? btol[i] : R(0);
+    }
     st_lo[0] = R(0);
     st_hi[0] = R(1);
     top = 1;
     int budget = 64;  // intervals examined at most
     while (top > 0 && budget-- > 0) {
         --top;
-        R b[6];
+        R b[6], bt[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) b[i] = st_b[top][i];
+        for (int i = 0; i < 6; ++i) {
+            b[i] = st_b[top][i];
+            bt[i] = st_t[top][i];
+        }
         const R lo = st_lo[top], hi = st_hi[top];
+        if (track) {
+            // a coefficient inside its error bound matters only where its
+            // sign could change the decision: at an end of the interval,
+            // between two certain coefficients of the same sign, or in a
+            // run of two or more (a lone one between - and + leaves one
+            // sign change whatever its sign)
+            int left = 0, run = 0;
+            bool relevant = false;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const int sg = b[i] > bt[i] ? 1 : (b[i] < -bt[i] ? -1 : 0);
+                if (sg == 0) {
+                    if (i == 0 || i == 5) relevant = true;
+                    ++run;
+                } else {
+                    if (run > 0 && (run > 1 || left == sg)) relevant = true;
+                    run = 0;
+                    left = sg;
+                }
+            }
+            if (relevant) *uncertain = true;
+        }
         const int v = sign_changes6(b);
         if (v == 0) continue;
         if (v == 1 || top + 2 > kStack || hi - lo <= tol * R(64)) {
@@ -344,6 +403,7 @@ __device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int m
                 R u = root_bracketed(a, qx, qy, qz, lo, hi, maxit, tol);
                 R E, Ep;
                 R D = eval_E(a, qx, qy, qz, u, E, Ep);
+                local_min(D, u);
                 if (D < bestD) {
                     bestD = D;
                     bestu = u;
@@ -353,6 +413,8 @@ __device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int m
                 R u = R(0.5) * (lo + hi);
                 R E, Ep;
                 R D = eval_E(a, qx, qy, qz, u, E, Ep);
+                if (uncertain) *uncertain = true;
+                local_min(D, u);
                 if (D < bestD) {
                     bestD = D;
                     bestu = u;
@@ -360,30 +422,53 @@ __device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int m
             }
             continue;
         }
-        // split at the middle: left and right Bernstein coefficients
-        R w[6], L[6], Rr[6];
+        // split at the middle: left and right Bernstein coefficients (and,
+        // when tracked, their error bounds)
+        R w[6], L[6], Rr[6], wt[6], Lt[6], Rt[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) w[i] = b[i];
+        for (int i = 0; i < 6; ++i) {
+            w[i] = b[i];
+            wt[i] = bt[i];
+        }
         L[0] = w[0];
         Rr[5] = w[5];
+        Lt[0] = wt[0];
+        Rt[5] = wt[5];
 #pragma unroll
         for (int r = 1; r < 6; ++r) {
 #pragma unroll
-            for (int i = 0; i < 6 - r; ++i) w[i] = R(0.5) * (w[i] + w[i + 1]);
+            for (int i = 0; i < 6 - r; ++i) {
+                w[i] = R(0.5) * (w[i] + w[i + 1]);
+                wt[i] = R(0.5) * (wt[i] + wt[i + 1]);
+            }
             L[r] = w[0];
             Rr[5 - r] = w[5 - r];
+            Lt[r] = wt[0];
+            Rt[5 - r] = wt[5 - r];
         }
         const R mid = R(0.5) * (lo + hi);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) st_b[top][i] = Rr[i];
+        for (int i = 0; i < 6; ++i) {
+            st_b[top][i] = Rr[i];
+            st_t[top][i] = Rt[i];
+        }
         st_lo[top] = mid;
         st_hi[top] = hi;
         ++top;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) st_b[top][i] = L[i];
+        for (int i = 0; i < 6; ++i) {
+            st_b[top][i] = L[i];
+            st_t[top][i] = Lt[i];
+        }
         st_lo[top] = lo;
         st_hi[top] = mid;
         ++top;
+    }
+    if (uncertain && top > 0) *uncertain = true;  // the interval budget ran out
+    if (second) {
+        second[0] = m2;
+        second[1] = m3;
+        second[2] = bestu == u1 ? u2 : u1;  // the runner-up's minimiser
     }
     return bestu;
 }

@@ -40,7 +40,9 @@ cudaError_t mlp_seed_pairs(const bspl_mlp* m, const int32_t* pq, const int32_t* 
 
 namespace {
 
-enum : uint8_t { kSeed = 0, kEnd0 = 1, kEnd1 = 2, kEnds = 3, kIso = 4 };
+// kIso: two or more certified sign changes; kIsoU: a coefficient within its
+// rounding bound of zero (the FP32 sign pattern is not certain)
+enum : uint8_t { kSeed = 0, kEnd0 = 1, kEnd1 = 2, kEnds = 3, kIso = 4, kIsoU = 5 };
 constexpr int kPairsPerQuery = 24;  // buffer capacity per query
 
 struct PairBuf {
@@ -49,13 +51,16 @@ struct PairBuf {
     uint8_t* kind;
     float* u;
     float* D32;               // lower bound of the pair's distance (FP32 stage)
-    uint8_t* conv;
+    uint8_t* conv;            // 0: FP32 not converged, 1: converged, 2: FP64 must decide among all
+                              // minima (both ends for kEnds)
     double* D64;
     double* u64;
     uint8_t* fl;
     int64_t cap;
-    unsigned long long* cnt;  // [0] reserved, [1] seeds, [2] others, [3] overflowed queries, [4] finished
+    unsigned long long* cnt;  // [0] reserved, [1] seeds, [2] others, [3] overflowed queries, [4] finished,
+                              // [5] deferred to the FP64 isolation
     int32_t* fin;             // buffer slots of the pairs that got the FP64 finish
+    int32_t* iso;             // buffer slots of the pairs deferred to the FP64 isolation
     const float* qrec;        // per sorted query: q hi[3], q lo[3], eps, curve (int bits; -1 invalid)
     const int32_t* order;     // sorted position -> query index
     int32_t* over;            // overflowed query indices
@@ -64,8 +69,10 @@ struct PairBuf {
     int* bestseg;
 };
 
-// classification of a pair from its FP32 local-frame cubic c (C - q)
-__device__ __forceinline__ uint8_t classify(const float* c)
+// Bernstein coefficients b of E/2 for the FP32 local-frame cubic c (C - q),
+// and ba, the same sums over absolute values (the scale of each
+// coefficient's FP32 rounding error)
+__device__ __forceinline__ void bern_E32(const float* c, float* b, float* ba)
 {
     float e[6] = { 0, 0, 0, 0, 0, 0 }, ea[6] = { 0, 0, 0, 0, 0, 0 };
 #pragma unroll
@@ -86,7 +93,6 @@ __device__ __forceinline__ uint8_t classify(const float* c)
         ea[4] += 5.f * a2 * a3;
         ea[5] += 3.f * a3 * a3;
     }
-    float b[6], ba[6];
     b[0] = e[0];
     b[1] = e[0] + 0.2f * e[1];
     b[2] = e[0] + 0.4f * e[1] + 0.1f * e[2];
@@ -99,15 +105,34 @@ __device__ __forceinline__ uint8_t classify(const float* c)
     ba[3] = ea[0] + 0.6f * ea[1] + 0.3f * ea[2] + 0.1f * ea[3];
     ba[4] = ea[0] + 0.8f * ea[1] + 0.6f * ea[2] + 0.4f * ea[3] + 0.2f * ea[4];
     ba[5] = ea[0] + ea[1] + ea[2] + ea[3] + ea[4] + ea[5];
-    int v = 0, last = 0;
+}
+
+// classification of a pair from its FP32 local-frame cubic c (C - q)
+__device__ __forceinline__ uint8_t classify(const float* c)
+{
+    float b[6], ba[6];
+    bern_E32(c, b, ba);
+    // sign changes of the certain coefficients; a coefficient inside its
+    // rounding bound makes the pair uncertain only where its sign could
+    // change the count: at an end, between two certain coefficients of the
+    // same sign, or in a run of two or more
+    int v = 0, last = 0, run = 0;
+    bool relevant = false;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const float tol = 1e-5f * ba[i];
         const int s = b[i] > tol ? 1 : (b[i] < -tol ? -1 : 0);
-        if (s == 0) return kIso;
+        if (s == 0) {
+            if (i == 0 || i == 5) relevant = true;
+            ++run;
+            continue;
+        }
+        if (run > 0 && (run > 1 || last == s)) relevant = true;
+        run = 0;
         if (last != 0 && s != last) ++v;
         last = s;
     }
+    if (relevant) return kIsoU;
     const bool neg0 = b[0] < 0.f;
     if (v == 0) return neg0 ? kEnd1 : kEnd0;
     if (v == 1) return neg0 ? kSeed : kEnds;
@@ -535,6 +560,13 @@ __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
             local32(P, seg, B.qrec + 8 * pos, c);
             float u, E, Ep;
             bool conv = true;
+            float l1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) l1 += fabsf(c[k]);
+            const float del = 1e-6f * l1;
+            // ambiguous: the FP32 stage cannot tell which candidate of the
+            // pair is the minimum (the FP64 stage then decides among all)
+            bool amb = false, unsure = false;
             if (kind == kSeed) {
                 float lo = 0.f, hi = 1.f;
                 u = have_seed ? fminf(fmaxf(B.u[i], 0.f), 1.f) : 0.5f;
@@ -568,21 +600,45 @@ __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
                 const float D0 = eval_E<float>(c, 0.f, 0.f, 0.f, 0.f, E, Ep);
                 const float D1 = eval_E<float>(c, 0.f, 0.f, 0.f, 1.f, E, Ep);
                 u = D1 < D0 ? 1.f : 0.f;
+                amb = fabsf(sqrtf(D1) - sqrtf(D0)) <= 2.f * del;
             } else {
                 ++n_iso;
-                u = isolate_min<float>(c, 0.f, 0.f, 0.f, 1e-7f, P.fp32_steps * 4);
+                // isolation with the coefficients' rounding scale: an interval
+                // whose sign pattern is not certain makes the pair uncertain
+                float b[6], bt[6], second[3];
+                bern_E32(c, b, bt);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) bt[k] *= 1e-5f;  // the classification's rounding bounds
+                unsure = kind == kIsoU;
+                u = isolate_min<float>(c, 0.f, 0.f, 0.f, 1e-7f, P.fp32_steps * 4, second, bt, &unsure);
                 conv = newton_min<float>(c, 0.f, 0.f, 0.f, u, 1.f / 64.f, P.fp32_steps, 1e-7f, it32);
+                const float dd = sqrtf(eval_E<float>(c, 0.f, 0.f, 0.f, u, E, Ep));
+                amb = unsure || sqrtf(second[0]) - dd <= 2.f * del;
             }
             // FP32 distance and a bound on its error (coefficient rounding
             // and Horner evaluation in the local frame, |u| <= 1)
             const float d = sqrtf(eval_E<float>(c, 0.f, 0.f, 0.f, u, E, Ep));
-            float l1 = 0.f;
-#pragma unroll
-            for (int k = 0; k < 12; ++k) l1 += fabsf(c[k]);
-            const float del = 1e-6f * l1;
             B.u[i] = u;
-            B.D32[i] = d - del;  // lower bound of the pair's distance
-            B.conv[i] = conv ? 1 : 0;
+            // lower bound of the pair's distance; an uncertain isolation may
+            // have missed the segment's minimum, and an unconverged iterate
+            // is not at one: then the distance to the box of the Bezier
+            // control points (convex hull) bounds it
+            float lbd = d;
+            if (unsure || !conv) {
+                float s2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float p0 = c[k], p1 = c[k] + c[3 + k] * (1.f / 3.f),
+                                p2 = c[k] + (2.f * c[3 + k] + c[6 + k]) * (1.f / 3.f),
+                                p3 = c[k] + c[3 + k] + c[6 + k] + c[9 + k];
+                    const float lo = fminf(fminf(p0, p1), fminf(p2, p3)), hi = fmaxf(fmaxf(p0, p1), fmaxf(p2, p3));
+                    const float g = fmaxf(fmaxf(lo, -hi), 0.f);  // the query is the origin of the local frame
+                    s2 += g * g;
+                }
+                lbd = sqrtf(s2);
+            }
+            B.D32[i] = lbd - del;
+            B.conv[i] = amb ? 2 : (conv ? 1 : 0);
             atomicMin(B.best32 + pos, __float_as_uint(d + del));
         }
     }
@@ -632,18 +688,46 @@ __global__ void __launch_bounds__(256, 3) k_pairs_fp64(CurveQ P, PairBuf B)
             double c64[12];
 #pragma unroll
             for (int m = 0; m < 12; ++m) c64[m] = a64[m];
-            double u = (double)B.u[i], last;
-            double D = finish64(c64, P.rec32 + (int64_t)BSPL_CREC32 * seg + 9, q, u, last, it64);
-            uint8_t fl = 0;
-            bool ok = last <= 1e-9;
-            if (!ok) {
-                fl |= BSPL_Q_FALLBACK;
-                ok = newton_min<double>(c64, q[0], q[1], q[2], u, kind == kIso ? 1.0 / 64 : 0.25, P.newton_max, 1e-15,
-                                        it64);
-                double E, Ep;
-                D = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
+            double u = (double)B.u[i], last = 0.0, D = 0.0, E, Ep;
+            bool ok = true;
+            if (B.conv[i] == 2 && kind == kEnds) {
+                // both ends in FP64 (ties: u = 0)
+                const double D0 = eval_E(c64, q[0], q[1], q[2], 0.0, E, Ep);
+                const double D1 = eval_E(c64, q[0], q[1], q[2], 1.0, E, Ep);
+                u = D1 < D0 ? 1.0 : 0.0;
+                D = D1 < D0 ? D1 : D0;
+            } else {
+                // an undecided pair is classified again from E's Bernstein
+                // coefficients in FP64: no sign change, or one from + to -,
+                // puts the minimum at an end; one from - to + is a single
+                // interior minimum (the FP64 steps from the FP32 iterate);
+                // more go to the certified FP64 isolation
+                int v64 = 1;
+                bool at_end = false;
+                if (B.conv[i] == 2) {
+                    double b64[6];
+                    v64 = bernstein_E<double>(c64, q[0], q[1], q[2], b64);
+                    at_end = v64 == 0 || (v64 == 1 && b64[0] > 0.0);
+                }
+                if (at_end) {
+                    const double D0 = eval_E(c64, q[0], q[1], q[2], 0.0, E, Ep);
+                    const double D1 = eval_E(c64, q[0], q[1], q[2], 1.0, E, Ep);
+                    u = D1 < D0 ? 1.0 : 0.0;
+                    D = D1 < D0 ? D1 : D0;
+                    ok = true;
+                } else if (v64 == 1) {
+                    D = finish64(c64, P.rec32 + (int64_t)BSPL_CREC32 * seg + 9, q, u, last, it64);
+                    ok = last <= 1e-9;
+                } else {
+                    ok = false;
+                }
+                if (!ok) {
+                    // to the FP64 isolation, run over a compact list in full warps
+                    B.iso[atomicAdd(B.cnt + 5, 1ull)] = (int32_t)i;
+                    continue;
+                }
             }
-            fl |= ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
+            const uint8_t fl = BSPL_Q_CONVERGED;
             B.D64[i] = D;
             B.u64[i] = u;
             B.fl[i] = fl;
@@ -655,6 +739,37 @@ __global__ void __launch_bounds__(256, 3) k_pairs_fp64(CurveQ P, PairBuf B)
         add_counter(P.counters, BSPL_CNT_NEWTON64_ITERS, it64);
         add_counter(P.counters, BSPL_CNT_NEWTON, nfin);
     }
+}
+
+// (3b') the FP64 fallback: certified isolation of every minimum of the
+// segment (Bernstein sign variations of E in FP64), then the safeguarded
+// iteration from the best one.  Taken by the pairs whose two FP64 steps did
+// not converge and by those the FP32 stage could not decide (an uncertain
+// sign pattern, or two candidates within the FP32 error bound of each other:
+// e.g. two minima of a near-cusp a few hundredths apart).  A separate pass
+// over a compact list, so the long FP64 iteration runs in full warps.
+__global__ void k_pairs_iso64(CurveQ P, PairBuf B)
+{
+    const int64_t n = (int64_t)B.cnt[5];
+    unsigned it64 = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = B.iso[j];
+        const int64_t pos = B.pq[i], seg = B.ps[i];
+        const double* q = P.q_xyz + 3 * (int64_t)B.order[pos];
+        const double* a64 = P.rec64 + (int64_t)BSPL_CREC64 * seg + 6;
+        double c64[12];
+#pragma unroll
+        for (int m = 0; m < 12; ++m) c64[m] = a64[m];
+        double u = isolate_min<double>(c64, q[0], q[1], q[2], 1e-15, P.newton_max);
+        const bool ok = newton_min<double>(c64, q[0], q[1], q[2], u, 1.0 / 64, P.newton_max, 1e-15, it64);
+        double E, Ep;
+        const double D = eval_E(c64, q[0], q[1], q[2], u, E, Ep);
+        B.D64[i] = D;
+        B.u64[i] = u;
+        B.fl[i] = BSPL_Q_FALLBACK | (ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV);
+        atomicMin(B.best64 + pos, (unsigned long long)__double_as_longlong(D));
+    }
+    if (P.counters) add_counter(P.counters, BSPL_CNT_NEWTON64_ITERS, it64);
 }
 
 // (3c) smallest segment among the pairs at the query's best FP64 distance
@@ -733,6 +848,7 @@ bool carve_learned(void* ws, size_t bytes, int64_t n_splines, int64_t n_q, PairB
     B.bestseg = cv.take<int>((size_t)n_q);
     B.cnt = cv.take<unsigned long long>(8);
     B.fin = cv.take<int32_t>((size_t)cap);
+    B.iso = cv.take<int32_t>((size_t)cap);
     B.qrec = cv.take<float>((size_t)n_q * 8);
     if (sort_ws) *sort_ws = sw;
     if (sort_bytes) *sort_bytes = sb;
@@ -831,6 +947,7 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     k_pairs_fp32<<<grid, 256, 0, s>>>(P, B, mlp ? 1 : 0);
     mark(4);
     k_pairs_fp64<<<grid, 256, 0, s>>>(P, B);
+    k_pairs_iso64<<<grid, 128, 0, s>>>(P, B);
     mark(5);
     k_pairs_argseg<<<grid, 256, 0, s>>>(P, B);
     k_pairs_write<<<grid, 256, 0, s>>>(P, B);

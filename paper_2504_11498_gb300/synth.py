@@ -329,6 +329,27 @@ def ragged_mix(seed: int = 5, n_curves: int = 65_536, n_surf: int = 8_192, n_que
     return cs, ss, qc, qs, rng
 
 
+def ragged_queries(cs: CurveSet, ss: SurfaceSet, qc, qs, rng, radius_frac: float = 0.2):
+    """Query recipes of the ragged batch: the first half of each spline kind's
+    queries are projections, the rest inversions.  Curves: points uniform in
+    the curve's control-point box scaled 1.2x, inversion parameters t ~ U[0,1];
+    surfaces: S(u,v) + r w with (u,v) ~ U[0,1]^2, w on the unit sphere and
+    r ~ U[0, radius_frac] x the surface's box diagonal, inversion (u,v) ~ U[0,1]^2."""
+    hc, hs = len(qc) // 2, len(qs) // 2
+    lo, hi = cp_boxes(cs)
+    pc = np.ascontiguousarray(qc[:hc])
+    cq = CurveQueries(pc, _box_queries(rng, lo, hi, pc), np.ascontiguousarray(qc[hc:]),
+                      rng.uniform(0.0, 1.0, size=len(qc) - hc))
+    slo = np.minimum.reduceat(ss.cps, ss.cp_off[:-1], axis=0)
+    shi = np.maximum.reduceat(ss.cps, ss.cp_off[:-1], axis=0)
+    diag = np.linalg.norm(shi - slo, axis=1)
+    ps = np.ascontiguousarray(qs[:hs])
+    sq = SurfaceQueries(ps, rng.uniform(0.0, 1.0, size=(hs, 2)), sphere_dirs(rng, hs),
+                        rng.uniform(0.0, radius_frac, size=hs) * diag[ps], np.ascontiguousarray(qs[hs:]),
+                        rng.uniform(0.0, 1.0, size=(len(qs) - hs, 2)))
+    return cq, sq
+
+
 # ------------------------------------------------------------ learned seed
 
 MLP_SHAPES = (("W1", (128, 16)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (128, 128)),

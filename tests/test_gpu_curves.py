@@ -267,3 +267,36 @@ def test_counters_and_unsorted_order_agree():
     assert np.array_equal(d1, d2) and np.array_equal(t1, t2)
     c = cnt.cpu().numpy()
     assert c[0] == 3000 and c[3] >= 3000 and c[4] >= 3000
+
+
+def test_near_cusp_segment():
+    """A cubic whose last three control points nearly coincide ends in a
+    hook where E = (C - q).C' stays below FP32 resolution over a range of u
+    and D can have two minima a few hundredths apart in u.  Inversion points
+    on the hook must be found at distance ~0 by every path (the FP32 stages
+    cannot tell those minima apart; the FP64 stage must)."""
+    R = np.array([[0.84270971, 0.61142076, 0.05979669], [0.89519636, 0.69535237, 0.12377618],
+                  [0.88879253, 0.68117491, 0.11230443], [0.88830283, 0.68292934, 0.11401205]])
+    cs = synth.pack_curves([3], [np.array([0, 0, 0, 0, 1, 1, 1, 1.0])], [R])
+    segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), 1e-10)
+    t = np.linspace(0.55, 1.0, 20001)
+    qc = np.zeros(len(t), np.int32)
+    on = O.eval_curves(cs, qc, t)[0]
+    rng = np.random.default_rng(31)
+    near = on + rng.normal(0, 2e-5, on.shape)
+    diag = O.curve_diag(cs)[0]
+    mlp = bspl.Mlp(synth.mlp_init(7), DEV)
+    _, d_o = O.project_curves(cs, qc, near)
+    for prec, kw in ((bspl.FP64, {}), (bspl.LEARNED_MIXED, {"mlp": mlp}), (bspl.LEARNED_MIXED, {})):
+        _, d, _ = run_queries(segs, qc, on, invert=True, prec=prec, **kw)
+        assert np.max(d) <= 1e-9 * diag, (prec, np.max(d) / diag, t[np.argmax(d)])
+        _, d, _ = run_queries(segs, qc, near, prec=prec, **kw)
+        assert np.max(np.abs(d - d_o)) <= 1e-9 * diag, (prec, np.max(np.abs(d - d_o)) / diag)
+    assert bspl.mlp_check() == bspl.OK
+    # the mixed grid path seeds from FP32 samples: two minima closer than
+    # the sample spacing form one basin, and its FP64 finish polishes the
+    # one FP32 picked (a known limitation of that path; bounded, reported)
+    _, d, _ = run_queries(segs, qc, on, invert=True, prec=bspl.MIXED)
+    miss = d > 1e-9 * diag
+    print(f"mixed grid path, near-cusp inversions: {int(miss.sum())} of {len(t)} off the curve")
+    assert miss.mean() < 0.02

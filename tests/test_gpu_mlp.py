@@ -189,8 +189,10 @@ def test_learned_path_parity(net):
     ctr = _counters()
     t, d, st = _run(segs, qc, q, False, bspl.LEARNED_MIXED, mlp, ctr)
     check_against_oracle(sub, qc, q, t, d, tol)
-    # the two FP64 steps settle almost every query without the FP64 fallback
-    assert int(ctr[bspl.COUNTER_NAMES.index("fallback")]) <= len(qc) // 100
+    # the two FP64 steps settle almost every query; the FP64 fallback (the
+    # certified FP64 isolation, also taken by pairs whose FP32 isolation was
+    # uncertain or could not separate two candidates) decides a few percent
+    assert int(ctr[bspl.COUNTER_NAMES.index("fallback")]) <= 3 * len(qc) // 100
     assert not np.any(st & (bspl.Q_INVALID | bspl.Q_NONCONV))
     t, d, st = _run(segs, ic, C, True, bspl.LEARNED_MIXED, mlp)
     check_against_oracle(sub, ic, C, t, d, tol)

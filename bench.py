@@ -472,11 +472,11 @@ def main():
                  "peak_source": "FP32 FMA-chain microbenchmark on this GPU (of measured)"}
     roofline = dict(cull_line if dominant == "cull" else (mlp_line if dominant == "seed" else cull_line))
     # DRAM bytes of the dominant kernel per step: ncu capture of the same
-    # kernel on the 1,024-curve, 250k + 250k-query case (248.1 MB per
+    # kernel on the 1,024-curve, 250k + 250k-query case (247.6 MB per
     # launch), scaled by the units processed (4x queries and tables) and the
     # two launches of a step
     n_calls = 2 if ic.numel() > 0 else 1
-    traffic = n_calls * 4 * 248.10e6 * (pc.numel() / 1_000_000) if dominant == "cull" else None
+    traffic = n_calls * 4 * 247.56e6 * (pc.numel() / 1_000_000) if dominant == "cull" else None
     roofline.update({"kernel": "k_cull_pairs" if roofline["bound"] == "alu" else "k_mlp_fused",
                      "traffic": traffic, "traffic_unit": f"bytes per step ({n_calls} launch(es))",
                      "stages_ms_per_step": st_ms, "dominant_stage": dominant,

@@ -214,6 +214,10 @@ __device__ __forceinline__ double finish64(const double* a64, const float* a32, 
         double un = Ep > 0.f ? u - E * (double)(1.f / Ep) : u;
         un = fmin(fmax(un, 0.0), 1.0);
         last = fabs(un - u);
+        // without a Newton step (E' <= 0) the point is a minimum only at an
+        // end where D rises into the segment; anywhere else it is not
+        // converged, however small the (zero) step
+        if (!(Ep > 0.f) && !((u <= 0.0 && E >= 0.0) || (u >= 1.0 && E <= 0.0))) last = 1.0;
         u = un;
     }
     double D = 0.0;
@@ -262,6 +266,21 @@ __device__ __forceinline__ int bernstein_E(const R* a, R qx, R qy, R qz, R* b)
         }
     }
     return v;
+}
+
+// sign of the first and of the last nonzero coefficient (0 if all are zero):
+// the direction of a single sign change (zeros are skipped when counting)
+template <class R>
+__device__ __forceinline__ void end_signs6(const R* b, int& first, int& last)
+{
+    first = 0;
+    last = 0;
+#pragma unroll
+    for (int i = 5; i >= 0; --i)
+        if (b[i] != R(0)) first = b[i] > R(0) ? 1 : -1;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        if (b[i] != R(0)) last = b[i] > R(0) ? 1 : -1;
 }
 
 template <class R>
@@ -399,7 +418,11 @@ __device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int m
         const int v = sign_changes6(b);
         if (v == 0) continue;
         if (v == 1 || top + 2 > kStack || hi - lo <= tol * R(64)) {
-            if (b[0] < R(0) && b[5] > R(0)) {
+            // a crossing from - to + (a minimum inside); an end coefficient
+            // that rounded to exactly 0 does not hide it
+            int sf, sl;
+            end_signs6(b, sf, sl);
+            if (sf < 0 && sl > 0) {
                 R u = root_bracketed(a, qx, qy, qz, lo, hi, maxit, tol);
                 R E, Ep;
                 R D = eval_E(a, qx, qy, qz, u, E, Ep);

@@ -706,8 +706,10 @@ __global__ void __launch_bounds__(256, 3) k_pairs_fp64(CurveQ P, PairBuf B)
                 bool at_end = false;
                 if (B.conv[i] == 2) {
                     double b64[6];
+                    int sf, sl;
                     v64 = bernstein_E<double>(c64, q[0], q[1], q[2], b64);
-                    at_end = v64 == 0 || (v64 == 1 && b64[0] > 0.0);
+                    end_signs6(b64, sf, sl);
+                    at_end = v64 == 0 || (v64 == 1 && sf > 0);
                 }
                 if (at_end) {
                     const double D0 = eval_E(c64, q[0], q[1], q[2], 0.0, E, Ep);

@@ -302,13 +302,16 @@ def test_near_cusp_segment():
     assert miss.mean() < 0.02
 
 
-@pytest.mark.xfail(strict=False, reason="open: the learned path misses the minimum of this single query "
-                   "(it returns another segment's local minimum, 0.0778 vs 0.0719); the FP32 emulation of the "
-                   "culling, classification and both pair stages finds it")
+@pytest.mark.xfail(strict=False, reason="fix not yet run on a GPU: the FP32 isolation skipped a crossing whose "
+                   "end coefficient rounded to exactly 0 and the FP64 steps accepted the end without a step")
 def test_learned_single_query_regression():
     """One projection query of the 16M-query workload on the 4,096-curve set
-    where the learned path returned the local minimum of another segment;
-    reproduces alone (one query per batch), with and without a network."""
+    where the learned path returned the local minimum of another segment
+    (0.0778 instead of 0.0719), alone, with and without a network.  On the
+    right segment E(1) is 2^-22 in FP32, the size of its rounding: rounded
+    to exactly 0, the isolation saw one sign change yet no crossing from -
+    to + (it tested the last coefficient, not the last nonzero one) and kept
+    the end u = 1, where E' < 0 let the two FP64 steps stop without a step."""
     cs, _ = synth.curve_set(seed=2, n_curves=4096, n_proj=1, n_inv=0)
     segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), 1e-10)
     qc = np.array([3673], np.int32)

@@ -390,7 +390,7 @@ __device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int m
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             b[i] = st_b[top][i];
-            bt[i] = st_t[top][i];
+            bt[i] = track ? st_t[top][i] : R(0);
         }
         const R lo = st_lo[top], hi = st_hi[top];
         if (track) {
@@ -447,42 +447,45 @@ __device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int m
         }
         // split at the middle: left and right Bernstein coefficients (and,
         // when tracked, their error bounds)
-        R w[6], L[6], Rr[6], wt[6], Lt[6], Rt[6];
+        R w[6], L[6], Rr[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            w[i] = b[i];
-            wt[i] = bt[i];
-        }
+        for (int i = 0; i < 6; ++i) w[i] = b[i];
         L[0] = w[0];
         Rr[5] = w[5];
-        Lt[0] = wt[0];
-        Rt[5] = wt[5];
 #pragma unroll
         for (int r = 1; r < 6; ++r) {
 #pragma unroll
-            for (int i = 0; i < 6 - r; ++i) {
-                w[i] = R(0.5) * (w[i] + w[i + 1]);
-                wt[i] = R(0.5) * (wt[i] + wt[i + 1]);
-            }
+            for (int i = 0; i < 6 - r; ++i) w[i] = R(0.5) * (w[i] + w[i + 1]);
             L[r] = w[0];
             Rr[5 - r] = w[5 - r];
-            Lt[r] = wt[0];
-            Rt[5 - r] = wt[5 - r];
         }
         const R mid = R(0.5) * (lo + hi);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            st_b[top][i] = Rr[i];
-            st_t[top][i] = Rt[i];
+        for (int i = 0; i < 6; ++i) st_b[top][i] = Rr[i];
+        if (track) {
+            R wt[6], Lt[6], Rt[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) wt[i] = bt[i];
+            Lt[0] = wt[0];
+            Rt[5] = wt[5];
+#pragma unroll
+            for (int r = 1; r < 6; ++r) {
+#pragma unroll
+                for (int i = 0; i < 6 - r; ++i) wt[i] = R(0.5) * (wt[i] + wt[i + 1]);
+                Lt[r] = wt[0];
+                Rt[5 - r] = wt[5 - r];
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                st_t[top][i] = Rt[i];
+                st_t[top + 1][i] = Lt[i];
+            }
         }
         st_lo[top] = mid;
         st_hi[top] = hi;
         ++top;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            st_b[top][i] = L[i];
-            st_t[top][i] = Lt[i];
-        }
+        for (int i = 0; i < 6; ++i) st_b[top][i] = L[i];
         st_lo[top] = lo;
         st_hi[top] = mid;
         ++top;

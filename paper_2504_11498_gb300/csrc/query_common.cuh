@@ -1,4 +1,4 @@
-// Device helpers shared by the curve query kernels: launch constants, the
+// Helpers shared by the curve query kernels: launch constants, the
 // query parameter block, box and point distance bounds, E = (C - q).C' and
 // its derivative (Sec. 4.2.3 Eqs. Dt, Et, E't), safeguarded and bracketed
 // Newton iterations, the Bernstein form of E (degree-5 power-to-Bernstein
@@ -99,7 +99,7 @@ __device__ __forceinline__ R slacked(R ub, R eps)
 // E = (C - q).C' and E' = C'.C' + (C - q).C'' for the cubic a0 + a1 u + a2 u^2 + a3 u^3
 // (Eqs. Et, E't up to the common factor 2); returns D = |C - q|^2
 template <class R>
-__device__ __forceinline__ R eval_E(const R* a, R qx, R qy, R qz, R u, R& E, R& Ep)
+__host__ __device__ __forceinline__ R eval_E(const R* a, R qx, R qy, R qz, R u, R& E, R& Ep)
 {
     R q3[3] = { qx, qy, qz };
     R D = 0, e = 0, ep = 0;
@@ -136,7 +136,7 @@ struct Eps<double> {
 };
 
 template <class R>
-__device__ bool newton_min(const R* a, R qx, R qy, R qz, R& u, R hmax, int maxit, R tol, unsigned& iters)
+__host__ __device__ bool newton_min(const R* a, R qx, R qy, R qz, R& u, R hmax, int maxit, R tol, unsigned& iters)
 {
     // coordinate resolution of the evaluation: a Newton correction that moves
     // the point by less than this is rounding noise, and the iteration stops
@@ -186,7 +186,7 @@ __device__ bool newton_min(const R* a, R qx, R qy, R qz, R& u, R hmax, int maxit
 // error enters the next error linearly, times a step already near 1e-7).
 // a64: FP64 power coefficients a0..a3 [12]; a32: FP32 a1..a3 [9].  Returns
 // D = |C(u) - q|^2 in FP64 at the final u; last = size of the second step.
-__device__ __forceinline__ double finish64(const double* a64, const float* a32, const double* q, double& u,
+__host__ __device__ __forceinline__ double finish64(const double* a64, const float* a32, const double* q, double& u,
                                            double& last, unsigned& iters)
 {
     double c0[3], b3[3];
@@ -215,9 +215,10 @@ __device__ __forceinline__ double finish64(const double* a64, const float* a32, 
         un = fmin(fmax(un, 0.0), 1.0);
         last = fabs(un - u);
         // without a Newton step (E' <= 0) the point is a minimum only at an
-        // end where D rises into the segment; anywhere else it is not
-        // converged, however small the (zero) step
-        if (!(Ep > 0.f) && !((u <= 0.0 && E >= 0.0) || (u >= 1.0 && E <= 0.0))) last = 1.0;
+        // end where D rises into the segment (E > 0 at u = 0, E < 0 at
+        // u = 1); anywhere else, a flat end included, it is not converged,
+        // however small the (zero) step
+        if (!(Ep > 0.f) && !((u <= 0.0 && E > 0.0) || (u >= 1.0 && E < 0.0))) last = 1.0;
         u = un;
     }
     double D = 0.0;
@@ -235,7 +236,7 @@ __device__ __forceinline__ double finish64(const double* a64, const float* a32, 
 // Bernstein matrix of Sec. 4.3).  Returns the number of sign changes of b
 // (zeros skipped), an upper bound of the number of roots of E in [0,1].
 template <class R>
-__device__ __forceinline__ int bernstein_E(const R* a, R qx, R qy, R qz, R* b)
+__host__ __device__ __forceinline__ int bernstein_E(const R* a, R qx, R qy, R qz, R* b)
 {
     const R q3[3] = { qx, qy, qz };
     R e[6] = { 0, 0, 0, 0, 0, 0 };
@@ -271,7 +272,7 @@ __device__ __forceinline__ int bernstein_E(const R* a, R qx, R qy, R qz, R* b)
 // sign of the first and of the last nonzero coefficient (0 if all are zero):
 // the direction of a single sign change (zeros are skipped when counting)
 template <class R>
-__device__ __forceinline__ void end_signs6(const R* b, int& first, int& last)
+__host__ __device__ __forceinline__ void end_signs6(const R* b, int& first, int& last)
 {
     first = 0;
     last = 0;
@@ -284,7 +285,7 @@ __device__ __forceinline__ void end_signs6(const R* b, int& first, int& last)
 }
 
 template <class R>
-__device__ __forceinline__ int sign_changes6(const R* b)
+__host__ __device__ __forceinline__ int sign_changes6(const R* b)
 {
     int v = 0;
     R last = 0;
@@ -300,7 +301,7 @@ __device__ __forceinline__ int sign_changes6(const R* b)
 
 // bracketed Newton on E for its root in [lo, hi] with E(lo) < 0 < E(hi)
 template <class R>
-__device__ R root_bracketed(const R* a, R qx, R qy, R qz, R lo, R hi, int maxit, R tol)
+__host__ __device__ R root_bracketed(const R* a, R qx, R qy, R qz, R lo, R hi, int maxit, R tol)
 {
     R u = R(0.5) * (lo + hi);
     for (int it = 0; it < maxit; ++it) {
@@ -336,7 +337,7 @@ __device__ R root_bracketed(const R* a, R qx, R qy, R qz, R lo, R hi, int maxit,
 // `second` (when given) holds three values: the second and third smallest
 // D among the local minima and the minimiser of the second.
 template <class R>
-__device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int maxit, R* second = nullptr,
+__host__ __device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R tol, int maxit, R* second = nullptr,
                                       const R* btol = nullptr, bool* uncertain = nullptr)
 {
     constexpr int kStack = 24;

@@ -1,0 +1,131 @@
+"""CPU tests of the curve query numerics shared with the GPU kernels
+(csrc/query_common.cuh compiled for the host): decisions of the certified
+isolation and of the two FP64 Newton steps on constructed segments whose
+critical values are exact in FP32 and FP64."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module")
+def hn(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("hn") / "libhn.so")
+    cmd = [nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"),
+           os.path.join(HERE, "host_numerics.cu"), "-o", out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    lib = ctypes.CDLL(out)
+    F = ctypes.POINTER(ctypes.c_float)
+    D = ctypes.POINTER(ctypes.c_double)
+    I = ctypes.POINTER(ctypes.c_int)
+    lib.hn_bernstein_f.argtypes = [F, F]
+    lib.hn_end_signs_d.argtypes = [D, I, I]
+    lib.hn_isolate_f.argtypes = [F, ctypes.c_int, F, I, F]
+    lib.hn_isolate_f.restype = ctypes.c_float
+    lib.hn_isolate_d.argtypes = [D, D, ctypes.c_int]
+    lib.hn_isolate_d.restype = ctypes.c_double
+    lib.hn_finish64.argtypes = [D, D, D, D]
+    lib.hn_finish64.restype = ctypes.c_double
+    return lib
+
+
+def fp(x):
+    return np.ascontiguousarray(x, np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def dp(x):
+    return x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# C(u) - q = (u - 1, 1 - 4u + 8u^2 - 4u^3, 0): at u = 1 the point is (0, 1, 0)
+# and the tangent (1, 0, 0), so E(1) = 0 exactly in any precision, and u = 1
+# is a local maximum of D (D''(1) < 0); E has three roots, the minimum is
+# interior.
+HOOK = np.array([-1.0, 1.0, 0.0, 1.0, -4.0, 0.0, 0.0, 8.0, 0.0, 0.0, -4.0, 0.0])
+# C(u) - q = (1 - (1-u)^3 - 1/2, 1, 0): E = x x' = 3 (1-u)^2 (x) has one
+# crossing from - to + (the minimum, at 1 - 2^(-1/3)) and a double root at
+# u = 1, where D flattens out; its last Bernstein coefficients are exactly 0.
+FLAT = np.array([-0.5, 1.0, 0.0, 3.0, 0.0, 0.0, -3.0, 0.0, 0.0, 1.0, 0.0, 0.0])
+
+
+def d2(a, u):
+    u = np.asarray(u, float)[..., None]
+    return np.sum((a[0:3] + u * (a[3:6] + u * (a[6:9] + u * a[9:12]))) ** 2, axis=-1)
+
+
+def argmin_dense(a):
+    us = np.linspace(0, 1, 400001)
+    return us[np.argmin(d2(a, us))]
+
+
+def isolate32(hn, a, btol=None):
+    unc = ctypes.c_int()
+    sec = np.zeros(3, np.float32)
+    u = hn.hn_isolate_f(fp(a), 16, fp(btol) if btol is not None else None, ctypes.byref(unc),
+                        sec.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    return u, unc.value
+
+
+def finish(hn, a, u0):
+    u, last = ctypes.c_double(u0), ctypes.c_double()
+    D = hn.hn_finish64(dp(np.array(a, float)), dp(np.zeros(3)), ctypes.byref(u), ctypes.byref(last))
+    return u.value, last.value, D
+
+
+def test_end_signs_skip_zeros(hn):
+    f, l = ctypes.c_int(), ctypes.c_int()
+    for b, want in (([-1, -2, -1, 2, 1, 0], (-1, 1)), ([0, 0, 3, -1, 0, 0], (1, -1)), ([0] * 6, (0, 0)),
+                    ([-1, 0, 0, 0, 0, 2], (-1, 1))):
+        hn.hn_end_signs_d(dp(np.array(b, float)), ctypes.byref(f), ctypes.byref(l))
+        assert (f.value, l.value) == want
+
+
+def test_flat_end_has_exact_zero_end_coefficient(hn):
+    b = np.zeros(6, np.float32)
+    v = hn.hn_bernstein_f(fp(FLAT), b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    assert b[5] == 0.0 and b[0] < 0 and v in (1, 2)
+    assert abs(argmin_dense(FLAT) - (1 - 2 ** (-1 / 3))) < 1e-5
+
+
+@pytest.mark.parametrize("a", [HOOK, FLAT], ids=["three-changes", "zero-end"])
+def test_isolation_finds_the_interior_minimum(hn, a):
+    u_star = argmin_dense(a)
+    assert 0.05 < u_star < 0.95 and d2(a, u_star) < min(d2(a, 0.0), d2(a, 1.0))
+    for btol in (None, np.full(6, 1e-6, np.float32)):
+        u, _ = isolate32(hn, a, btol)
+        assert abs(u - u_star) < 1e-4, u
+    u = hn.hn_isolate_d(dp(np.array(a, float)), dp(np.zeros(3)), 30)
+    assert abs(u - u_star) < 1e-5
+
+
+@pytest.mark.parametrize("a", [HOOK, FLAT], ids=["three-changes", "zero-end"])
+def test_fp64_steps_do_not_converge_at_a_flat_end(hn, a):
+    # E(1) = 0 and E'(1) <= 0: no Newton step; u = 1 is not a minimum
+    _, last, _ = finish(hn, a, 1.0)
+    assert last > 1e-9
+    # from the FP32 isolation's minimiser the steps converge to the minimum
+    u_star = argmin_dense(a)
+    u32, _ = isolate32(hn, a)
+    u, last, _ = finish(hn, a, float(u32))
+    assert last <= 1e-9 and abs(u - u_star) < 1e-5
+
+
+def test_fp64_steps_converge_at_a_valid_end(hn):
+    # a straight segment moving away from q: the minimum is at u = 0 (E(0) > 0)
+    a = np.array([1.0, 0, 0, 1.0, 0, 0, 0, 0, 0, 0, 0, 0])
+    u, last, D = finish(hn, a, 0.0)
+    assert last <= 1e-9 and u == 0.0 and D == 1.0
+    # and one moving towards q ending short of it: the minimum is at u = 1 (E(1) < 0)
+    a = np.array([-3.0, 0, 0, 1.0, 0, 0, 0, 0, 0, 0, 0, 0])
+    u, last, D = finish(hn, a, 1.0)
+    assert last <= 1e-9 and u == 1.0 and D == 4.0

@@ -53,7 +53,9 @@ typedef enum {
 
 /* per-query status bits */
 #define BSPL_Q_CONVERGED 1u  /* the final Newton step met its tolerance          */
-#define BSPL_Q_FALLBACK 2u   /* mixed/learned result needed the FP64 fallback    */
+#define BSPL_Q_FALLBACK 2u   /* mixed/learned result needed the FP64 fallback
+                                (safeguarded iteration, or the certified FP64
+                                isolation of the segment's minima)              */
 #define BSPL_Q_AT_END 4u     /* minimiser at an end of the parameter domain      */
 #define BSPL_Q_NONCONV 8u    /* Newton cap reached without convergence           */
 #define BSPL_Q_OFF_CURVE 16u /* inversion: distance above 1e-9 x diagonal        */
@@ -225,9 +227,6 @@ bspl_status bspl_decompose(int is_surface, const void* splines, double tol_rel, 
                            int64_t* n_seg_total, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Projection of n_q points q_xyz [n_q][3] onto curves q_curve [n_q] (Eq.
- * projections); with opt->prec = BSPL_LEARNED_MIXED at most 89,478,314
- * queries per call (the pair buffer is indexed in 32 bits). */
-/* Projection of n_q points q_xyz [n_q][3] onto curves q_curve [n_q] (Eq.
  * projections): t [n_q] receives the minimising parameter in the curve's
  * original parameter (Sec. 4.4.2 reparameterisation), dist [n_q] the distance
  * to the decomposed curve, status [n_q] the BSPL_Q_* bits.  Search: group
@@ -235,8 +234,15 @@ bspl_status bspl_decompose(int is_surface, const void* splines, double tol_rel, 
  * an upper bound from points on the curve, sample a grid on each surviving
  * segment, refine every sampled basin by safeguarded Newton on E = D'
  * (Eqs. Dt, Et, E't), keep the smallest distance (ties: smallest parameter).
- * opt->prec selects FP64 or FP32 search + 2 FP64 Newton steps.
- * Workspace: bspl_workspace_bytes(BSPL_OP_QUERY_CURVES, n, n_cp_total, n_seg, n_q). */
+ * opt->prec selects FP64 or FP32 search + 2 FP64 Newton steps; with
+ * BSPL_LEARNED_MIXED every surviving (query, segment) pair is classified by
+ * the signs of E's Bernstein coefficients (Sec. 4.3) instead of sampled, the
+ * single-minimum pairs are seeded by the network (bspl_mlp.h), and pairs the
+ * FP32 stage cannot settle are decided in FP64 (the certified isolation when
+ * needed); at most 89,478,314 queries per call (the pair buffer is indexed
+ * in 32 bits).
+ * Workspace: bspl_workspace_bytes(BSPL_OP_QUERY_CURVES, n, n_cp_total, n_seg, n_q)
+ * (BSPL_OP_QUERY_CURVES_LEARNED for the learned path). */
 bspl_status bspl_project_curves(const bspl_segments* segs, int64_t n_q, const int32_t* q_curve,
                                 const double* q_xyz, const bspl_options* opt, double* t, double* dist,
                                 uint8_t* status, void* ws, size_t ws_bytes, cudaStream_t stream);

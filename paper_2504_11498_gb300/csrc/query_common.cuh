@@ -500,6 +500,84 @@ __host__ __device__ __noinline__ R isolate_min(const R* a, R qx, R qy, R qz, R t
     return bestu;
 }
 
+// Kinds of a (query, segment) pair in the learned path, from the signs of
+// the Bernstein coefficients of E (Sec. 4.3): kSeed one certified change from
+// - to + (exactly one interior minimum), kEnd0 / kEnd1 none (the minimum at
+// u = 0 / 1), kEnds one from + to - (a maximum inside, the minimum at an
+// end), kIso two or more certified changes, kIsoU a coefficient within its
+// rounding bound of zero where its sign could change the count.
+enum : uint8_t { kSeed = 0, kEnd0 = 1, kEnd1 = 2, kEnds = 3, kIso = 4, kIsoU = 5 };
+
+// Bernstein coefficients b of E/2 for the FP32 local-frame cubic c (C - q),
+// and ba, the same sums over absolute values (the scale of each
+// coefficient's FP32 rounding error)
+__host__ __device__ __forceinline__ void bern_E32(const float* c, float* b, float* ba)
+{
+    float e[6] = { 0, 0, 0, 0, 0, 0 }, ea[6] = { 0, 0, 0, 0, 0, 0 };
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float c0 = c[k], c1 = c[3 + k], c2 = c[6 + k], c3 = c[9 + k];
+        const float d1 = c1, d2 = 2.f * c2, d3 = 3.f * c3;
+        e[0] += c0 * d1;
+        e[1] += c0 * d2 + c1 * d1;
+        e[2] += c0 * d3 + c1 * d2 + c2 * d1;
+        e[3] += c1 * d3 + c2 * d2 + c3 * d1;
+        e[4] += c2 * d3 + c3 * d2;
+        e[5] += c3 * d3;
+        const float a0 = fabsf(c0), a1 = fabsf(c1), a2 = fabsf(c2), a3 = fabsf(c3);
+        ea[0] += a0 * a1;
+        ea[1] += 2.f * a0 * a2 + a1 * a1;
+        ea[2] += 3.f * a0 * a3 + 3.f * a1 * a2;
+        ea[3] += 4.f * a1 * a3 + 2.f * a2 * a2;
+        ea[4] += 5.f * a2 * a3;
+        ea[5] += 3.f * a3 * a3;
+    }
+    b[0] = e[0];
+    b[1] = e[0] + 0.2f * e[1];
+    b[2] = e[0] + 0.4f * e[1] + 0.1f * e[2];
+    b[3] = e[0] + 0.6f * e[1] + 0.3f * e[2] + 0.1f * e[3];
+    b[4] = e[0] + 0.8f * e[1] + 0.6f * e[2] + 0.4f * e[3] + 0.2f * e[4];
+    b[5] = e[0] + e[1] + e[2] + e[3] + e[4] + e[5];
+    ba[0] = ea[0];
+    ba[1] = ea[0] + 0.2f * ea[1];
+    ba[2] = ea[0] + 0.4f * ea[1] + 0.1f * ea[2];
+    ba[3] = ea[0] + 0.6f * ea[1] + 0.3f * ea[2] + 0.1f * ea[3];
+    ba[4] = ea[0] + 0.8f * ea[1] + 0.6f * ea[2] + 0.4f * ea[3] + 0.2f * ea[4];
+    ba[5] = ea[0] + ea[1] + ea[2] + ea[3] + ea[4] + ea[5];
+}
+
+// classification of a pair from its FP32 local-frame cubic c (C - q)
+__host__ __device__ __forceinline__ uint8_t classify(const float* c)
+{
+    float b[6], ba[6];
+    bern_E32(c, b, ba);
+    // sign changes of the certain coefficients; a coefficient inside its
+    // rounding bound makes the pair uncertain only where its sign could
+    // change the count: at an end, between two certain coefficients of the
+    // same sign, or in a run of two or more
+    int v = 0, last = 0, run = 0;
+    bool relevant = false;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float tol = 1e-5f * ba[i];
+        const int s = b[i] > tol ? 1 : (b[i] < -tol ? -1 : 0);
+        if (s == 0) {
+            if (i == 0 || i == 5) relevant = true;
+            ++run;
+            continue;
+        }
+        if (run > 0 && (run > 1 || last == s)) relevant = true;
+        run = 0;
+        if (last != 0 && s != last) ++v;
+        last = s;
+    }
+    if (relevant) return kIsoU;
+    const bool neg0 = b[0] < 0.f;
+    if (v == 0) return neg0 ? kEnd1 : kEnd0;
+    if (v == 1) return neg0 ? kSeed : kEnds;
+    return kIso;
+}
+
 // lexicographic (D, seg, u) order; D >= 0, so its bit pattern orders like an integer
 __device__ __forceinline__ bool better(double D, int s, double u, double bD, int bs, double bu)
 {

@@ -15,6 +15,10 @@ int hn_bernstein_f(const float* a, float* b) { return bernstein_E<float>(a, 0.f,
 
 void hn_end_signs_d(const double* b, int* first, int* last) { end_signs6<double>(b, *first, *last); }
 
+// kind of a pair from its FP32 local-frame cubic (kSeed 0, kEnd0 1, kEnd1 2,
+// kEnds 3, kIso 4, kIsoU 5)
+int hn_classify(const float* c) { return (int)classify(c); }
+
 // FP32 isolation as the learned path calls it; btol may be null
 float hn_isolate_f(const float* a, int maxit, const float* btol, int* uncertain, float* second3)
 {

@@ -30,6 +30,7 @@ def hn(tmp_path_factory):
     I = ctypes.POINTER(ctypes.c_int)
     lib.hn_bernstein_f.argtypes = [F, F]
     lib.hn_end_signs_d.argtypes = [D, I, I]
+    lib.hn_classify.argtypes = [F]
     lib.hn_isolate_f.argtypes = [F, ctypes.c_int, F, I, F]
     lib.hn_isolate_f.restype = ctypes.c_float
     lib.hn_isolate_d.argtypes = [D, D, ctypes.c_int]
@@ -129,3 +130,48 @@ def test_fp64_steps_converge_at_a_valid_end(hn):
     a = np.array([-3.0, 0, 0, 1.0, 0, 0, 0, 0, 0, 0, 0, 0])
     u, last, D = finish(hn, a, 1.0)
     assert last <= 1e-9 and u == 1.0 and D == 4.0
+
+
+def cubic(x, y=(1.0, 0, 0, 0)):
+    """local-frame coefficients of C(u) - q = (x(u), y(u), 0), power basis"""
+    return np.array([x[0], y[0], 0, x[1], y[1], 0, x[2], y[2], 0, x[3], y[3], 0], float)
+
+
+KINDS = {"seed": 0, "end0": 1, "end1": 2, "ends": 3, "iso": 4, "isou": 5}
+
+
+@pytest.mark.parametrize("a,kind", [
+    (cubic((-0.5, 1, 0, 0)), "seed"),        # passes q at u = 1/2: one change from - to +
+    (cubic((1, 1, 0, 0)), "end0"),           # moves away from q
+    (cubic((-2, 1, 0, 0)), "end1"),          # moves towards q, stops short
+    (cubic((1, 1, -1, 0), (0, 0, 0, 0)), "ends"),  # x = 1 + u - u^2 > 0 peaks inside: + to -
+    (FLAT, "isou"),                          # last coefficients exactly 0: uncertain at the end
+    (cubic((-0.4, 1, 0, 0)), "seed"),        # b2 exactly 0 between - and +: one change either way
+], ids=["seed", "end0", "end1", "ends", "flat-end", "lone-zero"])
+def test_classification(hn, a, kind):
+    assert hn.hn_classify(fp(a)) == KINDS[kind]
+
+
+def test_classification_iso_certain(hn):
+    # a random cubic whose E has three certified sign changes
+    rng = np.random.default_rng(3)
+    for _ in range(20000):
+        a = rng.uniform(-1, 1, 12)
+        b = np.zeros(6, np.float32)
+        v = hn.hn_bernstein_f(fp(a), b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if v >= 2 and np.min(np.abs(b)) > 1e-2 * np.max(np.abs(b)):
+            assert hn.hn_classify(fp(a)) == KINDS["iso"]
+            return
+    pytest.fail("no cubic with certified changes found")
+
+
+@pytest.mark.parametrize("btol,unsure", [
+    ([0, 0, 0.2, 0, 0, 0], 0),    # b2 = -0.1 between -0.3 and +0.1: the count cannot change
+    ([0, 0.4, 0, 0, 0, 0], 1),    # b1 = -0.3 between -0.5 and -0.1: could add two changes
+    ([0, 0, 0.2, 0.2, 0, 0], 1),  # a run of two
+    ([0.6, 0, 0, 0, 0, 0], 1),    # at an end
+])
+def test_uncertainty_only_where_it_matters(hn, btol, unsure):
+    a = cubic((-0.5, 1, 0, 0))    # b = (-0.5, -0.3, -0.1, 0.1, 0.3, 0.5), one change
+    _, unc = isolate32(hn, a, np.array(btol, np.float32))
+    assert unc == unsure

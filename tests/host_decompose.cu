@@ -1,0 +1,67 @@
+// Host build of the decomposition walk of one surface span pair (the code the
+// GPU runs, csrc/decompose.cu), for CPU tests of its bit-exact agreement
+// with the oracle.  The block-shared coefficient tables are filled here by
+// the same FP64 operations as on the device.
+#include "../paper_2504_11498_gb300/csrc/decompose.cu"
+
+namespace bspl {
+namespace {
+template <int MP>
+void host_fill_coef(RedCoef<MP>& cf)
+{
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) cf.g33[i][j] = gram_d(3, 3, i, j);
+    for (int p = 0; p <= MP; ++p)
+        for (int r = 0; r < 2; ++r)
+            for (int j = 0; j <= MP; ++j) cf.gp[p][r][j] = j <= p ? gram_d(3, p, 1 + r, j) : 0.0;
+    for (int p = 0; p <= MP; ++p) cf.ap[p] = fdiv((double)p, 3.0);
+    for (int n = 0; n < MP; ++n)
+        for (int i = 0; i <= MP; ++i) {
+            cf.ea[n][i] = fdiv((double)i, (double)(n + 1));
+            cf.eb[n][i] = fdiv((double)(n + 1 - i), (double)(n + 1));
+        }
+}
+}  // namespace
+}  // namespace bspl
+
+using namespace bspl;
+
+extern "C" {
+
+// box diagonal of a control net, as the device computes it
+double hd_box_diag(const double* P, int64_t np) { return box_diag_d(P, np); }
+
+// leaves of span pair (qu, qv) of a surface with degrees (pu, pv), knots U, V
+// and net P [n_u][n_v][3]; writes up to cap leaves (ctrl [48], prange [4])
+// and returns their count (the count is returned even when above cap)
+int64_t hd_surface_span(int pu, int pv, const double* U, int qu, const double* V, int qv, const double* P, int nv,
+                        double tol_rel, double diag, double* ctrl, double* prange, int64_t cap, int* err)
+{
+    static SurfCoef cf;
+    static bool filled = false;
+    if (!filled) {
+        host_fill_coef<kMaxSurfDegree>(cf);
+        filled = true;
+    }
+    const double thr = tol_rel * diag, thr2 = thr * thr;  // the device computes the same two IEEE products
+    *err = 0;
+    SurfLeafOut none{};
+    const int64_t n = walk_span_surface<false>(pu, pv, U, qu, V, qv, P, nv, thr2, 0, 0, none, err, cf);
+    if (n > cap) return n;
+    double* rec64 = new double[(size_t)BSPL_SREC64 * (size_t)(n > 0 ? n : 1)];
+    float* rec32 = new float[(size_t)BSPL_SREC32 * (size_t)(n > 0 ? n : 1)];
+    int64_t* span = new int64_t[(size_t)(n > 0 ? n : 1)];
+    double* pbox = new double[4 * (size_t)(n > 0 ? n : 1)];
+    double* net = new double[BSPL_SPAN_NET];
+    float* net32 = new float[BSPL_SPAN_NET];
+    SurfLeafOut out{ ctrl, prange, span, pbox, rec64, rec32, net, net32 };
+    walk_span_surface<true>(pu, pv, U, qu, V, qv, P, nv, thr2, 0, 0, out, err, cf);
+    delete[] rec64;
+    delete[] rec32;
+    delete[] span;
+    delete[] pbox;
+    delete[] net;
+    delete[] net32;
+    return n;
+}
+}

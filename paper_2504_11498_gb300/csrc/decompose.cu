@@ -570,43 +570,13 @@ __host__ __device__ double surf_bound2(int pu, int pv, const double* Q, const do
     return b;
 }
 
-// squared certified deviation of the reduction along one direction alone:
-// every column (dir 0, along u) or row (dir 1, along v) of the net reduced to
-// a cubic and bounded against itself (degree > 3 in that direction)
-__host__ __device__ double surf_dir_dev2(int pu, int pv, const double* Q, int dir, const SurfCoef& cf)
-{
-    double b = 0.0;
-    if (dir == 0) {
-        for (int j = 0; j <= pv; ++j) {
-            double col[kSN * 3], r[12];
-            for (int i = 0; i <= pu; ++i)
-                for (int c = 0; c < 3; ++c) col[3 * i + c] = Q[(i * kSN + j) * 3 + c];
-            to_cubic<kMaxSurfDegree>(pu, col, 3, r, 3, cf);
-            const double e = bound2_curve<kMaxSurfDegree>(pu, col, 3, r, 3, cf);
-            if (e > b) b = e;
-        }
-    } else {
-        for (int i = 0; i <= pu; ++i) {
-            double row[kSN * 3], r[12];
-            for (int j = 0; j <= pv; ++j)
-                for (int c = 0; c < 3; ++c) row[3 * j + c] = Q[(i * kSN + j) * 3 + c];
-            to_cubic<kMaxSurfDegree>(pv, row, 3, r, 3, cf);
-            const double e = bound2_curve<kMaxSurfDegree>(pv, row, 3, r, 3, cf);
-            if (e > b) b = e;
-        }
-    }
-    return b;
-}
-
-// split direction of a net that failed the bound: the reduced direction when
-// only one is reduced, else the one whose reduction alone deviates more
-// (ties -> u).  (The parameter lengths of a span pair can differ by orders
-// of magnitude from where its deviation lies.)
-__host__ __device__ int surf_split_dir(int pu, int pv, const double* Q, const SurfCoef& cf)
+// split direction: the reduced direction when only one is reduced, else the
+// longer parameter side (ties -> u)
+__host__ __device__ int surf_split_dir(int pu, int pv, double du, double dv, int Lu, int Lv)
 {
     if (pu > 3 && pv <= 3) return 0;
     if (pv > 3 && pu <= 3) return 1;
-    return surf_dir_dev2(pu, pv, Q, 0, cf) >= surf_dir_dev2(pu, pv, Q, 1, cf) ? 0 : 1;
+    return ldexp(du, -Lu) >= ldexp(dv, -Lv) ? 0 : 1;
 }
 
 __host__ __device__ void surf_halve_keep(int pu, int pv, double* Q, int dir, int side)
@@ -685,9 +655,9 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
             dst32[i] = (float)W[i];
         }
     }
+    double du = fsub(U[qu + 1], U[qu]), dv = fsub(V[qv + 1], V[qv]);
     int L = 0;
     uint64_t bits = 0;  // path bits, most recent in bit 0
-    uint64_t dirs = 0;  // bit l: the direction the ancestor at depth l was split in
     int64_t count = 0;
     for (;;) {
         // replay the path from the root
@@ -696,7 +666,7 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
         int64_t ku = 0, kv = 0;
         for (int l = 0; l < L; ++l) {
             int side = (int)((bits >> (L - 1 - l)) & 1);
-            int dir = (int)((dirs >> l) & 1);
+            int dir = surf_split_dir(pu, pv, du, dv, Lu, Lv);
             surf_halve_keep(pu, pv, Q, dir, side);
             if (dir == 0) {
                 ++Lu;
@@ -755,8 +725,6 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
             if (L == 0) break;
             bits |= 1;
         } else {
-            const int dir = surf_split_dir(pu, pv, Q, cf);
-            dirs = (dirs & ~(1ull << L)) | ((uint64_t)dir << L);
             ++L;
             bits <<= 1;
         }

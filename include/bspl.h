@@ -278,8 +278,12 @@ bspl_status bspl_invert_surfaces(const bspl_segments* segs, int64_t n_q, const i
  * BSPL_NOALLOC_SCRATCH_BYTES array inside the library, which every GPU that
  * loads the library keeps reserved until the process exits.
  *
- * Limits: n_q <= BSPL_NOALLOC_MAX_QUERIES and segs->n <= BSPL_NOALLOC_MAX_SPLINES;
- * larger calls return BSPL_ENOSPACE before anything is launched.
+ * Limits: n_q <= BSPL_NOALLOC_MAX_QUERIES and segs->n <= BSPL_NOALLOC_MAX_SPLINES.
+ * With opt->prec = BSPL_LEARNED_MIXED the candidate-pair buffer (about 1 KB
+ * per query) shares the array, which lowers the limit to about 7,500 queries
+ * (exactly: bspl_workspace_bytes(BSPL_OP_QUERY_CURVES_LEARNED, segs->n, 0, 0,
+ * n_q) must not exceed BSPL_NOALLOC_SCRATCH_BYTES).  Larger calls return
+ * BSPL_ENOSPACE before anything is launched.
  * The first call on a device looks up the array's device address for that
  * device (with that device current); make that first call before any stream
  * capture.  All calls share the one array: its contents are those of the

@@ -778,13 +778,41 @@ static double surf_bound2(int pu, int pv, const double* Q, const double* R)
     return b;
 }
 
+/* squared certified deviation of the reduction along one direction alone:
+ * every column (dir 0, along u) or row (dir 1, along v) of the net reduced
+ * to a cubic and bounded against itself (degree > 3 in that direction) */
+static double surf_dir_dev2(int pu, int pv, const double* Q, int dir)
+{
+    double b = 0.0;
+    if (dir == 0) {
+        for (int j = 0; j <= pv; ++j) {
+            double col[SNP * 3], r[12];
+            for (int i = 0; i <= pu; ++i)
+                for (int c = 0; c < 3; ++c) col[3 * i + c] = Q[NETI(i, j) + c];
+            to_cubic(pu, col, 3, r, 3);
+            double e = bound2_curve(pu, col, 3, r, 3);
+            if (e > b) b = e;
+        }
+    } else {
+        for (int i = 0; i <= pu; ++i) {
+            double row[SNP * 3], r[12];
+            for (int j = 0; j <= pv; ++j)
+                for (int c = 0; c < 3; ++c) row[3 * j + c] = Q[NETI(i, j) + c];
+            to_cubic(pv, row, 3, r, 3);
+            double e = bound2_curve(pv, row, 3, r, 3);
+            if (e > b) b = e;
+        }
+    }
+    return b;
+}
+
 /* split direction: the reduced direction if only one is reduced, else the
- * longer parameter side (ties -> u) */
-static int surf_split_dir(int pu, int pv, double du, double dv, int Lu, int Lv)
+ * one whose reduction alone deviates more (ties -> u) */
+static int surf_split_dir(int pu, int pv, const double* Q)
 {
     if (pu > 3 && pv <= 3) return 0;
     if (pv > 3 && pu <= 3) return 1;
-    return ldexp(du, -Lu) >= ldexp(dv, -Lv) ? 0 : 1;
+    return surf_dir_dev2(pu, pv, Q, 0) >= surf_dir_dev2(pu, pv, Q, 1) ? 0 : 1;
 }
 
 static void surf_node(surf_ctx* X, const double* Q, int Lu, int64_t ku, int Lv, int64_t kv)
@@ -808,7 +836,7 @@ static void surf_node(surf_ctx* X, const double* Q, int Lu, int64_t ku, int Lv, 
         if (Lu + Lv > X->maxdepth) X->maxdepth = Lu + Lv;
         return;
     }
-    int dir = surf_split_dir(pu, pv, X->u1 - X->u0, X->v1 - X->v0, Lu, Lv);
+    int dir = surf_split_dir(pu, pv, Q);
     double* A = (double*)malloc(sizeof(double) * NETN);
     double* B = (double*)malloc(sizeof(double) * NETN);
     if (dir == 0) {

@@ -258,8 +258,13 @@ def bspl_decompose(is_surface, splines, tol_rel, seg_struct, ws, stream=None):
     return rc, tot.value
 
 
-def decompose(splines, tol_rel: float, is_surface: bool | None = None, stream=None) -> Segments:
-    """Two-phase decomposition: count, allocate, fill."""
+def decompose(splines, tol_rel: float, is_surface: bool | None = None, stream=None,
+              allow_capped: bool = False) -> Segments:
+    """Two-phase decomposition: count, allocate, fill.
+
+    BSPL_ENOTCONV (a span or span pair reached the subdivision depth cap or
+    its piece cap, so some accepted pieces exceed the tolerance) raises
+    BsplError unless ``allow_capped``; the status is kept in ``segs.status``."""
     if is_surface is None:
         is_surface = isinstance(splines, DeviceSurfaces)
     op = OP_DECOMPOSE_SURFACES if is_surface else OP_DECOMPOSE_CURVES
@@ -267,10 +272,11 @@ def decompose(splines, tol_rel: float, is_surface: bool | None = None, stream=No
     probe = Segments(splines, is_surface, 0, splines.cp_off.device)
     probe.c.ctrl = None
     rc, total = bspl_decompose(is_surface, splines, tol_rel, probe.c, ws, stream)
-    _check(rc, "bspl_decompose(count)", (OK, ENOTCONV))
+    ok = (OK, ENOTCONV) if allow_capped else (OK,)
+    _check(rc, "bspl_decompose(count)", ok)
     segs = Segments(splines, is_surface, total, splines.cp_off.device)
     rc, total2 = bspl_decompose(is_surface, splines, tol_rel, segs.c, ws, stream)
-    _check(rc, "bspl_decompose(fill)", (OK, ENOTCONV))
+    _check(rc, "bspl_decompose(fill)", ok)
     assert total2 == total
     segs.total = total
     segs.tol_rel = float(tol_rel)
@@ -357,6 +363,7 @@ def bspl_invert_surfaces(segs, q_surf, q_xyz, opts=None, bufs=None, stream=None)
 
 NOALLOC_MAX_QUERIES = 1 << 20
 NOALLOC_MAX_SPLINES = 1 << 18
+SCRATCH_BYTES = 8 << 20  # BSPL_NOALLOC_SCRATCH_BYTES
 
 
 def bspl_project_curves_noalloc(segs, q_curve, q_xyz, opts=None, out=None, stream=None):

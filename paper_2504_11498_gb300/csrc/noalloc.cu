@@ -42,6 +42,10 @@ extern "C" bspl_status bspl_project_curves_noalloc(const bspl_segments* segs, in
     if (!segs || n_q < 0) return BSPL_EINVAL;
     if (n_q > BSPL_NOALLOC_MAX_QUERIES || segs->n > BSPL_NOALLOC_MAX_SPLINES) return BSPL_ENOSPACE;
     if (bspl::query_ws_bytes(segs->n, n_q) > kScratchBytes) return BSPL_ENOSPACE;
+    // the learned precision adds its candidate-pair buffer (about 1 KB per
+    // query), so it fits far fewer queries into the same array
+    if (opt && opt->prec == BSPL_LEARNED_MIXED && bspl::learned_ws_bytes(segs->n, n_q) > kScratchBytes)
+        return BSPL_ENOSPACE;
     void* ws = nullptr;
     bspl_status st = scratch_address(&ws);
     if (st != BSPL_OK) return st;

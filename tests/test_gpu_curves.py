@@ -302,8 +302,6 @@ def test_near_cusp_segment():
     assert miss.mean() < 0.02
 
 
-@pytest.mark.xfail(strict=False, reason="fix not yet run on a GPU: the FP32 isolation skipped a crossing whose "
-                   "end coefficient rounded to exactly 0 and the FP64 steps accepted the end without a step")
 def test_learned_single_query_regression():
     """One projection query of the 16M-query workload on the 4,096-curve set
     where the learned path returned the local minimum of another segment

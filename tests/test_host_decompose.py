@@ -1,7 +1,8 @@
 """CPU check of the surface decomposition the GPU runs (csrc/decompose.cu,
 compiled for the host span pair by span pair) against the oracle, bit for
-bit: patch counts, bicubic nets and parameter boxes, on surfaces of the
-random-surface recipe."""
+bit: patch counts, bicubic nets and parameter boxes.  Surfaces of the
+random-surface recipe, including nets whose span pairs are far longer in
+one parameter than the other (where the split direction matters)."""
 import ctypes
 import os
 import shutil
@@ -81,3 +82,17 @@ def test_surface_walk_bit_exact_with_oracle(hd, tol):
     assert np.array_equal(off, ref.seg_off)
     assert np.array_equal(pr, ref.prange)
     assert np.array_equal(ctrl.reshape(ref.ctrl.shape), ref.ctrl)
+
+
+def test_anisotropic_span_pairs_stay_small(hd):
+    """Surfaces of the 1,024-surface set with span pairs whose parameter
+    lengths differ by four orders of magnitude: every span pair meets the
+    tolerance well before the leaf cap, and host walk and oracle agree."""
+    ss, _ = synth.surface_set(seed=3, n_surf=1024, n_proj=1, n_inv=1)
+    sub = ss.subset([557, 81])
+    off, ctrl, pr = host_decompose(hd, sub, 1e-4)
+    ref = O.decompose_surfaces(sub, 1e-4)
+    assert ref.status == 0
+    assert np.array_equal(off, ref.seg_off) and np.array_equal(pr, ref.prange)
+    assert np.array_equal(ctrl.reshape(ref.ctrl.shape), ref.ctrl)
+    assert off[-1] < 20000

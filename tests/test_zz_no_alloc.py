@@ -53,3 +53,37 @@ def test_noalloc_rejects_batches_over_its_limit():
     q = torch.zeros((n, 3), dtype=torch.float64, device=dev)
     with pytest.raises(bspl.BsplError, match="ENOSPACE"):
         bspl.bspl_project_curves_noalloc(segs, qc, q)
+
+
+def test_noalloc_learned_precision_within_and_over_its_limit():
+    """The learned precision also keeps its candidate-pair buffer in the
+    fixed array, about 1 KB per query: a batch that fits answers like the
+    regular entry point (two calls in a row), a larger one is refused with
+    ENOSPACE rather than mistaken for a caller error."""
+    from oracle import oracle as O
+    from paper_2504_11498_gb300 import build, bspl, synth
+    build.build()
+    dev = "cuda"
+    cs, qs = synth.curve_set(seed=7, n_curves=512, n_proj=40_000, n_inv=1)
+    segs = bspl.decompose(bspl.DeviceCurves(cs, dev), 1e-10)
+    limit = bspl.SCRATCH_BYTES
+    n_fit = 4000
+    assert bspl.workspace_bytes(bspl.OP_QUERY_CURVES_LEARNED, segs.n, 0, 0, n_fit) <= limit
+    assert bspl.workspace_bytes(bspl.OP_QUERY_CURVES_LEARNED, segs.n, 0, 0, 40_000) > limit
+    mlp = bspl.Mlp(synth.mlp_init(7), dev)
+    opts = bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp)
+    qc = torch.as_tensor(qs.proj_curve[:n_fit], device=dev)
+    q = torch.as_tensor(qs.proj_xyz[:n_fit], device=dev)
+    diag = O.curve_diag(cs)[qs.proj_curve[:n_fit]]
+    ref = bspl.bspl_project_curves(segs, qc, q, opts)
+    torch.cuda.synchronize()
+    d_ref, st_ref = ref.dist.cpu().numpy().copy(), ref.status.cpu().numpy().copy()
+    for call in range(2):
+        r = bspl.bspl_project_curves_noalloc(segs, qc, q, opts)
+        torch.cuda.synchronize()
+        assert np.all(np.abs(r.dist.cpu().numpy() - d_ref) <= 1e-12 * diag), call
+        assert np.array_equal(r.status.cpu().numpy(), st_ref)
+    qc = torch.as_tensor(qs.proj_curve, device=dev)
+    q = torch.as_tensor(qs.proj_xyz, device=dev)
+    with pytest.raises(bspl.BsplError, match="ENOSPACE"):
+        bspl.bspl_project_curves_noalloc(segs, qc, q, opts)

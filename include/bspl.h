@@ -98,7 +98,13 @@ typedef struct {
 #define BSPL_CREC64 18       /* curve FP64: lo[3] hi[3] a0[3] a1[3] a2[3] a3[3] (power basis in u) */
 #define BSPL_CREC32 24       /* curve FP32: same layout (box rounded outward), then a0 - (float)a0 [3] and 3 pad */
 #define BSPL_SREC64 54       /* patch FP64: lo[3] hi[3] a[4][4][3] (power basis in u,v) */
-#define BSPL_SREC32 56       /* patch FP32: same layout + span-pair degrees (pu, pv) */
+#define BSPL_SREC32 72       /* patch FP32: same layout, then [54] pu, [55] pv (span-pair
+                                degrees), [56..60] bounds of the ORIGINAL piece's
+                                |S_s|, |S_t|, |S_ss|, |S_st|, |S_tt| over the patch in
+                                its own parameters (s, t) in [0,1]^2, [61] edge flags
+                                (bit 0: s=0, 1: s=1, 2: t=0, 3: t=1 set where the
+                                surface is C1 across that edge), [62..65] bounds of
+                                |S_sss|, |S_sst|, |S_stt|, |S_ttt|, [66..71] pad */
 #define BSPL_GREC64 12       /* group FP64: lo[3] hi[3] ref[3] pad[3] */
 #define BSPL_GREC32 12       /* group FP32: same, box rounded outward */
 
@@ -121,7 +127,13 @@ typedef struct {
  *                        ORIGINAL span-pair patch (degree <= 7 per direction in
  *                        the query path), indexed by slot, used for the final
  *                        FP64 Newton steps on the original surface;
- *   span_net32 [n_cp_total][BSPL_SPAN_NET]  the same in FP32 (mixed precision).
+ *   span_net32 [n_cp_total][BSPL_SPAN_NET]  the same in FP32 (mixed precision);
+ *   patch_net32 [cap][BSPL_SPAN_NET]  the ORIGINAL piece over each patch's own
+ *                        parameter box, in the patch's power basis (s, t in
+ *                        [0,1]^2), FP32, same layout as span_net; its constant
+ *                        term is the patch corner, whose FP64 value is
+ *                        rec64[6..8].  Coefficients of the patch's size keep
+ *                        the FP32 search accurate on small patches.
  */
 #define BSPL_SPAN_NET (8 * 8 * 3)
 typedef struct {
@@ -144,6 +156,7 @@ typedef struct {
     float* span_net32;
     int64_t n_cp_total;  /* in: cp_off[n] of the decomposed set (sizes the slot arrays) */
     double tol_rel;      /* out: tolerance the tables were built with */
+    float* patch_net32;  /* surfaces: [capacity][BSPL_SPAN_NET], see above */
 } bspl_segments;
 
 /* Query options.  Zero fields take the defaults given. */
@@ -173,6 +186,10 @@ typedef struct {
                             them on the stream at its stage boundaries (start,
                             sort, cull, seed, FP32, FP64, select, leftovers);
                             profiling only                                */
+    int32_t cert_depth;  /* surfaces: refinement levels of the certification
+                            search on the original surface (default 2, at most
+                            4); negative: no certification (grid-seeded search
+                            only, for timing comparisons)                 */
 } bspl_options;
 #define BSPL_NSTAGE_EVENTS 8
 
@@ -187,7 +204,10 @@ typedef struct {
 #define BSPL_CNT_NEWTON32_ITERS 7 /* FP32 Newton iterations */
 #define BSPL_CNT_NEWTON64_ITERS 8 /* FP64 Newton iterations */
 #define BSPL_CNT_ISO_PAIRS 9   /* learned path: pairs sent to certified root isolation */
-#define BSPL_NCOUNTERS 10
+#define BSPL_CNT_CERT_CELLS 10 /* surfaces: cells evaluated by the certification search */
+#define BSPL_CNT_CERT_LEAVES 11 /* surfaces: certification cells handed to Newton */
+#define BSPL_CNT_CERT_OVERFLOW 12 /* surfaces: cells sent to Newton early (stack full) */
+#define BSPL_NCOUNTERS 13
 
 /* workspace sizes: op is one of */
 #define BSPL_OP_DECOMPOSE_CURVES 1

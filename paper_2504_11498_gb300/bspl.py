@@ -22,16 +22,16 @@ OK, EINVAL, ENOSPACE, ECUDA, ENOTCONV, ETIMEOUT = 0, 1, 2, 3, 4, 5
 FP64, MIXED, LEARNED_MIXED = 0, 1, 2
 Q_CONVERGED, Q_FALLBACK, Q_AT_END, Q_NONCONV, Q_OFF_CURVE, Q_INVALID = 1, 2, 4, 8, 16, 32
 GROUP = 32
-CREC64, CREC32, SREC64, SREC32, GREC64, GREC32 = 18, 24, 54, 56, 12, 12
+CREC64, CREC32, SREC64, SREC32, GREC64, GREC32 = 18, 24, 54, 72, 12, 12
 SPAN_NET = 8 * 8 * 3
 OP_DECOMPOSE_CURVES, OP_DECOMPOSE_SURFACES, OP_QUERY_CURVES, OP_QUERY_SURFACES = 1, 2, 3, 4
 OP_QUERY_CURVES_LEARNED, OP_MLP_TRAIN = 5, 6
 # learned seed (include/bspl_mlp.h)
 MLP_IN, MLP_HIDDEN, MLP_NPARAM, MLP_NBF16, MLP_MAX_BATCH = 16, 128, 35332, 2048 + 4 * 16384 + 128, 65536
 MLP_OFF = {"W1": 0, "b1": 2048, "W2": 2176, "b2": 18560, "W3": 18688, "b3": 35072, "w4": 35200, "b4": 35328}
-NCOUNTERS = 10
+NCOUNTERS = 13
 COUNTER_NAMES = ["queries", "seg_tested", "grp_tested", "candidates", "newton", "fallback", "nonconv",
-                 "newton32_iters", "newton64_iters", "iso_pairs"]
+                 "newton32_iters", "newton64_iters", "iso_pairs", "cert_cells", "cert_leaves", "cert_overflow"]
 
 
 class BsplError(RuntimeError):
@@ -55,14 +55,14 @@ class bspl_segments(C.Structure):
                 ("rec64", C.c_void_p), ("rec32", C.c_void_p), ("grp_off", C.c_void_p), ("grp64", C.c_void_p),
                 ("grp32", C.c_void_p), ("patch_span", C.c_void_p), ("patch_box", C.c_void_p),
                 ("span_net", C.c_void_p), ("span_net32", C.c_void_p), ("n_cp_total", C.c_int64),
-                ("tol_rel", C.c_double)]
+                ("tol_rel", C.c_double), ("patch_net32", C.c_void_p)]
 
 
 class bspl_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("samples", C.c_int32), ("newton_max", C.c_int32), ("fp32_steps", C.c_int32),
                 ("sort_queries", C.c_int32), ("occupancy", C.c_int32), ("pairs_per_query", C.c_int32),
                 ("mlp", C.c_void_p),
-                ("counters", C.c_void_p), ("stage_events", C.c_void_p)]
+                ("counters", C.c_void_p), ("stage_events", C.c_void_p), ("cert_depth", C.c_int32)]
 
 
 NSTAGE_EVENTS = 8
@@ -215,12 +215,13 @@ class Segments:
             self.patch_box = z((cap, 4), f64)
             self.span_net = z((splines.n_cp_total, SPAN_NET), f64)
             self.span_net32 = z((splines.n_cp_total, SPAN_NET), f32)
+            self.patch_net32 = z((cap, SPAN_NET), f32)
         else:
             self.ctrl = z((cap, 4, 3), f64)
             self.prange = z((cap, 2), f64)
             self.rec64 = z((cap, CREC64), f64)
             self.rec32 = z((cap, CREC32), f32)
-            self.patch_span = self.patch_box = self.span_net = self.span_net32 = None
+            self.patch_span = self.patch_box = self.span_net = self.span_net32 = self.patch_net32 = None
         self.grp64 = z((self.grp_capacity, GREC64), f64)
         self.grp32 = z((self.grp_capacity, GREC32), f32)
         self.n_cp_total = splines.n_cp_total
@@ -234,7 +235,7 @@ class Segments:
                              _ptr(self.rec32), _ptr(self.grp_off), _ptr(self.grp64), _ptr(self.grp32),
                              _ptr(self.patch_span), _ptr(self.patch_box), _ptr(self.span_net), _ptr(self.span_net32),
                              self.n_cp_total,
-                             self.tol_rel)
+                             self.tol_rel, _ptr(self.patch_net32))
 
     def view(self):
         """Host copies (seg_off, ctrl, prange) trimmed to the segment count."""
@@ -295,7 +296,7 @@ class QueryResult:
 
 
 def make_options(prec=FP64, samples=0, newton_max=0, fp32_steps=0, sort_queries=1, counters=None, mlp=None,
-                 occupancy=0, stage_events=None, pairs_per_query=0):
+                 occupancy=0, stage_events=None, pairs_per_query=0, cert_depth=0):
     """mlp: an ``Mlp`` (learned seed for prec=LEARNED_MIXED) or None;
     stage_events: NSTAGE_EVENTS torch.cuda.Event(enable_timing=True) that the
     learned path records at its stage boundaries (profiling)."""
@@ -310,7 +311,7 @@ def make_options(prec=FP64, samples=0, newton_max=0, fp32_steps=0, sort_queries=
     o = bspl_options(int(prec), int(samples), int(newton_max), int(fp32_steps), int(sort_queries), int(occupancy),
                      int(pairs_per_query), C.cast(C.pointer(mlp.c), C.c_void_p) if mlp is not None else C.c_void_p(0),
                      _ptr(counters) if counters is not None else None,
-                     C.cast(ev, C.c_void_p) if ev is not None else None)
+                     C.cast(ev, C.c_void_p) if ev is not None else None, int(cert_depth))
     o._keep = (mlp, ev)  # what the pointers refer to stays alive with the options
     return o
 

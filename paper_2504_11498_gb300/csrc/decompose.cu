@@ -570,13 +570,43 @@ __host__ __device__ double surf_bound2(int pu, int pv, const double* Q, const do
     return b;
 }
 
-// split direction: the reduced direction when only one is reduced, else the
-// longer parameter side (ties -> u)
-__host__ __device__ int surf_split_dir(int pu, int pv, double du, double dv, int Lu, int Lv)
+// squared certified deviation of the reduction along one direction alone:
+// every column (dir 0, along u) or row (dir 1, along v) of the net reduced to
+// a cubic and bounded against itself (degree > 3 in that direction)
+__host__ __device__ double surf_dir_dev2(int pu, int pv, const double* Q, int dir, const SurfCoef& cf)
+{
+    double b = 0.0;
+    if (dir == 0) {
+        for (int j = 0; j <= pv; ++j) {
+            double col[kSN * 3], r[12];
+            for (int i = 0; i <= pu; ++i)
+                for (int c = 0; c < 3; ++c) col[3 * i + c] = Q[(i * kSN + j) * 3 + c];
+            to_cubic<kMaxSurfDegree>(pu, col, 3, r, 3, cf);
+            const double e = bound2_curve<kMaxSurfDegree>(pu, col, 3, r, 3, cf);
+            if (e > b) b = e;
+        }
+    } else {
+        for (int i = 0; i <= pu; ++i) {
+            double row[kSN * 3], r[12];
+            for (int j = 0; j <= pv; ++j)
+                for (int c = 0; c < 3; ++c) row[3 * j + c] = Q[(i * kSN + j) * 3 + c];
+            to_cubic<kMaxSurfDegree>(pv, row, 3, r, 3, cf);
+            const double e = bound2_curve<kMaxSurfDegree>(pv, row, 3, r, 3, cf);
+            if (e > b) b = e;
+        }
+    }
+    return b;
+}
+
+// split direction of a net that failed the bound: the reduced direction when
+// only one is reduced, else the one whose reduction alone deviates more
+// (ties -> u).  (The parameter lengths of a span pair can differ by orders
+// of magnitude from where its deviation lies.)
+__host__ __device__ int surf_split_dir(int pu, int pv, const double* Q, const SurfCoef& cf)
 {
     if (pu > 3 && pv <= 3) return 0;
     if (pv > 3 && pu <= 3) return 1;
-    return ldexp(du, -Lu) >= ldexp(dv, -Lv) ? 0 : 1;
+    return surf_dir_dev2(pu, pv, Q, 0, cf) >= surf_dir_dev2(pu, pv, Q, 1, cf) ? 0 : 1;
 }
 
 __host__ __device__ void surf_halve_keep(int pu, int pv, double* Q, int dir, int side)
@@ -615,11 +645,96 @@ struct SurfLeafOut {
     float* rec32;      // the degrees (pu, pv) go to the two pad entries
     double* span_net;  // original span-pair piece, power basis [8][8][3]
     float* span_net32; // the same in FP32
+    float* patch_net32; // original piece over each patch, the patch's own power basis, FP32
 };
 
+// x rounded up to FP32 (a bound must not shrink when it is stored)
+__host__ __device__ inline float up_f(double x)
+{
+    float f = (float)x;
+    if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// Bounds of the ORIGINAL piece's derivatives over its patch box, in the
+// patch's own parameters (s, t) in [0,1]^2, from the Bernstein net Q of
+// degree (pu, pv) that the walk holds for the patch: a derivative of a
+// Bezier patch is a Bezier patch whose control points are scaled forward
+// differences of Q, and the convex-hull property bounds its length by the
+// longest of them.  out[0..4]: |S_s|, |S_t|, |S_ss|, |S_st|, |S_tt|;
+// out[6..9]: |S_sss|, |S_sst|, |S_stt|, |S_ttt| (rounded up; out[5] is
+// left to the caller).
+__host__ __device__ inline void patch_bounds(int pu, int pv, const double* Q, float* out)
+{
+    double m[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
+    // order-(i, j) forward difference of Q at (a, b), one coordinate
+    auto diff = [&](int a, int b, int i, int j, int c) {
+        const double bi[4][4] = { { 1, 0, 0, 0 }, { -1, 1, 0, 0 }, { 1, -2, 1, 0 }, { -1, 3, -3, 1 } };
+        double acc = 0.0;
+        for (int x = 0; x <= i; ++x)
+            for (int y = 0; y <= j; ++y) acc += bi[i][x] * bi[j][y] * Q[((a + x) * kSN + (b + y)) * 3 + c];
+        return acc;
+    };
+    // falling factorials p!/(p-k)!
+    auto ff = [](int p, int k) {
+        double r = 1.0;
+        for (int i = 0; i < k; ++i) r *= (double)(p - i);
+        return r;
+    };
+    const int ord[9][2] = { { 1, 0 }, { 0, 1 }, { 2, 0 }, { 1, 1 }, { 0, 2 }, { 0, 0 }, { 3, 0 }, { 2, 1 }, { 1, 2 } };
+    for (int k = 0; k < 10; ++k) {
+        if (k == 5) continue;
+        const int i = k < 9 ? ord[k][0] : 0, j = k < 9 ? ord[k][1] : 3;
+        if (i > pu || j > pv) continue;  // that derivative vanishes
+        const double f = ff(pu, i) * ff(pv, j);
+        double mk = 0.0;
+        for (int a = 0; a + i <= pu; ++a)
+            for (int b = 0; b + j <= pv; ++b) {
+                double w2 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    const double d = f * diff(a, b, i, j, c);
+                    w2 += d * d;
+                }
+                mk = fmax(mk, sqrt(w2));
+            }
+        if (k < 9) m[k] = mk;
+        else m[5] = mk;  // k = 9: (0, 3) stored in m[5] temporarily
+    }
+    for (int k = 0; k < 5; ++k) out[k] = up_f(m[k] * (1.0 + 1e-12));
+    out[6] = up_f(m[6] * (1.0 + 1e-12));
+    out[7] = up_f(m[7] * (1.0 + 1e-12));
+    out[8] = up_f(m[8] * (1.0 + 1e-12));
+    out[9] = up_f(m[5] * (1.0 + 1e-12));
+}
+
+// Which edges of a patch the distance function is continuously
+// differentiable across (bit 0: s = 0, 1: s = 1, 2: t = 0, 3: t = 1).  An
+// edge inside its span pair always is; an edge on a knot line is when that
+// knot is inside the parameter domain [K[p], K[n]] (n control points, n + p
+// + 1 knots) and its multiplicity is below the degree p (the spline is C1 or
+// better there).  Span (p <= q <= n - 1, K[q] < K[q + 1]).
+__host__ __device__ inline bool knot_line_smooth(const double* K, int p, int n, double x)
+{
+    if (!(x > K[p] && x < K[n])) return false;
+    int mult = 0;
+    for (int k = 0; k <= n + p; ++k) mult += K[k] == x ? 1 : 0;
+    return mult < p;
+}
+
+__host__ __device__ inline int patch_edge_flags(int pu, int pv, const double* U, int nu, int qu, const double* V,
+                                                int nv, int qv, const double* pb)
+{
+    int f = 0;
+    if (pb[0] > 0.0 || knot_line_smooth(U, pu, nu, U[qu])) f |= 1;
+    if (pb[1] < 1.0 || knot_line_smooth(U, pu, nu, U[qu + 1])) f |= 2;
+    if (pb[2] > 0.0 || knot_line_smooth(V, pv, nv, V[qv])) f |= 4;
+    if (pb[3] < 1.0 || knot_line_smooth(V, pv, nv, V[qv + 1])) f |= 8;
+    return f;
+}
+
 template <bool FILL>
-__host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, int qu, const double* V, int qv,
-                                     const double* P, int nv, double thr2, int64_t slot, int64_t first,
+__host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, int nu, int qu, const double* V,
+                                     int qv, const double* P, int nv, double thr2, int64_t slot, int64_t first,
                                      SurfLeafOut out, int* err, const SurfCoef& cf)
 {
     double root[kSN * kSN * 3], Q[kSN * kSN * 3];
@@ -655,9 +770,9 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
             dst32[i] = (float)W[i];
         }
     }
-    double du = fsub(U[qu + 1], U[qu]), dv = fsub(V[qv + 1], V[qv]);
     int L = 0;
     uint64_t bits = 0;  // path bits, most recent in bit 0
+    uint64_t dirs = 0;  // bit l: the direction the ancestor at depth l was split in
     int64_t count = 0;
     for (;;) {
         // replay the path from the root
@@ -666,7 +781,7 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
         int64_t ku = 0, kv = 0;
         for (int l = 0; l < L; ++l) {
             int side = (int)((bits >> (L - 1 - l)) & 1);
-            int dir = surf_split_dir(pu, pv, du, dv, Lu, Lv);
+            int dir = (int)((dirs >> l) & 1);
             surf_halve_keep(pu, pv, Q, dir, side);
             if (dir == 0) {
                 ++Lu;
@@ -716,6 +831,21 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
                 float* rf = out.rec32 + (int64_t)BSPL_SREC32 * o;
                 rf[54] = (float)pu;
                 rf[55] = (float)pv;
+                // the original piece over the patch in its own power basis
+                {
+                    double W[kSN * kSN * 3];
+                    for (int a = 0; a < kSN; ++a)
+                        for (int b = 0; b < kSN; ++b)
+                            for (int c = 0; c < 3; ++c)
+                                W[(a * kSN + b) * 3 + c] = (a <= pu && b <= pv) ? Q[(a * kSN + b) * 3 + c] : 0.0;
+                    for (int b = 0; b <= pv; ++b) bern_to_power(pu, W + 3 * b, 3 * kSN);
+                    for (int a = 0; a <= pu; ++a) bern_to_power(pv, W + 3 * kSN * a, 3);
+                    float* pn = out.patch_net32 + (int64_t)BSPL_SPAN_NET * o;
+                    for (int i = 0; i < kSN * kSN * 3; ++i) pn[i] = (float)W[i];
+                }
+                patch_bounds(pu, pv, Q, rf + 56);
+                rf[61] = (float)patch_edge_flags(pu, pv, U, nu, qu, V, nv, qv, pb);
+                for (int k = 66; k < BSPL_SREC32; ++k) rf[k] = 0.f;
             }
             ++count;
             while (L > 0 && (bits & 1)) {
@@ -725,6 +855,8 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
             if (L == 0) break;
             bits |= 1;
         } else {
+            const int dir = surf_split_dir(pu, pv, Q, cf);
+            dirs = (dirs & ~(1ull << L)) | ((uint64_t)dir << L);
             ++L;
             bits <<= 1;
         }
@@ -752,7 +884,7 @@ __global__ void k_walk_surfaces(bspl_surfaces S, const double* __restrict__ diag
     int64_t r = 0;
     if (qu <= nu - 1 && qv <= nv - 1 && U[qu] < U[qu + 1] && V[qv] < V[qv + 1]) {
         double thr = fmul(tol_rel, diag[s]);
-        r = walk_span_surface<FILL>(pu, pv, U, qu, V, qv, S.cps + 3 * S.cp_off[s], nv, fmul(thr, thr), slot,
+        r = walk_span_surface<FILL>(pu, pv, U, nu, qu, V, qv, S.cps + 3 * S.cp_off[s], nv, fmul(thr, thr), slot,
                                     FILL ? cnt[slot] : 0, out, err, cf);
     }
     if (!FILL) cnt[slot] = r;
@@ -988,7 +1120,9 @@ static bspl_status decompose_impl(int is_surface, const void* splines, double to
     if (h[0] > out->capacity || n_grp > out->grp_capacity) return BSPL_ENOSPACE;
     if (!out->prange || !out->rec64 || !out->rec32 || !out->grp_off || !out->grp64 || !out->grp32)
         return BSPL_EINVAL;
-    if (is_surface && (!out->patch_span || !out->patch_box || !out->span_net || !out->span_net32)) return BSPL_EINVAL;
+    if (is_surface && (!out->patch_span || !out->patch_box || !out->span_net || !out->span_net32 ||
+                       !out->patch_net32))
+        return BSPL_EINVAL;
     out->is_surface = is_surface;
     out->n = n;
     out->tol_rel = tol_rel;
@@ -996,7 +1130,7 @@ static bspl_status decompose_impl(int is_surface, const void* splines, double to
     // filling pass and query tables
     if (is_surface) {
         SurfLeafOut o{ out->ctrl, out->prange, out->patch_span, out->patch_box, out->rec64, out->rec32,
-                       out->span_net, out->span_net32 };
+                       out->span_net, out->span_net32, out->patch_net32 };
         launch1d(k_walk_surfaces<true>, n_cp, s, *SS, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
         launch1d(k_patch_records, h[0], s, (const double*)out->ctrl, h[0], out->rec64, out->rec32);
         launch1d(k_group_records, n_grp, s, (const int64_t*)out->seg_off, (const int64_t*)out->grp_off, n, n_grp,

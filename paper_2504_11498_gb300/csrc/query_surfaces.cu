@@ -48,6 +48,7 @@ struct SurfQ {
     const int64_t* patch_span;
     const double* span_net;
     const float* span_net32;
+    const float* patch_net32;
     const double* diag;
     double tol_rel;
     int64_t n, n_q;
@@ -60,6 +61,7 @@ struct SurfQ {
     int invert;
     int newton_max;
     int fp32_steps;
+    int cert_depth;  // refinement levels of the certification search; < 0: none
     unsigned long long* counters;
 };
 
@@ -116,8 +118,10 @@ struct SD {
     R S[3], Su[3], Sv[3], Suu[3], Suv[3], Svv[3];
 };
 
+// a00: the constant term (coordinate c at a00[c]); the local-frame callers
+// pass a(0,0) - q formed in FP64 there, the others a itself
 template <class R>
-__device__ __forceinline__ void eval_patch(const R* a, int du, int dv, int stride, R u, R v, SD<R>& o)
+__device__ __forceinline__ void eval_patch(const R* a, const R* a00, int du, int dv, int stride, R u, R v, SD<R>& o)
 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -126,7 +130,7 @@ __device__ __forceinline__ void eval_patch(const R* a, int du, int dv, int strid
             // row polynomial in v and its first two derivatives
             R p = 0, p1 = 0, p2 = 0;
             for (int j = dv; j >= 0; --j) {
-                R coef = a[(i * stride + j) * 3 + c];
+                R coef = (i | j) ? a[(i * stride + j) * 3 + c] : a00[c];
                 p2 = p2 * v + R(2) * p1;
                 p1 = p1 * v + p;
                 p = p * v + coef;
@@ -180,24 +184,31 @@ __device__ __forceinline__ R grad_hess(const SD<R>& o, R qx, R qy, R qz, GH<R>& 
     return D;
 }
 
-// projected Newton with active set and halving safeguard on [0,1]^2: the
-// Newton step where the Hessian is positive definite, the Gauss-Newton step
-// (J^T J, positive definite on a regular surface) elsewhere, so the step
-// does not depend on how the parameters are scaled.  A coordinate on a bound
-// whose gradient points outward is held.  Returns true when converged (step
-// below tol, KKT point on the bounds, or no descent left at this precision).
+// a parameter box [u0, u1] x [v0, v1]
 template <class R>
-__device__ bool newton2(const R* a, int du, int dv, int stride, R qx, R qy, R qz, R& u, R& v, int maxit, R tol,
-                        R& Dout)
+struct Box2 {
+    R u0, u1, v0, v1;
+};
+
+// projected Newton with active set and halving safeguard on a box (default
+// [0,1]^2): the Newton step where the Hessian is positive definite, the
+// Gauss-Newton step (J^T J, positive definite on a regular surface)
+// elsewhere, so the step does not depend on how the parameters are scaled.
+// A coordinate on a bound whose gradient points outward is held.  Returns
+// true when converged (step below tol, KKT point on the bounds, or no descent
+// left at this precision).
+template <class R>
+__device__ bool newton2(const R* a, const R* a00, int du, int dv, int stride, R qx, R qy, R qz, R& u, R& v, int maxit,
+                        R tol, R& Dout, Box2<R> bx = Box2<R>{ R(0), R(1), R(0), R(1) })
 {
     SD<R> o;
-    eval_patch(a, du, dv, stride, u, v, o);
+    eval_patch(a, a00, du, dv, stride, u, v, o);
     GH<R> h;
     R D = grad_hess(o, qx, qy, qz, h);
     bool conv = false;
     for (int it = 0; it < maxit; ++it) {
-        const bool fu = !((u <= R(0) && h.gu > R(0)) || (u >= R(1) && h.gu < R(0)));
-        const bool fv = !((v <= R(0) && h.gv > R(0)) || (v >= R(1) && h.gv < R(0)));
+        const bool fu = !((u <= bx.u0 && h.gu > R(0)) || (u >= bx.u1 && h.gu < R(0)));
+        const bool fv = !((v <= bx.v0 && h.gv > R(0)) || (v >= bx.v1 && h.gv < R(0)));
         R su = 0, sv = 0;
         if (fu && fv) {
             R a11 = h.huu, a12 = h.huv, a22 = h.hvv;
@@ -228,9 +239,9 @@ __device__ bool newton2(const R* a, int du, int dv, int stride, R qx, R qy, R qz
         GH<R> hn = h;
         bool acc = false;
         for (int ls = 0; ls < 30; ++ls) {
-            un = fmin(fmax(u + lam * su, R(0)), R(1));
-            vn = fmin(fmax(v + lam * sv, R(0)), R(1));
-            eval_patch(a, du, dv, stride, un, vn, o);
+            un = fmin(fmax(u + lam * su, bx.u0), bx.u1);
+            vn = fmin(fmax(v + lam * sv, bx.v0), bx.v1);
+            eval_patch(a, a00, du, dv, stride, un, vn, o);
             Dn = grad_hess(o, qx, qy, qz, hn);
             if (Dn <= D) {
                 acc = true;
@@ -258,14 +269,29 @@ __device__ bool newton2(const R* a, int du, int dv, int stride, R qx, R qy, R qz
 
 struct PoolEntry {
     int patch;
-    int slot;
-    float u0, v0;
+    short slot;
+    short direct;  // 1: a certification leaf: Newton on the original patch, inside the leaf
+    float u0, v0;  // start in the patch's own parameters (a leaf: its centre)
+    float hs, ht;  // a leaf: its half-sides (patch parameters)
 };
+
+// a cell of the certification search, in the patch's own parameters; cell
+// sides are dyadic fractions (every split is by 8 or 4), exact in FP32
+struct CertCell {
+    float s0, s1, t0, t1;
+    int depth;
+};
+constexpr int kStackCap = 64;
 
 template <class R>
 struct WarpSmem {
-    int cand[kCandCap];
-    R cand_lb[kCandCap];
+    union {
+        struct {
+            int cand[kCandCap];
+            R cand_lb[kCandCap];
+        };
+        R net[kSN * kSN * 3];  // certification: the span-pair net being searched
+    };
     PoolEntry pool[kPoolCap];
     double pool_D[kPoolCap];
     double pool_u[kPoolCap];
@@ -273,11 +299,14 @@ struct WarpSmem {
     float pool_s32[kPoolCap];  // mixed: FP32 minimiser in the span pair and its squared distance
     float pool_t32[kPoolCap];
     float pool_D32[kPoolCap];
-    unsigned char pool_conv32[kPoolCap];  // mixed: the FP32 stage converged
+    unsigned char pool_conv32[kPoolCap];  // mixed: the FP32 stage converged (1), not (0), or left its leaf (3)
     short fin[kPoolCap];
     unsigned char pool_flags[kPoolCap];
+    CertCell stk[kStackCap];
     double q64[kQPW][3];
     float eps32[kQPW];
+    float eps32r[kQPW];  // rounding part of eps32 (distances on the original surface)
+    int surf[kQPW];
     float best_D32[kQPW];
     double best_D[kQPW];
     double best_u[kQPW];
@@ -286,32 +315,20 @@ struct WarpSmem {
     unsigned char best_flags[kQPW];
 };
 
-// local-frame copy of a patch's power coefficients: the constant term
-// becomes a(0,0) - q, formed in FP64 and rounded, so the FP32 iteration keeps
-// its relative accuracy on small patches far from the origin
-__device__ __forceinline__ void local_frame32(const float* a32, const double* a64_00, const double* q, int du, int dv,
-                                              int stride, float* out)
-{
-    for (int i = 0; i <= du; ++i)
-        for (int j = 0; j <= dv; ++j)
-            for (int c = 0; c < 3; ++c) out[(i * stride + j) * 3 + c] = a32[(i * stride + j) * 3 + c];
-    for (int c = 0; c < 3; ++c) out[c] = (float)(a64_00[c] - q[c]);
-}
-
 // Newton on the bicubic from a sampled basin; when it stops on an edge of the
 // patch, a second start half a grid cell inside the patch guards against a
 // minimum hidden behind a ridge of D next to that edge.  Keeps the better.
 template <class R>
-__device__ bool bicubic_newton(const R* c, R qx, R qy, R qz, R& u, R& v, int maxit, R tol, R hu, R hv)
+__device__ bool bicubic_newton(const R* c, const R* c00, R qx, R qy, R qz, R& u, R& v, int maxit, R tol, R hu, R hv)
 {
     R D;
-    bool ok = newton2<R>(c, 3, 3, 4, qx, qy, qz, u, v, maxit, tol, D);
+    bool ok = newton2<R>(c, c00, 3, 3, 4, qx, qy, qz, u, v, maxit, tol, D);
     const bool eu = u <= R(0) || u >= R(1), ev = v <= R(0) || v >= R(1);
     if (eu || ev) {
         R u2 = eu ? (u <= R(0) ? R(0.5) * hu : R(1) - R(0.5) * hu) : u;
         R v2 = ev ? (v <= R(0) ? R(0.5) * hv : R(1) - R(0.5) * hv) : v;
         R D2;
-        bool ok2 = newton2<R>(c, 3, 3, 4, qx, qy, qz, u2, v2, maxit, tol, D2);
+        bool ok2 = newton2<R>(c, c00, 3, 3, 4, qx, qy, qz, u2, v2, maxit, tol, D2);
         if (D2 < D) {
             u = u2;
             v = v2;
@@ -336,21 +353,58 @@ __device__ void flush_pool(const SurfQ& P, WarpSmem<R>& W, int npool, int lane)
         for (int k = lane; k < npool; k += 32) {
             const PoolEntry e = W.pool[k];
             const double* q = W.q64[e.slot];
-            float c[48];
-            local_frame32(P.rec32 + (int64_t)BSPL_SREC32 * e.patch + 6,
-                          P.rec64 + (int64_t)BSPL_SREC64 * e.patch + 6, q, 3, 3, 4, c);
+            // FP32 iterations in the local frame of q: the constant term
+            // a(0,0) - q is formed in FP64 and rounded, so the iteration keeps
+            // its relative accuracy on small patches far from the origin
             float uf = e.u0, vf = e.v0, Df;
-            const bool ok1 = bicubic_newton<float>(c, 0.f, 0.f, 0.f, uf, vf, P.fp32_steps, 1e-7f, kHu, kHv);
+            bool ok1 = true, off_leaf = false;
+            if (e.direct) {
+                // a certification leaf: FP32 Newton on the original piece in
+                // the patch's own power basis (coefficients of the patch's
+                // size), inside the patch, then on to the span-pair net
+                const double* a00 = P.rec64 + (int64_t)BSPL_SREC64 * e.patch + 6;
+                const float off[3] = { (float)(a00[0] - q[0]), (float)(a00[1] - q[1]), (float)(a00[2] - q[2]) };
+                const float* r32 = P.rec32 + (int64_t)BSPL_SREC32 * e.patch;
+                const Box2<float> lb{ fmaxf(e.u0 - e.hs, 0.f), fminf(e.u0 + e.hs, 1.f), fmaxf(e.v0 - e.ht, 0.f),
+                                      fminf(e.v0 + e.ht, 1.f) };
+                const float* pn = P.patch_net32 + (int64_t)BSPL_SPAN_NET * e.patch;
+                const int du = (int)r32[54], dv = (int)r32[55];
+                ok1 = newton2<float>(pn, off, du, dv, kSN, 0.f, 0.f, 0.f, uf, vf, 2 * P.fp32_steps, 1e-7f, Df, lb);
+                // the leaf's minimum sits on a leaf side where D still falls
+                // outward (a side inside the patch, or a patch edge the surface
+                // is C1 across): not a minimum of D -- the neighbouring leaf,
+                // or patch, holds the one it leads to; no FP64 finish.  A
+                // minimum on the side itself has a vanishing gradient and stays.
+                SD<float> o;
+                eval_patch<float>(pn, off, du, dv, kSN, uf, vf, o);
+                GH<float> h;
+                grad_hess<float>(o, 0.f, 0.f, 0.f, h);
+                const int ef = (int)r32[61];
+                const float thr_u = 1e-4f * sqrtf(h.juu * Df), thr_v = 1e-4f * sqrtf(h.jvv * Df);
+                const bool out_u = (uf <= lb.u0 && (lb.u0 > 0.f || (ef & 1)) && h.gu > thr_u) ||
+                                   (uf >= lb.u1 && (lb.u1 < 1.f || (ef & 2)) && h.gu < -thr_u);
+                const bool out_v = (vf <= lb.v0 && (lb.v0 > 0.f || (ef & 4)) && h.gv > thr_v) ||
+                                   (vf >= lb.v1 && (lb.v1 < 1.f || (ef & 8)) && h.gv < -thr_v);
+                off_leaf = out_u || out_v;
+            } else {
+                const double* a00 = P.rec64 + (int64_t)BSPL_SREC64 * e.patch + 6;
+                const float off[3] = { (float)(a00[0] - q[0]), (float)(a00[1] - q[1]), (float)(a00[2] - q[2]) };
+                ok1 = bicubic_newton<float>(P.rec32 + (int64_t)BSPL_SREC32 * e.patch + 6, off, 0.f, 0.f, 0.f, uf, vf,
+                                            P.fp32_steps, 1e-7f, kHu, kHv);
+            }
             const double* pb = P.patch_box + 4 * (int64_t)e.patch;
             float s = (float)(pb[0] + uf * (pb[1] - pb[0])), t = (float)(pb[2] + vf * (pb[3] - pb[2]));
             const float* r32 = P.rec32 + (int64_t)BSPL_SREC32 * e.patch;
             const int pu = (int)r32[54], pv = (int)r32[55];
             const int64_t slot = P.patch_span[e.patch];
-            float net[kSN * kSN * 3];
-            local_frame32(P.span_net32 + (int64_t)BSPL_SPAN_NET * slot, P.span_net + (int64_t)BSPL_SPAN_NET * slot, q,
-                          pu, pv, kSN, net);
-            const bool ok2 = newton2<float>(net, pu, pv, kSN, 0.f, 0.f, 0.f, s, t, P.fp32_steps, 1e-7f, Df);
-            W.pool_conv32[k] = ok1 && ok2;
+            bool ok2 = true;
+            if (!e.direct) {
+                const double* n00 = P.span_net + (int64_t)BSPL_SPAN_NET * slot;
+                const float noff[3] = { (float)(n00[0] - q[0]), (float)(n00[1] - q[1]), (float)(n00[2] - q[2]) };
+                ok2 = newton2<float>(P.span_net32 + (int64_t)BSPL_SPAN_NET * slot, noff, pu, pv, kSN, 0.f, 0.f, 0.f,
+                                     s, t, P.fp32_steps, 1e-7f, Df);
+            }
+            W.pool_conv32[k] = off_leaf ? 3 : (ok1 && ok2);
             W.pool_s32[k] = s;
             W.pool_t32[k] = t;
             W.pool_D32[k] = Df;
@@ -371,8 +425,11 @@ __device__ void flush_pool(const SurfQ& P, WarpSmem<R>& W, int npool, int lane)
             bool take = false;
             if (k < npool) {
                 const int sl = W.pool[k].slot;
-                const float sm = sqrtf(W.best_D32[sl]) + 2.f * W.eps32[sl];
-                take = !W.pool_conv32[k] || W.pool_D32[k] <= sm * sm;
+                // every D32 is a distance on the ORIGINAL surface, so only
+                // the FP32 rounding separates candidates
+                const float sm = sqrtf(W.best_D32[sl]) + 2.f * W.eps32r[sl];
+                const int cv = W.pool_conv32[k];
+                take = cv != 3 && (!cv || W.pool_D32[k] <= sm * sm);
             }
             const unsigned m = __ballot_sync(kFull, take);
             if (take) W.fin[nfin + __popc(m & ((1u << lane) - 1))] = (short)k;
@@ -388,16 +445,16 @@ __device__ void flush_pool(const SurfQ& P, WarpSmem<R>& W, int npool, int lane)
             const double* net = P.span_net + (int64_t)BSPL_SPAN_NET * P.patch_span[e.patch];
             double s = W.pool_s32[k], t = W.pool_t32[k], D;
             double s1 = s, t1 = t;
-            newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s1, t1, 1, 0.0, D);
+            newton2<double>(net, net, pu, pv, kSN, q[0], q[1], q[2], s1, t1, 1, 0.0, D);
             double s2 = s1, t2 = t1;
-            newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s2, t2, 1, 0.0, D);
+            newton2<double>(net, net, pu, pv, kSN, q[0], q[1], q[2], s2, t2, 1, 0.0, D);
             unsigned char fl = 0;
             bool ok = fabs(s2 - s1) + fabs(t2 - t1) <= 1e-9;
             s = s2;
             t = t2;
             if (!ok) {
                 fl |= BSPL_Q_FALLBACK;
-                ok = newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s, t, P.newton_max, 1e-15, D);
+                ok = newton2<double>(net, net, pu, pv, kSN, q[0], q[1], q[2], s, t, P.newton_max, 1e-15, D);
             }
             fl |= ok ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
             W.pool_D[k] = D;
@@ -411,13 +468,20 @@ __device__ void flush_pool(const SurfQ& P, WarpSmem<R>& W, int npool, int lane)
             const double* q = W.q64[e.slot];
             const double* a = P.rec64 + (int64_t)BSPL_SREC64 * e.patch + 6;
             double D, u = e.u0, v = e.v0;
-            bicubic_newton<double>(a, q[0], q[1], q[2], u, v, P.newton_max, 1e-15, kHu, kHv);
+            if (!e.direct) bicubic_newton<double>(a, a, q[0], q[1], q[2], u, v, P.newton_max, 1e-15, kHu, kHv);
             const double* pb = P.patch_box + 4 * (int64_t)e.patch;
             double s = pb[0] + u * (pb[1] - pb[0]), t = pb[2] + v * (pb[3] - pb[2]);
             const float* r32 = P.rec32 + (int64_t)BSPL_SREC32 * e.patch;
             const int pu = (int)r32[54], pv = (int)r32[55];
             const double* net = P.span_net + (int64_t)BSPL_SPAN_NET * P.patch_span[e.patch];
-            bool ok = newton2<double>(net, pu, pv, kSN, q[0], q[1], q[2], s, t, P.newton_max, 1e-15, D);
+            Box2<double> bx{ 0.0, 1.0, 0.0, 1.0 };
+            if (e.direct) {
+                // a certification leaf: the minimum of D over the leaf
+                const double w = pb[1] - pb[0], x = pb[3] - pb[2];
+                bx = Box2<double>{ fmax(pb[0] + ((double)e.u0 - e.hs) * w, 0.0), fmin(pb[0] + ((double)e.u0 + e.hs) * w, 1.0),
+                                   fmax(pb[2] + ((double)e.v0 - e.ht) * x, 0.0), fmin(pb[2] + ((double)e.v0 + e.ht) * x, 1.0) };
+            }
+            bool ok = newton2<double>(net, net, pu, pv, kSN, q[0], q[1], q[2], s, t, P.newton_max, 1e-15, D, bx);
             W.pool_D[k] = D;
             W.pool_u[k] = s;
             W.pool_v[k] = t;
@@ -451,10 +515,470 @@ __device__ void flush_pool(const SurfQ& P, WarpSmem<R>& W, int npool, int lane)
     __syncwarp();
 }
 
+// ------------------------------------------------------------------
+// Certification of the minimum on the ORIGINAL surface (branch and bound).
+//
+// The sample grid of the bicubics finds every minimum whose basin holds a
+// grid minimum; a narrower basin can be missed.  After the grid stage and
+// its Newton refinement have given each query a distance D* (an upper bound
+// of the minimum), every patch whose box could still hold something closer
+// is searched cell by cell on the original span-pair polynomial restricted
+// to the patch.  With the bounds the decomposition stored for the patch
+// (the lengths of the first, second and third partials of S over the
+// patch, in its own parameters), the third partials of D = |S - q|^2 are
+// bounded on a cell (e.g. |D_sss| <= 2(3 |S_s||S_ss| + R |S_sss|), R the
+// largest distance on the cell), and a cell of half-sides (hs, ht) around
+// its centre c is discarded when
+//   * a lower bound of D on the cell is at least the current upper bound:
+//     the minimum over the cell of the quadratic Taylor model of D at c
+//     (D, grad D and the Hessian evaluated there) less the cubic remainder,
+//     or the first-order bound (|S(c) - q| - |S_s| hs - |S_t| ht)^2; or
+//   * a component of grad D keeps its sign on the whole cell (|D_s(c)|
+//     exceeds its largest change over the cell, from the Hessian at c and
+//     the third-derivative bounds): then every point of the cell can move
+//     against the gradient and lower D, so none is a minimum -- except on a
+//     cell side that is a patch edge the surface is not C1 across (a C0
+//     crease or the domain boundary), where the cell is kept.
+// A kept cell on which the Hessian of D is positive definite throughout
+// (its value at c less its largest change, from the third-derivative
+// bounds) holds at most one minimum: it is discarded when it holds the
+// query's best point so far (that point is then its minimum), else it is a
+// leaf.  Any other kept cell is split into an 8 x 4 grid of cells along its
+// longer side (one cell per lane) until cert_depth levels, after which it is
+// a leaf.  Each leaf runs Newton on the original patch from its centre,
+// confined to the leaf, which finds the minimum of D over the leaf (the
+// Newton pool).  Every sampled distance also lowers the upper bound.  All
+// quantities carry a bound on their rounding error (FP32 in the mixed path,
+// FP64 in the plain one), so the discarding is safe in either precision.
+template <class R>
+struct URound;
+template <>
+struct URound<float> {
+    static constexpr float v = 5.9604645e-08f;  // 2^-24
+};
+template <>
+struct URound<double> {
+    static constexpr double v = 1.1102230246251565e-16;  // 2^-53
+};
+
+template <class R>
+__device__ __forceinline__ const R* span_coef(const SurfQ& P, int64_t slot);
+template <>
+__device__ __forceinline__ const float* span_coef<float>(const SurfQ& P, int64_t slot)
+{
+    return P.span_net32 + (int64_t)BSPL_SPAN_NET * slot;
+}
+template <>
+__device__ __forceinline__ const double* span_coef<double>(const SurfQ& P, int64_t slot)
+{
+    return P.span_net + (int64_t)BSPL_SPAN_NET * slot;
+}
+
+// value and first partials of the span-pair polynomial minus q; the
+// constant term is passed in (formed in FP64 in the local frame of q)
+template <class R>
+__device__ __forceinline__ void eval_d1(const R* a, const R* off, int du, int dv, R u, R v, R* S, R* Su, R* Sv)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        R s = 0, su = 0, sv = 0;
+        for (int i = du; i >= 0; --i) {
+            R p = 0, p1 = 0;
+            for (int j = dv; j >= 0; --j) {
+                const R coef = (i | j) ? a[(i * kSN + j) * 3 + c] : off[c];
+                p1 = p1 * v + p;
+                p = p * v + coef;
+            }
+            su = su * u + s;
+            s = s * u + p;
+            sv = sv * u + p1;
+        }
+        S[c] = s;
+        Su[c] = su;
+        Sv[c] = sv;
+    }
+}
+
+// minimum over the box |x| <= X, |y| <= Y of g.(x, y) + (a x^2 + 2 b x y +
+// c y^2) / 2: exact where the form is positive definite (interior
+// stationary point, else the best of the four sides), otherwise a lower
+// bound that takes each term at its worst
+template <class R>
+__device__ __forceinline__ R quad_box_min(R gx, R gy, R a, R b, R c, R X, R Y)
+{
+    const R det = a * c - b * b;
+    if (a > R(0) && det > R(0)) {
+        auto q = [&](R x, R y) { return gx * x + gy * y + R(0.5) * (a * x * x + R(2) * b * x * y + c * y * y); };
+        const R x0 = -(c * gx - b * gy) / det, y0 = -(a * gy - b * gx) / det;
+        if (fabs(x0) <= X && fabs(y0) <= Y) return q(x0, y0);
+        R m = INFINITY;
+        for (int k = 0; k < 2; ++k) {
+            const R sx = k ? X : -X, sy = k ? Y : -Y;
+            m = fmin(m, q(sx, fmin(fmax(-(gy + b * sx) / c, -Y), Y)));
+            m = fmin(m, q(fmin(fmax(-(gx + b * sy) / a, -X), X), sy));
+        }
+        return m;
+    }
+    return -fabs(gx) * X - fabs(gy) * Y +
+           R(0.5) * (fmin(a, R(0)) * X * X - R(2) * fabs(b) * X * Y + fmin(c, R(0)) * Y * Y);
+}
+
+// what the cell test of one (query, patch) pair needs: the net searched and
+// its constant term in the frame of q, how a cell's (s, t) maps to the net's
+// parameters, the patch's derivative bounds, and the rounding bounds of the
+// Horner evaluation.  FP32: the original piece in the patch's own power
+// basis (coefficients of the patch's size); FP64: the span-pair net.
+template <class R>
+struct CellCtx {
+    const R* a;
+    R off[3];
+    int du, dv, eflags;
+    R e_org_s, e_w_s, e_org_t, e_w_t;
+    R Vs, Vt, Ass, Ast, Att, Tsss, Tsst, Tstt, Tttt;
+    R eS, eSs, eSt, eSss, eSst, eStt;
+};
+
+// everything but the net pointer and the rounding bounds (which need the
+// weighted L1 norms of the coefficients)
+template <class R, bool MIXED>
+__device__ __forceinline__ void cell_ctx_init(const SurfQ& P, const double* q, int pch, CellCtx<R>& C)
+{
+    const float* r32 = P.rec32 + (int64_t)BSPL_SREC32 * pch;
+    C.du = (int)r32[54];
+    C.dv = (int)r32[55];
+    C.Vs = r32[56];
+    C.Vt = r32[57];
+    C.Ass = r32[58];
+    C.Ast = r32[59];
+    C.Att = r32[60];
+    C.eflags = (int)r32[61];
+    C.Tsss = r32[62];
+    C.Tsst = r32[63];
+    C.Tstt = r32[64];
+    C.Tttt = r32[65];
+    const double* pb = P.patch_box + 4 * (int64_t)pch;
+    C.e_org_s = MIXED ? R(0) : (R)pb[0];
+    C.e_w_s = MIXED ? R(1) : (R)(pb[1] - pb[0]);
+    C.e_org_t = MIXED ? R(0) : (R)pb[2];
+    C.e_w_t = MIXED ? R(1) : (R)(pb[3] - pb[2]);
+    const double* a64 =
+        MIXED ? P.rec64 + (int64_t)BSPL_SREC64 * pch + 6 : P.span_net + (int64_t)BSPL_SPAN_NET * P.patch_span[pch];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) C.off[c] = (R)(a64[c] - q[c]);
+}
+
+template <class R>
+__device__ __forceinline__ void cell_ctx_errors(CellCtx<R>& C, const R* L /* weights 1, i, j, i(i-1), ij, j(j-1) */)
+{
+    const R kE = R(48) * URound<R>::v;  // Horner error factor for degree <= 7 + 7, with margin
+    C.eS = kE * L[0];
+    C.eSs = kE * L[1] * C.e_w_s;
+    C.eSt = kE * L[2] * C.e_w_t;
+    C.eSss = kE * L[3] * C.e_w_s * C.e_w_s;
+    C.eSst = kE * L[4] * C.e_w_s * C.e_w_t;
+    C.eStt = kE * L[5] * C.e_w_t * C.e_w_t;
+}
+
+template <class R>
+__device__ __forceinline__ void l1_add(R* L, int i, int j, R x)
+{
+    L[0] += x;
+    L[1] += R(i) * x;
+    L[2] += R(j) * x;
+    L[3] += R(i * (i - 1)) * x;
+    L[4] += R(i * j) * x;
+    L[5] += R(j * (j - 1)) * x;
+}
+
+struct CellRes {
+    bool live, convex;
+};
+
+// The test of one cell [cs0, cs0 + hs] x [ct0, ct0 + ht] (patch parameters)
+// against the upper bound ub: lower bounds of D and the gradient test
+// (described above), and whether the Hessian of D is positive definite on
+// the whole cell.  Dub: an upper bound of D at the cell's centre.
+template <class R>
+__device__ CellRes cell_test(const CellCtx<R>& C, float cs0, float hs, float ct0, float ht, R ub, R& Dub)
+{
+    constexpr R U = URound<R>::v;
+    const R ds = R(0.5) * (R)hs, dt = R(0.5) * (R)ht;
+    const R sc = (R)cs0 + ds, tc = (R)ct0 + dt;
+    SD<R> o;
+    eval_patch<R>(C.a, C.off, C.du, C.dv, kSN, C.e_org_s + sc * C.e_w_s, C.e_org_t + tc * C.e_w_t, o);
+    // D, its gradient and Hessian at the centre, in the patch's parameters
+    R D = 0, Ds = 0, Dt = 0, Hss = 0, Hst = 0, Htt = 0, n1 = 0, n2 = 0, m11 = 0, m12 = 0, m22 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R S = o.S[c], Ss = o.Su[c] * C.e_w_s, St = o.Sv[c] * C.e_w_t;
+        const R Sss = o.Suu[c] * C.e_w_s * C.e_w_s, Sst = o.Suv[c] * C.e_w_s * C.e_w_t,
+                Stt = o.Svv[c] * C.e_w_t * C.e_w_t;
+        D += S * S;
+        Ds += S * Ss;
+        Dt += S * St;
+        Hss += Ss * Ss + S * Sss;
+        Hst += Ss * St + S * Sst;
+        Htt += St * St + S * Stt;
+        n1 += Ss * Ss;
+        n2 += St * St;
+        m11 += Sss * Sss;
+        m12 += Sst * Sst;
+        m22 += Stt * Stt;
+    }
+    Ds *= R(2);
+    Dt *= R(2);
+    Hss *= R(2);
+    Hst *= R(2);
+    Htt *= R(2);
+    const R dist = sqrt(D), nSs = sqrt(n1), nSt = sqrt(n2);
+    const R nSss = sqrt(m11), nSst = sqrt(m12), nStt = sqrt(m22);
+    const R eS = C.eS, eSs = C.eSs, eSt = C.eSt, eSss = C.eSss, eSst = C.eSst, eStt = C.eStt;
+    // rounding bounds of D, its gradient and Hessian from those of S - q and
+    // its derivatives
+    const R eD = R(2) * dist * eS + eS * eS + R(8) * U * D;
+    const R eDs = R(2) * (dist * eSs + nSs * eS + eS * eSs) + R(8) * U * dist * nSs;
+    const R eDt = R(2) * (dist * eSt + nSt * eS + eS * eSt) + R(8) * U * dist * nSt;
+    const R eHss = R(2) * (R(2) * nSs * eSs + eSs * eSs + dist * eSss + nSss * eS + eS * eSss) +
+                   R(8) * U * (n1 + dist * nSss);
+    const R eHst = R(2) * (nSs * eSt + nSt * eSs + eSs * eSt + dist * eSst + nSst * eS + eS * eSst) +
+                   R(8) * U * (nSs * nSt + dist * nSst);
+    const R eHtt = R(2) * (R(2) * nSt * eSt + eSt * eSt + dist * eStt + nStt * eS + eS * eStt) +
+                   R(8) * U * (n2 + dist * nStt);
+    Dub = D + eD;
+    ub = fmin(ub, Dub);
+    // third partials of D on the cell
+    const R reach = C.Vs * ds + C.Vt * dt;
+    const R Rmax = dist + eS + reach;
+    const R Ksss = R(2) * (R(3) * C.Vs * C.Ass + Rmax * C.Tsss);
+    const R Ksst = R(2) * (R(2) * C.Vs * C.Ast + C.Vt * C.Ass + Rmax * C.Tsst);
+    const R Kstt = R(2) * (R(2) * C.Vt * C.Ast + C.Vs * C.Att + Rmax * C.Tstt);
+    const R Kttt = R(2) * (R(3) * C.Vt * C.Att + Rmax * C.Tttt);
+    // lower bound of D on the cell: the quadratic model's minimum over the
+    // cell, less the cubic remainder and the rounding bounds
+    const R cub = (Ksss * ds * ds * ds + R(3) * Ksst * ds * ds * dt + R(3) * Kstt * ds * dt * dt +
+                   Kttt * dt * dt * dt) * R(1.0 / 6.0);
+    const R eq = eDs * ds + eDt * dt + R(0.5) * (eHss * ds * ds + R(2) * eHst * ds * dt + eHtt * dt * dt);
+    const R qm = quad_box_min<R>(Ds, Dt, Hss, Hst, Htt, ds, dt);
+    const R qscale = fabs(Ds) * ds + fabs(Dt) * dt + fabs(Hss) * ds * ds + R(2) * fabs(Hst) * ds * dt +
+                     fabs(Htt) * dt * dt;
+    const R lbQ = D - eD + qm - eq - cub - R(32) * U * (D + qscale);
+    const R l1 = fmax(dist - eS - reach, R(0));
+    const R lb = fmax(lbQ, l1 * l1 * (R(1) - R(8) * U));
+    CellRes r{ lb < ub, false };
+    // gradient test: a sign of D_s (D_t) fixed on the cell
+    const R vs = fabs(Hss) * ds + fabs(Hst) * dt + R(0.5) * (Ksss * ds * ds + R(2) * Ksst * ds * dt + Kstt * dt * dt) +
+                 eHss * ds + eHst * dt;
+    const R vt = fabs(Hst) * ds + fabs(Htt) * dt + R(0.5) * (Ksst * ds * ds + R(2) * Kstt * ds * dt + Kttt * dt * dt) +
+                 eHst * ds + eHtt * dt;
+    if (r.live && fabs(Ds) - eDs > vs * (R(1) + R(32) * U)) {
+        const bool blocked = Ds > R(0) ? (cs0 <= 0.f && !(C.eflags & 1)) : (cs0 + hs >= 1.f && !(C.eflags & 2));
+        if (!blocked) r.live = false;
+    }
+    if (r.live && fabs(Dt) - eDt > vt * (R(1) + R(32) * U)) {
+        const bool blocked = Dt > R(0) ? (ct0 <= 0.f && !(C.eflags & 4)) : (ct0 + ht >= 1.f && !(C.eflags & 8));
+        if (!blocked) r.live = false;
+    }
+    if (r.live) {
+        // Hessian positive definite on the whole cell: its centre value less
+        // the largest change the third-derivative bounds allow
+        const R a_lo = Hss - (Ksss * ds + Ksst * dt) - eHss, c_lo = Htt - (Kstt * ds + Kttt * dt) - eHtt;
+        const R b_hi = fabs(Hst) + Ksst * ds + Kstt * dt + eHst;
+        r.convex = a_lo > R(0) && c_lo > R(0) && a_lo * c_lo > b_hi * b_hi * (R(1) + R(32) * U);
+    }
+    return r;
+}
+
+// the query's best point, when it is a converged Newton end point (a KKT
+// point of D on its span pair) on span pair `span`, lies in the cell: a
+// convex cell that holds it holds nothing better
+template <class R>
+__device__ __forceinline__ bool holds_best(const SurfQ& P, const WarpSmem<R>& W, int sl, int64_t span,
+                                           const double* pb, float cs0, float hs, float ct0, float ht)
+{
+    const int bp = W.best_patch[sl];
+    if (bp == 0x7fffffff || !(W.best_flags[sl] & BSPL_Q_CONVERGED) || P.patch_span[bp] != span) return false;
+    const double w = pb[1] - pb[0], x = pb[3] - pb[2];
+    const double s0 = pb[0] + (double)cs0 * w, s1 = pb[0] + (double)(cs0 + hs) * w;
+    const double t0 = pb[2] + (double)ct0 * x, t1 = pb[2] + (double)(ct0 + ht) * x;
+    const double bu = W.best_u[sl], bv = W.best_v[sl];
+    return bu >= s0 && bu <= s1 && bv >= t0 && bv <= t1;
+}
+
+// a leaf to the Newton pool (warp-cooperative; leaf: this lane's flag)
+template <class R, bool MIXED, int GU, int GV>
+__device__ __forceinline__ void push_leaves(const SurfQ& P, WarpSmem<R>& W, int sl, int pch, bool leaf, float sc,
+                                            float tc, float hs2, float ht2, int lane, int& npool,
+                                            unsigned long long* cnt)
+{
+    const unsigned lm = __ballot_sync(kFull, leaf);
+    const int nl = __popc(lm);
+    if (nl == 0) return;
+    if (npool + nl > kPoolCap) {
+        flush_pool<R, MIXED, GU, GV>(P, W, npool, lane);
+        cnt[3] += (unsigned long long)npool;
+        npool = 0;
+    }
+    if (leaf) {
+        PoolEntry e;
+        e.patch = pch;
+        e.slot = (short)sl;
+        e.direct = 1;
+        e.u0 = sc;
+        e.v0 = tc;
+        e.hs = hs2;
+        e.ht = ht2;
+        W.pool[npool + __popc(lm & ((1u << lane) - 1))] = e;
+    }
+    npool += nl;
+    if (lane == 0) cnt[1] += (unsigned long long)nl;
+    __syncwarp();
+}
+
+// the cell search of one patch whose whole-patch test left it live and not
+// convex: its net staged in shared memory, cells split 8 x 4 (one per lane)
+template <class R, bool MIXED, int GU, int GV>
+__device__ void certify_patch(const SurfQ& P, WarpSmem<R>& W, int sl, int pch, int lane, R& ub, int& npool,
+                              unsigned long long* cnt /* cells, leaves, overflow, newton */)
+{
+    const double* q = W.q64[sl];
+    const int64_t span = P.patch_span[pch];
+    const double* pb = P.patch_box + 4 * (int64_t)pch;
+    CellCtx<R> C;
+    cell_ctx_init<R, MIXED>(P, q, pch, C);
+    {
+        const R* ag = MIXED ? (const R*)(P.patch_net32 + (int64_t)BSPL_SPAN_NET * pch) : span_coef<R>(P, span);
+        __syncwarp();
+        for (int k = lane; k < kSN * kSN * 3; k += 32) W.net[k] = ag[k];
+        __syncwarp();
+    }
+    C.a = W.net;
+    R L[6] = { 0, 0, 0, 0, 0, 0 };
+    const int ncoef = (C.du + 1) * (C.dv + 1) * 3;
+    for (int k = lane; k < ncoef; k += 32) {
+        const int i = k / ((C.dv + 1) * 3), r = k - i * (C.dv + 1) * 3, j = r / 3, c = r - 3 * j;
+        l1_add(L, i, j, fabs((i | j) ? C.a[(i * kSN + j) * 3 + c] : C.off[c]));
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) L[k] += __shfl_xor_sync(kFull, L[k], o);
+    cell_ctx_errors(C, L);
+    const int maxdepth = P.cert_depth;
+
+    int top = 1;
+    if (lane == 0) W.stk[0] = CertCell{ 0.f, 1.f, 0.f, 1.f, 0 };
+    __syncwarp();
+    while (top > 0) {
+        const CertCell cc = W.stk[top - 1];
+        __syncwarp();
+        --top;
+        const bool along_s = C.Vs * R(cc.s1 - cc.s0) >= C.Vt * R(cc.t1 - cc.t0);
+        const int ns = along_s ? 8 : 4, nt = 32 / ns;
+        const int is = lane % ns, it = lane / ns;
+        const float hs = (cc.s1 - cc.s0) / (float)ns, ht = (cc.t1 - cc.t0) / (float)nt;
+        const float cs0 = cc.s0 + (float)is * hs, ct0 = cc.t0 + (float)it * ht;
+        R Dub;
+        CellRes r = cell_test<R>(C, cs0, hs, ct0, ht, ub, Dub);
+        ub = fmin(ub, warp_min(Dub));
+        if (r.live && r.convex && holds_best(P, W, sl, span, pb, cs0, hs, ct0, ht)) r.live = false;
+        cnt[0] += 32;
+        // every lane takes the same branches here (cc.depth, top and the
+        // ballot are warp-uniform), so the stack top stays uniform
+        bool leaf = r.live;
+        if (cc.depth < maxdepth) {
+            const bool split = r.live && !r.convex;
+            const unsigned m = __ballot_sync(kFull, split);
+            const int k = __popc(m);
+            if (top + k <= kStackCap) {
+                if (split)
+                    W.stk[top + __popc(m & ((1u << lane) - 1))] =
+                        CertCell{ cs0, cs0 + hs, ct0, ct0 + ht, cc.depth + 1 };
+                top += k;
+                leaf = r.live && r.convex;
+            } else if (lane == 0) {
+                cnt[2] += (unsigned long long)k;  // stack full: straight to Newton (counted)
+            }
+        }
+        push_leaves<R, MIXED, GU, GV>(P, W, sl, pch, leaf, cs0 + 0.5f * hs, ct0 + 0.5f * ht, 0.5f * hs, 0.5f * ht,
+                                      lane, npool, cnt);
+    }
+}
+
+// The certification search of every query slot of the warp.  Patches whose
+// box lower bound does not exceed the slot's best distance are first tested
+// whole, one per lane (the net read from global memory): discarded, a single
+// leaf (convex), or searched cell by cell.
+template <class R, bool MIXED, int GU, int GV>
+__device__ void certify_slots(const SurfQ& P, WarpSmem<R>& W, int nslots, int lane, int& npool,
+                              unsigned long long* cnt)
+{
+    const R* rec = STab<R>::rec(P);
+    const R* grp = STab<R>::grp(P);
+    constexpr int RW = STab<R>::RW, GW = STab<R>::GW;
+    for (int sl = 0; sl < nslots; ++sl) {
+        if ((W.best_flags[sl] & BSPL_Q_INVALID) || W.best_patch[sl] == 0x7fffffff) continue;
+        const int c = W.surf[sl];
+        const double* q = W.q64[sl];
+        const R qx = (R)q[0], qy = (R)q[1], qz = (R)q[2];
+        R ub;
+        if (MIXED) ub = (R)__double2float_ru(W.best_D[sl]);
+        else ub = (R)W.best_D[sl];
+        const R epsb = (R)W.eps32r[sl];  // box tests in R: rounding slack
+        const int64_t s0 = P.seg_off[c], s1 = P.seg_off[c + 1];
+        const int64_t g0 = P.grp_off[c], g1 = P.grp_off[c + 1];
+        for (int64_t gb = g0; gb < g1; gb += 32) {
+            const int64_t g = gb + lane;
+            const R lbg = g < g1 ? box_d2(grp + (int64_t)GW * g, qx, qy, qz) : R(INFINITY);
+            unsigned m = __ballot_sync(kFull, lbg <= slacked(ub, epsb));
+            while (m) {
+                const int jg = __ffs(m) - 1;
+                m &= m - 1;
+                if (!(__shfl_sync(kFull, lbg, jg) <= slacked(ub, epsb))) continue;
+                const int64_t ss = s0 + (gb + jg - g0) * BSPL_GROUP;
+                const int64_t se = min(ss + BSPL_GROUP, s1);
+                const int64_t sg = ss + lane;
+                bool cand = sg < se && box_d2(rec + (int64_t)RW * sg, qx, qy, qz) <= slacked(ub, epsb);
+                // the whole-patch test, one patch per lane
+                CellRes r{ false, false };
+                R Dub = R(INFINITY);
+                if (cand) {
+                    const int pch = (int)sg;
+                    CellCtx<R> C;
+                    cell_ctx_init<R, MIXED>(P, q, pch, C);
+                    C.a = MIXED ? (const R*)(P.patch_net32 + (int64_t)BSPL_SPAN_NET * pch)
+                                : span_coef<R>(P, P.patch_span[pch]);
+                    R L[6] = { 0, 0, 0, 0, 0, 0 };
+                    for (int i = 0; i <= C.du; ++i)
+                        for (int j = 0; j <= C.dv; ++j)
+                            for (int k = 0; k < 3; ++k)
+                                l1_add(L, i, j, fabs((i | j) ? C.a[(i * kSN + j) * 3 + k] : C.off[k]));
+                    cell_ctx_errors(C, L);
+                    r = cell_test<R>(C, 0.f, 1.f, 0.f, 1.f, ub, Dub);
+                    if (r.live && r.convex &&
+                        holds_best(P, W, sl, P.patch_span[pch], P.patch_box + 4 * (int64_t)pch, 0.f, 1.f, 0.f, 1.f))
+                        r.live = false;
+                }
+                ub = fmin(ub, warp_min(Dub));
+                const unsigned cm = __ballot_sync(kFull, cand);
+                if (lane == 0) cnt[0] += (unsigned long long)__popc(cm);  // one cell per patch tested
+                push_leaves<R, MIXED, GU, GV>(P, W, sl, (int)sg, r.live && r.convex, 0.5f, 0.5f, 0.5f, 0.5f, lane,
+                                              npool, cnt);
+                unsigned km = __ballot_sync(kFull, r.live && !r.convex);
+                while (km) {
+                    const int jp = __ffs(km) - 1;
+                    km &= km - 1;
+                    certify_patch<R, MIXED, GU, GV>(P, W, sl, (int)(ss + jp), lane, ub, npool, cnt);
+                }
+            }
+        }
+    }
+}
+
 template <class R, int GU, int GV, bool MIXED>
 __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
 {
-    __shared__ WarpSmem<R> smem[kWarps];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem<R>* smem = reinterpret_cast<WarpSmem<R>*>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpSmem<R>& W = smem[wid];
     const int64_t batch = (int64_t)blockIdx.x * kWarps + wid;
@@ -496,6 +1020,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
             W.q64[sl][1] = qy64;
             W.q64[sl][2] = qz64;
             W.eps32[sl] = (float)eps;
+            W.eps32r[sl] = (float)((MIXED ? R(4e-6) : R(1e-13)) * (fabs(qx) + fabs(qy) + fabs(qz) + (R)P.diag[cc_]));
+            W.surf[sl] = cc_;
             if (bad) W.best_flags[sl] = BSPL_Q_INVALID;
         }
         if (bad) continue;
@@ -571,7 +1097,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
                     const int pos = npool + __popc(m & ((1u << lane) - 1));
                     PoolEntry e;
                     e.patch = pch;
-                    e.slot = sl;
+                    e.slot = (short)sl;
+                    e.direct = 0;
+                    e.hs = e.ht = 0.f;
                     e.u0 = (float)u;
                     e.v0 = (float)v;
                     W.pool[pos] = e;
@@ -621,8 +1149,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
     if (npool > 0) {
         flush_pool<R, MIXED, GU, GV>(P, W, npool, lane);
         n_newton += npool;
+        npool = 0;
     }
     __syncwarp();
+    unsigned long long ccnt[4] = { 0, 0, 0, 0 };  // cells, leaves, overflow, newton
+    if (P.cert_depth >= 0) {
+        certify_slots<R, MIXED, GU, GV>(P, W, nslots, lane, npool, ccnt);
+        if (npool > 0) {
+            flush_pool<R, MIXED, GU, GV>(P, W, npool, lane);
+            ccnt[3] += npool;
+            npool = 0;
+        }
+        n_newton += ccnt[3];
+        __syncwarp();
+    }
 
     if (lane < nslots) {
         const int64_t qi = P.order ? (int64_t)P.order[qbase + lane] : qbase + lane;
@@ -672,6 +1212,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
             atomicAdd(P.counters + BSPL_CNT_NEWTON, n_newton);
             atomicAdd(P.counters + BSPL_CNT_FALLBACK, fb);
             atomicAdd(P.counters + BSPL_CNT_NONCONV, nc);
+            atomicAdd(P.counters + BSPL_CNT_CERT_CELLS, ccnt[0]);
+            atomicAdd(P.counters + BSPL_CNT_CERT_LEAVES, ccnt[1]);
+            atomicAdd(P.counters + BSPL_CNT_CERT_OVERFLOW, ccnt[2]);
         }
     }
 }
@@ -681,7 +1224,14 @@ void launch_surf(const SurfQ& P, cudaStream_t s)
 {
     int64_t batches = (P.n_q + kQPW - 1) / kQPW;
     int64_t blocks = (batches + kWarps - 1) / kWarps;
-    k_query_surfaces<R, GU, GV, MIXED><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P);
+    const size_t smem = sizeof(WarpSmem<R>) * kWarps;
+    static bool attr_set = false;  // per process; the attribute is per device function
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_query_surfaces<R, GU, GV, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr_set = true;
+    }
+    k_query_surfaces<R, GU, GV, MIXED><<<(unsigned)blocks, kWarps * 32, smem, s>>>(P);
 }
 
 }  // namespace
@@ -694,7 +1244,7 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
     if (n_q == 0) return BSPL_OK;
     if (!q_surf || !q_xyz || !uv || !dist || !status || !segs->seg_off || !segs->grp_off || !segs->rec64 ||
         !segs->rec32 || !segs->grp64 || !segs->grp32 || !segs->prange || !segs->diag || !segs->patch_box ||
-        !segs->patch_span || !segs->span_net || !segs->span_net32)
+        !segs->patch_span || !segs->span_net || !segs->span_net32 || !segs->patch_net32)
         return BSPL_EINVAL;
     if (n_q > 0x7fffffffLL || segs->capacity > 0x7fffffffLL) return BSPL_EINVAL;
     bspl_options o{};
@@ -715,6 +1265,7 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
     P.patch_span = segs->patch_span;
     P.span_net = segs->span_net;
     P.span_net32 = segs->span_net32;
+    P.patch_net32 = segs->patch_net32;
     P.diag = segs->diag;
     P.tol_rel = segs->tol_rel;
     P.n = segs->n;
@@ -727,6 +1278,8 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
     P.invert = invert;
     P.newton_max = o.newton_max > 0 ? o.newton_max : 30;
     P.fp32_steps = o.fp32_steps > 0 ? o.fp32_steps : 8;
+    if (o.cert_depth > 4) return BSPL_EINVAL;
+    P.cert_depth = o.cert_depth < 0 ? -1 : (o.cert_depth == 0 ? 2 : o.cert_depth);
     P.counters = (unsigned long long*)o.counters;
     P.order = nullptr;
     if (sort) {

@@ -34,7 +34,8 @@ double hd_box_diag(const double* P, int64_t np) { return box_diag_d(P, np); }
 // leaves of span pair (qu, qv) of a surface with degrees (pu, pv), knots U, V
 // and net P [n_u][n_v][3]; writes up to cap leaves (ctrl [48], prange [4])
 // and returns their count (the count is returned even when above cap)
-int64_t hd_surface_span(int pu, int pv, const double* U, int qu, const double* V, int qv, const double* P, int nv,
+int64_t hd_surface_span(int pu, int pv, const double* U, int nu, int qu, const double* V, int qv, const double* P,
+                        int nv,
                         double tol_rel, double diag, double* ctrl, double* prange, int64_t cap, int* err)
 {
     static SurfCoef cf;
@@ -46,7 +47,7 @@ int64_t hd_surface_span(int pu, int pv, const double* U, int qu, const double* V
     const double thr = tol_rel * diag, thr2 = thr * thr;  // the device computes the same two IEEE products
     *err = 0;
     SurfLeafOut none{};
-    const int64_t n = walk_span_surface<false>(pu, pv, U, qu, V, qv, P, nv, thr2, 0, 0, none, err, cf);
+    const int64_t n = walk_span_surface<false>(pu, pv, U, nu, qu, V, qv, P, nv, thr2, 0, 0, none, err, cf);
     if (n > cap) return n;
     double* rec64 = new double[(size_t)BSPL_SREC64 * (size_t)(n > 0 ? n : 1)];
     float* rec32 = new float[(size_t)BSPL_SREC32 * (size_t)(n > 0 ? n : 1)];
@@ -54,12 +55,52 @@ int64_t hd_surface_span(int pu, int pv, const double* U, int qu, const double* V
     double* pbox = new double[4 * (size_t)(n > 0 ? n : 1)];
     double* net = new double[BSPL_SPAN_NET];
     float* net32 = new float[BSPL_SPAN_NET];
-    SurfLeafOut out{ ctrl, prange, span, pbox, rec64, rec32, net, net32 };
-    walk_span_surface<true>(pu, pv, U, qu, V, qv, P, nv, thr2, 0, 0, out, err, cf);
+    float* pnet = new float[(size_t)BSPL_SPAN_NET * (size_t)(n > 0 ? n : 1)];
+    SurfLeafOut out{ ctrl, prange, span, pbox, rec64, rec32, net, net32, pnet };
+    walk_span_surface<true>(pu, pv, U, nu, qu, V, qv, P, nv, thr2, 0, 0, out, err, cf);
     delete[] rec64;
     delete[] rec32;
     delete[] span;
     delete[] pbox;
+    delete[] net;
+    delete[] net32;
+    delete[] pnet;
+    return n;
+}
+
+// derivative bounds and edge flags the filling walk writes into a patch's
+// FP32 record (entries 56..61): the bicubic leaves' records of span pair
+// (qu, qv), rec32 [cap][BSPL_SREC32], pbox [cap][4]
+int64_t hd_surface_records(int pu, int pv, const double* U, int nu, int qu, const double* V, int qv,
+                           const double* P, int nv, double tol_rel, double diag, float* rec32, double* pbox,
+                           int64_t cap, int* err)
+{
+    static SurfCoef cf;
+    static bool filled = false;
+    if (!filled) {
+        host_fill_coef<kMaxSurfDegree>(cf);
+        filled = true;
+    }
+    const double thr = tol_rel * diag, thr2 = thr * thr;
+    *err = 0;
+    SurfLeafOut none{};
+    const int64_t n = walk_span_surface<false>(pu, pv, U, nu, qu, V, qv, P, nv, thr2, 0, 0, none, err, cf);
+    if (n > cap) return n;
+    const size_t m = (size_t)(n > 0 ? n : 1);
+    double* ctrl = new double[48 * m];
+    double* prange = new double[4 * m];
+    double* rec64 = new double[(size_t)BSPL_SREC64 * m];
+    int64_t* span = new int64_t[m];
+    double* net = new double[BSPL_SPAN_NET];
+    float* net32 = new float[BSPL_SPAN_NET];
+    float* pnet = new float[(size_t)BSPL_SPAN_NET * m];
+    SurfLeafOut out{ ctrl, prange, span, pbox, rec64, rec32, net, net32, pnet };
+    walk_span_surface<true>(pu, pv, U, nu, qu, V, qv, P, nv, thr2, 0, 0, out, err, cf);
+    delete[] pnet;
+    delete[] ctrl;
+    delete[] prange;
+    delete[] rec64;
+    delete[] span;
     delete[] net;
     delete[] net32;
     return n;

@@ -3,7 +3,8 @@ through the C ABI, against the CPU oracle.
 
 Decomposition: patch counts, offsets, bicubic nets and parameter boxes
 bit-exact.  Queries: the last Newton steps run on the original span-pair
-patch, so |d_gpu - d_oracle| <= 1e-9 x diag for every query whatever the
+patch and the certification search bounds D on the original surface, so
+|d_gpu - d_oracle| <= 1e-9 x diag for every query whatever the
 decomposition tolerance, and the GPU (u, v), evaluated on the original
 surface by the oracle, reproduces the GPU distance.
 """
@@ -148,8 +149,8 @@ def test_surface_edge_cases_and_invalid():
 def test_surface_set_sampled():
     """128 surfaces of the random-surface workload at the paper's alpha:
     200k projection + 200k inversion queries through the kernels, oracle
-    parity on a sample, inversion bound and mixed-vs-plain agreement on every
-    query."""
+    parity on a sample of 1,000 per precision, inversion bound and
+    mixed-vs-plain agreement on every query."""
     ss, sq = synth.surface_set(seed=3, n_surf=128, n_proj=200_000, n_inv=200_000)
     dsf = bspl.DeviceSurfaces(ss, DEV)
     segs = bspl.decompose(dsf, TOL_S)
@@ -168,14 +169,38 @@ def test_surface_set_sampled():
     diag_i = O.surface_diag(ss)[sq.inv_surf]
     for prec in res:
         assert np.all(res[prec][3] <= 1e-9 * diag_i), np.max(res[prec][3] / diag_i)
-    # mixed vs plain on every projection query: the mixed path may settle in
-    # the other of two minima whose distances differ by a few 1e-6 x diag
-    # (FP32 Newton near a tie); measured at 1 query in 200k for this set
-    dis = np.where(np.abs(res[bspl.FP64][1] - res[bspl.MIXED][1]) > 1e-9 * diag_p)[0]
-    assert len(dis) <= 2, (len(dis), (np.abs(res[bspl.FP64][1] - res[bspl.MIXED][1]) / diag_p)[dis][:5])
+    # mixed vs plain on every query (both certified on the original surface)
+    rel = np.abs(res[bspl.FP64][1] - res[bspl.MIXED][1]) / diag_p
+    assert np.all(rel <= 1e-9), (int((rel > 1e-9).sum()), rel.max())
+    rel = np.abs(res[bspl.FP64][3] - res[bspl.MIXED][3]) / diag_i
+    assert np.all(rel <= 1e-9), (int((rel > 1e-9).sum()), rel.max())
     rng = np.random.default_rng(4)
-    pick = np.concatenate([rng.choice(len(sq.proj_surf), 300, replace=False), dis])
+    pick = rng.choice(len(sq.proj_surf), 1000, replace=False)
     qn = q.cpu().numpy()
-    check(ss, sq.proj_surf[pick], qn[pick], res[bspl.FP64][0][pick], res[bspl.FP64][1][pick])
-    keep = np.setdiff1d(pick, dis)
-    check(ss, sq.proj_surf[keep], qn[keep], res[bspl.MIXED][0][keep], res[bspl.MIXED][1][keep])
+    for prec in res:
+        check(ss, sq.proj_surf[pick], qn[pick], res[prec][0][pick], res[prec][1][pick])
+
+
+def test_certification_counters_and_switch():
+    """The certification search runs by default (its cells and leaves are
+    counted), can be switched off for timing comparisons (cert_depth < 0),
+    and rejects depths above 4."""
+    ss, sq = synth.surface_set(seed=3, n_surf=16, n_proj=20_000, n_inv=1)
+    dsf = bspl.DeviceSurfaces(ss, DEV)
+    segs = bspl.decompose(dsf, TOL_S)
+    ps = dev(sq.proj_surf, torch.int32)
+    q = bspl.bspl_eval_surfaces(dsf, ps, dev(sq.proj_uv, torch.float64)) + \
+        dev(sq.proj_dir, torch.float64) * dev(sq.proj_r, torch.float64)[:, None]
+    names = bspl.COUNTER_NAMES
+    for prec in (bspl.FP64, bspl.MIXED):
+        got = {}
+        for cd in (-1, 0, 3):
+            cnt = torch.zeros(bspl.NCOUNTERS, dtype=torch.int64, device=DEV)
+            bspl.bspl_project_surfaces(segs, ps, q, bspl.make_options(prec=prec, cert_depth=cd, counters=cnt))
+            got[cd] = dict(zip(names, cnt.cpu().tolist()))
+        assert got[-1]["cert_cells"] == 0 and got[-1]["cert_leaves"] == 0
+        assert got[0]["cert_cells"] > 0
+        assert got[3]["cert_cells"] >= got[0]["cert_cells"]
+        assert got[0]["queries"] == len(sq.proj_surf)
+    with pytest.raises(bspl.BsplError, match="EINVAL"):
+        bspl.bspl_project_surfaces(segs, ps, q, bspl.make_options(cert_depth=5))

@@ -13,6 +13,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2504_11498_gb300 import synth
+from paper_2504_11498_gb300.bspl import SREC32
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -33,7 +34,8 @@ def hd(tmp_path_factory):
     D = ctypes.POINTER(ctypes.c_double)
     lib.hd_box_diag.argtypes = [D, ctypes.c_int64]
     lib.hd_box_diag.restype = ctypes.c_double
-    lib.hd_surface_span.argtypes = [ctypes.c_int, ctypes.c_int, D, ctypes.c_int, D, ctypes.c_int, D, ctypes.c_int,
+    lib.hd_surface_span.argtypes = [ctypes.c_int, ctypes.c_int, D, ctypes.c_int, ctypes.c_int, D, ctypes.c_int, D,
+                                    ctypes.c_int,
                                     ctypes.c_double, ctypes.c_double, D, D, ctypes.c_int64,
                                     ctypes.POINTER(ctypes.c_int)]
     lib.hd_surface_span.restype = ctypes.c_int64
@@ -62,7 +64,7 @@ def host_decompose(hd, ss, tol):
                 ctrl = np.zeros((cap, 48))
                 pr = np.zeros((cap, 4))
                 err = ctypes.c_int()
-                k = hd.hd_surface_span(pu, pv, dp(U), qu, dp(V), qv, dp(P), nv, tol, diag, dp(ctrl), dp(pr), cap,
+                k = hd.hd_surface_span(pu, pv, dp(U), nu, qu, dp(V), qv, dp(P), nv, tol, diag, dp(ctrl), dp(pr), cap,
                                        ctypes.byref(err))
                 assert 0 < k <= cap
                 ctrl_all.append(ctrl[:k])
@@ -96,3 +98,94 @@ def test_anisotropic_span_pairs_stay_small(hd):
     assert np.array_equal(off, ref.seg_off) and np.array_equal(pr, ref.prange)
     assert np.array_equal(ctrl.reshape(ref.ctrl.shape), ref.ctrl)
     assert off[-1] < 20000
+
+
+def test_patch_derivative_bounds_and_edge_flags(hd):
+    """The certification search of the surface queries rests on the bounds
+    the filling walk stores with each patch (FP32 record entries 56..61):
+    |S_s|, |S_t|, |S_ss|, |S_st|, |S_tt| (and the third partials, entries
+    62..65) of the ORIGINAL surface over the patch, in the patch's own
+    parameters, and the edges across which the surface is C1.  Checked against the oracle's derivatives (Cox-de Boor,
+    sampled on a 17 x 17 grid inside every patch), and the flags against the
+    knot multiplicities, on surfaces with C0 creases and repeated knots."""
+    hd.hd_surface_records.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                      ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
+    hd.hd_surface_records.restype = ctypes.c_int64
+    rng = np.random.default_rng(41)
+    pus, pvs, KU, KV, nets = [], [], [], [], []
+    for pu, pv, nu, nv in ((3, 2, 7, 6), (5, 4, 9, 8), (2, 3, 6, 7), (4, 4, 8, 8)):
+        U = synth.random_clamped_knots(rng, pu, nu, 0.3)  # repeated knots, creases where multiplicity = degree
+        V = synth.random_clamped_knots(rng, pv, nv, 0.3)
+        pus.append(pu)
+        pvs.append(pv)
+        KU.append(U)
+        KV.append(V)
+        nets.append(synth._sinusoid_net(rng, nu, nv))
+    ss = synth.pack_surfaces(pus, pvs, KU, KV, nets)
+    # strictly inside the patch: on a knot line the evaluator takes the next
+    # span, whose derivatives differ at a crease
+    g = np.concatenate([[1e-10], (np.arange(15) + 0.5) / 15, [1 - 1e-10]])
+    checked = 0
+    for s in range(ss.n):
+        pu, pv, nu, nv = int(ss.deg_u[s]), int(ss.deg_v[s]), int(ss.n_u[s]), int(ss.n_v[s])
+        U = np.ascontiguousarray(ss.knots_u[ss.knot_u_off[s]:ss.knot_u_off[s + 1]])
+        V = np.ascontiguousarray(ss.knots_v[ss.knot_v_off[s]:ss.knot_v_off[s + 1]])
+        P = np.ascontiguousarray(ss.cps[ss.cp_off[s]:ss.cp_off[s + 1]])
+        diag = hd.hd_box_diag(dp(P), len(P))
+
+        def smooth(K, p, n, x):
+            return bool(K[p] < x < K[n] and np.sum(K == x) < p)
+
+        for qu in range(pu, nu):
+            for qv in range(pv, nv):
+                if not (U[qu] < U[qu + 1] and V[qv] < V[qv + 1]):
+                    continue
+                cap = 4096
+                rec = np.zeros((cap, SREC32), np.float32)
+                pb = np.zeros((cap, 4))
+                err = ctypes.c_int()
+                k = hd.hd_surface_records(pu, pv, dp(U), nu, qu, dp(V), qv, dp(P), nv, 1e-3, diag,
+                                          rec.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), dp(pb), cap,
+                                          ctypes.byref(err))
+                assert 0 < k <= cap
+                for j in range(k):
+                    a0 = U[qu] + pb[j, 0] * (U[qu + 1] - U[qu])
+                    a1 = U[qu] + pb[j, 1] * (U[qu + 1] - U[qu])
+                    b0 = V[qv] + pb[j, 2] * (V[qv + 1] - V[qv])
+                    b1 = V[qv] + pb[j, 3] * (V[qv + 1] - V[qv])
+                    uu, vv = np.meshgrid(a0 + g * (a1 - a0), b0 + g * (b1 - b0), indexing="ij")
+                    uv = np.stack([uu.ravel(), vv.ravel()], 1)
+                    _, Su, Sv, Suu, Suv, Svv = O.eval_surfaces(ss, np.full(len(uv), s, np.int32), uv)
+                    wu, wv = a1 - a0, b1 - b0  # d/ds = wu d/du
+                    got = [np.linalg.norm(x, axis=1).max() for x in (Su * wu, Sv * wv, Suu * wu * wu,
+                                                                     Suv * wu * wv, Svv * wv * wv)]
+                    for m, bound in zip(got, rec[j, 56:61]):
+                        assert m <= bound * (1 + 1e-6) + 1e-12, (s, qu, qv, j, m, bound)
+                    # the bound is not loose beyond the convex-hull factor on these nets
+                    assert rec[j, 56] <= 4 * got[0] + 1e-9
+                    # third partials by central differences of the oracle's second
+                    # partials (inner samples; relative error ~1e-8)
+                    if j % 3:
+                        checked += 1
+                        continue
+                    inner = uv[(uv[:, 0] > a0 + 0.05 * wu) & (uv[:, 0] < a1 - 0.05 * wu) &
+                               (uv[:, 1] > b0 + 0.05 * wv) & (uv[:, 1] < b1 - 0.05 * wv)]
+                    hu, hv = 1e-5 * wu, 1e-5 * wv
+                    idx = np.full(len(inner), s, np.int32)
+                    ev = lambda du_, dv_: O.eval_surfaces(ss, idx, inner + np.array([du_, dv_]))
+                    up, um, vp, vm = ev(hu, 0), ev(-hu, 0), ev(0, hv), ev(0, -hv)
+                    t3 = [(up[3] - um[3]) / (2 * hu) * wu ** 3, (vp[3] - vm[3]) / (2 * hv) * wu * wu * wv,
+                          (up[5] - um[5]) / (2 * hu) * wu * wv * wv, (vp[5] - vm[5]) / (2 * hv) * wv ** 3]
+                    for fd, bound in zip(t3, rec[j, 62:66]):
+                        m3 = np.linalg.norm(fd, axis=1).max()
+                        assert m3 <= bound * (1 + 1e-4) + 1e-9, (s, qu, qv, j, m3, bound)
+                    f = int(rec[j, 61])
+                    assert bool(f & 1) == (pb[j, 0] > 0 or smooth(U, pu, nu, U[qu]))
+                    assert bool(f & 2) == (pb[j, 1] < 1 or smooth(U, pu, nu, U[qu + 1]))
+                    assert bool(f & 4) == (pb[j, 2] > 0 or smooth(V, pv, nv, V[qv]))
+                    assert bool(f & 8) == (pb[j, 3] < 1 or smooth(V, pv, nv, V[qv + 1]))
+                    checked += 1
+    assert checked > 50

@@ -1,9 +1,13 @@
-"""Benchmark: batched projection + inversion on the 4,096-curve workload.
+"""Benchmark: batched point projection / inversion on B-spline curves and
+surfaces (learned seed + FP32/BF16 bulk + FP64 finish vs plain FP64).
 
-One step = one pass of the query hot path over one batch: 1M projection and
-1M inversion queries on 4,096 random curves (degree 2-7, 8-64 control points,
-clamped non-uniform knots), decomposed into cubic Beziers at 1e-10 x diag.
-Decomposition is preprocessing: timed once and reported separately.
+Default (--workload c4): one step = 16M projection queries on the 4,096-curve
+set (degree 2-7, 8-64 control points, clamped non-uniform knots) decomposed
+into cubic Beziers at 1e-10 x diag, through the learned-seed path; the 1M
+projection + 1M inversion batch on the same curves (c2) is measured in the
+same run and reported beside it.  --workload c3 / c5: the 1,024-surface set
+and the ragged curve + surface batch.  Decomposition and the seed network's
+training are preprocessing: timed once and reported separately.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
 the host cores on a bounded sample of the same workload instead.
@@ -28,6 +32,10 @@ METRIC = "projected pts/s, learned+mixed vs plain FP64, same GB300, at 1e-9 rel.
 TOL = 1e-10
 SURF_TOL = 1e-4  # surfaces: decomposed at the paper's alpha, last Newton steps on the original patch
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one k_cull_pairs launch on the 16M-query
+# workload, from the ncu capture summarised in
+# profiles/k_cull_pairs_dram_c4_full.md (none yet: None)
+CULL_TRAFFIC_PER_LAUNCH = None
 
 
 def parse():
@@ -41,8 +49,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--curves", type=int, default=4096, help="curves in the workload")
     ap.add_argument("--queries", type=int, default=1_000_000, help="projection and inversion queries each")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c3", "c5"],
-                    help="c2: 1M projection + 1M inversion queries; c4: 16M projection queries, same curves; "
+    ap.add_argument("--workload", default="c4", choices=["c2", "c4", "c3", "c5"],
+                    help="c4 (default): 16M projection queries on the 4,096-curve set (learned seed), with the "
+                         "c2 batch measured beside it; c2: 1M projection + 1M inversion queries; "
                          "c3: 1,024 surfaces, 4M + 4M queries; c5: 65,536 cubic curves + 8,192 bicubic "
                          "surfaces, 64M Zipf-skewed queries")
     ap.add_argument("--train-curves", type=int, default=2048, help="curves of the seed network's training set")
@@ -192,21 +201,24 @@ def train_seed(args, rank, dev):
 
 def main():
     args = parse()
-    n_inv = None
-    if args.workload == "c4":  # the learned-seed configuration: projection queries only
-        args.queries = 16_000_000 if args.queries == 1_000_000 else args.queries
-        n_inv = 0
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.workload in ("c3", "c5"):
         return run_surface_workloads(args, rank, world, local)
+    # c4 (default): 16M projection queries on the 4,096-curve set, the
+    # learned-seed configuration, with the c2 batch (1M + 1M) measured beside
+    # it; c2: the 1M + 1M batch alone
+    n_proj = 16_000_000 if args.workload == "c4" else args.queries
+    n_inv = 0 if args.workload == "c4" else args.queries
+    label = {"c4": f"curve_set_{args.curves}: {n_proj} projection queries per GPU (learned seed)",
+             "c2": f"curve_set_{args.curves}: {n_proj} projection + {n_inv} inversion queries per GPU"}[args.workload]
 
     if args.impl == "reference":
         if rank != 0:
             return
-        cs, qs = build_workload(args.seed, 0, args.curves, args.queries, n_inv)
+        cs, qs = build_workload(args.seed, 0, args.curves, n_proj, n_inv)
         rates = []
         for _ in range(args.warmup):
             cpu_oracle_rate(cs, qs, budget_s=2.0, max_q=2000)
@@ -219,10 +231,9 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pts/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": "curve_set_4096: 1M projection + 1M inversion queries",
-                                                "tol_rel": TOL},
+                "data": "synthetic", "config": {"workload": label, "tol_rel": TOL},
                 "cpu_baseline": {"value": v, "unit": "pts/s", "cores": cores, "kind": "oracle",
-                                 "sample": f"{nq} queries per step (half projection, half inversion)"},
+                                 "sample": f"{nq} queries of the workload per step"},
                 "e2e": {"value": v, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -238,7 +249,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    cs, qs = build_workload(args.seed, rank, args.curves, args.queries, n_inv)
+    cs, qs = build_workload(args.seed, rank, args.curves, n_proj, n_inv)
     dc = bspl.DeviceCurves(cs, dev)
 
     # decomposition (preprocessing, timed separately)
@@ -247,47 +258,99 @@ def main():
     segs = bspl.decompose(dc, TOL)
     torch.cuda.synchronize()
     decomp_ms = 1e3 * (time.perf_counter() - t0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    mlp, train = train_seed(args, rank, dev)
+    p32 = bspl.measure_fma_peak(False)
+    p64 = bspl.measure_fma_peak(True)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16_peak = peaks["bf16_tflops"] * 1e12
+    clocks = ClockSampler(local)
+    clocks.start()
+    head = measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, full=True,
+                          peaks=(p32, p64, bf16_peak))
+    beside = None
+    if args.workload == "c4":
+        _, q2 = build_workload(args.seed, rank, args.curves, args.queries, args.queries)
+        beside = measure_curves(args, world, dist, dev, stream, flush, segs, dc, q2, mlp, full=False,
+                                peaks=(p32, p64, bf16_peak))
+    clk = clocks.stop()
+    if bspl.mlp_check() != bspl.OK:
+        raise SystemExit("a tensor-core wait timed out")
 
+    train.update(head.pop("seed_quality"))
+    out = {"metric": METRIC, "value": head["value"], "unit": "pts/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16+f32+f64 (BF16 tensor-core seed, FP32 search, FP64 finish)",
+           "data": "synthetic",
+           "config": {"workload": label, "tol_rel": TOL, "prec": "learned_mixed", "launch": head.pop("launch"),
+                      "l2": "512 MB flush between timed steps (inputs and tables also exceed L2)",
+                      "segments": int(segs.total), "decompose_ms": decomp_ms, "seed_network": train}}
+    out.update(head)
+    out["clocks"] = clk
+    if beside is not None:
+        beside.pop("seed_quality", None)
+        beside.pop("launch", None)
+        out["c2_curve_set_1M_proj_1M_inv"] = beside
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, cores, nq, el = cpu_oracle_rate(cs, qs)
+        r1, _, nq1, el1 = cpu_oracle_rate(cs, qs, budget_s=5.0, threads=1)
+        out["cpu_baseline"] = {"value": r, "unit": "pts/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{nq} queries of the same workload, {el:.1f} s",
+                               "one_core": {"value": r1, "sample": f"{nq1} queries, {el1:.1f} s"}}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, full, peaks):
+    """One curve workload: the learned step (captured once as a CUDA graph by
+    the library and replayed) against the plain FP64 path, accuracy against
+    plain on every query, and (full) the ablations, counters, stage times,
+    rooflines and the end-to-end number."""
+    import torch
+    from paper_2504_11498_gb300 import autotune, bspl
+    p32, p64, bf16_peak = peaks
     pc = torch.as_tensor(qs.proj_curve, device=dev)
     pq = torch.as_tensor(qs.proj_xyz, device=dev)
     ic = torch.as_tensor(qs.inv_curve, device=dev)
-    iq = bspl.bspl_eval_curves(dc, ic, torch.as_tensor(qs.inv_t, device=dev))
+    iq = bspl.bspl_eval_curves(dc, ic, torch.as_tensor(qs.inv_t, device=dev)) if ic.numel() else \
+        torch.empty((0, 3), dtype=torch.float64, device=dev)
+    has_inv = ic.numel() > 0
     n_step = pc.numel() + ic.numel()
     bufs_p = bspl.QueryBuffers(segs, pc.numel(), dev, learned=True)
-    bufs_i = bspl.QueryBuffers(segs, ic.numel(), dev, learned=True)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    bufs_i = bspl.QueryBuffers(segs, max(ic.numel(), 1), dev, learned=True) if has_inv else None
 
-    # the learned seed, trained before anything is timed; its error on this
-    # workload's own seeded pairs, against the midpoint seed
-    mlp, train = train_seed(args, rank, dev)
-    rows = 0
-    for qcur, qpts in ((pc, pq), (ic, iq)):
-        sp, ss, found = bspl.bspl_mlp_collect_pairs(segs, qcur, qpts, cap=1_000_000)
-        rows += found
-        if qcur is pc:
-            ystar = bspl.bspl_mlp_labels(segs, sp, ss, qpts)
-            pred = mlp.forward(bspl.bspl_mlp_features(segs, sp, ss, qpts))
-            train["heldout_seed_abs_err"] = float((pred - ystar).abs().mean().item())
-            train["heldout_midpoint_abs_err"] = float((0.5 - ystar).abs().mean().item())
-    train["eval_seed_rows_per_step"] = int(rows)
+    # the seed network's error on this workload's own seeded pairs, against
+    # the midpoint seed
+    seed_q = {}
+    sp, ss_, found = bspl.bspl_mlp_collect_pairs(segs, pc, pq, cap=1_000_000)
+    ystar = bspl.bspl_mlp_labels(segs, sp, ss_, pq)
+    pred = mlp.forward(bspl.bspl_mlp_features(segs, sp, ss_, pq))
+    seed_q["heldout_seed_abs_err"] = float((pred - ystar).abs().mean().item())
+    seed_q["heldout_midpoint_abs_err"] = float((0.5 - ystar).abs().mean().item())
+    del sp, ss_, ystar, pred
 
     # launch configuration per precision, chosen by the autotuner (untimed)
     cfg = {p: (autotune.tune_curves(segs, pc, pq, p) if args.samples == 0 else dict(samples=args.samples))
            for p in (bspl.MIXED, bspl.FP64)}
     cfg[bspl.LEARNED_MIXED] = (autotune.tune_curves(segs, pc, pq, bspl.LEARNED_MIXED, mlp=mlp)
                                if args.samples == 0 else {"occupancy": 0})
+    use_mlp = [mlp]
 
     def opts(prec, **kw):
-        return bspl.make_options(prec=prec, mlp=mlp if prec == bspl.LEARNED_MIXED else None, **cfg[prec], **kw)
+        return bspl.make_options(prec=prec, mlp=use_mlp[0] if prec == bspl.LEARNED_MIXED else None, **cfg[prec],
+                                 **kw)
 
     def step(prec, **kw):
         o = opts(prec, **kw)
         bspl.bspl_project_curves(segs, pc, pq, o, bufs_p)
-        bspl.bspl_invert_curves(segs, ic, iq, o, bufs_i)
+        if has_inv:
+            bspl.bspl_invert_curves(segs, ic, iq, o, bufs_i)
 
-    def timed(prec, steps, warmup):
+    def timed(run, steps, warmup):
         for _ in range(warmup):
-            step(prec)
+            run()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if world > 1:
             dist.barrier()
@@ -295,12 +358,56 @@ def main():
         for a, b in ev:
             flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
             a.record(stream)
-            step(prec)
+            run()
             b.record(stream)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    # the learned step captured once as a CUDA graph by the library (static
+    # buffers), then replayed: what a serving loop does
+    for _ in range(2):
+        step(bspl.LEARNED_MIXED)
+    torch.cuda.synchronize()
+    with bspl.Graph() as graph:
+        step(bspl.LEARNED_MIXED)
+    torch.cuda.synchronize()
+    ms_learned = timed(lambda: graph.replay(stream), args.steps, args.warmup)
+    res = {}
+    if full:
+        ms_direct = timed(lambda: step(bspl.LEARNED_MIXED), args.steps, args.warmup)
+        use_mlp[0] = None  # the same pipeline without its network (midpoint seed)
+        ms_no_net = timed(lambda: step(bspl.LEARNED_MIXED), args.steps, args.warmup)
+        use_mlp[0] = mlp
+        ms_mixed = timed(lambda: step(bspl.MIXED), args.steps, args.warmup)
+    ms_plain = timed(lambda: step(bspl.FP64), max(2, args.steps // 3), 2)
+
+    # accuracy of the timed paths against the plain FP64 path on every query,
+    # and of the learned path against the oracle on a sample
+    diag_p = segs.diag[pc.long()]
+    diag_i = segs.diag[ic.long()] if has_inv else None
+    step(bspl.FP64)
+    ref = (bufs_p.dist.clone(), bufs_i.dist.clone() if has_inv else None)
+    acc = {}
+    for name, prec in (("learned_mixed", bspl.LEARNED_MIXED),) + ((("mixed", bspl.MIXED),) if full else ()):
+        step(prec)
+        rel = (bufs_p.dist - ref[0]).abs() / diag_p
+        if has_inv:
+            rel = torch.cat([rel, (bufs_i.dist - ref[1]).abs() / diag_i])
+        acc[name] = {"max_rel_dist_diff_vs_plain_fp64": float(rel.max().item()),
+                     "queries_over_1e-9": int((rel > 1e-9).sum().item()),
+                     "fallback_rate": float(((bufs_p.status & bspl.Q_FALLBACK) != 0).float().mean().item())}
+
+    out = {"value": world * n_step / (ms_learned * 1e-3), "ms_per_step": ms_learned,
+           "gpu_launches": int(graph.n_kernels),
+           "graph": "learned step captured once by bspl_graph_begin/end (include/bspl_graph.h) and replayed; "
+                    "gpu_launches = its kernel nodes",
+           "plain_fp64": {"value": world * n_step / (ms_plain * 1e-3), "ms_per_step": ms_plain},
+           "speedup_learned_vs_plain": ms_plain / ms_learned, "accuracy": acc, "seed_quality": seed_q,
+           "launch": {str(k): v for k, v in cfg.items()}}
+    if not full:
+        return out
 
     def counted(prec):
         cnt = torch.zeros(bspl.NCOUNTERS, dtype=torch.int64, device=dev)
@@ -308,128 +415,40 @@ def main():
         torch.cuda.synchronize()
         return dict(zip(bspl.COUNTER_NAMES, cnt.cpu().tolist()))
 
-    # the learned step captured once as a CUDA graph (static buffers), then
-    # replayed: what a serving loop does
-    def capture(prec):
-        side = torch.cuda.Stream(device=dev)
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
-            for _ in range(2):
-                step(prec)
-        stream.wait_stream(side)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            step(prec)
-        torch.cuda.synchronize()
-        return g
-
-    graph = capture(bspl.LEARNED_MIXED)
-
-    def timed_graph(steps, warmup):
-        for _ in range(warmup):
-            graph.replay()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        for a, b in ev:
-            flush.fill_(1.0)
-            a.record(stream)
-            graph.replay()
-            b.record(stream)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
-
-    # clocks are sampled across the timed loops
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms_learned = timed_graph(args.steps, args.warmup)
-    ms_learned_direct = timed(bspl.LEARNED_MIXED, args.steps, args.warmup)
-    # the same pipeline without its network (midpoint seed): what the network
-    # costs and saves in time
-    mlp_keep = mlp
-    mlp = None
-    ms_no_net = timed(bspl.LEARNED_MIXED, args.steps, args.warmup)
-    mlp = mlp_keep
-    ms_mixed = timed(bspl.MIXED, args.steps, args.warmup)
-    ms_plain = timed(bspl.FP64, max(2, args.steps // 3), 2)
-    clk = clocks.stop()
-    if bspl.mlp_check() != bspl.OK:
-        raise SystemExit("a tensor-core wait timed out")
-
-    # accuracy of the timed paths against the plain FP64 path, every query
-    acc = {}
-    diag_p = segs.diag[pc.long()]
-    diag_i = segs.diag[ic.long()]
-    step(bspl.FP64)
-    ref = (bufs_p.dist.clone(), bufs_i.dist.clone())
-    for name, prec in (("learned_mixed", bspl.LEARNED_MIXED), ("mixed", bspl.MIXED)):
-        step(prec)
-        rel = torch.cat([(bufs_p.dist - ref[0]).abs() / diag_p, (bufs_i.dist - ref[1]).abs() / diag_i])
-        acc[name] = {"max_rel_dist_diff_vs_plain_fp64": float(rel.max().item()),
-                     "queries_over_1e-9": int((rel > 1e-9).sum().item())}
-
-    c_learned = counted(bspl.LEARNED_MIXED)
-    c_mixed = counted(bspl.MIXED)
-    c_plain = counted(bspl.FP64)
+    c_learned, c_mixed, c_plain = counted(bspl.LEARNED_MIXED), counted(bspl.MIXED), counted(bspl.FP64)
 
     # per-stage device time of the learned path (events recorded by the
-    # library at its stage boundaries, both calls of a step summed)
+    # library at its stage boundaries, every call of a step summed)
     def stage_ms(steps):
         tot = np.zeros(bspl.NSTAGE_EVENTS - 1)
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(bspl.NSTAGE_EVENTS)] for _ in range(2)]
         for _ in range(steps):
             flush.fill_(1.0)
             bspl.bspl_project_curves(segs, pc, pq, opts(bspl.LEARNED_MIXED, stage_events=evs[0]), bufs_p)
-            flush.fill_(1.0)
-            bspl.bspl_invert_curves(segs, ic, iq, opts(bspl.LEARNED_MIXED, stage_events=evs[1]), bufs_i)
+            if has_inv:
+                flush.fill_(1.0)
+                bspl.bspl_invert_curves(segs, ic, iq, opts(bspl.LEARNED_MIXED, stage_events=evs[1]), bufs_i)
             torch.cuda.synchronize()
-            for e in evs:
+            for e in evs[:2 if has_inv else 1]:
                 tot += [e[k].elapsed_time(e[k + 1]) for k in range(bspl.NSTAGE_EVENTS - 1)]
         return dict(zip(bspl.STAGE_NAMES, (tot / steps).tolist()))
 
     st_ms = stage_ms(max(3, args.steps // 2))
+    n_calls = 2 if has_inv else 1
 
-    # the grid kernel alone (mixed), pre-grouped inputs, events around launches
-    op = torch.as_tensor(np.argsort(qs.proj_curve, kind="stable"), device=dev)
-    oi = torch.as_tensor(np.argsort(qs.inv_curve, kind="stable"), device=dev)
-    spc, spq, sic, siq = pc[op], pq[op], ic[oi], iq[oi]
-
-    def kernel_ms(prec, steps):
-        o = bspl.make_options(prec=prec, sort_queries=0, **cfg[prec])
-        tot = 0.0
-        for it in range(steps + 2):
-            flush.fill_(1.0)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            ev[0].record(stream)
-            bspl.bspl_project_curves(segs, spc, spq, o, bufs_p)
-            ev[1].record(stream)
-            flush.fill_(1.0)
-            ev[2].record(stream)
-            bspl.bspl_invert_curves(segs, sic, siq, o, bufs_i)
-            ev[3].record(stream)
-            torch.cuda.synchronize()
-            if it >= 2:
-                tot += ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
-        return tot / steps
-
-    kms_mixed = kernel_ms(bspl.MIXED, max(3, args.steps // 2))
-
-    # end to end through the public API with pinned host buffers
-    h_in = [x.cpu().pin_memory() for x in (pc, pq, ic, iq)]
-    h_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in
-             (bufs_p.param, bufs_p.dist, bufs_p.status, bufs_i.param, bufs_i.dist, bufs_i.status)]
+    # end to end through the public API with pinned host buffers: inputs into
+    # the graph's static buffers, replay, results back
+    h_in = [x.cpu().pin_memory() for x in ((pc, pq, ic, iq) if has_inv else (pc, pq))]
+    outs = [bufs_p.param, bufs_p.dist, bufs_p.status] + \
+        ([bufs_i.param, bufs_i.dist, bufs_i.status] if has_inv else [])
+    h_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in outs]
+    dins = (pc, pq, ic, iq) if has_inv else (pc, pq)
 
     def e2e_step():
-        # inputs into the graph's static buffers, replay, results back
-        for d, h in zip((pc, pq, ic, iq), h_in):
+        for d, h in zip(dins, h_in):
             d.copy_(h, non_blocking=True)
-        graph.replay()
-        for h, d in zip(h_out, (bufs_p.param, bufs_p.dist, bufs_p.status, bufs_i.param, bufs_i.dist,
-                                bufs_i.status)):
+        graph.replay(stream)
+        for h, d in zip(h_out, outs):
             h.copy_(d, non_blocking=True)
 
     for _ in range(2):
@@ -447,91 +466,81 @@ def main():
     d2h = sum(x.numel() * x.element_size() for x in h_out)
 
     # max over ranks; every rank processed its own n_step queries
-    (ms_learned, ms_mixed, ms_plain, ms_e2e), total_q = combine_over_ranks(
-        [ms_learned, ms_mixed, ms_plain, ms_e2e], n_step, world, dist if world > 1 else None, dev)
+    (ms_learned, ms_direct, ms_no_net, ms_mixed, ms_plain, ms_e2e), total_q = combine_over_ranks(
+        [ms_learned, ms_direct, ms_no_net, ms_mixed, ms_plain, ms_e2e], n_step, world,
+        dist if world > 1 else None, dev)
 
     # rooflines.  ALU work from device counters with per-unit figures: 12
-    # FP32 flops per box test, 110 per pair classification (E in Bernstein
-    # form with its rounding bound), 15 per grid sample, 45 per Newton
-    # iteration; the MLP 2 (16*128 + 2*128*128 + 128) = 69,888 flops per row.
-    p32 = bspl.measure_fma_peak(False)
-    p64 = bspl.measure_fma_peak(True)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    bf16_peak = peaks["bf16_tflops"] * 1e12
-    cull_flops = 12 * (c_learned["grp_tested"] + c_learned["seg_tested"]) + 110 * c_learned["candidates"]
+    # flops per box test, 110 per pair classification (E in Bernstein form
+    # with its rounding bound), 15 per grid sample, 45 per Newton iteration;
+    # the seed network 2 (16*128 + 2*128*128 + 128) = 69,888 flops per row.
+    rows = c_learned["candidates"]  # every pair the culling emitted; the seeded ones run the network
+    seeded = int(train_rows(segs, pc, pq, ic, iq, has_inv))
+    cull_flops = 12 * (c_learned["grp_tested"] + c_learned["seg_tested"]) + 110 * rows
     t_cull = st_ms["cull"] * 1e-3
-    rows = train["eval_seed_rows_per_step"]
-    mlp_flops = 69888 * rows
-    t_seed = st_ms["seed"] * 1e-3
+    mlp_flops = 69888 * seeded
+    t_seed = max(st_ms["seed"], 1e-6) * 1e-3
     dominant = max(st_ms, key=st_ms.get)
     mlp_line = {"bound": "tensor", "achieved": mlp_flops / t_seed / 1e12, "peak": bf16_peak / 1e12,
-                "unit": "TFLOP/s", "frac": mlp_flops / t_seed / bf16_peak, "rows_per_step": rows,
+                "unit": "TFLOP/s", "frac": mlp_flops / t_seed / bf16_peak, "rows_per_step": seeded,
                 "ms_per_step": st_ms["seed"], "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    cull_box_flops = 12 * (c_learned["grp_tested"] + c_learned["seg_tested"])
     cull_line = {"bound": "alu", "achieved": cull_flops / t_cull / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
                  "frac": cull_flops / t_cull / p32, "ms_per_step": st_ms["cull"],
+                 "frac_box_tests_only": cull_box_flops / t_cull / p32,
                  "peak_source": "FP32 FMA-chain microbenchmark on this GPU (of measured)"}
-    roofline = dict(cull_line if dominant == "cull" else (mlp_line if dominant == "seed" else cull_line))
-    # DRAM bytes of the dominant kernel per step: ncu capture of the same
-    # kernel on the 1,024-curve, 250k + 250k-query case (247.6 MB per
-    # launch), scaled by the units processed (4x queries and tables) and the
-    # two launches of a step
-    n_calls = 2 if ic.numel() > 0 else 1
-    traffic = n_calls * 4 * 247.56e6 * (pc.numel() / 1_000_000) if dominant == "cull" else None
-    roofline.update({"kernel": "k_cull_pairs" if roofline["bound"] == "alu" else "k_mlp_fused",
-                     "traffic": traffic, "traffic_unit": f"bytes per step ({n_calls} launch(es))",
-                     "stages_ms_per_step": st_ms, "dominant_stage": dominant,
-                     "mlp_seed_kernel": mlp_line})
-
-    # the whole learned step: counted FP32 flops / FP32 peak + FP64 flops /
-    # FP64 peak + MLP flops / BF16 peak, per second of the timed step
+    roofline = dict(cull_line if dominant != "seed" else mlp_line)
+    roofline.update({"kernel": "k_cull_pairs" if dominant != "seed" else "k_mlp_fused",
+                     "traffic": (CULL_TRAFFIC_PER_LAUNCH * n_calls
+                                 if dominant == "cull" and CULL_TRAFFIC_PER_LAUNCH is not None else None),
+                     "traffic_unit": f"DRAM bytes per step ({n_calls} launch(es), ncu at full size)",
+                     "stages_ms_per_step": st_ms, "dominant_stage": dominant, "mlp_seed_kernel": mlp_line})
     f32_step = cull_flops + 45 * c_learned["newton32_iters"]
     f64_step = 60 * c_learned["newton"] + 45 * max(0, c_learned["newton64_iters"] - 2 * c_learned["newton"])
     t_step = ms_learned * 1e-3
     roofline["step"] = {"frac": f32_step / t_step / p32 + f64_step / t_step / p64 + mlp_flops / t_step / bf16_peak,
                         "fp32_flops": f32_step, "fp64_flops": f64_step, "bf16_flops": mlp_flops,
                         "note": "sum of the three pipes' fractions over the timed step (ms_per_step)"}
-
+    # the plain FP64 path: FP64 flops from its counters over the FP64 FMA
+    # peak (box tests, S grid samples per candidate segment, Newton
+    # iterations), over its whole timed step
+    S64 = cfg[bspl.FP64]["samples"]
+    f64_plain = 12 * (c_plain["grp_tested"] + c_plain["seg_tested"]) + 15 * S64 * c_plain["candidates"] + \
+        45 * c_plain["newton64_iters"]
+    roofline["plain_fp64"] = {"kernel": "k_query_curves<double>", "bound": "alu",
+                              "achieved": f64_plain / (ms_plain * 1e-3) / 1e12, "peak": p64 / 1e12,
+                              "unit": "TFLOP/s (FP64)", "frac": f64_plain / (ms_plain * 1e-3) / p64,
+                              "fp64_flops": f64_plain, "ms_per_step": ms_plain,
+                              "peak_source": "FP64 FMA-chain microbenchmark on this GPU (of measured)"}
     S = cfg[bspl.MIXED]["samples"]
     f32m = 12 * (c_mixed["grp_tested"] + c_mixed["seg_tested"]) + 15 * S * c_mixed["candidates"] + \
         45 * c_mixed["newton32_iters"]
     f64m = 45 * c_mixed["newton64_iters"]
-    eq_m = (f32m + f64m * p32 / p64) / (kms_mixed * 1e-3)
-    roofline["mixed_grid_kernel"] = {"kernel": "k_query_curves<float>", "bound": "alu", "achieved": eq_m / 1e12,
-                                     "peak": p32 / 1e12, "unit": "TFLOP/s (FP32-equivalent)", "frac": eq_m / p32,
-                                     "ms_per_step": kms_mixed, "fp64_peak_tflops": p64 / 1e12}
+    roofline["mixed_grid"] = {"kernel": "k_query_curves<float>", "bound": "alu",
+                              "achieved": (f32m + f64m * p32 / p64) / (ms_mixed * 1e-3) / 1e12, "peak": p32 / 1e12,
+                              "unit": "TFLOP/s (FP32-equivalent)",
+                              "frac": (f32m + f64m * p32 / p64) / (ms_mixed * 1e-3) / p32, "ms_per_step": ms_mixed}
+    out.update({"value": total_q / (ms_learned * 1e-3), "ms_per_step": ms_learned,
+                "learned_direct": {"value": total_q / (ms_direct * 1e-3), "ms_per_step": ms_direct},
+                "learned_without_network": {"value": total_q / (ms_no_net * 1e-3), "ms_per_step": ms_no_net,
+                                            "note": "same pipeline, seed u = 1/2 instead of the network"},
+                "mixed_grid": {"value": total_q / (ms_mixed * 1e-3), "ms_per_step": ms_mixed},
+                "plain_fp64": {"value": total_q / (ms_plain * 1e-3), "ms_per_step": ms_plain},
+                "speedup_learned_vs_plain": ms_plain / ms_learned, "speedup_mixed_vs_plain": ms_plain / ms_mixed,
+                "e2e": {"value": total_q / (ms_e2e * 1e-3), "unit": "pts/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "roofline": roofline, "peaks_measured": {"fp32_tflops": p32 / 1e12, "fp64_tflops": p64 / 1e12},
+                "counters": {"learned_mixed": c_learned, "mixed": c_mixed, "plain_fp64": c_plain}})
+    return out
 
-    out = {"metric": METRIC, "value": total_q / (ms_learned * 1e-3), "unit": "pts/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None,
-           "dtype": "bf16+f32+f64 (BF16 tensor-core seed, FP32 search, FP64 finish)", "data": "synthetic",
-           "config": {"workload": f"curve_set_{args.curves}: {pc.numel()} projection + {ic.numel()} inversion "
-                                  "queries per GPU",
-                      "tol_rel": TOL, "prec": "learned_mixed", "launch": {str(k): v for k, v in cfg.items()},
-                      "l2": "512 MB flush between timed steps", "segments": int(segs.total),
-                      "decompose_ms": decomp_ms, "seed_network": train},
-           "graph": "learned step captured once as a CUDA graph and replayed",
-           "learned_direct": {"value": total_q / (ms_learned_direct * 1e-3), "ms_per_step": ms_learned_direct},
-           "learned_without_network": {"value": total_q / (ms_no_net * 1e-3), "ms_per_step": ms_no_net,
-                                       "note": "same pipeline, seed u = 1/2 instead of the network"},
-           "mixed_grid": {"value": total_q / (ms_mixed * 1e-3), "ms_per_step": ms_mixed},
-           "plain_fp64": {"value": total_q / (ms_plain * 1e-3), "ms_per_step": ms_plain},
-           "speedup_learned_vs_plain": ms_plain / ms_learned, "speedup_mixed_vs_plain": ms_plain / ms_mixed,
-           "accuracy": acc,
-           "e2e": {"value": total_q / (ms_e2e * 1e-3), "unit": "pts/s", "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": d2h},
-           "gpu_launches": 26, "roofline": roofline, "clocks": clk,
-           "counters": {"learned_mixed": c_learned, "mixed": c_mixed, "plain_fp64": c_plain}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, cores, nq, el = cpu_oracle_rate(cs, qs)
-        r1, _, nq1, el1 = cpu_oracle_rate(cs, qs, budget_s=5.0, threads=1)
-        out["cpu_baseline"] = {"value": r, "unit": "pts/s", "cores": cores, "kind": "oracle",
-                               "sample": f"{nq} queries of the same workload (half projection, half inversion), "
-                                         f"{el:.1f} s",
-                               "one_core": {"value": r1, "sample": f"{nq1} queries, {el1:.1f} s"}}
-    if rank == 0:
-        print(json.dumps(out))
-    if world > 1:
-        dist.destroy_process_group()
+
+def train_rows(segs, pc, pq, ic, iq, has_inv):
+    """Seeded pairs (rows through the network) of one learned step."""
+    from paper_2504_11498_gb300 import bspl
+    n = bspl.bspl_mlp_collect_pairs(segs, pc, pq, cap=0)[2]
+    if has_inv:
+        n += bspl.bspl_mlp_collect_pairs(segs, ic, iq, cap=0)[2]
+    return n
 
 
 # ------------------------------------------------- surfaces and ragged batch
@@ -683,9 +692,33 @@ def run_surface_workloads(args, rank, world, local):
             dist.barrier()
         return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
+    # the fast step captured once as a CUDA graph by the library, replayed
+    step(True)
+    torch.cuda.synchronize()
+    with bspl.Graph() as graph:
+        step(True)
+    torch.cuda.synchronize()
+
+    def timed_graph(steps, warmup):
+        for _ in range(warmup):
+            graph.replay(stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            graph.replay(stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
     clocks = ClockSampler(local)
     clocks.start()
-    ms_fast = timed(True, args.steps, args.warmup)
+    ms_fast = timed_graph(args.steps, args.warmup)
     ms_plain = timed(False, max(2, args.steps // 3), 2)
     per_call = {name: timed(True, max(2, args.steps // 2), 1, only=name) for name, *_ in calls}
     clk = clocks.stop()
@@ -719,7 +752,7 @@ def run_surface_workloads(args, rank, world, local):
         for name, _, _, qi, qx in calls:
             qi.copy_(h_in[name][0], non_blocking=True)
             qx.copy_(h_in[name][1], non_blocking=True)
-        step(True)
+        graph.replay(stream)
         for name in bufs:
             for h, d in zip(h_out[name], (bufs[name].param, bufs[name].dist, bufs[name].status)):
                 h.copy_(d, non_blocking=True)
@@ -766,10 +799,6 @@ def run_surface_workloads(args, rank, world, local):
            "l2": "512 MB flush between timed steps", "patches": int(ssegs.total), "decompose_surfaces_ms": dec_s}
     if has_c:
         cfg.update({"segments": int(csegs.total), "decompose_curves_ms": dec_c, "seed_network": train})
-    # per call: counting sort (histogram, scan, scatter; the scan is one
-    # launch up to 2,048 splines, three above) and the query kernel; the
-    # learned curve call 13
-    launches = {"c3": 2 * 4, "c5": 2 * 6 + 2 * 13}[args.workload]
     out = {"metric": METRIC, "value": total_q / (ms_fast * 1e-3), "unit": "pts/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fast, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -779,7 +808,9 @@ def run_surface_workloads(args, rank, world, local):
            "speedup_vs_plain": ms_plain / ms_fast, "accuracy": acc,
            "e2e": {"value": total_q / (ms_e2e * 1e-3), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
-           "gpu_launches": launches, "roofline": roofline, "clocks": clk, "counters": cnt}
+           "gpu_launches": int(graph.n_kernels),
+           "graph": "fast step captured once by bspl_graph_begin/end and replayed; gpu_launches = its kernel nodes",
+           "roofline": roofline, "clocks": clk, "counters": cnt}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, nq, el = cpu_oracle_surface_rate(cs, cq, ss, sq)
         out["cpu_baseline"] = {"value": r, "unit": "pts/s", "cores": cores, "kind": "oracle",

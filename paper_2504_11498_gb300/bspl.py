@@ -73,7 +73,8 @@ class bspl_mlp(C.Structure):
     _fields_ = [("params", C.c_void_p), ("wbf16", C.c_void_p)]
 
 
-EXPORTS = ["bspl_project_curves_noalloc", "bspl_measure_fma_peak", "bspl_workspace_bytes", "bspl_decompose", "bspl_project_curves", "bspl_invert_curves",
+EXPORTS = ["bspl_graph_begin", "bspl_graph_end", "bspl_graph_launch", "bspl_graph_destroy",
+           "bspl_project_curves_noalloc", "bspl_measure_fma_peak", "bspl_workspace_bytes", "bspl_decompose", "bspl_project_curves", "bspl_invert_curves",
            "bspl_project_surfaces", "bspl_invert_surfaces", "bspl_eval_curves", "bspl_eval_surfaces",
            "bspl_status_string"]
 
@@ -110,6 +111,14 @@ def lib():
             L.bspl_project_curves_noalloc.restype = st
             L.bspl_project_curves_noalloc.argtypes = [C.POINTER(bspl_segments), i64, vp, vp, C.POINTER(bspl_options),
                                                       vp, vp, vp, vp]
+            L.bspl_graph_begin.restype = st
+            L.bspl_graph_begin.argtypes = [vp]
+            L.bspl_graph_end.restype = st
+            L.bspl_graph_end.argtypes = [vp, C.POINTER(vp), C.POINTER(i64)]
+            L.bspl_graph_launch.restype = st
+            L.bspl_graph_launch.argtypes = [vp, vp]
+            L.bspl_graph_destroy.restype = None
+            L.bspl_graph_destroy.argtypes = [vp]
             L.bspl_measure_fma_peak.restype = C.c_int
             L.bspl_measure_fma_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, vp]
             mp = C.POINTER(bspl_mlp)
@@ -382,6 +391,46 @@ def bspl_project_curves_noalloc(segs, q_curve, q_xyz, opts=None, out=None, strea
                                            _stream(stream))
     _check(rc, "bspl_project_curves_noalloc")
     return QueryResult(t, d, st)
+
+
+class Graph:
+    """Query calls captured once as a CUDA graph (include/bspl_graph.h) and
+    replayed: ``with Graph(stream) as g: <calls on that stream>`` then
+    ``g.replay()``.  ``n_kernels`` is the number of kernel launches a replay
+    makes.  The calls must use preallocated buffers (a replay reads and writes
+    the same device addresses)."""
+
+    def __init__(self, stream=None):
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.exec = C.c_void_p(0)
+        self.n_kernels = 0
+        self._ctx = None
+
+    def __enter__(self):
+        self._ctx = torch.cuda.stream(self.stream)
+        self._ctx.__enter__()
+        _check(lib().bspl_graph_begin(_stream(self.stream)), "bspl_graph_begin")
+        return self
+
+    def __exit__(self, exc_type, exc, tb):
+        n = C.c_int64(0)
+        rc = lib().bspl_graph_end(_stream(self.stream), C.byref(self.exec), C.byref(n))
+        self._ctx.__exit__(exc_type, exc, tb)
+        if exc_type is None:
+            _check(rc, "bspl_graph_end")
+        self.n_kernels = int(n.value)
+        return False
+
+    def replay(self, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().bspl_graph_launch(self.exec, _stream(s)), "bspl_graph_launch")
+
+    def __del__(self):
+        try:
+            if self.exec and self.exec.value:
+                lib().bspl_graph_destroy(self.exec)
+        except Exception:
+            pass
 
 
 def bspl_eval_curves(curves: DeviceCurves, q_curve, t, stream=None):

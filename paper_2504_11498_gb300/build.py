@@ -18,7 +18,7 @@ LIB = os.path.join(OUT, "libbspl.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["api.cu", "decompose.cu", "query_curves.cu", "query_surfaces.cu", "eval.cu", "scan.cu", "mlp.cu", "query_learned.cu",
-           "measure.cu", "noalloc.cu"]
+           "measure.cu", "noalloc.cu", "graph.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 EXTRA = {"decompose.cu": ["-fmad=false"]}
@@ -35,7 +35,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "bspl.h")]
+    inc = os.path.join(ROOT, "include")
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(inc, f) for f in os.listdir(inc)]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

@@ -116,7 +116,9 @@ typedef struct {
  *           [cap][4]     (u0, u1, v0, v1) of each patch
  *   diag    [n]          diagonal of each spline's control-point box (NaN
  *                        for a spline that failed validation)
- *   rec64/rec32          per-segment search records (BSPL_*REC* above)
+ *   rec64/rec32          per-segment search records (BSPL_*REC* above); rec32
+ *                        and grp32 must be 16-byte aligned (the query kernels
+ *                        stage them into shared memory by bulk copies)
  *   grp_off [n+1], grp64/grp32: culling groups of BSPL_GROUP consecutive
  *                        segments (box of the group + a point on it);
  *                        grp_capacity >= n + capacity / BSPL_GROUP + 1 always suffices

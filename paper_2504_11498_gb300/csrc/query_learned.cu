@@ -137,11 +137,13 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
     __shared__ uint8_t s_pkind[kWarps][kEmitCap];
     __shared__ int32_t s_qi[kWarps][kQPW];
     __shared__ float s_ub[kWarps][kQPW];
+    // level 1 stages group records here; level 2 reuses it as one of the two
+    // buffers of segment records (BSPL_GROUP x BSPL_CREC32 floats = the same 3 KB)
     __shared__ __align__(128) float s_grp[kWarps][kGrpChunk * BSPL_GREC32];
-    __shared__ int s_sv[kWarps][kSurvCap];
-    __shared__ float s_svlb[kWarps][kSurvCap];
-    __shared__ uint8_t s_svslot[kWarps][kSurvCap];
-    __shared__ __align__(8) uint64_t s_bar[kWarps];
+    __shared__ __align__(128) float s_seg2[kWarps][BSPL_GROUP * BSPL_CREC32];
+    __shared__ int s_sv[kWarps][kSurvCap];       // surviving groups of the batch, in order
+    __shared__ unsigned s_svm[kWarps][kSurvCap]; // the query slots that kept each
+    __shared__ __align__(8) uint64_t s_bar[kWarps][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* cseg = s_seg[wid];
     float* clb = s_lb[wid];
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
     uint8_t* pkind = s_pkind[wid];
     int32_t* qis = s_qi[wid];
     float* grs = s_grp[wid];
-    uint64_t* bar = &s_bar[wid];
+    uint64_t* bar = &s_bar[wid][0];
     const int64_t qbase = ((int64_t)blockIdx.x * kWarps + wid) * kQPW;
     if (qbase >= P.n_q) return;
     const int nslots = (int)min((int64_t)kQPW, P.n_q - qbase);
@@ -165,10 +167,11 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
 
     if (lane == 0) {
         tc::mbar_init(bar, 1);
+        tc::mbar_init(bar + 1, 1);
         tc::fence_mbar_init();
     }
     __syncwarp();
-    uint32_t phase = 0;
+    uint32_t phase = 0, phase1 = 0;  // parities of the two barriers
 
     // this lane's query (lane = slot)
     float qx = 0.f, qy = 0.f, qz = 0.f, eps = 0.f;
@@ -238,14 +241,12 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
                 const bool keep = in_run && lb <= ubs;
                 const unsigned m = __ballot_sync(kFull, keep);
                 if (!m) continue;
-                if (nsv + __popc(m) <= kSurvCap) {
-                    if (keep) {
-                        const int e = nsv + __popc(m & lt);
-                        s_sv[wid][e] = (int)(g0 + cg + k);
-                        s_svlb[wid][e] = lb;
-                        s_svslot[wid][e] = (uint8_t)lane;
+                if (nsv < kSurvCap) {
+                    if (lane == 0) {
+                        s_sv[wid][nsv] = (int)(g0 + cg + k);
+                        s_svm[wid][nsv] = m;
                     }
-                    nsv += __popc(m);
+                    ++nsv;
                 } else {
                     sv_over |= m;
                 }
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
             lbs = box_d2(E.b, sx, sy, sz);
             ups = pt_d2(E.p, sx, sy, sz);
         }
-        n_seg += (unsigned long long)E.nseg;
+        if (lane == E.sl) n_seg += (unsigned long long)E.nseg;
         const float m = warp_min(ups);
         if (lane == sl && m < ub) {
             ub = m;
@@ -413,13 +414,64 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
         fetch(sl, g, E);
         scan(E);
     };
+    // level 2 over the surviving groups, in list order: a group's segment
+    // records are bulk-copied into shared memory once (two buffers: the copy
+    // of the next group is in flight while this one is scanned), then every
+    // query slot that kept the group scans it warp-cooperatively, one segment
+    // per lane, reading the records from shared memory.
     if (nsv > 0) {
-        Ent cur, nxt;
-        fetch(s_svslot[wid][0], s_sv[wid][0], cur);
-        for (int e = 0; e < nsv; ++e) {
-            if (e + 1 < nsv) fetch(s_svslot[wid][e + 1], s_sv[wid][e + 1], nxt);
-            if (s_svlb[wid][e] <= __shfl_sync(kFull, ubs_l, cur.sl)) scan(cur);
-            cur = nxt;
+        float* buf[2] = { s_grp[wid], s_seg2[wid] };
+        // segment range of list entry j (the curve of the first query that kept it)
+        auto range = [&](int j, int64_t& ss, int& ns) {
+            const int g = s_sv[wid][j];
+            const int sl = __ffs(s_svm[wid][j]) - 1;
+            const int64_t s0 = __shfl_sync(kFull, s0l, sl), s1 = __shfl_sync(kFull, s1l, sl);
+            const int64_t g0 = __shfl_sync(kFull, g0l, sl);
+            ss = s0 + ((int64_t)g - g0) * BSPL_GROUP;
+            ns = (int)min((int64_t)BSPL_GROUP, s1 - ss);
+        };
+        auto issue = [&](int j, int b) {
+            int64_t ss;
+            int ns;
+            range(j, ss, ns);
+            __syncwarp();  // every lane is done with the buffer's previous contents
+            if (lane == 0) {
+                tc::fence_async_smem();
+                tc::bulk_load(buf[b], rec + (int64_t)RW * ss, (uint32_t)(ns * RW * sizeof(float)), bar + b);
+            }
+        };
+        issue(0, 0);
+        for (int j = 0; j < nsv; ++j) {
+            const int b = j & 1;
+            if (j + 1 < nsv) issue(j + 1, b ^ 1);
+            int64_t ss;
+            int ns;
+            range(j, ss, ns);
+            const bool ok = tc::mbar_wait(bar + b, b ? phase1 : phase, kCopyWaitNs);
+            if (b) phase1 ^= 1;
+            else phase ^= 1;
+            if (!ok && lane == 0) atomicExch(&g_copy_timeout, 1);
+            const float* src = __all_sync(kFull, ok) ? buf[b] : rec + (int64_t)RW * ss;
+            // this lane's segment of the group
+            Ent E;
+            E.s = ss + lane;
+            E.nseg = ns;
+            E.valid = lane < ns;
+            if (E.valid) {
+                const float* r = src + RW * lane;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) E.b[k] = r[k];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) E.p[k] = r[6 + k];
+            }
+            // the slots that kept the group, if its box still passes their bound
+            const float* gr = grp + (int64_t)GW * s_sv[wid][j];
+            const bool pass = ((s_svm[wid][j] >> lane) & 1u) && box_d2(gr, qx, qy, qz) <= ubs_l;
+            for (unsigned m = __ballot_sync(kFull, pass); m; m &= m - 1) {
+                E.sl = __ffs(m) - 1;
+                scan(E);
+            }
+            __syncwarp();
         }
     }
     // queries whose surviving groups did not fit the list: scan all groups
@@ -450,6 +502,7 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
         for (int o = 16; o > 0; o >>= 1) {
             n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
             n_grp += __shfl_xor_sync(kFull, n_grp, o);
+            n_seg += __shfl_xor_sync(kFull, n_seg, o);
         }
         if (lane == 0) {
             atomicAdd(P.counters + BSPL_CNT_QUERIES, (unsigned long long)nslots);

@@ -663,12 +663,26 @@ def run_surface_workloads(args, rank, world, local):
     n_step = sum(qi.numel() for _, _, _, qi, _ in calls)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    # launch configuration per call and precision, chosen by the autotuner
+    # (untimed; curves: occupancy and FP32 steps, surfaces: sample tile and
+    # FP32 steps)
+    from paper_2504_11498_gb300 import autotune
+    tuned = {}
+    for name, fn, sg, qi, qx in calls:
+        for fast in (True, False):
+            if name.startswith("curve"):
+                prec = bspl.LEARNED_MIXED if fast else bspl.FP64
+                tuned[(name, fast)] = autotune.tune_curves(sg, qi, qx, prec, mlp=mlp if fast else None)
+            else:
+                tuned[(name, fast)] = autotune.tune_surfaces(sg, qi, qx, bspl.MIXED if fast else bspl.FP64)
+
     def opts(name, fast, **kw):
+        cfg_ = dict(tuned[(name, fast)], **kw)
         if not fast:
-            return bspl.make_options(prec=bspl.FP64, **kw)
+            return bspl.make_options(prec=bspl.FP64, **cfg_)
         if name.startswith("curve"):
-            return bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp, **kw)
-        return bspl.make_options(prec=bspl.MIXED, **kw)
+            return bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp, **cfg_)
+        return bspl.make_options(prec=bspl.MIXED, **cfg_)
 
     def step(fast, only=None, **kw):
         for name, fn, sg, qi, qx in calls:
@@ -795,6 +809,8 @@ def run_surface_workloads(args, rank, world, local):
                 "note": "counted FP32 flops only (Newton iterations of the surface kernel uncounted): a lower bound"}
 
     cfg = {"workload": label, "tol_rel_curves": TOL, "tol_rel_surfaces": SURF_TOL,
+           "launch": {f"{k[0]}|{'fast' if k[1] else 'plain'}": v for k, v in tuned.items()},
+           "schedule": "queries grouped heaviest spline first; persistent work-stealing launches",
            "prec": "surfaces mixed" + (", curves learned_mixed" if has_c else ""),
            "l2": "512 MB flush between timed steps", "patches": int(ssegs.total), "decompose_surfaces_ms": dec_s}
     if has_c:

@@ -16,8 +16,8 @@
  *   - all array pointers are DEVICE pointers owned by the caller unless stated
  *     otherwise; the library never allocates or frees device memory;
  *   - every call is asynchronous on the given stream, except bspl_decompose,
- *     which synchronises that stream twice (after validating the splines and
- *     after counting the segments);
+ *     which synchronises that stream (after validating the splines, after
+ *     counting the segments, and around computing spline_rank);
  *   - argument errors that the host can see (NULL pointers, negative sizes,
  *     workspace too small) return BSPL_EINVAL before anything is launched;
  *     per-query data problems (spline index out of range, non-finite point)
@@ -159,6 +159,11 @@ typedef struct {
     int64_t n_cp_total;  /* in: cp_off[n] of the decomposed set (sizes the slot arrays) */
     double tol_rel;      /* out: tolerance the tables were built with */
     float* patch_net32;  /* surfaces: [capacity][BSPL_SPAN_NET], see above */
+    int32_t* spline_rank;/* optional [n]: rank of each spline by descending piece
+                            count (ties by index), written by the filling pass;
+                            the query calls then group queries heaviest spline
+                            first, which their work-stealing launch hands out
+                            first.  NULL: queries grouped by spline index. */
 } bspl_segments;
 
 /* Query options.  Zero fields take the defaults given. */

@@ -55,7 +55,7 @@ class bspl_segments(C.Structure):
                 ("rec64", C.c_void_p), ("rec32", C.c_void_p), ("grp_off", C.c_void_p), ("grp64", C.c_void_p),
                 ("grp32", C.c_void_p), ("patch_span", C.c_void_p), ("patch_box", C.c_void_p),
                 ("span_net", C.c_void_p), ("span_net32", C.c_void_p), ("n_cp_total", C.c_int64),
-                ("tol_rel", C.c_double), ("patch_net32", C.c_void_p)]
+                ("tol_rel", C.c_double), ("patch_net32", C.c_void_p), ("spline_rank", C.c_void_p)]
 
 
 class bspl_options(C.Structure):
@@ -231,6 +231,7 @@ class Segments:
             self.rec64 = z((cap, CREC64), f64)
             self.rec32 = z((cap, CREC32), f32)
             self.patch_span = self.patch_box = self.span_net = self.span_net32 = self.patch_net32 = None
+        self.spline_rank = z(max(n, 1), torch.int32)
         self.grp64 = z((self.grp_capacity, GREC64), f64)
         self.grp32 = z((self.grp_capacity, GREC32), f32)
         self.n_cp_total = splines.n_cp_total
@@ -244,7 +245,7 @@ class Segments:
                              _ptr(self.rec32), _ptr(self.grp_off), _ptr(self.grp64), _ptr(self.grp32),
                              _ptr(self.patch_span), _ptr(self.patch_box), _ptr(self.span_net), _ptr(self.span_net32),
                              self.n_cp_total,
-                             self.tol_rel, _ptr(self.patch_net32))
+                             self.tol_rel, _ptr(self.patch_net32), _ptr(self.spline_rank))
 
     def view(self):
         """Host copies (seg_off, ctrl, prange) trimmed to the segment count."""

@@ -62,4 +62,30 @@ bspl_status eval_surfaces(const bspl_surfaces* c, int64_t n_q, const int32_t* qs
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Blocks of a persistent, work-stealing launch: as many as can be resident
+// on the GPU at once (SMs x blocks per SM for this kernel, threads and
+// dynamic shared memory), but no more than the batches need.
+template <class K>
+inline int persistent_blocks(K kernel, int threads, size_t smem, int64_t blocks_needed)
+{
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+    const int64_t g = (int64_t)(nsm > 0 ? nsm : 1) * (occ > 0 ? occ : 1);
+    return (int)(blocks_needed < g ? (blocks_needed > 0 ? blocks_needed : 1) : g);
+}
+
+// The next batch of a warp in a work-stealing launch: lane 0 takes it from
+// the counter (each batch is handed out once; the counter only grows, so the
+// loop that calls this ends once it passes the batch count).  Without a
+// counter the warp takes its own batch once.
+__device__ __forceinline__ int64_t next_batch(unsigned long long* work, int64_t own, int64_t nbatch, int& round)
+{
+    if (!work) return round++ == 0 ? own : nbatch;
+    unsigned long long b = 0;
+    if ((threadIdx.x & 31) == 0) b = atomicAdd(work, 1ull);
+    return (int64_t)__shfl_sync(0xffffffffu, b, 0);
+}
+
 }  // namespace bspl

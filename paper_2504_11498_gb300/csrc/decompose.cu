@@ -16,6 +16,9 @@
 // offset.
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "bspl_internal.cuh"
 
 namespace bspl {
@@ -1126,6 +1129,22 @@ static bspl_status decompose_impl(int is_surface, const void* splines, double to
     out->is_surface = is_surface;
     out->n = n;
     out->tol_rel = tol_rel;
+
+    // splines ranked by descending piece count (stable: ties by index), for
+    // the heaviest-first order of the query calls' work-stealing launches
+    if (out->spline_rank) {
+        std::vector<int64_t> off((size_t)n + 1);
+        CK(cudaMemcpyAsync(off.data(), out->seg_off, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::vector<int32_t> idx((size_t)n), rank((size_t)n);
+        for (int64_t i = 0; i < n; ++i) idx[(size_t)i] = (int32_t)i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+            return off[(size_t)a + 1] - off[(size_t)a] > off[(size_t)b + 1] - off[(size_t)b];
+        });
+        for (int64_t r = 0; r < n; ++r) rank[(size_t)idx[(size_t)r]] = (int32_t)r;
+        CK(cudaMemcpyAsync(out->spline_rank, rank.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
 
     // filling pass and query tables
     if (is_surface) {

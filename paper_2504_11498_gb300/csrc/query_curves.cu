@@ -190,10 +190,13 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_query_curves(CurveQ P)
     __shared__ WarpSmem<R> smem[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpSmem<R>& W = smem[wid];
-    const int64_t batch = (int64_t)blockIdx.x * kWarps + wid;
-    const int64_t qbase = batch * kQPW;
     const int64_t nq = P.n_q_dev ? min(P.n_q, *P.n_q_dev) : P.n_q;
-    if (qbase >= nq) return;
+    // persistent: each warp takes batches of 32 sorted queries until none is left
+    const int64_t nbatch = (nq + kQPW - 1) / kQPW;
+    int round = 0;
+    for (int64_t batch = next_batch(P.work, (int64_t)blockIdx.x * kWarps + wid, nbatch, round); batch < nbatch;
+         batch = next_batch(P.work, (int64_t)blockIdx.x * kWarps + wid, nbatch, round)) {
+    const int64_t qbase = batch * kQPW;
     const int nslots = (int)min((int64_t)kQPW, nq - qbase);
     const R* rec = Tab<R>::rec(P);
     const R* grp = Tab<R>::grp(P);
@@ -398,27 +401,34 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_query_curves(CurveQ P)
             atomicAdd(P.counters + BSPL_CNT_NEWTON64_ITERS, i64);
         }
     }
+    __syncwarp();
+    }  // batches
 }
 
 // ------------------------------------------------------------ query sorting
 
-__global__ void k_hist(const int32_t* __restrict__ qc, int64_t n_q, int64_t n, int64_t* __restrict__ hist)
+// bucket of a query: its spline's rank (heaviest first) or, without ranks,
+// its spline index; invalid queries go to the last bucket
+__device__ __forceinline__ int64_t sort_bucket(int c, int64_t n, const int32_t* __restrict__ rank)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_q) return;
-    int c = qc[i];
-    int64_t b = (c >= 0 && c < n) ? c : n;  // invalid queries go to the last bucket
-    atomicAdd((unsigned long long*)(hist + b), 1ull);
+    if (c < 0 || c >= n) return n;
+    return rank ? (int64_t)rank[c] : (int64_t)c;
 }
 
-__global__ void k_scatter(const int32_t* __restrict__ qc, int64_t n_q, int64_t n, int64_t* __restrict__ cursor,
-                          int32_t* __restrict__ order)
+__global__ void k_hist(const int32_t* __restrict__ qc, int64_t n_q, int64_t n, const int32_t* __restrict__ rank,
+                       int64_t* __restrict__ hist)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_q) return;
-    int c = qc[i];
-    int64_t b = (c >= 0 && c < n) ? c : n;
-    unsigned long long pos = atomicAdd((unsigned long long*)(cursor + b), 1ull);
+    atomicAdd((unsigned long long*)(hist + sort_bucket(qc[i], n, rank)), 1ull);
+}
+
+__global__ void k_scatter(const int32_t* __restrict__ qc, int64_t n_q, int64_t n, const int32_t* __restrict__ rank,
+                          int64_t* __restrict__ cursor, int32_t* __restrict__ order)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_q) return;
+    unsigned long long pos = atomicAdd((unsigned long long*)(cursor + sort_bucket(qc[i], n, rank)), 1ull);
     order[pos] = (int32_t)i;
 }
 
@@ -427,6 +437,7 @@ void launch_query(const CurveQ& P, cudaStream_t s)
 {
     int64_t batches = (P.n_q + kQPW - 1) / kQPW;
     int64_t blocks = (batches + kWarps - 1) / kWarps;
+    if (P.work) blocks = persistent_blocks(k_query_curves<R, S, MIXED, MINB>, kWarps * 32, 0, blocks);
     k_query_curves<R, S, MIXED, MINB><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P);
 }
 
@@ -455,26 +466,33 @@ size_t query_ws_bytes(int64_t n_splines, int64_t n_q)
     cv.take<int64_t>((size_t)n_splines + 2);
     cv.take<int64_t>(scan_tmp_elems(n_splines + 2));
     cv.take<int32_t>((size_t)n_q);
+    cv.take<unsigned long long>(2);
     return cv.used + 256;
 }
 
-// groups query indices by spline: order[] lists queries bucket by bucket
-cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, void* ws, size_t ws_bytes, int32_t** order,
-                           cudaStream_t s)
+// groups query indices by spline (heaviest spline first when ranks are
+// given): order[] lists queries bucket by bucket; *work receives a zeroed
+// counter for the work-stealing launch that follows
+cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int32_t* rank, void* ws,
+                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s)
 {
     Carver cv(ws, ws_bytes);
     int64_t* hist = cv.take<int64_t>((size_t)n + 2);
     int64_t* tmp = cv.take<int64_t>(scan_tmp_elems(n + 2));
     int32_t* ord = cv.take<int32_t>((size_t)n_q);
-    if (!hist || !tmp || !ord) return cudaErrorInvalidValue;
+    unsigned long long* wk = cv.take<unsigned long long>(2);
+    if (!hist || !tmp || !ord || !wk) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int64_t) * (size_t)(n + 2), s);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(wk, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     int th = 256;
-    k_hist<<<ceil_div(n_q, th), th, 0, s>>>(qc, n_q, n, hist);
+    k_hist<<<ceil_div(n_q, th), th, 0, s>>>(qc, n_q, n, rank, hist);
     e = exclusive_scan_i64(hist, hist, n + 2, tmp, s);
     if (e != cudaSuccess) return e;
-    k_scatter<<<ceil_div(n_q, th), th, 0, s>>>(qc, n_q, n, hist, ord);
+    k_scatter<<<ceil_div(n_q, th), th, 0, s>>>(qc, n_q, n, rank, hist, ord);
     *order = ord;
+    if (work) *work = wk;
     return cudaGetLastError();
 }
 
@@ -520,7 +538,9 @@ bspl_status query_curves(const bspl_segments* segs, int64_t n_q, const int32_t* 
     if (sort) {
         if (!ws || ws_bytes < query_ws_bytes(segs->n, n_q)) return BSPL_EINVAL;
         int32_t* ord = nullptr;
-        if (sort_by_spline(q_curve, n_q, segs->n, ws, ws_bytes, &ord, s) != cudaSuccess) return BSPL_ECUDA;
+        if (sort_by_spline(q_curve, n_q, segs->n, segs->spline_rank, ws, ws_bytes, &ord, &P.work, s) !=
+            cudaSuccess)
+            return BSPL_ECUDA;
         P.order = ord;
     }
     const bool mixed = o.prec == BSPL_MIXED;

@@ -61,6 +61,7 @@ struct PairBuf {
     const float* qrec;        // per sorted query: q hi[3], q lo[3], eps, curve (int bits; -1 invalid)
     const int32_t* order;     // sorted position -> query index
     int32_t* over;            // overflowed query indices
+    unsigned long long* work; // work-stealing batch counter of the culling launch (zeroed), or NULL
     unsigned* best32;         // per query: FP32 upper bound of the distance (float bits)
     unsigned long long* best64;
     int* bestseg;
@@ -154,24 +155,27 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
     int32_t* qis = s_qi[wid];
     float* grs = s_grp[wid];
     uint64_t* bar = &s_bar[wid][0];
-    const int64_t qbase = ((int64_t)blockIdx.x * kWarps + wid) * kQPW;
-    if (qbase >= P.n_q) return;
-    const int nslots = (int)min((int64_t)kQPW, P.n_q - qbase);
     const float* rec = P.rec32;
     const float* grp = P.grp32;
     constexpr int RW = BSPL_CREC32, GW = BSPL_GREC32;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long n_grp = 0, n_seg = 0, n_pairs = 0;
-    int npend = 0;
-    unsigned over_mask = 0;  // query slots with pairs that did not fit the buffer
-
     if (lane == 0) {
         tc::mbar_init(bar, 1);
         tc::mbar_init(bar + 1, 1);
         tc::fence_mbar_init();
     }
     __syncwarp();
-    uint32_t phase = 0, phase1 = 0;  // parities of the two barriers
+    uint32_t phase = 0, phase1 = 0;  // parities of the two barriers (they carry over between batches)
+    // persistent: each warp takes batches of 32 sorted queries until none is left
+    const int64_t nbatch = (P.n_q + kQPW - 1) / kQPW;
+    int round = 0;
+    for (int64_t batch = next_batch(B.work, (int64_t)blockIdx.x * kWarps + wid, nbatch, round); batch < nbatch;
+         batch = next_batch(B.work, (int64_t)blockIdx.x * kWarps + wid, nbatch, round)) {
+    const int64_t qbase = batch * kQPW;
+    const int nslots = (int)min((int64_t)kQPW, P.n_q - qbase);
+    unsigned long long n_grp = 0, n_seg = 0, n_pairs = 0;
+    int npend = 0;
+    unsigned over_mask = 0;  // query slots with pairs that did not fit the buffer
 
     // this lane's query (lane = slot)
     float qx = 0.f, qy = 0.f, qz = 0.f, eps = 0.f;
@@ -511,6 +515,8 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
             atomicAdd(P.counters + BSPL_CNT_CANDIDATES, n_pairs);
         }
     }
+    __syncwarp();
+    }  // batches
 }
 
 // pair index j in [0, seeds + others) -> buffer slot
@@ -912,16 +918,24 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     };
     mark(0);
     int32_t* order = nullptr;
-    if (sort_by_spline(q_curve, n_q, segs->n, sw, sb, &order, s) != cudaSuccess) return BSPL_ECUDA;
+    if (sort_by_spline(q_curve, n_q, segs->n, segs->spline_rank, sw, sb, &order, nullptr, s) != cudaSuccess)
+        return BSPL_ECUDA;
     P.order = order;
     B.order = order;
     k_qrec<<<ceil_div(n_q, 256), 256, 0, s>>>(q_curve, q_xyz, segs->diag, segs->n, order, n_q, (float*)B.qrec);
     if (cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess) return BSPL_ECUDA;
     mark(1);
     const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
-    if (o->occupancy >= 2) k_cull_pairs<false, 8><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
-    else if (o->occupancy == 1) k_cull_pairs<false, 6><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
-    else k_cull_pairs<false, 1><<<(unsigned)blocks, kWarps * 32, 0, s>>>(P, B);
+    B.work = B.cnt + 6;  // zeroed with the other counters
+    if (o->occupancy >= 2)
+        k_cull_pairs<false, 8><<<persistent_blocks(k_cull_pairs<false, 8>, kWarps * 32, 0, blocks), kWarps * 32, 0,
+                                 s>>>(P, B);
+    else if (o->occupancy == 1)
+        k_cull_pairs<false, 6><<<persistent_blocks(k_cull_pairs<false, 6>, kWarps * 32, 0, blocks), kWarps * 32, 0,
+                                 s>>>(P, B);
+    else
+        k_cull_pairs<false, 1><<<persistent_blocks(k_cull_pairs<false, 1>, kWarps * 32, 0, blocks), kWarps * 32, 0,
+                                 s>>>(P, B);
     mark(2);
     if (mlp && mlp_seed_pairs(mlp, B.pq, B.ps, B.qrec, segs, B.cap, B.cnt + 1, B.u, s) != cudaSuccess)
         return BSPL_ECUDA;
@@ -965,7 +979,9 @@ extern "C" bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t
         CurveQ P = make_params(segs, n_q, q_curve, q_xyz, o, 0, nullptr, nullptr, nullptr);
         P.counters = nullptr;
         int32_t* order = nullptr;
-        if (sort_by_spline(q_curve, n_q, segs->n, sw, sb, &order, stream) != cudaSuccess) return BSPL_ECUDA;
+        if (sort_by_spline(q_curve, n_q, segs->n, segs->spline_rank, sw, sb, &order, nullptr, stream) !=
+            cudaSuccess)
+            return BSPL_ECUDA;
         P.order = order;
         B.order = order;
         k_qrec<<<ceil_div(n_q, 256), 256, 0, stream>>>(q_curve, q_xyz, segs->diag, segs->n, order, n_q,
@@ -976,7 +992,9 @@ extern "C" bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t
         C.kind = nullptr;
         C.cap = cap;
         const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
-        k_cull_pairs<true, 1><<<(unsigned)blocks, kWarps * 32, 0, stream>>>(P, C);
+        C.work = B.cnt + 6;  // zeroed above
+        k_cull_pairs<true, 1><<<persistent_blocks(k_cull_pairs<true, 1>, kWarps * 32, 0, blocks), kWarps * 32, 0,
+                                stream>>>(P, C);
     }
     if (cudaMemcpyAsync(n_pairs, B.cnt + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess ||
         cudaMemcpyAsync(n_pairs + 1, B.cnt, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)

@@ -24,8 +24,8 @@
 
 namespace bspl {
 
-cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, void* ws, size_t ws_bytes, int32_t** order,
-                           cudaStream_t s);
+cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int32_t* rank, void* ws,
+                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s);
 
 namespace {
 
@@ -63,6 +63,7 @@ struct SurfQ {
     int fp32_steps;
     int cert_depth;  // refinement levels of the certification search; < 0: none
     unsigned long long* counters;
+    unsigned long long* work;  // work-stealing batch counter (zeroed), or NULL: one batch per warp
 };
 
 template <class R>
@@ -981,9 +982,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
     WarpSmem<R>* smem = reinterpret_cast<WarpSmem<R>*>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpSmem<R>& W = smem[wid];
-    const int64_t batch = (int64_t)blockIdx.x * kWarps + wid;
+    // persistent: each warp takes batches of 32 sorted queries (heaviest
+    // splines first when the segments carry ranks) until none is left
+    const int64_t nbatch = (P.n_q + kQPW - 1) / kQPW;
+    int round = 0;
+    for (int64_t batch = next_batch(P.work, (int64_t)blockIdx.x * kWarps + wid, nbatch, round); batch < nbatch;
+         batch = next_batch(P.work, (int64_t)blockIdx.x * kWarps + wid, nbatch, round)) {
     const int64_t qbase = batch * kQPW;
-    if (qbase >= P.n_q) return;
     const int nslots = (int)min((int64_t)kQPW, P.n_q - qbase);
     const R* rec = STab<R>::rec(P);
     const R* grp = STab<R>::grp(P);
@@ -1217,6 +1222,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
             atomicAdd(P.counters + BSPL_CNT_CERT_OVERFLOW, ccnt[2]);
         }
     }
+    __syncwarp();
+    }  // batches
 }
 
 template <class R, int GU, int GV, bool MIXED>
@@ -1231,6 +1238,7 @@ void launch_surf(const SurfQ& P, cudaStream_t s)
                              (int)smem);
         attr_set = true;
     }
+    if (P.work) blocks = persistent_blocks(k_query_surfaces<R, GU, GV, MIXED>, kWarps * 32, smem, blocks);
     k_query_surfaces<R, GU, GV, MIXED><<<(unsigned)blocks, kWarps * 32, smem, s>>>(P);
 }
 
@@ -1282,10 +1290,13 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
     P.cert_depth = o.cert_depth < 0 ? -1 : (o.cert_depth == 0 ? 2 : o.cert_depth);
     P.counters = (unsigned long long*)o.counters;
     P.order = nullptr;
+    P.work = nullptr;
     if (sort) {
         if (!ws || ws_bytes < query_ws_bytes(segs->n, n_q)) return BSPL_EINVAL;
         int32_t* ord = nullptr;
-        if (sort_by_spline(q_surf, n_q, segs->n, ws, ws_bytes, &ord, s) != cudaSuccess) return BSPL_ECUDA;
+        if (sort_by_spline(q_surf, n_q, segs->n, segs->spline_rank, ws, ws_bytes, &ord, &P.work, s) !=
+            cudaSuccess)
+            return BSPL_ECUDA;
         P.order = ord;
     }
     if (o.prec == BSPL_MIXED) {

@@ -48,7 +48,7 @@ typedef enum {
     BSPL_FP64 = 0,          /* cull, seed and Newton all in FP64                  */
     BSPL_MIXED = 1,         /* FP32 cull/seed/early Newton + 2 FP64 Newton steps  */
     BSPL_LEARNED_MIXED = 2  /* as MIXED with the MLP seed in place of the grid
-                               (curves only; bspl_mlp.h)                         */
+                               (bspl_mlp.h; surfaces: the surface network)      */
 } bspl_precision;
 
 /* per-query status bits */
@@ -223,6 +223,8 @@ typedef struct {
 #define BSPL_OP_QUERY_SURFACES 4
 #define BSPL_OP_QUERY_CURVES_LEARNED 5 /* curve queries with opt->prec = BSPL_LEARNED_MIXED */
 #define BSPL_OP_MLP_TRAIN 6            /* bspl_mlp_loss_grad / bspl_mlp_train, n_q = batch */
+#define BSPL_OP_SMLP_TRAIN 7           /* the same for the surface seed network */
+#define BSPL_OP_QUERY_SURFACES_LEARNED 8 /* surface queries with opt->prec = BSPL_LEARNED_MIXED */
 
 /* Bytes of device workspace a call of kind `op` needs.  n_splines = n,
  * n_cp_total = total control points (cp_off[n]), n_seg = segments of the

@@ -37,25 +37,30 @@ IN = 16
 NPARAM = 35332
 _SHAPES = (("W1", (H, IN)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, H)), ("b3", (H,)),
            ("w4", (H,)), ("b4", (1,)))
+# the surface network: 64 inputs (51 used) -> 2 outputs (u, v)
+SIN = 64
+SNPARAM = 41604
+SHAPES_SURF = (("W1", (H, SIN)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, H)), ("b3", (H,)),
+               ("W4", (2, H)), ("b4", (2,)))
 
 _K = math.sqrt(2.0 / math.pi)
 _C = 0.044715
 
 
-def unpack(theta):
+def unpack(theta, shapes=_SHAPES):
     """Parameter vector -> dict of arrays (views)."""
     out, o = {}, 0
-    for name, shp in _SHAPES:
+    for name, shp in shapes:
         n = int(np.prod(shp))
         out[name] = theta[o:o + n].reshape(shp)
         o += n
     return out
 
 
-def pack(p, total=NPARAM):
+def pack(p, total=NPARAM, shapes=_SHAPES):
     theta = np.zeros(total)
     o = 0
-    for name, shp in _SHAPES:
+    for name, shp in shapes:
         n = int(np.prod(shp))
         theta[o:o + n] = np.asarray(p[name], np.float64).reshape(-1)
         o += n
@@ -84,7 +89,8 @@ def round_bf16(x):
 
 
 def forward(p, X, bf16=False):
-    """p: dict of layer arrays (any widths), X [n][in].  Returns t [n] and
+    """p: dict of layer arrays (any widths), X [n][in].  Returns t [n] (one
+    output: w4 [H], b4 [1]) or t [n][k] (k outputs: W4 [k][H], b4 [k]) and
     the pre-activations (Z1, Z2, Z3) and activations (H0 = X, H1, H2, H3).
     bf16=True evaluates the network at the precision it is served in: every
     weight matrix and every layer input rounded to bfloat16 (biases and the
@@ -95,20 +101,25 @@ def forward(p, X, bf16=False):
         Z = r(Hs[-1]) @ r(W).T + b
         Zs.append(Z)
         Hs.append(gelu(Z))
+    if "W4" in p:
+        return sigmoid(r(Hs[-1]) @ r(p["W4"]).T + p["b4"]), Zs, Hs
     z4 = r(Hs[-1]) @ r(p["w4"]) + p["b4"][0]
     return sigmoid(z4), Zs, Hs
 
 
 def loss_and_grads(p, X, y):
-    """Mean squared error of t against y and its gradient, by the chain rule
-    written out layer by layer."""
+    """Mean squared error of t against y (the mean over rows and outputs)
+    and its gradient, by the chain rule written out layer by layer."""
     t, Zs, Hs = forward(p, X)
-    n = len(y)
     r = t - y
     loss = float(np.mean(r * r))
-    dz4 = (2.0 / n) * r * t * (1.0 - t)
-    g = {"w4": Hs[3].T @ dz4, "b4": np.array([dz4.sum()])}
-    dH = np.outer(dz4, p["w4"])
+    dz4 = (2.0 / r.size) * r * t * (1.0 - t)
+    if "W4" in p:
+        g = {"W4": dz4.T @ Hs[3], "b4": dz4.sum(axis=0)}
+        dH = dz4 @ p["W4"]
+    else:
+        g = {"w4": Hs[3].T @ dz4, "b4": np.array([dz4.sum()])}
+        dH = np.outer(dz4, p["w4"])
     for li in (3, 2, 1):
         dZ = dH * gelu_grad(Zs[li - 1])
         g[f"W{li}"] = dZ.T @ Hs[li - 1]
@@ -201,3 +212,124 @@ def segment_minimiser(P, q, samples=513):
     Dc = ((_bezier(P, cands) - q) ** 2).sum(axis=1)
     k = int(np.argmin(Dc))
     return float(cands[k]), float(Dc[k])
+
+
+# ------------------------------------------------------- surface network
+
+def surface_features(ctrl, q):
+    """ctrl [n][4][4][3] bicubic Bezier nets (first index along u), q [n][3]
+    -> X [n][64]: the 16 control points relative to the centre of their box,
+    scaled by 1 / its longest side (i along u, then j, then xyz); the query
+    in the same frame with its component along the normal of the frame
+    e1 = P30 - P00, e2 = (P03 - P00) without its e1 part clamped to [-1, 1]
+    (the tangential components kept); then 13 zeros."""
+    ctrl = np.asarray(ctrl, np.float64)
+    q = np.asarray(q, np.float64)
+    n = len(q)
+    d = ctrl - ctrl[:, :1, :1, :]
+    lo = np.minimum(d.reshape(n, 16, 3).min(axis=1), 0.0)
+    hi = np.maximum(d.reshape(n, 16, 3).max(axis=1), 0.0)
+    c = 0.5 * (lo + hi)
+    ext = (hi - lo).max(axis=1)
+    s = np.where(ext > 0, 1.0 / np.where(ext > 0, ext, 1.0), 1.0)
+    X = np.zeros((n, SIN))
+    X[:, :48] = ((d - c[:, None, None, :]) * s[:, None, None, None]).reshape(n, 48)
+    v = (q - ctrl[:, 0, 0] - c) * s[:, None]
+    e1 = d[:, 3, 0]
+    l1 = np.linalg.norm(e1, axis=1)
+    e1 = np.where(l1[:, None] > 0, e1 / np.where(l1 > 0, l1, 1.0)[:, None], np.array([1.0, 0.0, 0.0]))
+    w = d[:, 0, 3] - np.einsum("ij,ij->i", d[:, 0, 3], e1)[:, None] * e1
+    l2 = np.linalg.norm(w, axis=1)
+    # a degenerate second side: any unit vector across e1
+    t = np.where((np.abs(e1[:, 0]) < 0.9)[:, None], np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0]))
+    alt = t - np.einsum("ij,ij->i", t, e1)[:, None] * e1
+    alt /= np.linalg.norm(alt, axis=1)[:, None]
+    e2 = np.where(l2[:, None] > 0, w / np.where(l2 > 0, l2, 1.0)[:, None], alt)
+    nn = np.cross(e1, e2)
+    a1 = np.einsum("ij,ij->i", v, e1)
+    a2 = np.einsum("ij,ij->i", v, e2)
+    a3 = np.clip(np.einsum("ij,ij->i", v, nn), -1.0, 1.0)
+    X[:, 48:51] = a1[:, None] * e1 + a2[:, None] * e2 + a3[:, None] * nn
+    return X
+
+
+def _bern3(t):
+    t = np.asarray(t, np.float64)
+    w = 1.0 - t
+    return np.stack([w ** 3, 3 * w * w * t, 3 * w * t * t, t ** 3], axis=-1)
+
+
+def _bern3_d(t):
+    t = np.asarray(t, np.float64)
+    w = 1.0 - t
+    return np.stack([-3 * w * w, 3 * w * w - 6 * w * t, 6 * w * t - 3 * t * t, 3 * t * t], axis=-1)
+
+
+def _bern3_dd(t):
+    t = np.asarray(t, np.float64)
+    return np.stack([6 * (1 - t), -12 + 18 * t, 6 - 18 * t, 6 * t], axis=-1)
+
+
+def _patch(P, u, v, du=0, dv=0):
+    fu = (_bern3, _bern3_d, _bern3_dd)[du](u)
+    fv = (_bern3, _bern3_d, _bern3_dd)[dv](v)
+    return np.einsum("...i,...j,ijc->...c", fu, fv, P)
+
+
+def patch_minimiser(P, q, samples=33):
+    """Global minimiser of |S(u,v) - q|^2 over (u,v) in [0,1]^2 for one
+    bicubic Bezier patch P [4][4][3]: the four corners, the minimiser of each
+    edge (a cubic curve: segment_minimiser), and a damped Newton iteration on
+    grad D kept inside the square from every local minimum of a dense sample
+    grid; the smallest distance wins (ties -> smaller u, then smaller v)."""
+    P = np.asarray(P, np.float64)
+    q = np.asarray(q, np.float64)
+    cands = [(0.0, 0.0), (1.0, 0.0), (0.0, 1.0), (1.0, 1.0)]
+    for fixed_u, val in ((True, 0.0), (True, 1.0), (False, 0.0), (False, 1.0)):
+        edge = P[0 if val == 0.0 else 3] if fixed_u else P[:, 0 if val == 0.0 else 3]
+        t, _ = segment_minimiser(edge, q)
+        cands.append((val, t) if fixed_u else (t, val))
+    g = np.linspace(0.0, 1.0, samples)
+    uu, vv = np.meshgrid(g, g, indexing="ij")
+    D = ((_patch(P, uu, vv) - q) ** 2).sum(axis=-1)
+    for i in range(samples):
+        for j in range(samples):
+            nb = D[max(i - 1, 0):i + 2, max(j - 1, 0):j + 2]
+            if D[i, j] > nb.min():
+                continue
+            u, v = g[i], g[j]
+            for _ in range(100):
+                S = _patch(P, u, v) - q
+                Su, Sv = _patch(P, u, v, 1, 0), _patch(P, u, v, 0, 1)
+                gr = np.array([S @ Su, S @ Sv])
+                Hm = np.array([[Su @ Su + S @ _patch(P, u, v, 2, 0), Su @ Sv + S @ _patch(P, u, v, 1, 1)],
+                               [0.0, Sv @ Sv + S @ _patch(P, u, v, 0, 2)]])
+                Hm[1, 0] = Hm[0, 1]
+                if np.all(np.linalg.eigvalsh(Hm) > 0):
+                    step = -np.linalg.solve(Hm, gr)
+                else:
+                    step = -gr / max(np.linalg.norm(gr), 1e-300) / samples
+                D0 = float(S @ S)
+                lam, acc = 1.0, False
+                for _ in range(60):
+                    un, vn = min(max(u + lam * step[0], 0.0), 1.0), min(max(v + lam * step[1], 0.0), 1.0)
+                    Sn = _patch(P, un, vn) - q
+                    if float(Sn @ Sn) <= D0:
+                        acc = True
+                        break
+                    lam *= 0.5
+                if not acc:
+                    break
+                moved = abs(un - u) + abs(vn - v)
+                u, v = un, vn
+                if moved <= 1e-16:
+                    break
+            cands.append((u, v))
+    best = None
+    for u, v in cands:
+        S = _patch(P, u, v) - q
+        Dc = float(S @ S)
+        key = (Dc, u, v)
+        if best is None or key < best:
+            best = key
+    return best[1], best[2], best[0]

@@ -25,10 +25,16 @@ GROUP = 32
 CREC64, CREC32, SREC64, SREC32, GREC64, GREC32 = 18, 24, 54, 72, 12, 12
 SPAN_NET = 8 * 8 * 3
 OP_DECOMPOSE_CURVES, OP_DECOMPOSE_SURFACES, OP_QUERY_CURVES, OP_QUERY_SURFACES = 1, 2, 3, 4
-OP_QUERY_CURVES_LEARNED, OP_MLP_TRAIN = 5, 6
+OP_QUERY_CURVES_LEARNED, OP_MLP_TRAIN, OP_SMLP_TRAIN, OP_QUERY_SURFACES_LEARNED = 5, 6, 7, 8
 # learned seed (include/bspl_mlp.h)
 MLP_IN, MLP_HIDDEN, MLP_NPARAM, MLP_NBF16, MLP_MAX_BATCH = 16, 128, 35332, 2048 + 4 * 16384 + 128, 65536
 MLP_OFF = {"W1": 0, "b1": 2048, "W2": 2176, "b2": 18560, "W3": 18688, "b3": 35072, "w4": 35200, "b4": 35328}
+MLP_CURVE, MLP_SURFACE = 0, 1
+# the surface seed network (bspl_mlp.h BSPL_SMLP_*): 64 inputs (51 used) -> 2
+SMLP_IN, SMLP_OUT, SMLP_NPARAM, SMLP_NBF16 = 64, 2, 41604, 8192 + 4 * 16384 + 256
+SMLP_OFF = {"W1": 0, "b1": 8192, "W2": 8320, "b2": 24704, "W3": 24832, "b3": 41216, "W4": 41344, "b4": 41600}
+NET = {MLP_CURVE: (MLP_IN, 1, MLP_NPARAM, MLP_NBF16, OP_MLP_TRAIN),
+       MLP_SURFACE: (SMLP_IN, SMLP_OUT, SMLP_NPARAM, SMLP_NBF16, OP_SMLP_TRAIN)}
 NCOUNTERS = 13
 COUNTER_NAMES = ["queries", "seg_tested", "grp_tested", "candidates", "newton", "fallback", "nonconv",
                  "newton32_iters", "newton64_iters", "iso_pairs", "cert_cells", "cert_leaves", "cert_overflow"]
@@ -70,7 +76,7 @@ STAGE_NAMES = ["sort", "cull", "seed", "fp32", "fp64", "select", "leftovers"]
 
 
 class bspl_mlp(C.Structure):
-    _fields_ = [("params", C.c_void_p), ("wbf16", C.c_void_p)]
+    _fields_ = [("params", C.c_void_p), ("wbf16", C.c_void_p), ("kind", C.c_int32)]
 
 
 EXPORTS = ["bspl_graph_begin", "bspl_graph_end", "bspl_graph_launch", "bspl_graph_destroy",
@@ -132,7 +138,10 @@ def lib():
                                ("bspl_mlp_loss_grad", [mp, i64, vp, vp, vp, vp, vp, C.c_size_t, vp]),
                                ("bspl_mlp_adam", [mp, vp, vp, vp, C.c_int32, f32, f32, f32, f32, vp]),
                                ("bspl_mlp_train", [mp, vp, vp, i64, vp, vp, C.c_int32, C.c_int32, f32, C.c_uint64,
-                                                   C.c_int32, vp, vp, C.c_size_t, vp])):
+                                                   C.c_int32, vp, vp, C.c_size_t, vp]),
+                               ("bspl_smlp_features", [sp, i64, vp, vp, vp, vp, vp]),
+                               ("bspl_smlp_labels", [sp, i64, vp, vp, vp, vp, vp]),
+                               ("bspl_smlp_collect_pairs", [sp, i64, vp, vp, i64, vp, vp, vp, vp, C.c_size_t, vp])):
                 f = getattr(L, name)
                 f.restype = st
                 f.argtypes = args
@@ -335,7 +344,10 @@ class QueryBuffers:
         self.param = torch.empty(shape, dtype=torch.float64, device=device)
         self.dist = torch.empty(n_q, dtype=torch.float64, device=device)
         self.status = torch.empty(n_q, dtype=torch.uint8, device=device)
-        op = OP_QUERY_SURFACES if segs.is_surface else (OP_QUERY_CURVES_LEARNED if learned else OP_QUERY_CURVES)
+        if segs.is_surface:
+            op = OP_QUERY_SURFACES_LEARNED if learned else OP_QUERY_SURFACES
+        else:
+            op = OP_QUERY_CURVES_LEARNED if learned else OP_QUERY_CURVES
         self.ws = _ws(workspace_bytes(op, segs.n, segs.n_cp_total, segs.total, n_q), device)
 
 
@@ -363,12 +375,12 @@ def bspl_invert_curves(segs, q_curve, q_xyz, opts=None, bufs=None, stream=None):
 
 
 def bspl_project_surfaces(segs, q_surf, q_xyz, opts=None, bufs=None, stream=None):
-    bufs = bufs or QueryBuffers(segs, q_surf.numel(), q_xyz.device)
+    bufs = bufs or QueryBuffers(segs, q_surf.numel(), q_xyz.device, _learned(opts))
     return _query("bspl_project_surfaces", segs, q_surf, q_xyz, opts or make_options(), bufs, stream)
 
 
 def bspl_invert_surfaces(segs, q_surf, q_xyz, opts=None, bufs=None, stream=None):
-    bufs = bufs or QueryBuffers(segs, q_surf.numel(), q_xyz.device)
+    bufs = bufs or QueryBuffers(segs, q_surf.numel(), q_xyz.device, _learned(opts))
     return _query("bspl_invert_surfaces", segs, q_surf, q_xyz, opts or make_options(), bufs, stream)
 
 
@@ -462,17 +474,20 @@ def measure_fma_peak(fp64: bool, iters: int = 4096, reps: int = 5, stream=None) 
 # ------------------------------------------------------------ learned seed
 
 class Mlp:
-    """Parameters of the learned seed on the GPU (include/bspl_mlp.h): FP32
-    master weights, the BF16 copy the kernels read, and Adam's moments."""
+    """Parameters of a learned seed network on the GPU (include/bspl_mlp.h):
+    FP32 master weights, the BF16 copy the kernels read, and Adam's moments.
+    kind MLP_CURVE (16 -> 1) or MLP_SURFACE (64 -> 2)."""
 
-    def __init__(self, params, device="cuda"):
-        self.params = torch.as_tensor(np.asarray(params, np.float32)).to(device).contiguous()
-        assert self.params.numel() == MLP_NPARAM
-        self.wbf16 = torch.zeros(MLP_NBF16, dtype=torch.int16, device=device)
-        self.adam_m = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=device)
-        self.adam_v = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=device)
+    def __init__(self, params, device="cuda", kind=MLP_CURVE):
+        self.kind = int(kind)
+        self.n_in, self.n_out, npar, nbf, self.train_op = NET[self.kind]
+        self.params = torch.tensor(np.array(params, np.float32)).to(device).contiguous()
+        assert self.params.numel() == npar
+        self.wbf16 = torch.zeros(nbf, dtype=torch.int16, device=device)
+        self.adam_m = torch.zeros(npar, dtype=torch.float32, device=device)
+        self.adam_v = torch.zeros(npar, dtype=torch.float32, device=device)
         self.step = 0
-        self.c = bspl_mlp(self.params.data_ptr(), self.wbf16.data_ptr())
+        self.c = bspl_mlp(self.params.data_ptr(), self.wbf16.data_ptr(), self.kind)
         self.sync()
 
     def sync(self, stream=None):
@@ -480,16 +495,17 @@ class Mlp:
 
     def forward(self, X, stream=None):
         X = X.contiguous()
-        t = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        shape = (X.shape[0],) if self.n_out == 1 else (X.shape[0], self.n_out)
+        t = torch.empty(shape, dtype=torch.float32, device=X.device)
         _check(lib().bspl_mlp_forward(C.byref(self.c), X.shape[0], _ptr(X), _ptr(t), _stream(stream)),
                "bspl_mlp_forward")
         return t
 
     def loss_grad(self, X, y, stream=None):
         n = X.shape[0]
-        grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
+        grad = torch.empty(self.params.numel(), dtype=torch.float32, device=X.device)
         loss = torch.empty(1, dtype=torch.float32, device=X.device)
-        ws = _ws(workspace_bytes(OP_MLP_TRAIN, 0, 0, 0, n), X.device)
+        ws = _ws(workspace_bytes(self.train_op, 0, 0, 0, n), X.device)
         _check(lib().bspl_mlp_loss_grad(C.byref(self.c), n, _ptr(X.contiguous()), _ptr(y.contiguous()), _ptr(grad),
                                         _ptr(loss), _ptr(ws), ws.numel(), _stream(stream)), "bspl_mlp_loss_grad")
         return loss, grad
@@ -504,7 +520,7 @@ class Mlp:
         """Returns the per-epoch mean loss (device tensor)."""
         n = X.shape[0]
         loss = torch.empty(epochs, dtype=torch.float32, device=X.device)
-        ws = _ws(workspace_bytes(OP_MLP_TRAIN, 0, 0, 0, batch), X.device)
+        ws = _ws(workspace_bytes(self.train_op, 0, 0, 0, batch), X.device)
         _check(lib().bspl_mlp_train(C.byref(self.c), _ptr(self.adam_m), _ptr(self.adam_v), n, _ptr(X.contiguous()),
                                     _ptr(y.contiguous()), int(epochs), int(batch), float(lr), int(seed) & (2**64 - 1),
                                     self.step, _ptr(loss), _ptr(ws), ws.numel(), _stream(stream)), "bspl_mlp_train")
@@ -520,7 +536,9 @@ class Mlp:
         import zlib
         payload = b"".join(t.detach().cpu().numpy().astype("<f4").tobytes()
                            for t in (self.params, self.adam_m, self.adam_v))
-        hdr = self._MAGIC + struct.pack("<IIqI", 1, MLP_NPARAM, self.step, zlib.crc32(payload))
+        # version 1: the curve network; version 2: the surface network
+        hdr = self._MAGIC + struct.pack("<IIqI", 1 + self.kind, self.params.numel(), self.step,
+                                        zlib.crc32(payload))
         with open(path, "wb") as f:
             f.write(hdr + payload)
 
@@ -533,10 +551,11 @@ class Mlp:
             raise BsplError(f"{path}: not an MLP checkpoint")
         ver, npar, step, crc = struct.unpack("<IIqI", raw[8:28])
         payload = raw[28:]
-        if ver != 1 or npar != MLP_NPARAM or len(payload) != 12 * MLP_NPARAM or zlib.crc32(payload) != crc:
+        kind = ver - 1
+        if kind not in NET or npar != NET[kind][2] or len(payload) != 12 * npar or zlib.crc32(payload) != crc:
             raise BsplError(f"{path}: corrupt or incompatible MLP checkpoint")
-        a = np.frombuffer(payload, "<f4").reshape(3, MLP_NPARAM)
-        m = cls(a[0], device)
+        a = np.frombuffer(payload, "<f4").reshape(3, npar)
+        m = cls(a[0], device, kind)
         m.adam_m.copy_(torch.from_numpy(a[1].copy()))
         m.adam_v.copy_(torch.from_numpy(a[2].copy()))
         m.step = step
@@ -575,3 +594,34 @@ def bspl_mlp_collect_pairs(segs, q_curve, q_xyz, cap, stream=None):
            "bspl_mlp_collect_pairs")
     written, found = (int(v) for v in n.tolist())
     return pq[:written], ps[:written], found
+
+
+# ------------------------------------------------------ surface seed network
+
+def bspl_smlp_features(segs, pair_q, pair_patch, q_xyz, stream=None):
+    X = torch.empty((pair_q.numel(), SMLP_IN), dtype=torch.float32, device=q_xyz.device)
+    _check(lib().bspl_smlp_features(C.byref(segs.c), pair_q.numel(), _ptr(pair_q), _ptr(pair_patch), _ptr(q_xyz),
+                                    _ptr(X), _stream(stream)), "bspl_smlp_features")
+    return X
+
+
+def bspl_smlp_labels(segs, pair_q, pair_patch, q_xyz, stream=None):
+    uv = torch.empty((pair_q.numel(), 2), dtype=torch.float32, device=q_xyz.device)
+    _check(lib().bspl_smlp_labels(C.byref(segs.c), pair_q.numel(), _ptr(pair_q), _ptr(pair_patch), _ptr(q_xyz),
+                                  _ptr(uv), _stream(stream)), "bspl_smlp_labels")
+    return uv
+
+
+def bspl_smlp_collect_pairs(segs, q_surf, q_xyz, cap, stream=None):
+    """(pair_q, pair_patch) of the (query, patch) pairs the learned surface
+    path seeds (at most cap written) and the number found."""
+    dev = q_xyz.device
+    pq = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    pp = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    n = torch.zeros(2, dtype=torch.int64, device=dev)
+    ws = _ws(workspace_bytes(OP_QUERY_SURFACES_LEARNED, segs.n, 0, 0, q_surf.numel()), dev)
+    _check(lib().bspl_smlp_collect_pairs(C.byref(segs.c), q_surf.numel(), _ptr(q_surf), _ptr(q_xyz), int(cap),
+                                         _ptr(pq), _ptr(pp), _ptr(n), _ptr(ws), ws.numel(), _stream(stream)),
+           "bspl_smlp_collect_pairs")
+    written, found = (int(v) for v in n.tolist())
+    return pq[:written], pp[:written], found

@@ -50,9 +50,10 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
                                  const double* q_xyz, const bspl_options* o, int invert, double* t, double* dist,
                                  uint8_t* status, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t learned_ws_bytes(int64_t n_splines, int64_t n_q);
+size_t learned_surf_ws_bytes(int64_t n_splines, int64_t n_q);
 
 // learned seed (mlp.cu)
-size_t train_ws_bytes(int64_t batch);
+size_t train_ws_bytes(int kind, int64_t batch);
 
 // evaluation (eval.cu)
 bspl_status eval_curves(const bspl_curves* c, int64_t n_q, const int32_t* qc, const double* t, double* xyz,

@@ -903,7 +903,7 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     if (n_q == 0) return BSPL_OK;
     if (!q_curve || !q_xyz || !t || !dist || !status) return BSPL_EINVAL;
     const bspl_mlp* mlp = (const bspl_mlp*)o->mlp;
-    if (mlp && (!mlp->params || !mlp->wbf16)) return BSPL_EINVAL;
+    if (mlp && (!mlp->params || !mlp->wbf16 || mlp->kind != BSPL_MLP_CURVE)) return BSPL_EINVAL;
     if (o->occupancy < 0 || o->occupancy > 2) return BSPL_EINVAL;
     if (o->pairs_per_query < 0 || o->pairs_per_query > kPairsPerQuery) return BSPL_EINVAL;
     PairBuf B{};

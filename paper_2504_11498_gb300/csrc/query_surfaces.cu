@@ -20,10 +20,14 @@
 // halving safeguard on D.
 #include <math.h>
 
+#include "../../include/bspl_mlp.h"
 #include "bspl_internal.cuh"
 
 namespace bspl {
 
+cudaError_t mlp_seed_surface_pairs(const bspl_mlp* m, const int32_t* pq, const int32_t* pp, const int32_t* order,
+                                   const double* q_xyz, const bspl_segments* segs, int64_t cap,
+                                   const unsigned long long* n_dev, float* uv0, cudaStream_t s);
 cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int32_t* rank, void* ws,
                            size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s);
 
@@ -64,6 +68,19 @@ struct SurfQ {
     int cert_depth;  // refinement levels of the certification search; < 0: none
     unsigned long long* counters;
     unsigned long long* work;  // work-stealing batch counter (zeroed), or NULL: one batch per warp
+    // learned seeds: mode 0 -- the sample grid seeds Newton; 1 -- the culled
+    // (query, patch) candidates are written out instead (nothing else); 2 --
+    // Newton starts from the network's (u, v) of each written pair (queries
+    // without pairs fall back to the grid)
+    int mode;
+    int pair_index;          // mode 1: pair_q holds the query index (else the sorted position)
+    int32_t* pair_q;
+    int32_t* pair_p;         // patch of each pair
+    const float* pair_uv;    // mode 2: (u, v) per pair
+    int64_t pair_cap;
+    unsigned long long* pair_n;  // [0] pairs written, [1] pairs found
+    int32_t* q_first;        // per sorted position: first pair, or -1 (grid)
+    int32_t* q_count;
 };
 
 template <class R>
@@ -1029,7 +1046,40 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
             W.surf[sl] = cc_;
             if (bad) W.best_flags[sl] = BSPL_Q_INVALID;
         }
+        if (P.mode == 1 && bad) {
+            if (lane == 0 && !P.pair_index) P.q_first[qbase + sl] = -1;
+            continue;
+        }
         if (bad) continue;
+        if (P.mode == 2 && P.q_first[qbase + sl] >= 0) {
+            // the network's seeds: one Newton start per written pair
+            const int f = P.q_first[qbase + sl], cnt = P.q_count[qbase + sl];
+            for (int base = 0; base < cnt; base += 32) {
+                const int k = base + lane;
+                const bool has = k < cnt;
+                const unsigned m = __ballot_sync(kFull, has);
+                const int nm = __popc(m);
+                if (npool + nm > kPoolCap) {
+                    flush_pool<R, MIXED, GU, GV>(P, W, npool, lane);
+                    n_newton += npool;
+                    npool = 0;
+                }
+                if (has) {
+                    PoolEntry e;
+                    e.patch = P.pair_p[f + k];
+                    e.slot = (short)sl;
+                    e.direct = 0;
+                    e.hs = e.ht = 0.f;
+                    e.u0 = P.pair_uv ? P.pair_uv[2 * (int64_t)(f + k)] : 0.5f;
+                    e.v0 = P.pair_uv ? P.pair_uv[2 * (int64_t)(f + k) + 1] : 0.5f;
+                    W.pool[npool + __popc(m & ((1u << lane) - 1))] = e;
+                }
+                npool += nm;
+                __syncwarp();
+            }
+            n_cand += (unsigned long long)cnt;
+            continue;
+        }
         const int64_t s0 = P.seg_off[c], s1 = P.seg_off[c + 1];
         const int64_t g0 = P.grp_off[c], g1 = P.grp_off[c + 1];
 
@@ -1040,6 +1090,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
         n_grp_tested += (unsigned long long)(g1 - g0);
 
         int ncand = 0;
+        bool collect_over = false;
         auto grid_stage = [&]() {
             __syncwarp();
             const int sub = lane / GS, j = lane % GS;
@@ -1146,11 +1197,59 @@ __global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
                     W.cand_lb[pos] = lbs;
                 }
                 ncand += __popc(km);
-                if (ncand > kCandCap - 32) grid_stage();
+                if (ncand > kCandCap - 32) {
+                    if (P.mode == 1) {
+                        collect_over = true;  // too many candidates: this query keeps the grid
+                        break;
+                    }
+                    grid_stage();
+                }
             }
+            if (collect_over) break;
+        }
+        if (P.mode == 1) {
+            // write this query's surviving candidates as (query, patch) pairs
+            int keep_n = 0;
+            unsigned long long base = 0;
+            if (!collect_over) {
+                for (int b0 = 0; b0 < ncand; b0 += 32)
+                    keep_n += __popc(__ballot_sync(kFull, b0 + lane < ncand && W.cand_lb[b0 + lane] <= ubs));
+                int ok = 0;
+                if (lane == 0) {
+                    atomicAdd(P.pair_n + 1, (unsigned long long)keep_n);
+                    base = atomicAdd(P.pair_n, (unsigned long long)keep_n);
+                    ok = base + keep_n <= (unsigned long long)P.pair_cap;
+                }
+                ok = __shfl_sync(kFull, ok, 0);
+                base = __shfl_sync(kFull, base, 0);
+                if (ok) {
+                    int w = 0;
+                    for (int b0 = 0; b0 < ncand; b0 += 32) {
+                        const bool kp = b0 + lane < ncand && W.cand_lb[b0 + lane] <= ubs;
+                        const unsigned km = __ballot_sync(kFull, kp);
+                        if (kp) {
+                            const int64_t j = (int64_t)base + w + __popc(km & ((1u << lane) - 1));
+                            P.pair_q[j] = P.pair_index ? (int32_t)qi : (int32_t)(qbase + sl);
+                            P.pair_p[j] = W.cand[b0 + lane];
+                        }
+                        w += __popc(km);
+                    }
+                } else {
+                    keep_n = -1;
+                }
+            } else {
+                keep_n = -1;
+            }
+            if (lane == 0 && !P.pair_index) {
+                P.q_first[qbase + sl] = keep_n >= 0 ? (int32_t)base : -1;
+                P.q_count[qbase + sl] = keep_n >= 0 ? keep_n : 0;
+            }
+            __syncwarp();
+            continue;
         }
         grid_stage();
     }
+    if (P.mode == 1) continue;  // collecting only
     if (npool > 0) {
         flush_pool<R, MIXED, GU, GV>(P, W, npool, lane);
         n_newton += npool;
@@ -1242,7 +1341,76 @@ void launch_surf(const SurfQ& P, cudaStream_t s)
     k_query_surfaces<R, GU, GV, MIXED><<<(unsigned)blocks, kWarps * 32, smem, s>>>(P);
 }
 
+// workspace of the learned surface path: the sort's part, then the pair
+// buffer (16 pairs per query on average), per-query pair ranges, counters
+struct SurfPairWs {
+    int32_t *pq, *pp, *first, *count;
+    float* uv;
+    unsigned long long* n;
+    int64_t cap;
+};
+
+int64_t surf_pair_cap(int64_t n_q) { return 16 * n_q + 4096; }
+
+bool carve_surf_pairs(void* ws, size_t bytes, int64_t n_splines, int64_t n_q, SurfPairWs& W, size_t* total)
+{
+    Carver cv(ws, bytes);
+    cv.take<char>(query_ws_bytes(n_splines, n_q));
+    W.cap = surf_pair_cap(n_q);
+    W.pq = cv.take<int32_t>((size_t)W.cap);
+    W.pp = cv.take<int32_t>((size_t)W.cap);
+    W.uv = cv.take<float>(2 * (size_t)W.cap);
+    W.first = cv.take<int32_t>((size_t)n_q);
+    W.count = cv.take<int32_t>((size_t)n_q);
+    W.n = cv.take<unsigned long long>(2);
+    if (total) *total = cv.used + 256;
+    return ws != nullptr && cv.used <= bytes && W.n != nullptr;
+}
+
+template <int GU, int GV>
+bspl_status query_surfaces_learned(const SurfQ& P0, const bspl_segments* segs, const bspl_mlp* mlp, void* ws,
+                                   size_t ws_bytes, cudaStream_t s)
+{
+    SurfPairWs PW{};
+    if (!carve_surf_pairs(ws, ws_bytes, segs->n, P0.n_q, PW, nullptr)) return BSPL_EINVAL;
+    SurfQ P = P0;
+    int32_t* ord = nullptr;
+    if (sort_by_spline(P.q_surf, P.n_q, segs->n, segs->spline_rank, ws, ws_bytes, &ord, &P.work, s) != cudaSuccess)
+        return BSPL_ECUDA;
+    P.order = ord;
+    if (cudaMemsetAsync(PW.n, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return BSPL_ECUDA;
+    P.pair_q = PW.pq;
+    P.pair_p = PW.pp;
+    P.pair_cap = PW.cap;
+    P.pair_n = PW.n;
+    P.q_first = PW.first;
+    P.q_count = PW.count;
+    // 1. the culled candidates of every query, as (query, patch) pairs
+    SurfQ C = P;
+    C.mode = 1;
+    C.counters = nullptr;
+    launch_surf<float, GU, GV, true>(C, s);
+    // 2. the network's (u, v) start of every pair
+    if (mlp && mlp_seed_surface_pairs(mlp, PW.pq, PW.pp, ord, P.q_xyz, segs, PW.cap, PW.n, PW.uv, s) != cudaSuccess)
+        return BSPL_ECUDA;
+    // 3. Newton from the seeds, certification, results
+    SurfQ D = P;
+    D.mode = 2;
+    D.pair_uv = mlp ? PW.uv : nullptr;
+    D.work = P.work + 1;
+    launch_surf<float, GU, GV, true>(D, s);
+    return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
+}
+
 }  // namespace
+
+size_t learned_surf_ws_bytes(int64_t n_splines, int64_t n_q)
+{
+    SurfPairWs W{};
+    size_t total = 0;
+    carve_surf_pairs(nullptr, 0, n_splines, n_q, W, &total);
+    return total;
+}
 
 bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t* q_surf, const double* q_xyz,
                            const bspl_options* opt, int invert, double* uv, double* dist, uint8_t* status,
@@ -1259,7 +1427,10 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
     if (opt) o = *opt;
     int samples = o.samples ? o.samples : 32;
     if (samples != 16 && samples != 32) return BSPL_EINVAL;
-    if (o.prec != BSPL_FP64 && o.prec != BSPL_MIXED) return BSPL_EINVAL;
+    if (o.prec != BSPL_FP64 && o.prec != BSPL_MIXED && o.prec != BSPL_LEARNED_MIXED) return BSPL_EINVAL;
+    const bspl_mlp* mlp = (const bspl_mlp*)o.mlp;
+    if (o.prec == BSPL_LEARNED_MIXED && mlp && (!mlp->params || !mlp->wbf16 || mlp->kind != BSPL_MLP_SURFACE))
+        return BSPL_EINVAL;
     int sort = opt ? o.sort_queries : 1;
     SurfQ P{};
     P.seg_off = segs->seg_off;
@@ -1291,6 +1462,11 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
     P.counters = (unsigned long long*)o.counters;
     P.order = nullptr;
     P.work = nullptr;
+    if (o.prec == BSPL_LEARNED_MIXED) {
+        if (!ws || ws_bytes < learned_surf_ws_bytes(segs->n, n_q)) return BSPL_EINVAL;
+        return samples == 16 ? query_surfaces_learned<4, 4>(P, segs, mlp, ws, ws_bytes, s)
+                             : query_surfaces_learned<8, 4>(P, segs, mlp, ws, ws_bytes, s);
+    }
     if (sort) {
         if (!ws || ws_bytes < query_ws_bytes(segs->n, n_q)) return BSPL_EINVAL;
         int32_t* ord = nullptr;
@@ -1310,3 +1486,60 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
 }
 
 }  // namespace bspl
+
+using namespace bspl;
+
+extern "C" bspl_status bspl_smlp_collect_pairs(const bspl_segments* segs, int64_t n_q, const int32_t* q_surf,
+                                               const double* q_xyz, int64_t cap, int32_t* pair_q, int32_t* pair_patch,
+                                               int64_t* n_pairs, void* ws, size_t ws_bytes, cudaStream_t stream)
+{
+    if (!segs || !segs->is_surface || n_q < 0 || n_q > 0x7fffffffLL || cap < 0 || !n_pairs) return BSPL_EINVAL;
+    if (n_q > 0 && (!q_surf || !q_xyz || (cap > 0 && (!pair_q || !pair_patch)))) return BSPL_EINVAL;
+    if (!segs->seg_off || !segs->grp_off || !segs->rec64 || !segs->rec32 || !segs->grp64 || !segs->grp32 ||
+        !segs->diag || !segs->patch_box || !segs->patch_span || !segs->span_net || !segs->span_net32 ||
+        !segs->patch_net32)
+        return BSPL_EINVAL;
+    SurfPairWs PW{};
+    if (!carve_surf_pairs(ws, ws_bytes, segs->n, n_q, PW, nullptr)) return BSPL_EINVAL;
+    if (cudaMemsetAsync(PW.n, 0, 2 * sizeof(unsigned long long), stream) != cudaSuccess) return BSPL_ECUDA;
+    if (n_q > 0) {
+        SurfQ P{};
+        P.seg_off = segs->seg_off;
+        P.grp_off = segs->grp_off;
+        P.rec64 = segs->rec64;
+        P.rec32 = segs->rec32;
+        P.grp64 = segs->grp64;
+        P.grp32 = segs->grp32;
+        P.prange = segs->prange;
+        P.patch_box = segs->patch_box;
+        P.patch_span = segs->patch_span;
+        P.span_net = segs->span_net;
+        P.span_net32 = segs->span_net32;
+        P.patch_net32 = segs->patch_net32;
+        P.diag = segs->diag;
+        P.tol_rel = segs->tol_rel;
+        P.n = segs->n;
+        P.n_q = n_q;
+        P.q_surf = q_surf;
+        P.q_xyz = q_xyz;
+        P.cert_depth = -1;
+        int32_t* ord = nullptr;
+        if (sort_by_spline(q_surf, n_q, segs->n, segs->spline_rank, ws, ws_bytes, &ord, &P.work, stream) !=
+            cudaSuccess)
+            return BSPL_ECUDA;
+        P.order = ord;
+        P.mode = 1;
+        P.pair_index = 1;
+        P.pair_q = pair_q;
+        P.pair_p = pair_patch;
+        P.pair_cap = cap;
+        P.pair_n = PW.n;
+        P.q_first = PW.first;
+        P.q_count = PW.count;
+        launch_surf<float, 8, 4, true>(P, stream);
+    }
+    if (cudaMemcpyAsync(n_pairs, PW.n, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(n_pairs + 1, PW.n + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+        return BSPL_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
+}

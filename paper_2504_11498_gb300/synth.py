@@ -357,6 +357,30 @@ MLP_SHAPES = (("W1", (128, 16)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128
 MLP_NPARAM = 35332
 
 
+SMLP_NPARAM = 41604
+SMLP_SHAPES = (("W1", (128, 64)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (128, 128)),
+               ("b3", (128,)), ("W4", (2, 128)), ("b4", (2,)))
+
+
+def smlp_init(seed: int = 8) -> np.ndarray:
+    """Initial parameter vector of the surface seed network (layout of
+    include/bspl_mlp.h, BSPL_SMLP_*): weights ~ N(0, 2 / fan_in), biases 0,
+    the weight columns of the 13 zero inputs 0."""
+    rng = np.random.default_rng(seed)
+    theta = np.zeros(SMLP_NPARAM, np.float32)
+    o = 0
+    for name, shp in SMLP_SHAPES:
+        n = int(np.prod(shp))
+        if name[0] in "Ww":
+            fan_in = 51 if name == "W1" else 128
+            w = rng.normal(0.0, np.sqrt(2.0 / fan_in), shp)
+            if name == "W1":
+                w[:, 51:] = 0.0
+            theta[o:o + n] = w.reshape(-1)
+        o += n
+    return theta
+
+
 def mlp_init(seed: int = 7) -> np.ndarray:
     """Initial parameter vector of the seed network (layout of
     include/bspl_mlp.h): weights ~ N(0, 2 / fan_in), biases 0, the weight

@@ -161,3 +161,107 @@ def test_segment_minimiser_tie_takes_smaller_u():
     P = np.array([[-1.0, 0, 0], [-0.5, -1, 0], [0.5, -1, 0], [1, 0, 0]])
     u, D = M.segment_minimiser(P, np.array([0.0, 5.0, 0.0]))
     assert u == 0.0 and D == pytest.approx(26.0)
+
+
+# ------------------------------------------------------- surface network
+
+def test_two_output_gradients_match_central_differences():
+    """The surface network's head (two sigmoid outputs, loss averaged over
+    rows and outputs) by the chain rule vs central differences."""
+    rng = np.random.default_rng(3)
+    p = tiny_params(rng, widths=(6, 4, 3, 3))
+    del p["w4"]
+    p["W4"] = rng.normal(0, 0.8, (2, 3))
+    p["b4"] = rng.normal(0, 0.3, 2)
+    X = rng.normal(0, 1, (5, 6))
+    y = rng.uniform(0, 1, (5, 2))
+    loss, g = M.loss_and_grads(p, X, y)
+    t, _, _ = M.forward(p, X)
+    assert t.shape == (5, 2) and np.isclose(loss, np.mean((t - y) ** 2))
+    h = 1e-6
+    for name, arr in p.items():
+        num = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            old = arr[idx]
+            arr[idx] = old + h
+            lp = M.loss_and_grads(p, X, y)[0]
+            arr[idx] = old - h
+            lm = M.loss_and_grads(p, X, y)[0]
+            arr[idx] = old
+            num[idx] = (lp - lm) / (2 * h)
+        assert np.allclose(g[name], num, rtol=1e-5, atol=1e-9), name
+
+
+def test_surface_layout_round_trip():
+    rng = np.random.default_rng(4)
+    theta = rng.normal(0, 1, M.SNPARAM)
+    theta[-2:] = 0.0
+    p = M.unpack(theta, M.SHAPES_SURF)
+    assert p["W1"].shape == (128, 64) and p["W4"].shape == (2, 128) and p["b4"].shape == (2,)
+    assert np.array_equal(M.pack(p, M.SNPARAM, M.SHAPES_SURF), theta)
+
+
+def _flat_patch(rng):
+    """A bicubic whose net is an affine image of the unit square (bilinear
+    precision): S(u, v) = o + u A + v B exactly."""
+    o, A, B = rng.normal(0, 1, 3), rng.normal(0, 1, 3), rng.normal(0, 1, 3)
+    g = np.arange(4) / 3.0
+    P = o + g[:, None, None] * A + g[None, :, None] * B
+    return P, o, A, B
+
+
+def test_patch_minimiser_flat_patch_closed_form():
+    """On a flat parallelogram the minimiser is the projection onto its
+    plane, clamped to the square: a small convex QP solved here by SciPy."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        P, o, A, B = _flat_patch(rng)
+        q = o + rng.uniform(-0.5, 1.5) * A + rng.uniform(-0.5, 1.5) * B + rng.normal(0, 1, 3)
+        res = optimize.minimize(lambda x: np.sum((o + x[0] * A + x[1] * B - q) ** 2), x0=[0.5, 0.5],
+                                bounds=[(0, 1), (0, 1)], method="L-BFGS-B", options={"ftol": 1e-15, "gtol": 1e-12})
+        u, v, D = M.patch_minimiser(P, q)
+        assert D <= res.fun + 1e-12
+        assert np.allclose([u, v], res.x, atol=1e-6)
+
+
+def test_patch_minimiser_point_on_patch_and_brute_force():
+    rng = np.random.default_rng(6)
+    for _ in range(6):
+        P = rng.uniform(0, 1, (4, 4, 3))
+        u0, v0 = rng.uniform(0, 1, 2)
+        q = M._patch(P, u0, v0)
+        u, v, D = M.patch_minimiser(P, q)
+        assert D <= 1e-24
+        # a random point: no sample of a 401 x 401 grid is closer
+        q = rng.uniform(-0.5, 1.5, 3)
+        u, v, D = M.patch_minimiser(P, q)
+        g = np.linspace(0, 1, 401)
+        uu, vv = np.meshgrid(g, g, indexing="ij")
+        Dg = ((M._patch(P, uu, vv) - q) ** 2).sum(axis=-1)
+        assert D <= Dg.min() + 1e-15
+        assert np.isclose(D, np.sum((M._patch(P, u, v) - q) ** 2), rtol=0, atol=1e-15)
+
+
+def test_surface_features_invariances():
+    """Translating or scaling the patch and the query together leaves the
+    inputs unchanged; a query far along the frame's normal is clamped to the
+    unit normal offset, its tangential part kept."""
+    rng = np.random.default_rng(7)
+    P = rng.uniform(0, 1, (3, 4, 4, 3))
+    q = rng.uniform(-1, 2, (3, 3))
+    X = M.surface_features(P, q)
+    s, t = 3.7, rng.normal(0, 5, 3)
+    assert np.allclose(M.surface_features(P * s + t, q * s + t), X, atol=1e-12)
+    assert np.all(X[:, 51:] == 0)
+    F, _, _, _ = _flat_patch(rng)
+    e1 = F[3, 0] - F[0, 0]
+    e1 /= np.linalg.norm(e1)
+    w = F[0, 3] - F[0, 0]
+    w -= (w @ e1) * e1
+    e2 = w / np.linalg.norm(w)
+    nn = np.cross(e1, e2)
+    q0 = F[0, 0] + 0.3 * (F[3, 0] - F[0, 0])
+    Xf = M.surface_features(np.stack([F, F]), np.stack([q0 + 50 * nn, q0 - 50 * nn]))
+    for k, sign in ((0, 1), (1, -1)):
+        assert np.isclose(Xf[k, 48:51] @ nn, sign)
+    assert np.allclose(Xf[0, 48:51] - Xf[0, 48:51] @ nn * nn, Xf[1, 48:51] - Xf[1, 48:51] @ nn * nn)

@@ -197,6 +197,48 @@ def train_seed(args, rank, dev):
                  "loss_first_epoch": float(loss[0]), "loss_last_epoch": float(loss[-1])}
 
 
+def train_surface_seed(kind, rank, dev, n_queries=600_000, max_pairs=6_000_000, epochs=3):
+    """Trains the surface seed network on (query, patch) pairs of a second
+    surface set of the workload's recipe (c3: the random surfaces, seed 13;
+    c5: the ragged batch's bicubic surfaces, seed 15): pairs from the learned
+    surface path's own culling, labels = the pair's bicubic minimiser,
+    hand-written training kernels.  Untimed preprocessing."""
+    import torch
+    from paper_2504_11498_gb300 import bspl, synth
+    t0 = time.perf_counter()
+    if kind == "c3":
+        ss, sq = synth.surface_set(seed=13 + 1000 * rank, n_surf=256, n_proj=n_queries, n_inv=1)
+    else:
+        cs_, ss, qc_, qs_, rng_ = synth.ragged_mix(seed=15 + 1000 * rank, n_curves=16, n_surf=2048,
+                                                   n_queries=2 * n_queries)
+        _, sq = synth.ragged_queries(cs_, ss, qc_, qs_, rng_)
+    dsf = bspl.DeviceSurfaces(ss, dev)
+    segs = bspl.decompose(dsf, SURF_TOL)
+    ps = torch.as_tensor(sq.proj_surf, device=dev)
+    q = bspl.bspl_eval_surfaces(dsf, ps, torch.as_tensor(sq.proj_uv, device=dev)) + \
+        torch.as_tensor(sq.proj_dir, device=dev) * torch.as_tensor(sq.proj_r, device=dev)[:, None]
+    pq, pp, found = bspl.bspl_smlp_collect_pairs(segs, ps, q, cap=max_pairs)
+    X = bspl.bspl_smlp_features(segs, pq, pp, q)
+    y = bspl.bspl_smlp_labels(segs, pq, pp, q)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    n = X.shape[0]
+    ntr = int(0.9 * n)
+    mlp = bspl.Mlp(synth.smlp_init(8), dev, kind=bspl.MLP_SURFACE)
+    loss = mlp.train(X[:ntr].contiguous(), y[:ntr].contiguous(), epochs=epochs, batch=8192, lr=2e-3,
+                     seed=5).cpu().numpy()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    held = (mlp.forward(X[ntr:].contiguous()) - y[ntr:]).abs().mean().item()
+    centre = (0.5 - y[ntr:]).abs().mean().item()
+    if bspl.mlp_check() != bspl.OK:
+        raise SystemExit("a tensor-core wait timed out during training")
+    return mlp, {"pairs": int(n), "pairs_found": int(found), "epochs": epochs, "batch": 8192,
+                 "surfaces": int(ss.n), "data_ms": 1e3 * (t1 - t0), "train_ms": 1e3 * (t2 - t1),
+                 "loss_first_epoch": float(loss[0]), "loss_last_epoch": float(loss[-1]),
+                 "heldout_seed_abs_err": held, "heldout_patch_centre_abs_err": centre}
+
+
 # ------------------------------------------------------------------- main
 
 def main():
@@ -658,8 +700,8 @@ def run_surface_workloads(args, rank, world, local):
         calls = [("curve_proj", bspl.bspl_project_curves, csegs, pc, cpq),
                  ("curve_inv", bspl.bspl_invert_curves, csegs, ic, ciq)] + calls
         mlp, train = train_seed(args, rank, dev)
-    bufs = {name: bspl.QueryBuffers(sg, qi.numel(), dev, learned=name.startswith("curve"))
-            for name, _, sg, qi, _ in calls}
+    smlp, strain = train_surface_seed(args.workload, rank, dev)
+    bufs = {name: bspl.QueryBuffers(sg, qi.numel(), dev, learned=True) for name, _, sg, qi, _ in calls}
     n_step = sum(qi.numel() for _, _, _, qi, _ in calls)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -674,7 +716,9 @@ def run_surface_workloads(args, rank, world, local):
                 prec = bspl.LEARNED_MIXED if fast else bspl.FP64
                 tuned[(name, fast)] = autotune.tune_curves(sg, qi, qx, prec, mlp=mlp if fast else None)
             else:
-                tuned[(name, fast)] = autotune.tune_surfaces(sg, qi, qx, bspl.MIXED if fast else bspl.FP64)
+                tuned[(name, fast)] = (autotune.tune_surfaces(sg, qi, qx, bspl.LEARNED_MIXED, mlp=smlp) if fast
+                                       else autotune.tune_surfaces(sg, qi, qx, bspl.FP64))
+    surf_mode = [bspl.LEARNED_MIXED, smlp]  # the surfaces' fast path (switched for the ablations)
 
     def opts(name, fast, **kw):
         cfg_ = dict(tuned[(name, fast)], **kw)
@@ -682,7 +726,7 @@ def run_surface_workloads(args, rank, world, local):
             return bspl.make_options(prec=bspl.FP64, **cfg_)
         if name.startswith("curve"):
             return bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp, **cfg_)
-        return bspl.make_options(prec=bspl.MIXED, **cfg_)
+        return bspl.make_options(prec=surf_mode[0], mlp=surf_mode[1], **cfg_)
 
     def step(fast, only=None, **kw):
         for name, fn, sg, qi, qx in calls:
@@ -735,6 +779,15 @@ def run_surface_workloads(args, rank, world, local):
     ms_fast = timed_graph(args.steps, args.warmup)
     ms_plain = timed(False, max(2, args.steps // 3), 2)
     per_call = {name: timed(True, max(2, args.steps // 2), 1, only=name) for name, *_ in calls}
+    # the surfaces through the grid-seeded mixed path, and through the
+    # learned path without its network (seed = patch centre)
+    surf_names = [name for name, *_ in calls if name.startswith("surf")]
+    surf_mode[:] = [bspl.MIXED, None]
+    ms_surf_grid = sum(timed(True, max(2, args.steps // 2), 1, only=nm) for nm in surf_names)
+    surf_mode[:] = [bspl.LEARNED_MIXED, None]
+    ms_surf_nonet = sum(timed(True, max(2, args.steps // 2), 1, only=nm) for nm in surf_names)
+    surf_mode[:] = [bspl.LEARNED_MIXED, smlp]
+    ms_surf_learned = sum(per_call[nm] for nm in surf_names)
     clk = clocks.stop()
     if bspl.mlp_check() != bspl.OK:
         raise SystemExit("a tensor-core wait timed out")
@@ -808,20 +861,23 @@ def run_surface_workloads(args, rank, world, local):
                 "peak_source": "FP32 FMA-chain microbenchmark on this GPU (of measured)",
                 "note": "counted FP32 flops only (Newton iterations of the surface kernel uncounted): a lower bound"}
 
-    cfg = {"workload": label, "tol_rel_curves": TOL, "tol_rel_surfaces": SURF_TOL,
+    cfg = {"workload": label, "tol_rel_curves": TOL, "tol_rel_surfaces": SURF_TOL, "surface_seed_network": strain,
            "launch": {f"{k[0]}|{'fast' if k[1] else 'plain'}": v for k, v in tuned.items()},
            "schedule": "queries grouped heaviest spline first; persistent work-stealing launches",
-           "prec": "surfaces mixed" + (", curves learned_mixed" if has_c else ""),
+           "prec": "surfaces learned_mixed" + (", curves learned_mixed" if has_c else ""),
            "l2": "512 MB flush between timed steps", "patches": int(ssegs.total), "decompose_surfaces_ms": dec_s}
     if has_c:
         cfg.update({"segments": int(csegs.total), "decompose_curves_ms": dec_c, "seed_network": train})
     out = {"metric": METRIC, "value": total_q / (ms_fast * 1e-3), "unit": "pts/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fast, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32+f64 (FP32 search, FP64 finish)" + ("; curves bf16+f32+f64" if has_c else ""),
+           "dtype": "bf16+f32+f64 (BF16 tensor-core seeds, FP32 search, FP64 finish)",
            "data": "synthetic", "config": cfg,
            "plain_fp64": {"value": total_q / (ms_plain * 1e-3), "ms_per_step": ms_plain},
            "speedup_vs_plain": ms_plain / ms_fast, "accuracy": acc,
+           "surfaces_ms_per_step": {"learned_mixed": ms_surf_learned, "learned_without_network": ms_surf_nonet,
+                                    "mixed_grid": ms_surf_grid,
+                                    "note": "surface calls only, each timed alone (not the graph replay)"},
            "e2e": {"value": total_q / (ms_e2e * 1e-3), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
            "gpu_launches": int(graph.n_kernels),

@@ -99,7 +99,7 @@ def tune_curves(segs, q_idx, q_xyz, prec, max_sample=262144, use_cache=True, can
     return dict(best)
 
 
-def tune_surfaces(segs, q_idx, q_xyz, prec, max_sample=131072, use_cache=True, candidates=None):
+def tune_surfaces(segs, q_idx, q_xyz, prec, max_sample=131072, use_cache=True, candidates=None, mlp=None):
     """Best {samples, fp32_steps} for surface queries of this workload (cached)."""
     return tune_curves(segs, q_idx, q_xyz, prec, max_sample=max_sample, use_cache=use_cache,
-                       candidates=candidates or SURFACE_CANDIDATES)
+                       candidates=candidates or SURFACE_CANDIDATES, mlp=mlp)

@@ -476,6 +476,11 @@ def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, ful
         return dict(zip(bspl.STAGE_NAMES, (tot / steps).tolist()))
 
     st_ms = stage_ms(max(3, args.steps // 2))
+    # the same stages without the network (seed u = 1/2): what the seed saves
+    # downstream, against what it costs
+    use_mlp[0] = None
+    st_ms_nonet = stage_ms(max(3, args.steps // 2))
+    use_mlp[0] = mlp
     n_calls = 2 if has_inv else 1
 
     # end to end through the public API with pinned host buffers: inputs into
@@ -565,7 +570,11 @@ def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, ful
     out.update({"value": total_q / (ms_learned * 1e-3), "ms_per_step": ms_learned,
                 "learned_direct": {"value": total_q / (ms_direct * 1e-3), "ms_per_step": ms_direct},
                 "learned_without_network": {"value": total_q / (ms_no_net * 1e-3), "ms_per_step": ms_no_net,
-                                            "note": "same pipeline, seed u = 1/2 instead of the network"},
+                                            "stages_ms_per_step": st_ms_nonet,
+                                            "network_at_bf16_peak_ms": mlp_flops / bf16_peak * 1e3,
+                                            "note": "same pipeline, seed u = 1/2 instead of the network; "
+                                                    "network_at_bf16_peak_ms: the seed stage's cost if it ran "
+                                                    "at the measured BF16 peak"},
                 "mixed_grid": {"value": total_q / (ms_mixed * 1e-3), "ms_per_step": ms_mixed},
                 "plain_fp64": {"value": total_q / (ms_plain * 1e-3), "ms_per_step": ms_plain},
                 "speedup_learned_vs_plain": ms_plain / ms_learned, "speedup_mixed_vs_plain": ms_plain / ms_mixed,

@@ -49,11 +49,14 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--curves", type=int, default=4096, help="curves in the workload")
     ap.add_argument("--queries", type=int, default=1_000_000, help="projection and inversion queries each")
-    ap.add_argument("--workload", default="c4", choices=["c2", "c4", "c3", "c5"],
+    ap.add_argument("--workload", default="c4", choices=["c2", "c4", "c3", "c5", "p"],
                     help="c4 (default): 16M projection queries on the 4,096-curve set (learned seed), with the "
                          "c2 batch measured beside it; c2: 1M projection + 1M inversion queries; "
                          "c3: 1,024 surfaces, 4M + 4M queries; c5: 65,536 cubic curves + 8,192 bicubic "
                          "surfaces, 64M Zipf-skewed queries")
+    ap.add_argument("--surfaces", type=int, default=1024, help="c3: surfaces in the workload")
+    ap.add_argument("--surface-queries", type=int, default=4_000_000,
+                    help="c3: projection and inversion queries each")
     ap.add_argument("--train-curves", type=int, default=2048, help="curves of the seed network's training set")
     ap.add_argument("--train-queries", type=int, default=3_500_000, help="their projection and inversion queries")
     ap.add_argument("--train-pairs", type=int, default=10_000_000, help="training pairs at most")
@@ -249,6 +252,8 @@ def main():
 
     if args.workload in ("c3", "c5"):
         return run_surface_workloads(args, rank, world, local)
+    if args.workload == "p":
+        return run_paper_suite(args, rank, world, local)
     # c4 (default): 16M projection queries on the 4,096-curve set, the
     # learned-seed configuration, with the c2 batch (1M + 1M) measured beside
     # it; c2: the 1M + 1M batch alone
@@ -378,6 +383,7 @@ def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, ful
            for p in (bspl.MIXED, bspl.FP64)}
     cfg[bspl.LEARNED_MIXED] = (autotune.tune_curves(segs, pc, pq, bspl.LEARNED_MIXED, mlp=mlp)
                                if args.samples == 0 else {"occupancy": 0})
+    cfg[bspl.CLIP_MIXED] = {k: v for k, v in cfg[bspl.LEARNED_MIXED].items() if k == "occupancy"}
     use_mlp = [mlp]
 
     def opts(prec, **kw):
@@ -423,6 +429,7 @@ def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, ful
         ms_no_net = timed(lambda: step(bspl.LEARNED_MIXED), args.steps, args.warmup)
         use_mlp[0] = mlp
         ms_mixed = timed(lambda: step(bspl.MIXED), args.steps, args.warmup)
+        ms_clip = timed(lambda: step(bspl.CLIP_MIXED), args.steps, args.warmup)
     ms_plain = timed(lambda: step(bspl.FP64), max(2, args.steps // 3), 2)
 
     # accuracy of the timed paths against the plain FP64 path on every query,
@@ -432,7 +439,8 @@ def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, ful
     step(bspl.FP64)
     ref = (bufs_p.dist.clone(), bufs_i.dist.clone() if has_inv else None)
     acc = {}
-    for name, prec in (("learned_mixed", bspl.LEARNED_MIXED),) + ((("mixed", bspl.MIXED),) if full else ()):
+    for name, prec in (("learned_mixed", bspl.LEARNED_MIXED),) + \
+            ((("mixed", bspl.MIXED), ("clip_search", bspl.CLIP_MIXED)) if full else ()):
         step(prec)
         rel = (bufs_p.dist - ref[0]).abs() / diag_p
         if has_inv:
@@ -458,6 +466,10 @@ def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, ful
         return dict(zip(bspl.COUNTER_NAMES, cnt.cpu().tolist()))
 
     c_learned, c_mixed, c_plain = counted(bspl.LEARNED_MIXED), counted(bspl.MIXED), counted(bspl.FP64)
+    c_clip = counted(bspl.CLIP_MIXED)
+    use_mlp[0] = None
+    c_no_net = counted(bspl.LEARNED_MIXED)
+    use_mlp[0] = mlp
 
     # per-stage device time of the learned path (events recorded by the
     # library at its stage boundaries, every call of a step summed)
@@ -513,15 +525,15 @@ def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, ful
     d2h = sum(x.numel() * x.element_size() for x in h_out)
 
     # max over ranks; every rank processed its own n_step queries
-    (ms_learned, ms_direct, ms_no_net, ms_mixed, ms_plain, ms_e2e), total_q = combine_over_ranks(
-        [ms_learned, ms_direct, ms_no_net, ms_mixed, ms_plain, ms_e2e], n_step, world,
+    (ms_learned, ms_direct, ms_no_net, ms_mixed, ms_clip, ms_plain, ms_e2e), total_q = combine_over_ranks(
+        [ms_learned, ms_direct, ms_no_net, ms_mixed, ms_clip, ms_plain, ms_e2e], n_step, world,
         dist if world > 1 else None, dev)
 
     # rooflines.  ALU work from device counters with per-unit figures: 12
     # flops per box test, 110 per pair classification (E in Bernstein form
     # with its rounding bound), 15 per grid sample, 45 per Newton iteration;
     # the seed network 2 (16*128 + 2*128*128 + 128) = 69,888 flops per row.
-    rows = c_learned["candidates"]  # every pair the culling emitted; the seeded ones run the network
+    rows = c_learned["classified"]  # every pair the culling classified; the seeded ones run the network
     seeded = int(train_rows(segs, pc, pq, ic, iq, has_inv))
     cull_flops = 12 * (c_learned["grp_tested"] + c_learned["seg_tested"]) + 110 * rows
     t_cull = st_ms["cull"] * 1e-3
@@ -576,12 +588,17 @@ def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, ful
                                                     "network_at_bf16_peak_ms: the seed stage's cost if it ran "
                                                     "at the measured BF16 peak"},
                 "mixed_grid": {"value": total_q / (ms_mixed * 1e-3), "ms_per_step": ms_mixed},
+                "clip_search": {"value": total_q / (ms_clip * 1e-3), "ms_per_step": ms_clip,
+                                "note": "the learned path's culling and certification with the paper's search "
+                                        "(closed-form roots of E', elimination, Bezier clipping) in place of "
+                                        "the network and the FP32 isolation"},
                 "plain_fp64": {"value": total_q / (ms_plain * 1e-3), "ms_per_step": ms_plain},
                 "speedup_learned_vs_plain": ms_plain / ms_learned, "speedup_mixed_vs_plain": ms_plain / ms_mixed,
                 "e2e": {"value": total_q / (ms_e2e * 1e-3), "unit": "pts/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "roofline": roofline, "peaks_measured": {"fp32_tflops": p32 / 1e12, "fp64_tflops": p64 / 1e12},
-                "counters": {"learned_mixed": c_learned, "mixed": c_mixed, "plain_fp64": c_plain}})
+                "counters": {"learned_mixed": c_learned, "learned_without_network": c_no_net, "mixed": c_mixed,
+                             "clip_search": c_clip, "plain_fp64": c_plain}})
     return out
 
 
@@ -594,15 +611,182 @@ def train_rows(segs, pc, pq, ic, iq, has_inv):
     return n
 
 
+# ------------------------------------------------------ paper-shaped suite
+
+PAPER_ALPHA = 1e-4  # the paper's decomposition tolerance
+P_SIZES = (10_000, 50_000, 100_000)
+
+
+def run_paper_suite(args, rank, world, local):
+    """--workload p: one curve per paper model (a-r: the models' degrees,
+    knot-vector lengths and control-point counts, 2D models at z = 0),
+    each decomposed on its own at the paper's alpha = 1e-4 (timed: the
+    paper counts it in its totals), then 1e4, 5e4 and 1e5 projection queries
+    per model, each call followed by the refinement on the original curve
+    (bspl_refine_curves), through the learned path (network trained on the
+    curve-set recipe), the mixed grid path and the plain FP64 path.  value =
+    learned pts/s over the 18 models at 1e5 queries each."""
+    from paper_2504_11498_gb300 import synth
+    label = "paper_suite_18: one curve per model a-r (2D at z = 0), 1e4/5e4/1e5 projection queries per model"
+    cs, qs = synth.paper_suite(seed=17 + 1000 * rank, n_proj=P_SIZES[-1], n_inv=0)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        rates, t_all = [], 0.0
+        for _ in range(args.warmup):
+            cpu_oracle_rate(cs, qs, budget_s=2.0, max_q=2000)
+        for _ in range(args.steps):
+            r, cores, nq, el = cpu_oracle_rate(cs, qs, budget_s=8.0, max_q=20000)
+            rates.append(r)
+            t_all += el
+        v = float(np.median(rates))
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "pts/s", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": label, "tol_rel": PAPER_ALPHA},
+                          "cpu_baseline": {"value": v, "unit": "pts/s", "cores": cores, "kind": "oracle",
+                                           "sample": f"{nq} queries of the suite per step"},
+                          "e2e": {"value": v, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2504_11498_gb300 import bspl, build
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    mlp, train = train_seed(args, rank, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    n_max = P_SIZES[-1]
+    per_model, tot = {}, {"learned": 0.0, "mixed": 0.0, "plain": 0.0, "e2e": 0.0}
+    worst, over, launches = 0.0, 0, None
+    for m, (name, dim, p, klen, ncp) in enumerate(synth.PAPER_MODELS):
+        sub = cs.subset([m])
+        dcm = bspl.DeviceCurves(sub, dev)
+        for _ in range(2):  # the first call on a new shape pays one-time setup
+            bspl.decompose(dcm, PAPER_ALPHA)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        segs = bspl.decompose(dcm, PAPER_ALPHA)
+        torch.cuda.synchronize()
+        dec_ms = 1e3 * (time.perf_counter() - t0)
+        sel = slice(m * n_max, (m + 1) * n_max)
+        qc_all = torch.zeros(n_max, dtype=torch.int32, device=dev)
+        q_all = torch.as_tensor(qs.proj_xyz[sel], device=dev)
+        row = {"dim": dim, "degree": p, "knots": klen, "cps": ncp, "segments": int(segs.total),
+               "decompose_ms": dec_ms}
+        paths = (("learned", bspl.LEARNED_MIXED, mlp), ("mixed", bspl.MIXED, None), ("plain", bspl.FP64, None))
+        res = {}
+        for n in P_SIZES:
+            qc, q = qc_all[:n], q_all[:n]
+            for key, prec, net in paths:
+                bufs = bspl.QueryBuffers(segs, n, dev, learned=prec == bspl.LEARNED_MIXED)
+                o = bspl.make_options(prec=prec, mlp=net)
+
+                def call():
+                    r = bspl.bspl_project_curves(segs, qc, q, o, bufs)
+                    bspl.bspl_refine_curves(dcm, qc, q, r)
+
+                for _ in range(max(3, args.warmup)):
+                    call()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
+                torch.cuda.synchronize()
+                for a, b in ev:
+                    flush.fill_(1.0)  # L2 flush between timed calls (outside the events)
+                    a.record(stream)
+                    call()
+                    b.record(stream)
+                torch.cuda.synchronize()
+                ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+                row.setdefault(f"{key}_ms", {})[str(n)] = ms
+                if n == n_max:
+                    tot[key] += ms
+                    res[key] = bufs.dist.clone()
+                    if key == "learned" and launches is None:
+                        with bspl.Graph() as g:
+                            call()
+                        torch.cuda.synchronize()
+                        launches = g.n_kernels
+        # end to end at 1e5: pinned host queries in, results out
+        h_in = torch.as_tensor(qs.proj_xyz[sel].copy()).pin_memory()
+        h_qc = torch.zeros(n_max, dtype=torch.int32).pin_memory()
+        bufs = bspl.QueryBuffers(segs, n_max, dev, learned=True)
+        h_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in (bufs.param, bufs.dist, bufs.status)]
+        o = bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp)
+
+        def e2e():
+            qc_all.copy_(h_qc, non_blocking=True)
+            q_all.copy_(h_in, non_blocking=True)
+            r = bspl.bspl_project_curves(segs, qc_all, q_all, o, bufs)
+            bspl.bspl_refine_curves(dcm, qc_all, q_all, r)
+            for h, d in zip(h_out, (bufs.param, bufs.dist, bufs.status)):
+                h.copy_(d, non_blocking=True)
+
+        for _ in range(3):
+            e2e()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            e2e()
+            b.record(stream)
+        torch.cuda.synchronize()
+        tot["e2e"] += float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        diag = float(segs.diag[0].item())
+        rel = ((res["learned"] - res["plain"]).abs() / diag)
+        worst = max(worst, float(rel.max().item()))
+        over += int((rel > 1e-9).sum().item())
+        row["total_ms_1e4_learned"] = dec_ms + row["learned_ms"][str(P_SIZES[0])]
+        per_model[name] = row
+    clk = clocks.stop()
+    if bspl.mlp_check() != bspl.OK:
+        raise SystemExit("a tensor-core wait timed out")
+    n_all = len(synth.PAPER_MODELS) * n_max
+    (t_l, t_m, t_p, t_e), total_q = combine_over_ranks([tot["learned"], tot["mixed"], tot["plain"], tot["e2e"]],
+                                                       n_all, world, dist if world > 1 else None, dev)
+    out = {"metric": METRIC, "value": total_q / (t_l * 1e-3), "unit": "pts/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_l, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16+f32+f64 (BF16 tensor-core seed, FP32 search, FP64 finish and refinement)",
+           "data": "synthetic",
+           "config": {"workload": label, "tol_rel": PAPER_ALPHA, "refine": "bspl_refine_curves after every call",
+                      "step": "18 calls (one per model) of 1e5 projection queries + refinement",
+                      "l2": "512 MB flush between timed calls", "seed_network": train},
+           "mixed_grid": {"value": total_q / (t_m * 1e-3), "ms_per_step": t_m},
+           "plain_fp64": {"value": total_q / (t_p * 1e-3), "ms_per_step": t_p},
+           "speedup_learned_vs_plain": t_p / t_l,
+           "accuracy": {"learned_vs_plain_fp64_refined": {"max_rel_dist_diff": worst, "queries_over_1e-9": over}},
+           "e2e": {"value": total_q / (t_e * 1e-3), "unit": "pts/s",
+                   "h2d_bytes_per_step": n_all * 28, "d2h_bytes_per_step": n_all * 17},
+           "gpu_launches": int(launches) * len(synth.PAPER_MODELS),
+           "per_model": per_model, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, cores, nq, el = cpu_oracle_rate(cs, qs)
+        out["cpu_baseline"] = {"value": r, "unit": "pts/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{nq} projection queries of the suite, {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------- surfaces and ragged batch
 
-def build_surface_workload(kind, rank):
-    """c3: the 1,024-surface set, 4M projection + 4M inversion queries.
+def build_surface_workload(kind, rank, n_surf=1024, n_q=4_000_000):
+    """c3: the 1,024-surface set, 4M projection + 4M inversion queries
+    (smaller with --surfaces / --surface-queries).
     c5: 65,536 cubic curves + 8,192 bicubic surfaces, 64M queries (32M per
     spline kind, half projection, half inversion), Zipf(1.1) over splines."""
     from paper_2504_11498_gb300 import synth
     if kind == "c3":
-        ss, sq = synth.surface_set(seed=3 + 1000 * rank)
+        ss, sq = synth.surface_set(seed=3 + 1000 * rank, n_surf=n_surf, n_proj=n_q, n_inv=n_q)
         return None, None, ss, sq
     cs, ss, qc, qs, rng = synth.ragged_mix(seed=5 + 1000 * rank)
     cq, sq = synth.ragged_queries(cs, ss, qc, qs, rng)
@@ -642,13 +826,14 @@ def run_surface_workloads(args, rank, world, local):
     Newton, last steps in FP64 on the original patch); the ragged batch's
     curves run the learned path.  Both are set against the plain FP64 path
     on the same queries."""
-    label = {"c3": "surface_set_1024: 4M projection + 4M inversion queries (bi-degree 2..5)",
+    label = {"c3": f"surface_set_{args.surfaces}: {args.surface_queries} projection + {args.surface_queries} "
+                   "inversion queries (bi-degree 2..5)",
              "c5": "ragged_mix: 65,536 cubic curves + 8,192 bicubic surfaces, 64M queries (Zipf 1.1), "
                    "half projection, half inversion per spline kind"}[args.workload]
     if args.impl == "reference":
         if rank != 0:
             return
-        cs, cq, ss, sq = build_surface_workload(args.workload, 0)
+        cs, cq, ss, sq = build_surface_workload(args.workload, 0, args.surfaces, args.surface_queries)
         rates, t_all = [], 0.0
         for _ in range(args.warmup):
             cpu_oracle_surface_rate(cs, cq, ss, sq, budget_s=1.0)
@@ -677,7 +862,7 @@ def run_surface_workloads(args, rank, world, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    cs, cq, ss, sq = build_surface_workload(args.workload, rank)
+    cs, cq, ss, sq = build_surface_workload(args.workload, rank, args.surfaces, args.surface_queries)
     has_c = cs is not None
 
     def T(x, dt):
@@ -861,7 +1046,7 @@ def run_surface_workloads(args, rank, world, local):
         flops = 12 * (c["grp_tested"] + c["seg_tested"]) + 95 * 32 * c["candidates"]
         kern = "k_query_surfaces<float,8,4,true>"
     else:
-        flops = 12 * (c["grp_tested"] + c["seg_tested"]) + 110 * c["candidates"] + 45 * c["newton32_iters"]
+        flops = 12 * (c["grp_tested"] + c["seg_tested"]) + 110 * c["classified"] + 45 * c["newton32_iters"]
         kern = "learned curve path (k_cull_pairs + pair kernels)"
     t_dom = per_call[dominant] * 1e-3
     roofline = {"bound": "alu", "achieved": flops / t_dom / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",

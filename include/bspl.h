@@ -47,8 +47,15 @@ typedef enum {
 typedef enum {
     BSPL_FP64 = 0,          /* cull, seed and Newton all in FP64                  */
     BSPL_MIXED = 1,         /* FP32 cull/seed/early Newton + 2 FP64 Newton steps  */
-    BSPL_LEARNED_MIXED = 2  /* as MIXED with the MLP seed in place of the grid
+    BSPL_LEARNED_MIXED = 2, /* as MIXED with the MLP seed in place of the grid
                                (bspl_mlp.h; surfaces: the surface network)      */
+    BSPL_CLIP_MIXED = 3     /* curves: the learned path's culling and
+                               certification with the paper's search (Secs.
+                               4.2.3-4.4: monotone split by the closed-form
+                               roots of E', elimination by Properties 1-2,
+                               three rounds of Bezier clipping) in place of the
+                               network and of the FP32 root isolation, then the
+                               FP32 and FP64 Newton steps; surfaces: EINVAL  */
 } bspl_precision;
 
 /* per-query status bits */
@@ -214,7 +221,8 @@ typedef struct {
 #define BSPL_CNT_CERT_CELLS 10 /* surfaces: cells evaluated by the certification search */
 #define BSPL_CNT_CERT_LEAVES 11 /* surfaces: certification cells handed to Newton */
 #define BSPL_CNT_CERT_OVERFLOW 12 /* surfaces: cells sent to Newton early (stack full) */
-#define BSPL_NCOUNTERS 13
+#define BSPL_CNT_CLASSIFIED 13 /* learned path: pairs classified by the Bernstein signs of E */
+#define BSPL_NCOUNTERS 14
 
 /* workspace sizes: op is one of */
 #define BSPL_OP_DECOMPOSE_CURVES 1
@@ -308,8 +316,9 @@ bspl_status bspl_invert_surfaces(const bspl_segments* segs, int64_t n_q, const i
  * loads the library keeps reserved until the process exits.
  *
  * Limits: n_q <= BSPL_NOALLOC_MAX_QUERIES and segs->n <= BSPL_NOALLOC_MAX_SPLINES.
- * With opt->prec = BSPL_LEARNED_MIXED the candidate-pair buffer (about 1 KB
- * per query) shares the array, which lowers the limit to about 7,500 queries
+ * With opt->prec = BSPL_LEARNED_MIXED the culling-candidate and pair buffers
+ * (about 1.4 KB per query) share the array, which lowers the limit to about
+ * 5,800 queries
  * (exactly: bspl_workspace_bytes(BSPL_OP_QUERY_CURVES_LEARNED, segs->n, 0, 0,
  * n_q) must not exceed BSPL_NOALLOC_SCRATCH_BYTES).  Larger calls return
  * BSPL_ENOSPACE before anything is launched.
@@ -335,6 +344,31 @@ bspl_status bspl_eval_curves(const bspl_curves* curves, int64_t n_q, const int32
 /* Evaluates the ORIGINAL surfaces at uv [n_q][2]: xyz [n_q][3]. */
 bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const int32_t* q_surf,
                                const double* uv, double* xyz, cudaStream_t stream);
+
+/* Refines curve projection / inversion results on the ORIGINAL curves (the
+ * problem of Sec. 3, Eqs. projection and inversion, posed on C itself rather
+ * than on the cubic approximant the query calls search): from t [n_q] (the
+ * original parameter, as bspl_project_curves / bspl_invert_curves return
+ * it), FP64 Newton on E = (C - q).C', E' = C'.C' + (C - q).C'' (Sec. 4.2.3,
+ * Eqs. Et and E't) with C, C', C'' by the Cox-de Boor recursion on the
+ * original knots and control points; every step is clamped to the domain and
+ * halved until the squared distance does not grow, until E is zero to its
+ * FP64 rounding.  At most max_iter steps (0: 16; at most 100).
+ *   in/out  t [n_q], dist [n_q]: the refined parameter and |C(t) - q|, never
+ *           larger than the distance at the starting t;
+ *   in/out  status [n_q]: queries with BSPL_Q_INVALID are skipped; otherwise
+ *           CONVERGED / NONCONV and AT_END are set from the refinement and,
+ *           with invert != 0 and diag != NULL (the per-curve diagonals, e.g.
+ *           bspl_segments.diag), OFF_CURVE from the refined distance.
+ * The result is the local minimum of the original curve reached from the
+ * approximant's answer: it is the global one unless the original curve has
+ * another local minimum whose distance is within twice the decomposition
+ * tolerance of it.  Degrees 1..31 (others are left unchanged).
+ * BSPL_EINVAL for NULL arrays with n_q > 0, n_q < 0 or max_iter outside
+ * 0..100. */
+bspl_status bspl_refine_curves(const bspl_curves* curves, const double* diag, int invert, int64_t n_q,
+                               const int32_t* q_curve, const double* q_xyz, int32_t max_iter, double* t,
+                               double* dist, uint8_t* status, cudaStream_t stream);
 
 /* Human-readable name of a status code (static string). */
 const char* bspl_status_string(bspl_status s);

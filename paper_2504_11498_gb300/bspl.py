@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libbspl.so")
 
 OK, EINVAL, ENOSPACE, ECUDA, ENOTCONV, ETIMEOUT = 0, 1, 2, 3, 4, 5
-FP64, MIXED, LEARNED_MIXED = 0, 1, 2
+FP64, MIXED, LEARNED_MIXED, CLIP_MIXED = 0, 1, 2, 3
 Q_CONVERGED, Q_FALLBACK, Q_AT_END, Q_NONCONV, Q_OFF_CURVE, Q_INVALID = 1, 2, 4, 8, 16, 32
 GROUP = 32
 CREC64, CREC32, SREC64, SREC32, GREC64, GREC32 = 18, 24, 54, 72, 12, 12
@@ -35,9 +35,10 @@ SMLP_IN, SMLP_OUT, SMLP_NPARAM, SMLP_NBF16 = 64, 2, 41604, 8192 + 4 * 16384 + 25
 SMLP_OFF = {"W1": 0, "b1": 8192, "W2": 8320, "b2": 24704, "W3": 24832, "b3": 41216, "W4": 41344, "b4": 41600}
 NET = {MLP_CURVE: (MLP_IN, 1, MLP_NPARAM, MLP_NBF16, OP_MLP_TRAIN),
        MLP_SURFACE: (SMLP_IN, SMLP_OUT, SMLP_NPARAM, SMLP_NBF16, OP_SMLP_TRAIN)}
-NCOUNTERS = 13
+NCOUNTERS = 14
 COUNTER_NAMES = ["queries", "seg_tested", "grp_tested", "candidates", "newton", "fallback", "nonconv",
-                 "newton32_iters", "newton64_iters", "iso_pairs", "cert_cells", "cert_leaves", "cert_overflow"]
+                 "newton32_iters", "newton64_iters", "iso_pairs", "cert_cells", "cert_leaves", "cert_overflow",
+                 "classified"]
 
 
 class BsplError(RuntimeError):
@@ -82,7 +83,7 @@ class bspl_mlp(C.Structure):
 EXPORTS = ["bspl_graph_begin", "bspl_graph_end", "bspl_graph_launch", "bspl_graph_destroy",
            "bspl_project_curves_noalloc", "bspl_measure_fma_peak", "bspl_workspace_bytes", "bspl_decompose", "bspl_project_curves", "bspl_invert_curves",
            "bspl_project_surfaces", "bspl_invert_surfaces", "bspl_eval_curves", "bspl_eval_surfaces",
-           "bspl_status_string"]
+           "bspl_refine_curves", "bspl_status_string"]
 
 _lib = None
 _lock = threading.Lock()
@@ -110,6 +111,9 @@ def lib():
                               C.c_size_t, vp]
             L.bspl_eval_curves.restype = st
             L.bspl_eval_curves.argtypes = [C.POINTER(bspl_curves), i64, vp, vp, vp, vp]
+            L.bspl_refine_curves.restype = st
+            L.bspl_refine_curves.argtypes = [C.POINTER(bspl_curves), vp, C.c_int, i64, vp, vp, C.c_int32, vp, vp,
+                                             vp, vp]
             L.bspl_eval_surfaces.restype = st
             L.bspl_eval_surfaces.argtypes = [C.POINTER(bspl_surfaces), i64, vp, vp, vp, vp]
             L.bspl_status_string.restype = C.c_char_p
@@ -361,7 +365,7 @@ def _query(fn_name, segs, q_idx, q_xyz, opts, bufs, stream):
 
 
 def _learned(opts):
-    return opts is not None and opts.prec == LEARNED_MIXED
+    return opts is not None and opts.prec in (LEARNED_MIXED, CLIP_MIXED)
 
 
 def bspl_project_curves(segs, q_curve, q_xyz, opts=None, bufs=None, stream=None):
@@ -452,6 +456,18 @@ def bspl_eval_curves(curves: DeviceCurves, q_curve, t, stream=None):
                                 _stream(stream))
     _check(rc, "bspl_eval_curves")
     return out
+
+
+def bspl_refine_curves(curves: DeviceCurves, q_curve, q_xyz, res: "QueryResult", invert: bool = False,
+                       diag=None, max_iter: int = 0, stream=None):
+    """Refines a curve projection / inversion result in place on the
+    original curves (include/bspl.h, bspl_refine_curves); diag: the per-curve
+    diagonals (e.g. the segments' diag) for the OFF_CURVE bit of inversions."""
+    rc = lib().bspl_refine_curves(C.byref(curves.c), _ptr(diag) if diag is not None else None, int(invert),
+                                  q_curve.numel(), _ptr(q_curve), _ptr(q_xyz), int(max_iter), _ptr(res.param),
+                                  _ptr(res.dist), _ptr(res.status), _stream(stream))
+    _check(rc, "bspl_refine_curves")
+    return res
 
 
 def bspl_eval_surfaces(surfs: DeviceSurfaces, q_surf, uv, stream=None):

@@ -71,6 +71,13 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
     return eval_surfaces(surfaces, n_q, q_surf, uv, xyz, stream);
 }
 
+bspl_status bspl_refine_curves(const bspl_curves* curves, const double* diag, int invert, int64_t n_q,
+                               const int32_t* q_curve, const double* q_xyz, int32_t max_iter, double* t,
+                               double* dist, uint8_t* status, cudaStream_t stream)
+{
+    return refine_curves(curves, diag, invert, n_q, q_curve, q_xyz, max_iter, t, dist, status, stream);
+}
+
 const char* bspl_status_string(bspl_status s)
 {
     switch (s) {

@@ -60,6 +60,8 @@ bspl_status eval_curves(const bspl_curves* c, int64_t n_q, const int32_t* qc, co
                         cudaStream_t s);
 bspl_status eval_surfaces(const bspl_surfaces* c, int64_t n_q, const int32_t* qs, const double* uv, double* xyz,
                           cudaStream_t s);
+bspl_status refine_curves(const bspl_curves* c, const double* diag, int invert, int64_t n_q, const int32_t* qc,
+                          const double* q_xyz, int max_iter, double* t, double* dist, uint8_t* status, cudaStream_t s);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

@@ -3,8 +3,9 @@
 // Inference (k_mlp_fused): one persistent block per SM of four warpgroups.
 // The BF16 weights of the three 128-wide layers stay in shared memory; each
 // warpgroup runs its own tiles of 128 rows: inputs -> shared memory (BF16) ->
-// tcgen05.mma into its 128 tensor-memory columns -> tcgen05.ld, bias, GELU,
-// BF16 -> shared memory -> next layer; the last layer's epilogue also takes
+// tcgen05.mma into its 128 tensor-memory columns -> tcgen05.ld, bias, GELU
+// (packed BF16 arithmetic, two columns per instruction) -> shared memory ->
+// next layer; the last layer's epilogue also takes
 // the dot product with w4 and the sigmoid.  One thread per warpgroup issues
 // the MMAs; completion comes back through an mbarrier.
 //
@@ -319,7 +320,7 @@ __device__ __forceinline__ void epi_hidden(uint32_t tl, const float* b, uint8_t*
         uint32_t pk[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-            pk[j] = tc::pack_bf16(tc::gelu(v[2 * j] + b[cb * 32 + 2 * j]), tc::gelu(v[2 * j + 1] + b[cb * 32 + 2 * j + 1]));
+            pk[j] = tc::gelu_bf16x2(v[2 * j] + b[cb * 32 + 2 * j], v[2 * j + 1] + b[cb * 32 + 2 * j + 1]);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             *reinterpret_cast<uint4*>(X + (r >> 3) * kH * 16 + (cb * 4 + q) * 128 + (r & 7) * 16) =
@@ -444,11 +445,12 @@ __global__ void __launch_bounds__(kFusedWG * 128, 1)
             float v[32];
             tc::tmem_ld32(tl + cb * 32, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
+            for (int j = 0; j < 32; j += 2) {
                 const int c = cb * 32 + j;
-                const float h = bf2f(f2bf(tc::gelu(v[j] + bias[2 * kH + c])));
+                const uint32_t hp = tc::gelu_bf16x2(v[j] + bias[2 * kH + c], v[j + 1] + bias[2 * kH + c + 1]);
+                const float h0 = __uint_as_float(hp << 16), h1 = __uint_as_float(hp & 0xffff0000u);
 #pragma unroll
-                for (int o = 0; o < N::OUT; ++o) z[o] = fmaf(h, w4[o * kH + c], z[o]);
+                for (int o = 0; o < N::OUT; ++o) z[o] = fmaf(h1, w4[o * kH + c + 1], fmaf(h0, w4[o * kH + c], z[o]));
             }
         }
         if (i < n) {

@@ -44,7 +44,8 @@ extern "C" bspl_status bspl_project_curves_noalloc(const bspl_segments* segs, in
     if (bspl::query_ws_bytes(segs->n, n_q) > kScratchBytes) return BSPL_ENOSPACE;
     // the learned precision adds its candidate-pair buffer (about 1 KB per
     // query), so it fits far fewer queries into the same array
-    if (opt && opt->prec == BSPL_LEARNED_MIXED && bspl::learned_ws_bytes(segs->n, n_q) > kScratchBytes)
+    if (opt && (opt->prec == BSPL_LEARNED_MIXED || opt->prec == BSPL_CLIP_MIXED) &&
+        bspl::learned_ws_bytes(segs->n, n_q) > kScratchBytes)
         return BSPL_ENOSPACE;
     void* ws = nullptr;
     bspl_status st = scratch_address(&ws);

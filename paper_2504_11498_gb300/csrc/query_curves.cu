@@ -510,7 +510,7 @@ bspl_status query_curves(const bspl_segments* segs, int64_t n_q, const int32_t* 
     if (opt) o = *opt;
     int samples = o.samples ? o.samples : 16;
     if (samples != 8 && samples != 16 && samples != 32) return BSPL_EINVAL;
-    if (o.prec == BSPL_LEARNED_MIXED)
+    if (o.prec == BSPL_LEARNED_MIXED || o.prec == BSPL_CLIP_MIXED)
         return query_curves_learned(segs, n_q, q_curve, q_xyz, &o, invert, t, dist, status, ws, ws_bytes, s);
     if (o.prec != BSPL_FP64 && o.prec != BSPL_MIXED) return BSPL_EINVAL;
     int sort = opt ? o.sort_queries : 1;

@@ -1,11 +1,14 @@
 // Curve projection / inversion with the learned Newton seed (bspl_mlp.h).
 //
 // Pipeline (one stream, no host synchronisation):
-//   1. k_cull_pairs: queries grouped by curve, one warp per 32 queries, the
-//      same two-level box culling as the grid kernel.  Every surviving
-//      (query, segment) pair is classified by the signs of the Bernstein
-//      coefficients of E = (C - q).C' (degree 5, the T matrix of Sec. 4.3),
-//      each coefficient compared with a bound on its FP32 rounding error:
+//   1. k_cull_cands: queries grouped by curve, one warp per 32 queries, the
+//      same two-level box culling as the grid kernel; the surviving (query,
+//      segment) candidates and each query's final upper bound go to global
+//      memory.  k_classify, one thread per candidate: every candidate whose
+//      box still passes its query's bound is classified by the signs of the
+//      Bernstein coefficients of E = (C - q).C' (degree 5, the T matrix of
+//      Sec. 4.3), each coefficient compared with a bound on its FP32
+//      rounding error:
 //        one sign change, E(0) < 0 < E(1)  -> exactly one minimum inside:
 //                                             SEED (the network's job);
 //        no sign change                     -> minimum at u = 0 or u = 1;
@@ -13,8 +16,11 @@
 //                                             end;
 //        more changes, or a coefficient within its rounding bound of 0
 //                                           -> certified isolation (ISO).
-//      Pairs go to one buffer: seeds from the front, the others from the
-//      back, so the network reads a dense range.
+//      A pair whose minimum is at an end is dropped when its FP32 distance
+//      there, less its rounding bound, exceeds the query's upper bound (most
+//      pairs that pass the box test are of this kind).  Pairs go to one
+//      buffer: seeds from the front, the others from the back, so the
+//      network reads a dense range.
 //   2. the fused MLP (mlp.cu) writes the seed u0 of every SEED pair (without
 //      a network: u0 = 1/2).
 //   3. one thread per pair: FP32 Newton in the segment's local frame
@@ -25,11 +31,13 @@
 //      below 1e-9) for the pairs whose lower bound does not exceed their
 //      query's best upper bound; then the per-query
 //      lexicographic minimum over (D, segment) by two more atomicMin passes,
-//      and the unique winning pair writes the result (Sec. 4.4.2).
+//      the unique winning pair is recorded per query, and one pass over the
+//      queries writes every result once (Sec. 4.4.2).
 //   4. queries whose pairs did not fit the buffer run through the grid
 //      kernel (mixed precision) over a device-side list.
 #include "../../include/bspl_mlp.h"
 #include "query_common.cuh"
+#include "clip.cuh"
 #include "tc05.cuh"
 
 namespace bspl {
@@ -55,7 +63,8 @@ struct PairBuf {
     uint8_t* fl;
     int64_t cap;
     unsigned long long* cnt;  // [0] reserved, [1] seeds, [2] others, [3] overflowed queries, [4] finished,
-                              // [5] deferred to the FP64 isolation
+                              // [5] deferred to the FP64 isolation, [6] culling batches taken,
+                              // [7] culling candidates reserved
     int32_t* fin;             // buffer slots of the pairs that got the FP64 finish
     int32_t* iso;             // buffer slots of the pairs deferred to the FP64 isolation
     const float* qrec;        // per sorted query: q hi[3], q lo[3], eps, curve (int bits; -1 invalid)
@@ -65,6 +74,13 @@ struct PairBuf {
     unsigned* best32;         // per query: FP32 upper bound of the distance (float bits)
     unsigned long long* best64;
     int* bestseg;
+    int32_t* cpos;            // culling candidates: sorted query position,
+    int32_t* cseg;            //   segment
+    float* clb;               //   and squared distance lower bound of its box
+    int64_t ccap;
+    float* ubq;               // per sorted query: its slacked squared upper bound after culling
+    int32_t* wslot;           // per sorted query: buffer slot of the winning pair, or -1
+    int32_t* ovf;             // per sorted query: 1 once it is sent to the grid kernel
 };
 
 
@@ -83,12 +99,17 @@ __device__ __forceinline__ void local32(const CurveQ& P, int64_t seg, const floa
 // that the culling kernels run without FP64 instructions (on this GPU one
 // FP64 warp instruction occupies its pipe for tens of cycles)
 __global__ void k_qrec(const int32_t* __restrict__ qc, const double* __restrict__ q_xyz,
-                       const double* __restrict__ diag, int64_t n, const int32_t* __restrict__ order, int64_t n_q,
-                       float* __restrict__ qrec)
+                       const double* __restrict__ diag, int64_t n, int64_t n_q, PairBuf B)
 {
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n_q) return;
-    const int64_t i = order[pos];
+    float* qrec = const_cast<float*>(B.qrec);
+    const int64_t i = B.order[pos];
+    B.best32[pos] = 0x7f800000u;
+    B.best64[pos] = 0x7ff0000000000000ull;
+    B.bestseg[pos] = 0x7fffffff;
+    B.wslot[pos] = -1;
+    B.ovf[pos] = 0;
     const int c = qc[i];
     float o[8];
     bool bad = c < 0 || c >= n;
@@ -108,8 +129,7 @@ __global__ void k_qrec(const int32_t* __restrict__ qc, const double* __restrict_
     d[1] = make_float4(o[4], o[5], o[6], o[7]);
 }
 
-constexpr int kEmitCap = 256;  // classified pairs staged per warp before one global reservation
-constexpr int kCandCap2 = 160; // tentative candidates of a warp batch before classification
+constexpr int kCandCap2 = 160; // candidates of a warp batch staged before one global reservation
 constexpr int kGrpChunk = 64;  // culling groups staged in shared memory per bulk copy
 constexpr int kSurvCap = 128;  // surviving (query, group) entries per warp batch
 constexpr uint64_t kCopyWaitNs = 1000000000ull;
@@ -127,21 +147,19 @@ __device__ int g_copy_timeout;
 // kernel, and the classified pairs are staged and written out in bulk.
 // MINB: blocks per SM the register allocation must allow (1: the compiler's
 // choice; 6 or 8 blocks of 4 warps, the latter with a few spilled registers)
-template <bool SEEDS_ONLY, int MINB>
-__global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, PairBuf B)
+template <int MINB>
+__global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_cands(CurveQ P, PairBuf B)
 {
+    // at 8 blocks per SM the shared memory holds one segment-record buffer
+    // per warp (the other warps of the SM hide the copy); below, two
+    constexpr bool kDouble = MINB < 8;
     __shared__ int s_seg[kWarps][kCandCap2];
     __shared__ float s_lb[kWarps][kCandCap2];
     __shared__ uint8_t s_cslot[kWarps][kCandCap2];
-    __shared__ int s_pseg[kWarps][kEmitCap];
-    __shared__ uint8_t s_pslot[kWarps][kEmitCap];
-    __shared__ uint8_t s_pkind[kWarps][kEmitCap];
-    __shared__ int32_t s_qi[kWarps][kQPW];
-    __shared__ float s_ub[kWarps][kQPW];
     // level 1 stages group records here; level 2 reuses it as one of the two
     // buffers of segment records (BSPL_GROUP x BSPL_CREC32 floats = the same 3 KB)
     __shared__ __align__(128) float s_grp[kWarps][kGrpChunk * BSPL_GREC32];
-    __shared__ __align__(128) float s_seg2[kWarps][BSPL_GROUP * BSPL_CREC32];
+    __shared__ __align__(128) float s_seg2[kWarps][kDouble ? BSPL_GROUP * BSPL_CREC32 : 4];
     __shared__ int s_sv[kWarps][kSurvCap];       // surviving groups of the batch, in order
     __shared__ unsigned s_svm[kWarps][kSurvCap]; // the query slots that kept each
     __shared__ __align__(8) uint64_t s_bar[kWarps][2];
@@ -149,10 +167,6 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
     int* cseg = s_seg[wid];
     float* clb = s_lb[wid];
     uint8_t* ctslot = s_cslot[wid];
-    int* pseg = s_pseg[wid];
-    uint8_t* pslot = s_pslot[wid];
-    uint8_t* pkind = s_pkind[wid];
-    int32_t* qis = s_qi[wid];
     float* grs = s_grp[wid];
     uint64_t* bar = &s_bar[wid][0];
     const float* rec = P.rec32;
@@ -173,16 +187,14 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
          batch = next_batch(B.work, (int64_t)blockIdx.x * kWarps + wid, nbatch, round)) {
     const int64_t qbase = batch * kQPW;
     const int nslots = (int)min((int64_t)kQPW, P.n_q - qbase);
-    unsigned long long n_grp = 0, n_seg = 0, n_pairs = 0;
-    int npend = 0;
-    unsigned over_mask = 0;  // query slots with pairs that did not fit the buffer
+    unsigned long long n_grp = 0, n_seg = 0;
+    unsigned over_mask = 0;  // query slots with candidates that did not fit the buffer
 
     // this lane's query (lane = slot)
     float qx = 0.f, qy = 0.f, qz = 0.f, eps = 0.f;
     int myc = -1;
     if (lane < nslots) {
         const int64_t pos = qbase + lane;
-        const int64_t qi = B.order[pos];
         const float4 qa = *reinterpret_cast<const float4*>(B.qrec + 8 * pos);
         const float4 qb = *reinterpret_cast<const float4*>(B.qrec + 8 * pos + 4);
         qx = qa.x;
@@ -190,17 +202,6 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
         qz = qa.z;
         eps = qb.z;
         myc = __float_as_int(qb.w);
-        qis[lane] = (int32_t)qi;
-        if (!SEEDS_ONLY) {
-            P.t[qi] = __longlong_as_double(0x7ff8000000000000LL);
-            P.dist[qi] = __longlong_as_double(0x7ff8000000000000LL);
-            P.status[qi] = myc < 0 ? BSPL_Q_INVALID : BSPL_Q_NONCONV;
-            if (myc >= 0) {
-                B.best32[pos] = 0x7f800000u;
-                B.best64[pos] = 0x7ff0000000000000ull;
-                B.bestseg[pos] = 0x7fffffff;
-            }
-        }
     }
 
     // stage groups [g, g + n) of the group table; returns where to read them
@@ -259,70 +260,13 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
         if (in_run) n_grp += (unsigned long long)G;
         done = done || in_run;
     }
-    if (lane < nslots) s_ub[wid][lane] = ub;
     __syncwarp();
-
-    // one reservation per kind for the staged pairs, then the copy out
-    auto flush_pending = [&]() {
-        __syncwarp();
-        int cs = 0, co = 0;
-        for (int base = 0; base < npend; base += 32) {
-            const int k = base + lane;
-            const bool in = k < npend;
-            cs += __popc(__ballot_sync(kFull, in && pkind[k] == kSeed));
-            co += __popc(__ballot_sync(kFull, in && pkind[k] != kSeed));
-        }
-        if (cs + co > 0) {
-            unsigned long long bs = 0, bo = 0;
-            int ok = 0;
-            if (lane == 0) {
-                const unsigned long long tot = atomicAdd(B.cnt, (unsigned long long)(cs + co));
-                ok = tot + cs + co <= (unsigned long long)B.cap;
-                if (ok) {
-                    bs = cs ? atomicAdd(B.cnt + 1, (unsigned long long)cs) : 0;
-                    bo = co ? atomicAdd(B.cnt + 2, (unsigned long long)co) : 0;
-                    n_pairs += (unsigned long long)(cs + co);
-                }
-            }
-            ok = __shfl_sync(kFull, ok, 0);
-            bs = __shfl_sync(kFull, bs, 0);
-            bo = __shfl_sync(kFull, bo, 0);
-            unsigned om = 0;
-            for (int base = 0; base < npend; base += 32) {
-                const int k = base + lane;
-                const bool in = k < npend;
-                const bool sd = in && pkind[k] == kSeed, ot = in && pkind[k] != kSeed;
-                const unsigned ms = __ballot_sync(kFull, sd), mo = __ballot_sync(kFull, ot);
-                if (ok) {
-                    if (sd) {
-                        const int64_t idx = (int64_t)bs + __popc(ms & lt);
-                        B.pq[idx] = SEEDS_ONLY ? qis[pslot[k]] : (int32_t)(qbase + pslot[k]);
-                        B.ps[idx] = pseg[k];
-                        if (B.kind) B.kind[idx] = kSeed;
-                    }
-                    if (ot) {
-                        const int64_t idx = B.cap - 1 - ((int64_t)bo + __popc(mo & lt));
-                        B.pq[idx] = (int32_t)(qbase + pslot[k]);
-                        B.ps[idx] = pseg[k];
-                        B.kind[idx] = pkind[k];
-                    }
-                } else if (in) {
-                    om |= 1u << pslot[k];
-                }
-                bs += __popc(ms);
-                bo += __popc(mo);
-            }
-            over_mask |= __reduce_or_sync(kFull, om);
-        }
-        npend = 0;
-        __syncwarp();
-    };
 
     // ---- level 2: every surviving (query, group) entry of the batch, in
     // list order; lanes = the group's 32 segments.  Each query's upper bound
     // lives in its own lane and tightens as its entries are scanned; the
-    // tentative candidates of all queries share one buffer and are classified
-    // 32 at a time.
+    // candidates of all queries share one staging buffer, which is filtered
+    // against the current bounds and written out in bulk when it fills.
     int64_t s0l = 0, s1l = 0, g0l = 0;
     if (lane < nslots && myc >= 0) {
         s0l = P.seg_off[myc];
@@ -331,37 +275,49 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
     }
     float ubs_l = slacked(ub, eps);
     int ncand = 0;
-    auto emit = [&]() {
+    auto flush_cands = [&]() {
         __syncwarp();
+        int nk = 0;
         for (int base = 0; base < ncand; base += 32) {
             const int k = base + lane;
             const bool in = k < ncand;
             const int sl = in ? ctslot[k] : 0;
             const float ubk = __shfl_sync(kFull, ubs_l, sl);
-            const bool act = in && clb[k] <= ubk;
-            const int seg = act ? cseg[k] : 0;
-            uint8_t kind = kIso;
-            if (act) {
-                float cl[12];
-                local32(P, seg, B.qrec + 8 * (qbase + sl), cl);
-                kind = classify(cl);
-            }
-            const bool keep = act && (!SEEDS_ONLY || kind == kSeed);
+            const float lb = in ? clb[k] : 0.f;
+            const int seg = in ? cseg[k] : 0;
+            const bool keep = in && lb <= ubk;
             const unsigned m = __ballot_sync(kFull, keep);
-            if (npend + __popc(m) > kEmitCap) flush_pending();
+            __syncwarp();  // every lane has read its entry before the compaction writes
             if (keep) {
-                const int pos = npend + __popc(m & lt);
-                pseg[pos] = seg;
-                pslot[pos] = (uint8_t)sl;
-                pkind[pos] = kind;
+                const int j = nk + __popc(m & lt);
+                cseg[j] = seg;
+                clb[j] = lb;
+                ctslot[j] = (uint8_t)sl;
             }
-            npend += __popc(m);
+            nk += __popc(m);
+        }
+        __syncwarp();
+        if (nk > 0) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(B.cnt + 7, (unsigned long long)nk);
+            base = __shfl_sync(kFull, base, 0);
+            unsigned om = 0;
+            for (int k = lane; k < nk; k += 32) {
+                const int64_t j = (int64_t)base + k;
+                if (j < B.ccap) {
+                    B.cpos[j] = (int32_t)(qbase + ctslot[k]);
+                    B.cseg[j] = cseg[k];
+                    B.clb[j] = clb[k];
+                } else {
+                    om |= 1u << ctslot[k];
+                }
+            }
+            over_mask |= __reduce_or_sync(kFull, om);
         }
         ncand = 0;
         __syncwarp();
     };
-    // one entry's segment records, loaded ahead of their use (the loads of
-    // entry e + 1 are in flight while entry e is reduced)
+    // box lower bounds and start-point upper bound of one segment per lane
     struct Ent {
         float b[6], p[3];
         int64_t s;
@@ -369,24 +325,6 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
         int sl;
         int nseg;
     };
-    auto fetch = [&](int sl, int64_t g, Ent& E) {
-        const int64_t s0 = __shfl_sync(kFull, s0l, sl), s1 = __shfl_sync(kFull, s1l, sl);
-        const int64_t g0 = __shfl_sync(kFull, g0l, sl);
-        const int64_t ss = s0 + (g - g0) * BSPL_GROUP;
-        const int64_t se = min(ss + BSPL_GROUP, s1);
-        E.sl = sl;
-        E.s = ss + lane;
-        E.nseg = (int)(se - ss);
-        E.valid = E.s < se;
-        if (E.valid) {
-            const float* r = rec + (int64_t)RW * E.s;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) E.b[k] = r[k];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) E.p[k] = r[6 + k];
-        }
-    };
-    // box lower bounds and start-point upper bound of one fetched entry
     auto scan = [&](const Ent& E) {
         const int sl = E.sl;
         const float sx = __shfl_sync(kFull, qx, sl), sy = __shfl_sync(kFull, qy, sl), sz = __shfl_sync(kFull, qz, sl);
@@ -411,20 +349,34 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
             ctslot[pos] = (uint8_t)sl;
         }
         ncand += __popc(km);
-        if (ncand > kCandCap2 - 32) emit();
+        if (ncand > kCandCap2 - 32) flush_cands();
     };
     auto scan_entry = [&](int sl, int64_t g) {
+        const int64_t s0 = __shfl_sync(kFull, s0l, sl), s1 = __shfl_sync(kFull, s1l, sl);
+        const int64_t g0 = __shfl_sync(kFull, g0l, sl);
+        const int64_t ss = s0 + (g - g0) * BSPL_GROUP;
+        const int64_t se = min(ss + BSPL_GROUP, s1);
         Ent E;
-        fetch(sl, g, E);
+        E.sl = sl;
+        E.s = ss + lane;
+        E.nseg = (int)(se - ss);
+        E.valid = E.s < se;
+        if (E.valid) {
+            const float* r = rec + (int64_t)RW * E.s;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) E.b[k] = r[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) E.p[k] = r[6 + k];
+        }
         scan(E);
     };
     // level 2 over the surviving groups, in list order: a group's segment
-    // records are bulk-copied into shared memory once (two buffers: the copy
-    // of the next group is in flight while this one is scanned), then every
-    // query slot that kept the group scans it warp-cooperatively, one segment
-    // per lane, reading the records from shared memory.
+    // records are bulk-copied into shared memory once (with two buffers the
+    // copy of the next group is in flight while this one is scanned), then
+    // every query slot that kept the group scans it warp-cooperatively, one
+    // segment per lane, reading the records from shared memory.
     if (nsv > 0) {
-        float* buf[2] = { s_grp[wid], s_seg2[wid] };
+        float* buf[2] = { s_grp[wid], kDouble ? s_seg2[wid] : s_grp[wid] };
         // segment range of list entry j (the curve of the first query that kept it)
         auto range = [&](int j, int64_t& ss, int& ns) {
             const int g = s_sv[wid][j];
@@ -444,10 +396,11 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
                 tc::bulk_load(buf[b], rec + (int64_t)RW * ss, (uint32_t)(ns * RW * sizeof(float)), bar + b);
             }
         };
-        issue(0, 0);
+        if (kDouble) issue(0, 0);
         for (int j = 0; j < nsv; ++j) {
-            const int b = j & 1;
-            if (j + 1 < nsv) issue(j + 1, b ^ 1);
+            const int b = kDouble ? (j & 1) : 0;
+            if (!kDouble) issue(j, 0);
+            else if (j + 1 < nsv) issue(j + 1, b ^ 1);
             int64_t ss;
             int ns;
             range(j, ss, ns);
@@ -495,16 +448,16 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
             }
         }
     }
-    emit();
-    flush_pending();
-    if (!SEEDS_ONLY && lane < nslots && ((over_mask >> lane) & 1u)) {
-        const unsigned long long pos = atomicAdd(B.cnt + 3, 1ull);
-        B.over[pos] = qis[lane];
+    flush_cands();
+    if (lane < nslots) {
+        const int64_t pos = qbase + lane;
+        B.ubq[pos] = ubs_l;
+        if (((over_mask >> lane) & 1u) && atomicExch(B.ovf + pos, 1) == 0)
+            B.over[atomicAdd(B.cnt + 3, 1ull)] = B.order[pos];
     }
-    if (!SEEDS_ONLY && P.counters) {
+    if (P.counters) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
             n_grp += __shfl_xor_sync(kFull, n_grp, o);
             n_seg += __shfl_xor_sync(kFull, n_seg, o);
         }
@@ -512,7 +465,6 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) k_cull_pairs(CurveQ P, Pair
             atomicAdd(P.counters + BSPL_CNT_QUERIES, (unsigned long long)nslots);
             atomicAdd(P.counters + BSPL_CNT_GRP_TESTED, n_grp);
             atomicAdd(P.counters + BSPL_CNT_SEG_TESTED, n_seg);
-            atomicAdd(P.counters + BSPL_CNT_CANDIDATES, n_pairs);
         }
     }
     __syncwarp();
@@ -532,7 +484,141 @@ __device__ __forceinline__ void add_counter(unsigned long long* ctr, int which, 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr + which, v);
 }
 
-// (3a) FP32 solve of every pair, per-query FP32 minimum
+// Classification of every culling candidate, one thread per candidate (Sec.
+// 4.3: the signs of the Bernstein coefficients of E, each against its FP32
+// rounding bound), and the emission of the pairs that can hold their
+// query's minimum: SEED pairs to the front of the pair buffer, the others to
+// the back.  A candidate whose box bound exceeds its query's final upper
+// bound is dropped, and so is a pair whose minimum is at an end when its
+// FP32 distance there less its rounding bound exceeds that bound.  A block
+// takes kClsRounds x 256 candidates at a time and reserves its slots in the
+// buffer once; when they do not fit, the queries concerned go to the grid
+// kernel.  SEEDS_ONLY: only SEED pairs, written with the query index (the
+// network's training pairs).
+constexpr int kClsRounds = 4;
+
+template <bool SEEDS_ONLY>
+__global__ void __launch_bounds__(256) k_classify(CurveQ P, PairBuf B)
+{
+    __shared__ int s_ns[kClsRounds][8], s_no[kClsRounds][8];
+    __shared__ unsigned long long s_bs, s_bo;
+    __shared__ int s_ok;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nc = min((int64_t)B.cnt[7], B.ccap);
+    unsigned long long n_cls = 0, n_emit = 0;
+    for (int64_t c0 = (int64_t)blockIdx.x * 256 * kClsRounds; c0 < nc;
+         c0 += (int64_t)gridDim.x * 256 * kClsRounds) {
+        int pos[kClsRounds], seg[kClsRounds];
+        uint8_t kind[kClsRounds];
+        unsigned ms[kClsRounds], mo[kClsRounds];
+#pragma unroll
+        for (int r = 0; r < kClsRounds; ++r) {
+            const int64_t j = c0 + r * 256 + threadIdx.x;
+            bool keep = false;
+            pos[r] = 0;
+            seg[r] = 0;
+            kind[r] = kIso;
+            if (j < nc) {
+                pos[r] = B.cpos[j];
+                seg[r] = B.cseg[j];
+                const float ubk = B.ubq[pos[r]];
+                if (B.clb[j] <= ubk) {
+                    float cl[12];
+                    local32(P, seg[r], B.qrec + 8 * (int64_t)pos[r], cl);
+                    kind[r] = classify(cl);
+                    ++n_cls;
+                    keep = !SEEDS_ONLY || kind[r] == kSeed;
+                    if (!SEEDS_ONLY && (kind[r] == kEnd0 || kind[r] == kEnd1 || kind[r] == kEnds)) {
+                        // the segment's minimum is at an end: its FP32
+                        // distance there less the rounding bound of the FP32
+                        // stage is a lower bound of the pair's distance
+                        float l1 = 0.f, d0 = 0.f, d1 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 12; ++k) l1 += fabsf(cl[k]);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float e = ((cl[9 + k] + cl[6 + k]) + cl[3 + k]) + cl[k];
+                            d0 += cl[k] * cl[k];
+                            d1 += e * e;
+                        }
+                        const float dm = kind[r] == kEnd0 ? d0 : (kind[r] == kEnd1 ? d1 : fminf(d0, d1));
+                        keep = sqrtf(dm) - 1e-6f * l1 <= sqrtf(ubk);
+                    }
+                }
+            }
+            ms[r] = __ballot_sync(kFull, keep && kind[r] == kSeed);
+            mo[r] = __ballot_sync(kFull, keep && kind[r] != kSeed);
+            if (lane == 0) {
+                s_ns[r][wid] = __popc(ms[r]);
+                s_no[r][wid] = __popc(mo[r]);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // exclusive prefix over (round, warp), then one reservation
+            int ns = 0, no = 0;
+            for (int r = 0; r < kClsRounds; ++r)
+                for (int w = 0; w < 8; ++w) {
+                    const int a = s_ns[r][w], b = s_no[r][w];
+                    s_ns[r][w] = ns;
+                    s_no[r][w] = no;
+                    ns += a;
+                    no += b;
+                }
+            int ok = 1;
+            unsigned long long bs = 0, bo = 0;
+            if (ns + no > 0) {
+                const unsigned long long tot = atomicAdd(B.cnt, (unsigned long long)(ns + no));
+                ok = tot + ns + no <= (unsigned long long)B.cap;
+                if (ok) {
+                    bs = ns ? atomicAdd(B.cnt + 1, (unsigned long long)ns) : 0;
+                    bo = no ? atomicAdd(B.cnt + 2, (unsigned long long)no) : 0;
+                }
+            }
+            s_ok = ok;
+            s_bs = bs;
+            s_bo = bo;
+        }
+        __syncthreads();
+        const bool ok = s_ok;
+#pragma unroll
+        for (int r = 0; r < kClsRounds; ++r) {
+            const bool sd = (ms[r] >> lane) & 1u, ot = (mo[r] >> lane) & 1u;
+            if (!(sd || ot)) continue;
+            if (!ok) {
+                if (!SEEDS_ONLY && atomicExch(B.ovf + pos[r], 1) == 0)
+                    B.over[atomicAdd(B.cnt + 3, 1ull)] = B.order[pos[r]];
+                continue;
+            }
+            ++n_emit;
+            if (sd) {
+                const int64_t idx = (int64_t)s_bs + s_ns[r][wid] + __popc(ms[r] & lt);
+                B.pq[idx] = SEEDS_ONLY ? B.order[pos[r]] : pos[r];
+                B.ps[idx] = seg[r];
+                if (B.kind) B.kind[idx] = kSeed;
+            } else {
+                const int64_t idx = B.cap - 1 - ((int64_t)s_bo + s_no[r][wid] + __popc(mo[r] & lt));
+                B.pq[idx] = pos[r];
+                B.ps[idx] = seg[r];
+                B.kind[idx] = kind[r];
+            }
+        }
+        __syncthreads();
+    }
+    if (!SEEDS_ONLY && P.counters) {
+        add_counter(P.counters, BSPL_CNT_CANDIDATES, n_emit);
+        add_counter(P.counters, BSPL_CNT_CLASSIFIED, n_cls);
+    }
+}
+
+// (3a) FP32 solve of every pair, per-query FP32 minimum.  CLIP: the pairs
+// with a minimum inside (one certified sign change, or more) are solved by
+// the paper's search (monotone split by the roots of E', elimination,
+// Bezier clipping; clip.cuh) and then by the FP32 Newton steps; a seeded
+// pair on which the search does not find exactly one interior minimum is
+// left for the FP64 stage to decide.
+template <bool CLIP>
 __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
 {
     const int64_t ns = (int64_t)B.cnt[1], no = (int64_t)B.cnt[2], np = ns + no;
@@ -554,7 +640,17 @@ __global__ void k_pairs_fp32(CurveQ P, PairBuf B, int have_seed)
             // ambiguous: the FP32 stage cannot tell which candidate of the
             // pair is the minimum (the FP64 stage then decides among all)
             bool amb = false, unsure = false;
-            if (kind == kSeed) {
+            if (CLIP && kind != kEnd0 && kind != kEnd1 && kind != kEnds) {
+                if (kind != kSeed) ++n_iso;
+                float b[6], ba[6], second[3];
+                bern_E32(c, b, ba);
+                ClipOut co;
+                u = clip_min<float>(c, 1e-5f * ba[5], 12, second, co);
+                unsure = co.unsure || kind == kIsoU || (kind == kSeed && co.n_min != 1);
+                conv = newton_min<float>(c, 0.f, 0.f, 0.f, u, 1.f / 64.f, P.fp32_steps, 1e-7f, it32);
+                const float dd = sqrtf(eval_E<float>(c, 0.f, 0.f, 0.f, u, E, Ep));
+                amb = unsure || sqrtf(second[0]) - dd <= 2.f * del;
+            } else if (kind == kSeed) {
                 float lo = 0.f, hi = 1.f;
                 u = have_seed ? fminf(fmaxf(B.u[i], 0.f), 1.f) : 0.5f;
                 conv = false;
@@ -772,33 +868,54 @@ __global__ void k_pairs_argseg(CurveQ P, PairBuf B)
     }
 }
 
-// (3d) the winning pair writes its query's result
-__global__ void k_pairs_write(CurveQ P, PairBuf B)
+// (3d) the winning pair of each query: the unique finished pair at its
+// best (D, segment)
+__global__ void k_pairs_win(CurveQ P, PairBuf B)
 {
     const int64_t nf = (int64_t)B.cnt[4];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = B.fin[j];
+        const int64_t pos = B.pq[i];
+        if ((unsigned long long)__double_as_longlong(B.D64[i]) == B.best64[pos] && B.ps[i] == B.bestseg[pos])
+            B.wslot[pos] = (int32_t)i;
+    }
+}
+
+// (3e) every query's result, once, in sorted order: the winning pair's
+// parameter mapped to the original one (Sec. 4.4.2), its distance and
+// flags.  An invalid query gets NaN and INVALID; a valid one without a
+// winner (none is expected: the pair holding the minimum is never dropped)
+// NaN and NONCONV; the queries sent to the grid kernel are left to it.
+__global__ void k_write_results(CurveQ P, PairBuf B)
+{
     unsigned fb = 0, nc = 0;
-    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < nf; j0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = j0 + threadIdx.x;
-        if (j < nf) {
-            const int64_t i = B.fin[j];
-            const int64_t pos = B.pq[i];
-            const int seg = B.ps[i];
-            if ((unsigned long long)__double_as_longlong(B.D64[i]) != B.best64[pos] || seg != B.bestseg[pos]) continue;
-            const int64_t qi = B.order[pos];
-            const double u = B.u64[i];
-            const double t0 = P.prange[2 * seg], t1 = P.prange[2 * seg + 1];
-            const double t = u <= 0.0 ? t0 : (u >= 1.0 ? t1 : t0 + u * (t1 - t0));
-            const double d = sqrt(B.D64[i]);
-            const int c = P.q_curve[qi];
-            unsigned char fl = B.fl[i];
-            if ((seg == P.seg_off[c] && u <= 0.0) || (seg == P.seg_off[c + 1] - 1 && u >= 1.0)) fl |= BSPL_Q_AT_END;
-            if (P.invert && d > 1e-9 * P.diag[c]) fl |= BSPL_Q_OFF_CURVE;
-            P.t[qi] = t;
-            P.dist[qi] = d;
-            P.status[qi] = fl;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < P.n_q; j0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pos = j0 + threadIdx.x;
+        if (pos >= P.n_q || B.ovf[pos]) continue;
+        const int64_t qi = B.order[pos];
+        const int c = __float_as_int(B.qrec[8 * pos + 7]);
+        double t = __longlong_as_double(0x7ff8000000000000LL), d = t;
+        unsigned char fl = BSPL_Q_INVALID;
+        if (c >= 0) {
+            const int32_t i = B.wslot[pos];
+            fl = BSPL_Q_NONCONV;
+            if (i >= 0) {
+                const int seg = B.ps[i];
+                const double u = B.u64[i];
+                const double t0 = P.prange[2 * seg], t1 = P.prange[2 * seg + 1];
+                t = u <= 0.0 ? t0 : (u >= 1.0 ? t1 : t0 + u * (t1 - t0));
+                d = sqrt(B.D64[i]);
+                fl = B.fl[i];
+                if ((seg == P.seg_off[c] && u <= 0.0) || (seg == P.seg_off[c + 1] - 1 && u >= 1.0))
+                    fl |= BSPL_Q_AT_END;
+                if (P.invert && d > 1e-9 * P.diag[c]) fl |= BSPL_Q_OFF_CURVE;
+            }
             fb += (fl & BSPL_Q_FALLBACK) ? 1 : 0;
             nc += (fl & BSPL_Q_NONCONV) ? 1 : 0;
         }
+        P.t[qi] = t;
+        P.dist[qi] = d;
+        P.status[qi] = fl;
     }
     if (P.counters) {
         add_counter(P.counters, BSPL_CNT_FALLBACK, fb);
@@ -839,6 +956,13 @@ bool carve_learned(void* ws, size_t bytes, int64_t n_splines, int64_t n_q, PairB
     B.fin = cv.take<int32_t>((size_t)cap);
     B.iso = cv.take<int32_t>((size_t)cap);
     B.qrec = cv.take<float>((size_t)n_q * 8);
+    B.ccap = cap;
+    B.cpos = cv.take<int32_t>((size_t)cap);
+    B.cseg = cv.take<int32_t>((size_t)cap);
+    B.clb = cv.take<float>((size_t)cap);
+    B.ubq = cv.take<float>((size_t)n_q);
+    B.wslot = cv.take<int32_t>((size_t)n_q);
+    B.ovf = cv.take<int32_t>((size_t)n_q);
     if (sort_ws) *sort_ws = sw;
     if (sort_bytes) *sort_bytes = sb;
     if (total) *total = cv.used + 256;
@@ -902,7 +1026,7 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     if (!segs_ok(segs) || n_q < 0 || pair_cap(n_q) > 0x7fffffffLL) return BSPL_EINVAL;
     if (n_q == 0) return BSPL_OK;
     if (!q_curve || !q_xyz || !t || !dist || !status) return BSPL_EINVAL;
-    const bspl_mlp* mlp = (const bspl_mlp*)o->mlp;
+    const bspl_mlp* mlp = o->prec == BSPL_CLIP_MIXED ? nullptr : (const bspl_mlp*)o->mlp;
     if (mlp && (!mlp->params || !mlp->wbf16 || mlp->kind != BSPL_MLP_CURVE)) return BSPL_EINVAL;
     if (o->occupancy < 0 || o->occupancy > 2) return BSPL_EINVAL;
     if (o->pairs_per_query < 0 || o->pairs_per_query > kPairsPerQuery) return BSPL_EINVAL;
@@ -922,32 +1046,32 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
         return BSPL_ECUDA;
     P.order = order;
     B.order = order;
-    k_qrec<<<ceil_div(n_q, 256), 256, 0, s>>>(q_curve, q_xyz, segs->diag, segs->n, order, n_q, (float*)B.qrec);
+    k_qrec<<<ceil_div(n_q, 256), 256, 0, s>>>(q_curve, q_xyz, segs->diag, segs->n, n_q, B);
     if (cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess) return BSPL_ECUDA;
     mark(1);
     const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
     B.work = B.cnt + 6;  // zeroed with the other counters
     if (o->occupancy >= 2)
-        k_cull_pairs<false, 8><<<persistent_blocks(k_cull_pairs<false, 8>, kWarps * 32, 0, blocks), kWarps * 32, 0,
-                                 s>>>(P, B);
+        k_cull_cands<8><<<persistent_blocks(k_cull_cands<8>, kWarps * 32, 0, blocks), kWarps * 32, 0, s>>>(P, B);
     else if (o->occupancy == 1)
-        k_cull_pairs<false, 6><<<persistent_blocks(k_cull_pairs<false, 6>, kWarps * 32, 0, blocks), kWarps * 32, 0,
-                                 s>>>(P, B);
+        k_cull_cands<6><<<persistent_blocks(k_cull_cands<6>, kWarps * 32, 0, blocks), kWarps * 32, 0, s>>>(P, B);
     else
-        k_cull_pairs<false, 1><<<persistent_blocks(k_cull_pairs<false, 1>, kWarps * 32, 0, blocks), kWarps * 32, 0,
-                                 s>>>(P, B);
+        k_cull_cands<1><<<persistent_blocks(k_cull_cands<1>, kWarps * 32, 0, blocks), kWarps * 32, 0, s>>>(P, B);
+    const int grid = pair_grid();
+    k_classify<false><<<grid, 256, 0, s>>>(P, B);
     mark(2);
     if (mlp && mlp_seed_pairs(mlp, B.pq, B.ps, B.qrec, segs, B.cap, B.cnt + 1, B.u, s) != cudaSuccess)
         return BSPL_ECUDA;
     mark(3);
-    const int grid = pair_grid();
-    k_pairs_fp32<<<grid, 256, 0, s>>>(P, B, mlp ? 1 : 0);
+    if (o->prec == BSPL_CLIP_MIXED) k_pairs_fp32<true><<<grid, 256, 0, s>>>(P, B, 0);
+    else k_pairs_fp32<false><<<grid, 256, 0, s>>>(P, B, mlp ? 1 : 0);
     mark(4);
     k_pairs_fp64<<<grid, 256, 0, s>>>(P, B);
     k_pairs_iso64<<<grid, 128, 0, s>>>(P, B);
     mark(5);
     k_pairs_argseg<<<grid, 256, 0, s>>>(P, B);
-    k_pairs_write<<<grid, 256, 0, s>>>(P, B);
+    k_pairs_win<<<grid, 256, 0, s>>>(P, B);
+    k_write_results<<<grid, 256, 0, s>>>(P, B);
     mark(6);
     // queries whose pairs did not fit: the grid kernel over the device-side list
     CurveQ F = P;
@@ -984,8 +1108,7 @@ extern "C" bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t
             return BSPL_ECUDA;
         P.order = order;
         B.order = order;
-        k_qrec<<<ceil_div(n_q, 256), 256, 0, stream>>>(q_curve, q_xyz, segs->diag, segs->n, order, n_q,
-                                                       (float*)B.qrec);
+        k_qrec<<<ceil_div(n_q, 256), 256, 0, stream>>>(q_curve, q_xyz, segs->diag, segs->n, n_q, B);
         PairBuf C = B;
         C.pq = pair_q;
         C.ps = pair_seg;
@@ -993,8 +1116,8 @@ extern "C" bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t
         C.cap = cap;
         const int64_t blocks = (n_q + kQPW * kWarps - 1) / (kQPW * kWarps);
         C.work = B.cnt + 6;  // zeroed above
-        k_cull_pairs<true, 1><<<persistent_blocks(k_cull_pairs<true, 1>, kWarps * 32, 0, blocks), kWarps * 32, 0,
-                                stream>>>(P, C);
+        k_cull_cands<1><<<persistent_blocks(k_cull_cands<1>, kWarps * 32, 0, blocks), kWarps * 32, 0, stream>>>(P, C);
+        k_classify<true><<<pair_grid(), 256, 0, stream>>>(P, C);
     }
     if (cudaMemcpyAsync(n_pairs, B.cnt + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess ||
         cudaMemcpyAsync(n_pairs + 1, B.cnt, sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)

@@ -186,5 +186,25 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// GELU (tanh form, as gelu above) of two values in packed BF16 arithmetic:
+// the pre-activations are rounded to BF16 once, then x^2, the inner
+// polynomial, tanh and the outer product each take one bf16x2 instruction
+// for both values (the result is the layer's BF16 activation pair, a in the
+// low half).  Each step rounds to BF16, so the result differs from the
+// FP32 form rounded once by a few BF16 units.
+__device__ __forceinline__ uint32_t gelu_bf16x2(float a, float b)
+{
+    const __nv_bfloat162 x = __floats2bfloat162_rn(a, b);
+    const __nv_bfloat162 k0 = __float2bfloat162_rn(0.7978845608028654f);
+    const __nv_bfloat162 k1 = __float2bfloat162_rn(0.7978845608028654f * 0.044715f);
+    const __nv_bfloat162 half = __float2bfloat162_rn(0.5f);
+    const __nv_bfloat162 u = __hmul2(__hfma2(__hmul2(x, x), k1, k0), x);
+    uint32_t th;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(*reinterpret_cast<const uint32_t*>(&u)));
+    const __nv_bfloat162 hx = __hmul2(x, half);
+    const __nv_bfloat162 y = __hfma2(hx, *reinterpret_cast<const __nv_bfloat162*>(&th), hx);
+    return *reinterpret_cast<const uint32_t*>(&y);
+}
+
 }  // namespace tc
 }  // namespace bspl

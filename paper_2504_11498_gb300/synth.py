@@ -218,6 +218,44 @@ def curve_set(seed: int = 2, n_curves: int = 4096, n_proj: int = 1_000_000, n_in
     return cs, CurveQueries(pc, q, ic, t)
 
 
+# The paper's 18 test curves (its per-module tables for the 2D models a-i
+# and the 3D models j-r): (model, dimension, degree, knot-vector length,
+# control points).  The curves themselves are not published: these shapes
+# with random control points stand in for them.
+PAPER_MODELS = (
+    ("a", 2, 4, 10, 5), ("b", 2, 5, 12, 6), ("c", 2, 6, 14, 7), ("d", 2, 4, 14, 9), ("e", 2, 5, 18, 12),
+    ("f", 2, 6, 22, 15), ("g", 2, 4, 35, 30), ("h", 2, 5, 22, 16), ("i", 2, 6, 57, 50),
+    ("j", 3, 4, 10, 5), ("k", 3, 5, 12, 6), ("l", 3, 6, 14, 7), ("m", 3, 4, 14, 9), ("n", 3, 5, 18, 12),
+    ("o", 3, 6, 22, 15), ("p", 3, 4, 35, 30), ("q", 3, 5, 46, 40), ("r", 3, 6, 57, 50),
+)
+
+
+def paper_suite(seed: int = 17, n_proj: int = 10_000, n_inv: int = 10_000):
+    """One curve per paper model (curve index = position in PAPER_MODELS):
+    the model's degree and control-point count, uniform clamped knots,
+    control points ~U[0,1]^2 with z = 0 for the 2D models and ~U[0,1]^3 for
+    the 3D ones; per model n_proj projection queries ~U over its control-
+    point box inflated 20% (z = 0 for 2D) and n_inv inversion parameters
+    ~U[0,1].  Queries are grouped by model."""
+    rng = np.random.default_rng(seed)
+    degs, knots, cps = [], [], []
+    for _, dim, p, klen, ncp in PAPER_MODELS:
+        assert klen == ncp + p + 1
+        P = np.zeros((ncp, 3))
+        P[:, :dim] = rng.uniform(0.0, 1.0, size=(ncp, dim))
+        degs.append(p)
+        knots.append(uniform_clamped_knots(p, ncp))
+        cps.append(P)
+    cs = pack_curves(degs, knots, cps)
+    lo, hi = cp_boxes(cs)
+    n = len(PAPER_MODELS)
+    pc = np.repeat(np.arange(n, dtype=np.int32), n_proj)
+    q = _box_queries(rng, lo, hi, pc)
+    ic = np.repeat(np.arange(n, dtype=np.int32), n_inv)
+    t = rng.uniform(0.0, 1.0, size=n * n_inv)
+    return cs, CurveQueries(pc, q, ic, t)
+
+
 # --------------------------------------------------------------------------
 # surface workloads
 # --------------------------------------------------------------------------

@@ -1,9 +1,11 @@
 // Host build of the pure-math helpers the curve query kernels share
-// (csrc/query_common.cuh), for CPU tests of their decisions: the Bernstein
-// form of E and its sign changes, the certified isolation of the minima of
-// D on a cubic segment, and the two FP64 Newton steps.  Plain C entry
+// (csrc/query_common.cuh, csrc/clip.cuh), for CPU tests of their decisions:
+// the Bernstein form of E and its sign changes, the certified isolation of
+// the minima of D on a cubic segment, the two FP64 Newton steps, and the
+// paper's search (closed-form quartic roots, elimination, clipping).  Plain C entry
 // points over host arrays; no device code runs.
 #include "../paper_2504_11498_gb300/csrc/query_common.cuh"
+#include "../paper_2504_11498_gb300/csrc/clip.cuh"
 
 using namespace bspl;
 
@@ -41,5 +43,19 @@ double hn_finish64(const double* a64, const double* q, double* u, double* last)
     for (int i = 0; i < 9; ++i) a32[i] = (float)a64[3 + i];
     unsigned it = 0;
     return finish64(a64, a32, q, *u, *last, it);
+}
+
+// real roots of c[4] x^4 + ... + c[0] (Ferrari)
+int hn_quartic_d(const double* c, double* x) { return quartic_roots<double>(c, x); }
+int hn_quartic_f(const float* c, float* x) { return quartic_roots<float>(c, x); }
+
+// the paper's search on the FP32 local-frame cubic a[12]
+float hn_clip_f(const float* a, float tolE, int rounds, float* second3, int* n_min, int* unsure)
+{
+    ClipOut o;
+    const float u = clip_min<float>(a, tolE, rounds, second3, o);
+    *n_min = o.n_min;
+    *unsure = o.unsure ? 1 : 0;
+    return u;
 }
 }

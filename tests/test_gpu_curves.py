@@ -112,7 +112,7 @@ def test_single_cubic_all_queries(prec, samples):
     check_against_oracle(cs, qs.inv_curve, C, t, d, 0.0)
 
 
-@pytest.mark.parametrize("prec", [bspl.FP64, bspl.MIXED])
+@pytest.mark.parametrize("prec", [bspl.FP64, bspl.MIXED, bspl.CLIP_MIXED])
 def test_curve_set_subset_parity(prec):
     cs, _ = synth.curve_set(seed=2, n_proj=1, n_inv=1)
     sub = cs.subset(np.arange(1, 4096, 16))  # 256 curves
@@ -146,9 +146,10 @@ def compare_with_oracle(cs, qc, q, t_o, d_o, t_gpu, d_gpu, tol):
 
 def test_full_size_curve_set_oracle_parity():
     """The 4,096-curve set, 1M projection + 1M inversion queries in the launch
-    configuration the benchmark times: the plain, mixed and learned paths
-    (the learned one captured as a CUDA graph by the library and replayed, as
-    the benchmark does) against the oracle on EVERY query."""
+    configuration the benchmark times: the plain, mixed, learned and
+    clipping-search paths (the learned one captured as a CUDA graph by the
+    library and replayed, as the benchmark does) against the oracle on EVERY
+    query."""
     cs, qs = synth.curve_set(seed=2)
     tol = 1e-10
     dc = bspl.DeviceCurves(cs, DEV)
@@ -179,7 +180,7 @@ def test_full_size_curve_set_oracle_parity():
     assert bspl.mlp_check() == bspl.OK
     res[bspl.LEARNED_MIXED] = tuple(x.cpu().numpy().copy() for x in (bp.param, bp.dist, bp.status, bi.param,
                                                                      bi.dist, bi.status))
-    for prec in (bspl.FP64, bspl.MIXED):
+    for prec in (bspl.FP64, bspl.MIXED, bspl.CLIP_MIXED):
         tp, dp, sp = run_queries(segs, qs.proj_curve, qs.proj_xyz, prec=prec)
         r = bspl.bspl_invert_curves(segs, dev(qs.inv_curve, torch.int32), inv_pts, bspl.make_options(prec=prec))
         torch.cuda.synchronize()
@@ -194,7 +195,7 @@ def test_full_size_curve_set_oracle_parity():
     inv = inv_pts.cpu().numpy()
     t_op, d_op = O.project_curves(cs, qs.proj_curve, qs.proj_xyz)
     t_oi, d_oi = O.project_curves(cs, qs.inv_curve, inv)
-    for prec in (bspl.FP64, bspl.MIXED, bspl.LEARNED_MIXED):
+    for prec in (bspl.FP64, bspl.MIXED, bspl.LEARNED_MIXED, bspl.CLIP_MIXED):
         tp, dp, sp, ti, di, si = res[prec]
         compare_with_oracle(cs, qs.proj_curve, qs.proj_xyz, t_op, d_op, tp, dp, tol)
         compare_with_oracle(cs, qs.inv_curve, inv, t_oi, d_oi, ti, di, tol)
@@ -245,7 +246,7 @@ def _edge_set():
     return synth.pack_curves(*zip(*curves))
 
 
-@pytest.mark.parametrize("prec", [bspl.FP64, bspl.MIXED])
+@pytest.mark.parametrize("prec", [bspl.FP64, bspl.MIXED, bspl.CLIP_MIXED])
 def test_edge_curves(prec):
     cs = _edge_set()
     tol = 1e-10
@@ -318,7 +319,8 @@ def test_near_cusp_segment():
     diag = O.curve_diag(cs)[0]
     mlp = bspl.Mlp(synth.mlp_init(7), DEV)
     _, d_o = O.project_curves(cs, qc, near)
-    for prec, kw in ((bspl.FP64, {}), (bspl.LEARNED_MIXED, {"mlp": mlp}), (bspl.LEARNED_MIXED, {})):
+    for prec, kw in ((bspl.FP64, {}), (bspl.LEARNED_MIXED, {"mlp": mlp}), (bspl.LEARNED_MIXED, {}),
+                     (bspl.CLIP_MIXED, {})):
         _, d, _ = run_queries(segs, qc, on, invert=True, prec=prec, **kw)
         assert np.max(d) <= 1e-9 * diag, (prec, np.max(d) / diag, t[np.argmax(d)])
         _, d, _ = run_queries(segs, qc, near, prec=prec, **kw)

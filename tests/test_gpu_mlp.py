@@ -53,7 +53,9 @@ def test_fused_forward_matches_bf16_reference():
     p = M.unpack(theta.astype(np.float32).astype(np.float64))
     ref16 = M.forward(p, X.astype(np.float32), bf16=True)[0]
     ref = M.forward(p, X)[0]
-    assert np.max(np.abs(t - ref16)) < 2e-3, np.max(np.abs(t - ref16))
+    # the reference rounds weights and layer inputs to BF16; the kernel also
+    # evaluates GELU in packed BF16 arithmetic (five roundings per value)
+    assert np.max(np.abs(t - ref16)) < 4e-3, np.max(np.abs(t - ref16))
     assert np.max(np.abs(t - ref)) < 1e-2
     assert bspl.mlp_check() == bspl.OK
 

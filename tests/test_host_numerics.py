@@ -37,6 +37,10 @@ def hn(tmp_path_factory):
     lib.hn_isolate_d.restype = ctypes.c_double
     lib.hn_finish64.argtypes = [D, D, D, D]
     lib.hn_finish64.restype = ctypes.c_double
+    lib.hn_quartic_d.argtypes = [D, D]
+    lib.hn_quartic_f.argtypes = [F, F]
+    lib.hn_clip_f.argtypes = [F, ctypes.c_float, ctypes.c_int, F, I, I]
+    lib.hn_clip_f.restype = ctypes.c_float
     return lib
 
 
@@ -175,3 +179,71 @@ def test_uncertainty_only_where_it_matters(hn, btol, unsure):
     a = cubic((-0.5, 1, 0, 0))    # b = (-0.5, -0.3, -0.1, 0.1, 0.3, 0.5), one change
     _, unc = isolate32(hn, a, np.array(btol, np.float32))
     assert unc == unsure
+
+
+# ------------------------------------------------ the paper's search stage
+
+def quartic(hn, c, f32=False):
+    x = np.zeros(4, np.float32 if f32 else np.float64)
+    if f32:
+        n = hn.hn_quartic_f(fp(c), x.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    else:
+        n = hn.hn_quartic_d(dp(np.array(c, float)), dp(x))
+    return np.sort(x[:n].astype(np.float64))
+
+
+def test_quartic_roots_closed_form_cases(hn):
+    # four real roots, two real and a complex pair, biquadratic, cubic fallback
+    assert np.allclose(quartic(hn, np.poly([0.9, 0.3, -1.2, 2.5])[::-1] * 3.0), [-1.2, 0.3, 0.9, 2.5], atol=1e-10)
+    c = np.polymul(np.poly([0.25, 0.75]), [1.0, 0.4, 2.0])[::-1]  # x^2 + 0.4 x + 2 has no real root
+    assert np.allclose(quartic(hn, c), [0.25, 0.75], atol=1e-12)
+    assert np.allclose(quartic(hn, [4.0, 0.0, -5.0, 0.0, 1.0]), [-2, -1, 1, 2], atol=1e-12)
+    assert np.allclose(quartic(hn, [6.0, -11.0, 6.0, -1.0, 0.0]), [1, 2, 3], atol=1e-9)  # -(x-1)(x-2)(x-3)
+    assert len(quartic(hn, [1.0, 0.0, 1.0, 0.0, 1.0])) == 0  # x^4 + x^2 + 1 > 0
+
+
+def test_quartic_roots_random_against_numpy(hn):
+    rng = np.random.default_rng(41)
+    for _ in range(2000):
+        r = np.sort(rng.uniform(-2, 2, 4))
+        if np.min(np.diff(r)) < 1e-2:
+            continue
+        c = (np.poly(r) * rng.uniform(0.5, 3) * rng.choice([-1, 1]))[::-1]
+        got = quartic(hn, c)
+        assert len(got) == 4 and np.allclose(got, r, atol=1e-8), (r, got)
+        # FP32: every root in (0, 1) found to FP32-level accuracy
+        g32 = quartic(hn, c, f32=True)
+        for x in r[(r > 0) & (r < 1)]:
+            assert np.min(np.abs(g32 - x)) < 2e-3, (r, g32)
+
+
+def dense_min(a, n=50001):
+    u = np.linspace(0, 1, n)
+    D = d2(a, u)
+    k = int(np.argmin(D))
+    return u[k], D[k]
+
+
+def test_clip_search_finds_the_global_minimum(hn):
+    """Random local-frame cubics (q at the origin): the paper's search
+    returns the global minimiser of D on [0, 1] to FP32 accuracy, as dense
+    FP64 sampling finds it, and agrees with the certified isolation."""
+    rng = np.random.default_rng(43)
+    worst = 0.0
+    for _ in range(1500):
+        P = rng.uniform(-1, 1, (4, 3))
+        # power coefficients of the Bezier cubic (component-wise), q = origin
+        a = np.array([P[0], 3 * (P[1] - P[0]), 3 * (P[2] - 2 * P[1] + P[0]), P[3] - 3 * P[2] + 3 * P[1] - P[0]])
+        a = a.reshape(-1)
+        sec = np.zeros(3, np.float32)
+        nmin, uns = ctypes.c_int(), ctypes.c_int()
+        u = hn.hn_clip_f(fp(a), 1e-6, 12, sec.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(nmin),
+                         ctypes.byref(uns))
+        _, Dm = dense_min(a)
+        Du = float(d2(a, np.array([u]))[0])
+        scale = np.sum(np.abs(a)) ** 2
+        worst = max(worst, (Du - Dm) / scale)
+        assert Du - Dm <= 2e-6 * scale, (P, u, Du, Dm)
+        u_iso, _ = isolate32(hn, a)
+        assert abs(Du - float(d2(a, np.array([u_iso]))[0])) <= 2e-6 * scale
+    print(f"worst (D_clip - D_dense) / scale: {worst:.3g}")

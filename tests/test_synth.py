@@ -31,3 +31,25 @@ def test_ragged_batch_recipe():
     shi = np.maximum.reduceat(ss.cps, ss.cp_off[:-1], axis=0)
     diag = np.linalg.norm(shi - slo, axis=1)
     assert np.all((sq.proj_r >= 0) & (sq.proj_r <= 0.2 * diag[sq.proj_surf]))
+
+
+def test_paper_suite_recipe():
+    """One curve per paper model with its degree, knot-vector length and
+    control-point count; 2D models (a-i) at z = 0; uniform clamped knots on
+    [0, 1]; queries grouped by model inside the inflated control box."""
+    cs, cq = synth.paper_suite(seed=17, n_proj=1000, n_inv=500)
+    assert cs.n == 18
+    for c, (name, dim, p, klen, ncp) in enumerate(synth.PAPER_MODELS):
+        deg, U, P = cs.curve(c)
+        assert (deg, len(U), len(P)) == (p, klen, ncp)
+        assert np.all(U[:p + 1] == 0) and np.all(U[-p - 1:] == 1)
+        assert np.allclose(np.diff(U[p:len(U) - p]), 1.0 / (ncp - p))
+        assert np.all((P[:, :dim] >= 0) & (P[:, :dim] <= 1))
+        if dim == 2:
+            assert np.all(P[:, 2] == 0) and np.all(cq.proj_xyz[cq.proj_curve == c, 2] == 0)
+    assert np.array_equal(cq.proj_curve, np.repeat(np.arange(18), 1000))
+    assert np.array_equal(cq.inv_curve, np.repeat(np.arange(18), 500))
+    lo, hi = synth.cp_boxes(cs)
+    c, h = 0.5 * (lo + hi), 0.6 * (hi - lo)
+    k = cq.proj_curve
+    assert np.all(np.abs(cq.proj_xyz - c[k]) <= h[k] + 1e-12)

@@ -56,8 +56,8 @@ def test_noalloc_rejects_batches_over_its_limit():
 
 
 def test_noalloc_learned_precision_within_and_over_its_limit():
-    """The learned precision also keeps its candidate-pair buffer in the
-    fixed array, about 1 KB per query: a batch that fits answers like the
+    """The learned precision also keeps its candidate and pair buffers in
+    the fixed array, about 1.4 KB per query: a batch that fits answers like the
     regular entry point (two calls in a row), a larger one is refused with
     ENOSPACE rather than mistaken for a caller error."""
     from oracle import oracle as O

@@ -32,10 +32,10 @@ METRIC = "projected pts/s, learned+mixed vs plain FP64, same GB300, at 1e-9 rel.
 TOL = 1e-10
 SURF_TOL = 1e-4  # surfaces: decomposed at the paper's alpha, last Newton steps on the original patch
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one k_cull_pairs launch on the 16M-query
+# DRAM bytes (read + write) of one k_cull_cands launch on the 16M-query
 # workload, from the ncu capture summarised in
-# profiles/k_cull_pairs_dram_c4_full.md (none yet: None)
-CULL_TRAFFIC_PER_LAUNCH = None
+# profiles/k_cull_cands_dram_curve_set_4096_16M.md
+CULL_TRAFFIC_PER_LAUNCH = 1_545_249_024 + 1_794_256_896
 
 
 def parse():
@@ -535,25 +535,30 @@ def measure_curves(args, world, dist, dev, stream, flush, segs, dc, qs, mlp, ful
     # the seed network 2 (16*128 + 2*128*128 + 128) = 69,888 flops per row.
     rows = c_learned["classified"]  # every pair the culling classified; the seeded ones run the network
     seeded = int(train_rows(segs, pc, pq, ic, iq, has_inv))
-    cull_flops = 12 * (c_learned["grp_tested"] + c_learned["seg_tested"]) + 110 * rows
-    t_cull = st_ms["cull"] * 1e-3
+    box_flops = 12 * (c_learned["grp_tested"] + c_learned["seg_tested"])
+    cls_flops = 110 * rows
+    cull_flops = box_flops + cls_flops
+    t_cull = max(st_ms["cull"], 1e-6) * 1e-3
+    t_cls = max(st_ms["classify"], 1e-6) * 1e-3
     mlp_flops = 69888 * seeded
     t_seed = max(st_ms["seed"], 1e-6) * 1e-3
     dominant = max(st_ms, key=st_ms.get)
     mlp_line = {"bound": "tensor", "achieved": mlp_flops / t_seed / 1e12, "peak": bf16_peak / 1e12,
                 "unit": "TFLOP/s", "frac": mlp_flops / t_seed / bf16_peak, "rows_per_step": seeded,
                 "ms_per_step": st_ms["seed"], "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
-    cull_box_flops = 12 * (c_learned["grp_tested"] + c_learned["seg_tested"])
-    cull_line = {"bound": "alu", "achieved": cull_flops / t_cull / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
-                 "frac": cull_flops / t_cull / p32, "ms_per_step": st_ms["cull"],
-                 "frac_box_tests_only": cull_box_flops / t_cull / p32,
+    cull_line = {"bound": "alu", "achieved": box_flops / t_cull / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
+                 "frac": box_flops / t_cull / p32, "ms_per_step": st_ms["cull"],
                  "peak_source": "FP32 FMA-chain microbenchmark on this GPU (of measured)"}
+    cls_line = {"bound": "alu", "achieved": cls_flops / t_cls / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
+                "frac": cls_flops / t_cls / p32, "ms_per_step": st_ms["classify"], "pairs_per_step": rows}
     roofline = dict(cull_line if dominant != "seed" else mlp_line)
-    roofline.update({"kernel": "k_cull_pairs" if dominant != "seed" else "k_mlp_fused",
+    roofline.update({"kernel": "k_cull_cands" if dominant != "seed" else "k_mlp_fused",
                      "traffic": (CULL_TRAFFIC_PER_LAUNCH * n_calls
-                                 if dominant == "cull" and CULL_TRAFFIC_PER_LAUNCH is not None else None),
-                     "traffic_unit": f"DRAM bytes per step ({n_calls} launch(es), ncu at full size)",
-                     "stages_ms_per_step": st_ms, "dominant_stage": dominant, "mlp_seed_kernel": mlp_line})
+                                 if dominant == "cull" and CULL_TRAFFIC_PER_LAUNCH is not None
+                                 and args.workload == "c4" and full else None),
+                     "traffic_unit": f"DRAM bytes per step ({n_calls} launch(es), full-size ncu capture)",
+                     "stages_ms_per_step": st_ms, "dominant_stage": dominant, "mlp_seed_kernel": mlp_line,
+                     "classify_kernel": cls_line})
     f32_step = cull_flops + 45 * c_learned["newton32_iters"]
     f64_step = 60 * c_learned["newton"] + 45 * max(0, c_learned["newton64_iters"] - 2 * c_learned["newton"])
     t_step = ms_learned * 1e-3

@@ -53,9 +53,10 @@ typedef enum {
                                certification with the paper's search (Secs.
                                4.2.3-4.4: monotone split by the closed-form
                                roots of E', elimination by Properties 1-2,
-                               three rounds of Bezier clipping) in place of the
-                               network and of the FP32 root isolation, then the
-                               FP32 and FP64 Newton steps; surfaces: EINVAL  */
+                               Bezier clipping to 1e-6 of each piece) in place
+                               of the network and of the FP32 root isolation,
+                               then the FP32 and FP64 Newton steps; surfaces:
+                               EINVAL                                          */
 } bspl_precision;
 
 /* per-query status bits */
@@ -198,14 +199,14 @@ typedef struct {
     const void* stage_events; /* optional host array of BSPL_NSTAGE_EVENTS cudaEvent_t
                             (created by the caller): the learned path records
                             them on the stream at its stage boundaries (start,
-                            sort, cull, seed, FP32, FP64, select, leftovers);
-                            profiling only                                */
+                            sort, cull, classify, seed, FP32, FP64, select,
+                            leftovers); profiling only                    */
     int32_t cert_depth;  /* surfaces: refinement levels of the certification
                             search on the original surface (default 2, at most
                             4); negative: no certification (grid-seeded search
                             only, for timing comparisons)                 */
 } bspl_options;
-#define BSPL_NSTAGE_EVENTS 8
+#define BSPL_NSTAGE_EVENTS 9
 
 /* device counters accumulated by the query calls when opt->counters != NULL */
 #define BSPL_CNT_QUERIES 0
@@ -352,8 +353,10 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
  * it), FP64 Newton on E = (C - q).C', E' = C'.C' + (C - q).C'' (Sec. 4.2.3,
  * Eqs. Et and E't) with C, C', C'' by the Cox-de Boor recursion on the
  * original knots and control points; every step is clamped to the domain and
- * halved until the squared distance does not grow, until E is zero to its
- * FP64 rounding.  At most max_iter steps (0: 16; at most 100).
+ * halved (at most 12 times) until the squared distance does not grow, until
+ * E is zero to its FP64 rounding, the step falls below the resolution of t
+ * or the distance stops decreasing.  At most max_iter steps (0: 16; at most
+ * 100).
  *   in/out  t [n_q], dist [n_q]: the refined parameter and |C(t) - q|, never
  *           larger than the distance at the starting t;
  *   in/out  status [n_q]: queries with BSPL_Q_INVALID are skipped; otherwise

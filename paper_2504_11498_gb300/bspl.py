@@ -72,8 +72,8 @@ class bspl_options(C.Structure):
                 ("counters", C.c_void_p), ("stage_events", C.c_void_p), ("cert_depth", C.c_int32)]
 
 
-NSTAGE_EVENTS = 8
-STAGE_NAMES = ["sort", "cull", "seed", "fp32", "fp64", "select", "leftovers"]
+NSTAGE_EVENTS = 9
+STAGE_NAMES = ["sort", "cull", "classify", "seed", "fp32", "fp64", "select", "leftovers"]
 
 
 class bspl_mlp(C.Structure):

@@ -160,6 +160,29 @@ __host__ __device__ inline R horner5(const R* e, R u)
     return e[0] + u * (e[1] + u * (e[2] + u * (e[3] + u * (e[4] + u * e[5]))));
 }
 
+// sign changes of degree-5 Bernstein coefficients whose magnitude exceeds
+// tol; `uncertain` is set when a coefficient within tol could change the
+// count (at an end, between two certain coefficients of the same sign, or
+// in a run of two or more)
+template <class R>
+__host__ __device__ inline int certain_changes5(const R* b, R tol, bool& uncertain)
+{
+    int v = 0, last = 0, run = 0;
+    for (int i = 0; i < 6; ++i) {
+        const int sg = b[i] > tol ? 1 : (b[i] < -tol ? -1 : 0);
+        if (sg == 0) {
+            if (i == 0 || i == 5) uncertain = true;
+            ++run;
+            continue;
+        }
+        if (run > 0 && (run > 1 || last == sg)) uncertain = true;
+        run = 0;
+        if (last != 0 && sg != last) ++v;
+        last = sg;
+    }
+    return v;
+}
+
 struct ClipOut {
     int n_min;        // interior minima found (pieces where E goes from - to +)
     int rounds;       // clipping rounds run
@@ -167,7 +190,11 @@ struct ClipOut {
 };
 
 // Every local minimum of D on [0, 1] by the paper's search; returns the best
-// minimiser.  second[0..2]: the second and third smallest D among the local
+// minimiser.  Each piece is certified by the sign changes of E's Bernstein
+// coefficients on it (an upper bound of its roots, of the same parity): at
+// most one, none of them within tolE, after halving the piece up to three
+// times; a part that stays uncertified (the closed-form roots of E', in the
+// precision R, may have missed one) sets out.unsure.  second[0..2]: the second and third smallest D among the local
 // minima and the minimiser of the second (as the sign-variation isolation
 // reports them).  tolE: the rounding bound of E's values (a sign within it
 // is not certain); rounds: clipping rounds per piece at most.
@@ -226,65 +253,90 @@ __host__ __device__ inline R clip_min(const R* c, R tolE, int rounds, R* second,
     const R E0 = horner5(e, R(0)), E1 = horner5(e, R(1));
     if (E0 >= -tolE) local_min(Dat(R(0)), R(0));
     if (E1 <= tolE) local_min(Dat(R(1)), R(1));
-    if (fabs(E0) <= tolE || fabs(E1) <= tolE) out.unsure = true;
-    R Elo = E0;
+    // every piece, certified by the sign changes of E's Bernstein
+    // coefficients on it (at most one, none of them within its rounding
+    // bound), halved up to three times where the control polygon is not yet
+    // close enough to E; Property 1 on each certified part
+    struct Part {
+        R b[6];
+        R lo, hi;
+        int depth;
+    };
     for (int k = 0; k + 1 < nc; ++k) {
-        const R t0 = cut[k], t1 = cut[k + 1];
-        const R Ehi = k + 2 == nc ? E1 : horner5(e, t1);
-        if (t1 > t0) {
-            if (fabs(Ehi) <= tolE && k + 2 < nc) out.unsure = true;
-            // Property 1: no minimum unless E goes from - to + on the piece
-            if (Elo < R(0) && Ehi > R(0)) {
-                R b[6];
-                restrict5(b01, t0, t1, b);
-                R lo = t0, hi = t1;
-                const R wmin = R(1e-6) * (t1 - t0);
-                for (int rd = 0; rd < rounds && hi - lo > wmin; ++rd) {
-                    // the convex hull of (i/5, b_i) cut with the axis: the
-                    // extreme crossings of the segments joining a negative
-                    // and a positive control point
-                    R zmin = R(1), zmax = R(0);
-                    for (int i = 0; i < 6; ++i)
-                        for (int j = i + 1; j < 6; ++j)
-                            if ((b[i] < R(0)) != (b[j] < R(0))) {
-                                const R z = (R(i) + R(j - i) * b[i] / (b[i] - b[j])) * R(0.2);
-                                zmin = fmin(zmin, z);
-                                zmax = fmax(zmax, z);
-                            }
-                    if (!(zmax > zmin)) break;
-                    if (zmax - zmin > R(0.5)) {
-                        // bisect: the half whose end values differ in sign
-                        R l[6];
-                        for (int i = 0; i < 6; ++i) l[i] = b[i];
-                        split5(l, R(0.5), true);
-                        const bool left = (l[0] < R(0)) != (l[5] < R(0));
-                        if (left) {
-                            for (int i = 0; i < 6; ++i) b[i] = l[i];
-                            zmin = R(0);
-                            zmax = R(0.5);
-                        } else {
-                            split5(b, R(0.5), false);
-                            zmin = R(0.5);
-                            zmax = R(1);
-                        }
-                    } else {
-                        split5(b, zmin, false);
-                        split5(b, zmin < R(1) ? (zmax - zmin) / (R(1) - zmin) : R(1), true);
-                    }
-                    const R w = hi - lo;
-                    hi = lo + zmax * w;
-                    lo = lo + zmin * w;
-                    ++out.rounds;
-                }
-                // the root of the last clip's chord
-                const R den = b[5] - b[0];
-                R u = den != R(0) ? lo + (hi - lo) * (-b[0] / den) : R(0.5) * (lo + hi);
-                u = fmin(fmax(u, lo), hi);
-                local_min(Dat(u), u);
-                ++out.n_min;
+        if (!(cut[k + 1] > cut[k])) continue;
+        Part st[5];
+        int top = 0;
+        restrict5(b01, cut[k], cut[k + 1], st[0].b);
+        st[0].lo = cut[k];
+        st[0].hi = cut[k + 1];
+        st[0].depth = 0;
+        top = 1;
+        while (top > 0) {
+            Part pt = st[--top];
+            bool unc = false;
+            const int v = certain_changes5(pt.b, tolE, unc);
+            if (!unc && v >= 2 && pt.depth < 3) {
+                const R mid = R(0.5) * (pt.lo + pt.hi);
+                Part l = pt, r = pt;
+                split5(l.b, R(0.5), true);
+                split5(r.b, R(0.5), false);
+                l.hi = mid;
+                r.lo = mid;
+                l.depth = r.depth = pt.depth + 1;
+                st[top++] = r;
+                st[top++] = l;
+                continue;
             }
+            if (unc || v >= 2) out.unsure = true;
+            // Property 1: a minimum inside only where E goes from - to +
+            if (!(pt.b[0] < R(0) && pt.b[5] > R(0))) continue;
+            R b[6];
+            for (int i = 0; i < 6; ++i) b[i] = pt.b[i];
+            R lo = pt.lo, hi = pt.hi;
+            const R wmin = R(1e-6) * (cut[k + 1] - cut[k]);
+            for (int rd = 0; rd < rounds && hi - lo > wmin; ++rd) {
+                // the convex hull of (i/5, b_i) cut with the axis: the
+                // extreme crossings of the segments joining a negative and
+                // a positive control point
+                R zmin = R(1), zmax = R(0);
+                for (int i = 0; i < 6; ++i)
+                    for (int j = i + 1; j < 6; ++j)
+                        if ((b[i] < R(0)) != (b[j] < R(0))) {
+                            const R z = (R(i) + R(j - i) * b[i] / (b[i] - b[j])) * R(0.2);
+                            zmin = fmin(zmin, z);
+                            zmax = fmax(zmax, z);
+                        }
+                if (!(zmax > zmin)) break;
+                if (zmax - zmin > R(0.5)) {
+                    // bisect: the half whose end values differ in sign
+                    R l[6];
+                    for (int i = 0; i < 6; ++i) l[i] = b[i];
+                    split5(l, R(0.5), true);
+                    if ((l[0] < R(0)) != (l[5] < R(0))) {
+                        for (int i = 0; i < 6; ++i) b[i] = l[i];
+                        zmin = R(0);
+                        zmax = R(0.5);
+                    } else {
+                        split5(b, R(0.5), false);
+                        zmin = R(0.5);
+                        zmax = R(1);
+                    }
+                } else {
+                    split5(b, zmin, false);
+                    split5(b, zmin < R(1) ? (zmax - zmin) / (R(1) - zmin) : R(1), true);
+                }
+                const R w = hi - lo;
+                hi = lo + zmax * w;
+                lo = lo + zmin * w;
+                ++out.rounds;
+            }
+            // the root of the last clip's chord
+            const R den = b[5] - b[0];
+            R u = den != R(0) ? lo + (hi - lo) * (-b[0] / den) : R(0.5) * (lo + hi);
+            u = fmin(fmax(u, lo), hi);
+            local_min(Dat(u), u);
+            ++out.n_min;
         }
-        Elo = Ehi;
     }
     if (second) {
         second[0] = m2;

@@ -74,20 +74,29 @@ __global__ void k_eval_curves(bspl_curves C, int64_t n_q, const int32_t* __restr
 // Basis values of degrees p, p - 1 and p - 2 at span q (entry j of the
 // degree-d row is N_{q-d+j,d}(t)): the triangular recursion above, keeping
 // its two rows before the last.
-__device__ void basis3(const double* U, int q, int p, double t, double* N, double* N1, double* N2)
+template <int MP>
+__device__ __forceinline__ void basis3(const double* U, int q, int p, double t, double* N, double* N1, double* N2)
 {
-    double left[kMaxCurveDegree + 1], right[kMaxCurveDegree + 1];
+    double left[MP + 1], right[MP + 1];
     N[0] = 1.0;
-    for (int j = 1; j <= p; ++j) {
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+    for (int j = 1; j <= MP; ++j) {
+        if (j > p) break;
         // N holds degree j - 1 here
         if (j - 1 == p - 2)
-            for (int r = 0; r < j; ++r) N2[r] = N[r];
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+            for (int r = 0; r < MP; ++r)
+                if (r < j) N2[r] = N[r];
         if (j - 1 == p - 1)
-            for (int r = 0; r < j; ++r) N1[r] = N[r];
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+            for (int r = 0; r < MP; ++r)
+                if (r < j) N1[r] = N[r];
         left[j] = t - U[q + 1 - j];
         right[j] = U[q + j] - t;
         double saved = 0.0;
-        for (int r = 0; r < j; ++r) {
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+        for (int r = 0; r < MP; ++r) {
+            if (r >= j) break;
             double den = right[r + 1] + left[j - r];
             double tmp = den != 0.0 ? N[r] / den : 0.0;
             N[r] = saved + right[r + 1] * tmp;
@@ -103,17 +112,23 @@ __device__ void basis3(const double* U, int q, int p, double t, double* N, doubl
 //   C'  = sum_j N_{q-p+1+j,p-1} Q_j,  Q_j = p (P_{q-p+j+1} - P_{q-p+j}) / (U_{q+j+1} - U_{q-p+j+1})
 //   C'' = sum_j N_{q-p+2+j,p-2} R_j,  R_j = (p-1) (Q_{j+1} - Q_j) / (U_{q+j+1} - U_{q-p+j+2})
 // Both denominators span [U_q, U_{q+1}], a non-empty span, so neither is 0.
-__device__ void curve_d2(const double* U, const double* P, int p, int m, double t, double* C, double* C1,
-                         double* C2)
+template <int MP>
+__device__ __forceinline__ void curve_d2(const double* U, const double* P, int p, int m, double t, double* C,
+                                         double* C1, double* C2)
 {
     const int q = span_of(U, p, m, t);
-    double N[kMaxCurveDegree + 1], N1[kMaxCurveDegree + 1], N2[kMaxCurveDegree + 1];
-    basis3(U, q, p, t, N, N1, N2);
+    double N[MP + 1], N1[MP + 1], N2[MP + 1];
+    basis3<MP>(U, q, p, t, N, N1, N2);
     for (int k = 0; k < 3; ++k) C[k] = C1[k] = C2[k] = 0.0;
-    for (int j = 0; j <= p; ++j)
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+    for (int j = 0; j <= MP; ++j) {
+        if (j > p) break;
         for (int k = 0; k < 3; ++k) C[k] += N[j] * P[3 * (q - p + j) + k];
+    }
     double Qp[3] = { 0.0, 0.0, 0.0 };
-    for (int j = 0; j < p; ++j) {
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+    for (int j = 0; j < MP; ++j) {
+        if (j >= p) break;
         const double s = p / (U[q + j + 1] - U[q - p + j + 1]);
         double Qj[3];
         for (int k = 0; k < 3; ++k) {
@@ -132,34 +147,24 @@ __device__ void curve_d2(const double* U, const double* P, int p, int m, double 
 // itself rather than on its cubic approximant): Newton on E = (C - q).C'
 // with E' = C'.C' + (C - q).C'' (Eqs. Et, E't) from the given parameter,
 // each step clamped to the domain and halved until the squared distance does
-// not grow.  Converged: E is zero to its rounding (|E| at most 64 units of
-// FP64 rounding of |C'| (|C - q| + |C| + |q|)), or a domain end where E
-// points outward, or no step decreases the distance, or the accepted step
+// not grow (at most 12 halvings).  Converged: E is zero to its rounding (|E|
+// at most 64 units of FP64 rounding of |C'| (|C - q| + |C| + |q|)), or a
+// domain end where E points outward, or the step is below the resolution of
+// t, or no halving of it decreases the distance, or the accepted step
 // (the longest of the halvings that does not raise D) lowers the squared
 // distance by at most 4 units of its rounding (a flat minimum, where t is
 // ill-conditioned but D is settled), or a step moves t by at most 1e-15 of
 // the domain.  The result never has a larger distance than the start.
-__global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag, int invert, int64_t n_q,
-                                const int32_t* __restrict__ qc, const double* __restrict__ q_xyz, int max_iter,
-                                double* __restrict__ t_io, double* __restrict__ d_io, uint8_t* __restrict__ st_io)
+// the refinement of one query on a curve of degree p <= MP; returns whether
+// it converged, with the final t and squared distance
+template <int MP>
+__device__ __noinline__ bool refine_one(const double* __restrict__ U, const double* __restrict__ P, int p, int m,
+                                        const double* q, int max_iter, double& t, double& D)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_q) return;
-    const int c = qc[i];
-    if (c < 0 || c >= Cv.n || (st_io[i] & BSPL_Q_INVALID)) return;
-    const int p = Cv.degree[c];
-    const int m = (int)(Cv.cp_off[c + 1] - Cv.cp_off[c]) - 1;
-    if (p < 1 || p > kMaxCurveDegree || m < p) return;
-    const double* U = Cv.knots + Cv.knot_off[c];
-    const double* P = Cv.cps + 3 * Cv.cp_off[c];
     const double a = U[p], b = U[m + 1];
-    double t = t_io[i];
-    if (!isfinite(t)) return;
-    t = fmin(fmax(t, a), b);
-    const double q[3] = { q_xyz[3 * i], q_xyz[3 * i + 1], q_xyz[3 * i + 2] };
     double C[3], C1[3], C2[3];
-    curve_d2(U, P, p, m, t, C, C1, C2);
-    double D = 0.0;
+    curve_d2<MP>(U, P, p, m, t, C, C1, C2);
+    D = 0.0;
     for (int k = 0; k < 3; ++k) D += (C[k] - q[k]) * (C[k] - q[k]);
     bool conv = false;
     for (int it = 0; it <= max_iter; ++it) {
@@ -177,11 +182,16 @@ __global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag,
         if (it == max_iter) break;
         const double Ep = g + h;
         double dt = Ep > 0.0 ? -E / Ep : (g > 0.0 ? -E / g : 0.0);
+        // a step below the resolution of t: converged
+        if (!(fabs(dt) > 1e-15 * (b - a) + 4.0 * 1.1102230246251565e-16 * fabs(t))) {
+            conv = true;
+            break;
+        }
         bool took = false;
         double tn = t, Dn = D, Cn[3], C1n[3], C2n[3];
-        for (int hv = 0; hv < 40 && dt != 0.0; ++hv, dt *= 0.5) {
+        for (int hv = 0; hv < 12; ++hv, dt *= 0.5) {
             tn = fmin(fmax(t + dt, a), b);
-            curve_d2(U, P, p, m, tn, Cn, C1n, C2n);
+            curve_d2<MP>(U, P, p, m, tn, Cn, C1n, C2n);
             Dn = 0.0;
             for (int k = 0; k < 3; ++k) Dn += (Cn[k] - q[k]) * (Cn[k] - q[k]);
             if (Dn <= D) {
@@ -206,6 +216,30 @@ __global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag,
             break;
         }
     }
+    return conv;
+}
+
+__global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag, int invert, int64_t n_q,
+                                const int32_t* __restrict__ qc, const double* __restrict__ q_xyz, int max_iter,
+                                double* __restrict__ t_io, double* __restrict__ d_io, uint8_t* __restrict__ st_io)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_q) return;
+    const int c = qc[i];
+    if (c < 0 || c >= Cv.n || (st_io[i] & BSPL_Q_INVALID)) return;
+    const int p = Cv.degree[c];
+    const int m = (int)(Cv.cp_off[c + 1] - Cv.cp_off[c]) - 1;
+    if (p < 1 || p > kMaxCurveDegree || m < p) return;
+    const double* U = Cv.knots + Cv.knot_off[c];
+    const double* P = Cv.cps + 3 * Cv.cp_off[c];
+    const double a = U[p], b = U[m + 1];
+    double t = t_io[i];
+    if (!isfinite(t)) return;
+    t = fmin(fmax(t, a), b);
+    const double q[3] = { q_xyz[3 * i], q_xyz[3 * i + 1], q_xyz[3 * i + 2] };
+    double D;
+    const bool conv = p <= 7 ? refine_one<7>(U, P, p, m, q, max_iter, t, D)
+                             : refine_one<kMaxCurveDegree>(U, P, p, m, q, max_iter, t, D);
     const double d = sqrt(D);
     uint8_t fl = st_io[i] & (uint8_t)~(BSPL_Q_CONVERGED | BSPL_Q_NONCONV | BSPL_Q_AT_END | BSPL_Q_OFF_CURVE);
     fl |= conv ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;

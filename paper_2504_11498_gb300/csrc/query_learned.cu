@@ -1057,29 +1057,30 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
         k_cull_cands<6><<<persistent_blocks(k_cull_cands<6>, kWarps * 32, 0, blocks), kWarps * 32, 0, s>>>(P, B);
     else
         k_cull_cands<1><<<persistent_blocks(k_cull_cands<1>, kWarps * 32, 0, blocks), kWarps * 32, 0, s>>>(P, B);
+    mark(2);
     const int grid = pair_grid();
     k_classify<false><<<grid, 256, 0, s>>>(P, B);
-    mark(2);
+    mark(3);
     if (mlp && mlp_seed_pairs(mlp, B.pq, B.ps, B.qrec, segs, B.cap, B.cnt + 1, B.u, s) != cudaSuccess)
         return BSPL_ECUDA;
-    mark(3);
+    mark(4);
     if (o->prec == BSPL_CLIP_MIXED) k_pairs_fp32<true><<<grid, 256, 0, s>>>(P, B, 0);
     else k_pairs_fp32<false><<<grid, 256, 0, s>>>(P, B, mlp ? 1 : 0);
-    mark(4);
+    mark(5);
     k_pairs_fp64<<<grid, 256, 0, s>>>(P, B);
     k_pairs_iso64<<<grid, 128, 0, s>>>(P, B);
-    mark(5);
+    mark(6);
     k_pairs_argseg<<<grid, 256, 0, s>>>(P, B);
     k_pairs_win<<<grid, 256, 0, s>>>(P, B);
     k_write_results<<<grid, 256, 0, s>>>(P, B);
-    mark(6);
+    mark(7);
     // queries whose pairs did not fit: the grid kernel over the device-side list
     CurveQ F = P;
     F.order = B.over;
     F.n_q_dev = reinterpret_cast<const int64_t*>(B.cnt + 3);
     F.counters = nullptr;
     launch_mixed_curves(F, o->occupancy, s);
-    mark(7);
+    mark(8);
     return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
 }
 

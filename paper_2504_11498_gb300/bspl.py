@@ -415,7 +415,21 @@ class Graph:
     replayed: ``with Graph(stream) as g: <calls on that stream>`` then
     ``g.replay()``.  ``n_kernels`` is the number of kernel launches a replay
     makes.  The calls must use preallocated buffers (a replay reads and writes
-    the same device addresses)."""
+    the same device addresses).
+
+    A graph released while a capture is open on this thread (for instance
+    the one ``g`` held before ``with Graph() as g`` rebinds it, which happens
+    after the new capture began) is destroyed when that capture ends:
+    destroying it inside the capture would invalidate the capture."""
+
+    _open = threading.local()
+
+    @classmethod
+    def _state(cls):
+        st = cls._open
+        if not hasattr(st, "depth"):
+            st.depth, st.pending = 0, []
+        return st
 
     def __init__(self, stream=None):
         self.stream = stream if stream is not None else torch.cuda.Stream()
@@ -427,11 +441,18 @@ class Graph:
         self._ctx = torch.cuda.stream(self.stream)
         self._ctx.__enter__()
         _check(lib().bspl_graph_begin(_stream(self.stream)), "bspl_graph_begin")
+        Graph._state().depth += 1
         return self
 
     def __exit__(self, exc_type, exc, tb):
         n = C.c_int64(0)
         rc = lib().bspl_graph_end(_stream(self.stream), C.byref(self.exec), C.byref(n))
+        st = Graph._state()
+        st.depth -= 1
+        if st.depth == 0:
+            for ex in st.pending:
+                lib().bspl_graph_destroy(ex)
+            st.pending = []
         self._ctx.__exit__(exc_type, exc, tb)
         if exc_type is None:
             _check(rc, "bspl_graph_end")
@@ -445,7 +466,11 @@ class Graph:
     def __del__(self):
         try:
             if self.exec and self.exec.value:
-                lib().bspl_graph_destroy(self.exec)
+                st = Graph._state()
+                if st.depth > 0:
+                    st.pending.append(self.exec)
+                else:
+                    lib().bspl_graph_destroy(self.exec)
         except Exception:
             pass
 

@@ -4,6 +4,13 @@
 
 using namespace bspl;
 
+namespace {
+// Every entry point reports the failures of its own CUDA calls: a launch
+// error left over from an earlier call (kept by the runtime until read) is
+// read and dropped first.
+inline void clear_stale_error() { (void)cudaGetLastError(); }
+}  // namespace
+
 extern "C" {
 
 size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64_t n_seg, int64_t n_q)
@@ -26,6 +33,7 @@ size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64
 bspl_status bspl_decompose(int is_surface, const void* splines, double tol_rel, bspl_segments* out,
                            int64_t* n_seg_total, void* ws, size_t ws_bytes, cudaStream_t stream)
 {
+    clear_stale_error();
     if (is_surface) return decompose_surfaces((const bspl_surfaces*)splines, tol_rel, out, n_seg_total, ws, ws_bytes,
                                               stream);
     return decompose_curves((const bspl_curves*)splines, tol_rel, out, n_seg_total, ws, ws_bytes, stream);
@@ -35,6 +43,7 @@ bspl_status bspl_project_curves(const bspl_segments* segs, int64_t n_q, const in
                                 const bspl_options* opt, double* t, double* dist, uint8_t* status, void* ws,
                                 size_t ws_bytes, cudaStream_t stream)
 {
+    clear_stale_error();
     return query_curves(segs, n_q, q_curve, q_xyz, opt, 0, t, dist, status, ws, ws_bytes, stream);
 }
 
@@ -42,6 +51,7 @@ bspl_status bspl_invert_curves(const bspl_segments* segs, int64_t n_q, const int
                                const bspl_options* opt, double* t, double* dist, uint8_t* status, void* ws,
                                size_t ws_bytes, cudaStream_t stream)
 {
+    clear_stale_error();
     return query_curves(segs, n_q, q_curve, q_xyz, opt, 1, t, dist, status, ws, ws_bytes, stream);
 }
 
@@ -49,6 +59,7 @@ bspl_status bspl_project_surfaces(const bspl_segments* segs, int64_t n_q, const 
                                   const bspl_options* opt, double* uv, double* dist, uint8_t* status, void* ws,
                                   size_t ws_bytes, cudaStream_t stream)
 {
+    clear_stale_error();
     return query_surfaces(segs, n_q, q_surf, q_xyz, opt, 0, uv, dist, status, ws, ws_bytes, stream);
 }
 
@@ -56,18 +67,21 @@ bspl_status bspl_invert_surfaces(const bspl_segments* segs, int64_t n_q, const i
                                  const bspl_options* opt, double* uv, double* dist, uint8_t* status, void* ws,
                                  size_t ws_bytes, cudaStream_t stream)
 {
+    clear_stale_error();
     return query_surfaces(segs, n_q, q_surf, q_xyz, opt, 1, uv, dist, status, ws, ws_bytes, stream);
 }
 
 bspl_status bspl_eval_curves(const bspl_curves* curves, int64_t n_q, const int32_t* q_curve, const double* t,
                              double* xyz, cudaStream_t stream)
 {
+    clear_stale_error();
     return eval_curves(curves, n_q, q_curve, t, xyz, stream);
 }
 
 bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const int32_t* q_surf, const double* uv,
                                double* xyz, cudaStream_t stream)
 {
+    clear_stale_error();
     return eval_surfaces(surfaces, n_q, q_surf, uv, xyz, stream);
 }
 
@@ -75,6 +89,7 @@ bspl_status bspl_refine_curves(const bspl_curves* curves, const double* diag, in
                                const int32_t* q_curve, const double* q_xyz, int32_t max_iter, double* t,
                                double* dist, uint8_t* status, cudaStream_t stream)
 {
+    clear_stale_error();
     return refine_curves(curves, diag, invert, n_q, q_curve, q_xyz, max_iter, t, dist, status, stream);
 }
 

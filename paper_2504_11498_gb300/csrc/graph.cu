@@ -6,6 +6,7 @@ extern "C" {
 
 bspl_status bspl_graph_begin(cudaStream_t stream)
 {
+    (void)cudaGetLastError();  // an error left over from an earlier call is not this capture's
     return cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
 }
 
@@ -56,7 +57,7 @@ bspl_status bspl_graph_launch(bspl_graph g, cudaStream_t stream)
 
 void bspl_graph_destroy(bspl_graph g)
 {
-    if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
+    if (g && cudaGraphExecDestroy((cudaGraphExec_t)g) != cudaSuccess) (void)cudaGetLastError();
 }
 
 }  // extern "C"

@@ -36,10 +36,12 @@ struct CurveQ {
 };
 
 // query_curves.cu: the mixed-precision grid kernel over P.order, and the
-// counting sort of query indices by curve
+// counting sort of query indices by curve (pos_of, when given, receives
+// each query's sorted position)
 void launch_mixed_curves(const CurveQ& P, int occ, cudaStream_t s);
 cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int32_t* rank, void* ws,
-                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s);
+                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s,
+                           int32_t* pos_of = nullptr);
 
 namespace {
 
@@ -71,6 +73,14 @@ __device__ __forceinline__ R warp_min(R v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
     return v;
+}
+
+// warp minimum of a non-negative float (a squared distance, or +inf): the
+// bit patterns of such values order as unsigned integers, so one warp
+// reduction instruction replaces the shuffle tree
+__device__ __forceinline__ float warp_min_nonneg(float v)
+{
+    return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(v)));
 }
 
 template <class R>

@@ -350,3 +350,24 @@ def test_learned_single_query_regression():
     _, d_o = O.project_curves(cs, qc, q)
     _, d, _ = run_queries(segs, qc, q, prec=bspl.LEARNED_MIXED)
     assert abs(d[0] - d_o[0]) <= 1e-9 * O.curve_diag(cs)[3673]
+
+
+def test_graph_captures_in_a_loop():
+    """Captures made one after another (each `with Graph() as g` releases
+    the previous graph while its own capture is open) replay the same
+    results as direct calls, for every curve precision."""
+    cs, qs = synth.curve_set(seed=2, n_curves=64, n_proj=5000, n_inv=1)
+    segs = bspl.decompose(bspl.DeviceCurves(cs, DEV), 1e-10)
+    qc, q = dev(qs.proj_curve, torch.int32), dev(qs.proj_xyz, torch.float64)
+    mlp = bspl.Mlp(synth.mlp_init(7), DEV)
+    g = None
+    for prec in (bspl.LEARNED_MIXED, bspl.MIXED, bspl.FP64, bspl.CLIP_MIXED) * 2:
+        o = bspl.make_options(prec=prec, mlp=mlp if prec == bspl.LEARNED_MIXED else None)
+        bufs = bspl.QueryBuffers(segs, qc.numel(), DEV, learned=prec in (bspl.LEARNED_MIXED, bspl.CLIP_MIXED))
+        ref = bspl.bspl_project_curves(segs, qc, q, o).dist.cpu().numpy().copy()
+        with bspl.Graph() as g:
+            bspl.bspl_project_curves(segs, qc, q, o, bufs)
+        bufs.dist.fill_(-1.0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(bufs.dist.cpu().numpy(), ref), prec

@@ -80,7 +80,11 @@ __device__ __forceinline__ R warp_min(R v)
 // reduction instruction replaces the shuffle tree
 __device__ __forceinline__ float warp_min_nonneg(float v)
 {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 800
     return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(v)));
+#else
+    return warp_min(v);  // targets without the reduction instruction (host test builds)
+#endif
 }
 
 template <class R>

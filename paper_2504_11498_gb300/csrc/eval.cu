@@ -71,13 +71,68 @@ __global__ void k_eval_curves(bspl_curves C, int64_t n_q, const int32_t* __restr
     for (int k = 0; k < 3; ++k) xyz[3 * i + k] = out[k];
 }
 
-// Basis values of degrees p, p - 1 and p - 2 at span q (entry j of the
-// degree-d row is N_{q-d+j,d}(t)): the triangular recursion above, keeping
-// its two rows before the last.
+// What the evaluation on one span q needs that does not depend on t: the
+// reciprocals of the knot differences of the triangular Cox-de Boor
+// recursion (row j, entry r: 1 / (U_{q+r+1} - U_{q+1-j+r}), 0 for an empty
+// one), and the control points of C' and C'' on the span (the derivative of
+// a B-spline as a B-spline of one degree less on the differences of its
+// control points, Sec. 3 Eq. bsplinebasis):
+//   Q_j = p (P_{q-p+j+1} - P_{q-p+j}) / (U_{q+j+1} - U_{q-p+j+1}),   j < p
+//   R_j = (p-1) (Q_{j+1} - Q_j) / (U_{q+j+1} - U_{q-p+j+2}),       j < p - 1
+// Both denominators span [U_q, U_{q+1}], a non-empty span, so neither is 0.
+// Computed once per span for degrees up to 8, so the Newton iterations
+// divide nothing; the rare higher degrees keep no cache (it would take
+// kilobytes of stack per thread) and divide at every evaluation.
 template <int MP>
-__device__ __forceinline__ void basis3(const double* U, int q, int p, double t, double* N, double* N1, double* N2)
+struct SpanCache {
+    static constexpr int K = MP <= 8 ? MP : 1;
+    int q;
+    double inv[K * (K + 1) / 2];
+    double Q[K][3];
+    double R[K][3];
+};
+
+template <int MP>
+__device__ __forceinline__ void span_prepare(const double* U, const double* P, int p, int q, SpanCache<MP>& S)
 {
-    double left[MP + 1], right[MP + 1];
+    static_assert(MP <= 8, "span cache for low degrees only");
+    S.q = q;
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+    for (int j = 1; j <= MP; ++j) {
+        if (j > p) break;
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+        for (int r = 0; r < MP; ++r) {
+            if (r >= j) break;
+            const double den = U[q + r + 1] - U[q + 1 - j + r];
+            S.inv[(j - 1) * j / 2 + r] = den != 0.0 ? 1.0 / den : 0.0;
+        }
+    }
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+    for (int j = 0; j < MP; ++j) {
+        if (j >= p) break;
+        const double sq = p / (U[q + j + 1] - U[q - p + j + 1]);
+        for (int k = 0; k < 3; ++k) S.Q[j][k] = sq * (P[3 * (q - p + j + 1) + k] - P[3 * (q - p + j) + k]);
+        if (j >= 1) {
+            const double sr = (p - 1) / (U[q + j] - U[q - p + j + 1]);
+            for (int k = 0; k < 3; ++k) S.R[j - 1][k] = sr * (S.Q[j][k] - S.Q[j - 1][k]);
+        }
+    }
+}
+
+// C(t), C'(t) and C''(t) of a curve of degree p with control points P[0..m]:
+// the basis values of degrees p, p - 1 and p - 2 at t by the triangular
+// recursion (its two rows before the last kept), times the span's control
+// points P, Q and R.
+template <int MP>
+__device__ __forceinline__ void curve_d2(const double* U, const double* P, int p, int m, double t,
+                                         SpanCache<MP>& S, double* C, double* C1, double* C2)
+{
+    constexpr bool kCache = MP <= 8;
+    const int q = span_of(U, p, m, t);
+    if constexpr (kCache) {
+        if (q != S.q) span_prepare<MP>(U, P, p, q, S);
+    }
+    double N[MP + 1], N1[MP + 1], N2[MP + 1], left[MP + 1], right[MP + 1];
     N[0] = 1.0;
 #pragma unroll(MP <= 8 ? MP + 1 : 1)
     for (int j = 1; j <= MP; ++j) {
@@ -97,49 +152,42 @@ __device__ __forceinline__ void basis3(const double* U, int q, int p, double t, 
 #pragma unroll(MP <= 8 ? MP + 1 : 1)
         for (int r = 0; r < MP; ++r) {
             if (r >= j) break;
-            double den = right[r + 1] + left[j - r];
-            double tmp = den != 0.0 ? N[r] / den : 0.0;
+            double tmp;
+            if constexpr (kCache) {
+                tmp = N[r] * S.inv[(j - 1) * j / 2 + r];
+            } else {
+                const double den = right[r + 1] + left[j - r];
+                tmp = den != 0.0 ? N[r] / den : 0.0;
+            }
             N[r] = saved + right[r + 1] * tmp;
             saved = left[j - r] * tmp;
         }
         N[j] = saved;
     }
-}
-
-// C(t), C'(t) and C''(t) of a curve of degree p with control points P[0..m]
-// (Sec. 3, Eq. bsplinebasis, and the derivative of a B-spline as a B-spline
-// of one degree less on the differences of its control points):
-//   C'  = sum_j N_{q-p+1+j,p-1} Q_j,  Q_j = p (P_{q-p+j+1} - P_{q-p+j}) / (U_{q+j+1} - U_{q-p+j+1})
-//   C'' = sum_j N_{q-p+2+j,p-2} R_j,  R_j = (p-1) (Q_{j+1} - Q_j) / (U_{q+j+1} - U_{q-p+j+2})
-// Both denominators span [U_q, U_{q+1}], a non-empty span, so neither is 0.
-template <int MP>
-__device__ __forceinline__ void curve_d2(const double* U, const double* P, int p, int m, double t, double* C,
-                                         double* C1, double* C2)
-{
-    const int q = span_of(U, p, m, t);
-    double N[MP + 1], N1[MP + 1], N2[MP + 1];
-    basis3<MP>(U, q, p, t, N, N1, N2);
     for (int k = 0; k < 3; ++k) C[k] = C1[k] = C2[k] = 0.0;
+    double Qp[3] = { 0.0, 0.0, 0.0 };
 #pragma unroll(MP <= 8 ? MP + 1 : 1)
     for (int j = 0; j <= MP; ++j) {
         if (j > p) break;
         for (int k = 0; k < 3; ++k) C[k] += N[j] * P[3 * (q - p + j) + k];
-    }
-    double Qp[3] = { 0.0, 0.0, 0.0 };
-#pragma unroll(MP <= 8 ? MP + 1 : 1)
-    for (int j = 0; j < MP; ++j) {
-        if (j >= p) break;
-        const double s = p / (U[q + j + 1] - U[q - p + j + 1]);
-        double Qj[3];
-        for (int k = 0; k < 3; ++k) {
-            Qj[k] = s * (P[3 * (q - p + j + 1) + k] - P[3 * (q - p + j) + k]);
-            C1[k] += N1[j] * Qj[k];
+        if constexpr (kCache) {
+            if (j < p)
+                for (int k = 0; k < 3; ++k) C1[k] += N1[j] * S.Q[j][k];
+            if (j + 1 < p)
+                for (int k = 0; k < 3; ++k) C2[k] += N2[j] * S.R[j][k];
+        } else if (j < p) {
+            const double sq = p / (U[q + j + 1] - U[q - p + j + 1]);
+            double Qj[3];
+            for (int k = 0; k < 3; ++k) {
+                Qj[k] = sq * (P[3 * (q - p + j + 1) + k] - P[3 * (q - p + j) + k]);
+                C1[k] += N1[j] * Qj[k];
+            }
+            if (j >= 1) {
+                const double sr = (p - 1) / (U[q + j] - U[q - p + j + 1]);
+                for (int k = 0; k < 3; ++k) C2[k] += N2[j - 1] * sr * (Qj[k] - Qp[k]);
+            }
+            for (int k = 0; k < 3; ++k) Qp[k] = Qj[k];
         }
-        if (j >= 1) {
-            const double r = (p - 1) / (U[q + j] - U[q - p + j + 1]);
-            for (int k = 0; k < 3; ++k) C2[k] += N2[j - 1] * r * (Qj[k] - Qp[k]);
-        }
-        for (int k = 0; k < 3; ++k) Qp[k] = Qj[k];
     }
 }
 
@@ -162,8 +210,10 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
                                         const double* q, int max_iter, double& t, double& D)
 {
     const double a = U[p], b = U[m + 1];
+    SpanCache<MP> S;
+    S.q = -1;
     double C[3], C1[3], C2[3];
-    curve_d2<MP>(U, P, p, m, t, C, C1, C2);
+    curve_d2<MP>(U, P, p, m, t, S, C, C1, C2);
     D = 0.0;
     for (int k = 0; k < 3; ++k) D += (C[k] - q[k]) * (C[k] - q[k]);
     bool conv = false;
@@ -191,7 +241,7 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
         double tn = t, Dn = D, Cn[3], C1n[3], C2n[3];
         for (int hv = 0; hv < 12; ++hv, dt *= 0.5) {
             tn = fmin(fmax(t + dt, a), b);
-            curve_d2<MP>(U, P, p, m, tn, Cn, C1n, C2n);
+            curve_d2<MP>(U, P, p, m, tn, S, Cn, C1n, C2n);
             Dn = 0.0;
             for (int k = 0; k < 3; ++k) Dn += (Cn[k] - q[k]) * (Cn[k] - q[k]);
             if (Dn <= D) {

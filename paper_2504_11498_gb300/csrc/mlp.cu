@@ -133,6 +133,9 @@ struct SrcX {
     const float* X;
     int64_t n;
     __device__ int64_t count() const { return n; }
+    // row i's inputs are contiguous: nothing to fetch ahead
+    __device__ int2 ahead_index(int64_t) const { return make_int2(0, 0); }
+    __device__ void ahead_fetch(int2) const {}
     __device__ void features(int64_t i, float* f) const
     {
         const float4* p = reinterpret_cast<const float4*>(X + N::IN * i);
@@ -159,6 +162,16 @@ struct SrcPairs {
     int64_t cap;
     const unsigned long long* n_dev;
     __device__ int64_t count() const { return min(cap, (int64_t)*n_dev); }
+    // the records row i gathers, fetched into L2 one tile ahead: the indices
+    // are loaded early, the prefetches issued once they have arrived
+    __device__ int2 ahead_index(int64_t i) const { return make_int2(ps[i], pq[i]); }
+    __device__ void ahead_fetch(int2 ix) const
+    {
+        const float* r = rec32 + (int64_t)BSPL_CREC32 * ix.x;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(r));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(r + 16));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(qrec + 8 * (int64_t)ix.y));
+    }
     __device__ void features(int64_t i, float* f) const
     {
         pair_features(rec32 + (int64_t)BSPL_CREC32 * ps[i], qrec + 8 * (int64_t)pq[i], f);
@@ -270,6 +283,13 @@ struct SrcSurfPairs {
     int64_t cap;
     const unsigned long long* n_dev;
     __device__ int64_t count() const { return min(cap, (int64_t)*n_dev); }
+    __device__ int2 ahead_index(int64_t i) const { return make_int2(pp[i], 0); }
+    __device__ void ahead_fetch(int2 ix) const
+    {
+        const float* r = rec32 + (int64_t)BSPL_SREC32 * ix.x;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(r));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(r + 32));
+    }
     __device__ void features(int64_t i, float* f) const
     {
         const int64_t p = pp[i];
@@ -406,8 +426,12 @@ __global__ void __launch_bounds__(kFusedWG * 128, 1)
         return okf[g] != 0;
     };
 
-    for (int64_t tile = (int64_t)blockIdx.x * kFusedWG + g; tile < ntiles; tile += (int64_t)gridDim.x * kFusedWG) {
+    const int64_t tstride = (int64_t)gridDim.x * kFusedWG;
+    for (int64_t tile = (int64_t)blockIdx.x * kFusedWG + g; tile < ntiles; tile += tstride) {
         const int64_t i = tile * 128 + r;
+        // the next tile's row: its indices now, its records into L2 below
+        const int64_t inext = i + tstride * 128;
+        const int2 ahead = inext < n ? src.ahead_index(inext) : make_int2(-1, -1);
         {
             float f[N::IN];
             if (i < n) src.features(i, f);
@@ -426,6 +450,7 @@ __global__ void __launch_bounds__(kFusedWG * 128, 1)
         tc::fence_async_smem();
         tc::fence_before_sync();
         named_sync(bar_id, 128);
+        if (ahead.x >= 0) src.ahead_fetch(ahead);
         if (!run_layer(0)) break;
         epi_hidden(tl, bias, X, r);
         tc::fence_async_smem();

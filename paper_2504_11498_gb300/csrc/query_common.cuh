@@ -36,12 +36,10 @@ struct CurveQ {
 };
 
 // query_curves.cu: the mixed-precision grid kernel over P.order, and the
-// counting sort of query indices by curve (pos_of, when given, receives
-// each query's sorted position)
+// counting sort of query indices by curve
 void launch_mixed_curves(const CurveQ& P, int occ, cudaStream_t s);
 cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int32_t* rank, void* ws,
-                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s,
-                           int32_t* pos_of = nullptr);
+                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s);
 
 namespace {
 

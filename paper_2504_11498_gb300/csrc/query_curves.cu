@@ -424,13 +424,12 @@ __global__ void k_hist(const int32_t* __restrict__ qc, int64_t n_q, int64_t n, c
 }
 
 __global__ void k_scatter(const int32_t* __restrict__ qc, int64_t n_q, int64_t n, const int32_t* __restrict__ rank,
-                          int64_t* __restrict__ cursor, int32_t* __restrict__ order, int32_t* __restrict__ pos_of)
+                          int64_t* __restrict__ cursor, int32_t* __restrict__ order)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_q) return;
     unsigned long long pos = atomicAdd((unsigned long long*)(cursor + sort_bucket(qc[i], n, rank)), 1ull);
     order[pos] = (int32_t)i;
-    if (pos_of) pos_of[i] = (int32_t)pos;
 }
 
 template <class R, int S, bool MIXED, int MINB>
@@ -475,8 +474,7 @@ size_t query_ws_bytes(int64_t n_splines, int64_t n_q)
 // given): order[] lists queries bucket by bucket; *work receives a zeroed
 // counter for the work-stealing launch that follows
 cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int32_t* rank, void* ws,
-                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s,
-                           int32_t* pos_of)
+                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s)
 {
     Carver cv(ws, ws_bytes);
     int64_t* hist = cv.take<int64_t>((size_t)n + 2);
@@ -492,7 +490,7 @@ cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int3
     k_hist<<<ceil_div(n_q, th), th, 0, s>>>(qc, n_q, n, rank, hist);
     e = exclusive_scan_i64(hist, hist, n + 2, tmp, s);
     if (e != cudaSuccess) return e;
-    k_scatter<<<ceil_div(n_q, th), th, 0, s>>>(qc, n_q, n, rank, hist, ord, pos_of);
+    k_scatter<<<ceil_div(n_q, th), th, 0, s>>>(qc, n_q, n, rank, hist, ord);
     *order = ord;
     if (work) *work = wk;
     return cudaGetLastError();

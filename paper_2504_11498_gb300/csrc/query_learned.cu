@@ -81,7 +81,6 @@ struct PairBuf {
     float* ubq;               // per sorted query: its slacked squared upper bound after culling
     int32_t* wslot;           // per sorted query: buffer slot of the winning pair, or -1
     int32_t* ovf;             // per sorted query: 1 once it is sent to the grid kernel
-    int32_t* pos_of;          // per query: its sorted position
 };
 
 
@@ -883,20 +882,21 @@ __global__ void k_pairs_win(CurveQ P, PairBuf B)
     }
 }
 
-// (3e) every query's result, once, in the caller's order (coalesced
-// writes; the per-position data are gathered through pos_of): the winning
-// pair's parameter mapped to the original one (Sec. 4.4.2), its distance and
+// (3e) every query's result, once, in sorted order: the winning pair's
+// parameter mapped to the original one (Sec. 4.4.2), its distance and
 // flags.  An invalid query gets NaN and INVALID; a valid one without a
 // winner (none is expected: the pair holding the minimum is never dropped)
 // NaN and NONCONV; the queries sent to the grid kernel are left to it.
+// (Writing in the caller's order instead, through the inverse of the sort,
+// turns these scattered writes into scattered reads of the per-query data
+// and measured slower.)
 __global__ void k_write_results(CurveQ P, PairBuf B)
 {
     unsigned fb = 0, nc = 0;
     for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < P.n_q; j0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t qi = j0 + threadIdx.x;
-        if (qi >= P.n_q) continue;
-        const int64_t pos = B.pos_of[qi];
-        if (B.ovf[pos]) continue;
+        const int64_t pos = j0 + threadIdx.x;
+        if (pos >= P.n_q || B.ovf[pos]) continue;
+        const int64_t qi = B.order[pos];
         const int c = __float_as_int(B.qrec[8 * pos + 7]);
         double t = __longlong_as_double(0x7ff8000000000000LL), d = t;
         unsigned char fl = BSPL_Q_INVALID;
@@ -967,7 +967,6 @@ bool carve_learned(void* ws, size_t bytes, int64_t n_splines, int64_t n_q, PairB
     B.ubq = cv.take<float>((size_t)n_q);
     B.wslot = cv.take<int32_t>((size_t)n_q);
     B.ovf = cv.take<int32_t>((size_t)n_q);
-    B.pos_of = cv.take<int32_t>((size_t)n_q);
     if (sort_ws) *sort_ws = sw;
     if (sort_bytes) *sort_bytes = sb;
     if (total) *total = cv.used + 256;
@@ -1047,8 +1046,7 @@ bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const i
     };
     mark(0);
     int32_t* order = nullptr;
-    if (sort_by_spline(q_curve, n_q, segs->n, segs->spline_rank, sw, sb, &order, nullptr, s, B.pos_of) !=
-        cudaSuccess)
+    if (sort_by_spline(q_curve, n_q, segs->n, segs->spline_rank, sw, sb, &order, nullptr, s) != cudaSuccess)
         return BSPL_ECUDA;
     P.order = order;
     B.order = order;

@@ -29,8 +29,7 @@ cudaError_t mlp_seed_surface_pairs(const bspl_mlp* m, const int32_t* pq, const i
                                    const double* q_xyz, const bspl_segments* segs, int64_t cap,
                                    const unsigned long long* n_dev, float* uv0, cudaStream_t s);
 cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int32_t* rank, void* ws,
-                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s,
-                           int32_t* pos_of = nullptr);
+                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s);
 
 namespace {
 

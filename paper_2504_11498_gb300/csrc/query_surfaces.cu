@@ -994,7 +994,7 @@ __device__ __noinline__ void certify_slots(const SurfQ& P, WarpSmem<R>& W, int n
 }
 
 template <class R, int GU, int GV, bool MIXED>
-__global__ void __launch_bounds__(kWarps * 32) k_query_surfaces(SurfQ P)
+__global__ void __launch_bounds__(kWarps * 32, 4) k_query_surfaces(SurfQ P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem<R>* smem = reinterpret_cast<WarpSmem<R>*>(smem_raw);

@@ -35,7 +35,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one k_cull_cands launch on the 16M-query
 # workload, from the ncu capture summarised in
 # profiles/k_cull_cands_dram_curve_set_4096_16M.md
-CULL_TRAFFIC_PER_LAUNCH = 1_545_249_024 + 1_794_256_896
+CULL_TRAFFIC_PER_LAUNCH = 1_545_019_136 + 1_797_668_352
 
 
 def parse():

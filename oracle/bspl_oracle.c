@@ -154,21 +154,46 @@ int orc_basis(int p, const double* U, int64_t nU, double t, int* span, double* N
     return ORC_OK;
 }
 
-/* C(t), C'(t), C''(t) of a curve (P is [m+1][3]) */
-static void curve_eval(int p, const double* U, int m, const double* P, double t,
+/* C(t), C'(t), C''(t) of a curve (P is [m+1][3]).  w: NULL for a
+ * non-rational curve, else the positive weights [m+1] of a rational one
+ * (NURBS): C = A/W with A = sum N_i w_i P_i and W = sum N_i w_i, whose
+ * derivatives follow from the quotient rule,
+ *   C' = (A' - W' C)/W,   C'' = (A'' - 2 W' C' - W'' C)/W. */
+static void curve_eval(int p, const double* U, int m, const double* P, const double* w, double t,
                        double* C, double* C1, double* C2)
 {
     double N0[ONP + 1], N1[ONP + 1], N2[ONP + 1];
     int q = find_span(U, m, p, t);
     cdb_basis_ders(U, q, p, t, N0, N1, N2);
     for (int c = 0; c < 3; ++c) { C[c] = 0.0; C1[c] = 0.0; C2[c] = 0.0; }
+    if (!w) {
+        for (int j = 0; j <= p; ++j) {
+            const double* Pi = P + 3 * (q - p + j);
+            for (int c = 0; c < 3; ++c) {
+                C[c] += N0[j] * Pi[c];
+                C1[c] += N1[j] * Pi[c];
+                C2[c] += N2[j] * Pi[c];
+            }
+        }
+        return;
+    }
+    double A0[3] = { 0, 0, 0 }, A1[3] = { 0, 0, 0 }, A2[3] = { 0, 0, 0 }, W0 = 0.0, W1 = 0.0, W2 = 0.0;
     for (int j = 0; j <= p; ++j) {
         const double* Pi = P + 3 * (q - p + j);
+        double wi = w[q - p + j];
+        W0 += N0[j] * wi;
+        W1 += N1[j] * wi;
+        W2 += N2[j] * wi;
         for (int c = 0; c < 3; ++c) {
-            C[c] += N0[j] * Pi[c];
-            C1[c] += N1[j] * Pi[c];
-            C2[c] += N2[j] * Pi[c];
+            A0[c] += N0[j] * wi * Pi[c];
+            A1[c] += N1[j] * wi * Pi[c];
+            A2[c] += N2[j] * wi * Pi[c];
         }
+    }
+    for (int c = 0; c < 3; ++c) {
+        C[c] = A0[c] / W0;
+        C1[c] = (A1[c] - W1 * C[c]) / W0;
+        C2[c] = (A2[c] - 2.0 * W1 * C1[c] - W2 * C[c]) / W0;
     }
 }
 
@@ -198,8 +223,9 @@ static void surface_eval(int pu, int pv, const double* U, int mu, const double* 
 /* batch evaluation                                                     */
 /* ------------------------------------------------------------------ */
 
+/* w: NULL (non-rational) or the weights [coff[n]] of every control point */
 int orc_eval_curves(int64_t n, const int32_t* deg, const int64_t* koff, const double* knots,
-                    const int64_t* coff, const double* cps, int64_t nq, const int32_t* qc,
+                    const int64_t* coff, const double* cps, const double* w, int64_t nq, const int32_t* qc,
                     const double* t, double* out /* [nq][3][3] */)
 {
     for (int64_t k = 0; k < nq; ++k) {
@@ -207,8 +233,8 @@ int orc_eval_curves(int64_t n, const int32_t* deg, const int64_t* koff, const do
         if (c < 0 || c >= n) return ORC_EINVAL;
         int p = deg[c];
         int m = (int)(coff[c + 1] - coff[c]) - 1;
-        curve_eval(p, knots + koff[c], m, cps + 3 * coff[c], t[k], out + 9 * k, out + 9 * k + 3,
-                   out + 9 * k + 6);
+        curve_eval(p, knots + koff[c], m, cps + 3 * coff[c], w ? w + coff[c] : NULL, t[k], out + 9 * k,
+                   out + 9 * k + 3, out + 9 * k + 6);
     }
     return ORC_OK;
 }
@@ -368,19 +394,22 @@ int orc_span_bezier(int p, const double* U, int64_t nU, const double* P, int64_t
 /* elevation, G1 reduction, bound, halving (Sec. 4.2.2)                 */
 /* ------------------------------------------------------------------ */
 
-/* degree n -> n+1:  Q'_i = (i/(n+1)) Q_{i-1} + ((n+1-i)/(n+1)) Q_i ; stride s between points */
-static void elevate(int n, const double* Q, double* E, int s)
+/* degree n -> n+1:  Q'_i = (i/(n+1)) Q_{i-1} + ((n+1-i)/(n+1)) Q_i ; stride s between points
+ * of nc coordinates each (3: points, 4: homogeneous points of a rational piece) */
+static void elevate_nc(int n, const double* Q, double* E, int s, int nc)
 {
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < nc; ++c) {
         E[c] = Q[c];
         E[(n + 1) * s + c] = Q[n * s + c];
     }
     for (int i = 1; i <= n; ++i) {
         double a = (double)i / (double)(n + 1);
         double b = (double)(n + 1 - i) / (double)(n + 1);
-        for (int c = 0; c < 3; ++c) E[i * s + c] = a * Q[(i - 1) * s + c] + b * Q[i * s + c];
+        for (int c = 0; c < nc; ++c) E[i * s + c] = a * Q[(i - 1) * s + c] + b * Q[i * s + c];
     }
 }
+
+static void elevate(int n, const double* Q, double* E, int s) { elevate_nc(n, Q, E, s, 3); }
 
 /* G1-continuous, L2-optimal reduction of a degree-p Bezier (p > 3) to a cubic.
  * R0 = Q0, R1 = Q0 + (p/3) d0 delta0, R2 = Qp - (p/3) d1 delta1, R3 = Qp
@@ -493,19 +522,22 @@ static double bound2_curve(int p, const double* Q, int s, const double* R, int r
     return b;
 }
 
-/* de Casteljau split at z = 1/2 (the matrix S(1/2) of Eq. subLandR) */
-static void halve(int p, const double* Q, int s, double* L, double* Rr)
+/* de Casteljau split at z = 1/2 (the matrix S(1/2) of Eq. subLandR); points
+ * of nc coordinates (3, or 4 for homogeneous points) at stride s */
+static void halve_nc(int p, const double* Q, int s, int nc, double* L, double* Rr)
 {
-    double w[ONP + 1][3];
+    double w[ONP + 1][4];
     for (int i = 0; i <= p; ++i)
-        for (int c = 0; c < 3; ++c) w[i][c] = Q[i * s + c];
-    for (int c = 0; c < 3; ++c) { L[c] = w[0][c]; Rr[p * s + c] = w[p][c]; }
+        for (int c = 0; c < nc; ++c) w[i][c] = Q[i * s + c];
+    for (int c = 0; c < nc; ++c) { L[c] = w[0][c]; Rr[p * s + c] = w[p][c]; }
     for (int r = 1; r <= p; ++r) {
         for (int i = 0; i <= p - r; ++i)
-            for (int c = 0; c < 3; ++c) w[i][c] = (w[i][c] + w[i + 1][c]) * 0.5;
-        for (int c = 0; c < 3; ++c) { L[r * s + c] = w[0][c]; Rr[(p - r) * s + c] = w[p - r][c]; }
+            for (int c = 0; c < nc; ++c) w[i][c] = (w[i][c] + w[i + 1][c]) * 0.5;
+        for (int c = 0; c < nc; ++c) { L[r * s + c] = w[0][c]; Rr[(p - r) * s + c] = w[p - r][c]; }
     }
 }
+
+static void halve(int p, const double* Q, int s, double* L, double* Rr) { halve_nc(p, Q, s, 3, L, Rr); }
 
 /* exported single-step helpers for the pins */
 int orc_reduce_g1(int p, const double* Q, double* R, double* deltas, int variant)
@@ -608,18 +640,177 @@ static int check_knots(int p, const double* U, int64_t nU, int64_t nP)
     return U[p] < U[nP];
 }
 
+/* ------------------------------------------------------------------ */
+/* rational curves (NURBS): homogeneous decomposition                    */
+/* ------------------------------------------------------------------ */
+/* A rational curve is C = A/W with A = sum N_i w_i P_i, W = sum N_i w_i,
+ * both non-rational B-splines of the homogeneous control points (w_i P_i,
+ * w_i).  The span-wise matrix route is linear in the control points, so it
+ * gives the span's rational Bezier piece as homogeneous points H_j = (W_j Q_j,
+ * W_j), and the midpoint halving of Eq. subLandR applies to H unchanged.  The
+ * paper's pieces are polynomial (its method covers non-rational splines
+ * only); a rational piece is replaced by the C1 Hermite cubic R of its end
+ * points and end derivatives, bounded and subdivided as below, so that the
+ * query tables hold cubic Beziers whatever the input. */
+
+/* homogeneous Bezier points H [p+1][4] of span q (the matrix route applied
+ * to (w_i P_i) and to (w_i), which are products of one rounding each) */
+static void rspan_bezier(int p, const double* U, int q, const double* Pl, const double* wl, double* H)
+{
+    double hp[(ONP + 1) * 3], hw[(ONP + 1) * 3], Qp[(ONP + 1) * 3], Qw[(ONP + 1) * 3];
+    for (int j = 0; j <= p; ++j) {
+        for (int c = 0; c < 3; ++c) hp[3 * j + c] = wl[j] * Pl[3 * j + c];
+        hw[3 * j] = wl[j];
+        hw[3 * j + 1] = 0.0;
+        hw[3 * j + 2] = 0.0;
+    }
+    span_bezier(p, U, q, hp, Qp);
+    span_bezier(p, U, q, hw, Qw);
+    for (int j = 0; j <= p; ++j) {
+        for (int c = 0; c < 3; ++c) H[4 * j + c] = Qp[3 * j + c];
+        H[4 * j + 3] = Qw[3 * j];
+    }
+}
+
+/* the C1 Hermite cubic R [4][3] of the rational piece H: R_0 = C(0), R_3 =
+ * C(1), R_1 = C(0) + C'(0)/3, R_2 = C(1) - C'(1)/3, with the end derivatives
+ * of a rational Bezier (quotient rule at u = 0 and 1)
+ *   C'(0) = p (H_1 - W_1 C(0)) / W_0,   C'(1) = p (W_{p-1} C(1) - H_{p-1}) / W_p
+ * (the numerator parts of H_1 and H_{p-1} written H_1, H_{p-1}). */
+static void rhermite(int p, const double* H, double* R)
+{
+    const double a = (double)p / 3.0;
+    const double* h0 = H;
+    const double* h1 = H + 4;
+    const double* hm = H + 4 * (p - 1);
+    const double* hp = H + 4 * p;
+    for (int c = 0; c < 3; ++c) {
+        double c0 = h0[c] / h0[3], c1 = hp[c] / hp[3];
+        R[c] = c0;
+        R[3 + c] = c0 + a * ((h1[c] - h1[3] * c0) / h0[3]);
+        R[6 + c] = c1 + a * ((hm[c] - hm[3] * c1) / hp[3]);
+        R[9 + c] = c1;
+    }
+}
+
+/* certified bound of max_u |C(u) - R(u)|^2 on [0, 1]:
+ *   C - R = (A - W R) / W,
+ * A - W R is a polynomial of degree p + 3 whose Bernstein coefficients are
+ * those of A elevated three times minus those of the product W R,
+ *   (W R)_k = sum_j [C(p, j) C(3, k - j) / C(p + 3, k)] W_j R_{k-j};
+ * Bernstein weights are a convex partition of unity, so the largest
+ * coefficient norm bounds |A - W R|, and W >= min_j W_j > 0. */
+static double rbound2(int p, const double* H, const double* R)
+{
+    double e[(ONP + 4) * 4], x[(ONP + 4) * 4];
+    for (int i = 0; i < 4 * (p + 1); ++i) e[i] = H[i];
+    for (int n = p; n < p + 3; ++n) {
+        elevate_nc(n, e, x, 4, 4);
+        memcpy(e, x, sizeof(double) * 4 * (size_t)(n + 2));
+    }
+    double wmin = H[3];
+    for (int j = 1; j <= p; ++j)
+        if (H[4 * j + 3] < wmin) wmin = H[4 * j + 3];
+    double b = 0.0;
+    for (int k = 0; k <= p + 3; ++k) {
+        double s[3] = { 0.0, 0.0, 0.0 };
+        int jlo = k - 3 > 0 ? k - 3 : 0, jhi = k < p ? k : p;
+        for (int j = jlo; j <= jhi; ++j) {
+            double cf = (binom(p, j) * binom(3, k - j)) / binom(p + 3, k);
+            for (int c = 0; c < 3; ++c) s[c] = s[c] + (cf * H[4 * j + 3]) * R[3 * (k - j) + c];
+        }
+        double dx = e[4 * k] - s[0], dy = e[4 * k + 1] - s[1], dz = e[4 * k + 2] - s[2];
+        double d2 = (dx * dx + dy * dy) + dz * dz;
+        if (d2 > b) b = d2;
+    }
+    return b / (wmin * wmin);
+}
+
+/* the rational counterpart of curve_node: the Hermite cubic of the node is
+ * accepted when its bound meets the tolerance, else the homogeneous piece is
+ * split at its parameter midpoint (same caps) */
+static void rcurve_node(curve_ctx* X, const double* H, int L, int64_t k)
+{
+    double R[12];
+    int p = X->p;
+    rhermite(p, H, R);
+    int accept = rbound2(p, H, R) <= X->thr2;
+    if (!accept && (L >= ODEPTH || X->count - X->span_first >= OLEAFCAP)) { accept = 1; X->notconv = 1; }
+    if (accept) {
+        if (X->count < X->cap && X->ctrl) {
+            memcpy(X->ctrl + 12 * X->count, R, sizeof(R));
+            X->prange[2 * X->count] = dyadic_t(X->tq, X->tq1, k, L);
+            X->prange[2 * X->count + 1] = dyadic_t(X->tq, X->tq1, k + 1, L);
+        }
+        X->count++;
+        if (L > X->maxdepth) X->maxdepth = L;
+        return;
+    }
+    double Lh[(ONP + 1) * 4], Rh[(ONP + 1) * 4];
+    halve_nc(p, H, 4, 4, Lh, Rh);
+    rcurve_node(X, Lh, L + 1, 2 * k);
+    rcurve_node(X, Rh, L + 1, 2 * k + 1);
+}
+
+/* weights of a curve: 1 = rational (not all equal), 0 = all equal (the
+ * curve is then the non-rational one: A/W = sum N_i P_i, the basis being a
+ * partition of unity), -1 = a weight that is not finite and positive */
+static int weights_kind(const double* w, int64_t nP)
+{
+    int rat = 0;
+    for (int64_t i = 0; i < nP; ++i) {
+        if (!(isfinite(w[i]) && w[i] > 0.0)) return -1;
+        if (w[i] != w[0]) rat = 1;
+    }
+    return rat;
+}
+
+/* exported for the pins */
+int orc_rspan_bezier(int p, const double* U, int64_t nU, const double* P, const double* w, int64_t nP,
+                     double* H, int64_t cap, int64_t* nspans)
+{
+    if (p < 1 || p > OMAXP || nU != nP + p + 1) return ORC_EINVAL;
+    int64_t ns = 0;
+    for (int q = p; q <= (int)nP - 1; ++q) {
+        if (!(U[q] < U[q + 1])) continue;
+        if (ns < cap) rspan_bezier(p, U, q, P + 3 * (q - p), w + (q - p), H + (size_t)ns * 4 * (p + 1));
+        ++ns;
+    }
+    *nspans = ns;
+    return ns <= cap ? ORC_OK : ORC_ENOSPACE;
+}
+int orc_rhermite(int p, const double* H, double* R)
+{
+    if (p < 1 || p > OMAXP) return ORC_EINVAL;
+    rhermite(p, H, R);
+    return ORC_OK;
+}
+double orc_rbound2(int p, const double* H, const double* R) { return rbound2(p, H, R); }
+int orc_rhalve(int p, const double* H, double* L, double* R)
+{
+    if (p < 1 || p > OMAXP) return ORC_EINVAL;
+    halve_nc(p, H, 4, 4, L, R);
+    return ORC_OK;
+}
+
 /* decomposes curve c with its segments written from index `first` (when the
- * arrays are given and fit); returns the count, or -1 for invalid data */
+ * arrays are given and fit); returns the count, or -1 for invalid data.
+ * w: NULL, or the weights of every control point of the set (a curve whose
+ * weights are all equal takes the non-rational route) */
 static int64_t decompose_one_curve(int64_t c, const int32_t* deg, const int64_t* koff, const double* knots,
-                                   const int64_t* coff, const double* cps, double tol_rel, int64_t first,
-                                   int64_t cap, double* ctrl, double* prange, int* maxdepth, int* notconv)
+                                   const int64_t* coff, const double* cps, const double* w, double tol_rel,
+                                   int64_t first, int64_t cap, double* ctrl, double* prange, int* maxdepth,
+                                   int* notconv)
 {
     int p = deg[c];
     int64_t nP = coff[c + 1] - coff[c], nU = koff[c + 1] - koff[c];
     const double* U = knots + koff[c];
     const double* P = cps + 3 * coff[c];
+    const double* wc = w ? w + coff[c] : NULL;
     if (!check_knots(p, U, nU, nP)) return -1;
     for (int64_t i = 0; i < 3 * nP; ++i) if (!isfinite(P[i])) return -1;
+    int rat = wc ? weights_kind(wc, nP) : 0;
+    if (rat < 0) return -1;
     double thr = tol_rel * box_diag(P, nP);
     curve_ctx X;
     X.p = p; X.thr2 = thr * thr; X.cap = cap; X.maxdepth = 0; X.notconv = 0;
@@ -627,11 +818,17 @@ static int64_t decompose_one_curve(int64_t c, const int32_t* deg, const int64_t*
     X.count = first;
     for (int q = p; q <= (int)nP - 1; ++q) {
         if (!(U[q] < U[q + 1])) continue;
-        double Q[(ONP + 1) * 3];
-        span_bezier(p, U, q, P + 3 * (q - p), Q);
         X.tq = U[q]; X.tq1 = U[q + 1];
         X.span_first = X.count;
-        curve_node(&X, Q, 0, 0);
+        if (rat) {
+            double H[(ONP + 1) * 4];
+            rspan_bezier(p, U, q, P + 3 * (q - p), wc + (q - p), H);
+            rcurve_node(&X, H, 0, 0);
+        } else {
+            double Q[(ONP + 1) * 3];
+            span_bezier(p, U, q, P + 3 * (q - p), Q);
+            curve_node(&X, Q, 0, 0);
+        }
     }
     *maxdepth = X.maxdepth;
     *notconv = X.notconv;
@@ -643,7 +840,7 @@ static int64_t decompose_one_curve(int64_t c, const int32_t* deg, const int64_t*
  * Curves are independent: counted in parallel, offsets by a prefix sum, then
  * filled in parallel. */
 int orc_decompose_curves(int64_t n, const int32_t* deg, const int64_t* koff, const double* knots,
-                         const int64_t* coff, const double* cps, double tol_rel, int64_t* seg_off,
+                         const int64_t* coff, const double* cps, const double* w, double tol_rel, int64_t* seg_off,
                          int64_t cap, double* ctrl, double* prange, int64_t* total, int* maxdepth)
 {
     int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -651,7 +848,7 @@ int orc_decompose_curves(int64_t n, const int32_t* deg, const int64_t* koff, con
 #pragma omp parallel for schedule(dynamic, 4) reduction(max : md) reduction(| : nc, bad)
     for (int64_t c = 0; c < n; ++c) {
         int m1 = 0, n1 = 0;
-        cnt[c] = decompose_one_curve(c, deg, koff, knots, coff, cps, tol_rel, 0, 0, NULL, NULL, &m1, &n1);
+        cnt[c] = decompose_one_curve(c, deg, koff, knots, coff, cps, w, tol_rel, 0, 0, NULL, NULL, &m1, &n1);
         if (cnt[c] < 0) bad = 1;
         if (m1 > md) md = m1;
         nc |= n1;
@@ -664,7 +861,8 @@ int orc_decompose_curves(int64_t n, const int32_t* deg, const int64_t* koff, con
 #pragma omp parallel for schedule(dynamic, 4)
         for (int64_t c = 0; c < n; ++c) {
             int m1, n1;
-            decompose_one_curve(c, deg, koff, knots, coff, cps, tol_rel, seg_off[c], cap, ctrl, prange, &m1, &n1);
+            decompose_one_curve(c, deg, koff, knots, coff, cps, w, tol_rel, seg_off[c], cap, ctrl, prange, &m1,
+                                &n1);
         }
     }
     free(cnt);
@@ -969,6 +1167,7 @@ typedef struct {
     int p, m;
     const double* U;
     const double* P;
+    const double* w; /* NULL: non-rational */
     const double* q;
 } curve_prob;
 
@@ -976,7 +1175,7 @@ typedef struct {
 static void dist_ders(const curve_prob* B, double t, double* D, double* E, double* Ep)
 {
     double C[3], C1[3], C2[3];
-    curve_eval(B->p, B->U, B->m, B->P, t, C, C1, C2);
+    curve_eval(B->p, B->U, B->m, B->P, B->w, t, C, C1, C2);
     double d[3] = { C[0] - B->q[0], C[1] - B->q[1], C[2] - B->q[2] };
     *D = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (E) *E = 2.0 * (d[0] * C1[0] + d[1] * C1[1] + d[2] * C1[2]);
@@ -1032,6 +1231,63 @@ static void curve_deriv_bounds(int p, const double* U, const double* P, int q, d
     *A = a;
 }
 
+/* the same bounds on span q of a rational curve C = A/W.  With the span's
+ * points taken relative to P_r = P_{q-p} (which changes neither derivative),
+ * C - P_r = A/W with A = sum N_i w_i (P_i - P_r), and the quotient rule gives
+ *   |C'|  <= (|A'| + |W'| r) / w_min,
+ *   |C''| <= (|A''| + 2 |W'| |C'| + |W''| r) / w_min,
+ * r = max_i |P_i - P_r| (C is a convex combination of the span's points),
+ * w_min = min_i w_i (W is one of the weights), and |A'|, |A''|, |W'|, |W''|
+ * bounded by the norms of their B-spline control points (the rule above
+ * applied to the homogeneous points (w_i (P_i - P_r), w_i)). */
+static void rcurve_deriv_bounds(int p, const double* U, const double* P, const double* w, int q, double* V,
+                                double* A)
+{
+    double H[ONP + 1][4], D1[ONP + 1][4];
+    const double* Pr = P + 3 * (q - p);
+    double r = 0.0, wmin = INFINITY;
+    for (int i = q - p; i <= q; ++i) {
+        int j = i - (q - p);
+        double d[3] = { P[3 * i] - Pr[0], P[3 * i + 1] - Pr[1], P[3 * i + 2] - Pr[2] };
+        double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (nd > r) r = nd;
+        if (w[i] < wmin) wmin = w[i];
+        for (int c = 0; c < 3; ++c) H[j][c] = w[i] * d[c];
+        H[j][3] = w[i];
+    }
+    double a1 = 0.0, w1 = 0.0, a2 = 0.0, w2 = 0.0;
+    for (int i = q - p + 1; i <= q; ++i) {
+        int j = i - (q - p);
+        double den = U[i + p] - U[i];
+        for (int c = 0; c < 4; ++c) D1[j][c] = den != 0.0 ? p * (H[j][c] - H[j - 1][c]) / den : 0.0;
+        double na = sqrt(D1[j][0] * D1[j][0] + D1[j][1] * D1[j][1] + D1[j][2] * D1[j][2]);
+        if (na > a1) a1 = na;
+        if (fabs(D1[j][3]) > w1) w1 = fabs(D1[j][3]);
+    }
+    for (int i = q - p + 2; i <= q; ++i) {
+        int j = i - (q - p);
+        double den = U[i + p - 1] - U[i];
+        if (den == 0.0) continue;
+        double x[4];
+        for (int c = 0; c < 4; ++c) x[c] = (p - 1) * (D1[j][c] - D1[j - 1][c]) / den;
+        double na = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (na > a2) a2 = na;
+        if (fabs(x[3]) > w2) w2 = fabs(x[3]);
+    }
+    *V = (a1 + w1 * r) / wmin;
+    *A = (a2 + 2.0 * w1 * *V + w2 * r) / wmin;
+}
+
+/* exported for the pins: V, A on span q (w NULL: non-rational) */
+int orc_curve_deriv_bounds(int p, const double* U, int64_t nU, const double* P, const double* w, int q, double* V,
+                           double* A)
+{
+    if (p < 1 || p > OMAXP || q < p || q >= nU - p - 1 || !(U[q] < U[q + 1])) return ORC_EINVAL;
+    if (w) rcurve_deriv_bounds(p, U, P, w, q, V, A);
+    else curve_deriv_bounds(p, U, P, q, V, A);
+    return ORC_OK;
+}
+
 typedef struct { double a, b, Da, Db; int depth; } ival_t;
 
 /* lower bound of D = |C-q|^2 on [a,b] inside one span (C polynomial there):
@@ -1056,10 +1312,10 @@ static double ival_lower_bound(const ival_t* iv, double V, double A)
  *     bisected (its midpoint evaluated, and polished by Newton when it is a
  *     local minimum) until the bound clears the best or the interval is
  *     2^-44 of its sample step.  No basin can therefore hide between samples. */
-static void project_curve_one(int p, const double* U, int m, const double* P, const double* q,
+static void project_curve_one(int p, const double* U, int m, const double* P, const double* w, const double* q,
                               double* t_out, double* d_out)
 {
-    curve_prob B = { p, m, U, P, q };
+    curve_prob B = { p, m, U, P, w, q };
     int ns = 0;
     for (int k = p; k <= m; ++k) if (U[k] < U[k + 1]) ++ns;
     int nsamp = ns * OSAMP + 1;
@@ -1072,7 +1328,8 @@ static void project_curve_one(int p, const double* U, int m, const double* P, co
     for (int k = p; k <= m; ++k) {
         if (!(U[k] < U[k + 1])) continue;
         double V, A;
-        curve_deriv_bounds(p, U, P, k, &V, &A);
+        if (w) rcurve_deriv_bounds(p, U, P, w, k, &V, &A);
+        else curve_deriv_bounds(p, U, P, k, &V, &A);
         for (int s = 0; s < OSAMP; ++s) {
             Vs[j] = V;
             As[j] = A;
@@ -1130,8 +1387,9 @@ static void project_curve_one(int p, const double* U, int m, const double* P, co
     free(ts); free(Ds); free(Vs); free(As);
 }
 
+/* w: NULL (non-rational) or the weights of every control point of the set */
 int orc_project_curves(int64_t n, const int32_t* deg, const int64_t* koff, const double* knots,
-                       const int64_t* coff, const double* cps, int64_t nq, const int32_t* qc,
+                       const int64_t* coff, const double* cps, const double* w, int64_t nq, const int32_t* qc,
                        const double* qxyz, double* t_out, double* d_out, int nthreads)
 {
     for (int64_t k = 0; k < nq; ++k)
@@ -1145,8 +1403,8 @@ int orc_project_curves(int64_t n, const int32_t* deg, const int64_t* koff, const
     for (int64_t k = 0; k < nq; ++k) {
         int64_t c = qc[k];
         int m = (int)(coff[c + 1] - coff[c]) - 1;
-        project_curve_one(deg[c], knots + koff[c], m, cps + 3 * coff[c], qxyz + 3 * k, &t_out[k],
-                          &d_out[k]);
+        project_curve_one(deg[c], knots + koff[c], m, cps + 3 * coff[c], w ? w + coff[c] : NULL, qxyz + 3 * k,
+                          &t_out[k], &d_out[k]);
     }
     return ORC_OK;
 }

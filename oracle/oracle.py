@@ -40,7 +40,7 @@ def lib():
             L.orc_gram.restype = D
             L.orc_gram.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
             L.orc_basis.argtypes = [C.c_int, _f64p, I64, D, C.POINTER(C.c_int), _f64p]
-            L.orc_eval_curves.argtypes = [I64, _i32p, _i64p, _f64p, _i64p, _f64p, I64, _i32p, _f64p, _f64p]
+            L.orc_eval_curves.argtypes = [I64, _i32p, _i64p, _f64p, _i64p, _f64p, vp, I64, _i32p, _f64p, _f64p]
             L.orc_eval_surfaces.argtypes = [I64, _i32p, _i32p, _i32p, _i32p, _i64p, _f64p, _i64p, _f64p,
                                             _i64p, _f64p, I64, _i32p, _f64p, _f64p]
             L.orc_boehm_bezier.argtypes = [C.c_int, _f64p, I64, _f64p, I64, _f64p, I64, C.POINTER(I64)]
@@ -51,13 +51,20 @@ def lib():
             L.orc_bound2.argtypes = [C.c_int, _f64p, _f64p]
             L.orc_halve.argtypes = [C.c_int, _f64p, _f64p, _f64p]
             L.orc_elevate.argtypes = [C.c_int, _f64p, _f64p]
-            L.orc_decompose_curves.argtypes = [I64, _i32p, _i64p, _f64p, _i64p, _f64p, D, _i64p, I64, vp, vp,
+            L.orc_decompose_curves.argtypes = [I64, _i32p, _i64p, _f64p, _i64p, _f64p, vp, D, _i64p, I64, vp, vp,
                                                C.POINTER(I64), C.POINTER(C.c_int)]
             L.orc_decompose_surfaces.argtypes = [I64, _i32p, _i32p, _i32p, _i32p, _i64p, _f64p, _i64p, _f64p,
                                                  _i64p, _f64p, D, _i64p, I64, vp, vp, C.POINTER(I64),
                                                  C.POINTER(C.c_int)]
-            L.orc_project_curves.argtypes = [I64, _i32p, _i64p, _f64p, _i64p, _f64p, I64, _i32p, _f64p, _f64p,
-                                             _f64p, C.c_int]
+            L.orc_project_curves.argtypes = [I64, _i32p, _i64p, _f64p, _i64p, _f64p, vp, I64, _i32p, _f64p,
+                                             _f64p, _f64p, C.c_int]
+            L.orc_rspan_bezier.argtypes = [C.c_int, _f64p, I64, _f64p, _f64p, I64, _f64p, I64, C.POINTER(I64)]
+            L.orc_rhermite.argtypes = [C.c_int, _f64p, _f64p]
+            L.orc_rbound2.restype = D
+            L.orc_rbound2.argtypes = [C.c_int, _f64p, _f64p]
+            L.orc_rhalve.argtypes = [C.c_int, _f64p, _f64p, _f64p]
+            L.orc_curve_deriv_bounds.argtypes = [C.c_int, _f64p, I64, _f64p, vp, C.c_int, C.POINTER(D),
+                                                 C.POINTER(D)]
             L.orc_project_surfaces.argtypes = [I64, _i32p, _i32p, _i32p, _i32p, _i64p, _f64p, _i64p, _f64p,
                                                _i64p, _f64p, I64, _i32p, _f64p, _f64p, _f64p, C.c_int]
             L.orc_num_threads.restype = C.c_int
@@ -72,6 +79,18 @@ def _a(x, dt):
 def _curve_args(cs):
     return (int(len(cs.degree)), _a(cs.degree, np.int32), _a(cs.knot_off, np.int64), _a(cs.knots, np.float64),
             _a(cs.cp_off, np.int64), _a(cs.cps, np.float64).reshape(-1))
+
+
+def _weights(cs):
+    """(array kept alive by the caller, pointer or None): the weights of a
+    rational curve set (attribute ``weights``, one per control point), or
+    None for a non-rational one."""
+    w = getattr(cs, "weights", None)
+    if w is None:
+        return None, None
+    w = _a(w, np.float64)
+    assert w.shape == (len(cs.cps),), w.shape
+    return w, w.ctypes.data
 
 
 def _surf_args(ss):
@@ -102,7 +121,8 @@ def eval_curves(cs, qc, t):
     qc = _a(qc, np.int32)
     t = _a(t, np.float64)
     out = np.zeros((len(qc), 3, 3))
-    rc = lib().orc_eval_curves(*_curve_args(cs), len(qc), qc, t, out.reshape(-1))
+    w, wp = _weights(cs)
+    rc = lib().orc_eval_curves(*_curve_args(cs), wp, len(qc), qc, t, out.reshape(-1))
     assert rc == OK, rc
     return out[:, 0], out[:, 1], out[:, 2]
 
@@ -186,6 +206,57 @@ def elevate(Q):
     return E.reshape(n + 2, 3)
 
 
+def rspan_bezier(p, U, P, w):
+    """Homogeneous Bezier points (W_j Q_j, W_j) of every non-empty span of a
+    rational curve by the matrix route: [ns][p+1][4]."""
+    U = _a(U, np.float64)
+    P = _a(P, np.float64).reshape(-1)
+    w = _a(w, np.float64)
+    cap = len(U)
+    H = np.zeros(cap * (p + 1) * 4)
+    ns = C.c_int64()
+    rc = lib().orc_rspan_bezier(p, U, len(U), P, w, len(w), H, cap, C.byref(ns))
+    assert rc == OK, rc
+    return H[: ns.value * (p + 1) * 4].reshape(ns.value, p + 1, 4)
+
+
+def rhermite(H):
+    """C1 Hermite cubic [4][3] of the rational piece H [p+1][4]."""
+    H = _a(H, np.float64)
+    R = np.zeros(12)
+    rc = lib().orc_rhermite(H.shape[0] - 1, H.reshape(-1), R)
+    assert rc == OK
+    return R.reshape(4, 3)
+
+
+def rbound2(H, R):
+    """Certified bound of max_u |C(u) - R(u)|^2 for the rational piece H and the cubic R."""
+    H = _a(H, np.float64)
+    return float(lib().orc_rbound2(H.shape[0] - 1, H.reshape(-1), _a(R, np.float64).reshape(-1)))
+
+
+def rhalve(H):
+    H = _a(H, np.float64)
+    p = H.shape[0] - 1
+    L = np.zeros((p + 1) * 4)
+    R = np.zeros((p + 1) * 4)
+    rc = lib().orc_rhalve(p, H.reshape(-1), L, R)
+    assert rc == OK
+    return L.reshape(p + 1, 4), R.reshape(p + 1, 4)
+
+
+def curve_deriv_bounds(p, U, P, w, q):
+    """(V, A): the oracle's bounds of |C'| and |C''| on span q (w None: non-rational)."""
+    U = _a(U, np.float64)
+    P = _a(P, np.float64).reshape(-1)
+    wa = None if w is None else _a(w, np.float64)
+    V, A = C.c_double(), C.c_double()
+    rc = lib().orc_curve_deriv_bounds(p, U, len(U), P, None if wa is None else wa.ctypes.data, int(q), C.byref(V),
+                                      C.byref(A))
+    assert rc == OK, rc
+    return V.value, A.value
+
+
 class Decomposition:
     """seg_off [n+1], ctrl [nseg][4][3] (surfaces [nseg][4][4][3]), prange [nseg][2] ([nseg][4])."""
 
@@ -203,7 +274,8 @@ def decompose_curves(cs, tol_rel, count_only=False):
     seg_off = np.zeros(n + 1, dtype=np.int64)
     tot = C.c_int64()
     md = C.c_int()
-    rc = lib().orc_decompose_curves(*args, float(tol_rel), seg_off, 0, None, None, C.byref(tot), C.byref(md))
+    w, wp = _weights(cs)
+    rc = lib().orc_decompose_curves(*args, wp, float(tol_rel), seg_off, 0, None, None, C.byref(tot), C.byref(md))
     if rc == EINVAL:
         raise ValueError("invalid curve set")
     if count_only:
@@ -211,7 +283,7 @@ def decompose_curves(cs, tol_rel, count_only=False):
     cap = max(tot.value, 1)
     ctrl = np.zeros(cap * 12)
     prange = np.zeros(cap * 2)
-    rc = lib().orc_decompose_curves(*args, float(tol_rel), seg_off, cap, ctrl.ctypes.data, prange.ctypes.data,
+    rc = lib().orc_decompose_curves(*args, wp, float(tol_rel), seg_off, cap, ctrl.ctypes.data, prange.ctypes.data,
                                     C.byref(tot), C.byref(md))
     assert rc in (OK, ENOTCONV), rc
     n_s = tot.value
@@ -249,7 +321,8 @@ def project_curves(cs, qc, q, nthreads=0):
     q = _a(q, np.float64).reshape(-1, 3)
     t = np.zeros(len(qc))
     d = np.zeros(len(qc))
-    rc = lib().orc_project_curves(*_curve_args(cs), len(qc), qc, q.reshape(-1), t, d, int(nthreads))
+    w, wp = _weights(cs)
+    rc = lib().orc_project_curves(*_curve_args(cs), wp, len(qc), qc, q.reshape(-1), t, d, int(nthreads))
     assert rc == OK, rc
     return t, d
 

@@ -21,6 +21,11 @@ Workloads (the shapes of the paper's experiments are curves of degree 4-6 with
                      with a sum-of-sinusoids height plus noise.
 * ``ragged_mix``     65,536 cubic curves + 8,192 bicubic surfaces with
                      log-normal segment counts and Zipf(1.1) query skew.
+* ``nurbs_curve_set`` the ``curve_set`` recipe with a positive weight per
+                     control point, log-uniform in [1/2, 2] (rational curves).
+* ``nurbs_circles``  full circles as rational quadratics (nine control
+                     points on a square, corner weights sqrt(2)/2), random
+                     centre, radius and plane.
 """
 from __future__ import annotations
 
@@ -31,11 +36,13 @@ import numpy as np
 
 @dataclass
 class CurveSet:
-    """CSR-packed non-rational B-spline curves.
+    """CSR-packed B-spline curves.
 
     degree[n] int32; knot_off[n+1] int64 into knots (float64);
     cp_off[n+1] int64 into cps (float64, [ncp][3]).  Curve c has
     cp_off[c+1]-cp_off[c] control points and that many + degree + 1 knots.
+    weights: None (non-rational), or [ncp total] float64, one positive
+    weight per control point (rational curves, NURBS).
     """
 
     degree: np.ndarray
@@ -43,6 +50,7 @@ class CurveSet:
     knots: np.ndarray
     cp_off: np.ndarray
     cps: np.ndarray
+    weights: np.ndarray | None = None
 
     @property
     def n(self) -> int:
@@ -54,10 +62,14 @@ class CurveSet:
         P = self.cps[self.cp_off[c]:self.cp_off[c + 1]]
         return p, U, P
 
+    def curve_weights(self, c: int):
+        return None if self.weights is None else self.weights[self.cp_off[c]:self.cp_off[c + 1]]
+
     def subset(self, idx) -> "CurveSet":
         idx = np.asarray(idx, dtype=np.int64)
         curves = [self.curve(int(c)) for c in idx]
-        return pack_curves([c[0] for c in curves], [c[1] for c in curves], [c[2] for c in curves])
+        w = None if self.weights is None else [self.curve_weights(int(c)) for c in idx]
+        return pack_curves([c[0] for c in curves], [c[1] for c in curves], [c[2] for c in curves], w)
 
 
 @dataclass
@@ -95,7 +107,7 @@ class SurfaceSet:
         return pack_surfaces(*zip(*parts))
 
 
-def pack_curves(degrees, knot_list, cp_list) -> CurveSet:
+def pack_curves(degrees, knot_list, cp_list, weight_list=None) -> CurveSet:
     degrees = np.asarray(degrees, dtype=np.int32)
     klen = np.array([len(k) for k in knot_list], dtype=np.int64)
     clen = np.array([len(c) for c in cp_list], dtype=np.int64)
@@ -106,7 +118,12 @@ def pack_curves(degrees, knot_list, cp_list) -> CurveSet:
     knots = np.concatenate([np.asarray(k, dtype=np.float64) for k in knot_list]) if len(knot_list) else np.zeros(0)
     cps = (np.concatenate([np.asarray(c, dtype=np.float64).reshape(-1, 3) for c in cp_list])
            if len(cp_list) else np.zeros((0, 3)))
-    return CurveSet(degrees, knot_off, np.ascontiguousarray(knots), cp_off, np.ascontiguousarray(cps))
+    w = None
+    if weight_list is not None:
+        w = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).reshape(-1) for x in weight_list])
+                                 if len(weight_list) else np.zeros(0))
+        assert w.shape == (len(cps),)
+    return CurveSet(degrees, knot_off, np.ascontiguousarray(knots), cp_off, np.ascontiguousarray(cps), w)
 
 
 def pack_surfaces(deg_u, deg_v, knots_u, knots_v, nets) -> SurfaceSet:
@@ -216,6 +233,61 @@ def curve_set(seed: int = 2, n_curves: int = 4096, n_proj: int = 1_000_000, n_in
     ic = rng.integers(0, n_curves, size=n_inv).astype(np.int32)
     t = rng.uniform(0.0, 1.0, size=n_inv)
     return cs, CurveQueries(pc, q, ic, t)
+
+
+def nurbs_curve_set(seed: int = 4, n_curves: int = 4096, n_proj: int = 1_000_000, n_inv: int = 1_000_000,
+                    deg_range=(2, 7), ncp_range=(8, 64), w_range=(0.5, 2.0)):
+    """The ``curve_set`` recipe (degree ~U{2..7}, 8..64 control points
+    ~U[0,1]^3, clamped non-uniform knots) with a weight per control point,
+    log-uniform in w_range: rational curves (NURBS)."""
+    rng = np.random.default_rng(seed)
+    degs = rng.integers(deg_range[0], deg_range[1] + 1, size=n_curves)
+    ncps = rng.integers(ncp_range[0], ncp_range[1] + 1, size=n_curves)
+    knots, cps, ws = [], [], []
+    lw0, lw1 = np.log(w_range[0]), np.log(w_range[1])
+    for p, ncp in zip(degs, ncps):
+        p, ncp = int(p), int(ncp)
+        knots.append(random_clamped_knots(rng, p, ncp))
+        cps.append(rng.uniform(0.0, 1.0, size=(ncp, 3)))
+        ws.append(np.exp(rng.uniform(lw0, lw1, size=ncp)))
+    cs = pack_curves(degs, knots, cps, ws)
+    lo, hi = cp_boxes(cs)
+    pc = rng.integers(0, n_curves, size=n_proj).astype(np.int32)
+    q = _box_queries(rng, lo, hi, pc)
+    ic = rng.integers(0, n_curves, size=n_inv).astype(np.int32)
+    t = rng.uniform(0.0, 1.0, size=n_inv)
+    return cs, CurveQueries(pc, q, ic, t)
+
+
+def nurbs_circles(seed: int = 6, n_curves: int = 16, n_proj: int = 10_000):
+    """Full circles as rational quadratic B-splines: nine control points on
+    the square circumscribing the circle (corners carry weight sqrt(2)/2,
+    the rest 1), knots 0,0,0,1/4,1/4,1/2,1/2,3/4,3/4,1,1,1.  Random centre
+    ~U[0,1]^3, radius ~U[0.05,0.5] and plane (orthonormal e1, e2).
+    Returns (cs, queries, centre [n][3], radius [n], normal [n][3]) so that
+    a test can compare against the closed-form distance to a circle;
+    queries ~U over the circle's box inflated 50% in every direction."""
+    rng = np.random.default_rng(seed)
+    s = np.sqrt(0.5)
+    unit = np.array([[1, 0], [1, 1], [0, 1], [-1, 1], [-1, 0], [-1, -1], [0, -1], [1, -1], [1, 0]], np.float64)
+    wts = np.array([1, s, 1, s, 1, s, 1, s, 1], np.float64)
+    U = np.array([0, 0, 0, 0.25, 0.25, 0.5, 0.5, 0.75, 0.75, 1, 1, 1], np.float64)
+    centre = rng.uniform(0.0, 1.0, size=(n_curves, 3))
+    radius = rng.uniform(0.05, 0.5, size=n_curves)
+    normal = np.zeros((n_curves, 3))
+    cps = []
+    for c in range(n_curves):
+        a = rng.normal(size=3)
+        e1 = a / np.linalg.norm(a)
+        b = rng.normal(size=3)
+        b -= (b @ e1) * e1
+        e2 = b / np.linalg.norm(b)
+        normal[c] = np.cross(e1, e2)
+        cps.append(centre[c] + radius[c] * (unit[:, :1] * e1 + unit[:, 1:] * e2))
+    cs = pack_curves([2] * n_curves, [U] * n_curves, cps, [wts] * n_curves)
+    pc = rng.integers(0, n_curves, size=n_proj).astype(np.int32)
+    q = centre[pc] + 1.5 * radius[pc, None] * rng.uniform(-1.0, 1.0, size=(n_proj, 3))
+    return cs, CurveQueries(pc, q, np.zeros(0, np.int32), np.zeros(0)), centre, radius, normal
 
 
 # The paper's 18 test curves (its per-module tables for the 2D models a-i

@@ -1,7 +1,8 @@
 /*
  * bspl.h -- C ABI of the GB300 (sm_103a) library for batched point projection
- * and inversion on non-rational B-spline curves and surfaces, after their
- * decomposition into cubic Bezier segments / bicubic Bezier patches.
+ * and inversion on B-spline curves (non-rational and rational) and
+ * non-rational B-spline surfaces, after their decomposition into cubic
+ * Bezier segments / bicubic Bezier patches.
  *
  * Method: Wu & Zou, "Matrix representation and GPU-optimized parallel
  * B-spline computing" (arXiv 2504.11498).
@@ -72,7 +73,18 @@ typedef enum {
 /* Curves in CSR form (Sec. 3): curve c has degree p = degree[c] (1..31),
  * control points cps[cp_off[c] .. cp_off[c+1]) (xyz, FP64, [ncp][3]) and
  * knots knots[knot_off[c] .. knot_off[c+1]) with ncp + p + 1 entries,
- * non-decreasing and finite.  The parameter domain is [t_p, t_{ncp}]. */
+ * non-decreasing and finite.  The parameter domain is [t_p, t_{ncp}].
+ *
+ * weights: NULL for non-rational curves (the paper's setting), else one
+ * finite positive weight per control point (weights[cp_off[c] + i] belongs
+ * to cps[cp_off[c] + i]) and the curves are rational (NURBS):
+ *   C(t) = sum_i N_{i,p}(t) w_i P_i / sum_i N_{i,p}(t) w_i.
+ * The paper names rational splines as outside its method; here the
+ * decomposition, the evaluation and the refinement take them (see
+ * bspl_decompose and bspl_refine_curves), and the query calls search the
+ * cubic Beziers the decomposition returns exactly as for any other curve.
+ * A curve whose weights are all equal is the non-rational curve and is
+ * treated as one. */
 typedef struct {
     int64_t n;
     const int32_t* degree;
@@ -80,6 +92,7 @@ typedef struct {
     const double* knots;
     const int64_t* cp_off;
     const double* cps;
+    const double* weights;
 } bspl_curves;
 
 /* Tensor-product surfaces in CSR form: surface s has degrees deg_u[s],
@@ -252,14 +265,25 @@ size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64
  *   midpoint of its parameter interval and both halves are reduced again
  *   from the original piece (depth cap 40 and at most 65536 pieces per span
  *   or span pair; reaching either accepts the piece and -> BSPL_ENOTCONV).
+ * Rational curves (bspl_curves.weights, weights not all equal): the matrix
+ * route is applied to the homogeneous control points (w_i P_i, w_i), which
+ * gives each span's rational Bezier piece as homogeneous points (W_j Q_j,
+ * W_j); a piece (or a half of one, by de Casteljau halving of the
+ * homogeneous points) is replaced by the C1 Hermite cubic of its end points
+ * and end derivatives, accepted when the certified bound
+ * max_k |(A - W R)_k| / min_j W_j (Bernstein coefficients of A - W R at
+ * degree p + 3, A and W the numerator and weight of the piece, R the
+ * cubic) is at most tol_rel x diag, else split at the midpoint like a
+ * reduced piece (same caps).
  * Two-phase use: with out->ctrl == NULL the call only counts: it writes
  * out->seg_off, out->diag and *n_seg_total and returns BSPL_OK.  Otherwise,
  * if *n_seg_total > out->capacity (or the group count exceeds
  * out->grp_capacity) it writes the counts and returns BSPL_ENOSPACE; else it
  * fills every array of *out.  out->n_cp_total must equal cp_off[n].
  * Invalid spline data (degree out of range, knot count
- * mismatch, decreasing or non-finite knots, non-finite control points, empty
- * domain) -> BSPL_EINVAL with nothing written beyond seg_off/diag.
+ * mismatch, decreasing or non-finite knots, non-finite control points, a
+ * weight that is not finite and positive, empty domain) -> BSPL_EINVAL with
+ * nothing written beyond seg_off/diag.
  * Workspace: bspl_workspace_bytes(BSPL_OP_DECOMPOSE_*, n, n_cp_total, 0, 0). */
 bspl_status bspl_decompose(int is_surface, const void* splines, double tol_rel, bspl_segments* out,
                            int64_t* n_seg_total, void* ws, size_t ws_bytes, cudaStream_t stream);
@@ -337,7 +361,8 @@ bspl_status bspl_project_curves_noalloc(const bspl_segments* segs, int64_t n_q, 
                                         uint8_t* status, cudaStream_t stream);
 
 /* Evaluates the ORIGINAL curves at t [n_q] (Cox-de Boor, Sec. 3 Eq.
- * bsplinebasis): xyz [n_q][3].  t outside the domain is clamped; an
+ * bsplinebasis; rational curves: the homogeneous sums divided by the
+ * weight sum): xyz [n_q][3].  t outside the domain is clamped; an
  * out-of-range curve index yields NaN.  Used to place inversion queries. */
 bspl_status bspl_eval_curves(const bspl_curves* curves, int64_t n_q, const int32_t* q_curve, const double* t,
                              double* xyz, cudaStream_t stream);
@@ -352,7 +377,9 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
  * original parameter, as bspl_project_curves / bspl_invert_curves return
  * it), FP64 Newton on E = (C - q).C', E' = C'.C' + (C - q).C'' (Sec. 4.2.3,
  * Eqs. Et and E't) with C, C', C'' by the Cox-de Boor recursion on the
- * original knots and control points; every step is clamped to the domain and
+ * original knots and control points (rational curves: on the homogeneous
+ * points, then C = A/W, C' = (A' - W'C)/W, C'' = (A'' - 2W'C' - W''C)/W, the
+ * quotient rule: rational Newton); every step is clamped to the domain and
  * halved (at most 12 times) until the squared distance does not grow, until
  * E is zero to its FP64 rounding, the step falls below the resolution of t
  * or the distance stops decreasing.  At most max_iter steps (0: 16; at most

@@ -47,7 +47,7 @@ class BsplError(RuntimeError):
 
 class bspl_curves(C.Structure):
     _fields_ = [("n", C.c_int64), ("degree", C.c_void_p), ("knot_off", C.c_void_p), ("knots", C.c_void_p),
-                ("cp_off", C.c_void_p), ("cps", C.c_void_p)]
+                ("cp_off", C.c_void_p), ("cps", C.c_void_p), ("weights", C.c_void_p)]
 
 
 class bspl_surfaces(C.Structure):
@@ -176,7 +176,9 @@ def _dev(x, dtype, device):
 # ------------------------------------------------------------------ inputs
 
 class DeviceCurves:
-    """A CSR curve set (see synth.CurveSet) resident on the GPU."""
+    """A CSR curve set (see synth.CurveSet) resident on the GPU; with a
+    ``weights`` attribute that is not None (one weight per control point)
+    the curves are rational."""
 
     def __init__(self, cs, device="cuda"):
         self.n = int(len(cs.degree))
@@ -185,9 +187,11 @@ class DeviceCurves:
         self.knots = _dev(cs.knots, torch.float64, device)
         self.cp_off = _dev(cs.cp_off, torch.int64, device)
         self.cps = _dev(np.asarray(cs.cps).reshape(-1, 3), torch.float64, device)
+        w = getattr(cs, "weights", None)
+        self.weights = None if w is None else _dev(np.asarray(w).reshape(-1), torch.float64, device)
         self.n_cp_total = int(cs.cp_off[-1])
         self.c = bspl_curves(self.n, _ptr(self.degree), _ptr(self.knot_off), _ptr(self.knots), _ptr(self.cp_off),
-                             _ptr(self.cps))
+                             _ptr(self.cps), None if self.weights is None else _ptr(self.weights))
 
 
 class DeviceSurfaces:

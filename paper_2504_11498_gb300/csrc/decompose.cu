@@ -100,9 +100,11 @@ __device__ void fill_coef(RedCoef<MP>& cf)
 // N_{q-p..q,p} in u = (t - t_q)/(t_{q+1} - t_q) by the Cox-de Boor recursion
 // on polynomials (the product M_{q,p,T} A_{q,p,T}), coefficients c = (M A) P,
 // Bezier points Q = B_p^{-1} c with (B_p^{-1})_{ij} = C(i,j)/C(p,j).
-template <int MP>
+// NC = 4: the homogeneous points (w_j P_j, w_j) of a rational curve, wl the
+// weights (the route is linear in the points); Q is then [p+1][4].
+template <int MP, int NC = 3>
 __host__ __device__ void span_bezier(int p, const double* __restrict__ U, int q, const double* __restrict__ Pl,
-                                     int64_t pstride, double* Q)
+                                     int64_t pstride, double* Q, const double* __restrict__ wl = nullptr)
 {
     double poly[MP + 1][MP + 1], nw[MP + 1][MP + 1];
     double du = fsub(U[q + 1], U[q]);
@@ -135,18 +137,23 @@ __host__ __device__ void span_bezier(int p, const double* __restrict__ U, int q,
         for (int j = 0; j <= k; ++j)
             for (int e = 0; e <= k; ++e) poly[j][e] = nw[j][e];
     }
-    double cc[MP + 1][3];
+    double cc[MP + 1][NC];
     for (int e = 0; e <= p; ++e)
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < NC; ++c) {
             double s = 0.0;
-            for (int j = 0; j <= p; ++j) s = fadd(s, fmul(poly[j][e], Pl[3 * pstride * j + c]));
+            for (int j = 0; j <= p; ++j) {
+                double v;
+                if constexpr (NC == 4) v = c < 3 ? fmul(wl[j], Pl[3 * pstride * j + c]) : wl[j];
+                else v = Pl[3 * pstride * j + c];
+                s = fadd(s, fmul(poly[j][e], v));
+            }
             cc[e][c] = s;
         }
     for (int i = 0; i <= p; ++i)
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < NC; ++c) {
             double s = 0.0;
             for (int e = 0; e <= i; ++e) s = fadd(s, fmul(fdiv(binom_d(i, e), binom_d(p, e)), cc[e][c]));
-            Q[3 * i + c] = s;
+            Q[NC * i + c] = s;
         }
 }
 
@@ -273,26 +280,102 @@ __host__ __device__ double bound2_curve(int p, const double* Q, int s, const dou
 
 // de Casteljau halving at 1/2; keeps the left (side = 0) or right (side = 1)
 // half in place.  Identical arithmetic to computing both halves at once.
-template <int MP>
+// (NC = 4: homogeneous points, whose halving is the same linear map)
+template <int MP, int NC = 3>
 __host__ __device__ void halve_keep(int p, double* Q, int s, int side)
 {
-    double w[(MP + 1) * 3], keep[(MP + 1) * 3];
+    double w[(MP + 1) * NC], keep[(MP + 1) * NC];
     for (int i = 0; i <= p; ++i)
-        for (int c = 0; c < 3; ++c) w[3 * i + c] = Q[i * s + c];
-    for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < NC; ++c) w[NC * i + c] = Q[i * s + c];
+    for (int c = 0; c < NC; ++c) {
         if (side == 0) keep[c] = w[c];
-        else keep[3 * p + c] = w[3 * p + c];
+        else keep[NC * p + c] = w[NC * p + c];
     }
     for (int r = 1; r <= p; ++r) {
         for (int i = 0; i <= p - r; ++i)
-            for (int c = 0; c < 3; ++c) w[3 * i + c] = fmul(fadd(w[3 * i + c], w[3 * (i + 1) + c]), 0.5);
-        for (int c = 0; c < 3; ++c) {
-            if (side == 0) keep[3 * r + c] = w[c];
-            else keep[3 * (p - r) + c] = w[3 * (p - r) + c];
+            for (int c = 0; c < NC; ++c) w[NC * i + c] = fmul(fadd(w[NC * i + c], w[NC * (i + 1) + c]), 0.5);
+        for (int c = 0; c < NC; ++c) {
+            if (side == 0) keep[NC * r + c] = w[c];
+            else keep[NC * (p - r) + c] = w[NC * (p - r) + c];
         }
     }
     for (int i = 0; i <= p; ++i)
-        for (int c = 0; c < 3; ++c) Q[i * s + c] = keep[3 * i + c];
+        for (int c = 0; c < NC; ++c) Q[i * s + c] = keep[NC * i + c];
+}
+
+// ------------------------------------------------------- rational pieces
+//
+// A rational curve is C = A/W, A = sum N_i w_i P_i, W = sum N_i w_i: its
+// span's piece is the rational Bezier of the homogeneous points H_j =
+// (W_j Q_j, W_j) that the matrix route gives for (w_i P_i, w_i), and its
+// halving is the halving of H.  The query tables hold polynomial cubics, so a
+// rational node is replaced by its C1 Hermite cubic R and accepted when a
+// certified bound of |C - R| meets the tolerance (the paper's method covers
+// non-rational splines only; this extends its error-controlled subdivision
+// to them).
+
+// R_0 = C(0), R_3 = C(1), R_1 = C(0) + C'(0)/3, R_2 = C(1) - C'(1)/3, with
+// C'(0) = p (H_1 - W_1 C(0)) / W_0 and C'(1) = p (W_{p-1} C(1) - H_{p-1}) / W_p
+// (the quotient rule at the ends of a rational Bezier; H_j its first three
+// coordinates)
+template <int MP>
+__host__ __device__ void rhermite(int p, const double* H, double* R, const RedCoef<MP>& cf)
+{
+    const double a = cf.ap[p];
+    const double* h0 = H;
+    const double* h1 = H + 4;
+    const double* hm = H + 4 * (p - 1);
+    const double* hp = H + 4 * p;
+    for (int c = 0; c < 3; ++c) {
+        const double c0 = fdiv(h0[c], h0[3]), c1 = fdiv(hp[c], hp[3]);
+        R[c] = c0;
+        R[3 + c] = fadd(c0, fmul(a, fdiv(fsub(h1[c], fmul(h1[3], c0)), h0[3])));
+        R[6 + c] = fadd(c1, fmul(a, fdiv(fsub(hm[c], fmul(hm[3], c1)), hp[3])));
+        R[9 + c] = c1;
+    }
+}
+
+// Certified bound of max_u |C(u) - R(u)|^2 over the node: C - R = (A - W R)/W
+// with A - W R a polynomial of degree p + 3, whose Bernstein coefficients
+// are A's elevated three times minus those of the product W R,
+//   (W R)_k = sum_j [C(p, j) C(3, k - j) / C(p + 3, k)] W_j R_{k-j};
+// the largest coefficient norm bounds |A - W R| (convex partition of unity)
+// and W >= min_j W_j > 0.
+template <int MP>
+__host__ __device__ double rbound2(int p, const double* H, const double* R)
+{
+    double e[(MP + 4) * 4], x[(MP + 4) * 4];
+    for (int i = 0; i < 4 * (p + 1); ++i) e[i] = H[i];
+    for (int n = p; n < p + 3; ++n) {
+        for (int c = 0; c < 4; ++c) {
+            x[c] = e[c];
+            x[4 * (n + 1) + c] = e[4 * n + c];
+        }
+        for (int i = 1; i <= n; ++i) {
+            const double a = fdiv((double)i, (double)(n + 1)), b = fdiv((double)(n + 1 - i), (double)(n + 1));
+            for (int c = 0; c < 4; ++c) x[4 * i + c] = fadd(fmul(a, e[4 * (i - 1) + c]), fmul(b, e[4 * i + c]));
+        }
+        for (int i = 0; i < 4 * (n + 2); ++i) e[i] = x[i];
+    }
+    double wmin = H[3];
+    for (int j = 1; j <= p; ++j)
+        if (H[4 * j + 3] < wmin) wmin = H[4 * j + 3];
+    double b = 0.0;
+    for (int k = 0; k <= p + 3; ++k) {
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        const int jlo = k - 3 > 0 ? k - 3 : 0, jhi = k < p ? k : p;
+        for (int j = jlo; j <= jhi; ++j) {
+            const double cw = fmul(fdiv(fmul(binom_d(p, j), binom_d(3, k - j)), binom_d(p + 3, k)), H[4 * j + 3]);
+            const double* r = R + 3 * (k - j);
+            sx = fadd(sx, fmul(cw, r[0]));
+            sy = fadd(sy, fmul(cw, r[1]));
+            sz = fadd(sz, fmul(cw, r[2]));
+        }
+        const double dx = fsub(e[4 * k], sx), dy = fsub(e[4 * k + 1], sy), dz = fsub(e[4 * k + 2], sz);
+        const double d2 = fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz));
+        if (d2 > b) b = d2;
+    }
+    return fdiv(b, fmul(wmin, wmin));
 }
 
 __host__ __device__ double dyadic_t(double tq, double tq1, int64_t k, int L)
@@ -347,7 +430,11 @@ __host__ __device__ double box_diag_d(const double* P, int64_t np)
     return fsqrt(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
 }
 
-__global__ void k_validate_curves(bspl_curves C, int64_t n_cp, double* diag, int* err, int* maxdeg)
+// rat [n]: 1 for a rational curve whose weights are not all equal (it takes
+// the rational walk), else 0 (equal weights: A/W = sum N_i P_i, the basis
+// being a partition of unity, so the curve is the non-rational one); flags
+// bit 2 of err when any curve is rational
+__global__ void k_validate_curves(bspl_curves C, int64_t n_cp, double* diag, int* err, int* maxdeg, int* rat)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C.n) return;
@@ -359,9 +446,22 @@ __global__ void k_validate_curves(bspl_curves C, int64_t n_cp, double* diag, int
     if (ok)
         for (int64_t i = 0; i < 3 * nP; ++i)
             if (!isfinite(P[i])) { ok = false; break; }
+    int r = 0;
+    if (ok && C.weights) {
+        const double* w = C.weights + C.cp_off[c];
+        for (int64_t i = 0; i < nP; ++i) {
+            if (!(isfinite(w[i]) && w[i] > 0.0)) {
+                ok = false;
+                break;
+            }
+            if (w[i] != w[0]) r = 1;
+        }
+    }
+    rat[c] = ok ? r : 0;
     diag[c] = ok ? box_diag_d(P, nP) : __longlong_as_double(0x7ff8000000000000LL);
     if (!ok) atomicOr(err, 1);
     else atomicMax(maxdeg, p);
+    if (ok && r) atomicOr(err, 4);
 }
 
 __global__ void k_validate_surfaces(bspl_surfaces S, int64_t n_cp, double* diag, int* err, int* maxdeg)
@@ -459,10 +559,68 @@ __host__ __device__ int64_t walk_span_curve(int p, const double* __restrict__ U,
     return count;
 }
 
-// slot = cp_off[c] + (q - p), q in [p, ncp-1]
+// the same walk over the homogeneous piece of a span of a rational curve
+// (weights wl of its p + 1 control points), each node replaced by its
+// Hermite cubic and accepted by the bound rbound2
 template <int MP, bool FILL>
+__host__ __device__ int64_t walk_span_rcurve(int p, const double* __restrict__ U, int q,
+                                             const double* __restrict__ Pl, const double* __restrict__ wl,
+                                             double thr2, int64_t first, CurveLeafOut out, int* err,
+                                             const RedCoef<MP>& cf)
+{
+    constexpr int kStack = MP == 7 ? 12 : (MP == 15 ? 6 : 3);
+    constexpr int W = (MP + 1) * 4;
+    double stk[kStack][W], H[W];
+    const int np4 = 4 * (p + 1);
+    span_bezier<MP, 4>(p, U, q, Pl, 1, stk[0], wl);
+    int L = 0;
+    int64_t k = 0, count = 0;
+    for (;;) {
+        if (L == 0) {
+            for (int i = 0; i < np4; ++i) H[i] = stk[0][i];
+        } else if (L < kStack) {
+            for (int i = 0; i < np4; ++i) H[i] = stk[L - 1][i];
+            halve_keep<MP, 4>(p, H, 4, (int)(k & 1));
+            for (int i = 0; i < np4; ++i) stk[L][i] = H[i];
+        } else {
+            for (int i = 0; i < np4; ++i) H[i] = stk[kStack - 1][i];
+            for (int d = kStack; d <= L; ++d) halve_keep<MP, 4>(p, H, 4, (int)((k >> (L - d)) & 1));
+        }
+        double R[12];
+        rhermite<MP>(p, H, R, cf);
+        bool accept = rbound2<MP>(p, H, R) <= thr2;
+        if (!accept && (L >= kDepthCap || count >= kLeafCap)) {
+            accept = true;
+            set_flag(err, 2);
+        }
+        if (accept) {
+            if (FILL) {
+                int64_t o = first + count;
+                double* dst = out.ctrl + 12 * o;
+                for (int i = 0; i < 12; ++i) dst[i] = R[i];
+                out.prange[2 * o] = dyadic_t(U[q], U[q + 1], k, L);
+                out.prange[2 * o + 1] = dyadic_t(U[q], U[q + 1], k + 1, L);
+            }
+            ++count;
+            while (L > 0 && (k & 1)) {
+                k >>= 1;
+                --L;
+            }
+            if (L == 0) break;
+            k += 1;
+        } else {
+            ++L;
+            k <<= 1;
+        }
+    }
+    return count;
+}
+
+// slot = cp_off[c] + (q - p), q in [p, ncp-1]; RAT: the rational curves
+// (rat[c] = 1) only, else the others
+template <int MP, bool FILL, bool RAT = false>
 __global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, double tol_rel, int64_t n_slots,
-                              int64_t* __restrict__ cnt, CurveLeafOut out, int* err)
+                              int64_t* __restrict__ cnt, CurveLeafOut out, int* err, const int* __restrict__ rat)
 {
     __shared__ RedCoef<MP> cf;
     fill_coef<MP>(cf);
@@ -473,15 +631,19 @@ __global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, do
     // this instance handles degrees (MP/2, MP] (1..7, 8..15, 16..31); invalid
     // curves carry a NaN diagonal and are skipped
     constexpr int lo = MP == 7 ? 1 : (MP + 1) / 2;
-    if (p < lo || p > MP || !(diag[c] >= 0.0)) return;
+    if (p < lo || p > MP || !(diag[c] >= 0.0) || (rat[c] != 0) != RAT) return;
     int64_t nP = C.cp_off[c + 1] - C.cp_off[c];
     int q = p + (int)(slot - C.cp_off[c]);
     const double* U = C.knots + C.knot_off[c];
     int64_t r = 0;
     if (q <= nP - 1 && U[q] < U[q + 1]) {
         double thr = fmul(tol_rel, diag[c]);
-        r = walk_span_curve<MP, FILL>(p, U, q, C.cps + 3 * (C.cp_off[c] + q - p), fmul(thr, thr),
-                                      FILL ? cnt[slot] : 0, out, err, cf);
+        if constexpr (RAT)
+            r = walk_span_rcurve<MP, FILL>(p, U, q, C.cps + 3 * (C.cp_off[c] + q - p), C.weights + C.cp_off[c] + q - p,
+                                           fmul(thr, thr), FILL ? cnt[slot] : 0, out, err, cf);
+        else
+            r = walk_span_curve<MP, FILL>(p, U, q, C.cps + 3 * (C.cp_off[c] + q - p), fmul(thr, thr),
+                                          FILL ? cnt[slot] : 0, out, err, cf);
     }
     if (!FILL) cnt[slot] = r;
 }
@@ -1035,6 +1197,22 @@ void launch1d(K kernel, int64_t n, cudaStream_t s, A... args)
 
 }  // namespace
 
+// the walks of every span of the curve set: one launch per degree class
+// (1-7, 8-15, 16-31) present, for the non-rational curves and, when there
+// are any, for the rational ones
+template <bool FILL>
+void walk_curves(const bspl_curves& C, const double* diag, double tol_rel, int64_t n_cp, int64_t* cnt,
+                 CurveLeafOut o, int* err, const int* rat, int maxdeg, bool any_rat, cudaStream_t s)
+{
+    launch1d(k_walk_curves<7, FILL>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
+    if (maxdeg > 7) launch1d(k_walk_curves<15, FILL>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
+    if (maxdeg > 15) launch1d(k_walk_curves<31, FILL>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
+    if (!any_rat) return;
+    launch1d(k_walk_curves<7, FILL, true>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
+    if (maxdeg > 7) launch1d(k_walk_curves<15, FILL, true>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
+    if (maxdeg > 15) launch1d(k_walk_curves<31, FILL, true>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
+}
+
 size_t decompose_ws_bytes(int is_surface, int64_t n, int64_t n_cp_total)
 {
     (void)is_surface;
@@ -1044,6 +1222,7 @@ size_t decompose_ws_bytes(int is_surface, int64_t n, int64_t n_cp_total)
     cv.take<int64_t>((size_t)n + 1);
     cv.take<int64_t>(scan_tmp_elems(n_cp_total + 1) + scan_tmp_elems(n + 1));
     cv.take<int64_t>(4);
+    cv.take<int>((size_t)n);
     return cv.used + 256;
 }
 
@@ -1073,19 +1252,21 @@ static bspl_status decompose_impl(int is_surface, const void* splines, double to
     w.gcnt = cv.take<int64_t>((size_t)n + 1);
     w.tmp = cv.take<int64_t>(scan_tmp_elems(n_cp + 1) + scan_tmp_elems(n + 1));
     int64_t* dev_tot = cv.take<int64_t>(4);
+    int* rat = cv.take<int>((size_t)n);
     CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
     CK(cudaMemsetAsync(w.cnt, 0, sizeof(int64_t) * (size_t)(n_cp + 1), s));
 
     // validation (invalid splines get a NaN diagonal, which the walks skip,
     // and raise bit 0)
     if (is_surface) launch1d(k_validate_surfaces, n, s, *SS, n_cp, out->diag, w.err, w.maxdeg);
-    else launch1d(k_validate_curves, n, s, *CC, n_cp, out->diag, w.err, w.maxdeg);
+    else launch1d(k_validate_curves, n, s, *CC, n_cp, out->diag, w.err, w.maxdeg, rat);
     CK(cudaGetLastError());
     int hf[2];
     CK(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hf[0] & 1) return BSPL_EINVAL;
     const int maxdeg = hf[1];
+    const bool any_rat = (hf[0] & 4) != 0;
 
     // counting pass
     if (is_surface) {
@@ -1094,13 +1275,7 @@ static bspl_status decompose_impl(int is_surface, const void* splines, double to
                  w.err);
     } else {
         CurveLeafOut o{};
-        launch1d(k_walk_curves<7, false>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
-        if (maxdeg > 7)
-            launch1d(k_walk_curves<15, false>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o,
-                     w.err);
-        if (maxdeg > 15)
-            launch1d(k_walk_curves<31, false>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o,
-                     w.err);
+        walk_curves<false>(*CC, out->diag, tol_rel, n_cp, w.cnt, o, w.err, rat, maxdeg, any_rat, s);
     }
     CK(cudaGetLastError());
     CK(exclusive_scan_i64(w.cnt, w.cnt, n_cp + 1, w.tmp, s));
@@ -1157,11 +1332,7 @@ static bspl_status decompose_impl(int is_surface, const void* splines, double to
                  out->grp32);
     } else {
         CurveLeafOut o{ out->ctrl, out->prange };
-        launch1d(k_walk_curves<7, true>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
-        if (maxdeg > 7)
-            launch1d(k_walk_curves<15, true>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
-        if (maxdeg > 15)
-            launch1d(k_walk_curves<31, true>, n_cp, s, *CC, (const double*)out->diag, tol_rel, n_cp, w.cnt, o, w.err);
+        walk_curves<true>(*CC, out->diag, tol_rel, n_cp, w.cnt, o, w.err, rat, maxdeg, any_rat, s);
         launch1d(k_curve_records, h[0], s, (const double*)out->ctrl, h[0], out->rec64, out->rec32);
         launch1d(k_group_records, n_grp, s, (const int64_t*)out->seg_off, (const int64_t*)out->grp_off, n, n_grp,
                  (const double*)out->rec64, (int)BSPL_CREC64, (const double*)out->ctrl, 12, out->grp64,

@@ -1,7 +1,9 @@
 // Evaluation of the ORIGINAL B-spline curves and surfaces (Sec. 3, Eq.
 // bsplinebasis) at given parameters: one thread per point, span by binary
 // search, basis by the triangular Cox-de Boor recursion.  Used to place
-// inversion queries on the spline.
+// inversion queries on the spline.  Rational curves (per-control-point
+// weights w_i): the same sums over the homogeneous points (w_i P_i, w_i),
+// divided by the weight sum, and for the refinement the quotient rule.
 #include <math.h>
 
 #include "bspl_internal.cuh"
@@ -64,8 +66,19 @@ __global__ void k_eval_curves(bspl_curves C, int64_t n_q, const int32_t* __restr
             basis<kMaxCurveDegree>(U, q, p, t, N);
             const double* P = C.cps + 3 * C.cp_off[c];
             for (int k = 0; k < 3; ++k) out[k] = 0.0;
-            for (int j = 0; j <= p; ++j)
-                for (int k = 0; k < 3; ++k) out[k] += N[j] * P[3 * (q - p + j) + k];
+            if (C.weights) {
+                const double* w = C.weights + C.cp_off[c];
+                double W = 0.0;
+                for (int j = 0; j <= p; ++j) {
+                    const double nw = N[j] * w[q - p + j];
+                    W += nw;
+                    for (int k = 0; k < 3; ++k) out[k] += nw * P[3 * (q - p + j) + k];
+                }
+                for (int k = 0; k < 3; ++k) out[k] /= W;
+            } else {
+                for (int j = 0; j <= p; ++j)
+                    for (int k = 0; k < 3; ++k) out[k] += N[j] * P[3 * (q - p + j) + k];
+            }
         }
     }
     for (int k = 0; k < 3; ++k) xyz[3 * i + k] = out[k];
@@ -82,18 +95,28 @@ __global__ void k_eval_curves(bspl_curves C, int64_t n_q, const int32_t* __restr
 // Both denominators span [U_q, U_{q+1}], a non-empty span, so neither is 0.
 // Computed once per span for degrees up to 8, so the Newton iterations
 // divide nothing; the rare higher degrees keep no cache (it would take
-// kilobytes of stack per thread) and divide at every evaluation.
-template <int MP>
+// kilobytes of stack per thread) and divide at every evaluation.  Rational
+// curves (NC = 4): the same for the homogeneous points (w_i P_i, w_i).
+template <int MP, int NC = 3>
 struct SpanCache {
     static constexpr int K = MP <= 8 ? MP : 1;
     int q;
     double inv[K * (K + 1) / 2];
-    double Q[K][3];
-    double R[K][3];
+    double Q[K][NC];
+    double R[K][NC];
 };
 
-template <int MP>
-__device__ __forceinline__ void span_prepare(const double* U, const double* P, int p, int q, SpanCache<MP>& S)
+// control point i of the curve: P_i, or (w_i P_i, w_i) for a rational one
+template <int NC>
+__device__ __forceinline__ double hpt(const double* P, const double* w, int i, int k)
+{
+    if constexpr (NC == 4) return k < 3 ? w[i] * P[3 * i + k] : w[i];
+    else return P[3 * i + k];
+}
+
+template <int MP, int NC>
+__device__ __forceinline__ void span_prepare(const double* U, const double* P, const double* w, int p, int q,
+                                             SpanCache<MP, NC>& S)
 {
     static_assert(MP <= 8, "span cache for low degrees only");
     S.q = q;
@@ -111,10 +134,11 @@ __device__ __forceinline__ void span_prepare(const double* U, const double* P, i
     for (int j = 0; j < MP; ++j) {
         if (j >= p) break;
         const double sq = p / (U[q + j + 1] - U[q - p + j + 1]);
-        for (int k = 0; k < 3; ++k) S.Q[j][k] = sq * (P[3 * (q - p + j + 1) + k] - P[3 * (q - p + j) + k]);
+        for (int k = 0; k < NC; ++k)
+            S.Q[j][k] = sq * (hpt<NC>(P, w, q - p + j + 1, k) - hpt<NC>(P, w, q - p + j, k));
         if (j >= 1) {
             const double sr = (p - 1) / (U[q + j] - U[q - p + j + 1]);
-            for (int k = 0; k < 3; ++k) S.R[j - 1][k] = sr * (S.Q[j][k] - S.Q[j - 1][k]);
+            for (int k = 0; k < NC; ++k) S.R[j - 1][k] = sr * (S.Q[j][k] - S.Q[j - 1][k]);
         }
     }
 }
@@ -122,15 +146,17 @@ __device__ __forceinline__ void span_prepare(const double* U, const double* P, i
 // C(t), C'(t) and C''(t) of a curve of degree p with control points P[0..m]:
 // the basis values of degrees p, p - 1 and p - 2 at t by the triangular
 // recursion (its two rows before the last kept), times the span's control
-// points P, Q and R.
-template <int MP>
-__device__ __forceinline__ void curve_d2(const double* U, const double* P, int p, int m, double t,
-                                         SpanCache<MP>& S, double* C, double* C1, double* C2)
+// points P, Q and R.  NC = 4: the same on the homogeneous points gives
+// A, A', A'' and W, W', W'', and then C = A/W, C' = (A' - W'C)/W,
+// C'' = (A'' - 2W'C' - W''C)/W.
+template <int MP, int NC = 3>
+__device__ __forceinline__ void curve_d2(const double* U, const double* P, const double* w, int p, int m, double t,
+                                         SpanCache<MP, NC>& S, double* Cout, double* C1out, double* C2out)
 {
     constexpr bool kCache = MP <= 8;
     const int q = span_of(U, p, m, t);
     if constexpr (kCache) {
-        if (q != S.q) span_prepare<MP>(U, P, p, q, S);
+        if (q != S.q) span_prepare<MP, NC>(U, P, w, p, q, S);
     }
     double N[MP + 1], N1[MP + 1], N2[MP + 1], left[MP + 1], right[MP + 1];
     N[0] = 1.0;
@@ -164,29 +190,45 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, int p
         }
         N[j] = saved;
     }
-    for (int k = 0; k < 3; ++k) C[k] = C1[k] = C2[k] = 0.0;
-    double Qp[3] = { 0.0, 0.0, 0.0 };
+    double C[NC], C1[NC], C2[NC];
+    for (int k = 0; k < NC; ++k) C[k] = C1[k] = C2[k] = 0.0;
+    double Qp[NC];
+    for (int k = 0; k < NC; ++k) Qp[k] = 0.0;
 #pragma unroll(MP <= 8 ? MP + 1 : 1)
     for (int j = 0; j <= MP; ++j) {
         if (j > p) break;
-        for (int k = 0; k < 3; ++k) C[k] += N[j] * P[3 * (q - p + j) + k];
+        for (int k = 0; k < NC; ++k) C[k] += N[j] * hpt<NC>(P, w, q - p + j, k);
         if constexpr (kCache) {
             if (j < p)
-                for (int k = 0; k < 3; ++k) C1[k] += N1[j] * S.Q[j][k];
+                for (int k = 0; k < NC; ++k) C1[k] += N1[j] * S.Q[j][k];
             if (j + 1 < p)
-                for (int k = 0; k < 3; ++k) C2[k] += N2[j] * S.R[j][k];
+                for (int k = 0; k < NC; ++k) C2[k] += N2[j] * S.R[j][k];
         } else if (j < p) {
             const double sq = p / (U[q + j + 1] - U[q - p + j + 1]);
-            double Qj[3];
-            for (int k = 0; k < 3; ++k) {
-                Qj[k] = sq * (P[3 * (q - p + j + 1) + k] - P[3 * (q - p + j) + k]);
+            double Qj[NC];
+            for (int k = 0; k < NC; ++k) {
+                Qj[k] = sq * (hpt<NC>(P, w, q - p + j + 1, k) - hpt<NC>(P, w, q - p + j, k));
                 C1[k] += N1[j] * Qj[k];
             }
             if (j >= 1) {
                 const double sr = (p - 1) / (U[q + j] - U[q - p + j + 1]);
-                for (int k = 0; k < 3; ++k) C2[k] += N2[j - 1] * sr * (Qj[k] - Qp[k]);
+                for (int k = 0; k < NC; ++k) C2[k] += N2[j - 1] * sr * (Qj[k] - Qp[k]);
             }
-            for (int k = 0; k < 3; ++k) Qp[k] = Qj[k];
+            for (int k = 0; k < NC; ++k) Qp[k] = Qj[k];
+        }
+    }
+    if constexpr (NC == 4) {
+        const double W = C[3], W1 = C1[3], W2 = C2[3];
+        for (int k = 0; k < 3; ++k) {
+            Cout[k] = C[k] / W;
+            C1out[k] = (C1[k] - W1 * Cout[k]) / W;
+            C2out[k] = (C2[k] - 2.0 * W1 * C1out[k] - W2 * Cout[k]) / W;
+        }
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            Cout[k] = C[k];
+            C1out[k] = C1[k];
+            C2out[k] = C2[k];
         }
     }
 }
@@ -205,15 +247,17 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, int p
 // the domain.  The result never has a larger distance than the start.
 // the refinement of one query on a curve of degree p <= MP; returns whether
 // it converged, with the final t and squared distance
-template <int MP>
-__device__ __noinline__ bool refine_one(const double* __restrict__ U, const double* __restrict__ P, int p, int m,
-                                        const double* q, int max_iter, double& t, double& D)
+// (NC = 4: a rational curve with weights w, rational Newton)
+template <int MP, int NC>
+__device__ __noinline__ bool refine_one(const double* __restrict__ U, const double* __restrict__ P,
+                                        const double* __restrict__ w, int p, int m, const double* q, int max_iter,
+                                        double& t, double& D)
 {
     const double a = U[p], b = U[m + 1];
-    SpanCache<MP> S;
+    SpanCache<MP, NC> S;
     S.q = -1;
     double C[3], C1[3], C2[3];
-    curve_d2<MP>(U, P, p, m, t, S, C, C1, C2);
+    curve_d2<MP, NC>(U, P, w, p, m, t, S, C, C1, C2);
     D = 0.0;
     for (int k = 0; k < 3; ++k) D += (C[k] - q[k]) * (C[k] - q[k]);
     bool conv = false;
@@ -241,7 +285,7 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
         double tn = t, Dn = D, Cn[3], C1n[3], C2n[3];
         for (int hv = 0; hv < 12; ++hv, dt *= 0.5) {
             tn = fmin(fmax(t + dt, a), b);
-            curve_d2<MP>(U, P, p, m, tn, S, Cn, C1n, C2n);
+            curve_d2<MP, NC>(U, P, w, p, m, tn, S, Cn, C1n, C2n);
             Dn = 0.0;
             for (int k = 0; k < 3; ++k) Dn += (Cn[k] - q[k]) * (Cn[k] - q[k]);
             if (Dn <= D) {
@@ -269,6 +313,7 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
     return conv;
 }
 
+template <int NC>
 __global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag, int invert, int64_t n_q,
                                 const int32_t* __restrict__ qc, const double* __restrict__ q_xyz, int max_iter,
                                 double* __restrict__ t_io, double* __restrict__ d_io, uint8_t* __restrict__ st_io)
@@ -288,8 +333,9 @@ __global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag,
     t = fmin(fmax(t, a), b);
     const double q[3] = { q_xyz[3 * i], q_xyz[3 * i + 1], q_xyz[3 * i + 2] };
     double D;
-    const bool conv = p <= 7 ? refine_one<7>(U, P, p, m, q, max_iter, t, D)
-                             : refine_one<kMaxCurveDegree>(U, P, p, m, q, max_iter, t, D);
+    const double* w = NC == 4 ? Cv.weights + Cv.cp_off[c] : nullptr;
+    const bool conv = p <= 7 ? refine_one<7, NC>(U, P, w, p, m, q, max_iter, t, D)
+                             : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D);
     const double d = sqrt(D);
     uint8_t fl = st_io[i] & (uint8_t)~(BSPL_Q_CONVERGED | BSPL_Q_NONCONV | BSPL_Q_AT_END | BSPL_Q_OFF_CURVE);
     fl |= conv ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
@@ -353,8 +399,12 @@ bspl_status refine_curves(const bspl_curves* c, const double* diag, int invert, 
     if (!c || n_q < 0 || max_iter < 0 || max_iter > 100) return BSPL_EINVAL;
     if (n_q > 0 && (!qc || !q_xyz || !t || !dist || !status)) return BSPL_EINVAL;
     if (n_q == 0) return BSPL_OK;
-    k_refine_curves<<<ceil_div(n_q, 128), 128, 0, s>>>(*c, diag, invert, n_q, qc, q_xyz, max_iter ? max_iter : 16,
-                                                       t, dist, status);
+    if (c->weights)
+        k_refine_curves<4><<<ceil_div(n_q, 128), 128, 0, s>>>(*c, diag, invert, n_q, qc, q_xyz,
+                                                              max_iter ? max_iter : 16, t, dist, status);
+    else
+        k_refine_curves<3><<<ceil_div(n_q, 128), 128, 0, s>>>(*c, diag, invert, n_q, qc, q_xyz,
+                                                              max_iter ? max_iter : 16, t, dist, status);
     return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
 }
 

@@ -68,6 +68,31 @@ int64_t hd_surface_span(int pu, int pv, const double* U, int nu, int qu, const d
     return n;
 }
 
+// leaves of span q of a curve of degree p (knots U, control points P, weights
+// w: the rational walk, or the non-rational one when w is NULL): up to cap
+// leaves (ctrl [12], prange [2]); returns their count
+int64_t hd_curve_span(int p, const double* U, int q, const double* P, const double* w, double tol_rel, double diag,
+                      double* ctrl, double* prange, int64_t cap, int* err)
+{
+    static RedCoef<kMaxCurveDegree> cf;
+    static bool filled = false;
+    if (!filled) {
+        host_fill_coef<kMaxCurveDegree>(cf);
+        filled = true;
+    }
+    const double thr = tol_rel * diag, thr2 = thr * thr;
+    *err = 0;
+    const double* Pl = P + 3 * (q - p);
+    CurveLeafOut none{};
+    const int64_t n = w ? walk_span_rcurve<kMaxCurveDegree, false>(p, U, q, Pl, w + (q - p), thr2, 0, none, err, cf)
+                        : walk_span_curve<kMaxCurveDegree, false>(p, U, q, Pl, thr2, 0, none, err, cf);
+    if (n > cap) return n;
+    CurveLeafOut out{ ctrl, prange };
+    if (w) walk_span_rcurve<kMaxCurveDegree, true>(p, U, q, Pl, w + (q - p), thr2, 0, out, err, cf);
+    else walk_span_curve<kMaxCurveDegree, true>(p, U, q, Pl, thr2, 0, out, err, cf);
+    return n;
+}
+
 // derivative bounds and edge flags the filling walk writes into a patch's
 // FP32 record (entries 56..61): the bicubic leaves' records of span pair
 // (qu, qv), rec32 [cap][BSPL_SREC32], pbox [cap][4]

@@ -39,6 +39,9 @@ def hd(tmp_path_factory):
                                     ctypes.c_double, ctypes.c_double, D, D, ctypes.c_int64,
                                     ctypes.POINTER(ctypes.c_int)]
     lib.hd_surface_span.restype = ctypes.c_int64
+    lib.hd_curve_span.argtypes = [ctypes.c_int, D, ctypes.c_int, D, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                  D, D, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
+    lib.hd_curve_span.restype = ctypes.c_int64
     return lib
 
 
@@ -187,3 +190,47 @@ def test_patch_derivative_bounds_and_edge_flags(hd):
                     assert bool(f & 8) == (pb[j, 3] < 1 or smooth(V, pv, nv, V[qv + 1]))
                     checked += 1
     assert checked > 50
+
+
+def host_decompose_curves(hd, cs, tol):
+    """The device's curve walk run on the host span by span (rational curves
+    through the rational walk): seg_off, ctrl, prange."""
+    ctrl_all, pr_all, offs = [], [], [0]
+    for c in range(cs.n):
+        p, U, P = cs.curve(c)
+        U, P = np.ascontiguousarray(U), np.ascontiguousarray(P)
+        w = cs.curve_weights(c)
+        rat = w is not None and np.any(w != w[0])
+        wa = np.ascontiguousarray(w) if rat else None
+        diag = hd.hd_box_diag(dp(P), len(P))
+        n = 0
+        for q in range(p, len(P)):
+            if not U[q] < U[q + 1]:
+                continue
+            cap = 1 << 16
+            ctrl = np.zeros((cap, 12))
+            pr = np.zeros((cap, 2))
+            err = ctypes.c_int()
+            k = hd.hd_curve_span(p, dp(U), q, dp(P), None if wa is None else wa.ctypes.data, tol, diag, dp(ctrl),
+                                 dp(pr), cap, ctypes.byref(err))
+            assert 0 < k <= cap and err.value == 0
+            ctrl_all.append(ctrl[:k])
+            pr_all.append(pr[:k])
+            n += k
+        offs.append(offs[-1] + n)
+    return np.array(offs), np.concatenate(ctrl_all).reshape(-1, 4, 3), np.concatenate(pr_all)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-8, 1e-11])
+def test_rational_curve_walk_bit_exact(hd, tol):
+    """The rational walk (homogeneous pieces, Hermite cubics, certified
+    bound) agrees with the oracle bit for bit, on random NURBS with weights
+    over a 16:1 range and on exact circles."""
+    cs, _ = synth.nurbs_curve_set(seed=31, n_curves=24, n_proj=1, n_inv=0, ncp_range=(8, 20), w_range=(0.25, 4.0))
+    circ = synth.nurbs_circles(seed=32, n_curves=4, n_proj=1)[0]
+    for s in (cs, circ):
+        offs, ctrl, pr = host_decompose_curves(hd, s, tol)
+        ref = O.decompose_curves(s, tol)
+        assert np.array_equal(offs, ref.seg_off)
+        assert np.array_equal(ctrl, ref.ctrl)
+        assert np.array_equal(pr, ref.prange)

@@ -49,11 +49,12 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--curves", type=int, default=4096, help="curves in the workload")
     ap.add_argument("--queries", type=int, default=1_000_000, help="projection and inversion queries each")
-    ap.add_argument("--workload", default="c4", choices=["c2", "c4", "c3", "c5", "p"],
+    ap.add_argument("--workload", default="c4", choices=["c2", "c4", "c3", "c5", "p", "nurbs"],
                     help="c4 (default): 16M projection queries on the 4,096-curve set (learned seed), with the "
                          "c2 batch measured beside it; c2: 1M projection + 1M inversion queries; "
                          "c3: 1,024 surfaces, 4M + 4M queries; c5: 65,536 cubic curves + 8,192 bicubic "
-                         "surfaces, 64M Zipf-skewed queries")
+                         "surfaces, 64M Zipf-skewed queries; p: the paper-shaped 18-curve suite; nurbs: 4,096 "
+                         "rational curves, 1M projection + 1M inversion queries, refined on the original curves")
     ap.add_argument("--surfaces", type=int, default=1024, help="c3: surfaces in the workload")
     ap.add_argument("--surface-queries", type=int, default=4_000_000,
                     help="c3: projection and inversion queries each")
@@ -171,16 +172,18 @@ def combine_over_ranks(times_ms, n_per_rank, world, dist=None, device="cpu"):
 
 # ------------------------------------------------------------ learned seed
 
-def train_seed(args, rank, dev):
+def train_seed(args, rank, dev, rational=False):
     """Trains the seed network on (segment, query, t*) pairs of a second
-    curve set of the same recipe (seed 12): pairs from the learned path's own
-    culling, labels from the FP64 solver, hand-written training kernels.
-    Returns the network and a summary (untimed preprocessing)."""
+    curve set of the same recipe (seed 12; rational=True: the NURBS recipe):
+    pairs from the learned path's own culling, labels from the FP64 solver,
+    hand-written training kernels.  Returns the network and a summary
+    (untimed preprocessing)."""
     import torch
     from paper_2504_11498_gb300 import bspl, synth
     t0 = time.perf_counter()
-    cs, qs = synth.curve_set(seed=12 + 1000 * rank, n_curves=args.train_curves, n_proj=args.train_queries,
-                             n_inv=args.train_queries)
+    make = synth.nurbs_curve_set if rational else synth.curve_set
+    cs, qs = make(seed=12 + 1000 * rank, n_curves=args.train_curves, n_proj=args.train_queries,
+                  n_inv=args.train_queries)
     dc = bspl.DeviceCurves(cs, dev)
     segs = bspl.decompose(dc, TOL)
     inv = bspl.bspl_eval_curves(dc, torch.as_tensor(qs.inv_curve, device=dev),
@@ -259,6 +262,8 @@ def main():
         return run_surface_workloads(args, rank, world, local)
     if args.workload == "p":
         return run_paper_suite(args, rank, world, local)
+    if args.workload == "nurbs":
+        return run_nurbs(args, rank, world, local)
     # c4 (default): 16M projection queries on the 4,096-curve set, the
     # learned-seed configuration, with the c2 batch (1M + 1M) measured beside
     # it; c2: the 1M + 1M batch alone
@@ -799,6 +804,208 @@ def run_paper_suite(args, rank, world, local):
         r, cores, nq, el = cpu_oracle_rate(cs, qs)
         out["cpu_baseline"] = {"value": r, "unit": "pts/s", "cores": cores, "kind": "oracle",
                                "sample": f"{nq} projection queries of the suite, {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ rational curves
+
+def refine_flops(evals, rational=True):
+    """Algorithmic FP64 flops of the refinement from its evaluation counts
+    per degree p (an FMA counts 2): the triangular basis recursion
+    2p^2 + 4p, the sums of C, C', C'' over the span's homogeneous points
+    2 * 4 * (3p) (3 coordinates for a non-rational curve), the quotient rule
+    27, the squared distance and the Newton quantities 30 per evaluation."""
+    nc = 4 if rational else 3
+    return float(sum(int(n) * (2 * p * p + 4 * p + 6 * nc * p + (27 if rational else 0) + 30)
+                     for p, n in enumerate(evals)))
+
+
+def run_nurbs(args, rank, world, local):
+    """--workload nurbs: 4,096 rational curves (the curve-set recipe with
+    per-control-point weights log-uniform in [1/2, 2]) decomposed at 1e-10 x
+    diag into certified cubics (timed once, preprocessing).  One step = 1M
+    projection + 1M inversion queries through the learned path (seed network
+    trained on pairs of a second NURBS set of the same recipe), each call
+    followed by the rational Newton refinement on the original curves, the
+    step captured once as a CUDA graph and replayed; the same step through
+    the mixed grid path and the plain FP64 path beside it.  value = learned
+    pts/s (projections + inversions) per step."""
+    from paper_2504_11498_gb300 import synth
+    n_q = args.queries
+    label = f"nurbs_curve_set_4096: {n_q} projection + {n_q} inversion queries per GPU, refined on the original curves"
+    cs, qs = synth.nurbs_curve_set(seed=4 + 1000 * rank, n_proj=n_q, n_inv=n_q)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        rates, t_all = [], 0.0
+        for _ in range(args.warmup):
+            cpu_oracle_rate(cs, qs, budget_s=2.0, max_q=2000)
+        for _ in range(args.steps):
+            r, cores, nq, el = cpu_oracle_rate(cs, qs, budget_s=8.0, max_q=20000)
+            rates.append(r)
+            t_all += el
+        v = float(np.median(rates))
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "pts/s", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": label, "tol_rel": TOL},
+                          "cpu_baseline": {"value": v, "unit": "pts/s", "cores": cores, "kind": "oracle",
+                                           "sample": f"{nq} queries of the workload per step"},
+                          "e2e": {"value": v, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2504_11498_gb300 import bspl, build
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    mlp, train = train_seed(args, rank, dev, rational=True)
+    dc = bspl.DeviceCurves(cs, dev)
+    for _ in range(2):
+        bspl.decompose(dc, TOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    segs = bspl.decompose(dc, TOL)
+    torch.cuda.synchronize()
+    dec_ms = 1e3 * (time.perf_counter() - t0)
+    pc, pq = torch.as_tensor(qs.proj_curve, device=dev), torch.as_tensor(qs.proj_xyz, device=dev)
+    ic = torch.as_tensor(qs.inv_curve, device=dev)
+    iq = bspl.bspl_eval_curves(dc, ic, torch.as_tensor(qs.inv_t, device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(run, prep=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            if prep is not None:
+                prep()
+            flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
+            a.record(stream)
+            run()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    paths = (("learned", bspl.LEARNED_MIXED, mlp), ("mixed", bspl.MIXED, None), ("plain", bspl.FP64, None))
+    ms, res, graphs, bufs_of = {}, {}, {}, {}
+    rws = bspl.refine_workspace(dc, n_q, dev)  # the refinement groups its queries by curve
+    clocks = ClockSampler(local)
+    clocks.start()
+    for key, prec, net in paths:
+        learned = prec == bspl.LEARNED_MIXED
+        bp = bspl.QueryBuffers(segs, n_q, dev, learned=learned)
+        bi = bspl.QueryBuffers(segs, n_q, dev, learned=learned)
+        o = bspl.make_options(prec=prec, mlp=net)
+
+        def step(bp=bp, bi=bi, o=o):
+            r = bspl.bspl_project_curves(segs, pc, pq, o, bp)
+            bspl.bspl_refine_curves(dc, pc, pq, r, ws=rws)
+            r = bspl.bspl_invert_curves(segs, ic, iq, o, bi)
+            bspl.bspl_refine_curves(dc, ic, iq, r, invert=True, diag=segs.diag, ws=rws)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        with bspl.Graph() as g:
+            step()
+        for _ in range(2):
+            g.replay(stream)
+        ms[key] = timed(lambda: g.replay(stream))
+        graphs[key], bufs_of[key] = g, (bp, bi, o)
+        res[key] = (bp.dist.clone(), bi.dist.clone())
+    # the refinement alone (learned path's results before refinement restored
+    # before each timed pair of refinement launches), and its evaluation counts
+    bp, bi, o = bufs_of["learned"]
+    bspl.bspl_project_curves(segs, pc, pq, o, bp)
+    bspl.bspl_invert_curves(segs, ic, iq, o, bi)
+    saved = [x.clone() for x in (bp.param, bp.dist, bp.status, bi.param, bi.dist, bi.status)]
+
+    def restore():
+        for x, y in zip((bp.param, bp.dist, bp.status, bi.param, bi.dist, bi.status), saved):
+            x.copy_(y)
+
+    def refine_pair(evals=None):
+        bspl.bspl_refine_curves(dc, pc, pq, bp, evals=evals, ws=rws)
+        bspl.bspl_refine_curves(dc, ic, iq, bi, invert=True, diag=segs.diag, evals=evals, ws=rws)
+
+    restore()
+    refine_pair()
+    refine_ms = timed(refine_pair, prep=restore)
+    evals = torch.zeros(bspl.REFINE_EVALS, dtype=torch.int64, device=dev)
+    restore()
+    refine_pair(evals)
+    torch.cuda.synchronize()
+    ev_counts = evals.cpu().numpy().tolist()
+    # end to end: pinned host queries in, results out, around the learned graph
+    h_in = [torch.as_tensor(x).pin_memory() for x in (qs.proj_curve, qs.proj_xyz, qs.inv_curve)]
+    h_iq = iq.cpu().pin_memory()
+    h_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+             for x in (bp.param, bp.dist, bp.status, bi.param, bi.dist, bi.status)]
+    g = graphs["learned"]
+
+    def e2e():
+        for d, h in zip((pc, pq, ic, iq), h_in + [h_iq]):
+            d.copy_(h, non_blocking=True)
+        g.replay(stream)
+        for h, d in zip(h_out, (bp.param, bp.dist, bp.status, bi.param, bi.dist, bi.status)):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(3):
+        e2e()
+    e2e_ms = timed(e2e)
+    clk = clocks.stop()
+    if bspl.mlp_check() != bspl.OK:
+        raise SystemExit("a tensor-core wait timed out")
+    diag = segs.diag.double()
+    worst, over = 0.0, 0
+    for a, b, idx in ((res["learned"][0], res["plain"][0], pc), (res["learned"][1], res["plain"][1], ic)):
+        rel = (a - b).abs() / diag[idx.long()]
+        worst = max(worst, float(rel.max().item()))
+        over += int((rel > 1e-9).sum().item())
+    dist_i = res["learned"][1] / diag[ic.long()]
+    off_curve = int((dist_i > 1e-9).sum().item())
+    (t_l, t_m, t_p, t_r, t_e), total_q = combine_over_ranks(
+        [ms["learned"], ms["mixed"], ms["plain"], refine_ms, e2e_ms], 2 * n_q, world, dist if world > 1 else None,
+        dev)
+    p64 = bspl.measure_fma_peak(True)
+    flops = refine_flops(ev_counts)
+    achieved = flops / (t_r * 1e-3)
+    roofline = {"kernel": "k_refine_curves<4> (rational Newton, FP64)", "bound": "alu",
+                "achieved": achieved / 1e12, "peak": p64 / 1e12, "unit": "TFLOP/s", "frac": achieved / p64,
+                "peak_kind": "FP64 FMA-chain peak measured by bspl.measure_fma_peak on this GPU",
+                "traffic": None, "flops_per_step": flops, "evaluations_per_step": int(sum(ev_counts)),
+                "share_of_learned_step": t_r / t_l}
+    out = {"metric": METRIC, "value": total_q / (t_l * 1e-3), "unit": "pts/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_l, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16+f32+f64 (BF16 tensor-core seed, FP32 search, FP64 finish and rational refinement)",
+           "data": "synthetic",
+           "config": {"workload": label, "tol_rel": TOL, "weights": "log-uniform in [1/2, 2]",
+                      "step": "learned projection + refinement, learned inversion + refinement, one CUDA graph",
+                      "l2": "512 MB flush between timed steps", "seed_network": train,
+                      "segments": int(segs.total), "decompose_ms": dec_ms},
+           "mixed_grid": {"value": total_q / (t_m * 1e-3), "ms_per_step": t_m},
+           "plain_fp64": {"value": total_q / (t_p * 1e-3), "ms_per_step": t_p},
+           "speedup_learned_vs_plain": t_p / t_l,
+           "refine": {"ms_per_step": t_r, "evaluations_by_degree": {str(p): int(n) for p, n in enumerate(ev_counts)
+                                                                     if n}},
+           "accuracy": {"learned_vs_plain_fp64_refined": {"max_rel_dist_diff": worst, "queries_over_1e-9": over},
+                        "inversions_over_1e-9": off_curve},
+           "e2e": {"value": total_q / (t_e * 1e-3), "unit": "pts/s",
+                   "h2d_bytes_per_step": n_q * (4 + 24 + 4 + 24), "d2h_bytes_per_step": 2 * n_q * 17},
+           "gpu_launches": int(graphs["learned"].n_kernels), "roofline": roofline, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, cores, nq, el = cpu_oracle_rate(cs, qs)
+        out["cpu_baseline"] = {"value": r, "unit": "pts/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{nq} queries of the workload (half projection, half inversion), "
+                                         f"{el:.1f} s"}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

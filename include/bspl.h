@@ -247,6 +247,7 @@ typedef struct {
 #define BSPL_OP_MLP_TRAIN 6            /* bspl_mlp_loss_grad / bspl_mlp_train, n_q = batch */
 #define BSPL_OP_SMLP_TRAIN 7           /* the same for the surface seed network */
 #define BSPL_OP_QUERY_SURFACES_LEARNED 8 /* surface queries with opt->prec = BSPL_LEARNED_MIXED */
+#define BSPL_OP_REFINE_CURVES 9          /* bspl_refine_curves grouping its queries by curve */
 
 /* Bytes of device workspace a call of kind `op` needs.  n_splines = n,
  * n_cp_total = total control points (cp_off[n]), n_seg = segments of the
@@ -394,11 +395,22 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
  * approximant's answer: it is the global one unless the original curve has
  * another local minimum whose distance is within twice the decomposition
  * tolerance of it.  Degrees 1..31 (others are left unchanged).
- * BSPL_EINVAL for NULL arrays with n_q > 0, n_q < 0 or max_iter outside
- * 0..100. */
+ *   out     evals: optional device array [BSPL_REFINE_EVALS], accumulated:
+ *           entry p counts the evaluations of C, C', C'' on curves of
+ *           degree p (profiling; NULL: not counted).
+ *   ws      optional device workspace of at least
+ *           bspl_workspace_bytes(BSPL_OP_REFINE_CURVES, curves->n, 0, 0, n_q)
+ *           bytes: the queries are then processed grouped by curve (a warp's
+ *           queries share a curve's degree and knots); NULL: in the caller's
+ *           order.  The results do not depend on the order.
+ * BSPL_EINVAL for NULL arrays with n_q > 0, n_q < 0, max_iter outside
+ * 0..100, or a workspace given with ws_bytes below the size above. */
 bspl_status bspl_refine_curves(const bspl_curves* curves, const double* diag, int invert, int64_t n_q,
                                const int32_t* q_curve, const double* q_xyz, int32_t max_iter, double* t,
-                               double* dist, uint8_t* status, cudaStream_t stream);
+                               double* dist, uint8_t* status, uint64_t* evals, void* ws, size_t ws_bytes,
+                               cudaStream_t stream);
+
+#define BSPL_REFINE_EVALS 32
 
 /* Human-readable name of a status code (static string). */
 const char* bspl_status_string(bspl_status s);

@@ -26,6 +26,7 @@ CREC64, CREC32, SREC64, SREC32, GREC64, GREC32 = 18, 24, 54, 72, 12, 12
 SPAN_NET = 8 * 8 * 3
 OP_DECOMPOSE_CURVES, OP_DECOMPOSE_SURFACES, OP_QUERY_CURVES, OP_QUERY_SURFACES = 1, 2, 3, 4
 OP_QUERY_CURVES_LEARNED, OP_MLP_TRAIN, OP_SMLP_TRAIN, OP_QUERY_SURFACES_LEARNED = 5, 6, 7, 8
+OP_REFINE_CURVES = 9
 # learned seed (include/bspl_mlp.h)
 MLP_IN, MLP_HIDDEN, MLP_NPARAM, MLP_NBF16, MLP_MAX_BATCH = 16, 128, 35332, 2048 + 4 * 16384 + 128, 65536
 MLP_OFF = {"W1": 0, "b1": 2048, "W2": 2176, "b2": 18560, "W3": 18688, "b3": 35072, "w4": 35200, "b4": 35328}
@@ -113,7 +114,7 @@ def lib():
             L.bspl_eval_curves.argtypes = [C.POINTER(bspl_curves), i64, vp, vp, vp, vp]
             L.bspl_refine_curves.restype = st
             L.bspl_refine_curves.argtypes = [C.POINTER(bspl_curves), vp, C.c_int, i64, vp, vp, C.c_int32, vp, vp,
-                                             vp, vp]
+                                             vp, vp, vp, C.c_size_t, vp]
             L.bspl_eval_surfaces.restype = st
             L.bspl_eval_surfaces.argtypes = [C.POINTER(bspl_surfaces), i64, vp, vp, vp, vp]
             L.bspl_status_string.restype = C.c_char_p
@@ -487,14 +488,27 @@ def bspl_eval_curves(curves: DeviceCurves, q_curve, t, stream=None):
     return out
 
 
+REFINE_EVALS = 32
+
+
+def refine_workspace(curves: DeviceCurves, n_q: int, device="cuda"):
+    """Workspace for bspl_refine_curves to group its n_q queries by curve."""
+    return _ws(workspace_bytes(OP_REFINE_CURVES, curves.n, 0, 0, n_q), device)
+
+
 def bspl_refine_curves(curves: DeviceCurves, q_curve, q_xyz, res: "QueryResult", invert: bool = False,
-                       diag=None, max_iter: int = 0, stream=None):
+                       diag=None, max_iter: int = 0, evals=None, ws=None, stream=None):
     """Refines a curve projection / inversion result in place on the
     original curves (include/bspl.h, bspl_refine_curves); diag: the per-curve
-    diagonals (e.g. the segments' diag) for the OFF_CURVE bit of inversions."""
+    diagonals (e.g. the segments' diag) for the OFF_CURVE bit of inversions;
+    evals: optional int64 device tensor [REFINE_EVALS] accumulating the
+    evaluations made per curve degree; ws: optional workspace
+    (refine_workspace) with which the queries are processed grouped by curve."""
     rc = lib().bspl_refine_curves(C.byref(curves.c), _ptr(diag) if diag is not None else None, int(invert),
                                   q_curve.numel(), _ptr(q_curve), _ptr(q_xyz), int(max_iter), _ptr(res.param),
-                                  _ptr(res.dist), _ptr(res.status), _stream(stream))
+                                  _ptr(res.dist), _ptr(res.status), _ptr(evals) if evals is not None else None,
+                                  _ptr(ws) if ws is not None else None, ws.numel() if ws is not None else 0,
+                                  _stream(stream))
     _check(rc, "bspl_refine_curves")
     return res
 

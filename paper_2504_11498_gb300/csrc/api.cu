@@ -26,6 +26,7 @@ size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64
     case BSPL_OP_MLP_TRAIN: return n_q >= 1 && n_q <= 65536 ? train_ws_bytes(0, n_q) : 0;
     case BSPL_OP_SMLP_TRAIN: return n_q >= 1 && n_q <= 65536 ? train_ws_bytes(1, n_q) : 0;
     case BSPL_OP_QUERY_SURFACES_LEARNED: return learned_surf_ws_bytes(n_splines, n_q);
+    case BSPL_OP_REFINE_CURVES: return query_ws_bytes(n_splines, n_q);
     default: return 0;
     }
 }
@@ -87,10 +88,12 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
 
 bspl_status bspl_refine_curves(const bspl_curves* curves, const double* diag, int invert, int64_t n_q,
                                const int32_t* q_curve, const double* q_xyz, int32_t max_iter, double* t,
-                               double* dist, uint8_t* status, cudaStream_t stream)
+                               double* dist, uint8_t* status, uint64_t* evals, void* ws, size_t ws_bytes,
+                               cudaStream_t stream)
 {
     clear_stale_error();
-    return refine_curves(curves, diag, invert, n_q, q_curve, q_xyz, max_iter, t, dist, status, stream);
+    return refine_curves(curves, diag, invert, n_q, q_curve, q_xyz, max_iter, t, dist, status, evals, ws, ws_bytes,
+                         stream);
 }
 
 const char* bspl_status_string(bspl_status s)

@@ -46,6 +46,11 @@ bspl_status query_surfaces(const bspl_segments* segs, int64_t n_q, const int32_t
                            const bspl_options* opt, int invert, double* uv, double* dist, uint8_t* status,
                            void* ws, size_t ws_bytes, cudaStream_t s);
 size_t query_ws_bytes(int64_t n_splines, int64_t n_q);
+// counting sort of query indices by spline (query_curves.cu): order[] lists
+// the queries bucket by bucket (heaviest spline first when ranks are given,
+// else by spline index); *work (when asked for) receives a zeroed counter
+cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int32_t* rank, void* ws,
+                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s);
 bspl_status query_curves_learned(const bspl_segments* segs, int64_t n_q, const int32_t* q_curve,
                                  const double* q_xyz, const bspl_options* o, int invert, double* t, double* dist,
                                  uint8_t* status, void* ws, size_t ws_bytes, cudaStream_t s);
@@ -61,7 +66,8 @@ bspl_status eval_curves(const bspl_curves* c, int64_t n_q, const int32_t* qc, co
 bspl_status eval_surfaces(const bspl_surfaces* c, int64_t n_q, const int32_t* qs, const double* uv, double* xyz,
                           cudaStream_t s);
 bspl_status refine_curves(const bspl_curves* c, const double* diag, int invert, int64_t n_q, const int32_t* qc,
-                          const double* q_xyz, int max_iter, double* t, double* dist, uint8_t* status, cudaStream_t s);
+                          const double* q_xyz, int max_iter, double* t, double* dist, uint8_t* status,
+                          uint64_t* evals, void* ws, size_t ws_bytes, cudaStream_t s);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

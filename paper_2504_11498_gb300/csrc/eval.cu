@@ -218,11 +218,11 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
         }
     }
     if constexpr (NC == 4) {
-        const double W = C[3], W1 = C1[3], W2 = C2[3];
+        const double iW = 1.0 / C[3], W1 = C1[3], W2 = C2[3];
         for (int k = 0; k < 3; ++k) {
-            Cout[k] = C[k] / W;
-            C1out[k] = (C1[k] - W1 * Cout[k]) / W;
-            C2out[k] = (C2[k] - 2.0 * W1 * C1out[k] - W2 * Cout[k]) / W;
+            Cout[k] = C[k] * iW;
+            C1out[k] = (C1[k] - W1 * Cout[k]) * iW;
+            C2out[k] = (C2[k] - 2.0 * W1 * C1out[k] - W2 * Cout[k]) * iW;
         }
     } else {
         for (int k = 0; k < 3; ++k) {
@@ -248,16 +248,18 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
 // the refinement of one query on a curve of degree p <= MP; returns whether
 // it converged, with the final t and squared distance
 // (NC = 4: a rational curve with weights w, rational Newton)
+// (nev: the evaluations of C, C', C'' made)
 template <int MP, int NC>
 __device__ __noinline__ bool refine_one(const double* __restrict__ U, const double* __restrict__ P,
                                         const double* __restrict__ w, int p, int m, const double* q, int max_iter,
-                                        double& t, double& D)
+                                        double& t, double& D, int& nev)
 {
     const double a = U[p], b = U[m + 1];
     SpanCache<MP, NC> S;
     S.q = -1;
     double C[3], C1[3], C2[3];
     curve_d2<MP, NC>(U, P, w, p, m, t, S, C, C1, C2);
+    nev = 1;
     D = 0.0;
     for (int k = 0; k < 3; ++k) D += (C[k] - q[k]) * (C[k] - q[k]);
     bool conv = false;
@@ -273,6 +275,17 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
             conv = true;
             break;
         }
+        // q on the curve to the rounding of its coordinates: D is rounding
+        // noise, which no step can lower reliably
+        {
+            double mag = 0.0;
+            for (int k = 0; k < 3; ++k) mag = fmax(mag, fabs(C[k]) + fabs(q[k]));
+            const double r = 16.0 * 1.1102230246251565e-16 * mag;
+            if (D <= r * r) {
+                conv = true;
+                break;
+            }
+        }
         if (it == max_iter) break;
         const double Ep = g + h;
         double dt = Ep > 0.0 ? -E / Ep : (g > 0.0 ? -E / g : 0.0);
@@ -286,6 +299,7 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
         for (int hv = 0; hv < 12; ++hv, dt *= 0.5) {
             tn = fmin(fmax(t + dt, a), b);
             curve_d2<MP, NC>(U, P, w, p, m, tn, S, Cn, C1n, C2n);
+            ++nev;
             Dn = 0.0;
             for (int k = 0; k < 3; ++k) Dn += (Cn[k] - q[k]) * (Cn[k] - q[k]);
             if (Dn <= D) {
@@ -313,29 +327,31 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
     return conv;
 }
 
+// the refinement of query i (one thread each); evals: optional per-degree
+// evaluation counts, gathered per block in shared memory
 template <int NC>
-__global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag, int invert, int64_t n_q,
-                                const int32_t* __restrict__ qc, const double* __restrict__ q_xyz, int max_iter,
-                                double* __restrict__ t_io, double* __restrict__ d_io, uint8_t* __restrict__ st_io)
+__device__ __forceinline__ int refine_query(const bspl_curves& Cv, const double* __restrict__ diag, int invert,
+                                            int64_t i, const int32_t* __restrict__ qc,
+                                            const double* __restrict__ q_xyz, int max_iter, double* __restrict__ t_io,
+                                            double* __restrict__ d_io, uint8_t* __restrict__ st_io, int& nev)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_q) return;
+    nev = 0;
     const int c = qc[i];
-    if (c < 0 || c >= Cv.n || (st_io[i] & BSPL_Q_INVALID)) return;
+    if (c < 0 || c >= Cv.n || (st_io[i] & BSPL_Q_INVALID)) return -1;
     const int p = Cv.degree[c];
     const int m = (int)(Cv.cp_off[c + 1] - Cv.cp_off[c]) - 1;
-    if (p < 1 || p > kMaxCurveDegree || m < p) return;
+    if (p < 1 || p > kMaxCurveDegree || m < p) return -1;
     const double* U = Cv.knots + Cv.knot_off[c];
     const double* P = Cv.cps + 3 * Cv.cp_off[c];
     const double a = U[p], b = U[m + 1];
     double t = t_io[i];
-    if (!isfinite(t)) return;
+    if (!isfinite(t)) return -1;
     t = fmin(fmax(t, a), b);
     const double q[3] = { q_xyz[3 * i], q_xyz[3 * i + 1], q_xyz[3 * i + 2] };
     double D;
     const double* w = NC == 4 ? Cv.weights + Cv.cp_off[c] : nullptr;
-    const bool conv = p <= 7 ? refine_one<7, NC>(U, P, w, p, m, q, max_iter, t, D)
-                             : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D);
+    const bool conv = p <= 7 ? refine_one<7, NC>(U, P, w, p, m, q, max_iter, t, D, nev)
+                             : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D, nev);
     const double d = sqrt(D);
     uint8_t fl = st_io[i] & (uint8_t)~(BSPL_Q_CONVERGED | BSPL_Q_NONCONV | BSPL_Q_AT_END | BSPL_Q_OFF_CURVE);
     fl |= conv ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
@@ -345,6 +361,30 @@ __global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag,
     t_io[i] = t;
     d_io[i] = d;
     st_io[i] = fl;
+    return p;
+}
+
+// thread k refines query order[k] (queries grouped by curve), or query k
+template <int NC>
+__global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag, int invert, int64_t n_q,
+                                const int32_t* __restrict__ qc, const double* __restrict__ q_xyz, int max_iter,
+                                double* __restrict__ t_io, double* __restrict__ d_io, uint8_t* __restrict__ st_io,
+                                unsigned long long* __restrict__ evals, const int32_t* __restrict__ order)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int nev = 0, p = -1;
+    if (k < n_q) {
+        const int64_t i = order ? (int64_t)order[k] : k;
+        p = refine_query<NC>(Cv, diag, invert, i, qc, q_xyz, max_iter, t_io, d_io, st_io, nev);
+    }
+    if (evals == nullptr) return;  // uniform over the launch
+    __shared__ unsigned int hist[BSPL_REFINE_EVALS];
+    for (int k = threadIdx.x; k < BSPL_REFINE_EVALS; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+    if (p >= 0 && nev > 0) atomicAdd(&hist[p], (unsigned int)nev);
+    __syncthreads();
+    for (int k = threadIdx.x; k < BSPL_REFINE_EVALS; k += blockDim.x)
+        if (hist[k]) atomicAdd(&evals[k], (unsigned long long)hist[k]);
 }
 
 // clamped parameter, span and basis values of one direction of a surface
@@ -394,17 +434,25 @@ bspl_status eval_curves(const bspl_curves* c, int64_t n_q, const int32_t* qc, co
 }
 
 bspl_status refine_curves(const bspl_curves* c, const double* diag, int invert, int64_t n_q, const int32_t* qc,
-                          const double* q_xyz, int max_iter, double* t, double* dist, uint8_t* status, cudaStream_t s)
+                          const double* q_xyz, int max_iter, double* t, double* dist, uint8_t* status,
+                          uint64_t* evals, void* ws, size_t ws_bytes, cudaStream_t s)
 {
     if (!c || n_q < 0 || max_iter < 0 || max_iter > 100) return BSPL_EINVAL;
     if (n_q > 0 && (!qc || !q_xyz || !t || !dist || !status)) return BSPL_EINVAL;
     if (n_q == 0) return BSPL_OK;
+    int32_t* order = nullptr;
+    if (ws) {
+        if (n_q > 0x7fffffffLL || c->n <= 0 || ws_bytes < query_ws_bytes(c->n, n_q)) return BSPL_EINVAL;
+        if (sort_by_spline(qc, n_q, c->n, nullptr, ws, ws_bytes, &order, nullptr, s) != cudaSuccess)
+            return BSPL_ECUDA;
+    }
+    auto* ev = reinterpret_cast<unsigned long long*>(evals);
     if (c->weights)
         k_refine_curves<4><<<ceil_div(n_q, 128), 128, 0, s>>>(*c, diag, invert, n_q, qc, q_xyz,
-                                                              max_iter ? max_iter : 16, t, dist, status);
+                                                              max_iter ? max_iter : 16, t, dist, status, ev, order);
     else
         k_refine_curves<3><<<ceil_div(n_q, 128), 128, 0, s>>>(*c, diag, invert, n_q, qc, q_xyz,
-                                                              max_iter ? max_iter : 16, t, dist, status);
+                                                              max_iter ? max_iter : 16, t, dist, status, ev, order);
     return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
 }
 

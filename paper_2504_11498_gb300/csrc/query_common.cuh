@@ -35,11 +35,10 @@ struct CurveQ {
     unsigned long long* work;  // work-stealing batch counter (zeroed), or NULL: one batch per warp
 };
 
-// query_curves.cu: the mixed-precision grid kernel over P.order, and the
-// counting sort of query indices by curve
+// query_curves.cu: the mixed-precision grid kernel over P.order (the
+// counting sort of query indices by curve, sort_by_spline, is declared in
+// bspl_internal.cuh)
 void launch_mixed_curves(const CurveQ& P, int occ, cudaStream_t s);
-cudaError_t sort_by_spline(const int32_t* qc, int64_t n_q, int64_t n, const int32_t* rank, void* ws,
-                           size_t ws_bytes, int32_t** order, unsigned long long** work, cudaStream_t s);
 
 namespace {
 

@@ -51,15 +51,16 @@ def test_library_loads_and_answers_host_queries(libpath):
 
 
 def test_binding_struct_layout_matches_header(libpath):
-    """Struct sizes the binding uses equal the C compiler's."""
+    """Struct sizes and constants the binding uses equal the C compiler's."""
     import ctypes as C
 
     from paper_2504_11498_gb300 import bspl
     code = r'''
 #include <stdio.h>
 #include "bspl.h"
-int main(void){printf("%zu %zu %zu %zu\n", sizeof(bspl_curves), sizeof(bspl_surfaces),
- sizeof(bspl_segments), sizeof(bspl_options)); return 0;}
+int main(void){printf("%zu %zu %zu %zu %d %d %d\n", sizeof(bspl_curves), sizeof(bspl_surfaces),
+ sizeof(bspl_segments), sizeof(bspl_options), BSPL_OP_REFINE_CURVES, BSPL_REFINE_EVALS, BSPL_NCOUNTERS);
+ return 0;}
 '''
     import tempfile
     with tempfile.TemporaryDirectory() as d:
@@ -70,7 +71,7 @@ int main(void){printf("%zu %zu %zu %zu\n", sizeof(bspl_curves), sizeof(bspl_surf
                        check=True)
         sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     assert sizes == [C.sizeof(bspl.bspl_curves), C.sizeof(bspl.bspl_surfaces), C.sizeof(bspl.bspl_segments),
-                     C.sizeof(bspl.bspl_options)]
+                     C.sizeof(bspl.bspl_options), bspl.OP_REFINE_CURVES, bspl.REFINE_EVALS, bspl.NCOUNTERS]
 
 
 def test_product_refuses_to_run_without_library(monkeypatch, tmp_path):

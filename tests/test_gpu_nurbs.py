@@ -165,10 +165,11 @@ def test_nurbs_full_size_sampled_parity():
     qc, q = dev(qs.proj_curve, torch.int32), dev(qs.proj_xyz, torch.float64)
     buf = bspl.QueryBuffers(segs, len(qs.proj_curve), DEV, learned=True)
     o = bspl.make_options(prec=bspl.LEARNED_MIXED, mlp=mlp)
+    rws = bspl.refine_workspace(dc, len(qs.proj_curve), DEV)
 
     def step():
         r = bspl.bspl_project_curves(segs, qc, q, o, buf)
-        bspl.bspl_refine_curves(dc, qc, q, r)
+        bspl.bspl_refine_curves(dc, qc, q, r, ws=rws)
 
     step()
     torch.cuda.synchronize()
@@ -190,3 +191,25 @@ def test_nurbs_full_size_sampled_parity():
     err = np.abs(d_f[pick] - d_o) / diag[pick]
     assert err.max() <= 1e-9, (int((err > 1e-9).sum()), err.max())
     assert bspl.mlp_check() == bspl.OK
+
+
+def test_refine_grouped_by_curve_matches_caller_order():
+    """The refinement with a workspace (queries grouped by curve) gives the
+    same results, bit for bit, and the same evaluation counts as in the
+    caller's order; a workspace below its size is refused."""
+    cs, qs = small_set(n=64, n_proj=30_000, n_inv=0)
+    dc = bspl.DeviceCurves(cs, DEV)
+    segs = bspl.decompose(dc, TOL)
+    qc, q = dev(qs.proj_curve, torch.int32), dev(qs.proj_xyz, torch.float64)
+    r = bspl.bspl_project_curves(segs, qc, q, bspl.make_options(prec=bspl.MIXED))
+    a = bspl.QueryResult(r.param.clone(), r.dist.clone(), r.status.clone())
+    ea = torch.zeros(bspl.REFINE_EVALS, dtype=torch.int64, device=DEV)
+    eb = torch.zeros_like(ea)
+    bspl.bspl_refine_curves(dc, qc, q, a, evals=ea)
+    ws = bspl.refine_workspace(dc, len(qs.proj_curve), DEV)
+    bspl.bspl_refine_curves(dc, qc, q, r, evals=eb, ws=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(a.param, r.param) and torch.equal(a.dist, r.dist) and torch.equal(a.status, r.status)
+    assert torch.equal(ea, eb) and int(ea.sum()) >= len(qs.proj_curve)
+    with pytest.raises(bspl.BsplError):
+        bspl.bspl_refine_curves(dc, qc, q, r, ws=ws[:16])

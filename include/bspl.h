@@ -386,7 +386,10 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
  * or the distance stops decreasing.  At most max_iter steps (0: 16; at most
  * 100).
  *   in/out  t [n_q], dist [n_q]: the refined parameter and |C(t) - q|, never
- *           larger than the distance at the starting t;
+ *           larger than the distance at the starting t beyond the FP64
+ *           rounding of the squared distance (a full Newton step whose
+ *           change of it is within that rounding is taken and ends the
+ *           iteration);
  *   in/out  status [n_q]: queries with BSPL_Q_INVALID are skipped; otherwise
  *           CONVERGED / NONCONV and AT_END are set from the refinement and,
  *           with invert != 0 and diag != NULL (the per-curve diagonals, e.g.

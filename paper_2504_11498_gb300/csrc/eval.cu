@@ -244,7 +244,11 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
 // (the longest of the halvings that does not raise D) lowers the squared
 // distance by at most 4 units of its rounding (a flat minimum, where t is
 // ill-conditioned but D is settled), or a step moves t by at most 1e-15 of
-// the domain.  The result never has a larger distance than the start.
+// the domain, or q lies on the curve to the rounding of its coordinates.  A
+// full Newton step that changes D by no more than D's rounding is taken and
+// ends the iteration (D cannot resolve it; halving it would only spend
+// evaluations).  The result's distance never exceeds the start's by more
+// than that rounding.
 // the refinement of one query on a curve of degree p <= MP; returns whether
 // it converged, with the final t and squared distance
 // (NC = 4: a rational curve with weights w, rational Newton)
@@ -296,13 +300,21 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
         }
         bool took = false;
         double tn = t, Dn = D, Cn[3], C1n[3], C2n[3];
+        // rounding of the computed D: its own sum (8 units) and the rounding
+        // of C's coordinates (16 units of |C| + |q|) through 2 |C - q|
+        double mag = 0.0;
+        for (int k = 0; k < 3; ++k) mag = fmax(mag, fabs(C[k]) + fabs(q[k]));
+        const double noise = 8.0 * 1.1102230246251565e-16 * D + 32.0 * 1.1102230246251565e-16 * mag * sqrt(D);
         for (int hv = 0; hv < 12; ++hv, dt *= 0.5) {
             tn = fmin(fmax(t + dt, a), b);
             curve_d2<MP, NC>(U, P, w, p, m, tn, S, Cn, C1n, C2n);
             ++nev;
             Dn = 0.0;
             for (int k = 0; k < 3; ++k) Dn += (Cn[k] - q[k]) * (Cn[k] - q[k]);
-            if (Dn <= D) {
+            // a full Newton step whose change of D is within D's rounding is
+            // taken (near a minimum the step is Newton's, and D cannot tell
+            // it apart); it ends the iteration below
+            if (Dn <= D || (hv == 0 && Dn <= D + noise)) {
                 took = true;
                 break;
             }

@@ -401,13 +401,20 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
  *   out     evals: optional device array [BSPL_REFINE_EVALS], accumulated:
  *           entry p counts the evaluations of C, C', C'' on curves of
  *           degree p (profiling; NULL: not counted).
- *   ws      optional device workspace of at least
- *           bspl_workspace_bytes(BSPL_OP_REFINE_CURVES, curves->n, 0, 0, n_q)
- *           bytes: the queries are then processed grouped by curve (a warp's
- *           queries share a curve's degree and knots); NULL: in the caller's
- *           order.  The results do not depend on the order.
+ *   ws      optional device workspace of
+ *           bspl_workspace_bytes(BSPL_OP_REFINE_CURVES, curves->n,
+ *           cp_off[n], 0, n_q) bytes: the queries are then processed grouped
+ *           by curve (a warp's queries share a curve's degree and knots), and
+ *           the factors of each span's evaluation that depend on the knots
+ *           alone (reciprocals of knot differences, for degrees up to 7) are
+ *           computed once per span for the call instead of once per query;
+ *           a smaller workspace (at least the n_cp_total = 0 size) groups the
+ *           queries and keeps the factors of the curves that fit.  NULL: the
+ *           caller's order, factors per query.  The results do not depend on
+ *           either (same operations).
  * BSPL_EINVAL for NULL arrays with n_q > 0, n_q < 0, max_iter outside
- * 0..100, or a workspace given with ws_bytes below the size above. */
+ * 0..100, or a workspace given with ws_bytes below the n_cp_total = 0 size
+ * above. */
 bspl_status bspl_refine_curves(const bspl_curves* curves, const double* diag, int invert, int64_t n_q,
                                const int32_t* q_curve, const double* q_xyz, int32_t max_iter, double* t,
                                double* dist, uint8_t* status, uint64_t* evals, void* ws, size_t ws_bytes,

@@ -493,7 +493,7 @@ REFINE_EVALS = 32
 
 def refine_workspace(curves: DeviceCurves, n_q: int, device="cuda"):
     """Workspace for bspl_refine_curves to group its n_q queries by curve."""
-    return _ws(workspace_bytes(OP_REFINE_CURVES, curves.n, 0, 0, n_q), device)
+    return _ws(workspace_bytes(OP_REFINE_CURVES, curves.n, curves.n_cp_total, 0, n_q), device)
 
 
 def bspl_refine_curves(curves: DeviceCurves, q_curve, q_xyz, res: "QueryResult", invert: bool = False,

@@ -26,7 +26,7 @@ size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64
     case BSPL_OP_MLP_TRAIN: return n_q >= 1 && n_q <= 65536 ? train_ws_bytes(0, n_q) : 0;
     case BSPL_OP_SMLP_TRAIN: return n_q >= 1 && n_q <= 65536 ? train_ws_bytes(1, n_q) : 0;
     case BSPL_OP_QUERY_SURFACES_LEARNED: return learned_surf_ws_bytes(n_splines, n_q);
-    case BSPL_OP_REFINE_CURVES: return query_ws_bytes(n_splines, n_q);
+    case BSPL_OP_REFINE_CURVES: return refine_ws_bytes(n_splines, n_cp_total, n_q);
     default: return 0;
     }
 }

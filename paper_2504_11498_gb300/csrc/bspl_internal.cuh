@@ -65,6 +65,7 @@ bspl_status eval_curves(const bspl_curves* c, int64_t n_q, const int32_t* qc, co
                         cudaStream_t s);
 bspl_status eval_surfaces(const bspl_surfaces* c, int64_t n_q, const int32_t* qs, const double* uv, double* xyz,
                           cudaStream_t s);
+size_t refine_ws_bytes(int64_t n_splines, int64_t n_cp_total, int64_t n_q);
 bspl_status refine_curves(const bspl_curves* c, const double* diag, int invert, int64_t n_q, const int32_t* qc,
                           const double* q_xyz, int max_iter, double* t, double* dist, uint8_t* status,
                           uint64_t* evals, void* ws, size_t ws_bytes, cudaStream_t s);

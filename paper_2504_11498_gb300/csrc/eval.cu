@@ -101,10 +101,62 @@ template <int MP, int NC = 3>
 struct SpanCache {
     static constexpr int K = MP <= 8 ? MP : 1;
     int q;
+    const double* rcp;  // the curve's rows of the per-span factors below, or nullptr
     double inv[K * (K + 1) / 2];
+    double H[K + 1][NC];  // the span's points (homogeneous for NC = 4)
     double Q[K][NC];
     double R[K][NC];
 };
+
+// The factors of span_prepare that depend on the knots alone, one row per
+// span slot s = cp_off[c] + (q - p) of the curves of degree <= 7, shared by
+// every query of a call: [0, 28) the reciprocals 1 / (U_{q+r+1} -
+// U_{q+1-j+r}) at (j - 1) j / 2 + r, [28, 35) the factors p / (U_{q+j+1} -
+// U_{q-p+j+1}) of C' (j < p), [35, 41) the factors (p - 1) / (U_{q+j} -
+// U_{q-p+j+1}) of C'' (1 <= j < p) at 34 + j; padded to 42 doubles.
+constexpr int kRcpW = 42;
+constexpr int kRcpMaxDeg = 7;
+
+__device__ __forceinline__ double rcp_inv(const double* U, int q, int j, int r)
+{
+    const double den = U[q + r + 1] - U[q + 1 - j + r];
+    return den != 0.0 ? 1.0 / den : 0.0;
+}
+__device__ __forceinline__ double rcp_sq(const double* U, int p, int q, int j)
+{
+    return p / (U[q + j + 1] - U[q - p + j + 1]);
+}
+__device__ __forceinline__ double rcp_sr(const double* U, int p, int q, int j)
+{
+    return (p - 1) / (U[q + j] - U[q - p + j + 1]);
+}
+
+// one thread per span slot below cap (slots past the set, of degrees above
+// 7 or of empty spans are left as they are: no query reads them)
+__global__ void k_span_rcp(bspl_curves C, int64_t cap, double* __restrict__ tab)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= cap || s >= C.cp_off[C.n]) return;
+    int64_t lo = 0, hi = C.n - 1;  // the curve: largest c with cp_off[c] <= s
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (C.cp_off[mid] <= s) lo = mid;
+        else hi = mid - 1;
+    }
+    const int c = (int)lo, p = C.degree[c];
+    const int m = (int)(C.cp_off[c + 1] - C.cp_off[c]) - 1;
+    if (p < 1 || p > kRcpMaxDeg || m < p) return;
+    const int q = p + (int)(s - C.cp_off[c]);
+    const double* U = C.knots + C.knot_off[c];
+    if (q > m || !(U[q] < U[q + 1])) return;
+    double* f = tab + (int64_t)kRcpW * s;
+    for (int j = 1; j <= p; ++j)
+        for (int r = 0; r < j; ++r) f[(j - 1) * j / 2 + r] = rcp_inv(U, q, j, r);
+    for (int j = 0; j < p; ++j) {
+        f[28 + j] = rcp_sq(U, p, q, j);
+        if (j >= 1) f[34 + j] = rcp_sr(U, p, q, j);
+    }
+}
 
 // control point i of the curve: P_i, or (w_i P_i, w_i) for a rational one
 template <int NC>
@@ -114,30 +166,36 @@ __device__ __forceinline__ double hpt(const double* P, const double* w, int i, i
     else return P[3 * i + k];
 }
 
+// the span's factors from the shared rows when there are any (the same
+// values: k_span_rcp computes them with the same operations), else here
 template <int MP, int NC>
 __device__ __forceinline__ void span_prepare(const double* U, const double* P, const double* w, int p, int q,
                                              SpanCache<MP, NC>& S)
 {
     static_assert(MP <= 8, "span cache for low degrees only");
     S.q = q;
+    const double* f = S.rcp ? S.rcp + (int64_t)kRcpW * (q - p) : nullptr;
 #pragma unroll(MP <= 8 ? MP + 1 : 1)
     for (int j = 1; j <= MP; ++j) {
         if (j > p) break;
 #pragma unroll(MP <= 8 ? MP + 1 : 1)
         for (int r = 0; r < MP; ++r) {
             if (r >= j) break;
-            const double den = U[q + r + 1] - U[q + 1 - j + r];
-            S.inv[(j - 1) * j / 2 + r] = den != 0.0 ? 1.0 / den : 0.0;
+            S.inv[(j - 1) * j / 2 + r] = f ? f[(j - 1) * j / 2 + r] : rcp_inv(U, q, j, r);
         }
+    }
+#pragma unroll(MP <= 8 ? MP + 1 : 1)
+    for (int j = 0; j <= MP; ++j) {
+        if (j > p) break;
+        for (int k = 0; k < NC; ++k) S.H[j][k] = hpt<NC>(P, w, q - p + j, k);
     }
 #pragma unroll(MP <= 8 ? MP + 1 : 1)
     for (int j = 0; j < MP; ++j) {
         if (j >= p) break;
-        const double sq = p / (U[q + j + 1] - U[q - p + j + 1]);
-        for (int k = 0; k < NC; ++k)
-            S.Q[j][k] = sq * (hpt<NC>(P, w, q - p + j + 1, k) - hpt<NC>(P, w, q - p + j, k));
+        const double sq = f ? f[28 + j] : rcp_sq(U, p, q, j);
+        for (int k = 0; k < NC; ++k) S.Q[j][k] = sq * (S.H[j + 1][k] - S.H[j][k]);
         if (j >= 1) {
-            const double sr = (p - 1) / (U[q + j] - U[q - p + j + 1]);
+            const double sr = f ? f[34 + j] : rcp_sr(U, p, q, j);
             for (int k = 0; k < NC; ++k) S.R[j - 1][k] = sr * (S.Q[j][k] - S.Q[j - 1][k]);
         }
     }
@@ -197,7 +255,11 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
 #pragma unroll(MP <= 8 ? MP + 1 : 1)
     for (int j = 0; j <= MP; ++j) {
         if (j > p) break;
-        for (int k = 0; k < NC; ++k) C[k] += N[j] * hpt<NC>(P, w, q - p + j, k);
+        if constexpr (kCache) {
+            for (int k = 0; k < NC; ++k) C[k] += N[j] * S.H[j][k];
+        } else {
+            for (int k = 0; k < NC; ++k) C[k] += N[j] * hpt<NC>(P, w, q - p + j, k);
+        }
         if constexpr (kCache) {
             if (j < p)
                 for (int k = 0; k < NC; ++k) C1[k] += N1[j] * S.Q[j][k];
@@ -253,14 +315,16 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
 // it converged, with the final t and squared distance
 // (NC = 4: a rational curve with weights w, rational Newton)
 // (nev: the evaluations of C, C', C'' made)
+// (rcp: the curve's rows of the shared per-span factors, or nullptr)
 template <int MP, int NC>
 __device__ __noinline__ bool refine_one(const double* __restrict__ U, const double* __restrict__ P,
                                         const double* __restrict__ w, int p, int m, const double* q, int max_iter,
-                                        double& t, double& D, int& nev)
+                                        double& t, double& D, int& nev, const double* rcp)
 {
     const double a = U[p], b = U[m + 1];
     SpanCache<MP, NC> S;
     S.q = -1;
+    S.rcp = rcp;
     double C[3], C1[3], C2[3];
     curve_d2<MP, NC>(U, P, w, p, m, t, S, C, C1, C2);
     nev = 1;
@@ -345,7 +409,8 @@ template <int NC>
 __device__ __forceinline__ int refine_query(const bspl_curves& Cv, const double* __restrict__ diag, int invert,
                                             int64_t i, const int32_t* __restrict__ qc,
                                             const double* __restrict__ q_xyz, int max_iter, double* __restrict__ t_io,
-                                            double* __restrict__ d_io, uint8_t* __restrict__ st_io, int& nev)
+                                            double* __restrict__ d_io, uint8_t* __restrict__ st_io, int& nev,
+                                            const double* __restrict__ rcp, int64_t rcp_cap)
 {
     nev = 0;
     const int c = qc[i];
@@ -362,8 +427,10 @@ __device__ __forceinline__ int refine_query(const bspl_curves& Cv, const double*
     const double q[3] = { q_xyz[3 * i], q_xyz[3 * i + 1], q_xyz[3 * i + 2] };
     double D;
     const double* w = NC == 4 ? Cv.weights + Cv.cp_off[c] : nullptr;
-    const bool conv = p <= 7 ? refine_one<7, NC>(U, P, w, p, m, q, max_iter, t, D, nev)
-                             : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D, nev);
+    // the curve's rows of the shared factors, when every one of them is there
+    const double* rc = rcp && Cv.cp_off[c + 1] <= rcp_cap ? rcp + (int64_t)kRcpW * Cv.cp_off[c] : nullptr;
+    const bool conv = p <= kRcpMaxDeg ? refine_one<kRcpMaxDeg, NC>(U, P, w, p, m, q, max_iter, t, D, nev, rc)
+                                      : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nullptr);
     const double d = sqrt(D);
     uint8_t fl = st_io[i] & (uint8_t)~(BSPL_Q_CONVERGED | BSPL_Q_NONCONV | BSPL_Q_AT_END | BSPL_Q_OFF_CURVE);
     fl |= conv ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
@@ -381,13 +448,14 @@ template <int NC>
 __global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag, int invert, int64_t n_q,
                                 const int32_t* __restrict__ qc, const double* __restrict__ q_xyz, int max_iter,
                                 double* __restrict__ t_io, double* __restrict__ d_io, uint8_t* __restrict__ st_io,
-                                unsigned long long* __restrict__ evals, const int32_t* __restrict__ order)
+                                unsigned long long* __restrict__ evals, const int32_t* __restrict__ order,
+                                const double* __restrict__ rcp, int64_t rcp_cap)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int nev = 0, p = -1;
     if (k < n_q) {
         const int64_t i = order ? (int64_t)order[k] : k;
-        p = refine_query<NC>(Cv, diag, invert, i, qc, q_xyz, max_iter, t_io, d_io, st_io, nev);
+        p = refine_query<NC>(Cv, diag, invert, i, qc, q_xyz, max_iter, t_io, d_io, st_io, nev, rcp, rcp_cap);
     }
     if (evals == nullptr) return;  // uniform over the launch
     __shared__ unsigned int hist[BSPL_REFINE_EVALS];
@@ -445,6 +513,12 @@ bspl_status eval_curves(const bspl_curves* c, int64_t n_q, const int32_t* qc, co
     return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
 }
 
+size_t refine_ws_bytes(int64_t n_splines, int64_t n_cp_total, int64_t n_q)
+{
+    const size_t sb = (query_ws_bytes(n_splines, n_q) + 255) & ~(size_t)255;
+    return sb + sizeof(double) * kRcpW * (size_t)n_cp_total;
+}
+
 bspl_status refine_curves(const bspl_curves* c, const double* diag, int invert, int64_t n_q, const int32_t* qc,
                           const double* q_xyz, int max_iter, double* t, double* dist, uint8_t* status,
                           uint64_t* evals, void* ws, size_t ws_bytes, cudaStream_t s)
@@ -453,18 +527,31 @@ bspl_status refine_curves(const bspl_curves* c, const double* diag, int invert, 
     if (n_q > 0 && (!qc || !q_xyz || !t || !dist || !status)) return BSPL_EINVAL;
     if (n_q == 0) return BSPL_OK;
     int32_t* order = nullptr;
+    double* rcp = nullptr;
+    int64_t rcp_cap = 0;
     if (ws) {
-        if (n_q > 0x7fffffffLL || c->n <= 0 || ws_bytes < query_ws_bytes(c->n, n_q)) return BSPL_EINVAL;
-        if (sort_by_spline(qc, n_q, c->n, nullptr, ws, ws_bytes, &order, nullptr, s) != cudaSuccess)
-            return BSPL_ECUDA;
+        const size_t sb = query_ws_bytes(c->n, n_q);
+        if (n_q > 0x7fffffffLL || c->n <= 0 || ws_bytes < sb) return BSPL_EINVAL;
+        if (sort_by_spline(qc, n_q, c->n, nullptr, ws, sb, &order, nullptr, s) != cudaSuccess) return BSPL_ECUDA;
+        // the per-span factors in the rest of the workspace: as many slots
+        // as fit (curves whose slots do not all fit compute their own)
+        const size_t off = (sb + 255) & ~(size_t)255;
+        if (ws_bytes > off) {
+            rcp_cap = (int64_t)((ws_bytes - off) / (sizeof(double) * kRcpW));
+            rcp = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + off);
+            if (rcp_cap > 0) k_span_rcp<<<ceil_div(rcp_cap, 128), 128, 0, s>>>(*c, rcp_cap, rcp);
+            else rcp = nullptr;
+        }
     }
     auto* ev = reinterpret_cast<unsigned long long*>(evals);
     if (c->weights)
         k_refine_curves<4><<<ceil_div(n_q, 128), 128, 0, s>>>(*c, diag, invert, n_q, qc, q_xyz,
-                                                              max_iter ? max_iter : 16, t, dist, status, ev, order);
+                                                              max_iter ? max_iter : 16, t, dist, status, ev, order,
+                                                              rcp, rcp_cap);
     else
         k_refine_curves<3><<<ceil_div(n_q, 128), 128, 0, s>>>(*c, diag, invert, n_q, qc, q_xyz,
-                                                              max_iter ? max_iter : 16, t, dist, status, ev, order);
+                                                              max_iter ? max_iter : 16, t, dist, status, ev, order,
+                                                              rcp, rcp_cap);
     return cudaGetLastError() == cudaSuccess ? BSPL_OK : BSPL_ECUDA;
 }
 

@@ -194,9 +194,11 @@ def test_nurbs_full_size_sampled_parity():
 
 
 def test_refine_grouped_by_curve_matches_caller_order():
-    """The refinement with a workspace (queries grouped by curve) gives the
-    same results, bit for bit, and the same evaluation counts as in the
-    caller's order; a workspace below its size is refused."""
+    """The refinement with a workspace (queries grouped by curve, the
+    per-span factors computed once per call) gives the same results, bit for
+    bit, and the same evaluation counts as in the caller's order without
+    one, and so does a workspace with room for only some curves' factors; a
+    workspace below the grouping's size is refused."""
     cs, qs = small_set(n=64, n_proj=30_000, n_inv=0)
     dc = bspl.DeviceCurves(cs, DEV)
     segs = bspl.decompose(dc, TOL)
@@ -211,5 +213,11 @@ def test_refine_grouped_by_curve_matches_caller_order():
     torch.cuda.synchronize()
     assert torch.equal(a.param, r.param) and torch.equal(a.dist, r.dist) and torch.equal(a.status, r.status)
     assert torch.equal(ea, eb) and int(ea.sum()) >= len(qs.proj_curve)
+    # a workspace holding the grouping and the factors of only some curves
+    part = bspl.workspace_bytes(bspl.OP_REFINE_CURVES, dc.n, dc.n_cp_total // 3, 0, len(qs.proj_curve))
+    r2 = bspl.bspl_project_curves(segs, qc, q, bspl.make_options(prec=bspl.MIXED))
+    bspl.bspl_refine_curves(dc, qc, q, r2, ws=ws[:part])
+    torch.cuda.synchronize()
+    assert torch.equal(a.param, r2.param) and torch.equal(a.dist, r2.dist) and torch.equal(a.status, r2.status)
     with pytest.raises(bspl.BsplError):
         bspl.bspl_refine_curves(dc, qc, q, r, ws=ws[:16])

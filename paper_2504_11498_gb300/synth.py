@@ -508,3 +508,31 @@ def mlp_init(seed: int = 7) -> np.ndarray:
             theta[o:o + n] = w.reshape(-1)
         o += n
     return theta
+
+
+def nurbs_edge_set(seed: int = 7):
+    """Rational edge cases: a degree-1 curve with unequal weights (a line
+    with a non-uniform parameterisation), a quarter circle (degree 2, weights
+    1, sqrt(2)/2, 1), a cubic with a C0 joint (interior knot of multiplicity
+    3), a single degree-7 span, a cubic on the domain [-3, 5], and a quartic
+    whose weights span 50:1.  Control points ~U[0,1]^3 where not fixed."""
+    rng = np.random.default_rng(seed)
+    degs, knots, cps, ws = [], [], [], []
+
+    def add(p, U, P, w):
+        degs.append(p)
+        knots.append(np.asarray(U, np.float64))
+        cps.append(np.asarray(P, np.float64))
+        ws.append(np.asarray(w, np.float64))
+
+    add(1, [0, 0, 1, 1], rng.uniform(0, 1, (2, 3)), [1.0, 3.0])
+    add(2, [0, 0, 0, 1, 1, 1], [[1, 0, 0], [1, 1, 0], [0, 1, 0]], [1.0, np.sqrt(0.5), 1.0])
+    add(3, [0, 0, 0, 0, 0.4, 0.4, 0.4, 0.7, 1, 1, 1, 1], rng.uniform(0, 1, (8, 3)),
+        np.exp(rng.uniform(np.log(0.5), np.log(2.0), 8)))
+    add(7, uniform_clamped_knots(7, 8), rng.uniform(0, 1, (8, 3)), np.exp(rng.uniform(np.log(0.5), np.log(2.0), 8)))
+    add(3, np.concatenate([[-3.0] * 4, [-1.0, 2.0], [5.0] * 4]), rng.uniform(0, 1, (6, 3)),
+        np.exp(rng.uniform(np.log(0.5), np.log(2.0), 6)))
+    w = np.exp(rng.uniform(0.0, np.log(50.0), 10))
+    w[0], w[-1] = 1.0, 50.0
+    add(4, random_clamped_knots(rng, 4, 10), rng.uniform(0, 1, (10, 3)), w)
+    return pack_curves(degs, knots, cps, ws)

@@ -221,3 +221,42 @@ def test_refine_grouped_by_curve_matches_caller_order():
     assert torch.equal(a.param, r2.param) and torch.equal(a.dist, r2.dist) and torch.equal(a.status, r2.status)
     with pytest.raises(bspl.BsplError):
         bspl.bspl_refine_curves(dc, qc, q, r, ws=ws[:16])
+
+
+@pytest.mark.parametrize("prec", _paths())
+def test_nurbs_edge_curves(prec):
+    """Rational edge cases (synth.nurbs_edge_set: a line with unequal
+    weights, a quarter circle, a C0 joint, one degree-7 span, the domain
+    [-3, 5], weights over 50:1): decomposition bit-exact, projection and
+    inversion refined against the oracle on every query."""
+    cs = synth.nurbs_edge_set()
+    dc = bspl.DeviceCurves(cs, DEV)
+    segs = bspl.decompose(dc, TOL)
+    ref = O.decompose_curves(cs, TOL)
+    n = ref.total
+    assert np.array_equal(segs.seg_off.cpu().numpy(), ref.seg_off)
+    assert np.array_equal(segs.ctrl[:n].cpu().numpy().reshape(n, 4, 3), ref.ctrl)
+    rng = np.random.default_rng(9)
+    lo, hi = synth.cp_boxes(cs)
+    qc_h = np.repeat(np.arange(cs.n, dtype=np.int32), 500)
+    q_h = synth._box_queries(rng, lo, hi, qc_h, scale=1.5)
+    _, d_o = O.project_curves(cs, qc_h, q_h)
+    diag = O.curve_diag(cs)[qc_h]
+    mlp = bspl.Mlp(synth.mlp_init(21)) if prec == bspl.LEARNED_MIXED else None
+    o = bspl.make_options(prec=prec, mlp=mlp)
+    qc, q = dev(qc_h, torch.int32), dev(q_h, torch.float64)
+    r = bspl.bspl_project_curves(segs, qc, q, o)
+    bspl.bspl_refine_curves(dc, qc, q, r, ws=bspl.refine_workspace(dc, len(qc_h), DEV))
+    torch.cuda.synchronize()
+    err = np.abs(r.dist.cpu().numpy() - d_o) / diag
+    assert err.max() <= 1e-9, (prec, int((err > 1e-9).sum()), err.max())
+    # inversion: parameters across each curve's own domain
+    t_in = np.concatenate([np.linspace(cs.curve(c)[1][cs.curve(c)[0]], cs.curve(c)[1][len(cs.curve(c)[2])], 300)
+                           for c in range(cs.n)])
+    ic = dev(np.repeat(np.arange(cs.n, dtype=np.int32), 300), torch.int32)
+    pts = bspl.bspl_eval_curves(dc, ic, dev(t_in, torch.float64))
+    ri = bspl.bspl_invert_curves(segs, ic, pts, o)
+    bspl.bspl_refine_curves(dc, ic, pts, ri, invert=True, diag=segs.diag)
+    torch.cuda.synchronize()
+    dgi = O.curve_diag(cs)[np.repeat(np.arange(cs.n), 300)]
+    assert np.all(ri.dist.cpu().numpy() <= 1e-9 * dgi)

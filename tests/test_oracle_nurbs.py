@@ -287,3 +287,41 @@ def test_projection_brute_force_tiny():
         # the returned parameter reproduces the distance
         Ck = O.eval_curves(cs, qc[sel], t[sel])[0]
         assert np.allclose(np.linalg.norm(Ck - q[sel], axis=1), d[sel], rtol=0, atol=1e-14)
+
+
+def test_edge_set_projection_brute_force_and_quarter_circle():
+    """Rational edge cases (a line with unequal weights, a quarter circle, a
+    C0 joint, one degree-7 span, the domain [-3, 5], weights over 50:1):
+    the oracle's projection against brute force, the quarter circle against
+    its closed form, the decomposition within the tolerance."""
+    cs = synth.nurbs_edge_set()
+    rng = np.random.default_rng(8)
+    lo, hi = synth.cp_boxes(cs)
+    qc = np.repeat(np.arange(cs.n, dtype=np.int32), 40)
+    q = synth._box_queries(rng, lo, hi, qc, scale=1.5)
+    t, d = O.project_curves(cs, qc, q)
+    for c in range(cs.n):
+        p, U, P = cs.curve(c)
+        tt = np.linspace(U[p], U[len(P)], 200_001)
+        S = O.eval_curves(cs, np.full(len(tt), c, np.int32), tt)[0]
+        for k in np.where(qc == c)[0]:
+            brute = np.sqrt(((S - q[k]) ** 2).sum(1)).min()
+            assert d[k] <= brute + 1e-15 and brute - d[k] <= 1e-7, (c, k, brute, d[k])
+    # quarter circle of radius 1 about the origin in z = 0
+    k = np.where(qc == 1)[0]
+    v = q[k]
+    rho = np.linalg.norm(v[:, :2], axis=1)
+    ang = np.arctan2(v[:, 1], v[:, 0])
+    on_arc = (ang >= 0) & (ang <= np.pi / 2)
+    exact = np.where(on_arc, np.sqrt(v[:, 2] ** 2 + (rho - 1) ** 2),
+                     np.minimum(np.linalg.norm(v - [1, 0, 0], axis=1), np.linalg.norm(v - [0, 1, 0], axis=1)))
+    assert np.abs(d[k] - exact).max() <= 1e-13
+    dec = O.decompose_curves(cs, 1e-8)
+    assert dec.status == 0
+    u = np.linspace(0.0, 1.0, 33)
+    diag = O.curve_diag(cs)
+    for c in range(cs.n):
+        for s in range(dec.seg_off[c], dec.seg_off[c + 1]):
+            t0, t1 = dec.prange[s]
+            C = O.eval_curves(cs, np.full(len(u), c, np.int32), t0 + u * (t1 - t0))[0]
+            assert np.linalg.norm(C - cubic(dec.ctrl[s], u), axis=1).max() <= 1e-8 * diag[c] * (1 + 1e-9)

@@ -814,13 +814,18 @@ def run_paper_suite(args, rank, world, local):
 
 def refine_flops(evals, rational=True):
     """Algorithmic FP64 flops of the refinement from its evaluation counts
-    per degree p (an FMA counts 2): the triangular basis recursion
-    2p^2 + 4p, the sums of C, C', C'' over the span's homogeneous points
-    2 * 4 * (3p) (3 coordinates for a non-rational curve), the quotient rule
-    27, the squared distance and the Newton quantities 30 per evaluation."""
+    per degree p (an FMA counts 2): entries 0..31 evaluate C, C', C'' (the
+    triangular basis recursion 2p^2 + 4p, the sums over the span's
+    homogeneous points 2 * 4 * (3p) (3 coordinates for a non-rational
+    curve), the quotient rule 27), entries 32..63 C and C' alone (the sums
+    2 * 4 * (2p + 1), the quotient rule 14); the squared distance and the
+    Newton quantities 30 per evaluation."""
     nc = 4 if rational else 3
-    return float(sum(int(n) * (2 * p * p + 4 * p + 6 * nc * p + (27 if rational else 0) + 30)
-                     for p, n in enumerate(evals)))
+    full = sum(int(n) * (2 * p * p + 4 * p + 6 * nc * p + (27 if rational else 0) + 30)
+               for p, n in enumerate(evals[:32]))
+    part = sum(int(n) * (2 * p * p + 4 * p + 2 * nc * (2 * p + 1) + (14 if rational else 0) + 30)
+               for p, n in enumerate(evals[32:64]))
+    return float(full + part)
 
 
 def run_nurbs(args, rank, world, local):
@@ -994,8 +999,9 @@ def run_nurbs(args, rank, world, local):
            "mixed_grid": {"value": total_q / (t_m * 1e-3), "ms_per_step": t_m},
            "plain_fp64": {"value": total_q / (t_p * 1e-3), "ms_per_step": t_p},
            "speedup_learned_vs_plain": t_p / t_l,
-           "refine": {"ms_per_step": t_r, "evaluations_by_degree": {str(p): int(n) for p, n in enumerate(ev_counts)
-                                                                     if n}},
+           "refine": {"ms_per_step": t_r,
+                      "evaluations_by_degree": {str(p): int(n) for p, n in enumerate(ev_counts[:32]) if n},
+                      "trial_evaluations_by_degree": {str(p): int(n) for p, n in enumerate(ev_counts[32:64]) if n}},
            "accuracy": {"learned_vs_plain_fp64_refined": {"max_rel_dist_diff": worst, "queries_over_1e-9": over},
                         "inversions_over_1e-9": off_curve},
            "e2e": {"value": total_q / (t_e * 1e-3), "unit": "pts/s",

@@ -125,7 +125,11 @@ typedef struct {
                                 its own parameters (s, t) in [0,1]^2, [61] edge flags
                                 (bit 0: s=0, 1: s=1, 2: t=0, 3: t=1 set where the
                                 surface is C1 across that edge), [62..65] bounds of
-                                |S_sss|, |S_sst|, |S_stt|, |S_ttt|, [66..71] pad */
+                                |S_sss|, |S_sst|, |S_stt|, |S_ttt|, [66..71] the sums
+                                over the non-constant terms s^i t^j of patch_net32 of
+                                |coefficient| x 1, i, j, i(i-1), ij, j(j-1) (summed over
+                                xyz, rounded up): the norms that bound the rounding of
+                                the FP32 search's Horner evaluation */
 #define BSPL_GREC64 12       /* group FP64: lo[3] hi[3] ref[3] pad[3] */
 #define BSPL_GREC32 12       /* group FP32: same, box rounded outward */
 
@@ -400,7 +404,8 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
  * tolerance of it.  Degrees 1..31 (others are left unchanged).
  *   out     evals: optional device array [BSPL_REFINE_EVALS], accumulated:
  *           entry p counts the evaluations of C, C', C'' on curves of
- *           degree p (profiling; NULL: not counted).
+ *           degree p, entry 32 + p those of C and C' alone (the trial points
+ *           of the steps) (profiling; NULL: not counted).
  *   ws      optional device workspace of
  *           bspl_workspace_bytes(BSPL_OP_REFINE_CURVES, curves->n,
  *           cp_off[n], 0, n_q) bytes: the queries are then processed grouped
@@ -420,7 +425,7 @@ bspl_status bspl_refine_curves(const bspl_curves* curves, const double* diag, in
                                double* dist, uint8_t* status, uint64_t* evals, void* ws, size_t ws_bytes,
                                cudaStream_t stream);
 
-#define BSPL_REFINE_EVALS 32
+#define BSPL_REFINE_EVALS 64
 
 /* Human-readable name of a status code (static string). */
 const char* bspl_status_string(bspl_status s);

@@ -488,7 +488,7 @@ def bspl_eval_curves(curves: DeviceCurves, q_curve, t, stream=None):
     return out
 
 
-REFINE_EVALS = 32
+REFINE_EVALS = 64
 
 
 def refine_workspace(curves: DeviceCurves, n_q: int, device="cuda"):

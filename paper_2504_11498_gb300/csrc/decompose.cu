@@ -783,6 +783,17 @@ __host__ __device__ void surf_halve_keep(int pu, int pv, double* Q, int dir, int
     }
 }
 
+// the float nearest above x (x itself when representable)
+__host__ __device__ inline float round_up_f32(double x)
+{
+#ifdef __CUDA_ARCH__
+    return __double2float_ru(x);
+#else
+    const float f = (float)x;
+    return (double)f < x ? nextafterf(f, INFINITY) : f;
+#endif
+}
+
 // Bernstein -> power coefficients of a degree-n piece in place (stride s doubles)
 __host__ __device__ void bern_to_power(int n, double* Q, int s)
 {
@@ -1007,10 +1018,27 @@ __host__ __device__ int64_t walk_span_surface(int pu, int pv, const double* U, i
                     for (int a = 0; a <= pu; ++a) bern_to_power(pv, W + 3 * kSN * a, 3);
                     float* pn = out.patch_net32 + (int64_t)BSPL_SPAN_NET * o;
                     for (int i = 0; i < kSN * kSN * 3; ++i) pn[i] = (float)W[i];
+                    // the weighted L1 norms of those FP32 coefficients that
+                    // bound the rounding of their Horner evaluation (weights
+                    // 1, i, j, i(i-1), ij, j(j-1) of the term s^i t^j),
+                    // without the constant term (the query's), rounded up
+                    double L[6] = { 0.0, 0.0, 0.0, 0.0, 0.0, 0.0 };
+                    for (int a = 0; a <= pu; ++a)
+                        for (int b = 0; b <= pv; ++b) {
+                            if ((a | b) == 0) continue;
+                            double x = 0.0;
+                            for (int c = 0; c < 3; ++c) x += fabs((double)pn[(a * kSN + b) * 3 + c]);
+                            L[0] += x;
+                            L[1] += a * x;
+                            L[2] += b * x;
+                            L[3] += a * (a - 1) * x;
+                            L[4] += a * b * x;
+                            L[5] += b * (b - 1) * x;
+                        }
+                    for (int k = 0; k < 6; ++k) rf[66 + k] = round_up_f32(L[k]);
                 }
                 patch_bounds(pu, pv, Q, rf + 56);
                 rf[61] = (float)patch_edge_flags(pu, pv, U, nu, qu, V, nv, qv, pb);
-                for (int k = 66; k < BSPL_SREC32; ++k) rf[k] = 0.f;
             }
             ++count;
             while (L > 0 && (bits & 1)) {

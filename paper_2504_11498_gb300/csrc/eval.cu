@@ -207,14 +207,23 @@ __device__ __forceinline__ void span_prepare(const double* U, const double* P, c
 // points P, Q and R.  NC = 4: the same on the homogeneous points gives
 // A, A', A'' and W, W', W'', and then C = A/W, C' = (A' - W'C)/W,
 // C'' = (A'' - 2W'C' - W''C)/W.
-template <int MP, int NC = 3>
+// D2 = false: C and C' only (C2out untouched).  t inside the cached span
+// (the usual case after the first evaluation) skips the span search.
+template <int MP, int NC = 3, bool D2 = true>
 __device__ __forceinline__ void curve_d2(const double* U, const double* P, const double* w, int p, int m, double t,
                                          SpanCache<MP, NC>& S, double* Cout, double* C1out, double* C2out)
 {
     constexpr bool kCache = MP <= 8;
-    const int q = span_of(U, p, m, t);
+    int q;
     if constexpr (kCache) {
-        if (q != S.q) span_prepare<MP, NC>(U, P, w, p, q, S);
+        if (S.q >= 0 && U[S.q] <= t && t < U[S.q + 1]) {
+            q = S.q;
+        } else {
+            q = span_of(U, p, m, t);
+            if (q != S.q) span_prepare<MP, NC>(U, P, w, p, q, S);
+        }
+    } else {
+        q = span_of(U, p, m, t);
     }
     double N[MP + 1], N1[MP + 1], N2[MP + 1], left[MP + 1], right[MP + 1];
     N[0] = 1.0;
@@ -222,7 +231,7 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
     for (int j = 1; j <= MP; ++j) {
         if (j > p) break;
         // N holds degree j - 1 here
-        if (j - 1 == p - 2)
+        if (D2 && j - 1 == p - 2)
 #pragma unroll(MP <= 8 ? MP + 1 : 1)
             for (int r = 0; r < MP; ++r)
                 if (r < j) N2[r] = N[r];
@@ -263,7 +272,7 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
         if constexpr (kCache) {
             if (j < p)
                 for (int k = 0; k < NC; ++k) C1[k] += N1[j] * S.Q[j][k];
-            if (j + 1 < p)
+            if (D2 && j + 1 < p)
                 for (int k = 0; k < NC; ++k) C2[k] += N2[j] * S.R[j][k];
         } else if (j < p) {
             const double sq = p / (U[q + j + 1] - U[q - p + j + 1]);
@@ -272,7 +281,7 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
                 Qj[k] = sq * (hpt<NC>(P, w, q - p + j + 1, k) - hpt<NC>(P, w, q - p + j, k));
                 C1[k] += N1[j] * Qj[k];
             }
-            if (j >= 1) {
+            if (D2 && j >= 1) {
                 const double sr = (p - 1) / (U[q + j] - U[q - p + j + 1]);
                 for (int k = 0; k < NC; ++k) C2[k] += N2[j - 1] * sr * (Qj[k] - Qp[k]);
             }
@@ -284,13 +293,13 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
         for (int k = 0; k < 3; ++k) {
             Cout[k] = C[k] * iW;
             C1out[k] = (C1[k] - W1 * Cout[k]) * iW;
-            C2out[k] = (C2[k] - 2.0 * W1 * C1out[k] - W2 * Cout[k]) * iW;
+            if constexpr (D2) C2out[k] = (C2[k] - 2.0 * W1 * C1out[k] - W2 * Cout[k]) * iW;
         }
     } else {
         for (int k = 0; k < 3; ++k) {
             Cout[k] = C[k];
             C1out[k] = C1[k];
-            C2out[k] = C2[k];
+            if constexpr (D2) C2out[k] = C2[k];
         }
     }
 }
@@ -314,12 +323,13 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
 // the refinement of one query on a curve of degree p <= MP; returns whether
 // it converged, with the final t and squared distance
 // (NC = 4: a rational curve with weights w, rational Newton)
-// (nev: the evaluations of C, C', C'' made)
+// (nev: the evaluations of C, C', C'' made; nev1: those of C and C' alone,
+// the trial points, whose C'' is computed only when another step follows)
 // (rcp: the curve's rows of the shared per-span factors, or nullptr)
 template <int MP, int NC>
 __device__ __noinline__ bool refine_one(const double* __restrict__ U, const double* __restrict__ P,
                                         const double* __restrict__ w, int p, int m, const double* q, int max_iter,
-                                        double& t, double& D, int& nev, const double* rcp)
+                                        double& t, double& D, int& nev, int& nev1, const double* rcp)
 {
     const double a = U[p], b = U[m + 1];
     SpanCache<MP, NC> S;
@@ -328,15 +338,16 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
     double C[3], C1[3], C2[3];
     curve_d2<MP, NC>(U, P, w, p, m, t, S, C, C1, C2);
     nev = 1;
+    nev1 = 0;
+    bool have2 = true;  // C2 belongs to the current t
     D = 0.0;
     for (int k = 0; k < 3; ++k) D += (C[k] - q[k]) * (C[k] - q[k]);
     bool conv = false;
     for (int it = 0; it <= max_iter; ++it) {
-        double E = 0.0, g = 0.0, h = 0.0, sc = 0.0;
+        double E = 0.0, g = 0.0, sc = 0.0;
         for (int k = 0; k < 3; ++k) {
             E += (C[k] - q[k]) * C1[k];
             g += C1[k] * C1[k];
-            h += (C[k] - q[k]) * C2[k];
             sc += fabs(C1[k]) * (fabs(C[k] - q[k]) + fabs(C[k]) + fabs(q[k]));
         }
         if ((t <= a && E >= 0.0) || (t >= b && E <= 0.0) || fabs(E) <= 64.0 * 1.1102230246251565e-16 * sc) {
@@ -355,6 +366,13 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
             }
         }
         if (it == max_iter) break;
+        if (!have2) {  // another step: C'' at t (C and C' come out the same)
+            curve_d2<MP, NC>(U, P, w, p, m, t, S, C, C1, C2);
+            ++nev;
+            have2 = true;
+        }
+        double h = 0.0;
+        for (int k = 0; k < 3; ++k) h += (C[k] - q[k]) * C2[k];
         const double Ep = g + h;
         double dt = Ep > 0.0 ? -E / Ep : (g > 0.0 ? -E / g : 0.0);
         // a step below the resolution of t: converged
@@ -363,24 +381,31 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
             break;
         }
         bool took = false;
-        double tn = t, Dn = D, Cn[3], C1n[3], C2n[3];
-        // rounding of the computed D: its own sum (8 units) and the rounding
-        // of C's coordinates (16 units of |C| + |q|) through 2 |C - q|
-        double mag = 0.0;
-        for (int k = 0; k < 3; ++k) mag = fmax(mag, fabs(C[k]) + fabs(q[k]));
-        const double noise = 8.0 * 1.1102230246251565e-16 * D + 32.0 * 1.1102230246251565e-16 * mag * sqrt(D);
+        double tn = t, Dn = D, Cn[3], C1n[3];
         for (int hv = 0; hv < 12; ++hv, dt *= 0.5) {
             tn = fmin(fmax(t + dt, a), b);
-            curve_d2<MP, NC>(U, P, w, p, m, tn, S, Cn, C1n, C2n);
-            ++nev;
+            curve_d2<MP, NC, false>(U, P, w, p, m, tn, S, Cn, C1n, nullptr);
+            ++nev1;
             Dn = 0.0;
             for (int k = 0; k < 3; ++k) Dn += (Cn[k] - q[k]) * (Cn[k] - q[k]);
-            // a full Newton step whose change of D is within D's rounding is
-            // taken (near a minimum the step is Newton's, and D cannot tell
-            // it apart); it ends the iteration below
-            if (Dn <= D || (hv == 0 && Dn <= D + noise)) {
+            if (Dn <= D) {
                 took = true;
                 break;
+            }
+            // a full Newton step whose change of D is within D's rounding
+            // (its own sum, 8 units, and the rounding of C's coordinates, 16
+            // units of |C| + |q|, through 2 |C - q|) is taken: near a minimum
+            // the step is Newton's and D cannot tell it apart; it ends the
+            // iteration below
+            if (hv == 0) {
+                double mag = 0.0;
+                for (int k = 0; k < 3; ++k) mag = fmax(mag, fabs(C[k]) + fabs(q[k]));
+                const double noise =
+                    8.0 * 1.1102230246251565e-16 * D + 32.0 * 1.1102230246251565e-16 * mag * sqrt(D);
+                if (Dn <= D + noise) {
+                    took = true;
+                    break;
+                }
             }
         }
         if (!took) {  // no step decreases the distance: t is a minimum to rounding
@@ -393,8 +418,8 @@ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const doub
         for (int k = 0; k < 3; ++k) {
             C[k] = Cn[k];
             C1[k] = C1n[k];
-            C2[k] = C2n[k];
         }
+        have2 = false;
         if (mv <= 1e-15 * (b - a) || drop <= 4.0 * 1.1102230246251565e-16 * D) {
             conv = true;
             break;
@@ -410,9 +435,10 @@ __device__ __forceinline__ int refine_query(const bspl_curves& Cv, const double*
                                             int64_t i, const int32_t* __restrict__ qc,
                                             const double* __restrict__ q_xyz, int max_iter, double* __restrict__ t_io,
                                             double* __restrict__ d_io, uint8_t* __restrict__ st_io, int& nev,
-                                            const double* __restrict__ rcp, int64_t rcp_cap)
+                                            int& nev1, const double* __restrict__ rcp, int64_t rcp_cap)
 {
     nev = 0;
+    nev1 = 0;
     const int c = qc[i];
     if (c < 0 || c >= Cv.n || (st_io[i] & BSPL_Q_INVALID)) return -1;
     const int p = Cv.degree[c];
@@ -429,8 +455,9 @@ __device__ __forceinline__ int refine_query(const bspl_curves& Cv, const double*
     const double* w = NC == 4 ? Cv.weights + Cv.cp_off[c] : nullptr;
     // the curve's rows of the shared factors, when every one of them is there
     const double* rc = rcp && Cv.cp_off[c + 1] <= rcp_cap ? rcp + (int64_t)kRcpW * Cv.cp_off[c] : nullptr;
-    const bool conv = p <= kRcpMaxDeg ? refine_one<kRcpMaxDeg, NC>(U, P, w, p, m, q, max_iter, t, D, nev, rc)
-                                      : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nullptr);
+    const bool conv = p <= kRcpMaxDeg
+                          ? refine_one<kRcpMaxDeg, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, rc)
+                          : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, nullptr);
     const double d = sqrt(D);
     uint8_t fl = st_io[i] & (uint8_t)~(BSPL_Q_CONVERGED | BSPL_Q_NONCONV | BSPL_Q_AT_END | BSPL_Q_OFF_CURVE);
     fl |= conv ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;
@@ -452,16 +479,17 @@ __global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag,
                                 const double* __restrict__ rcp, int64_t rcp_cap)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int nev = 0, p = -1;
+    int nev = 0, nev1 = 0, p = -1;
     if (k < n_q) {
         const int64_t i = order ? (int64_t)order[k] : k;
-        p = refine_query<NC>(Cv, diag, invert, i, qc, q_xyz, max_iter, t_io, d_io, st_io, nev, rcp, rcp_cap);
+        p = refine_query<NC>(Cv, diag, invert, i, qc, q_xyz, max_iter, t_io, d_io, st_io, nev, nev1, rcp, rcp_cap);
     }
     if (evals == nullptr) return;  // uniform over the launch
     __shared__ unsigned int hist[BSPL_REFINE_EVALS];
     for (int k = threadIdx.x; k < BSPL_REFINE_EVALS; k += blockDim.x) hist[k] = 0;
     __syncthreads();
     if (p >= 0 && nev > 0) atomicAdd(&hist[p], (unsigned int)nev);
+    if (p >= 0 && nev1 > 0) atomicAdd(&hist[32 + p], (unsigned int)nev1);
     __syncthreads();
     for (int k = threadIdx.x; k < BSPL_REFINE_EVALS; k += blockDim.x)
         if (hist[k]) atomicAdd(&evals[k], (unsigned long long)hist[k]);

@@ -709,6 +709,19 @@ __device__ __forceinline__ void l1_add(R* L, int i, int j, R x)
     L[5] += R(j * (j - 1)) * x;
 }
 
+// mixed precision (the patch's own FP32 power basis): the norms of the
+// non-constant terms stored in the patch's record by the decomposition,
+// plus the constant term |off| of this query (the FP64 path sums the span
+// pair's net on the fly)
+template <class R>
+__device__ __forceinline__ void patch_l1(const SurfQ& P, int pch, const CellCtx<R>& C, R* L)
+{
+    const float* r32 = P.rec32 + (int64_t)BSPL_SREC32 * pch;
+    L[0] = (R)r32[66] + (fabs(C.off[0]) + fabs(C.off[1]) + fabs(C.off[2]));
+#pragma unroll
+    for (int k = 1; k < 6; ++k) L[k] = (R)r32[66 + k];
+}
+
 struct CellRes {
     bool live, convex;
 };
@@ -872,15 +885,19 @@ __device__ __noinline__ void certify_patch(const SurfQ& P, WarpSmem<R>& W, int s
     }
     C.a = W.net;
     R L[6] = { 0, 0, 0, 0, 0, 0 };
-    const int ncoef = (C.du + 1) * (C.dv + 1) * 3;
-    for (int k = lane; k < ncoef; k += 32) {
-        const int i = k / ((C.dv + 1) * 3), r = k - i * (C.dv + 1) * 3, j = r / 3, c = r - 3 * j;
-        l1_add(L, i, j, fabs((i | j) ? C.a[(i * kSN + j) * 3 + c] : C.off[c]));
+    if (MIXED) {
+        patch_l1(P, pch, C, L);
+    } else {
+        const int ncoef = (C.du + 1) * (C.dv + 1) * 3;
+        for (int k = lane; k < ncoef; k += 32) {
+            const int i = k / ((C.dv + 1) * 3), r = k - i * (C.dv + 1) * 3, j = r / 3, c = r - 3 * j;
+            l1_add(L, i, j, fabs((i | j) ? C.a[(i * kSN + j) * 3 + c] : C.off[c]));
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) L[k] += __shfl_xor_sync(kFull, L[k], o);
     }
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) L[k] += __shfl_xor_sync(kFull, L[k], o);
     cell_ctx_errors(C, L);
     const int maxdepth = P.cert_depth;
 
@@ -967,10 +984,14 @@ __device__ __noinline__ void certify_slots(const SurfQ& P, WarpSmem<R>& W, int n
                     C.a = MIXED ? (const R*)(P.patch_net32 + (int64_t)BSPL_SPAN_NET * pch)
                                 : span_coef<R>(P, P.patch_span[pch]);
                     R L[6] = { 0, 0, 0, 0, 0, 0 };
-                    for (int i = 0; i <= C.du; ++i)
-                        for (int j = 0; j <= C.dv; ++j)
-                            for (int k = 0; k < 3; ++k)
-                                l1_add(L, i, j, fabs((i | j) ? C.a[(i * kSN + j) * 3 + k] : C.off[k]));
+                    if (MIXED) {
+                        patch_l1(P, pch, C, L);
+                    } else {
+                        for (int i = 0; i <= C.du; ++i)
+                            for (int j = 0; j <= C.dv; ++j)
+                                for (int k = 0; k < 3; ++k)
+                                    l1_add(L, i, j, fabs((i | j) ? C.a[(i * kSN + j) * 3 + k] : C.off[k]));
+                    }
                     cell_ctx_errors(C, L);
                     r = cell_test<R>(C, 0.f, 1.f, 0.f, 1.f, ub, Dub);
                     if (r.live && r.convex &&

@@ -341,8 +341,33 @@ __host__ __device__ void rhermite(int p, const double* H, double* R, const RedCo
 //   (W R)_k = sum_j [C(p, j) C(3, k - j) / C(p + 3, k)] W_j R_{k-j};
 // the largest coefficient norm bounds |A - W R| (convex partition of unity)
 // and W >= min_j W_j > 0.
+// the coefficients rbound2 uses, which depend on the degree alone: computed
+// once per span (the same operations as computing them at every node)
 template <int MP>
-__host__ __device__ double rbound2(int p, const double* H, const double* R)
+struct RBoundCoef {
+    double ea[3][MP + 3], eb[3][MP + 3];  // elevation n -> n + 1, n = p, p + 1, p + 2
+    double pc[MP + 4][4];                 // C(p, j) C(3, k - j) / C(p + 3, k), j = k - 3 + jj
+};
+
+template <int MP>
+__host__ __device__ void rbound_coef(int p, RBoundCoef<MP>& rc)
+{
+    for (int d = 0; d < 3; ++d) {
+        const int n = p + d;
+        for (int i = 1; i <= n; ++i) {
+            rc.ea[d][i] = fdiv((double)i, (double)(n + 1));
+            rc.eb[d][i] = fdiv((double)(n + 1 - i), (double)(n + 1));
+        }
+    }
+    for (int k = 0; k <= p + 3; ++k)
+        for (int jj = 0; jj < 4; ++jj) {
+            const int j = k - 3 + jj;
+            rc.pc[k][jj] = (j >= 0 && j <= p) ? fdiv(fmul(binom_d(p, j), binom_d(3, k - j)), binom_d(p + 3, k)) : 0.0;
+        }
+}
+
+template <int MP>
+__host__ __device__ double rbound2(int p, const double* H, const double* R, const RBoundCoef<MP>& rc)
 {
     double e[(MP + 4) * 4], x[(MP + 4) * 4];
     for (int i = 0; i < 4 * (p + 1); ++i) e[i] = H[i];
@@ -352,7 +377,7 @@ __host__ __device__ double rbound2(int p, const double* H, const double* R)
             x[4 * (n + 1) + c] = e[4 * n + c];
         }
         for (int i = 1; i <= n; ++i) {
-            const double a = fdiv((double)i, (double)(n + 1)), b = fdiv((double)(n + 1 - i), (double)(n + 1));
+            const double a = rc.ea[n - p][i], b = rc.eb[n - p][i];
             for (int c = 0; c < 4; ++c) x[4 * i + c] = fadd(fmul(a, e[4 * (i - 1) + c]), fmul(b, e[4 * i + c]));
         }
         for (int i = 0; i < 4 * (n + 2); ++i) e[i] = x[i];
@@ -365,7 +390,7 @@ __host__ __device__ double rbound2(int p, const double* H, const double* R)
         double sx = 0.0, sy = 0.0, sz = 0.0;
         const int jlo = k - 3 > 0 ? k - 3 : 0, jhi = k < p ? k : p;
         for (int j = jlo; j <= jhi; ++j) {
-            const double cw = fmul(fdiv(fmul(binom_d(p, j), binom_d(3, k - j)), binom_d(p + 3, k)), H[4 * j + 3]);
+            const double cw = fmul(rc.pc[k][j - (k - 3)], H[4 * j + 3]);
             const double* r = R + 3 * (k - j);
             sx = fadd(sx, fmul(cw, r[0]));
             sy = fadd(sy, fmul(cw, r[1]));
@@ -573,6 +598,8 @@ __host__ __device__ int64_t walk_span_rcurve(int p, const double* __restrict__ U
     double stk[kStack][W], H[W];
     const int np4 = 4 * (p + 1);
     span_bezier<MP, 4>(p, U, q, Pl, 1, stk[0], wl);
+    RBoundCoef<MP> rc;
+    rbound_coef<MP>(p, rc);
     int L = 0;
     int64_t k = 0, count = 0;
     for (;;) {
@@ -588,7 +615,7 @@ __host__ __device__ int64_t walk_span_rcurve(int p, const double* __restrict__ U
         }
         double R[12];
         rhermite<MP>(p, H, R, cf);
-        bool accept = rbound2<MP>(p, H, R) <= thr2;
+        bool accept = rbound2<MP>(p, H, R, rc) <= thr2;
         if (!accept && (L >= kDepthCap || count >= kLeafCap)) {
             accept = true;
             set_flag(err, 2);

@@ -42,8 +42,8 @@ extern "C" bspl_status bspl_project_curves_noalloc(const bspl_segments* segs, in
     if (!segs || n_q < 0) return BSPL_EINVAL;
     if (n_q > BSPL_NOALLOC_MAX_QUERIES || segs->n > BSPL_NOALLOC_MAX_SPLINES) return BSPL_ENOSPACE;
     if (bspl::query_ws_bytes(segs->n, n_q) > kScratchBytes) return BSPL_ENOSPACE;
-    // the learned precision adds its candidate-pair buffer (about 1 KB per
-    // query), so it fits far fewer queries into the same array
+    // the learned precision adds its culling-candidate and pair buffers
+    // (about 1.4 KB per query), so it fits far fewer queries into the array
     if (opt && (opt->prec == BSPL_LEARNED_MIXED || opt->prec == BSPL_CLIP_MIXED) &&
         bspl::learned_ws_bytes(segs->n, n_q) > kScratchBytes)
         return BSPL_ENOSPACE;

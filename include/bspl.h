@@ -19,8 +19,11 @@
  *   - every call is asynchronous on the given stream, except bspl_decompose,
  *     which synchronises that stream (after validating the splines, after
  *     counting the segments, and around computing spline_rank);
+ *   - a workspace (ws) must start on a 256-byte boundary, as cudaMalloc
+ *     returns (the library carves it at 256-byte offsets);
  *   - argument errors that the host can see (NULL pointers, negative sizes,
- *     workspace too small) return BSPL_EINVAL before anything is launched;
+ *     workspace too small or misaligned) return BSPL_EINVAL before anything
+ *     is launched;
  *     per-query data problems (spline index out of range, non-finite point)
  *     set BSPL_Q_INVALID in that query's status byte; nothing traps;
  *   - CUDA launch failures return BSPL_ECUDA.

@@ -34,6 +34,7 @@ size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64
 bspl_status bspl_decompose(int is_surface, const void* splines, double tol_rel, bspl_segments* out,
                            int64_t* n_seg_total, void* ws, size_t ws_bytes, cudaStream_t stream)
 {
+    if (ws_misaligned(ws)) return BSPL_EINVAL;
     clear_stale_error();
     if (is_surface) return decompose_surfaces((const bspl_surfaces*)splines, tol_rel, out, n_seg_total, ws, ws_bytes,
                                               stream);
@@ -44,6 +45,7 @@ bspl_status bspl_project_curves(const bspl_segments* segs, int64_t n_q, const in
                                 const bspl_options* opt, double* t, double* dist, uint8_t* status, void* ws,
                                 size_t ws_bytes, cudaStream_t stream)
 {
+    if (ws_misaligned(ws)) return BSPL_EINVAL;
     clear_stale_error();
     return query_curves(segs, n_q, q_curve, q_xyz, opt, 0, t, dist, status, ws, ws_bytes, stream);
 }
@@ -52,6 +54,7 @@ bspl_status bspl_invert_curves(const bspl_segments* segs, int64_t n_q, const int
                                const bspl_options* opt, double* t, double* dist, uint8_t* status, void* ws,
                                size_t ws_bytes, cudaStream_t stream)
 {
+    if (ws_misaligned(ws)) return BSPL_EINVAL;
     clear_stale_error();
     return query_curves(segs, n_q, q_curve, q_xyz, opt, 1, t, dist, status, ws, ws_bytes, stream);
 }
@@ -60,6 +63,7 @@ bspl_status bspl_project_surfaces(const bspl_segments* segs, int64_t n_q, const 
                                   const bspl_options* opt, double* uv, double* dist, uint8_t* status, void* ws,
                                   size_t ws_bytes, cudaStream_t stream)
 {
+    if (ws_misaligned(ws)) return BSPL_EINVAL;
     clear_stale_error();
     return query_surfaces(segs, n_q, q_surf, q_xyz, opt, 0, uv, dist, status, ws, ws_bytes, stream);
 }
@@ -68,6 +72,7 @@ bspl_status bspl_invert_surfaces(const bspl_segments* segs, int64_t n_q, const i
                                  const bspl_options* opt, double* uv, double* dist, uint8_t* status, void* ws,
                                  size_t ws_bytes, cudaStream_t stream)
 {
+    if (ws_misaligned(ws)) return BSPL_EINVAL;
     clear_stale_error();
     return query_surfaces(segs, n_q, q_surf, q_xyz, opt, 1, uv, dist, status, ws, ws_bytes, stream);
 }
@@ -91,6 +96,7 @@ bspl_status bspl_refine_curves(const bspl_curves* curves, const double* diag, in
                                double* dist, uint8_t* status, uint64_t* evals, void* ws, size_t ws_bytes,
                                cudaStream_t stream)
 {
+    if (ws_misaligned(ws)) return BSPL_EINVAL;
     clear_stale_error();
     return refine_curves(curves, diag, invert, n_q, q_curve, q_xyz, max_iter, t, dist, status, evals, ws, ws_bytes,
                          stream);

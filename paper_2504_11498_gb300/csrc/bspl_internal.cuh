@@ -27,6 +27,10 @@ struct Carver {
     }
 };
 
+// workspaces are carved at 256-byte offsets from their start, which must
+// itself be 256-byte aligned (as cudaMalloc returns)
+inline bool ws_misaligned(const void* ws) { return ws != nullptr && ((uintptr_t)ws & 255u) != 0; }
+
 // exclusive scan of int64 values (in place allowed); tmp from the workspace
 size_t scan_tmp_elems(int64_t n);
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);

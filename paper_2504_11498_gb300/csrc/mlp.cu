@@ -1186,7 +1186,7 @@ bspl_status bspl_mlp_loss_grad(const bspl_mlp* m, int64_t n, const float* X, con
                                float* loss, void* ws, size_t ws_bytes, cudaStream_t stream)
 {
     if (!mlp_ok(m) || n < 1 || n > BSPL_MLP_MAX_BATCH || !X || !y || !grad || !loss) return BSPL_EINVAL;
-    if (!ws || ws_bytes < train_ws_bytes(m->kind, n)) return BSPL_EINVAL;
+    if (!ws || ws_misaligned(ws) || ws_bytes < train_ws_bytes(m->kind, n)) return BSPL_EINVAL;
     if (m->kind == BSPL_MLP_SURFACE) return loss_grad_impl<SurfNet>(m, n, X, y, grad, loss, ws, ws_bytes, stream);
     return loss_grad_impl<CurveNet>(m, n, X, y, grad, loss, ws, ws_bytes, stream);
 }
@@ -1284,7 +1284,7 @@ bspl_status bspl_mlp_train(const bspl_mlp* m, float* adam_m, float* adam_v, int6
     if (!mlp_ok(m) || !adam_m || !adam_v || n < 1 || n > 0x7fffffffLL || !X || !y || epochs < 1 || batch < 1 ||
         batch > BSPL_MLP_MAX_BATCH || !epoch_loss || step0 < 0)
         return BSPL_EINVAL;
-    if (!ws || ws_bytes < train_ws_bytes(m->kind, batch)) return BSPL_EINVAL;
+    if (!ws || ws_misaligned(ws) || ws_bytes < train_ws_bytes(m->kind, batch)) return BSPL_EINVAL;
     if (m->kind == BSPL_MLP_SURFACE)
         return train_impl<SurfNet>(m, adam_m, adam_v, n, X, y, epochs, batch, lr, seed, step0, epoch_loss, ws,
                                    ws_bytes, stream);

@@ -1096,6 +1096,7 @@ extern "C" bspl_status bspl_mlp_collect_pairs(const bspl_segments* segs, int64_t
                                               const double* q_xyz, int64_t cap, int32_t* pair_q, int32_t* pair_seg,
                                               int64_t* n_pairs, void* ws, size_t ws_bytes, cudaStream_t stream)
 {
+    if (ws_misaligned(ws)) return BSPL_EINVAL;
     if (!segs_ok(segs) || n_q < 0 || n_q > 0x7fffffffLL || cap < 0 || !n_pairs) return BSPL_EINVAL;
     if (n_q > 0 && (!q_curve || !q_xyz || (cap > 0 && (!pair_q || !pair_seg)))) return BSPL_EINVAL;
     PairBuf B{};

@@ -1515,6 +1515,7 @@ extern "C" bspl_status bspl_smlp_collect_pairs(const bspl_segments* segs, int64_
                                                const double* q_xyz, int64_t cap, int32_t* pair_q, int32_t* pair_patch,
                                                int64_t* n_pairs, void* ws, size_t ws_bytes, cudaStream_t stream)
 {
+    if (ws_misaligned(ws)) return BSPL_EINVAL;
     if (!segs || !segs->is_surface || n_q < 0 || n_q > 0x7fffffffLL || cap < 0 || !n_pairs) return BSPL_EINVAL;
     if (n_q > 0 && (!q_surf || !q_xyz || (cap > 0 && (!pair_q || !pair_patch)))) return BSPL_EINVAL;
     if (!segs->seg_off || !segs->grp_off || !segs->rec64 || !segs->rec32 || !segs->grp64 || !segs->grp32 ||

@@ -80,3 +80,22 @@ def test_product_refuses_to_run_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(bspl, "_lib", None)
     with pytest.raises(bspl.BsplError):
         bspl.lib()
+
+
+def test_misaligned_workspace_refused_before_any_launch(libpath):
+    """A workspace that does not start on a 256-byte boundary is refused
+    with EINVAL by every entry point that takes one, before any use of the
+    device (so this runs without a GPU)."""
+    import ctypes as C
+
+    from paper_2504_11498_gb300 import bspl
+    L = bspl.lib()
+    bad = C.c_void_p(0x100010)
+    segs, curves, total = bspl.bspl_segments(), bspl.bspl_curves(), C.c_int64()
+    one = C.c_void_p(0x100000)  # never dereferenced: the check comes first
+    assert L.bspl_decompose(0, C.byref(curves), 1e-6, C.byref(segs), C.byref(total), bad, 1 << 20,
+                            None) == bspl.EINVAL
+    for fn in (L.bspl_project_curves, L.bspl_invert_curves, L.bspl_project_surfaces, L.bspl_invert_surfaces):
+        assert fn(C.byref(segs), 1, one, one, None, one, one, one, bad, 1 << 20, None) == bspl.EINVAL
+    assert L.bspl_refine_curves(C.byref(curves), None, 0, 1, one, one, 0, one, one, one, None, bad, 1 << 20,
+                                None) == bspl.EINVAL

@@ -53,3 +53,51 @@ def test_paper_suite_recipe():
     c, h = 0.5 * (lo + hi), 0.6 * (hi - lo)
     k = cq.proj_curve
     assert np.all(np.abs(cq.proj_xyz - c[k]) <= h[k] + 1e-12)
+
+
+def test_nurbs_recipes():
+    """The NURBS set: the curve-set recipe plus one weight per control point,
+    log-uniform in [1/2, 2]; circles: nine control points on the square
+    around the circle in its plane, corner weights sqrt(2)/2; the edge set's
+    curves; weights carried through subset()."""
+    cs, qs = synth.nurbs_curve_set(seed=4, n_curves=512, n_proj=1000, n_inv=500)
+    assert cs.weights.shape == (len(cs.cps),)
+    lw = np.log(cs.weights)
+    assert lw.min() >= np.log(0.5) and lw.max() <= np.log(2.0)
+    # log-uniform: mean of log w near 0, spread near (ln 4)/sqrt(12)
+    assert abs(lw.mean()) < 0.02 and abs(lw.std() - np.log(4.0) / np.sqrt(12.0)) < 0.02
+    assert np.all((cs.degree >= 2) & (cs.degree <= 7))
+    sub = cs.subset([3, 1])
+    assert np.array_equal(sub.weights, np.concatenate([cs.curve_weights(3), cs.curve_weights(1)]))
+    circ, cq, centre, radius, normal = synth.nurbs_circles(seed=6, n_curves=5, n_proj=100)
+    assert np.all(circ.degree == 2) and circ.weights.shape == (45,)
+    for c in range(circ.n):
+        _, U, P = circ.curve(c)
+        w = circ.curve_weights(c)
+        assert np.allclose(w[1::2], np.sqrt(0.5)) and np.all(w[0::2] == 1.0)
+        d = P - centre[c]
+        assert np.allclose(d @ normal[c], 0.0, atol=1e-14)
+        # edge midpoints at the radius, corners at radius * sqrt(2)
+        r = np.linalg.norm(d, axis=1)
+        assert np.allclose(r[0::2], radius[c]) and np.allclose(r[1::2], radius[c] * np.sqrt(2.0))
+        assert np.array_equal(U, [0, 0, 0, .25, .25, .5, .5, .75, .75, 1, 1, 1])
+    edge = synth.nurbs_edge_set()
+    assert edge.n == 6 and list(edge.degree) == [1, 2, 3, 7, 3, 4]
+    assert edge.curve_weights(5).max() / edge.curve_weights(5).min() == 50.0
+    p, U, _ = edge.curve(4)
+    assert U[p] == -3.0 and U[-1] == 5.0
+
+
+def test_refine_flop_count():
+    """The refinement's counted flops per evaluation of degree p (the
+    benchmark's roofline numerator)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    ev = [0] * 64
+    ev[3] = 10     # full evaluations of a cubic: 18 + 12 + 72 + 27 + 30 = 159 each
+    ev[32 + 3] = 5  # C and C' alone: 18 + 12 + 56 + 14 + 30 = 130 each
+    assert bench.refine_flops(ev) == 10 * 159 + 5 * 130
+    # non-rational: 3 coordinates, no quotient
+    assert bench.refine_flops(ev, rational=False) == 10 * (18 + 12 + 54 + 30) + 5 * (18 + 12 + 42 + 30)

@@ -320,12 +320,13 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
 // ends the iteration (D cannot resolve it; halving it would only spend
 // evaluations).  The result's distance never exceeds the start's by more
 // than that rounding.
-// the refinement of one query on a curve of degree p <= MP; returns whether
-// it converged, with the final t and squared distance
-// (NC = 4: a rational curve with weights w, rational Newton)
-// (nev: the evaluations of C, C', C'' made; nev1: those of C and C' alone,
-// the trial points, whose C'' is computed only when another step follows)
-// (rcp: the curve's rows of the shared per-span factors, or nullptr)
+//
+// refine_one: the refinement of one query on a curve of degree p <= MP;
+// returns whether it converged, with the final t and squared distance D.
+//   NC    3, or 4 for a rational curve with weights w (rational Newton);
+//   nev   evaluations of C, C', C'' made; nev1 those of C and C' alone (the
+//         trial points, whose C'' is computed only when another step follows);
+//   rcp   the curve's rows of the shared per-span factors, or nullptr.
 template <int MP, int NC>
 __device__ __noinline__ bool refine_one(const double* __restrict__ U, const double* __restrict__ P,
                                         const double* __restrict__ w, int p, int m, const double* q, int max_iter,

@@ -1,5 +1,7 @@
 // Error-controlled decomposition of B-spline curves and surfaces into cubic
-// Bezier segments and bicubic patches (Sec. 4.2.1 and 4.2.2), in FP64.
+// Bezier segments and bicubic patches (Sec. 4.2.1 and 4.2.2), in FP64;
+// rational curves through their homogeneous pieces and certified Hermite
+// cubics (the section "rational pieces" below).
 //
 // This translation unit is compiled with -fmad=false: every decision of the
 // subdivision (accept a reduced piece, or split it) is made from plain IEEE

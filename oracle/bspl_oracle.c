@@ -34,7 +34,9 @@
 #include <omp.h>
 #endif
 
-#define OMAXP 31          /* highest supported degree (paper Sec. 5.2 limit) */
+#define OMAXP 63          /* highest supported curve degree */
+#define OMATP 31          /* highest degree extracted by the matrix route (the
+                             paper's limit, Sec. 5.2); above it the blossom */
 #define ONP (OMAXP + 1)   /* control points of one span */
 #define ODEPTH 40         /* subdivision depth cap */
 #define OLEAFCAP 65536    /* leaves per span (pair) after which every node is accepted */
@@ -375,6 +377,55 @@ static void span_bezier(int p, const double* U, int q, const double* Pl, double*
         }
 }
 
+/* Bezier points Q[0..p] of span q from the blossom (polar form) of the
+ * span's polynomial: Q_j = f(t_q, .., t_q, t_{q+1}, .., t_{q+1}) with p - j
+ * arguments t_q followed by j arguments t_{q+1}, each by de Boor's algorithm
+ * with the arguments in that order: d_i = (1 - a) d_{i-1} + a d_i, a = (x -
+ * t_i)/(t_{i+p+1-r} - t_i) for r = 1..p, i = q..q-p+r downwards.  Every a
+ * lies in [0, 1] (x is t_q or t_{q+1}, inside [t_i, t_{i+p+1-r}]), so the
+ * points are convex combinations of the span's control points at any
+ * degree, whereas the matrix route's power-basis coefficients grow like
+ * C(p, p/2) and take as many digits with them. */
+static void span_blossom(int p, const double* U, int q, const double* Pl, double* Q)
+{
+    double d[ONP][3];
+    for (int j = 0; j <= p; ++j) {
+        for (int i = 0; i <= p; ++i)
+            for (int c = 0; c < 3; ++c) d[i][c] = Pl[3 * i + c];
+        for (int r = 1; r <= p; ++r) {
+            double x = r <= p - j ? U[q] : U[q + 1];
+            for (int i = p; i >= r; --i) {
+                int g = q - p + i;
+                double a = (x - U[g]) / (U[g + p + 1 - r] - U[g]);
+                for (int c = 0; c < 3; ++c) d[i][c] = (1.0 - a) * d[i - 1][c] + a * d[i][c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) Q[3 * j + c] = d[p][c];
+    }
+}
+
+/* the extraction the decomposition uses: the matrix route up to degree
+ * OMATP, the blossom above it */
+static void span_extract(int p, const double* U, int q, const double* Pl, double* Q)
+{
+    if (p <= OMATP) span_bezier(p, U, q, Pl, Q);
+    else span_blossom(p, U, q, Pl, Q);
+}
+
+int orc_span_blossom(int p, const double* U, int64_t nU, const double* P, int64_t nP, double* Q, int64_t cap,
+                     int64_t* nspans)
+{
+    if (p < 1 || p > OMAXP || nU != nP + p + 1) return ORC_EINVAL;
+    int64_t ns = 0;
+    for (int q = p; q <= (int)nP - 1; ++q) {
+        if (!(U[q] < U[q + 1])) continue;
+        if (ns < cap) span_blossom(p, U, q, P + 3 * (q - p), Q + (size_t)ns * 3 * (p + 1));
+        ++ns;
+    }
+    *nspans = ns;
+    return ns <= cap ? ORC_OK : ORC_ENOSPACE;
+}
+
 /* all non-empty spans of one curve by the matrix route (exported for pins) */
 int orc_span_bezier(int p, const double* U, int64_t nU, const double* P, int64_t nP,
                     double* Q, int64_t cap, int64_t* nspans)
@@ -664,8 +715,8 @@ static void rspan_bezier(int p, const double* U, int q, const double* Pl, const 
         hw[3 * j + 1] = 0.0;
         hw[3 * j + 2] = 0.0;
     }
-    span_bezier(p, U, q, hp, Qp);
-    span_bezier(p, U, q, hw, Qw);
+    span_extract(p, U, q, hp, Qp);
+    span_extract(p, U, q, hw, Qw);
     for (int j = 0; j <= p; ++j) {
         for (int c = 0; c < 3; ++c) H[4 * j + c] = Qp[3 * j + c];
         H[4 * j + 3] = Qw[3 * j];
@@ -826,7 +877,7 @@ static int64_t decompose_one_curve(int64_t c, const int32_t* deg, const int64_t*
             rcurve_node(&X, H, 0, 0);
         } else {
             double Q[(ONP + 1) * 3];
-            span_bezier(p, U, q, P + 3 * (q - p), Q);
+            span_extract(p, U, q, P + 3 * (q - p), Q);
             curve_node(&X, Q, 0, 0);
         }
     }

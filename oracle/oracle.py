@@ -45,6 +45,7 @@ def lib():
                                             _i64p, _f64p, I64, _i32p, _f64p, _f64p]
             L.orc_boehm_bezier.argtypes = [C.c_int, _f64p, I64, _f64p, I64, _f64p, I64, C.POINTER(I64)]
             L.orc_span_bezier.argtypes = [C.c_int, _f64p, I64, _f64p, I64, _f64p, I64, C.POINTER(I64)]
+            L.orc_span_blossom.argtypes = [C.c_int, _f64p, I64, _f64p, I64, _f64p, I64, C.POINTER(I64)]
             L.orc_reduce_g1.argtypes = [C.c_int, _f64p, _f64p, _f64p, C.c_int]
             L.orc_to_cubic.argtypes = [C.c_int, _f64p, _f64p]
             L.orc_bound2.restype = D
@@ -159,6 +160,19 @@ def span_bezier(p, U, P):
     Q = np.zeros(cap * (p + 1) * 3)
     ns = C.c_int64()
     rc = lib().orc_span_bezier(p, U, len(U), P, len(P) // 3, Q, cap, C.byref(ns))
+    assert rc == OK, rc
+    return Q[: ns.value * (p + 1) * 3].reshape(ns.value, p + 1, 3)
+
+
+def span_blossom(p, U, P):
+    """Bezier points of every non-empty span from the blossom (de Boor's
+    algorithm at the span's end knots): [ns][p+1][3]."""
+    U = _a(U, np.float64)
+    P = _a(P, np.float64).reshape(-1)
+    cap = len(U)
+    Q = np.zeros(cap * (p + 1) * 3)
+    ns = C.c_int64()
+    rc = lib().orc_span_blossom(p, U, len(U), P, len(P) // 3, Q, cap, C.byref(ns))
     assert rc == OK, rc
     return Q[: ns.value * (p + 1) * 3].reshape(ns.value, p + 1, 3)
 

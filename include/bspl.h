@@ -73,7 +73,8 @@ typedef enum {
 #define BSPL_Q_OFF_CURVE 16u /* inversion: distance above 1e-9 x diagonal        */
 #define BSPL_Q_INVALID 32u   /* spline index out of range or non-finite point    */
 
-/* Curves in CSR form (Sec. 3): curve c has degree p = degree[c] (1..31),
+/* Curves in CSR form (Sec. 3): curve c has degree p = degree[c] (1..63;
+ * the paper's method stops at 31, see bspl_decompose for degrees above),
  * control points cps[cp_off[c] .. cp_off[c+1]) (xyz, FP64, [ncp][3]) and
  * knots knots[knot_off[c] .. knot_off[c+1]) with ncp + p + 1 entries,
  * non-decreasing and finite.  The parameter domain is [t_p, t_{ncp}].
@@ -99,7 +100,8 @@ typedef struct {
 } bspl_curves;
 
 /* Tensor-product surfaces in CSR form: surface s has degrees deg_u[s],
- * deg_v[s] (1..15), an n_u[s] x n_v[s] control net stored row-major
+ * deg_v[s] (1..7; the span-pair nets the query kernels keep are 8 x 8;
+ * other degrees -> BSPL_EINVAL), an n_u[s] x n_v[s] control net stored row-major
  * [n_u][n_v][3] (first index along u) at cps[3*cp_off[s]...], and knot
  * vectors knots_u[knot_u_off[s]..], knots_v[knot_v_off[s]..] of lengths
  * n_u+deg_u+1 and n_v+deg_v+1. */
@@ -273,6 +275,11 @@ size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64
  *   midpoint of its parameter interval and both halves are reduced again
  *   from the original piece (depth cap 40 and at most 65536 pieces per span
  *   or span pair; reaching either accepts the piece and -> BSPL_ENOTCONV).
+ * Degrees 32..63 (above the paper's limit of 31): the power-basis
+ * coefficients of the matrix route grow like C(p, p/2) and would take as
+ * many digits, so each span's Bezier points are the blossom values at the
+ * span's end knots instead (de Boor's algorithm: convex combinations of the
+ * span's control points), then reduced, bounded and subdivided as above.
  * Rational curves (bspl_curves.weights, weights not all equal): the matrix
  * route is applied to the homogeneous control points (w_i P_i, w_i), which
  * gives each span's rational Bezier piece as homogeneous points (W_j Q_j,
@@ -404,7 +411,7 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
  * The result is the local minimum of the original curve reached from the
  * approximant's answer: it is the global one unless the original curve has
  * another local minimum whose distance is within twice the decomposition
- * tolerance of it.  Degrees 1..31 (others are left unchanged).
+ * tolerance of it.  Degrees 1..63 (others are left unchanged).
  *   out     evals: optional device array [BSPL_REFINE_EVALS], accumulated:
  *           entry p counts the evaluations of C, C', C'' on curves of
  *           degree p, entry 32 + p those of C and C' alone (the trial points

@@ -7,7 +7,8 @@
 
 namespace bspl {
 
-constexpr int kMaxCurveDegree = 31;
+constexpr int kMaxCurveDegree = 63;
+constexpr int kMatrixMaxDeg = 31;  // highest degree extracted by the matrix route (the paper's limit)
 constexpr int kMaxSurfDegree = 7;
 constexpr int kDepthCap = 40;
 constexpr int64_t kLeafCap = 65536;  // leaves per span (pair) after which every node is accepted

@@ -72,6 +72,22 @@ struct RedCoef {
     double ap[MP + 1];            // p / 3
     double ea[MP][MP + 1];        // elevation n -> n + 1: i / (n + 1)
     double eb[MP][MP + 1];        // (n + 1 - i) / (n + 1)
+    __host__ __device__ double g33_(int i, int j) const { return g33[i][j]; }
+    __host__ __device__ double gp_(int p, int r, int j) const { return gp[p][r][j]; }
+    __host__ __device__ double ap_(int p) const { return ap[p]; }
+    __host__ __device__ double ea_(int n, int i) const { return ea[n][i]; }
+    __host__ __device__ double eb_(int n, int i) const { return eb[n][i]; }
+};
+
+// The same coefficients computed where they are used (the same operations,
+// so the same values): for degrees above 31, whose tables would not fit in
+// shared memory.
+struct CoefInline {
+    __host__ __device__ double g33_(int i, int j) const { return gram_d(3, 3, i, j); }
+    __host__ __device__ double gp_(int p, int r, int j) const { return j <= p ? gram_d(3, p, 1 + r, j) : 0.0; }
+    __host__ __device__ double ap_(int p) const { return fdiv((double)p, 3.0); }
+    __host__ __device__ double ea_(int n, int i) const { return fdiv((double)i, (double)(n + 1)); }
+    __host__ __device__ double eb_(int n, int i) const { return fdiv((double)(n + 1 - i), (double)(n + 1)); }
 };
 
 // every thread of the block must call this
@@ -159,16 +175,47 @@ __host__ __device__ void span_bezier(int p, const double* __restrict__ U, int q,
         }
 }
 
+// Bezier points of span q from the blossom of the span's polynomial, for
+// degrees above 31 (where the matrix route's power-basis coefficients, of
+// the size of C(p, p/2), would take that many digits): Q_j is the blossom
+// at (t_q x (p - j), t_{q+1} x j), by de Boor's algorithm with the
+// arguments in that order, d_i <- (1 - a) d_{i-1} + a d_i with a = (x -
+// t_i) / (t_{i+p+1-r} - t_i) in [0, 1]; NC = 4: the homogeneous points
+// (w_i P_i, w_i), wl the weights
+template <int MP, int NC = 3>
+__host__ __device__ void span_blossom(int p, const double* __restrict__ U, int q, const double* __restrict__ Pl,
+                                      double* Q, const double* __restrict__ wl = nullptr)
+{
+    double d[MP + 1][NC];
+    for (int j = 0; j <= p; ++j) {
+        for (int i = 0; i <= p; ++i)
+            for (int c = 0; c < NC; ++c) {
+                if constexpr (NC == 4) d[i][c] = c < 3 ? fmul(wl[i], Pl[3 * i + c]) : wl[i];
+                else d[i][c] = Pl[3 * i + c];
+            }
+        for (int r = 1; r <= p; ++r) {
+            const double x = r <= p - j ? U[q] : U[q + 1];
+            for (int i = p; i >= r; --i) {
+                const int g = q - p + i;
+                const double a = fdiv(fsub(x, U[g]), fsub(U[g + p + 1 - r], U[g]));
+                const double b = fsub(1.0, a);
+                for (int c = 0; c < NC; ++c) d[i][c] = fadd(fmul(b, d[i - 1][c]), fmul(a, d[i][c]));
+            }
+        }
+        for (int c = 0; c < NC; ++c) Q[NC * j + c] = d[p][c];
+    }
+}
+
 // degree n -> n+1 (exact degree elevation); Q and E indexed with stride s (points)
-template <int MP>
-__host__ __device__ void elevate(int n, const double* Q, double* E, int s, const RedCoef<MP>& cf)
+template <int MP, class CF>
+__host__ __device__ void elevate(int n, const double* Q, double* E, int s, const CF& cf)
 {
     for (int c = 0; c < 3; ++c) {
         E[c] = Q[c];
         E[(n + 1) * s + c] = Q[n * s + c];
     }
     for (int i = 1; i <= n; ++i) {
-        const double a = cf.ea[n][i], b = cf.eb[n][i];
+        const double a = cf.ea_(n, i), b = cf.eb_(n, i);
         for (int c = 0; c < 3; ++c) E[i * s + c] = fadd(fmul(a, Q[(i - 1) * s + c]), fmul(b, Q[i * s + c]));
     }
 }
@@ -179,26 +226,26 @@ __host__ __device__ void elevate(int n, const double* Q, double* E, int s, const
 // delta0 (B0.d1) + delta1 (B1.d1) = V2.d1, A0 = a g11 d0, A1 = -a g12 d1,
 // B0 = a g21 d0, B1 = -a g22 d1, a = p/3; degenerate systems fall back to
 // delta0 = delta1 = 1.
-template <int MP>
-__host__ __device__ void reduce_g1(int p, const double* Q, int s, double* R, int rs, const RedCoef<MP>& cf)
+template <int MP, class CF>
+__host__ __device__ void reduce_g1(int p, const double* Q, int s, double* R, int rs, const CF& cf)
 {
     const double* Q0 = Q;
     const double* Q1 = Q + s;
     const double* Qm = Q + (p - 1) * s;
     const double* Qp = Q + p * s;
-    const double a = cf.ap[p];
-    const double g11 = cf.g33[1][1], g12 = cf.g33[1][2];
-    const double g21 = cf.g33[2][1], g22 = cf.g33[2][2];
-    const double g10 = cf.g33[1][0], g13 = cf.g33[1][3];
-    const double g20 = cf.g33[2][0], g23 = cf.g33[2][3];
+    const double a = cf.ap_(p);
+    const double g11 = cf.g33_(1, 1), g12 = cf.g33_(1, 2);
+    const double g21 = cf.g33_(2, 1), g22 = cf.g33_(2, 2);
+    const double g10 = cf.g33_(1, 0), g13 = cf.g33_(1, 3);
+    const double g20 = cf.g33_(2, 0), g23 = cf.g33_(2, 3);
     double d0[3], d1[3], V1[3], V2[3];
     for (int c = 0; c < 3; ++c) {
         d0[c] = fsub(Q1[c], Q0[c]);
         d1[c] = fsub(Qp[c], Qm[c]);
         double s1 = 0.0, s2 = 0.0;
         for (int j = 0; j <= p; ++j) {
-            s1 = fadd(s1, fmul(cf.gp[p][0][j], Q[j * s + c]));
-            s2 = fadd(s2, fmul(cf.gp[p][1][j], Q[j * s + c]));
+            s1 = fadd(s1, fmul(cf.gp_(p, 0, j), Q[j * s + c]));
+            s2 = fadd(s2, fmul(cf.gp_(p, 1, j), Q[j * s + c]));
         }
         double t1 = fadd(fadd(fadd(fmul(g10, Q0[c]), fmul(g11, Q0[c])), fmul(g12, Qp[c])), fmul(g13, Qp[c]));
         double t2 = fadd(fadd(fadd(fmul(g20, Q0[c]), fmul(g21, Q0[c])), fmul(g22, Qp[c])), fmul(g23, Qp[c]));
@@ -236,8 +283,8 @@ __host__ __device__ void reduce_g1(int p, const double* Q, int s, double* R, int
     }
 }
 
-template <int MP>
-__host__ __device__ void to_cubic(int p, const double* Q, int s, double* R, int rs, const RedCoef<MP>& cf)
+template <int MP, class CF>
+__host__ __device__ void to_cubic(int p, const double* Q, int s, double* R, int rs, const CF& cf)
 {
     if (p == 3) {
         for (int i = 0; i < 4; ++i)
@@ -259,8 +306,8 @@ __host__ __device__ void to_cubic(int p, const double* Q, int s, double* R, int 
 }
 
 // max_i |Q_i - (R elevated to p)_i|^2 (certified deviation bound)
-template <int MP>
-__host__ __device__ double bound2_curve(int p, const double* Q, int s, const double* R, int rs, const RedCoef<MP>& cf)
+template <int MP, class CF>
+__host__ __device__ double bound2_curve(int p, const double* Q, int s, const double* R, int rs, const CF& cf)
 {
     double w[(MP + 1) * 3], x[(MP + 1) * 3];
     for (int i = 0; i < 4; ++i)
@@ -320,10 +367,10 @@ __host__ __device__ void halve_keep(int p, double* Q, int s, int side)
 // C'(0) = p (H_1 - W_1 C(0)) / W_0 and C'(1) = p (W_{p-1} C(1) - H_{p-1}) / W_p
 // (the quotient rule at the ends of a rational Bezier; H_j its first three
 // coordinates)
-template <int MP>
-__host__ __device__ void rhermite(int p, const double* H, double* R, const RedCoef<MP>& cf)
+template <int MP, class CF>
+__host__ __device__ void rhermite(int p, const double* H, double* R, const CF& cf)
 {
-    const double a = cf.ap[p];
+    const double a = cf.ap_(p);
     const double* h0 = H;
     const double* h1 = H + 4;
     const double* hm = H + 4 * (p - 1);
@@ -532,16 +579,16 @@ __host__ __device__ inline void set_flag(int* err, int bit)
 #endif
 }
 
-template <int MP, bool FILL>
+template <int MP, bool FILL, class CF>
 __host__ __device__ int64_t walk_span_curve(int p, const double* __restrict__ U, int q, const double* __restrict__ Pl,
-                                            double thr2, int64_t first, CurveLeafOut out, int* err,
-                                            const RedCoef<MP>& cf)
+                                            double thr2, int64_t first, CurveLeafOut out, int* err, const CF& cf)
 {
     constexpr int kStack = MP == 7 ? 16 : (MP == 15 ? 8 : 4);
     constexpr int W = (MP + 1) * 3;
     double stk[kStack][W], Q[W];
     const int np3 = 3 * (p + 1);
-    span_bezier<MP>(p, U, q, Pl, 1, stk[0]);
+    if constexpr (MP > kMatrixMaxDeg) span_blossom<MP>(p, U, q, Pl, stk[0]);
+    else span_bezier<MP>(p, U, q, Pl, 1, stk[0]);
     int L = 0;
     int64_t k = 0, count = 0;
     for (;;) {
@@ -589,17 +636,17 @@ __host__ __device__ int64_t walk_span_curve(int p, const double* __restrict__ U,
 // the same walk over the homogeneous piece of a span of a rational curve
 // (weights wl of its p + 1 control points), each node replaced by its
 // Hermite cubic and accepted by the bound rbound2
-template <int MP, bool FILL>
+template <int MP, bool FILL, class CF>
 __host__ __device__ int64_t walk_span_rcurve(int p, const double* __restrict__ U, int q,
                                              const double* __restrict__ Pl, const double* __restrict__ wl,
-                                             double thr2, int64_t first, CurveLeafOut out, int* err,
-                                             const RedCoef<MP>& cf)
+                                             double thr2, int64_t first, CurveLeafOut out, int* err, const CF& cf)
 {
     constexpr int kStack = MP == 7 ? 12 : (MP == 15 ? 6 : 3);
     constexpr int W = (MP + 1) * 4;
     double stk[kStack][W], H[W];
     const int np4 = 4 * (p + 1);
-    span_bezier<MP, 4>(p, U, q, Pl, 1, stk[0], wl);
+    if constexpr (MP > kMatrixMaxDeg) span_blossom<MP, 4>(p, U, q, Pl, stk[0], wl);
+    else span_bezier<MP, 4>(p, U, q, Pl, 1, stk[0], wl);
     RBoundCoef<MP> rc;
     rbound_coef<MP>(p, rc);
     int L = 0;
@@ -645,20 +692,19 @@ __host__ __device__ int64_t walk_span_rcurve(int p, const double* __restrict__ U
     return count;
 }
 
-// slot = cp_off[c] + (q - p), q in [p, ncp-1]; RAT: the rational curves
-// (rat[c] = 1) only, else the others
-template <int MP, bool FILL, bool RAT = false>
-__global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, double tol_rel, int64_t n_slots,
-                              int64_t* __restrict__ cnt, CurveLeafOut out, int* err, const int* __restrict__ rat)
+// the walk of one span slot by one thread: slot = cp_off[c] + (q - p); this
+// instance handles degrees (MP/2, MP] (1..7, 8..15, 16..31, 32..63) of the
+// rational curves (RAT) or of the others; invalid curves carry a NaN
+// diagonal and are skipped
+template <int MP, bool FILL, bool RAT, class CF>
+__device__ __forceinline__ void walk_slot(const bspl_curves& C, const double* __restrict__ diag, double tol_rel,
+                                          int64_t n_slots, int64_t* __restrict__ cnt, CurveLeafOut out, int* err,
+                                          const int* __restrict__ rat, const CF& cf)
 {
-    __shared__ RedCoef<MP> cf;
-    fill_coef<MP>(cf);
     int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= n_slots) return;
     int c = find_le(C.cp_off, C.n, slot);
     int p = C.degree[c];
-    // this instance handles degrees (MP/2, MP] (1..7, 8..15, 16..31); invalid
-    // curves carry a NaN diagonal and are skipped
     constexpr int lo = MP == 7 ? 1 : (MP + 1) / 2;
     if (p < lo || p > MP || !(diag[c] >= 0.0) || (rat[c] != 0) != RAT) return;
     int64_t nP = C.cp_off[c + 1] - C.cp_off[c];
@@ -675,6 +721,21 @@ __global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, do
                                           FILL ? cnt[slot] : 0, out, err, cf);
     }
     if (!FILL) cnt[slot] = r;
+}
+
+// slot = cp_off[c] + (q - p), q in [p, ncp-1]; RAT: the rational curves
+// (rat[c] = 1) only, else the others
+template <int MP, bool FILL, bool RAT = false>
+__global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, double tol_rel, int64_t n_slots,
+                              int64_t* __restrict__ cnt, CurveLeafOut out, int* err, const int* __restrict__ rat)
+{
+    if constexpr (MP <= kMatrixMaxDeg) {
+        __shared__ RedCoef<MP> cf;  // the block's coefficient tables
+        fill_coef<MP>(cf);
+        walk_slot<MP, FILL, RAT>(C, diag, tol_rel, n_slots, cnt, out, err, rat, cf);
+    } else {
+        walk_slot<MP, FILL, RAT>(C, diag, tol_rel, n_slots, cnt, out, err, rat, CoefInline{});
+    }
 }
 
 // ---------------------------------------------------------------- surfaces
@@ -1255,8 +1316,8 @@ void launch1d(K kernel, int64_t n, cudaStream_t s, A... args)
 }  // namespace
 
 // the walks of every span of the curve set: one launch per degree class
-// (1-7, 8-15, 16-31) present, for the non-rational curves and, when there
-// are any, for the rational ones
+// (1-7, 8-15, 16-31, 32-63) present, for the non-rational curves and, when
+// there are any, for the rational ones
 template <bool FILL>
 void walk_curves(const bspl_curves& C, const double* diag, double tol_rel, int64_t n_cp, int64_t* cnt,
                  CurveLeafOut o, int* err, const int* rat, int maxdeg, bool any_rat, cudaStream_t s)
@@ -1264,10 +1325,12 @@ void walk_curves(const bspl_curves& C, const double* diag, double tol_rel, int64
     launch1d(k_walk_curves<7, FILL>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
     if (maxdeg > 7) launch1d(k_walk_curves<15, FILL>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
     if (maxdeg > 15) launch1d(k_walk_curves<31, FILL>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
+    if (maxdeg > 31) launch1d(k_walk_curves<63, FILL>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
     if (!any_rat) return;
     launch1d(k_walk_curves<7, FILL, true>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
     if (maxdeg > 7) launch1d(k_walk_curves<15, FILL, true>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
     if (maxdeg > 15) launch1d(k_walk_curves<31, FILL, true>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
+    if (maxdeg > 31) launch1d(k_walk_curves<63, FILL, true>, n_cp, s, C, diag, tol_rel, n_cp, cnt, o, err, rat);
 }
 
 size_t decompose_ws_bytes(int is_surface, int64_t n, int64_t n_cp_total)

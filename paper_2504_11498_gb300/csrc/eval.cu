@@ -48,6 +48,32 @@ __host__ __device__ void basis(const double* U, int q, int p, double t, double* 
     }
 }
 
+// C(t) of curve c, degree p <= MP, t clamped to the domain
+template <int MP>
+__device__ __noinline__ void eval_point(const bspl_curves& C, int c, int p, int m, double t, double* out)
+{
+    const double* U = C.knots + C.knot_off[c];
+    t = fmin(fmax(t, U[p]), U[m + 1]);
+    const int q = span_of(U, p, m, t);
+    double N[MP + 1];
+    basis<MP>(U, q, p, t, N);
+    const double* P = C.cps + 3 * C.cp_off[c];
+    for (int k = 0; k < 3; ++k) out[k] = 0.0;
+    if (C.weights) {
+        const double* w = C.weights + C.cp_off[c];
+        double W = 0.0;
+        for (int j = 0; j <= p; ++j) {
+            const double nw = N[j] * w[q - p + j];
+            W += nw;
+            for (int k = 0; k < 3; ++k) out[k] += nw * P[3 * (q - p + j) + k];
+        }
+        for (int k = 0; k < 3; ++k) out[k] /= W;
+    } else {
+        for (int j = 0; j <= p; ++j)
+            for (int k = 0; k < 3; ++k) out[k] += N[j] * P[3 * (q - p + j) + k];
+    }
+}
+
 __global__ void k_eval_curves(bspl_curves C, int64_t n_q, const int32_t* __restrict__ qc,
                               const double* __restrict__ tq, double* __restrict__ xyz)
 {
@@ -59,26 +85,8 @@ __global__ void k_eval_curves(bspl_curves C, int64_t n_q, const int32_t* __restr
         int p = C.degree[c];
         int m = (int)(C.cp_off[c + 1] - C.cp_off[c]) - 1;
         if (p >= 1 && p <= kMaxCurveDegree && m >= p) {
-            const double* U = C.knots + C.knot_off[c];
-            double t = fmin(fmax(tq[i], U[p]), U[m + 1]);
-            int q = span_of(U, p, m, t);
-            double N[kMaxCurveDegree + 1];
-            basis<kMaxCurveDegree>(U, q, p, t, N);
-            const double* P = C.cps + 3 * C.cp_off[c];
-            for (int k = 0; k < 3; ++k) out[k] = 0.0;
-            if (C.weights) {
-                const double* w = C.weights + C.cp_off[c];
-                double W = 0.0;
-                for (int j = 0; j <= p; ++j) {
-                    const double nw = N[j] * w[q - p + j];
-                    W += nw;
-                    for (int k = 0; k < 3; ++k) out[k] += nw * P[3 * (q - p + j) + k];
-                }
-                for (int k = 0; k < 3; ++k) out[k] /= W;
-            } else {
-                for (int j = 0; j <= p; ++j)
-                    for (int k = 0; k < 3; ++k) out[k] += N[j] * P[3 * (q - p + j) + k];
-            }
+            if (p <= kMatrixMaxDeg) eval_point<kMatrixMaxDeg>(C, c, p, m, tq[i], out);
+            else eval_point<kMaxCurveDegree>(C, c, p, m, tq[i], out);
         }
     }
     for (int k = 0; k < 3; ++k) xyz[3 * i + k] = out[k];
@@ -456,9 +464,10 @@ __device__ __forceinline__ int refine_query(const bspl_curves& Cv, const double*
     const double* w = NC == 4 ? Cv.weights + Cv.cp_off[c] : nullptr;
     // the curve's rows of the shared factors, when every one of them is there
     const double* rc = rcp && Cv.cp_off[c + 1] <= rcp_cap ? rcp + (int64_t)kRcpW * Cv.cp_off[c] : nullptr;
-    const bool conv = p <= kRcpMaxDeg
-                          ? refine_one<kRcpMaxDeg, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, rc)
-                          : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, nullptr);
+    const bool conv =
+        p <= kRcpMaxDeg     ? refine_one<kRcpMaxDeg, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, rc)
+        : p <= kMatrixMaxDeg ? refine_one<kMatrixMaxDeg, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, nullptr)
+                             : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, nullptr);
     const double d = sqrt(D);
     uint8_t fl = st_io[i] & (uint8_t)~(BSPL_Q_CONVERGED | BSPL_Q_NONCONV | BSPL_Q_AT_END | BSPL_Q_OFF_CURVE);
     fl |= conv ? BSPL_Q_CONVERGED : BSPL_Q_NONCONV;

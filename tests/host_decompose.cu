@@ -26,6 +26,24 @@ void host_fill_coef(RedCoef<MP>& cf)
 
 using namespace bspl;
 
+// (degrees up to 31: the walk instance of degrees 16..31 with the block's
+// coefficient tables; above: the instance of degrees 32..63 with the
+// coefficients computed inline, as the device launches them)
+template <int MP, class CF>
+int64_t curve_span(int p, const double* U, int q, const double* P, const double* w, double thr2, double* ctrl,
+                   double* prange, int64_t cap, int* err, const CF& cf)
+{
+    const double* Pl = P + 3 * (q - p);
+    CurveLeafOut none{};
+    const int64_t n = w ? walk_span_rcurve<MP, false>(p, U, q, Pl, w + (q - p), thr2, 0, none, err, cf)
+                        : walk_span_curve<MP, false>(p, U, q, Pl, thr2, 0, none, err, cf);
+    if (n > cap) return n;
+    CurveLeafOut out{ ctrl, prange };
+    if (w) walk_span_rcurve<MP, true>(p, U, q, Pl, w + (q - p), thr2, 0, out, err, cf);
+    else walk_span_curve<MP, true>(p, U, q, Pl, thr2, 0, out, err, cf);
+    return n;
+}
+
 extern "C" {
 
 // box diagonal of a control net, as the device computes it
@@ -74,23 +92,16 @@ int64_t hd_surface_span(int pu, int pv, const double* U, int nu, int qu, const d
 int64_t hd_curve_span(int p, const double* U, int q, const double* P, const double* w, double tol_rel, double diag,
                       double* ctrl, double* prange, int64_t cap, int* err)
 {
-    static RedCoef<kMaxCurveDegree> cf;
+    static RedCoef<kMatrixMaxDeg> cf;
     static bool filled = false;
     if (!filled) {
-        host_fill_coef<kMaxCurveDegree>(cf);
+        host_fill_coef<kMatrixMaxDeg>(cf);
         filled = true;
     }
     const double thr = tol_rel * diag, thr2 = thr * thr;
     *err = 0;
-    const double* Pl = P + 3 * (q - p);
-    CurveLeafOut none{};
-    const int64_t n = w ? walk_span_rcurve<kMaxCurveDegree, false>(p, U, q, Pl, w + (q - p), thr2, 0, none, err, cf)
-                        : walk_span_curve<kMaxCurveDegree, false>(p, U, q, Pl, thr2, 0, none, err, cf);
-    if (n > cap) return n;
-    CurveLeafOut out{ ctrl, prange };
-    if (w) walk_span_rcurve<kMaxCurveDegree, true>(p, U, q, Pl, w + (q - p), thr2, 0, out, err, cf);
-    else walk_span_curve<kMaxCurveDegree, true>(p, U, q, Pl, thr2, 0, out, err, cf);
-    return n;
+    if (p <= kMatrixMaxDeg) return curve_span<kMatrixMaxDeg>(p, U, q, P, w, thr2, ctrl, prange, cap, err, cf);
+    return curve_span<kMaxCurveDegree>(p, U, q, P, w, thr2, ctrl, prange, cap, err, CoefInline{});
 }
 
 // derivative bounds and edge flags the filling walk writes into a patch's

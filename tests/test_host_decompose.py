@@ -234,3 +234,24 @@ def test_rational_curve_walk_bit_exact(hd, tol):
         assert np.array_equal(offs, ref.seg_off)
         assert np.array_equal(ctrl, ref.ctrl)
         assert np.array_equal(pr, ref.prange)
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-9])
+def test_high_degree_curve_walk_bit_exact(hd, tol):
+    """Degrees 32..63 (the blossom extraction, coefficients computed inline)
+    and, beside them, degrees up to 31, non-rational and rational: the walk
+    agrees with the oracle bit for bit."""
+    rng = np.random.default_rng(44)
+    degs, knots, cps, ws = [], [], [], []
+    for p in (5, 31, 32, 40, 51, 63):
+        ncp = p + int(rng.integers(1, 6))
+        degs.append(p)
+        knots.append(synth.random_clamped_knots(rng, p, ncp))
+        cps.append(rng.uniform(0.0, 1.0, size=(ncp, 3)))
+        ws.append(np.exp(rng.uniform(np.log(0.5), np.log(2.0), ncp)))
+    for s in (synth.pack_curves(degs, knots, cps), synth.pack_curves(degs, knots, cps, ws)):
+        offs, ctrl, pr = host_decompose_curves(hd, s, tol)
+        ref = O.decompose_curves(s, tol)
+        assert np.array_equal(offs, ref.seg_off)
+        assert np.array_equal(ctrl, ref.ctrl)
+        assert np.array_equal(pr, ref.prange)

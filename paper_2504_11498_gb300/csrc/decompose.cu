@@ -80,8 +80,9 @@ struct RedCoef {
 };
 
 // The same coefficients computed where they are used (the same operations,
-// so the same values): for degrees above 31, whose tables would not fit in
-// shared memory.
+// so the same values): for the degrees 32..63, whose tables would not fit
+// in shared memory.
+constexpr int kCoefTableMaxDeg = 31;
 struct CoefInline {
     __host__ __device__ double g33_(int i, int j) const { return gram_d(3, 3, i, j); }
     __host__ __device__ double gp_(int p, int r, int j) const { return j <= p ? gram_d(3, p, 1 + r, j) : 0.0; }
@@ -176,8 +177,9 @@ __host__ __device__ void span_bezier(int p, const double* __restrict__ U, int q,
 }
 
 // Bezier points of span q from the blossom of the span's polynomial, for
-// degrees above 31 (where the matrix route's power-basis coefficients, of
-// the size of C(p, p/2), would take that many digits): Q_j is the blossom
+// degrees above 7 (where the matrix route's power-basis coefficients, of
+// the size of C(p, p/2), take that many digits: 2e-10 of the control
+// points' size at degree 15, 1e-2 at 31): Q_j is the blossom
 // at (t_q x (p - j), t_{q+1} x j), by de Boor's algorithm with the
 // arguments in that order, d_i <- (1 - a) d_{i-1} + a d_i with a = (x -
 // t_i) / (t_{i+p+1-r} - t_i) in [0, 1]; NC = 4: the homogeneous points
@@ -729,7 +731,7 @@ template <int MP, bool FILL, bool RAT = false>
 __global__ void k_walk_curves(bspl_curves C, const double* __restrict__ diag, double tol_rel, int64_t n_slots,
                               int64_t* __restrict__ cnt, CurveLeafOut out, int* err, const int* __restrict__ rat)
 {
-    if constexpr (MP <= kMatrixMaxDeg) {
+    if constexpr (MP <= kCoefTableMaxDeg) {
         __shared__ RedCoef<MP> cf;  // the block's coefficient tables
         fill_coef<MP>(cf);
         walk_slot<MP, FILL, RAT>(C, diag, tol_rel, n_slots, cnt, out, err, rat, cf);

@@ -85,7 +85,7 @@ __global__ void k_eval_curves(bspl_curves C, int64_t n_q, const int32_t* __restr
         int p = C.degree[c];
         int m = (int)(C.cp_off[c + 1] - C.cp_off[c]) - 1;
         if (p >= 1 && p <= kMaxCurveDegree && m >= p) {
-            if (p <= kMatrixMaxDeg) eval_point<kMatrixMaxDeg>(C, c, p, m, tq[i], out);
+            if (p <= kEvalMidDeg) eval_point<kEvalMidDeg>(C, c, p, m, tq[i], out);
             else eval_point<kMaxCurveDegree>(C, c, p, m, tq[i], out);
         }
     }
@@ -125,16 +125,16 @@ struct SpanCache {
 constexpr int kRcpW = 42;
 constexpr int kRcpMaxDeg = 7;
 
-__device__ __forceinline__ double rcp_inv(const double* U, int q, int j, int r)
+__host__ __device__ __forceinline__ double rcp_inv(const double* U, int q, int j, int r)
 {
     const double den = U[q + r + 1] - U[q + 1 - j + r];
     return den != 0.0 ? 1.0 / den : 0.0;
 }
-__device__ __forceinline__ double rcp_sq(const double* U, int p, int q, int j)
+__host__ __device__ __forceinline__ double rcp_sq(const double* U, int p, int q, int j)
 {
     return p / (U[q + j + 1] - U[q - p + j + 1]);
 }
-__device__ __forceinline__ double rcp_sr(const double* U, int p, int q, int j)
+__host__ __device__ __forceinline__ double rcp_sr(const double* U, int p, int q, int j)
 {
     return (p - 1) / (U[q + j] - U[q - p + j + 1]);
 }
@@ -168,7 +168,7 @@ __global__ void k_span_rcp(bspl_curves C, int64_t cap, double* __restrict__ tab)
 
 // control point i of the curve: P_i, or (w_i P_i, w_i) for a rational one
 template <int NC>
-__device__ __forceinline__ double hpt(const double* P, const double* w, int i, int k)
+__host__ __device__ __forceinline__ double hpt(const double* P, const double* w, int i, int k)
 {
     if constexpr (NC == 4) return k < 3 ? w[i] * P[3 * i + k] : w[i];
     else return P[3 * i + k];
@@ -177,7 +177,7 @@ __device__ __forceinline__ double hpt(const double* P, const double* w, int i, i
 // the span's factors from the shared rows when there are any (the same
 // values: k_span_rcp computes them with the same operations), else here
 template <int MP, int NC>
-__device__ __forceinline__ void span_prepare(const double* U, const double* P, const double* w, int p, int q,
+__host__ __device__ __forceinline__ void span_prepare(const double* U, const double* P, const double* w, int p, int q,
                                              SpanCache<MP, NC>& S)
 {
     static_assert(MP <= 8, "span cache for low degrees only");
@@ -218,7 +218,7 @@ __device__ __forceinline__ void span_prepare(const double* U, const double* P, c
 // D2 = false: C and C' only (C2out untouched).  t inside the cached span
 // (the usual case after the first evaluation) skips the span search.
 template <int MP, int NC = 3, bool D2 = true>
-__device__ __forceinline__ void curve_d2(const double* U, const double* P, const double* w, int p, int m, double t,
+__host__ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const double* w, int p, int m, double t,
                                          SpanCache<MP, NC>& S, double* Cout, double* C1out, double* C2out)
 {
     constexpr bool kCache = MP <= 8;
@@ -336,7 +336,7 @@ __device__ __forceinline__ void curve_d2(const double* U, const double* P, const
 //         trial points, whose C'' is computed only when another step follows);
 //   rcp   the curve's rows of the shared per-span factors, or nullptr.
 template <int MP, int NC>
-__device__ __noinline__ bool refine_one(const double* __restrict__ U, const double* __restrict__ P,
+__host__ __device__ __noinline__ bool refine_one(const double* __restrict__ U, const double* __restrict__ P,
                                         const double* __restrict__ w, int p, int m, const double* q, int max_iter,
                                         double& t, double& D, int& nev, int& nev1, const double* rcp)
 {
@@ -466,7 +466,7 @@ __device__ __forceinline__ int refine_query(const bspl_curves& Cv, const double*
     const double* rc = rcp && Cv.cp_off[c + 1] <= rcp_cap ? rcp + (int64_t)kRcpW * Cv.cp_off[c] : nullptr;
     const bool conv =
         p <= kRcpMaxDeg     ? refine_one<kRcpMaxDeg, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, rc)
-        : p <= kMatrixMaxDeg ? refine_one<kMatrixMaxDeg, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, nullptr)
+        : p <= kEvalMidDeg ? refine_one<kEvalMidDeg, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, nullptr)
                              : refine_one<kMaxCurveDegree, NC>(U, P, w, p, m, q, max_iter, t, D, nev, nev1, nullptr);
     const double d = sqrt(D);
     uint8_t fl = st_io[i] & (uint8_t)~(BSPL_Q_CONVERGED | BSPL_Q_NONCONV | BSPL_Q_AT_END | BSPL_Q_OFF_CURVE);

@@ -26,9 +26,10 @@ void host_fill_coef(RedCoef<MP>& cf)
 
 using namespace bspl;
 
-// (degrees up to 31: the walk instance of degrees 16..31 with the block's
-// coefficient tables; above: the instance of degrees 32..63 with the
-// coefficients computed inline, as the device launches them)
+// (degrees up to 7: the walk instance of degrees 1..7 (the matrix route)
+// with the block's coefficient tables; above: the instance of degrees up to
+// 63 (the blossom) with the coefficients computed inline, which are the
+// tables' values)
 template <int MP, class CF>
 int64_t curve_span(int p, const double* U, int q, const double* P, const double* w, double thr2, double* ctrl,
                    double* prange, int64_t cap, int* err, const CF& cf)

@@ -1,6 +1,7 @@
-"""Pins of the oracle for curves of degree 32..63 (above the paper's limit
-of 31, where the decomposition extracts each span from the blossom instead
-of the power-basis matrix route):
+"""Pins of the oracle for curves of high degree (up to 63; the paper stops
+at 31).  The decomposition extracts each span by the power-basis matrix
+route up to degree 7 and from the blossom above, because the matrix route's
+FP64 error grows about tenfold every two degrees:
 
 * the blossom extraction against textbook knot insertion at degrees 33..63;
 * the matrix route's loss of digits at high degree (why the switch), and
@@ -32,6 +33,25 @@ def test_blossom_extraction_matches_knot_insertion(p):
     Qk = O.boehm_bezier(p, U, P)
     assert Qb.shape == Qk.shape and Qb.shape[0] >= 1
     assert np.abs(Qb - Qk).max() <= 1e-12
+
+
+def test_matrix_route_error_by_degree():
+    """Against knot insertion: the matrix route stays within 1e-13 up to
+    degree 7 and passes 1e-11 by degree 15 and 1e-4 by degree 31; the blossom
+    stays within 1e-14 at every degree (hence the switch above 7)."""
+    rng = np.random.default_rng(1)
+    err_m, err_b = {}, {}
+    for p in (3, 5, 7, 15, 31):
+        em = eb = 0.0
+        for _ in range(20):
+            U, P = high_curve(rng, p, p + int(rng.integers(1, 12)))
+            Qk = O.boehm_bezier(p, U, P)
+            em = max(em, np.abs(O.span_bezier(p, U, P) - Qk).max())
+            eb = max(eb, np.abs(O.span_blossom(p, U, P) - Qk).max())
+        err_m[p], err_b[p] = em, eb
+    assert max(err_m[3], err_m[5], err_m[7]) <= 1e-13, err_m
+    assert err_m[15] >= 1e-11 and err_m[31] >= 1e-4, err_m
+    assert max(err_b.values()) <= 1e-14, err_b
 
 
 def test_matrix_route_loses_digits_at_high_degree():

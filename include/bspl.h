@@ -74,7 +74,7 @@ typedef enum {
 #define BSPL_Q_INVALID 32u   /* spline index out of range or non-finite point    */
 
 /* Curves in CSR form (Sec. 3): curve c has degree p = degree[c] (1..63;
- * the paper's method stops at 31, see bspl_decompose for degrees above),
+ * the paper's method stops at 31; see bspl_decompose for degrees above 7),
  * control points cps[cp_off[c] .. cp_off[c+1]) (xyz, FP64, [ncp][3]) and
  * knots knots[knot_off[c] .. knot_off[c+1]) with ncp + p + 1 entries,
  * non-decreasing and finite.  The parameter domain is [t_p, t_{ncp}].
@@ -275,11 +275,13 @@ size_t bspl_workspace_bytes(int op, int64_t n_splines, int64_t n_cp_total, int64
  *   midpoint of its parameter interval and both halves are reduced again
  *   from the original piece (depth cap 40 and at most 65536 pieces per span
  *   or span pair; reaching either accepts the piece and -> BSPL_ENOTCONV).
- * Degrees 32..63 (above the paper's limit of 31): the power-basis
- * coefficients of the matrix route grow like C(p, p/2) and would take as
- * many digits, so each span's Bezier points are the blossom values at the
- * span's end knots instead (de Boor's algorithm: convex combinations of the
- * span's control points), then reduced, bounded and subdivided as above.
+ * Degrees 8..63: the power-basis coefficients of the matrix route grow like
+ * C(p, p/2) and take as many digits (measured against knot insertion:
+ * 6e-14 of the control points' size at degree 7, 2e-10 at 15, 1e-2 at 31,
+ * the paper's own limit), so above degree 7 each span's Bezier points are
+ * the blossom values at the span's end knots instead (de Boor's algorithm:
+ * convex combinations of the span's control points), then reduced, bounded
+ * and subdivided as above.
  * Rational curves (bspl_curves.weights, weights not all equal): the matrix
  * route is applied to the homogeneous control points (w_i P_i, w_i), which
  * gives each span's rational Bezier piece as homogeneous points (W_j Q_j,

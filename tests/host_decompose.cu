@@ -26,10 +26,9 @@ void host_fill_coef(RedCoef<MP>& cf)
 
 using namespace bspl;
 
-// (degrees up to 7: the walk instance of degrees 1..7 (the matrix route)
-// with the block's coefficient tables; above: the instance of degrees up to
-// 63 (the blossom) with the coefficients computed inline, which are the
-// tables' values)
+// (the device's walk instances: degrees 1..7 (the matrix route), 8..15 and
+// 16..31 (the blossom) with the block's coefficient tables, 32..63 (the
+// blossom) with the coefficients computed inline)
 template <int MP, class CF>
 int64_t curve_span(int p, const double* U, int q, const double* P, const double* w, double thr2, double* ctrl,
                    double* prange, int64_t cap, int* err, const CF& cf)
@@ -93,15 +92,21 @@ int64_t hd_surface_span(int pu, int pv, const double* U, int nu, int qu, const d
 int64_t hd_curve_span(int p, const double* U, int q, const double* P, const double* w, double tol_rel, double diag,
                       double* ctrl, double* prange, int64_t cap, int* err)
 {
-    static RedCoef<kMatrixMaxDeg> cf;
+    static RedCoef<7> cf7;
+    static RedCoef<15> cf15;
+    static RedCoef<31> cf31;
     static bool filled = false;
     if (!filled) {
-        host_fill_coef<kMatrixMaxDeg>(cf);
+        host_fill_coef<7>(cf7);
+        host_fill_coef<15>(cf15);
+        host_fill_coef<31>(cf31);
         filled = true;
     }
     const double thr = tol_rel * diag, thr2 = thr * thr;
     *err = 0;
-    if (p <= kMatrixMaxDeg) return curve_span<kMatrixMaxDeg>(p, U, q, P, w, thr2, ctrl, prange, cap, err, cf);
+    if (p <= 7) return curve_span<7>(p, U, q, P, w, thr2, ctrl, prange, cap, err, cf7);
+    if (p <= 15) return curve_span<15>(p, U, q, P, w, thr2, ctrl, prange, cap, err, cf15);
+    if (p <= 31) return curve_span<31>(p, U, q, P, w, thr2, ctrl, prange, cap, err, cf31);
     return curve_span<kMaxCurveDegree>(p, U, q, P, w, thr2, ctrl, prange, cap, err, CoefInline{});
 }
 

@@ -238,12 +238,14 @@ def test_rational_curve_walk_bit_exact(hd, tol):
 
 @pytest.mark.parametrize("tol", [1e-6, 1e-9])
 def test_high_degree_curve_walk_bit_exact(hd, tol):
-    """Degrees 32..63 (the blossom extraction, coefficients computed inline)
-    and, beside them, degrees up to 31, non-rational and rational: the walk
-    agrees with the oracle bit for bit."""
+    """Every walk instance the device launches (degrees 1..7 by the matrix
+    route, 8..15 and 16..31 by the blossom with the coefficient tables,
+    32..63 by the blossom with the coefficients computed inline),
+    non-rational and rational: the walk agrees with the oracle bit for
+    bit."""
     rng = np.random.default_rng(44)
     degs, knots, cps, ws = [], [], [], []
-    for p in (5, 31, 32, 40, 51, 63):
+    for p in (5, 7, 8, 12, 15, 16, 31, 32, 40, 51, 63):
         ncp = p + int(rng.integers(1, 6))
         degs.append(p)
         knots.append(synth.random_clamped_knots(rng, p, ncp))

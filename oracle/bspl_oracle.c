@@ -201,9 +201,15 @@ static void curve_eval(int p, const double* U, int m, const double* P, const dou
     }
 }
 
-/* surface S(u,v) with partials; P is [nu][nv][3] row-major, index i along u */
+/* surface S(u,v) with partials; P is [nu][nv][3] row-major, index i along u.
+ * wt: NULL for a non-rational surface, else the positive weights [nu][nv]
+ * of a rational one: S = A/W with A, W the sums over (w P, w), and the
+ * quotient rule
+ *   S_u  = (A_u - W_u S)/W,                 S_v  = (A_v - W_v S)/W,
+ *   S_uu = (A_uu - 2 W_u S_u - W_uu S)/W,   S_vv = (A_vv - 2 W_v S_v - W_vv S)/W,
+ *   S_uv = (A_uv - W_u S_v - W_v S_u - W_uv S)/W. */
 static void surface_eval(int pu, int pv, const double* U, int mu, const double* V, int mv,
-                         const double* P, int nv, double u, double v, double* out /* [6][3]:
+                         const double* P, const double* wt, int nv, double u, double v, double* out /* [6][3]:
                          S, Su, Sv, Suu, Suv, Svv */)
 {
     double Nu0[ONP + 1], Nu1[ONP + 1], Nu2[ONP + 1];
@@ -211,15 +217,36 @@ static void surface_eval(int pu, int pv, const double* U, int mu, const double* 
     int qu = find_span(U, mu, pu, u), qv = find_span(V, mv, pv, v);
     cdb_basis_ders(U, qu, pu, u, Nu0, Nu1, Nu2);
     cdb_basis_ders(V, qv, pv, v, Nv0, Nv1, Nv2);
-    for (int k = 0; k < 18; ++k) out[k] = 0.0;
+    double A[18], W[6];
+    for (int k = 0; k < 18; ++k) A[k] = 0.0;
+    for (int k = 0; k < 6; ++k) W[k] = 0.0;
     for (int a = 0; a <= pu; ++a) {
         for (int b = 0; b <= pv; ++b) {
-            const double* Pij = P + 3 * ((int64_t)(qu - pu + a) * nv + (qv - pv + b));
+            int64_t ij = (int64_t)(qu - pu + a) * nv + (qv - pv + b);
+            const double* Pij = P + 3 * ij;
+            double wij = wt ? wt[ij] : 1.0;
             double w[6] = { Nu0[a] * Nv0[b], Nu1[a] * Nv0[b], Nu0[a] * Nv1[b],
                             Nu2[a] * Nv0[b], Nu1[a] * Nv1[b], Nu0[a] * Nv2[b] };
-            for (int k = 0; k < 6; ++k)
-                for (int c = 0; c < 3; ++c) out[3 * k + c] += w[k] * Pij[c];
+            for (int k = 0; k < 6; ++k) {
+                for (int c = 0; c < 3; ++c) A[3 * k + c] += wt ? w[k] * wij * Pij[c] : w[k] * Pij[c];
+                W[k] += w[k] * wij;
+            }
         }
+    }
+    if (!wt) {
+        memcpy(out, A, sizeof(A));
+        return;
+    }
+    for (int c = 0; c < 3; ++c) {
+        double S = A[c] / W[0];
+        double Su = (A[3 + c] - W[1] * S) / W[0];
+        double Sv = (A[6 + c] - W[2] * S) / W[0];
+        out[c] = S;
+        out[3 + c] = Su;
+        out[6 + c] = Sv;
+        out[9 + c] = (A[9 + c] - 2.0 * W[1] * Su - W[3] * S) / W[0];
+        out[12 + c] = (A[12 + c] - W[1] * Sv - W[2] * Su - W[4] * S) / W[0];
+        out[15 + c] = (A[15 + c] - 2.0 * W[2] * Sv - W[5] * S) / W[0];
     }
 }
 
@@ -243,17 +270,18 @@ int orc_eval_curves(int64_t n, const int32_t* deg, const int64_t* koff, const do
     return ORC_OK;
 }
 
+/* w: NULL (non-rational) or the weights [coff[n]] of every control point */
 int orc_eval_surfaces(int64_t n, const int32_t* pu, const int32_t* pv, const int32_t* nu,
                       const int32_t* nv, const int64_t* kuoff, const double* ku,
                       const int64_t* kvoff, const double* kv, const int64_t* coff,
-                      const double* cps, int64_t nq, const int32_t* qs, const double* uv,
+                      const double* cps, const double* w, int64_t nq, const int32_t* qs, const double* uv,
                       double* out /* [nq][6][3] */)
 {
     for (int64_t k = 0; k < nq; ++k) {
         int64_t s = qs[k];
         if (s < 0 || s >= n) return ORC_EINVAL;
-        surface_eval(pu[s], pv[s], ku + kuoff[s], nu[s] - 1, kv + kvoff[s], nv[s] - 1,
-                     cps + 3 * coff[s], nv[s], uv[2 * k], uv[2 * k + 1], out + 18 * k);
+        surface_eval(pu[s], pv[s], ku + kuoff[s], nu[s] - 1, kv + kvoff[s], nv[s] - 1, cps + 3 * coff[s],
+                     w ? w + coff[s] : NULL, nv[s], uv[2 * k], uv[2 * k + 1], out + 18 * k);
     }
     return ORC_OK;
 }
@@ -1484,12 +1512,13 @@ typedef struct {
     const double* V;
     const double* P;
     const double* q;
+    const double* w; /* NULL: non-rational */
 } surf_prob;
 
 static double sdist(const surf_prob* B, double u, double v, double* g, double* H)
 {
     double o[18];
-    surface_eval(B->pu, B->pv, B->U, B->mu, B->V, B->mv, B->P, B->nv, u, v, o);
+    surface_eval(B->pu, B->pv, B->U, B->mu, B->V, B->mv, B->P, B->w, B->nv, u, v, o);
     double d[3] = { o[0] - B->q[0], o[1] - B->q[1], o[2] - B->q[2] };
     double D = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (g) {
@@ -1600,6 +1629,76 @@ static void surf_deriv_bounds(const surf_prob* B, int qu, int qv, double* Vu, do
     }
 #undef PT
     *Vu = vu; *Vv = vv; *Auu = au; *Avv = av;
+}
+
+/* the same bounds for a rational surface S = A/W on span pair (qu, qv):
+ * with the span pair's points relative to P_r = P_{qu-pu, qv-pv} (which
+ * changes no derivative), S - P_r = A/W with A = sum N w (P - P_r), and the
+ * quotient rule gives, along u (v alike),
+ *   |S_u|  <= (|A_u| + |W_u| r) / w_min,
+ *   |S_uu| <= (|A_uu| + 2 |W_u| |S_u| + |W_uu| r) / w_min,
+ * r = max |P - P_r| over the span pair's points (S is a convex combination
+ * of them), w_min their smallest weight, and |A_u|, |A_uu|, |W_u|, |W_uu|
+ * bounded by the norms of the derivative control nets of the homogeneous
+ * points (w (P - P_r), w), as in surf_deriv_bounds. */
+static void rsurf_deriv_bounds(const surf_prob* B, int qu, int qv, double* Vu, double* Vv, double* Auu,
+                               double* Avv)
+{
+    int pu = B->pu, pv = B->pv;
+    const double* U = B->U;
+    const double* V = B->V;
+#define PT(i, j) (B->P + 3 * ((int64_t)(i) * B->nv + (j)))
+#define WT(i, j) (B->w[(int64_t)(i) * B->nv + (j)])
+    const double* Pr = PT(qu - pu, qv - pv);
+    double r = 0.0, wmin = INFINITY;
+    for (int i = qu - pu; i <= qu; ++i)
+        for (int j = qv - pv; j <= qv; ++j) {
+            double d[3] = { PT(i, j)[0] - Pr[0], PT(i, j)[1] - Pr[1], PT(i, j)[2] - Pr[2] };
+            double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (nd > r) r = nd;
+            if (WT(i, j) < wmin) wmin = WT(i, j);
+        }
+    /* a1/w1: first derivative net norms (numerator / weight), a2/w2: second;
+     * index 0 along u, 1 along v */
+    double a1[2] = { 0, 0 }, w1[2] = { 0, 0 }, a2[2] = { 0, 0 }, w2[2] = { 0, 0 };
+    for (int dir = 0; dir < 2; ++dir) {
+        int p = dir == 0 ? pu : pv, q = dir == 0 ? qu : qv;
+        const double* K = dir == 0 ? U : V;
+        int olo = dir == 0 ? qv - pv : qu - pu, ohi = dir == 0 ? qv : qu;
+        for (int o = olo; o <= ohi; ++o) {
+            double H[SNP][4], D1[SNP][4];
+            for (int i = q - p; i <= q; ++i) {
+                int ii = dir == 0 ? i : o, jj = dir == 0 ? o : i;
+                double wij = WT(ii, jj);
+                for (int c = 0; c < 3; ++c) H[i - (q - p)][c] = wij * (PT(ii, jj)[c] - Pr[c]);
+                H[i - (q - p)][3] = wij;
+            }
+            for (int i = q - p + 1; i <= q; ++i) {
+                int k = i - (q - p);
+                double den = K[i + p] - K[i];
+                for (int c = 0; c < 4; ++c) D1[k][c] = den != 0.0 ? p * (H[k][c] - H[k - 1][c]) / den : 0.0;
+                double na = sqrt(D1[k][0] * D1[k][0] + D1[k][1] * D1[k][1] + D1[k][2] * D1[k][2]);
+                if (na > a1[dir]) a1[dir] = na;
+                if (fabs(D1[k][3]) > w1[dir]) w1[dir] = fabs(D1[k][3]);
+            }
+            for (int i = q - p + 2; i <= q; ++i) {
+                int k = i - (q - p);
+                double den = K[i + p - 1] - K[i];
+                if (den == 0.0) continue;
+                double x[4];
+                for (int c = 0; c < 4; ++c) x[c] = (p - 1) * (D1[k][c] - D1[k - 1][c]) / den;
+                double na = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+                if (na > a2[dir]) a2[dir] = na;
+                if (fabs(x[3]) > w2[dir]) w2[dir] = fabs(x[3]);
+            }
+        }
+    }
+#undef PT
+#undef WT
+    *Vu = (a1[0] + w1[0] * r) / wmin;
+    *Vv = (a1[1] + w1[1] * r) / wmin;
+    *Auu = (a2[0] + 2.0 * w1[0] * *Vu + w2[0] * r) / wmin;
+    *Avv = (a2[1] + 2.0 * w1[1] * *Vv + w2[1] * r) / wmin;
 }
 
 typedef struct { double u0, u1, v0, v1, D[4]; int depth; } cell_t; /* D: (u0,v0),(u1,v0),(u0,v1),(u1,v1) */
@@ -1754,7 +1853,8 @@ static void project_surface_one(const surf_prob* B, double* uv_out, double* d_ou
             for (int qv = B->pv; qv <= B->mv; ++qv) {
                 if (!(B->V[qv] < B->V[qv + 1])) continue;
                 double Vu, Vv, Au, Av;
-                surf_deriv_bounds(B, qu, qv, &Vu, &Vv, &Au, &Av);
+                if (B->w) rsurf_deriv_bounds(B, qu, qv, &Vu, &Vv, &Au, &Av);
+                else surf_deriv_bounds(B, qu, qv, &Vu, &Vv, &Au, &Av);
                 for (int a = 0; a < OSAMP2; ++a)
                     for (int b = 0; b < OSAMP2; ++b) {
                         int i = i0 + a, jj = j0 + b;
@@ -1799,10 +1899,11 @@ static void project_surface_one(const surf_prob* B, double* uv_out, double* d_ou
     free(us); free(vs); free(Dg);
 }
 
+/* w: NULL (non-rational) or the weights of every control point of the set */
 int orc_project_surfaces(int64_t n, const int32_t* pu, const int32_t* pv, const int32_t* nu,
                          const int32_t* nv, const int64_t* kuoff, const double* ku,
                          const int64_t* kvoff, const double* kv, const int64_t* coff,
-                         const double* cps, int64_t nq, const int32_t* qs, const double* qxyz,
+                         const double* cps, const double* w, int64_t nq, const int32_t* qs, const double* qxyz,
                          double* uv_out, double* d_out, int nthreads)
 {
     for (int64_t k = 0; k < nq; ++k)
@@ -1816,8 +1917,20 @@ int orc_project_surfaces(int64_t n, const int32_t* pu, const int32_t* pv, const 
     for (int64_t k = 0; k < nq; ++k) {
         int64_t s = qs[k];
         surf_prob B = { pu[s], pv[s], nu[s] - 1, nv[s] - 1, nv[s], ku + kuoff[s], kv + kvoff[s],
-                        cps + 3 * coff[s], qxyz + 3 * k };
+                        cps + 3 * coff[s], qxyz + 3 * k, w ? w + coff[s] : NULL };
         project_surface_one(&B, uv_out + 2 * k, &d_out[k]);
     }
+    return ORC_OK;
+}
+
+/* exported for the pins: the bounds of |S_u|, |S_v|, |S_uu|, |S_vv| on span
+ * pair (qu, qv) of one surface (w NULL: non-rational) */
+int orc_surf_deriv_bounds(int pu, int pv, const double* U, int nu, const double* V, int nv, const double* P,
+                          const double* w, int qu, int qv, double* out /* Vu, Vv, Auu, Avv */)
+{
+    if (pu < 1 || pv < 1 || pu > SMAXP || pv > SMAXP || qu < pu || qu >= nu || qv < pv || qv >= nv) return ORC_EINVAL;
+    surf_prob B = { pu, pv, nu - 1, nv - 1, nv, U, V, P, NULL, w };
+    if (w) rsurf_deriv_bounds(&B, qu, qv, out, out + 1, out + 2, out + 3);
+    else surf_deriv_bounds(&B, qu, qv, out, out + 1, out + 2, out + 3);
     return ORC_OK;
 }

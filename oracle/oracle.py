@@ -42,7 +42,7 @@ def lib():
             L.orc_basis.argtypes = [C.c_int, _f64p, I64, D, C.POINTER(C.c_int), _f64p]
             L.orc_eval_curves.argtypes = [I64, _i32p, _i64p, _f64p, _i64p, _f64p, vp, I64, _i32p, _f64p, _f64p]
             L.orc_eval_surfaces.argtypes = [I64, _i32p, _i32p, _i32p, _i32p, _i64p, _f64p, _i64p, _f64p,
-                                            _i64p, _f64p, I64, _i32p, _f64p, _f64p]
+                                            _i64p, _f64p, vp, I64, _i32p, _f64p, _f64p]
             L.orc_boehm_bezier.argtypes = [C.c_int, _f64p, I64, _f64p, I64, _f64p, I64, C.POINTER(I64)]
             L.orc_span_bezier.argtypes = [C.c_int, _f64p, I64, _f64p, I64, _f64p, I64, C.POINTER(I64)]
             L.orc_span_blossom.argtypes = [C.c_int, _f64p, I64, _f64p, I64, _f64p, I64, C.POINTER(I64)]
@@ -67,7 +67,9 @@ def lib():
             L.orc_curve_deriv_bounds.argtypes = [C.c_int, _f64p, I64, _f64p, vp, C.c_int, C.POINTER(D),
                                                  C.POINTER(D)]
             L.orc_project_surfaces.argtypes = [I64, _i32p, _i32p, _i32p, _i32p, _i64p, _f64p, _i64p, _f64p,
-                                               _i64p, _f64p, I64, _i32p, _f64p, _f64p, _f64p, C.c_int]
+                                               _i64p, _f64p, vp, I64, _i32p, _f64p, _f64p, _f64p, C.c_int]
+            L.orc_surf_deriv_bounds.argtypes = [C.c_int, C.c_int, _f64p, C.c_int, _f64p, C.c_int, _f64p, vp,
+                                                C.c_int, C.c_int, _f64p]
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -84,8 +86,8 @@ def _curve_args(cs):
 
 def _weights(cs):
     """(array kept alive by the caller, pointer or None): the weights of a
-    rational curve set (attribute ``weights``, one per control point), or
-    None for a non-rational one."""
+    rational curve or surface set (attribute ``weights``, one per control
+    point), or None for a non-rational one."""
     w = getattr(cs, "weights", None)
     if w is None:
         return None, None
@@ -133,7 +135,8 @@ def eval_surfaces(ss, qs, uv):
     qs = _a(qs, np.int32)
     uv = _a(uv, np.float64).reshape(-1, 2)
     out = np.zeros((len(qs), 6, 3))
-    rc = lib().orc_eval_surfaces(*_surf_args(ss), len(qs), qs, uv.reshape(-1), out.reshape(-1))
+    w, wp = _weights(ss)
+    rc = lib().orc_eval_surfaces(*_surf_args(ss), wp, len(qs), qs, uv.reshape(-1), out.reshape(-1))
     assert rc == OK, rc
     return tuple(out[:, k] for k in range(6))
 
@@ -347,9 +350,24 @@ def project_surfaces(ss, qs, q, nthreads=0):
     q = _a(q, np.float64).reshape(-1, 3)
     uv = np.zeros((len(qs), 2))
     d = np.zeros(len(qs))
-    rc = lib().orc_project_surfaces(*_surf_args(ss), len(qs), qs, q.reshape(-1), uv.reshape(-1), d, int(nthreads))
+    w, wp = _weights(ss)
+    rc = lib().orc_project_surfaces(*_surf_args(ss), wp, len(qs), qs, q.reshape(-1), uv.reshape(-1), d,
+                                    int(nthreads))
     assert rc == OK, rc
     return uv, d
+
+
+def surf_deriv_bounds(pu, pv, U, V, P, w, qu, qv):
+    """(Vu, Vv, Auu, Avv): the oracle's bounds of |S_u|, |S_v|, |S_uu|, |S_vv|
+    on span pair (qu, qv); P [nu][nv][3], w [nu][nv] or None."""
+    P = _a(P, np.float64)
+    nu, nv = P.shape[0], P.shape[1]
+    wa = None if w is None else _a(w, np.float64).reshape(-1)
+    out = np.zeros(4)
+    rc = lib().orc_surf_deriv_bounds(pu, pv, _a(U, np.float64), nu, _a(V, np.float64), nv, P.reshape(-1),
+                                     None if wa is None else wa.ctypes.data, int(qu), int(qv), out)
+    assert rc == OK, rc
+    return tuple(out)
 
 
 def curve_diag(cs):

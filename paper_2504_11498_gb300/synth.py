@@ -74,11 +74,13 @@ class CurveSet:
 
 @dataclass
 class SurfaceSet:
-    """CSR-packed non-rational tensor-product B-spline surfaces.
+    """CSR-packed tensor-product B-spline surfaces.
 
     deg_u, deg_v, n_u, n_v: [n] int32.  knot_u_off/knot_v_off [n+1] int64
     into knots_u/knots_v.  cp_off [n+1] int64 into cps, each surface's net
-    stored row-major [n_u][n_v][3] (first index along u).
+    stored row-major [n_u][n_v][3] (first index along u).  weights: None
+    (non-rational), or [ncp total] float64, one positive weight per control
+    point in the same order (rational surfaces).
     """
 
     deg_u: np.ndarray
@@ -91,10 +93,17 @@ class SurfaceSet:
     knots_v: np.ndarray
     cp_off: np.ndarray
     cps: np.ndarray
+    weights: np.ndarray | None = None
 
     @property
     def n(self) -> int:
         return int(self.deg_u.shape[0])
+
+    def surface_weights(self, s: int):
+        """[n_u][n_v] weights of surface s, or None."""
+        if self.weights is None:
+            return None
+        return self.weights[self.cp_off[s]:self.cp_off[s + 1]].reshape(int(self.n_u[s]), int(self.n_v[s]))
 
     def surface(self, s: int):
         U = self.knots_u[self.knot_u_off[s]:self.knot_u_off[s + 1]]
@@ -103,8 +112,10 @@ class SurfaceSet:
         return int(self.deg_u[s]), int(self.deg_v[s]), U, V, P
 
     def subset(self, idx) -> "SurfaceSet":
-        parts = [self.surface(int(s)) for s in np.asarray(idx, dtype=np.int64)]
-        return pack_surfaces(*zip(*parts))
+        idx = np.asarray(idx, dtype=np.int64)
+        parts = [self.surface(int(s)) for s in idx]
+        w = None if self.weights is None else [self.surface_weights(int(s)) for s in idx]
+        return pack_surfaces(*zip(*parts), weight_list=w)
 
 
 def pack_curves(degrees, knot_list, cp_list, weight_list=None) -> CurveSet:
@@ -126,7 +137,7 @@ def pack_curves(degrees, knot_list, cp_list, weight_list=None) -> CurveSet:
     return CurveSet(degrees, knot_off, np.ascontiguousarray(knots), cp_off, np.ascontiguousarray(cps), w)
 
 
-def pack_surfaces(deg_u, deg_v, knots_u, knots_v, nets) -> SurfaceSet:
+def pack_surfaces(deg_u, deg_v, knots_u, knots_v, nets, weight_list=None) -> SurfaceSet:
     nets = [np.asarray(P, dtype=np.float64) for P in nets]
     n_u = np.array([P.shape[0] for P in nets], dtype=np.int32)
     n_v = np.array([P.shape[1] for P in nets], dtype=np.int32)
@@ -142,6 +153,8 @@ def pack_surfaces(deg_u, deg_v, knots_u, knots_v, nets) -> SurfaceSet:
         offs([len(k) for k in knots_v]), np.concatenate([np.asarray(k, np.float64) for k in knots_v]),
         offs([P.shape[0] * P.shape[1] for P in nets]),
         np.ascontiguousarray(np.concatenate([P.reshape(-1, 3) for P in nets])),
+        None if weight_list is None else np.ascontiguousarray(
+            np.concatenate([np.asarray(w, np.float64).reshape(-1) for w in weight_list])),
     )
 
 
@@ -536,3 +549,57 @@ def nurbs_edge_set(seed: int = 7):
     w[0], w[-1] = 1.0, 50.0
     add(4, random_clamped_knots(rng, 4, 10), rng.uniform(0, 1, (10, 3)), w)
     return pack_curves(degs, knots, cps, ws)
+
+
+def nurbs_surface_set(seed: int = 8, n_surf: int = 64, n_proj: int = 10_000, deg_range=(2, 5), n_range=(8, 16),
+                      w_range=(0.5, 2.0)):
+    """The surface_set recipe (sinusoid nets on a grid, clamped non-uniform
+    knots) with one weight per control point, log-uniform in w_range:
+    rational surfaces; projection queries as for surface_set."""
+    ss, sq = surface_set(seed=seed, n_surf=n_surf, n_proj=n_proj, n_inv=0, deg_range=deg_range, n_range=n_range)
+    rng = np.random.default_rng(seed + 1)
+    ss.weights = np.exp(rng.uniform(np.log(w_range[0]), np.log(w_range[1]), size=len(ss.cps)))
+    return ss, sq
+
+
+def nurbs_cylinders(seed: int = 9, n_surf: int = 8, n_proj: int = 2000):
+    """Open cylinders as rational surfaces: along u the full circle of
+    nurbs_circles (degree 2, nine control points, corner weights
+    sqrt(2)/2), along v a straight segment (degree 1) of height h along the
+    axis.  Random centre ~U[0,1]^3, radius ~U[0.05, 0.5], height
+    ~U[0.2, 1], axis direction.  Returns (ss, queries [n][3], surface index
+    [n], centre [n_surf][3], axis [n_surf][3], radius, height); queries lie
+    at heights ~U[0.1 h, 0.9 h] and radial distances ~U[0, 2 r] from the
+    axis, so that the nearest point is on the cylinder's side."""
+    rng = np.random.default_rng(seed)
+    s2 = np.sqrt(0.5)
+    unit = np.array([[1, 0], [1, 1], [0, 1], [-1, 1], [-1, 0], [-1, -1], [0, -1], [1, -1], [1, 0]], np.float64)
+    wc = np.array([1, s2, 1, s2, 1, s2, 1, s2, 1], np.float64)
+    U = np.array([0, 0, 0, 0.25, 0.25, 0.5, 0.5, 0.75, 0.75, 1, 1, 1], np.float64)
+    V = np.array([0, 0, 1, 1], np.float64)
+    centre = rng.uniform(0.0, 1.0, size=(n_surf, 3))
+    radius = rng.uniform(0.05, 0.5, size=n_surf)
+    height = rng.uniform(0.2, 1.0, size=n_surf)
+    axis = np.zeros((n_surf, 3))
+    nets, ws, frames = [], [], []
+    for c in range(n_surf):
+        a = rng.normal(size=3)
+        a /= np.linalg.norm(a)
+        e1 = rng.normal(size=3)
+        e1 -= (e1 @ a) * a
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(a, e1)
+        axis[c] = a
+        ring = centre[c] + radius[c] * (unit[:, :1] * e1 + unit[:, 1:] * e2)   # [9][3]
+        nets.append(np.stack([ring, ring + height[c] * a], axis=1))            # [9][2][3]
+        ws.append(np.stack([wc, wc], axis=1))
+        frames.append((e1, e2))
+    ss = pack_surfaces([2] * n_surf, [1] * n_surf, [U] * n_surf, [V] * n_surf, nets, ws)
+    sidx = rng.integers(0, n_surf, size=n_proj).astype(np.int32)
+    hq = rng.uniform(0.1, 0.9, size=n_proj) * height[sidx]
+    rq = rng.uniform(0.0, 2.0, size=n_proj) * radius[sidx]
+    ang = rng.uniform(0.0, 2 * np.pi, size=n_proj)
+    e1 = np.array([frames[c][0] for c in sidx])
+    e2 = np.array([frames[c][1] for c in sidx])
+    q = centre[sidx] + hq[:, None] * axis[sidx] + rq[:, None] * (np.cos(ang)[:, None] * e1 + np.sin(ang)[:, None] * e2)
+    return ss, q, sidx, centre, axis, radius, height

@@ -1166,11 +1166,228 @@ static void surf_span_bezier(int pu, int pv, const double* U, int qu, const doub
     free(T1);
 }
 
+/* ------------------------------------------------------------------ */
+/* rational surfaces: homogeneous decomposition                          */
+/* ------------------------------------------------------------------ */
+/* The curves' reading carried to tensor-product surfaces: the span pair's
+ * piece is the rational tensor Bezier of the homogeneous net H_ab = (W_ab
+ * Q_ab, W_ab) that the matrix route gives for (w P, w); a node is replaced
+ * by its bicubic Hermite patch (corner values, first partials and twists of
+ * the rational piece), accepted when the certified bound of Eq. below meets
+ * the tolerance, else halved along the direction whose lines deviate more
+ * from their Hermite cubics. */
+
+#define HNETI(a, b) (((a) * SNP + (b)) * 4)
+#define HNETN (SNP * SNP * 4)
+#define ENP (SNP + 3)                        /* points per direction after elevation by 3 */
+#define ENETI(a, b) (((a) * ENP + (b)) * 4)
+
+/* homogeneous net H of span pair (qu, qv): the matrix route applied to the
+ * numerator points wP [nu][nv][3] and to (w, 0, 0) */
+static void rsurf_span_bezier(int pu, int pv, const double* U, int qu, const double* V, int qv, const double* wP,
+                              const double* w3, int nv, double* H)
+{
+    double* A = (double*)malloc(sizeof(double) * NETN);
+    double* B = (double*)malloc(sizeof(double) * NETN);
+    surf_span_bezier(pu, pv, U, qu, V, qv, wP, nv, A);
+    surf_span_bezier(pu, pv, U, qu, V, qv, w3, nv, B);
+    for (int a = 0; a <= pu; ++a)
+        for (int b = 0; b <= pv; ++b) {
+            for (int c = 0; c < 3; ++c) H[HNETI(a, b) + c] = A[NETI(a, b) + c];
+            H[HNETI(a, b) + 3] = B[NETI(a, b)];
+        }
+    free(A); free(B);
+}
+
+/* value, u- and v-partials and twist of the rational piece at corner (ca,
+ * cb) in {0,1}^2 of its [0,1]^2 parameters: from A, W and their partials at
+ * the corner (differences of the homogeneous net, times the degrees) by
+ * the quotient rule */
+static void rsurf_corner(int pu, int pv, const double* H, int ca, int cb, double* S, double* Su, double* Sv,
+                         double* Suv)
+{
+    int a0 = ca ? pu : 0, a1 = ca ? pu - 1 : 1, b0 = cb ? pv : 0, b1 = cb ? pv - 1 : 1;
+    double su = ca ? -1.0 : 1.0, sv = cb ? -1.0 : 1.0; /* d/du = pu (H_a1 - H_a0) at u = 0, pu (H_a0 - H_a1) at 1 */
+    double A[4], Au[4], Av[4], Auv[4];
+    for (int c = 0; c < 4; ++c) {
+        double h00 = H[HNETI(a0, b0) + c], h10 = H[HNETI(a1, b0) + c];
+        double h01 = H[HNETI(a0, b1) + c], h11 = H[HNETI(a1, b1) + c];
+        A[c] = h00;
+        Au[c] = su * pu * (h10 - h00);
+        Av[c] = sv * pv * (h01 - h00);
+        Auv[c] = su * sv * (double)pu * (double)pv * (((h11 - h10) - h01) + h00);
+    }
+    for (int c = 0; c < 3; ++c) {
+        S[c] = A[c] / A[3];
+        Su[c] = (Au[c] - Au[3] * S[c]) / A[3];
+        Sv[c] = (Av[c] - Av[3] * S[c]) / A[3];
+        Suv[c] = (((Auv[c] - Au[3] * Sv[c]) - Av[3] * Su[c]) - Auv[3] * S[c]) / A[3];
+    }
+}
+
+/* the bicubic Hermite patch R [4][4][3] (index i along u): corner values,
+ * first partials over 3 and twists over 9 placed in the Bezier net (the
+ * corner's point, its neighbours along u and v, and the inner point) */
+static void rsurf_hermite(int pu, int pv, const double* H, double* R)
+{
+    for (int ca = 0; ca < 2; ++ca)
+        for (int cb = 0; cb < 2; ++cb) {
+            double S[3], Su[3], Sv[3], Suv[3];
+            rsurf_corner(pu, pv, H, ca, cb, S, Su, Sv, Suv);
+            double su = ca ? -1.0 : 1.0, sv = cb ? -1.0 : 1.0;
+            int i0 = ca ? 3 : 0, i1 = ca ? 2 : 1, j0 = cb ? 3 : 0, j1 = cb ? 2 : 1;
+            for (int c = 0; c < 3; ++c) {
+                R[(i0 * 4 + j0) * 3 + c] = S[c];
+                R[(i1 * 4 + j0) * 3 + c] = S[c] + su * (Su[c] / 3.0);
+                R[(i0 * 4 + j1) * 3 + c] = S[c] + sv * (Sv[c] / 3.0);
+                R[(i1 * 4 + j1) * 3 + c] = ((S[c] + su * (Su[c] / 3.0)) + sv * (Sv[c] / 3.0)) + su * sv * (Suv[c] / 9.0);
+            }
+        }
+}
+
+/* elevate the line of n+1 homogeneous points at stride s by three degrees
+ * (into the same line, which must have room for n+4 points) */
+static void elevate3_line(int n, double* L, int s)
+{
+    double a[(ENP + 1) * 4], b[(ENP + 1) * 4];
+    for (int i = 0; i <= n; ++i)
+        for (int c = 0; c < 4; ++c) a[4 * i + c] = L[i * s + c];
+    for (int k = n; k < n + 3; ++k) {
+        elevate_nc(k, a, b, 4, 4);
+        memcpy(a, b, sizeof(double) * 4 * (size_t)(k + 2));
+    }
+    for (int i = 0; i <= n + 3; ++i)
+        for (int c = 0; c < 4; ++c) L[i * s + c] = a[4 * i + c];
+}
+
+/* certified bound of max |S - R|^2 over the piece: S - R = (A - W R)/W with
+ * A - W R of degrees (pu + 3, pv + 3); its Bernstein coefficients are A's
+ * elevated three times in each direction minus the product
+ *   (W R)_kl = sum_ij [C(pu,i) C(3,k-i) / C(pu+3,k)] [C(pv,j) C(3,l-j) / C(pv+3,l)] W_ij R_{k-i,l-j};
+ * the largest coefficient norm bounds |A - W R| and W >= min W_ij > 0. */
+static double rsurf_bound2(int pu, int pv, const double* H, const double* R)
+{
+    double* E = (double*)calloc((size_t)ENP * ENP * 4, sizeof(double));
+    double wmin = INFINITY;
+    for (int a = 0; a <= pu; ++a)
+        for (int b = 0; b <= pv; ++b) {
+            for (int c = 0; c < 4; ++c) E[ENETI(a, b) + c] = H[HNETI(a, b) + c];
+            if (H[HNETI(a, b) + 3] < wmin) wmin = H[HNETI(a, b) + 3];
+        }
+    for (int b = 0; b <= pv; ++b) elevate3_line(pu, E + ENETI(0, b), ENP * 4);
+    for (int a = 0; a <= pu + 3; ++a) elevate3_line(pv, E + ENETI(a, 0), 4);
+    double bmax = 0.0;
+    for (int k = 0; k <= pu + 3; ++k)
+        for (int l = 0; l <= pv + 3; ++l) {
+            double sm[3] = { 0.0, 0.0, 0.0 };
+            for (int i = (k - 3 > 0 ? k - 3 : 0); i <= (k < pu ? k : pu); ++i) {
+                double cu = (binom(pu, i) * binom(3, k - i)) / binom(pu + 3, k);
+                for (int j = (l - 3 > 0 ? l - 3 : 0); j <= (l < pv ? l : pv); ++j) {
+                    double cv = (binom(pv, j) * binom(3, l - j)) / binom(pv + 3, l);
+                    double cw = (cu * cv) * H[HNETI(i, j) + 3];
+                    const double* r = R + ((k - i) * 4 + (l - j)) * 3;
+                    for (int c = 0; c < 3; ++c) sm[c] = sm[c] + cw * r[c];
+                }
+            }
+            double dx = E[ENETI(k, l)] - sm[0], dy = E[ENETI(k, l) + 1] - sm[1], dz = E[ENETI(k, l) + 2] - sm[2];
+            double d2 = (dx * dx + dy * dy) + dz * dz;
+            if (d2 > bmax) bmax = d2;
+        }
+    free(E);
+    return bmax / (wmin * wmin);
+}
+
+/* split direction: the one whose lines (the rational curves of the net along
+ * it) deviate more from their Hermite cubics, by the curves' bound (ties:
+ * u) */
+static int rsurf_split_dir(int pu, int pv, const double* H)
+{
+    double du = 0.0, dv = 0.0;
+    double line[(SNP + 1) * 4], R[12];
+    for (int b = 0; b <= pv; ++b) {
+        for (int a = 0; a <= pu; ++a)
+            for (int c = 0; c < 4; ++c) line[4 * a + c] = H[HNETI(a, b) + c];
+        rhermite(pu, line, R);
+        double e = rbound2(pu, line, R);
+        if (e > du) du = e;
+    }
+    for (int a = 0; a <= pu; ++a) {
+        for (int b = 0; b <= pv; ++b)
+            for (int c = 0; c < 4; ++c) line[4 * b + c] = H[HNETI(a, b) + c];
+        rhermite(pv, line, R);
+        double e = rbound2(pv, line, R);
+        if (e > dv) dv = e;
+    }
+    return du >= dv ? 0 : 1;
+}
+
+static void rsurf_node(surf_ctx* X, const double* H, int Lu, int64_t ku, int Lv, int64_t kv)
+{
+    int pu = X->pu, pv = X->pv;
+    double R[48];
+    rsurf_hermite(pu, pv, H, R);
+    int accept = rsurf_bound2(pu, pv, H, R) <= X->thr2;
+    if (!accept && (Lu + Lv >= ODEPTH || X->count - X->span_first >= OLEAFCAP)) { accept = 1; X->notconv = 1; }
+    if (accept) {
+        if (X->count < X->cap && X->ctrl) {
+            memcpy(X->ctrl + 48 * X->count, R, sizeof(R));
+            double* pr = X->prange + 4 * X->count;
+            pr[0] = dyadic_t(X->u0, X->u1, ku, Lu);
+            pr[1] = dyadic_t(X->u0, X->u1, ku + 1, Lu);
+            pr[2] = dyadic_t(X->v0, X->v1, kv, Lv);
+            pr[3] = dyadic_t(X->v0, X->v1, kv + 1, Lv);
+        }
+        X->count++;
+        if (Lu + Lv > X->maxdepth) X->maxdepth = Lu + Lv;
+        return;
+    }
+    int dir = rsurf_split_dir(pu, pv, H);
+    double* A = (double*)malloc(sizeof(double) * HNETN);
+    double* B = (double*)malloc(sizeof(double) * HNETN);
+    if (dir == 0) {
+        for (int j = 0; j <= pv; ++j) halve_nc(pu, H + HNETI(0, j), SNP * 4, 4, A + HNETI(0, j), B + HNETI(0, j));
+        rsurf_node(X, A, Lu + 1, 2 * ku, Lv, kv);
+        rsurf_node(X, B, Lu + 1, 2 * ku + 1, Lv, kv);
+    } else {
+        for (int i = 0; i <= pu; ++i) halve_nc(pv, H + HNETI(i, 0), 4, 4, A + HNETI(i, 0), B + HNETI(i, 0));
+        rsurf_node(X, A, Lu, ku, Lv + 1, 2 * kv);
+        rsurf_node(X, B, Lu, ku, Lv + 1, 2 * kv + 1);
+    }
+    free(A); free(B);
+}
+
+/* exported for the pins; H compact [pu+1][pv+1][4] */
+static void compact_to_hnet(int pu, int pv, const double* Hc, double* H)
+{
+    for (int a = 0; a <= pu; ++a)
+        for (int b = 0; b <= pv; ++b)
+            for (int c = 0; c < 4; ++c) H[HNETI(a, b) + c] = Hc[((a * (pv + 1)) + b) * 4 + c];
+}
+int orc_rsurf_hermite(int pu, int pv, const double* Hc, double* R)
+{
+    if (pu < 1 || pv < 1 || pu > SMAXP || pv > SMAXP) return ORC_EINVAL;
+    double* H = (double*)calloc(HNETN, sizeof(double));
+    compact_to_hnet(pu, pv, Hc, H);
+    rsurf_hermite(pu, pv, H, R);
+    free(H);
+    return ORC_OK;
+}
+double orc_rsurf_bound2(int pu, int pv, const double* Hc, const double* R)
+{
+    double* H = (double*)calloc(HNETN, sizeof(double));
+    compact_to_hnet(pu, pv, Hc, H);
+    double b = rsurf_bound2(pu, pv, H, R);
+    free(H);
+    return b;
+}
+
+/* (w: NULL, or the weights of every control point of the set; a surface
+ * whose weights are all equal takes the non-rational route) */
 static int64_t decompose_one_surface(int64_t s, const int32_t* pu_, const int32_t* pv_, const int32_t* nu_,
                                      const int32_t* nv_, const int64_t* kuoff, const double* ku,
                                      const int64_t* kvoff, const double* kv, const int64_t* coff,
-                                     const double* cps, double tol_rel, int64_t first, int64_t cap,
-                                     double* ctrl, double* prange, int* maxdepth, int* notconv)
+                                     const double* cps, const double* w, double tol_rel, int64_t first,
+                                     int64_t cap, double* ctrl, double* prange, int* maxdepth, int* notconv)
 {
     int pu = pu_[s], pv = pv_[s], nu = nu_[s], nv = nv_[s];
     if (pu > SMAXP || pv > SMAXP) return -1;
@@ -1181,22 +1398,44 @@ static int64_t decompose_one_surface(int64_t s, const int32_t* pu_, const int32_
     if (!check_knots(pu, U, kuoff[s + 1] - kuoff[s], nu)) return -1;
     if (!check_knots(pv, V, kvoff[s + 1] - kvoff[s], nv)) return -1;
     for (int64_t i = 0; i < 3 * (int64_t)nu * nv; ++i) if (!isfinite(P[i])) return -1;
+    const double* ws = w ? w + coff[s] : NULL;
+    int rat = ws ? weights_kind(ws, (int64_t)nu * nv) : 0;
+    if (rat < 0) return -1;
     double thr = tol_rel * box_diag(P, (int64_t)nu * nv);
     surf_ctx X;
     X.pu = pu; X.pv = pv; X.thr2 = thr * thr; X.cap = cap; X.ctrl = ctrl; X.prange = prange;
     X.count = first; X.maxdepth = 0; X.notconv = 0;
-    double* Q = (double*)malloc(sizeof(double) * NETN);
+    double* Q = (double*)malloc(sizeof(double) * (rat ? HNETN : NETN));
+    double *wP = NULL, *w3 = NULL;
+    if (rat) {
+        int64_t np = (int64_t)nu * nv;
+        wP = (double*)malloc(sizeof(double) * 3 * (size_t)np);
+        w3 = (double*)malloc(sizeof(double) * 3 * (size_t)np);
+        for (int64_t i = 0; i < np; ++i) {
+            for (int c = 0; c < 3; ++c) wP[3 * i + c] = ws[i] * P[3 * i + c];
+            w3[3 * i] = ws[i];
+            w3[3 * i + 1] = 0.0;
+            w3[3 * i + 2] = 0.0;
+        }
+    }
     for (int qu = pu; qu <= nu - 1; ++qu) {
         if (!(U[qu] < U[qu + 1])) continue;
         for (int qv = pv; qv <= nv - 1; ++qv) {
             if (!(V[qv] < V[qv + 1])) continue;
-            surf_span_bezier(pu, pv, U, qu, V, qv, P, nv, Q);
             X.u0 = U[qu]; X.u1 = U[qu + 1]; X.v0 = V[qv]; X.v1 = V[qv + 1];
             X.span_first = X.count;
-            surf_node(&X, Q, 0, 0, 0, 0);
+            if (rat) {
+                rsurf_span_bezier(pu, pv, U, qu, V, qv, wP, w3, nv, Q);
+                rsurf_node(&X, Q, 0, 0, 0, 0);
+            } else {
+                surf_span_bezier(pu, pv, U, qu, V, qv, P, nv, Q);
+                surf_node(&X, Q, 0, 0, 0, 0);
+            }
         }
     }
     free(Q);
+    free(wP);
+    free(w3);
     *maxdepth = X.maxdepth;
     *notconv = X.notconv;
     return X.count - first;
@@ -1205,7 +1444,7 @@ static int64_t decompose_one_surface(int64_t s, const int32_t* pu_, const int32_
 int orc_decompose_surfaces(int64_t n, const int32_t* pu_, const int32_t* pv_, const int32_t* nu_,
                            const int32_t* nv_, const int64_t* kuoff, const double* ku,
                            const int64_t* kvoff, const double* kv, const int64_t* coff,
-                           const double* cps, double tol_rel, int64_t* seg_off, int64_t cap,
+                           const double* cps, const double* w, double tol_rel, int64_t* seg_off, int64_t cap,
                            double* ctrl, double* prange, int64_t* total, int* maxdepth)
 {
     int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -1213,7 +1452,7 @@ int orc_decompose_surfaces(int64_t n, const int32_t* pu_, const int32_t* pv_, co
 #pragma omp parallel for schedule(dynamic, 1) reduction(max : md) reduction(| : nc, bad)
     for (int64_t s = 0; s < n; ++s) {
         int m1 = 0, n1 = 0;
-        cnt[s] = decompose_one_surface(s, pu_, pv_, nu_, nv_, kuoff, ku, kvoff, kv, coff, cps, tol_rel, 0, 0,
+        cnt[s] = decompose_one_surface(s, pu_, pv_, nu_, nv_, kuoff, ku, kvoff, kv, coff, cps, w, tol_rel, 0, 0,
                                        NULL, NULL, &m1, &n1);
         if (cnt[s] < 0) bad = 1;
         if (m1 > md) md = m1;
@@ -1227,7 +1466,7 @@ int orc_decompose_surfaces(int64_t n, const int32_t* pu_, const int32_t* pv_, co
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t s = 0; s < n; ++s) {
             int m1, n1;
-            decompose_one_surface(s, pu_, pv_, nu_, nv_, kuoff, ku, kvoff, kv, coff, cps, tol_rel, seg_off[s], cap,
+            decompose_one_surface(s, pu_, pv_, nu_, nv_, kuoff, ku, kvoff, kv, coff, cps, w, tol_rel, seg_off[s], cap,
                                   ctrl, prange, &m1, &n1);
         }
     }

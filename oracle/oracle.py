@@ -55,8 +55,11 @@ def lib():
             L.orc_decompose_curves.argtypes = [I64, _i32p, _i64p, _f64p, _i64p, _f64p, vp, D, _i64p, I64, vp, vp,
                                                C.POINTER(I64), C.POINTER(C.c_int)]
             L.orc_decompose_surfaces.argtypes = [I64, _i32p, _i32p, _i32p, _i32p, _i64p, _f64p, _i64p, _f64p,
-                                                 _i64p, _f64p, D, _i64p, I64, vp, vp, C.POINTER(I64),
+                                                 _i64p, _f64p, vp, D, _i64p, I64, vp, vp, C.POINTER(I64),
                                                  C.POINTER(C.c_int)]
+            L.orc_rsurf_hermite.argtypes = [C.c_int, C.c_int, _f64p, _f64p]
+            L.orc_rsurf_bound2.restype = D
+            L.orc_rsurf_bound2.argtypes = [C.c_int, C.c_int, _f64p, _f64p]
             L.orc_project_curves.argtypes = [I64, _i32p, _i64p, _f64p, _i64p, _f64p, vp, I64, _i32p, _f64p,
                                              _f64p, _f64p, C.c_int]
             L.orc_rspan_bezier.argtypes = [C.c_int, _f64p, I64, _f64p, _f64p, I64, _f64p, I64, C.POINTER(I64)]
@@ -274,6 +277,22 @@ def curve_deriv_bounds(p, U, P, w, q):
     return V.value, A.value
 
 
+def rsurf_hermite(H):
+    """Bicubic Hermite patch [4][4][3] of the rational piece H [pu+1][pv+1][4]."""
+    H = _a(H, np.float64)
+    R = np.zeros(48)
+    rc = lib().orc_rsurf_hermite(H.shape[0] - 1, H.shape[1] - 1, H.reshape(-1), R)
+    assert rc == OK
+    return R.reshape(4, 4, 3)
+
+
+def rsurf_bound2(H, R):
+    """Certified bound of max |S - R|^2 for the rational piece H and the bicubic R."""
+    H = _a(H, np.float64)
+    return float(lib().orc_rsurf_bound2(H.shape[0] - 1, H.shape[1] - 1, H.reshape(-1),
+                                        _a(R, np.float64).reshape(-1)))
+
+
 class Decomposition:
     """seg_off [n+1], ctrl [nseg][4][3] (surfaces [nseg][4][4][3]), prange [nseg][2] ([nseg][4])."""
 
@@ -314,7 +333,9 @@ def decompose_surfaces(ss, tol_rel, count_only=False):
     seg_off = np.zeros(n + 1, dtype=np.int64)
     tot = C.c_int64()
     md = C.c_int()
-    rc = lib().orc_decompose_surfaces(*args, float(tol_rel), seg_off, 0, None, None, C.byref(tot), C.byref(md))
+    w, wp = _weights(ss)
+    rc = lib().orc_decompose_surfaces(*args, wp, float(tol_rel), seg_off, 0, None, None, C.byref(tot),
+                                      C.byref(md))
     if rc == EINVAL:
         raise ValueError("invalid surface set")
     if count_only:
@@ -322,8 +343,8 @@ def decompose_surfaces(ss, tol_rel, count_only=False):
     cap = max(tot.value, 1)
     ctrl = np.zeros(cap * 48)
     prange = np.zeros(cap * 4)
-    rc = lib().orc_decompose_surfaces(*args, float(tol_rel), seg_off, cap, ctrl.ctypes.data, prange.ctypes.data,
-                                      C.byref(tot), C.byref(md))
+    rc = lib().orc_decompose_surfaces(*args, wp, float(tol_rel), seg_off, cap, ctrl.ctypes.data,
+                                      prange.ctypes.data, C.byref(tot), C.byref(md))
     assert rc in (OK, ENOTCONV), rc
     n_s = tot.value
     return Decomposition(seg_off, ctrl[: n_s * 48].reshape(n_s, 4, 4, 3), prange[: n_s * 4].reshape(n_s, 4),

@@ -207,3 +207,121 @@ def test_equal_weights_give_non_rational_surfaces():
     _, d0 = O.project_surfaces(ss, sq.proj_surf, q)
     _, d1 = O.project_surfaces(rat, sq.proj_surf, q)
     assert np.allclose(d0, d1, rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------- homogeneous decomposition
+
+def rbez2(H, u, v):
+    """Explicit rational tensor Bernstein sum of the homogeneous net H
+    [pu+1][pv+1][4] at parameter arrays u, v of equal length."""
+    import math
+    H = np.asarray(H)
+    pu, pv = H.shape[0] - 1, H.shape[1] - 1
+    u, v = np.atleast_1d(u), np.atleast_1d(v)
+    Bu = np.stack([math.comb(pu, i) * u ** i * (1 - u) ** (pu - i) for i in range(pu + 1)], 1)
+    Bv = np.stack([math.comb(pv, j) * v ** j * (1 - v) ** (pv - j) for j in range(pv + 1)], 1)
+    S = np.einsum("ki,kj,ijc->kc", Bu, Bv, H)
+    return S[:, :3] / S[:, 3:]
+
+
+def bicubic(R, u, v):
+    import math
+    Bu = np.stack([math.comb(3, i) * u ** i * (1 - u) ** (3 - i) for i in range(4)], 1)
+    Bv = np.stack([math.comb(3, j) * v ** j * (1 - v) ** (3 - j) for j in range(4)], 1)
+    return np.einsum("ki,kj,ijc->kc", Bu, Bv, R)
+
+
+def random_rnet(rng, pu, pv, wlo=0.2, whi=5.0):
+    P = rng.uniform(-1, 1, size=(pu + 1, pv + 1, 3))
+    w = np.exp(rng.uniform(np.log(wlo), np.log(whi), size=(pu + 1, pv + 1)))
+    return np.concatenate([P * w[..., None], w[..., None]], axis=2)
+
+
+def test_bicubic_hermite_matches_corner_values_partials_twists():
+    rng = np.random.default_rng(31)
+    h = 1e-5
+    for pu in range(1, 5):
+        for pv in range(1, 5):
+            H = random_rnet(rng, pu, pv)
+            R = O.rsurf_hermite(H)
+            for cu in (0.0, 1.0):
+                for cv in (0.0, 1.0):
+                    su, sv = (1.0 if cu == 0 else -1.0), (1.0 if cv == 0 else -1.0)
+                    i0, i1 = (0, 1) if cu == 0 else (3, 2)
+                    j0, j1 = (0, 1) if cv == 0 else (3, 2)
+                    f = lambda du, dv: rbez2(H, np.array([cu + su * du]), np.array([cv + sv * dv]))[0]
+                    assert np.allclose(R[i0, j0], f(0, 0), atol=1e-14)
+                    # one-sided second-order differences into the piece
+                    fu = (-3 * f(0, 0) + 4 * f(h, 0) - f(2 * h, 0)) / (2 * h)
+                    fv = (-3 * f(0, 0) + 4 * f(0, h) - f(0, 2 * h)) / (2 * h)
+                    # second-order one-sided stencil in both directions
+                    cst = (-3.0, 4.0, -1.0)
+                    fuv = sum(cst[a] * cst[b] * f(a * h, b * h) for a in range(3) for b in range(3)) / (4 * h * h)
+                    sc = 1 + np.abs(fu).max() + np.abs(fv).max()
+                    assert np.abs(3 * (R[i1, j0] - R[i0, j0]) - fu).max() <= 1e-5 * sc, (pu, pv, cu, cv)
+                    assert np.abs(3 * (R[i0, j1] - R[i0, j0]) - fv).max() <= 1e-5 * sc, (pu, pv, cu, cv)
+                    twist = 9 * (R[i1, j1] - R[i1, j0] - R[i0, j1] + R[i0, j0])
+                    assert np.abs(twist - fuv).max() <= 1e-4 * (1 + np.abs(fuv).max()), (pu, pv, cu, cv)
+
+
+def test_surface_bound_covers_sampled_deviation():
+    rng = np.random.default_rng(32)
+    g = np.linspace(0.0, 1.0, 41)
+    uu, vv = np.meshgrid(g, g, indexing="ij")
+    u, v = uu.ravel(), vv.ravel()
+    for pu in range(1, 5):
+        for pv in range(1, 5):
+            for _ in range(4):
+                H = random_rnet(rng, pu, pv)
+                R = O.rsurf_hermite(H)
+                b2 = O.rsurf_bound2(H, R)
+                dev = np.linalg.norm(rbez2(H, u, v) - bicubic(R, u, v), axis=1).max()
+                assert dev ** 2 <= b2 * (1 + 1e-9) + 1e-28, (pu, pv, dev, np.sqrt(b2))
+    # the net scaled by a constant is the same surface: same patch, same bound
+    for pu, pv in ((1, 1), (2, 3), (4, 2)):
+        H = random_rnet(rng, pu, pv)
+        R = O.rsurf_hermite(H)
+        for lam in (1e-2, 1e3):
+            assert np.allclose(O.rsurf_hermite(lam * H), R, rtol=1e-12, atol=1e-13)
+            assert np.isclose(O.rsurf_bound2(lam * H, R), O.rsurf_bound2(H, R), rtol=1e-9)
+    # a polynomial piece of degree <= 3 is its own Hermite patch: bound ~0
+    for pu, pv in ((1, 2), (3, 3), (2, 3)):
+        P = rng.uniform(-1, 1, size=(pu + 1, pv + 1, 3))
+        H = np.concatenate([2.0 * P, np.full((pu + 1, pv + 1, 1), 2.0)], axis=2)
+        R = O.rsurf_hermite(H)
+        assert O.rsurf_bound2(H, R) <= 1e-28
+        assert np.abs(bicubic(R, u, v) - rbez2(H, u, v)).max() <= 1e-14
+
+
+@pytest.mark.parametrize("which,tol", [("random", 1e-3), ("cylinders", 1e-7)])
+def test_rational_surface_decomposition_within_tolerance(which, tol):
+    if which == "random":
+        ss, _ = synth.nurbs_surface_set(seed=15, n_surf=3, n_proj=1, deg_range=(2, 3), n_range=(5, 7))
+    else:
+        ss = synth.nurbs_cylinders(seed=16, n_surf=3, n_proj=1)[0]
+    dec = O.decompose_surfaces(ss, tol)
+    assert dec.status == 0
+    diag = O.surface_diag(ss)
+    g = np.linspace(0.0, 1.0, 9)
+    uu, vv = np.meshgrid(g, g, indexing="ij")
+    u, v = uu.ravel(), vv.ravel()
+    worst = 0.0
+    for s in range(ss.n):
+        area = 0.0
+        for k in range(dec.seg_off[s], dec.seg_off[s + 1]):
+            u0, u1, v0, v1 = dec.prange[k]
+            area += (u1 - u0) * (v1 - v0)
+            S = O.eval_surfaces(ss, np.full(len(u), s, np.int32),
+                                np.stack([u0 + u * (u1 - u0), v0 + v * (v1 - v0)], 1))[0]
+            worst = max(worst, np.linalg.norm(S - bicubic(dec.ctrl[k], u, v), axis=1).max() / (tol * diag[s]))
+        assert abs(area - 1.0) <= 1e-12  # the patches tile the domain
+    assert worst <= 1.0 + 1e-9, worst
+
+
+def test_equal_weights_decompose_as_non_rational():
+    ss, _ = synth.surface_set(seed=17, n_surf=3, n_proj=1, n_inv=0, deg_range=(2, 4), n_range=(6, 8))
+    rat = synth.SurfaceSet(ss.deg_u, ss.deg_v, ss.n_u, ss.n_v, ss.knot_u_off, ss.knots_u, ss.knot_v_off,
+                           ss.knots_v, ss.cp_off, ss.cps, np.full(len(ss.cps), 3.0))
+    d0, d1 = O.decompose_surfaces(ss, 1e-4), O.decompose_surfaces(rat, 1e-4)
+    assert np.array_equal(d0.seg_off, d1.seg_off)
+    assert np.array_equal(d0.ctrl, d1.ctrl) and np.array_equal(d0.prange, d1.prange)

@@ -6,7 +6,9 @@ class (1..7, 8..31, 32..63), non-rational and rational:
 * the whole query path emulated: the minimum of the decomposed cubics (the
   oracle's decomposition, searched here by sampling and Newton on the cubic,
   as the query kernels do), then the refinement from it, within 1e-9 x diag
-  of the oracle's projection on every query.  At degrees 8 and above the
+  of the oracle's projection on every query;
+* from those starts, the refinement converges in about two evaluations and
+  never ends farther than it started (beyond rounding).  At degrees 8 and above the
   cubics come from the blossom extraction; with the matrix route the
   degree-31 curve's cubics were off by about 1e-2 of the control points'
   size and a query's refined distance by 2.8e-3 x diag.
@@ -157,3 +159,44 @@ def test_query_path_emulated_then_refined_matches_oracle(hr, rational):
         worst = max(worst, err)
         assert err <= 1e-9, (c, p, int(k), err, t.value)
     assert worst <= 1e-9
+
+
+def test_refinement_settles_in_about_two_evaluations(hr):
+    """From the query path's answer (emulated as above) on the curve-set
+    recipe, non-rational and rational, projections and inversions: the
+    refinement converges, taking about two evaluations per query (the start
+    and one Newton step, whose change of D is within D's rounding), and
+    never ends farther than its start beyond that rounding."""
+    for make in (synth.curve_set, synth.nurbs_curve_set):
+        cs, qs = make(seed=61, n_curves=24, n_proj=300, n_inv=300, ncp_range=(8, 20))
+        dec = O.decompose_curves(cs, 1e-10)
+        inv_pts = O.eval_curves(cs, qs.inv_curve, qs.inv_t)[0]
+        qc = np.concatenate([qs.proj_curve, qs.inv_curve])
+        q = np.concatenate([qs.proj_xyz, inv_pts])
+        evals, conv = [], []
+        u = np.linspace(0.0, 1.0, 33)
+        B = np.stack([math.comb(3, i) * u ** i * (1 - u) ** (3 - i) for i in range(4)], 1)
+        for k in range(len(qc)):
+            c = int(qc[k])
+            p, U, P, w = curve_arrays(cs, c)
+            s0, s1 = dec.seg_off[c], dec.seg_off[c + 1]
+            pts = np.einsum("ui,sic->suc", B, dec.ctrl[s0:s1])
+            dmin = ((pts - q[k]) ** 2).sum(2).min(1)
+            best = (np.inf, 0.0)
+            for s in np.argsort(dmin)[:4]:
+                x, d2 = cubic_minimum(dec.ctrl[s0 + s], q[k])
+                if d2 < best[0]:
+                    t0, t1 = dec.prange[s0 + s]
+                    best = (d2, t0 + x * (t1 - t0))
+            t = ctypes.c_double(best[1])
+            Dv, nev = ctypes.c_double(), ctypes.c_int()
+            qq = np.ascontiguousarray(q[k])
+            C0 = O.eval_curves(cs, np.array([c], np.int32), np.array([best[1]]))[0][0]
+            d_start = np.linalg.norm(C0 - q[k])
+            ok = hr.hr_refine(p, dp(U), len(P) - 1, dp(P), None if w is None else w.ctypes.data, dp(qq), 16,
+                              ctypes.byref(t), ctypes.byref(Dv), ctypes.byref(nev))
+            assert math.sqrt(Dv.value) <= d_start + 1e-14 * (1 + d_start)
+            evals.append(nev.value)
+            conv.append(ok)
+        assert all(conv)
+        assert np.mean(evals) <= 2.3 and max(evals) <= 14, (make.__name__, np.mean(evals), max(evals))

@@ -326,8 +326,10 @@ __host__ __device__ __forceinline__ void curve_d2(const double* U, const double*
 // the domain, or q lies on the curve to the rounding of its coordinates.  A
 // full Newton step that changes D by no more than D's rounding is taken and
 // ends the iteration (D cannot resolve it; halving it would only spend
-// evaluations).  The result's distance never exceeds the start's by more
-// than that rounding.
+// evaluations).  A full step that raises D and leaves the span of t is
+// first replaced by the knot it crossed (D has a kink at a C0 joint, and a
+// minimum on or just across it is out of the span polynomial's reach).  The
+// result's distance never exceeds the start's by more than that rounding.
 //
 // refine_one: the refinement of one query on a curve of degree p <= MP;
 // returns whether it converged, with the final t and squared distance D.
@@ -415,6 +417,28 @@ __host__ __device__ __noinline__ bool refine_one(const double* __restrict__ U, c
                     took = true;
                     break;
                 }
+                // the full step left the span of t: its model (the span's
+                // polynomial) ends at the knot it crossed, where D may have a
+                // kink (a C0 joint); that knot is tried before the halvings
+                const int q0 = span_of(U, p, m, t);
+                const double kn = tn > U[q0 + 1] ? U[q0 + 1] : (tn < U[q0] && U[q0] < t ? U[q0] : t);
+                if (kn != t) {
+                    double Ck[3], C1k[3];
+                    curve_d2<MP, NC, false>(U, P, w, p, m, kn, S, Ck, C1k, nullptr);
+                    ++nev1;
+                    double Dk = 0.0;
+                    for (int k = 0; k < 3; ++k) Dk += (Ck[k] - q[k]) * (Ck[k] - q[k]);
+                    if (Dk <= D) {
+                        tn = kn;
+                        Dn = Dk;
+                        for (int k = 0; k < 3; ++k) {
+                            Cn[k] = Ck[k];
+                            C1n[k] = C1k[k];
+                        }
+                        took = true;
+                        break;
+                    }
+                }
             }
         }
         if (!took) {  // no step decreases the distance: t is a minimum to rounding
@@ -482,7 +506,7 @@ __device__ __forceinline__ int refine_query(const bspl_curves& Cv, const double*
 
 // thread k refines query order[k] (queries grouped by curve), or query k
 template <int NC>
-__global__ void k_refine_curves(bspl_curves Cv, const double* __restrict__ diag, int invert, int64_t n_q,
+__global__ void __launch_bounds__(128, 4) k_refine_curves(bspl_curves Cv, const double* __restrict__ diag, int invert, int64_t n_q,
                                 const int32_t* __restrict__ qc, const double* __restrict__ q_xyz, int max_iter,
                                 double* __restrict__ t_io, double* __restrict__ d_io, uint8_t* __restrict__ st_io,
                                 unsigned long long* __restrict__ evals, const int32_t* __restrict__ order,

@@ -200,3 +200,35 @@ def test_refinement_settles_in_about_two_evaluations(hr):
             conv.append(ok)
         assert all(conv)
         assert np.mean(evals) <= 2.3 and max(evals) <= 14, (make.__name__, np.mean(evals), max(evals))
+
+
+def test_refinement_reaches_minima_at_c0_joints(hr):
+    """Starts a short way (1e-9 and 1e-6 of the domain, either side) from
+    minima that lie on or next to a C0 joint (a knot of full multiplicity,
+    where D has a kink): the refinement reaches them.  (The full Newton step
+    from the far side of the joint overshoots it; the knot it crossed is
+    tried as well.)"""
+    cs = high_set(False)
+    p, U, P, w = curve_arrays(cs, 0)  # the cubic with a triple interior knot
+    inner, counts = np.unique(U[p + 1:len(P)], return_counts=True)
+    joints = inner[counts >= p]
+    assert len(joints) >= 1
+    rng = np.random.default_rng(53)
+    rng.uniform(0.0, 1.0, 3000)
+    qc = np.repeat(np.arange(cs.n, dtype=np.int32), 500)
+    lo, hi = synth.cp_boxes(cs)
+    q = synth._box_queries(rng, lo, hi, qc, scale=1.3)
+    sel = np.where(qc == 0)[0]
+    t_o, d_o = O.project_curves(cs, qc[sel], q[sel])
+    near = np.min(np.abs(t_o[:, None] - joints[None, :]), axis=1) <= 1e-5
+    assert near.sum() >= 5
+    diag = O.curve_diag(cs)[0]
+    for k in np.where(near)[0]:
+        qq = np.ascontiguousarray(q[sel[k]])
+        for off in (-1e-6, -1e-9, 1e-9, 1e-6):
+            t = ctypes.c_double(min(max(t_o[k] + off, U[p]), U[len(P)]))
+            Dv, nev = ctypes.c_double(), ctypes.c_int()
+            hr.hr_refine(p, dp(U), len(P) - 1, dp(P), None, dp(qq), 16, ctypes.byref(t), ctypes.byref(Dv),
+                         ctypes.byref(nev))
+            err = abs(math.sqrt(Dv.value) - d_o[k]) / diag
+            assert err <= 1e-9, (int(k), off, err, t.value, t_o[k])

@@ -397,10 +397,11 @@ bspl_status bspl_eval_surfaces(const bspl_surfaces* surfaces, int64_t n_q, const
  * original knots and control points (rational curves: on the homogeneous
  * points, then C = A/W, C' = (A' - W'C)/W, C'' = (A'' - 2W'C' - W''C)/W, the
  * quotient rule: rational Newton); every step is clamped to the domain and
- * halved (at most 12 times) until the squared distance does not grow, until
- * E is zero to its FP64 rounding, the step falls below the resolution of t
- * or the distance stops decreasing.  At most max_iter steps (0: 16; at most
- * 100).
+ * halved (at most 12 times) until the squared distance does not grow (a full
+ * step that leaves the knot span of t is first replaced by the knot it
+ * crossed, where a C0 joint may hold the minimum), until E is zero to its
+ * FP64 rounding, the step falls below the resolution of t or the distance
+ * stops decreasing.  At most max_iter steps (0: 16; at most 100).
  *   in/out  t [n_q], dist [n_q]: the refined parameter and |C(t) - q|, never
  *           larger than the distance at the starting t beyond the FP64
  *           rounding of the squared distance (a full Newton step whose

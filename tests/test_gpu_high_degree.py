@@ -68,3 +68,35 @@ def test_high_degree_curves_vs_oracle(rational):
     bspl.bspl_refine_curves(dc, qc, pts, ri, invert=True, diag=segs.diag)
     torch.cuda.synchronize()
     assert np.all(ri.dist.cpu().numpy() <= 1e-9 * diag)
+
+
+def test_refine_reaches_minima_at_c0_joints():
+    """Starts 1e-9 and 1e-6 either side of minima on or next to the C0 joint
+    of the cubic in the set above: the refinement (through the C ABI) ends
+    within 1e-9 x diag of the oracle (the full step from the far side of the
+    joint is first replaced by the knot it crossed)."""
+    cs = high_set(False)
+    p, U, P = cs.curve(0)
+    inner, counts = np.unique(U[p + 1:len(P)], return_counts=True)
+    joints = inner[counts >= p]
+    assert len(joints) >= 1
+    rng = np.random.default_rng(53)
+    rng.uniform(0.0, 1.0, 3000)
+    qc_all = np.repeat(np.arange(cs.n, dtype=np.int32), 500)
+    lo, hi = synth.cp_boxes(cs)
+    q_all = synth._box_queries(rng, lo, hi, qc_all, scale=1.3)
+    sel = np.where(qc_all == 0)[0]
+    t_o, d_o = O.project_curves(cs, qc_all[sel], q_all[sel])
+    near = np.where(np.min(np.abs(t_o[:, None] - joints[None, :]), axis=1) <= 1e-5)[0]
+    assert len(near) >= 5
+    offs = np.array([-1e-6, -1e-9, 1e-9, 1e-6])
+    t0 = np.clip(np.repeat(t_o[near], 4) + np.tile(offs, len(near)), U[p], U[len(P)])
+    q = np.repeat(q_all[sel][near], 4, axis=0)
+    dc = bspl.DeviceCurves(cs, DEV)
+    qc = dev(np.zeros(len(t0), np.int32), torch.int32)
+    r = bspl.QueryResult(dev(t0, torch.float64), dev(np.zeros(len(t0)), torch.float64),
+                         dev(np.zeros(len(t0), np.uint8), torch.uint8))
+    bspl.bspl_refine_curves(dc, qc, dev(q, torch.float64), r)
+    torch.cuda.synchronize()
+    err = np.abs(r.dist.cpu().numpy() - np.repeat(d_o[near], 4)) / O.curve_diag(cs)[0]
+    assert err.max() <= 1e-9, (int((err > 1e-9).sum()), err.max())
